@@ -1,0 +1,189 @@
+"""ctypes wrapper of the FP64 oracle library (``libcog_oracle.so``).
+
+Test infrastructure only.  The wrapper marshals numpy arrays; every step of
+the method runs in ``cog_oracle.c``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cog_oracle.c")
+_LIB = os.path.join(_HERE, "libcog_oracle.so")
+
+ORC_FD, ORC_RGA, ORC_CONF, ORC_ILLUM = 1, 2, 4, 8
+NEAR_BITS = {"fd": 1, "rga": 2, "match": 4, "bgset": 8, "rank": 16, "halt": 32}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build_oracle(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP when available).  FP contraction
+    is off so x86 and Arm give the same FP64 results."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "cog_oracle.h"))):
+        return _LIB
+    base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+            "-fno-fast-math", "-o", _LIB + ".tmp", _SRC, "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
+                       capture_output=True, text=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True, text=True)
+    os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+class _Params(C.Structure):
+    _fields_ = [
+        ("width", C.c_int), ("height", C.c_int), ("K", C.c_int),
+        ("alpha", C.c_double), ("lambda_", C.c_double), ("T_bg", C.c_double),
+        ("w_init", C.c_double), ("var_init", C.c_double), ("var_min", C.c_double),
+        ("var_max", C.c_double), ("tau_fd", C.c_double), ("eta", C.c_double),
+        ("c_halt", C.c_double), ("w_illum", C.c_double),
+        ("q_null", C.c_int), ("kde_bw", C.c_int), ("r1", C.c_int), ("r2", C.c_int),
+        ("illum_permille", C.c_int), ("flags", C.c_uint),
+    ]
+
+
+class _State(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in (
+        "w", "mu", "var", "rga_m", "rga_v", "conf", "label", "prev", "kde",
+        "qa", "qb", "illum")]
+
+
+class _Stats(C.Structure):
+    _fields_ = [("n_stage", C.c_int64 * 5), ("n_gmm", C.c_int64),
+                ("illum_flag", C.c_int32), ("pad", C.c_int32)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build_oracle()
+            lib = C.CDLL(_LIB)
+            lib.orc_kde_weights.argtypes = [C.c_int, C.c_void_p, C.c_int]
+            lib.orc_kde_weights.restype = C.c_int
+            lib.orc_train.argtypes = [C.POINTER(_Params), C.c_void_p, C.c_int, C.POINTER(_State)]
+            lib.orc_train.restype = C.c_int
+            lib.orc_apply.argtypes = [C.POINTER(_Params), C.POINTER(_State), C.c_void_p,
+                                      C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(_Stats)]
+            lib.orc_apply.restype = C.c_int
+            lib.orc_plain_gmm.argtypes = [C.POINTER(_Params)] + [C.c_void_p] * 5
+            lib.orc_plain_gmm.restype = C.c_int
+            lib.orc_threads.restype = C.c_int
+            _lib = lib
+    return _lib
+
+
+def oracle_threads() -> int:
+    return int(_load().orc_threads())
+
+
+def default_params(width: int, height: int, K: int = 3) -> dict:
+    """The oracle's own copy of the default constants (the paper states
+    none; these are the readings recorded in the design notes)."""
+    return dict(width=width, height=height, K=K, alpha=0.01, lambda_=2.5, T_bg=0.7,
+                w_init=0.05, var_init=225.0, var_min=4.0, var_max=900.0, tau_fd=8.0,
+                eta=0.125, c_halt=0.9, w_illum=0.75, q_null=13, kde_bw=4, r1=10, r2=30,
+                illum_permille=700, flags=ORC_FD | ORC_RGA | ORC_CONF | ORC_ILLUM)
+
+
+def _params(p: dict) -> _Params:
+    q = _Params()
+    for name, _ in _Params._fields_:
+        key = "lambda" if name == "lambda_" and "lambda" in p else name
+        setattr(q, name, p[key])
+    return q
+
+
+def kde_weights(bw: int) -> np.ndarray:
+    g = np.zeros(3 * bw + 1, dtype=np.int64)
+    r = _load().orc_kde_weights(bw, g.ctypes.data, g.size)
+    if r < 0:
+        raise ValueError("bad bandwidth")
+    return g
+
+
+class OracleState:
+    """FP64 model state of P pixels (numpy arrays the C code writes into)."""
+
+    def __init__(self, P: int, K: int):
+        self.P, self.K = P, K
+        self.w = np.zeros((P, K))
+        self.mu = np.zeros((P, K, 3))
+        self.var = np.zeros((P, K, 3))
+        self.rga_m = np.zeros((P, 3))
+        self.rga_v = np.zeros((P, 3))
+        self.conf = np.zeros(P)
+        self.label = np.zeros(P, np.uint8)
+        self.prev = np.zeros((P, 3), np.uint8)
+        self.kde = np.zeros((P, 3, 256), np.uint8)
+        self.qa = np.zeros(P, np.uint8)
+        self.qb = np.zeros(P, np.uint8)
+        self.illum = np.zeros(1, np.int64)
+
+    def _c(self) -> _State:
+        s = _State()
+        for n, _ in _State._fields_:
+            a = getattr(self, n)
+            assert a.flags.c_contiguous
+            setattr(s, n, a.ctypes.data)
+        return s
+
+    def copy(self) -> "OracleState":
+        o = OracleState(self.P, self.K)
+        for n, _ in _State._fields_:
+            getattr(o, n)[...] = getattr(self, n)
+        return o
+
+
+class Oracle:
+    """One FP64 model of a W x H stream."""
+
+    def __init__(self, params: dict):
+        self.p = dict(params)
+        self.P = int(params["width"]) * int(params["height"])
+        self.K = int(params["K"])
+        self.state = OracleState(self.P, self.K)
+        self._cp = _params(self.p)
+        self.lib = _load()
+
+    def train(self, frames: np.ndarray) -> None:
+        f = np.ascontiguousarray(frames, dtype=np.uint8).reshape(-1, self.P, 3)
+        s = self.state._c()
+        if self.lib.orc_train(C.byref(self._cp), f.ctypes.data, f.shape[0], C.byref(s)) != 0:
+            raise ValueError("orc_train rejected its arguments")
+
+    def apply(self, frame: np.ndarray, want_stage: bool = True, want_near: bool = True):
+        f = np.ascontiguousarray(frame, dtype=np.uint8).reshape(self.P, 3)
+        mask = np.empty(self.P, np.uint8)
+        stage = np.empty(self.P, np.uint8) if want_stage else None
+        near = np.empty(self.P, np.uint8) if want_near else None
+        st = _Stats()
+        s = self.state._c()
+        r = self.lib.orc_apply(C.byref(self._cp), C.byref(s), f.ctypes.data, mask.ctypes.data,
+                               stage.ctypes.data if stage is not None else None,
+                               near.ctypes.data if near is not None else None, C.byref(st))
+        if r != 0:
+            raise ValueError("orc_apply rejected its arguments")
+        stats = dict(n_stage=list(st.n_stage), n_gmm=int(st.n_gmm), illum_flag=int(st.illum_flag))
+        return mask, stage, near, stats
+
+    def plain_gmm(self, w: np.ndarray, mu: np.ndarray, var: np.ndarray, frame: np.ndarray):
+        for a in (w, mu, var):
+            assert a.dtype == np.float64 and a.flags.c_contiguous
+        f = np.ascontiguousarray(frame, dtype=np.uint8).reshape(self.P, 3)
+        mask = np.empty(self.P, np.uint8)
+        r = self.lib.orc_plain_gmm(C.byref(self._cp), w.ctypes.data, mu.ctypes.data,
+                                   var.ctypes.data, f.ctypes.data, mask.ctypes.data)
+        if r != 0:
+            raise ValueError("orc_plain_gmm rejected its arguments")
+        return mask

@@ -1,0 +1,410 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Every expected value here comes from a closed form, an invariant, a
+brute-force evaluation of a definition, or a hand-worked case whose
+arithmetic is written out beside it -- never from the oracle itself and
+never from the CUDA path.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import ORC_CONF, ORC_FD, ORC_ILLUM, ORC_RGA, Oracle, default_params, kde_weights
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+ALL = ORC_FD | ORC_RGA | ORC_CONF | ORC_ILLUM
+
+
+def _golden_ints(name):
+    with open(os.path.join(GOLD, name)) as f:
+        rows = [l for l in f if l.strip() and not l.startswith("#")]
+    return [int(x) for x in rows[0].split()]
+
+
+def one_pixel(K=3, flags=0, **over):
+    p = default_params(1, 1, K)
+    p.update(flags=flags, **over)
+    return Oracle(p)
+
+
+# --------------------------------------------------------------------- KDE
+def test_kde_weights_match_rational_taylor_table():
+    # Sec. 2 scene prior: Gaussian kernel, bandwidth 4, 3-bandwidth support
+    assert list(kde_weights(4)) == _golden_ints("kde_weights_bw4.txt")
+
+
+def test_kde_weights_semigroup_property():
+    # exp(-a) exp(-b) = exp(-(a+b)): 3-4-5 and 6-8-10 triangles
+    g = kde_weights(4)
+    assert abs(g[3] * g[4] / 65536 - g[5]) <= 1.0
+    assert abs(g[6] * g[8] / 65536 - g[10]) <= 1.0
+
+
+@pytest.mark.parametrize("v", [0, 3, 100, 250, 255])
+def test_kde_of_constant_training_is_the_normalised_kernel(v):
+    # all N training values equal v: k = N g[|u - v|], peak N g[0]
+    o = one_pixel()
+    frames = np.full((6, 1, 3), v, np.uint8)
+    o.train(frames)
+    g = kde_weights(4)
+    for c in range(3):
+        q = o.state.kde[0, c]
+        for u in range(256):
+            d = abs(u - v)
+            exp = (255 * int(g[d]) + int(g[0]) // 2) // int(g[0]) if d <= 12 else 0
+            assert q[u] == exp, (u, v)
+
+
+def test_kde_bruteforce_direct_sum_over_samples():
+    # the density at v is a sum over the training samples of g[|v - I_t|];
+    # evaluated here sample by sample instead of through a histogram
+    rng = np.random.default_rng(7)
+    g = [int(x) for x in kde_weights(4)]
+    for trial in range(20):
+        N = int(rng.integers(2, 5))
+        frames = rng.integers(0, 256, (N, 1, 3), dtype=np.uint8)
+        if trial % 3 == 0:
+            frames = np.clip(frames // 8 + 120, 0, 255).astype(np.uint8)
+        o = one_pixel()
+        o.train(frames)
+        for c in range(3):
+            k = [sum(g[abs(v - int(frames[t, 0, c]))] if abs(v - int(frames[t, 0, c])) <= 12 else 0
+                     for t in range(N)) for v in range(256)]
+            M = max(k)
+            exp = [(255 * x + M // 2) // M for x in k]
+            assert list(o.state.kde[0, c]) == exp
+
+
+# ---------------------------------------------------------------- residues
+def test_residue_classes_crafted_sequence():
+    # Sec. 2 residue classes: R_t = max_c |I_t - I_{t-1}|; r1 = 10, r2 = 30.
+    # channel-0 sequence: steps 0, 10, 11, 30, 31, 255 and back down 255, then 0s
+    seq = [100, 100, 110, 121, 151, 182, 0, 255, 255, 255, 255]
+    # residues: 0,10,11,30,31,182,255,0,0,0  -> n0 = 5 (0,10,0,0,0), n1 = 2 (11,30),
+    # n2 = 3 (31,182,255); N-1 = 10
+    frames = np.zeros((len(seq), 1, 3), np.uint8)
+    frames[:, 0, 0] = seq
+    frames[:, 0, 1] = 50          # other channels constant: residue 0
+    o = one_pixel()
+    o.train(frames)
+    assert o.state.qa[0] == (255 * 5 + 5) // 10 == 128
+    assert o.state.qb[0] == (255 * 3 + 5) // 10 == 77
+
+
+def test_residue_weights_clamped_to_sum_255():
+    # n0 = n2 = 1 of N-1 = 2: both round up to 128; b is clamped to 255 - a
+    frames = np.zeros((3, 1, 3), np.uint8)
+    frames[:, 0, 0] = [10, 10, 200]
+    o = one_pixel()
+    o.train(frames)
+    assert o.state.qa[0] == 128 and o.state.qb[0] == 127
+
+
+# ------------------------------------------------------ mixture closed forms
+def test_static_pixel_variance_decay():
+    # stages and confidence off, noiseless constant input: always background,
+    # omega = (1, 0, 0) exactly, v_0 after n updates = max(v_min, v_init (1-a)^n)
+    p = default_params(1, 1, 3)
+    p["flags"] = 0
+    o = Oracle(p)
+    o.train(np.full((40, 1, 3), 90, np.uint8))
+    n = 39
+    for i in range(400):
+        m, _, _, _ = o.apply(np.full((1, 3), 90, np.uint8))
+        n += 1
+        assert m[0] == 0
+        assert list(o.state.w[0]) == [1.0, 0.0, 0.0]
+        exp = max(p["var_min"], p["var_init"] * (1 - p["alpha"]) ** n)
+        assert np.allclose(o.state.var[0, 0], exp, rtol=1e-12, atol=0)
+
+
+def test_step_absorption_time():
+    # a step from 100 to 200: no mode matches, so the pixel is foreground and
+    # the weakest mode restarts at 200 with weight w_init; the old mode keeps
+    # omega' = (1-a)/((1-a)+w_init) and decays by (1-a) per frame.  The pixel
+    # turns background once the weight ranked before the new mode is <= T:
+    # first at j = 1 + ceil(ln(T/omega') / ln(1-a)) frames after the step.
+    p = default_params(1, 1, 3)
+    p["flags"] = 0
+    a, T, wi = p["alpha"], p["T_bg"], p["w_init"]
+    wp = (1 - a) / ((1 - a) + wi)
+    j_exp = 1 + math.ceil(math.log(T / wp) / math.log(1 - a))
+    assert j_exp == 32
+    for flags in (0, ORC_FD | ORC_RGA):
+        p["flags"] = flags
+        o = Oracle(p)
+        o.train(np.full((300, 1, 3), 100, np.uint8))
+        labels, stages = [], []
+        for j in range(j_exp + 5):
+            m, st, _, _ = o.apply(np.full((1, 3), 200, np.uint8))
+            labels.append(int(m[0]))
+            stages.append(int(st[0]))
+        first_bg = labels.index(0)
+        assert first_bg == j_exp
+        assert all(x == 255 for x in labels[:first_bg])
+        assert all(x == 0 for x in labels[first_bg:])
+        if flags:
+            # afterwards the value repeats, so the pixel leaves at stage 0
+            assert stages[first_bg] == 2 and all(s == 0 for s in stages[first_bg + 1:])
+
+
+def test_weights_stay_normalised():
+    from cogsynth import Scene
+    sc = Scene(24, 16, 11, kind="dynamic", n_train=30, fg_frac=0.1, switch_at=20)
+    p = default_params(24, 16, 5)
+    p["flags"] = ALL
+    o = Oracle(p)
+    tr, _ = sc.frames(0, 30)
+    o.train(tr)
+    for t in range(30, 90):
+        f, _ = sc.render(t)
+        o.apply(f)
+        assert np.max(np.abs(o.state.w.sum(axis=1) - 1.0)) <= 1e-12
+        assert o.state.w.min() >= 0.0
+
+
+def test_cascade_with_everything_off_is_the_plain_mixture():
+    # the cascade is a decomposition of the GMM: with every rejection stage
+    # and modulation off it must reproduce the background-set form bit for bit
+    from cogsynth import Scene
+    sc = Scene(32, 20, 5, kind="dynamic", n_train=25, fg_frac=0.05, switch_at=10)
+    for K in (1, 3, 5):
+        p = default_params(32, 20, K)
+        p["flags"] = 0
+        o = Oracle(p)
+        tr, _ = sc.frames(0, 25)
+        o.train(tr)
+        w, mu, var = o.state.w.copy(), o.state.mu.copy(), o.state.var.copy()
+        for t in range(25, 60):
+            f, _ = sc.render(t)
+            m1, _, _, _ = o.apply(f)
+            m2 = o.plain_gmm(w, mu, var, f)
+            assert np.array_equal(m1, m2)
+            assert np.array_equal(w, o.state.w)
+            assert np.array_equal(mu, o.state.mu)
+            assert np.array_equal(var, o.state.var)
+
+
+def test_constant_input_confidence_recursion():
+    # a repeating value leaves at stage 0 with instantaneous confidence 1, so
+    # C_n = 1 - (1 - C_0)(1 - eta)^n
+    p = default_params(1, 1, 3)
+    p["flags"] = ORC_FD | ORC_CONF
+    o = Oracle(p)
+    o.train(np.full((10, 1, 3), 77, np.uint8))
+    C0 = o.state.conf[0]
+    assert C0 == 0.5
+    for n in range(1, 60):
+        _, st, _, _ = o.apply(np.full((1, 3), 77, np.uint8))
+        assert st[0] == 0
+        assert abs(o.state.conf[0] - (1 - (1 - C0) * (1 - p["eta"]) ** n)) <= 1e-12
+
+
+def test_global_jump_flags_illumination_change():
+    # > 70 % of the pixels jump by +60: foreground at the jump frame, the
+    # counter of that frame flags the next one, which is forced to background
+    W, H = 10, 10
+    p = default_params(W, H, 3)
+    p["flags"] = ALL
+    o = Oracle(p)
+    o.train(np.full((40, W * H, 3), 100, np.uint8))
+    for _ in range(5):
+        m, st, _, stats = o.apply(np.full((W * H, 3), 100, np.uint8))
+        assert (m == 0).all() and stats["illum_flag"] == 0
+    jump = np.full((W * H, 3), 100, np.uint8)
+    jump[:80] = 160                     # 80 % of the pixels
+    m, st, _, stats = o.apply(jump)
+    assert (m[:80] == 255).all() and (m[80:] == 0).all()
+    assert stats["illum_flag"] == 0 and stats["n_gmm"] == 80
+    m, st, _, stats = o.apply(jump)
+    assert stats["illum_flag"] == 1
+    assert (m == 0).all() and (st[:80] == 4).all() and (st[80:] == 0).all()
+    i = 0
+    assert o.state.w[i].max() == p["w_illum"]
+    assert abs(o.state.w[i].sum() - 1) <= 1e-12
+    # frame s+1 still had 80 pixels at the mixture stage, so s+2 is flagged as
+    # well; its pixels repeat their values and leave at stage 0 regardless
+    m, st, _, stats = o.apply(jump)
+    assert stats["illum_flag"] == 1 and (m == 0).all() and (st == 0).all()
+    m, st, _, stats = o.apply(jump)
+    assert stats["illum_flag"] == 0 and (m == 0).all() and (st == 0).all()
+
+
+def test_global_jump_below_threshold_is_not_an_illumination_change():
+    W, H = 10, 10
+    p = default_params(W, H, 3)
+    p["flags"] = ALL
+    o = Oracle(p)
+    o.train(np.full((40, W * H, 3), 100, np.uint8))
+    jump = np.full((W * H, 3), 100, np.uint8)
+    jump[:70] = 160                     # exactly 70 %: not above the threshold
+    o.apply(jump)
+    m, st, _, stats = o.apply(jump)
+    assert stats["illum_flag"] == 0 and (m[:70] == 255).all()
+
+
+def test_stage0_exit_leaves_model_untouched():
+    from cogsynth import Scene
+    sc = Scene(40, 30, 9, kind="dynamic", n_train=30, fg_frac=0.05)
+    p = default_params(40, 30, 3)
+    p["flags"] = ALL
+    o = Oracle(p)
+    tr, _ = sc.frames(0, 30)
+    o.train(tr)
+    for t in range(30, 45):
+        before = o.state.copy()
+        f, _ = sc.render(t)
+        _, st, _, _ = o.apply(f)
+        fd = st == 0
+        assert fd.sum() > 100
+        for name in ("w", "mu", "var", "rga_m", "rga_v"):
+            assert np.array_equal(getattr(before, name)[fd], getattr(o.state, name)[fd])
+        rga = st == 1
+        for name in ("w", "mu", "var"):
+            assert np.array_equal(getattr(before, name)[rga], getattr(o.state, name)[rga])
+
+
+# ------------------------------------------------------- hand-worked pixels
+def _hand_state(o, label=0, prev=(100, 100, 100)):
+    s = o.state
+    s.w[0] = [0.5, 0.3, 0.2]
+    s.mu[0] = [[100, 100, 100], [50, 50, 50], [200, 200, 200]]
+    s.var[0] = [[16, 16, 16], [4, 4, 4], [64, 64, 64]]
+    s.rga_m[0] = [100, 100, 100]
+    s.rga_v[0] = [16, 16, 16]
+    s.conf[0] = 0.5
+    s.label[0] = label
+    s.prev[0] = prev
+    s.kde[0] = 200
+    s.qa[0], s.qb[0] = 153, 51
+    s.illum[0] = 0
+
+
+HAND = dict(alpha=0.25, var_min=1.0, var_max=1000.0, var_init=100.0, w_init=0.05)
+
+
+def test_hand_gmm_match_second_ranked_is_background():
+    # keys w^2/vbar: comp0 .25/16 = .015625, comp1 .09/4 = .0225, comp2 .04/64;
+    # order 1, 0, 2.  I = (104,100,98): comp1 t = 54^2/25 >> 1; comp0 t = max(16,
+    # 0, 4)/100 = .16 < 1 -> match at rank 2; weight before = .3 <= .7 -> BG.
+    # update a = .25: w = (.75*.5+.25, .75*.3, .75*.2) = (.625, .225, .15);
+    # mu0 = (101, 100, 99.5); v0 = (.75*16 + .25*3^2, .75*16, .75*16 + .25*1.5^2)
+    #      = (14.25, 12, 12.5625); running average reseeded from comp0.
+    o = one_pixel(flags=0, **HAND)
+    _hand_state(o)
+    m, st, _, stats = o.apply(np.array([[104, 100, 98]], np.uint8))
+    assert m[0] == 0 and st[0] == 2 and stats["n_gmm"] == 1
+    np.testing.assert_allclose(o.state.w[0], [0.625, 0.225, 0.15], rtol=1e-15)
+    assert list(o.state.mu[0, 0]) == [101.0, 100.0, 99.5]
+    assert list(o.state.var[0, 0]) == [14.25, 12.0, 12.5625]
+    assert list(o.state.mu[0, 1]) == [50.0] * 3 and list(o.state.var[0, 2]) == [64.0] * 3
+    assert list(o.state.rga_m[0]) == [101.0, 100.0, 99.5]
+    assert list(o.state.rga_v[0]) == [14.25, 12.0, 12.5625]
+
+
+def test_hand_gmm_no_match_replaces_weakest():
+    # I = (0,255,0) matches nothing: FG; decay (.375,.225,.15), the lowest-ranked
+    # comp2 becomes (I, v_init=100, w_init=.05); sum .65 -> (15/26, 9/26, 2/26)
+    o = one_pixel(flags=0, **HAND)
+    _hand_state(o)
+    m, st, _, _ = o.apply(np.array([[0, 255, 0]], np.uint8))
+    assert m[0] == 255 and st[0] == 3
+    np.testing.assert_allclose(o.state.w[0], [15 / 26, 9 / 26, 2 / 26], rtol=1e-15)
+    assert list(o.state.mu[0, 2]) == [0.0, 255.0, 0.0]
+    assert list(o.state.var[0, 2]) == [100.0] * 3
+    assert list(o.state.rga_m[0]) == [100.0] * 3      # FG: running average untouched
+
+
+def test_hand_gmm_match_behind_too_much_weight_is_foreground():
+    # I = comp2's mean: match at rank 3, weight before = .3 + .5 = .8 > .7 -> FG;
+    # w = (.375, .225, .15 + .25) ; v2 = .75 * 64 = 48
+    o = one_pixel(flags=0, **HAND)
+    _hand_state(o)
+    m, st, _, _ = o.apply(np.array([[200, 200, 200]], np.uint8))
+    assert m[0] == 255 and st[0] == 3
+    np.testing.assert_allclose(o.state.w[0], [0.375, 0.225, 0.4], rtol=1e-15)
+    assert list(o.state.var[0, 2]) == [48.0] * 3
+
+
+def test_hand_rga_stage():
+    # running average (100, 16): I = (104,100,98) -> t_r = .16 < 1 -> BG at stage 1,
+    # same arithmetic as the matched mode above; the mixture is untouched
+    o = one_pixel(flags=ORC_RGA, **HAND)
+    _hand_state(o)
+    m, st, _, stats = o.apply(np.array([[104, 100, 98]], np.uint8))
+    assert m[0] == 0 and st[0] == 1 and stats["n_gmm"] == 0
+    assert list(o.state.rga_m[0]) == [101.0, 100.0, 99.5]
+    assert list(o.state.rga_v[0]) == [14.25, 12.0, 12.5625]
+    assert list(o.state.w[0]) == [0.5, 0.3, 0.2]
+
+
+def test_hand_fd_threshold_inclusive():
+    # D = 8 <= tau_fd (0.5 + 0.5) = 8 -> stage 0; D = 9 -> falls through
+    o = one_pixel(flags=ORC_FD, **HAND)
+    _hand_state(o)
+    _, st, near, _ = o.apply(np.array([[108, 95, 100]], np.uint8))
+    assert st[0] == 0 and near[0] & 1
+    _hand_state(o)
+    _, st, _, _ = o.apply(np.array([[109, 100, 100]], np.uint8))
+    assert st[0] == 2
+    _hand_state(o, label=1)             # a foreground pixel never exits at stage 0
+    _, st, _, _ = o.apply(np.array([[100, 100, 100]], np.uint8))
+    assert st[0] != 0
+
+
+def test_hand_confidence_terms():
+    # a = 153/255 = .6, b = 51/255 = .2, g = .2; C- = .5, eta = 1/8
+    # stage 1 (I = (104,100,98), J = (100,100,100)): D = 4, t_r = .16
+    #   c = .6 + .2 (1 - 4/255) + .2 (1 - .16);  C = 7/8 * 1/2 + c / 8
+    o = one_pixel(flags=ORC_RGA | ORC_CONF, **HAND)
+    _hand_state(o)
+    o.apply(np.array([[104, 100, 98]], np.uint8))
+    c = Fraction(3, 5) + Fraction(1, 5) * (1 - Fraction(4, 255)) + Fraction(1, 5) * (1 - Fraction(4, 25))
+    assert abs(o.state.conf[0] - float(Fraction(7, 16) + c / 8)) <= 1e-15
+    # stage 2 with the prior at 200/255 everywhere: match comp0 (t = .16), D = 4
+    #   c = .6 * 200/255 + .2 (1 - 4/255) + .2 (1 - .16)
+    o = one_pixel(flags=ORC_CONF, **HAND)
+    _hand_state(o)
+    o.apply(np.array([[104, 100, 98]], np.uint8))
+    c = Fraction(3, 5) * Fraction(200, 255) + Fraction(1, 5) * (1 - Fraction(4, 255)) \
+        + Fraction(1, 5) * (1 - Fraction(4, 25))
+    assert abs(o.state.conf[0] - float(Fraction(7, 16) + c / 8)) <= 1e-15
+    # prior nullified (q = 5 < 13): the a term drops and b, g are renormalised
+    #   c = (.2 (1 - 4/255) + .2 (1 - .16)) / .4
+    o = one_pixel(flags=ORC_CONF, **HAND)
+    _hand_state(o)
+    o.state.kde[0] = 5
+    o.apply(np.array([[104, 100, 98]], np.uint8))
+    c = (Fraction(1, 5) * (1 - Fraction(4, 255)) + Fraction(1, 5) * (1 - Fraction(4, 25))) / Fraction(2, 5)
+    assert abs(o.state.conf[0] - float(Fraction(7, 16) + c / 8)) <= 1e-15
+
+
+def test_confidence_modulates_rate_and_halts_rga():
+    # C- = .95 >= c_halt: the running average does not move; the rate factor
+    # (1.5 - C) applies to the mixture: a_eff = .25 * .55
+    o = one_pixel(flags=ORC_RGA | ORC_CONF, **HAND)
+    _hand_state(o)
+    o.state.conf[0] = 0.95
+    _, st, _, _ = o.apply(np.array([[104, 100, 98]], np.uint8))
+    assert st[0] == 1 and list(o.state.rga_m[0]) == [100.0] * 3
+    o = one_pixel(flags=ORC_CONF, **HAND)
+    _hand_state(o)
+    o.state.conf[0] = 0.95
+    o.apply(np.array([[104, 100, 98]], np.uint8))
+    ae = 0.25 * (1.5 - 0.95)
+    assert abs(o.state.mu[0, 0, 0] - (100 + ae * 4)) <= 1e-12
+
+
+def test_near_threshold_record():
+    # t_r within 1e-4 of 1 is recorded; far from it is not
+    o = one_pixel(flags=ORC_RGA, **HAND)
+    _hand_state(o)
+    o.state.rga_v[0] = [16 * 16 / 6.25 * (1 - 3e-5)] * 3   # t = 16^2 / (6.25 v) ~ 1 + 3e-5
+    _, _, near, _ = o.apply(np.array([[116, 100, 100]], np.uint8))
+    assert near[0] & 2
+    _hand_state(o)
+    _, _, near, _ = o.apply(np.array([[104, 100, 98]], np.uint8))
+    assert near[0] == 0
