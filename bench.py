@@ -1,0 +1,387 @@
+#!/usr/bin/env python3
+"""Benchmark: Cascade-of-Gaussians background subtraction on GB300.
+
+One step = one 1920x1080 frame of a synthetic surveillance stream through
+the whole cascade (one cog_apply launch), K = 5 Gaussians, FP16 model state
+with FP32 arithmetic.  Frames are generated on the device before timing;
+the L2 cache is flushed (a 512 MB write) between timed frames and each
+frame is timed with CUDA events on the stream the kernel runs on.  The
+plain full-GMM path runs over the same frames with the same protocol.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: one process per GPU (torchrun); each rank owns its own camera
+stream (pixels and streams are independent), no data-path collective;
+weak scaling.  --impl reference times the FP64 CPU oracle on a bounded
+sample of the same workload (one band of rows per step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CoG Mpixel/s and % HBM peak vs plain full-GMM on same GB300; mask agreement vs FP64"
+UNIT = "Mpixel/s"
+W_, H_, K_ = 1920, 1080, 5
+N_TRAIN = 500
+N_TEST_MAX = 2000
+FALLBACK_HBM = 6800.0
+
+
+def rank_info():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+# ---------------------------------------------------------------- byte model
+def cog_bytes(stats: dict, P: int, elem: int, K: int) -> int:
+    """Algorithmic bytes the cascade touches for a set of frames, from the
+    per-stage occupancy counters: every pixel reads I, J, label, C and
+    writes mask, label, C (3+3+1+e + 1+1+e); a pixel past stage 0 reads
+    the residue weights and the running average and writes it back
+    (2 + 12e); a pixel at the mixture stage reads and writes its K*7
+    parameters, reads three prior bytes at 32-byte sector granularity and
+    reseeds the running average (14Ke + 96 + 6e)."""
+    n = stats["n_stage"]
+    frames = stats["frames"]
+    past0 = n[1] + stats["n_gmm"]
+    return int(frames * P * (9 + 2 * elem) + past0 * (2 + 12 * elem) + stats["n_gmm"] * (14 * K * elem + 96 + 6 * elem))
+
+
+def plain_bytes(frames: int, P: int, elem: int, K: int) -> int:
+    """The plain mixture reads I and the K*7 parameters and writes them
+    back with the mask: 3 + 14Ke + 1 bytes per pixel."""
+    return int(frames * P * (4 + 14 * K * elem))
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1705_09339_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was
+    taken on the current kernel sources; else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            d = json.load(f)
+        e = d.get(kernel)
+        if e and e.get("source_hash") == source_hash():
+            return float(e["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.idx = gpu_index
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                v = [x.strip() for x in line.split(",")]
+                if len(v) < 9:
+                    continue
+                try:
+                    sm.append(float(v[1]))
+                    mx = max(mx, float(v[2]))
+                except ValueError:
+                    continue
+                for n, x in zip(names, v[5:9]):
+                    if x.lower().startswith("active"):
+                        reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, rank, local_rank, world):
+    import torch
+    import torch.distributed as dist
+    from cogsynth import workload
+    from cogsynth.gpu import GpuScene
+    from paper_1705_09339_gb300 import cog
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    wl = workload("hd_dynamic", fg_frac=args.fg, seed=3 + rank)
+    sc = wl["scene"]
+    P = sc.P
+    n_test = min(N_TEST_MAX, args.warmup + args.steps)
+    if args.warmup + args.steps > N_TEST_MAX:
+        raise SystemExit(f"--warmup + --steps must be <= {N_TEST_MAX} test frames")
+    stream = torch.cuda.current_stream(dev)
+    gs = GpuScene(sc, dev)
+    train = gs.render(0, N_TRAIN)
+    test = gs.render(N_TRAIN, n_test)
+    p_cog = cog.cog_default_params(W_, H_, K_, state_dtype="f16")
+    p_gmm = cog.cog_default_params(W_, H_, K_, state_dtype="f16")
+    ctx = cog.cog_create(p_cog, stream.cuda_stream)
+    ctx_g = cog.cog_create(p_gmm, stream.cuda_stream)
+    cog.cog_train_prior(ctx, train, N_TRAIN)
+    cog.cog_train_prior(ctx_g, train, N_TRAIN)
+    cog.cog_sync(ctx)
+    del train
+    torch.cuda.empty_cache()
+    masks = torch.empty((n_test, H_, W_), dtype=torch.uint8, device=dev)
+    masks_g = torch.empty((n_test, H_, W_), dtype=torch.uint8, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def timed(fn, first, k):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        for i in range(k):
+            flush.zero_()
+            ev[i][0].record(stream)
+            fn(first + i)
+            ev[i][1].record(stream)
+        return ev
+
+    for i in range(args.warmup):
+        cog.cog_apply(ctx, test[i], masks[i])
+        cog.cog_apply_plain_gmm(ctx_g, test[i], masks_g[i])
+    cog.cog_sync(ctx)
+    _, tot0 = cog.cog_read_stats(ctx)
+    clocks = Clocks(local_rank)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    ev_c = timed(lambda i: cog.cog_apply(ctx, test[i], masks[i]), args.warmup, args.steps)
+    torch.cuda.synchronize()
+    ev_g = timed(lambda i: cog.cog_apply_plain_gmm(ctx_g, test[i], masks_g[i]), args.warmup, args.steps)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    cog.cog_sync(ctx)
+    _, tot1 = cog.cog_read_stats(ctx)
+    ms_c = sum(a.elapsed_time(b) for a, b in ev_c)
+    ms_g = sum(a.elapsed_time(b) for a, b in ev_g)
+    st = dict(n_stage=[b - a for a, b in zip(tot0["n_stage"], tot1["n_stage"])],
+              n_gmm=tot1["n_gmm"] - tot0["n_gmm"], frames=args.steps)
+    if world > 1:
+        t = torch.tensor([ms_c, ms_g], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_c, ms_g = t.tolist()
+
+    # end to end through the C ABI with host buffers (pinned)
+    n_e2e = min(args.steps, 100)
+    host_frames = test[args.warmup:args.warmup + n_e2e].cpu().pin_memory()
+    host_masks = torch.empty((n_e2e, H_, W_), dtype=torch.uint8).pin_memory()
+    hf, hm = host_frames.numpy(), host_masks.numpy()
+    ctx_e = cog.cog_create(p_cog, stream.cuda_stream)
+    tr2 = gs.render(0, N_TRAIN)
+    cog.cog_train_prior(ctx_e, tr2, N_TRAIN)
+    cog.cog_sync(ctx_e)
+    del tr2
+    for i in range(3):
+        cog.cog_apply_host(ctx_e, hf[i], hm[i])
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for i in range(n_e2e):
+        cog.cog_apply_host(ctx_e, hf[i], hm[i])
+    t_e2e = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = t.item()
+    cog.cog_destroy(ctx_e)
+
+    result = None
+    if rank == 0:
+        hbm, hbm_src = peaks()
+        value = world * P * args.steps / (ms_c / 1e3) / 1e6
+        value_g = world * P * args.steps / (ms_g / 1e3) / 1e6
+        bytes_c = cog_bytes(st, P, 2, K_)
+        bytes_g = plain_bytes(args.steps, P, 2, K_)
+        ach_c = bytes_c / (ms_c / 1e3) / 1e9
+        ach_g = bytes_g / (ms_g / 1e3) / 1e9
+        tr_c = ncu_traffic("apply_kernel")
+        tr_g = ncu_traffic("plain_gmm_kernel")
+        occ = {k: v / (P * args.steps) for k, v in zip(("fd", "rga", "gmm_bg", "fg", "illum"), st["n_stage"])}
+        cpu = cpu_baseline(sc, masks[args.warmup:args.warmup + args.steps], args) if not args.no_cpu_baseline else None
+        result = {
+            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_c / args.steps, 5), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{W_}x{H_} RGB u8 dynamic-background stream, K={K_}, FP16 state / FP32 math, "
+                                   f"{N_TRAIN} train frames, fg {args.fg:.3f}, one frame per step",
+                       "width": W_, "height": H_, "K": K_, "state_dtype": "f16", "n_train": N_TRAIN,
+                       "fg_frac": args.fg, "l2": "flushed (512 MB write) between timed steps",
+                       "parallelism": f"stream-sharded x{world} (one camera per GPU, no collective)"},
+            "roofline": {"bound": "hbm", "achieved": round(ach_c, 1), "peak": hbm, "unit": "GB/s",
+                         "frac": round(ach_c / hbm, 4), "traffic": tr_c, "peak_source": hbm_src,
+                         "algorithmic_bytes_per_step": bytes_c // args.steps},
+            "plain_gmm": {"value": round(value_g, 1), "unit": UNIT, "ms_per_step": round(ms_g / args.steps, 5),
+                          "roofline": {"bound": "hbm", "achieved": round(ach_g, 1), "peak": hbm, "unit": "GB/s",
+                                       "frac": round(ach_g / hbm, 4), "traffic": tr_g,
+                                       "algorithmic_bytes_per_step": bytes_g // args.steps}},
+            "speedup_vs_plain_gmm": round(ms_g / ms_c, 3),
+            "stage_occupancy": {k: round(v, 5) for k, v in occ.items()},
+            "e2e": {"value": round(world * P * n_e2e / t_e2e / 1e6, 1), "unit": UNIT,
+                    "h2d_bytes_per_step": P * 3, "d2h_bytes_per_step": P, "steps": n_e2e,
+                    "api": "cog_apply_host (pinned host frame in, mask out, synchronous)"},
+            "gpu_launches": args.steps,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "wall_s_timed_region": round(t_wall, 3),
+        }
+    for c in (ctx, ctx_g):
+        cog.cog_destroy(c)
+    if world > 1:
+        dist.destroy_process_group()
+    return result
+
+
+def _oracle_sample(sc, rows, n_frames, t0):
+    """Pixels of a band of rows and their frames t0..t0+n-1 (numpy renderer)."""
+    y0 = sc.height // 2 - rows // 2
+    pix = np.arange(y0 * sc.width, (y0 + rows) * sc.width)
+    fr = np.stack([sc.render(t, pix)[0] for t in range(t0, t0 + n_frames)])
+    return pix, fr
+
+
+def cpu_baseline(sc, gpu_masks, args):
+    """The FP64 oracle on a bounded sample: a band of 10 rows (19,200
+    pixels) trained on the 500 training frames, then the timed frames.
+    Also the FP16 GPU masks' agreement with it on that band."""
+    import oracle
+    rows = 10
+    n = args.steps
+    pix, tr = _oracle_sample(sc, rows, N_TRAIN, 0)
+    _, te = _oracle_sample(sc, rows, args.warmup + n, N_TRAIN)
+    d = oracle.default_params(sc.width, rows, K_)
+    o = oracle.Oracle(d)
+    o.train(tr)
+    for i in range(args.warmup):
+        o.apply(te[i], want_stage=False, want_near=False)
+    gm = gpu_masks.reshape(n, -1)[:, pix].cpu().numpy()
+    agree = 0
+    t0 = time.perf_counter()
+    for i in range(n):
+        m, _, _, _ = o.apply(te[args.warmup + i], want_stage=False, want_near=False)
+        agree += int((m == gm[i]).sum())
+    dt = time.perf_counter() - t0
+    return {"value": round(len(pix) * n / dt / 1e6, 3), "unit": UNIT, "cores": oracle.oracle_threads(),
+            "kind": "oracle",
+            "sample": f"{rows} rows x {sc.width} px (band at mid-height) x {n} test frames of the same stream, "
+                      f"after the same {N_TRAIN} training frames; apply phase timed",
+            "mask_agreement_fp16_gpu_vs_fp64": round(agree / (len(pix) * n), 6)}
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    """The FP64 CPU oracle, as it stands, on the host cores: each step is
+    one frame of a 20-row band (38,400 pixels) of the same stream."""
+    if rank != 0:
+        return None
+    import oracle
+    from cogsynth import workload
+    sc = workload("hd_dynamic", fg_frac=args.fg, seed=3)["scene"]
+    rows = 20
+    pix, tr = _oracle_sample(sc, rows, N_TRAIN, 0)
+    _, te = _oracle_sample(sc, rows, args.warmup + args.steps, N_TRAIN)
+    o = oracle.Oracle(oracle.default_params(sc.width, rows, K_))
+    o.train(tr)
+    for i in range(args.warmup):
+        o.apply(te[i], want_stage=False, want_near=False)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        o.apply(te[args.warmup + i], want_stage=False, want_near=False)
+    dt = time.perf_counter() - t0
+    v = round(len(pix) * args.steps / dt / 1e6, 3)
+    cores = oracle.oracle_threads()
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{W_}x{H_} RGB u8 dynamic-background stream, K={K_}, FP64 oracle on the host",
+                       "width": W_, "height": H_, "K": K_, "n_train": N_TRAIN, "fg_frac": args.fg},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{rows} rows x {sc.width} px band of the stream per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fg", type=float, default=0.02)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    rank, local_rank, world = rank_info()
+    if args.impl == "reference":
+        r = run_reference(args, rank, world)
+    else:
+        import __graft_entry__
+        __graft_entry__.build()
+        r = run_ours(args, rank, local_rank, world)
+    if r is not None and rank == 0:
+        print(json.dumps(r), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,191 @@
+/*
+ * cog.h -- C ABI of the GB300 Cascade-of-Gaussians (CoG) background
+ * subtraction library (libcog.so).
+ *
+ * The method is that of Kiran, Das and Yogamani, "Rejection-Cascade of
+ * Gaussians: real-time adaptive background subtraction framework"
+ * (arXiv 1705.09339).  The problem it states: learn a per-pixel scene prior
+ * over N training frames (Sec. 2, "Scene Prior in Background Model"), then
+ * classify every incoming frame pixel by pixel through a rejection cascade of
+ * increasingly complex background models, adapting only the level that
+ * classified the pixel (Sec. 2, "Cascade of Gaussians CoG").
+ *
+ * Conventions for every call
+ *   - Pointers named *_dev are CUDA device pointers (for example torch
+ *     tensors' data_ptr()); pointers named *_host are host pointers.  The
+ *     caller owns every buffer it passes; the library never frees them.
+ *   - Frames are 8-bit RGB, row-major, channels interleaved: byte
+ *     (y*width + x)*3 + c.  Masks and stage maps are one byte per pixel.
+ *   - Device calls are asynchronous and ordered on the CUDA stream given to
+ *     cog_create.  Argument errors are reported synchronously.  CUDA launch
+ *     errors and the device error word are sticky per context: the failing
+ *     call, or the next call, or cog_sync, returns them.
+ *   - A context is not thread-safe; different contexts are independent.
+ *   - No call allocates device memory except cog_create (when it is not
+ *     given a state buffer) and the first cog_apply_host (its staging
+ *     buffers).
+ */
+#ifndef COG_H
+#define COG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    COG_OK = 0,
+    COG_ERR_INVALID_ARG = 1, /* null pointer, bad size, misaligned buffer, bad parameter */
+    COG_ERR_OOM = 2,         /* device allocation failed                                 */
+    COG_ERR_CUDA = 3,        /* a CUDA runtime call or a launch failed                   */
+    COG_ERR_STATE = 4,       /* call out of order (apply before train, ...)              */
+    COG_ERR_TIMEOUT = 5,     /* a bounded device wait gave up                            */
+    COG_ERR_DEVICE = 6       /* the device error word was set                            */
+} cog_status;
+
+/* Storage type of the model state; all arithmetic is FP32. */
+typedef enum { COG_F32 = 0, COG_F16 = 1, COG_BF16 = 2 } cog_dtype;
+
+/* Cascade switches (cog_params.flags). */
+#define COG_FD    1u  /* stage 0: frame difference / consistent-hypothesis propagation */
+#define COG_RGA   2u  /* stage 1: running Gaussian average                              */
+#define COG_CONF  4u  /* confidence-driven learning rate, thresholds and halting        */
+#define COG_ILLUM 8u  /* abrupt-illumination counter and response                       */
+#define COG_ALL   15u
+
+/* Stage codes written to a stage map (the cascade level that labelled the
+ * pixel; the paper's per-level occupancy figure). */
+#define COG_ST_FD     0
+#define COG_ST_RGA    1
+#define COG_ST_GMM_BG 2
+#define COG_ST_FG     3
+#define COG_ST_ILLUM  4
+
+typedef struct cog_params {
+    int32_t width, height;   /* frame size in pixels, each >= 1                           */
+    int32_t K;               /* Gaussians per pixel, 1..8 (Eq. 2)                         */
+    int32_t state_dtype;     /* cog_dtype                                                 */
+    float alpha;             /* base learning rate of Eq. 2                               */
+    float lambda;            /* match threshold in standard deviations, per channel       */
+    float T_bg;              /* background weight fraction T of the ordered Gaussians     */
+    float w_init;            /* weight of a newly created component                       */
+    float var_init;          /* variance of a newly created component                     */
+    float var_min, var_max;  /* variance clamp                                            */
+    float tau_fd;            /* stage-0 threshold on max_c |I - I_prev| at C = 0.5        */
+    float eta_conf;          /* smoothing rate of the confidence C                        */
+    float c_halt;            /* confidence at which stage-1 updates halt                  */
+    float w_illum;           /* weight of the new mode after an illumination change       */
+    int32_t q_null;          /* prior nullified below this peak-normalised level (/255)   */
+    int32_t kde_bw;          /* scene-prior kernel bandwidth in grey levels, 1..32        */
+    int32_t r1, r2;          /* residue class bounds (static <= r1 < oscillating <= r2)   */
+    int32_t illum_permille;  /* illumination change when > this per mille of pixels       */
+    uint32_t flags;          /* COG_* switches                                            */
+} cog_params;
+
+/* Per-frame statistics (the stage occupancy n_i of the paper's speed-up
+ * model, Sec. 3.2). */
+typedef struct cog_stats {
+    int64_t n_stage[5];      /* pixels labelled at each COG_ST_* level   */
+    int64_t n_gmm;           /* pixels that reached the mixture stage    */
+    int32_t illum_flag;      /* illumination response active this frame  */
+    int32_t frame;           /* index of the frame these counts describe */
+} cog_stats;
+
+/* Byte offsets of the state buffer's planes (for export/import decoding).
+ * P = width*height; Pp = P rounded up to a multiple of 4096. */
+typedef struct cog_layout {
+    uint64_t total;          /* bytes of the whole state buffer                         */
+    uint64_t ctl;            /* control block (counters), 4096 bytes                    */
+    uint64_t jl;             /* uint32[Pp]: previous frame R,G,B in bytes 0..2, label 3 */
+    uint64_t conf;           /* dtype[Pp]: confidence C                                 */
+    uint64_t qab;            /* uint16[Pp]: residue weights qa | qb << 8 (of 255)       */
+    uint64_t rga;            /* 6 planes dtype[Pp]: m0 m1 m2 v0 v1 v2                   */
+    uint64_t rga_plane;      /* bytes between consecutive running-average planes        */
+    uint64_t gmm;            /* per-pixel records of rec_bytes: K x (w, mu0..2, v0..2)  */
+    uint64_t rec_bytes;      /* K*7*sizeof(dtype) rounded up to 16                      */
+    uint64_t kde;            /* uint8[P][3][256]: peak-normalised prior                 */
+    uint64_t elem_bytes;     /* sizeof(dtype)                                           */
+} cog_layout;
+
+typedef struct cog_ctx cog_ctx;
+
+/* Fills *p with the library defaults for a width x height stream with K
+ * Gaussians: FP32 state, every stage on.  The paper states no constants;
+ * the defaults are this library's documented readings. */
+void cog_default_params(cog_params *p, int32_t width, int32_t height, int32_t K);
+
+/* Validates *p and returns the state size and plane offsets.  Host only. */
+cog_status cog_state_bytes(const cog_params *p, size_t *out_bytes);
+cog_status cog_state_layout(const cog_params *p, cog_layout *out);
+
+/* Creates a context bound to the current CUDA device and to cuda_stream
+ * (a cudaStream_t; NULL = the legacy default stream).  state_dev: NULL to
+ * let the library allocate the state, or a caller-owned device buffer of at
+ * least cog_state_bytes bytes, 256-byte aligned, that outlives the context.
+ * The state is zeroed on the stream. */
+cog_status cog_create(const cog_params *p, void *cuda_stream, void *state_dev, cog_ctx **out);
+
+/* Training phase (Sec. 2): frames_dev holds n_frames >= 2 frames back to
+ * back (n_frames x height x width x 3 bytes, 16-byte aligned).  Builds the
+ * per-pixel, per-channel kernel-density prior over the frames (Sec. 2,
+ * "Scene Prior"), the residue-class confidence weights (Sec. 2,
+ * "Determining Learning Rate Hyper-parameters"), and warms the mixture of
+ * Eq. 2 up over the frames with every rejection stage off; the running
+ * average starts at the top-ranked mode and C at 0.5.  Requires
+ * n_frames * sum_d g[d] < 2^32 (n_frames <= 6500 at bandwidth 4). */
+cog_status cog_train_prior(cog_ctx *ctx, const uint8_t *frames_dev, int32_t n_frames);
+
+/* One frame through the cascade (Sec. 2, "Cascade of Gaussians CoG"):
+ * stage 0 frame difference, stage 1 running Gaussian average, stage 2 the
+ * ordered Gaussians of Eq. 2 with the scene prior and the confidence of
+ * Sec. 2 "Confidence Measure"; only the level that labels a pixel adapts.
+ * frame_dev: height x width x 3 bytes, 16-byte aligned.  mask_dev: one byte
+ * per pixel (255 = foreground), 8-byte aligned.  stagemap_dev: NULL, or one
+ * COG_ST_* byte per pixel, 8-byte aligned.  stats_host: NULL, or receives
+ * this frame's counts (the call then synchronises the stream).
+ * COG_ERR_STATE before cog_train_prior. */
+cog_status cog_apply(cog_ctx *ctx, const uint8_t *frame_dev, uint8_t *mask_dev,
+                     uint8_t *stagemap_dev, cog_stats *stats_host);
+
+/* The comparison baseline: one frame of the plain Stauffer-Grimson mixture
+ * (Eq. 2 at rate alpha, no cascade, no prior, no confidence) on this
+ * context's mixture state.  Same buffer rules as cog_apply. */
+cog_status cog_apply_plain_gmm(cog_ctx *ctx, const uint8_t *frame_dev, uint8_t *mask_dev);
+
+/* cog_apply for host buffers: copies frame_host (height x width x 3 bytes)
+ * to the device, runs the cascade and copies the mask back into mask_host
+ * (one byte per pixel).  Returns when mask_host is filled.  Page-locked host
+ * buffers give full copy bandwidth; pageable ones work.  The first call
+ * allocates two device staging buffers that the context keeps. */
+cog_status cog_apply_host(cog_ctx *ctx, const uint8_t *frame_host, uint8_t *mask_host);
+
+/* Statistics of the most recent cog_apply frame and running totals of the
+ * stage counts over every frame applied since the last training.
+ * Synchronises the stream. */
+cog_status cog_read_stats(cog_ctx *ctx, cog_stats *last, cog_stats *total);
+
+/* Waits for the context's stream; returns any sticky error. */
+cog_status cog_sync(cog_ctx *ctx);
+
+/* Byte image of the state buffer (cog_layout.total bytes) to or from host
+ * memory.  Synchronous. */
+cog_status cog_export_state(cog_ctx *ctx, void *dst_host, size_t bytes);
+cog_status cog_import_state(cog_ctx *ctx, const void *src_host, size_t bytes);
+
+/* Number of frames applied since training, and the device state pointer. */
+cog_status cog_info(cog_ctx *ctx, int64_t *frames_applied, void **state_dev);
+
+/* Human-readable description of the context's last error ("" if none).
+ * With ctx == NULL: the last error of a failed cog_create on this thread. */
+const char *cog_last_error_string(cog_ctx *ctx);
+
+/* Waits for the stream, frees what the library allocated, and destroys the
+ * context.  Returns the sticky error, if any. */
+cog_status cog_destroy(cog_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* COG_H */

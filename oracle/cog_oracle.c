@@ -77,9 +77,9 @@ static void kde_one(const uint8_t *frames, int N, int64_t P, int64_t p, int c,
     int64_t M = 0;
     for (int v = 0; v < 256; v++) {
         int64_t acc = 0;
-        for (int u = 0; u < 256; u++) {
+        for (int u = (v - R > 0 ? v - R : 0); u <= (v + R < 255 ? v + R : 255); u++) {
             int d = v > u ? v - u : u - v;
-            if (d <= R) acc += h[u] * g[d];
+            acc += h[u] * g[d];
         }
         k[v] = acc;
         if (acc > M) M = acc;

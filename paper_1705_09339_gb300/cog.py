@@ -1,0 +1,272 @@
+"""Thin ctypes binding of libcog.so (include/cog.h), same names as the C ABI.
+
+This module only marshals arguments: every step of the method runs in the
+CUDA library.  Device buffers are passed as torch CUDA tensors (their
+``data_ptr()``); PyTorch supplies device memory and streams only.  There is
+no CPU fallback: if the library is missing or fails to load, importing this
+module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libcog.so")
+
+COG_OK, COG_ERR_INVALID_ARG, COG_ERR_OOM, COG_ERR_CUDA, COG_ERR_STATE, COG_ERR_TIMEOUT, COG_ERR_DEVICE = range(7)
+STATUS_NAMES = ["COG_OK", "COG_ERR_INVALID_ARG", "COG_ERR_OOM", "COG_ERR_CUDA", "COG_ERR_STATE",
+                "COG_ERR_TIMEOUT", "COG_ERR_DEVICE"]
+COG_F32, COG_F16, COG_BF16 = 0, 1, 2
+COG_FD, COG_RGA, COG_CONF, COG_ILLUM = 1, 2, 4, 8
+COG_ALL = 15
+DTYPES = {"f32": COG_F32, "f16": COG_F16, "bf16": COG_BF16}
+
+
+class cog_params(C.Structure):
+    _fields_ = [
+        ("width", C.c_int32), ("height", C.c_int32), ("K", C.c_int32), ("state_dtype", C.c_int32),
+        ("alpha", C.c_float), ("lambda_", C.c_float), ("T_bg", C.c_float), ("w_init", C.c_float),
+        ("var_init", C.c_float), ("var_min", C.c_float), ("var_max", C.c_float), ("tau_fd", C.c_float),
+        ("eta_conf", C.c_float), ("c_halt", C.c_float), ("w_illum", C.c_float),
+        ("q_null", C.c_int32), ("kde_bw", C.c_int32), ("r1", C.c_int32), ("r2", C.c_int32),
+        ("illum_permille", C.c_int32), ("flags", C.c_uint32),
+    ]
+
+
+class cog_stats(C.Structure):
+    _fields_ = [("n_stage", C.c_int64 * 5), ("n_gmm", C.c_int64), ("illum_flag", C.c_int32),
+                ("frame", C.c_int32)]
+
+    def as_dict(self) -> dict:
+        return dict(n_stage=list(self.n_stage), n_gmm=int(self.n_gmm), illum_flag=int(self.illum_flag),
+                    frame=int(self.frame))
+
+
+class cog_layout(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in ("total", "ctl", "jl", "conf", "qab", "rga", "rga_plane", "gmm",
+                                          "rec_bytes", "kde", "elem_bytes")]
+
+
+class CogError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 7 else status}: {msg}")
+        self.status = status
+
+
+def _load() -> C.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libcog.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+    lib = C.CDLL(LIB_PATH)
+    vp, i32, sz = C.c_void_p, C.c_int32, C.c_size_t
+    P = C.POINTER
+    sig = {
+        "cog_default_params": (None, [P(cog_params), i32, i32, i32]),
+        "cog_state_bytes": (C.c_int, [P(cog_params), P(sz)]),
+        "cog_state_layout": (C.c_int, [P(cog_params), P(cog_layout)]),
+        "cog_create": (C.c_int, [P(cog_params), vp, vp, P(vp)]),
+        "cog_train_prior": (C.c_int, [vp, vp, i32]),
+        "cog_apply": (C.c_int, [vp, vp, vp, vp, P(cog_stats)]),
+        "cog_apply_plain_gmm": (C.c_int, [vp, vp, vp]),
+        "cog_apply_host": (C.c_int, [vp, vp, vp]),
+        "cog_read_stats": (C.c_int, [vp, P(cog_stats), P(cog_stats)]),
+        "cog_sync": (C.c_int, [vp]),
+        "cog_export_state": (C.c_int, [vp, vp, sz]),
+        "cog_import_state": (C.c_int, [vp, vp, sz]),
+        "cog_info": (C.c_int, [vp, P(C.c_int64), P(vp)]),
+        "cog_last_error_string": (C.c_char_p, [vp]),
+        "cog_destroy": (C.c_int, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def _check(status: int, ctx=None):
+    if status != COG_OK:
+        msg = lib.cog_last_error_string(ctx)
+        raise CogError(status, msg.decode() if msg else "")
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def cog_default_params(width: int, height: int, K: int = 3, **over) -> cog_params:
+    p = cog_params()
+    lib.cog_default_params(C.byref(p), width, height, K)
+    for k, v in over.items():
+        if k == "state_dtype" and isinstance(v, str):
+            v = DTYPES[v]
+        setattr(p, "lambda_" if k == "lambda" else k, v)
+    return p
+
+
+def cog_state_layout(p: cog_params) -> cog_layout:
+    l = cog_layout()
+    _check(lib.cog_state_layout(C.byref(p), C.byref(l)))
+    return l
+
+
+def cog_state_bytes(p: cog_params) -> int:
+    n = C.c_size_t()
+    _check(lib.cog_state_bytes(C.byref(p), C.byref(n)))
+    return n.value
+
+
+def cog_create(p: cog_params, stream: int | None = None, state=None) -> C.c_void_p:
+    ctx = C.c_void_p()
+    _check(lib.cog_create(C.byref(p), stream, _ptr(state), C.byref(ctx)))
+    return ctx
+
+
+def cog_train_prior(ctx, frames, n_frames: int) -> None:
+    _check(lib.cog_train_prior(ctx, _ptr(frames), n_frames), ctx)
+
+
+def cog_apply(ctx, frame, mask, stagemap=None, want_stats: bool = False):
+    st = cog_stats() if want_stats else None
+    _check(lib.cog_apply(ctx, _ptr(frame), _ptr(mask), _ptr(stagemap), C.byref(st) if st else None), ctx)
+    return st.as_dict() if st else None
+
+
+def cog_apply_plain_gmm(ctx, frame, mask) -> None:
+    _check(lib.cog_apply_plain_gmm(ctx, _ptr(frame), _ptr(mask)), ctx)
+
+
+def cog_apply_host(ctx, frame: np.ndarray, mask: np.ndarray) -> None:
+    assert frame.dtype == np.uint8 and mask.dtype == np.uint8
+    assert frame.flags.c_contiguous and mask.flags.c_contiguous
+    _check(lib.cog_apply_host(ctx, frame.ctypes.data, mask.ctypes.data), ctx)
+
+
+def cog_read_stats(ctx):
+    a, b = cog_stats(), cog_stats()
+    _check(lib.cog_read_stats(ctx, C.byref(a), C.byref(b)), ctx)
+    return a.as_dict(), b.as_dict()
+
+
+def cog_sync(ctx) -> None:
+    _check(lib.cog_sync(ctx), ctx)
+
+
+def cog_export_state(ctx, p: cog_params) -> np.ndarray:
+    n = cog_state_layout(p).total
+    buf = np.empty(n, np.uint8)
+    _check(lib.cog_export_state(ctx, buf.ctypes.data, n), ctx)
+    return buf
+
+
+def cog_import_state(ctx, buf: np.ndarray) -> None:
+    buf = np.ascontiguousarray(buf, dtype=np.uint8)
+    _check(lib.cog_import_state(ctx, buf.ctypes.data, buf.size), ctx)
+
+
+def cog_info(ctx):
+    n, s = C.c_int64(), C.c_void_p()
+    _check(lib.cog_info(ctx, C.byref(n), C.byref(s)), ctx)
+    return n.value, s.value
+
+
+def cog_last_error_string(ctx=None) -> str:
+    m = lib.cog_last_error_string(ctx)
+    return m.decode() if m else ""
+
+
+def cog_destroy(ctx) -> None:
+    _check(lib.cog_destroy(ctx))
+
+
+# ----------------------------------------------------------------------------
+# Decoding an exported state image into numpy views (documented layout).
+# ----------------------------------------------------------------------------
+_NP_DT = {COG_F32: np.float32, COG_F16: np.float16}
+
+
+def _plane(buf: np.ndarray, off: int, n: int, dtype) -> np.ndarray:
+    itemsize = np.dtype(dtype).itemsize
+    return buf[off:off + n * itemsize].view(dtype)
+
+
+def _bf16_to_f32(u16: np.ndarray) -> np.ndarray:
+    return (u16.astype(np.uint32) << 16).view(np.float32)
+
+
+def decode_state(buf: np.ndarray, p: cog_params) -> dict:
+    """FP64 copies of the model planes of an exported state image:
+    w [P,K], mu [P,K,3], var [P,K,3], rga_m [P,3], rga_v [P,3], conf [P],
+    label [P], prev [P,3], kde [P,3,256], qa [P], qb [P]."""
+    L = cog_state_layout(p)
+    P, K = p.width * p.height, p.K
+    Pp = (P + 4095) // 4096 * 4096
+
+    def vals(off, n):
+        if p.state_dtype == COG_BF16:
+            return _bf16_to_f32(_plane(buf, off, n, np.uint16)).astype(np.float64)
+        return _plane(buf, off, n, _NP_DT[p.state_dtype]).astype(np.float64)
+
+    jl = _plane(buf, L.jl, P, np.uint32)
+    prev = np.stack([(jl >> (8 * c)) & 0xFF for c in range(3)], axis=1).astype(np.uint8)
+    label = (jl >> 24).astype(np.uint8)
+    conf = vals(L.conf, P)
+    qab = _plane(buf, L.qab, P, np.uint16)
+    rga = np.stack([vals(L.rga + i * L.rga_plane, P) for i in range(6)], axis=1)
+    rec_elems = L.rec_bytes // L.elem_bytes
+    if p.state_dtype == COG_BF16:
+        recs = _bf16_to_f32(_plane(buf, L.gmm, Pp * rec_elems, np.uint16)).astype(np.float64)
+    else:
+        recs = _plane(buf, L.gmm, Pp * rec_elems, _NP_DT[p.state_dtype]).astype(np.float64)
+    recs = recs.reshape(Pp, rec_elems)[:P, :7 * K].reshape(P, K, 7)
+    kde = buf[L.kde:L.kde + P * 768].reshape(P, 3, 256)
+    return dict(w=recs[:, :, 0].copy(), mu=recs[:, :, 1:4].copy(), var=recs[:, :, 4:7].copy(),
+                rga_m=rga[:, :3].copy(), rga_v=rga[:, 3:].copy(), conf=conf, label=label, prev=prev,
+                kde=kde, qa=(qab & 0xFF).astype(np.uint8), qb=(qab >> 8).astype(np.uint8))
+
+
+def encode_state(buf: np.ndarray, p: cog_params, st: dict) -> np.ndarray:
+    """Writes model planes (same keys as decode_state) into a state image.
+    Used to start the CUDA path and the oracle from one seeded state."""
+    L = cog_state_layout(p)
+    P, K = p.width * p.height, p.K
+    Pp = (P + 4095) // 4096 * 4096
+    out = buf.copy()
+
+    def put(off, arr):
+        arr = np.asarray(arr, np.float64).reshape(-1)
+        if p.state_dtype == COG_BF16:
+            f = arr.astype(np.float32).view(np.uint32)
+            r = ((f + 0x7FFF + ((f >> 16) & 1)) >> 16).astype(np.uint16)
+            out[off:off + r.nbytes] = r.view(np.uint8)
+        else:
+            r = arr.astype(_NP_DT[p.state_dtype])
+            out[off:off + r.nbytes] = r.view(np.uint8)
+
+    jl = (st["prev"][:, 0].astype(np.uint32) | (st["prev"][:, 1].astype(np.uint32) << 8)
+          | (st["prev"][:, 2].astype(np.uint32) << 16) | (st["label"].astype(np.uint32) << 24))
+    out[L.jl:L.jl + 4 * P] = jl.view(np.uint8)
+    put(L.conf, st["conf"])
+    qab = st["qa"].astype(np.uint16) | (st["qb"].astype(np.uint16) << 8)
+    out[L.qab:L.qab + 2 * P] = qab.view(np.uint8)
+    for c in range(3):
+        put(L.rga + c * L.rga_plane, st["rga_m"][:, c])
+        put(L.rga + (3 + c) * L.rga_plane, st["rga_v"][:, c])
+    rec_elems = L.rec_bytes // L.elem_bytes
+    recs = np.zeros((Pp, rec_elems))
+    r = np.concatenate([st["w"][:, :, None], st["mu"], st["var"]], axis=2).reshape(P, 7 * K)
+    recs[:P, :7 * K] = r
+    put(L.gmm, recs)
+    out[L.kde:L.kde + P * 768] = np.asarray(st["kde"], np.uint8).reshape(-1)
+    return out

@@ -1,0 +1,473 @@
+// cog_api.cu -- host side of the C ABI declared in include/cog.h: parameter
+// validation, the state layout, context lifetime, stream-ordered launches,
+// sticky error reporting, statistics and state export/import.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "cog_internal.h"
+
+namespace cog {
+cudaError_t launch_apply_f32(int, const ApplyArgs &, cudaStream_t);
+cudaError_t launch_apply_f16(int, const ApplyArgs &, cudaStream_t);
+cudaError_t launch_apply_bf16(int, const ApplyArgs &, cudaStream_t);
+cudaError_t launch_plain_f32(int, const DevParams &, const StatePtrs &, const uint8_t *, uint8_t *, cudaStream_t);
+cudaError_t launch_plain_f16(int, const DevParams &, const StatePtrs &, const uint8_t *, uint8_t *, cudaStream_t);
+cudaError_t launch_plain_bf16(int, const DevParams &, const StatePtrs &, const uint8_t *, uint8_t *, cudaStream_t);
+cudaError_t launch_warmup_f32(int, const DevParams &, const StatePtrs &, const uint8_t *, int, int, int, cudaStream_t);
+cudaError_t launch_warmup_f16(int, const DevParams &, const StatePtrs &, const uint8_t *, int, int, int, cudaStream_t);
+cudaError_t launch_warmup_bf16(int, const DevParams &, const StatePtrs &, const uint8_t *, int, int, int, cudaStream_t);
+
+int elem_bytes(int dtype) { return dtype == COG_F32 ? 4 : 2; }
+
+int rec_bytes(int dtype, int K) { return (K * 7 * elem_bytes(dtype) + 15) / 16 * 16; }
+
+static size_t up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+bool make_layout(const cog_params &p, Layout &L)
+{
+    L.P = (int64_t)p.width * p.height;
+    L.Pp = (int64_t)up((size_t)L.P, PX_ALIGN);
+    L.elem = (size_t)elem_bytes(p.state_dtype);
+    L.rec_bytes = (size_t)rec_bytes(p.state_dtype, p.K);
+    size_t o = 0;
+    L.ctl = o;  o += CTL_BYTES;
+    L.jl = o;   o = up(o + (size_t)L.Pp * 4, 256);
+    L.conf = o; o = up(o + (size_t)L.Pp * L.elem, 256);
+    L.qab = o;  o = up(o + (size_t)L.Pp * 2, 256);
+    L.rga = o;  L.rga_plane_bytes = (size_t)L.Pp * L.elem;
+    o = up(o + 6 * L.rga_plane_bytes, 256);
+    L.gmm = o;  o = up(o + (size_t)L.Pp * L.rec_bytes, 256);
+    L.kde = o;  o = up(o + (size_t)L.P * 768, 256);
+    L.total = o;
+    return true;
+}
+
+}  // namespace cog
+
+using namespace cog;
+
+struct cog_ctx {
+    cog_params p;
+    Layout L;
+    DevParams dp;
+    StatePtrs sp;
+    cudaStream_t stream;
+    int device;
+    uint8_t *state;
+    bool owns;
+    bool trained;
+    int64_t frame_no;
+    cog_status sticky;
+    char err[512];
+    uint8_t *stage_in, *stage_out;   // cog_apply_host staging buffers
+};
+
+static thread_local char g_create_err[512];
+
+static cog_status set_err(cog_ctx *c, cog_status s, const char *fmt, ...)
+{
+    char *dst = c ? c->err : g_create_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 512, fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+static cog_status cuda_fail(cog_ctx *c, cudaError_t e, const char *where)
+{
+    set_err(c, COG_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+    if (c) c->sticky = COG_ERR_CUDA;
+    return COG_ERR_CUDA;
+}
+
+static const char *check_params(const cog_params *p)
+{
+    if (!p) return "params is NULL";
+    if (p->width < 1 || p->height < 1) return "width and height must be >= 1";
+    if ((int64_t)p->width * p->height > (int64_t)1 << 28) return "frame larger than 2^28 pixels";
+    if (p->K < 1 || p->K > KMAX) return "K must be in 1..8";
+    if (p->state_dtype < COG_F32 || p->state_dtype > COG_BF16) return "unknown state_dtype";
+    if (!(p->alpha > 0.f && p->alpha <= 1.f)) return "alpha must be in (0, 1]";
+    if (!(p->lambda > 0.f)) return "lambda must be > 0";
+    if (!(p->T_bg >= 0.f && p->T_bg <= 1.f)) return "T_bg must be in [0, 1]";
+    if (!(p->w_init > 0.f && p->w_init <= 1.f)) return "w_init must be in (0, 1]";
+    if (!(p->var_min > 0.f) || !(p->var_max >= p->var_min)) return "need 0 < var_min <= var_max";
+    if (!(p->var_init > 0.f)) return "var_init must be > 0";
+    if (!(p->tau_fd >= 0.f)) return "tau_fd must be >= 0";
+    if (!(p->eta_conf >= 0.f && p->eta_conf <= 1.f)) return "eta_conf must be in [0, 1]";
+    if (!(p->w_illum > 0.f && p->w_illum < 1.f)) return "w_illum must be in (0, 1)";
+    if (p->q_null < 0 || p->q_null > 256) return "q_null must be in 0..256";
+    if (p->kde_bw < 1 || p->kde_bw > 32) return "kde_bw must be in 1..32";
+    if (p->r1 < 0 || p->r2 < p->r1) return "need 0 <= r1 <= r2";
+    if (p->illum_permille < 0 || p->illum_permille > 1000) return "illum_permille must be in 0..1000";
+    if (p->flags & ~COG_ALL) return "unknown flag bits";
+    return nullptr;
+}
+
+extern "C" {
+
+void cog_default_params(cog_params *p, int32_t width, int32_t height, int32_t K)
+{
+    if (!p) return;
+    memset(p, 0, sizeof *p);
+    p->width = width;
+    p->height = height;
+    p->K = K;
+    p->state_dtype = COG_F32;
+    p->alpha = 0.01f;
+    p->lambda = 2.5f;
+    p->T_bg = 0.7f;
+    p->w_init = 0.05f;
+    p->var_init = 225.f;
+    p->var_min = 4.f;
+    p->var_max = 900.f;
+    p->tau_fd = 8.f;
+    p->eta_conf = 0.125f;
+    p->c_halt = 0.9f;
+    p->w_illum = 0.75f;
+    p->q_null = 13;
+    p->kde_bw = 4;
+    p->r1 = 10;
+    p->r2 = 30;
+    p->illum_permille = 700;
+    p->flags = COG_ALL;
+}
+
+cog_status cog_state_layout(const cog_params *p, cog_layout *out)
+{
+    if (const char *m = check_params(p)) return set_err(nullptr, COG_ERR_INVALID_ARG, "%s", m);
+    if (!out) return set_err(nullptr, COG_ERR_INVALID_ARG, "out is NULL");
+    Layout L;
+    make_layout(*p, L);
+    out->total = L.total; out->ctl = L.ctl; out->jl = L.jl; out->conf = L.conf; out->qab = L.qab;
+    out->rga = L.rga; out->rga_plane = L.rga_plane_bytes; out->gmm = L.gmm; out->rec_bytes = L.rec_bytes;
+    out->kde = L.kde; out->elem_bytes = L.elem;
+    return COG_OK;
+}
+
+cog_status cog_state_bytes(const cog_params *p, size_t *out)
+{
+    cog_layout l;
+    cog_status s = cog_state_layout(p, &l);
+    if (s != COG_OK) return s;
+    if (!out) return set_err(nullptr, COG_ERR_INVALID_ARG, "out is NULL");
+    *out = (size_t)l.total;
+    return COG_OK;
+}
+
+cog_status cog_create(const cog_params *p, void *cuda_stream, void *state_dev, cog_ctx **out)
+{
+    if (!out) return set_err(nullptr, COG_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (const char *m = check_params(p)) return set_err(nullptr, COG_ERR_INVALID_ARG, "%s", m);
+    if (state_dev && ((uintptr_t)state_dev & 255))
+        return set_err(nullptr, COG_ERR_INVALID_ARG, "state buffer must be 256-byte aligned");
+    cog_ctx *c = new (std::nothrow) cog_ctx();
+    if (!c) return set_err(nullptr, COG_ERR_OOM, "host allocation failed");
+    c->p = *p;
+    make_layout(*p, c->L);
+    c->stream = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) {
+        set_err(nullptr, COG_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+        delete c;
+        return COG_ERR_CUDA;
+    }
+    if (state_dev) {
+        c->state = (uint8_t *)state_dev;
+        c->owns = false;
+    } else {
+        e = cudaMalloc((void **)&c->state, c->L.total);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_err(nullptr, COG_ERR_OOM, "cudaMalloc of %zu state bytes: %s", c->L.total, cudaGetErrorString(e));
+            delete c;
+            return COG_ERR_OOM;
+        }
+        c->owns = true;
+    }
+    e = cudaMemsetAsync(c->state, 0, c->L.total, c->stream);
+    if (e != cudaSuccess) {
+        set_err(nullptr, COG_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+        if (c->owns) cudaFree(c->state);
+        delete c;
+        return COG_ERR_CUDA;
+    }
+    DevParams &d = c->dp;
+    d.P = c->L.P;
+    d.K = p->K;
+    d.flags = p->flags;
+    d.alpha = p->alpha;
+    d.lam2 = p->lambda * p->lambda;
+    d.T_bg = p->T_bg;
+    d.w_init = p->w_init;
+    d.var_init = p->var_init;
+    d.var_min = p->var_min;
+    d.var_max = p->var_max;
+    d.tau_fd = p->tau_fd;
+    d.eta = p->eta_conf;
+    d.c_halt = p->c_halt;
+    d.w_illum = p->w_illum;
+    d.q_null = p->q_null;
+    d.illum_permille = p->illum_permille;
+    StatePtrs &s = c->sp;
+    s.ctl = (uint32_t *)(c->state + c->L.ctl);
+    s.jl = (uint32_t *)(c->state + c->L.jl);
+    s.conf = c->state + c->L.conf;
+    s.qab = (uint16_t *)(c->state + c->L.qab);
+    s.rga = c->state + c->L.rga;
+    s.rga_plane = c->L.Pp;
+    s.gmm = c->state + c->L.gmm;
+    s.kde = c->state + c->L.kde;
+    c->sticky = COG_OK;
+    c->err[0] = 0;
+    *out = c;
+    return COG_OK;
+}
+
+static cog_status check_ctx(cog_ctx *c)
+{
+    if (!c) return COG_ERR_INVALID_ARG;
+    if (c->sticky != COG_OK) return c->sticky;
+    return COG_OK;
+}
+
+cog_status cog_train_prior(cog_ctx *c, const uint8_t *frames_dev, int32_t n_frames)
+{
+    cog_status s = check_ctx(c);
+    if (s) return s;
+    if (!frames_dev) return set_err(c, COG_ERR_INVALID_ARG, "frames_dev is NULL");
+    if ((uintptr_t)frames_dev & 15) return set_err(c, COG_ERR_INVALID_ARG, "frames_dev must be 16-byte aligned");
+    if (n_frames < 2) return set_err(c, COG_ERR_INVALID_ARG, "need at least 2 training frames");
+    const int bw = c->p.kde_bw, R = 3 * bw;
+    uint32_t g[100];
+    uint64_t gsum = 0;
+    for (int d = 0; d <= R; d++) {
+        g[d] = (uint32_t)std::floor(65536.0 * std::exp(-(double)(d * d) / (2.0 * bw * bw)) + 0.5);
+        gsum += (d ? 2u : 1u) * (uint64_t)g[d];
+    }
+    if ((uint64_t)n_frames * gsum >= (1ull << 32))
+        return set_err(c, COG_ERR_INVALID_ARG, "n_frames too large for the exact 32-bit prior (%d)", n_frames);
+    cudaError_t e = launch_kde_train(c->dp, c->sp, frames_dev, n_frames, g, R, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "kde_train launch");
+    switch (c->p.state_dtype) {
+    case COG_F32: e = launch_warmup_f32(c->p.K, c->dp, c->sp, frames_dev, n_frames, c->p.r1, c->p.r2, c->stream); break;
+    case COG_F16: e = launch_warmup_f16(c->p.K, c->dp, c->sp, frames_dev, n_frames, c->p.r1, c->p.r2, c->stream); break;
+    default: e = launch_warmup_bf16(c->p.K, c->dp, c->sp, frames_dev, n_frames, c->p.r1, c->p.r2, c->stream); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "warmup launch");
+    e = cudaMemsetAsync(c->sp.ctl, 0, CTL_BYTES, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync(ctl)");
+    c->trained = true;
+    c->frame_no = 0;
+    return COG_OK;
+}
+
+static cog_status read_ctl(cog_ctx *c, std::vector<uint32_t> &ctl)
+{
+    ctl.assign(CTL_BYTES / 4, 0);
+    cudaError_t e = cudaMemcpyAsync(ctl.data(), c->sp.ctl, CTL_BYTES, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "reading the control block");
+    if (ctl[CTL_ERR_WORD]) {
+        c->sticky = COG_ERR_DEVICE;
+        return set_err(c, COG_ERR_DEVICE, "device error word 0x%x (a bounded wait gave up)", ctl[CTL_ERR_WORD]);
+    }
+    return COG_OK;
+}
+
+static void frame_stats(const std::vector<uint32_t> &ctl, int64_t frame, cog_stats *st)
+{
+    memset(st, 0, sizeof *st);
+    st->frame = (int32_t)frame;
+    if (frame < 0) return;
+    const uint32_t *b = ctl.data() + (frame % 3) * CTL_BUF_WORDS;
+    for (int f = 0; f < 6; f++) {
+        int64_t v = 0;
+        for (int s = 0; s < CTL_SLOTS; s++) v += b[f * CTL_SLOTS + s];
+        if (f < 5) st->n_stage[f] = v; else st->n_gmm = v;
+    }
+}
+
+static int prev_flag(const cog_ctx *c, const std::vector<uint32_t> &ctl, int64_t frame)
+{
+    if (!(c->p.flags & COG_ILLUM) || frame < 1) return 0;
+    cog_stats prev;
+    frame_stats(ctl, frame - 1, &prev);
+    return (uint64_t)prev.n_gmm * 1000u > (uint64_t)c->p.illum_permille * (uint64_t)c->L.P;
+}
+
+cog_status cog_apply(cog_ctx *c, const uint8_t *frame_dev, uint8_t *mask_dev, uint8_t *stagemap_dev,
+                     cog_stats *stats_host)
+{
+    cog_status s = check_ctx(c);
+    if (s) return s;
+    if (!c->trained) return set_err(c, COG_ERR_STATE, "cog_apply before cog_train_prior");
+    if (!frame_dev || !mask_dev) return set_err(c, COG_ERR_INVALID_ARG, "frame_dev and mask_dev are required");
+    if ((uintptr_t)frame_dev & 15) return set_err(c, COG_ERR_INVALID_ARG, "frame_dev must be 16-byte aligned");
+    if ((uintptr_t)mask_dev & 7) return set_err(c, COG_ERR_INVALID_ARG, "mask_dev must be 8-byte aligned");
+    if ((uintptr_t)stagemap_dev & 7) return set_err(c, COG_ERR_INVALID_ARG, "stagemap_dev must be 8-byte aligned");
+    ApplyArgs a;
+    a.dp = c->dp;
+    a.s = c->sp;
+    a.frame = frame_dev;
+    a.mask = mask_dev;
+    a.stagemap = stagemap_dev;
+    a.frame_no = (uint32_t)(c->frame_no % 3);
+    cudaError_t e;
+    switch (c->p.state_dtype) {
+    case COG_F32: e = launch_apply_f32(c->p.K, a, c->stream); break;
+    case COG_F16: e = launch_apply_f16(c->p.K, a, c->stream); break;
+    default: e = launch_apply_bf16(c->p.K, a, c->stream); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "cog_apply launch");
+    c->frame_no++;
+    if (stats_host) {
+        std::vector<uint32_t> ctl;
+        if ((s = read_ctl(c, ctl)) != COG_OK) return s;
+        frame_stats(ctl, c->frame_no - 1, stats_host);
+        stats_host->illum_flag = prev_flag(c, ctl, c->frame_no - 1);
+    }
+    return COG_OK;
+}
+
+cog_status cog_apply_plain_gmm(cog_ctx *c, const uint8_t *frame_dev, uint8_t *mask_dev)
+{
+    cog_status s = check_ctx(c);
+    if (s) return s;
+    if (!c->trained) return set_err(c, COG_ERR_STATE, "cog_apply_plain_gmm before cog_train_prior");
+    if (!frame_dev || !mask_dev) return set_err(c, COG_ERR_INVALID_ARG, "frame_dev and mask_dev are required");
+    cudaError_t e;
+    switch (c->p.state_dtype) {
+    case COG_F32: e = launch_plain_f32(c->p.K, c->dp, c->sp, frame_dev, mask_dev, c->stream); break;
+    case COG_F16: e = launch_plain_f16(c->p.K, c->dp, c->sp, frame_dev, mask_dev, c->stream); break;
+    default: e = launch_plain_bf16(c->p.K, c->dp, c->sp, frame_dev, mask_dev, c->stream); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "cog_apply_plain_gmm launch");
+    return COG_OK;
+}
+
+cog_status cog_apply_host(cog_ctx *c, const uint8_t *frame_host, uint8_t *mask_host)
+{
+    cog_status s = check_ctx(c);
+    if (s) return s;
+    if (!c->trained) return set_err(c, COG_ERR_STATE, "cog_apply_host before cog_train_prior");
+    if (!frame_host || !mask_host) return set_err(c, COG_ERR_INVALID_ARG, "frame_host and mask_host are required");
+    const size_t P = (size_t)c->L.P;
+    cudaError_t e;
+    if (!c->stage_in) {
+        e = cudaMalloc((void **)&c->stage_in, up(P * 3, 256) + up(P, 256));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            c->stage_in = nullptr;
+            return set_err(c, COG_ERR_OOM, "staging allocation: %s", cudaGetErrorString(e));
+        }
+        c->stage_out = c->stage_in + up(P * 3, 256);
+    }
+    e = cudaMemcpyAsync(c->stage_in, frame_host, P * 3, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "frame upload");
+    if ((s = cog_apply(c, c->stage_in, c->stage_out, nullptr, nullptr)) != COG_OK) return s;
+    e = cudaMemcpyAsync(mask_host, c->stage_out, P, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "mask download");
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cog_apply_host sync");
+    return COG_OK;
+}
+
+cog_status cog_read_stats(cog_ctx *c, cog_stats *last, cog_stats *total)
+{
+    cog_status s = check_ctx(c);
+    if (s) return s;
+    std::vector<uint32_t> ctl;
+    if ((s = read_ctl(c, ctl)) != COG_OK) return s;
+    cog_stats l;
+    frame_stats(ctl, c->frame_no - 1, &l);
+    l.illum_flag = prev_flag(c, ctl, c->frame_no - 1);
+    if (last) *last = l;
+    if (total) {
+        memset(total, 0, sizeof *total);
+        total->frame = (int32_t)c->frame_no;
+        const uint64_t *tot = reinterpret_cast<const uint64_t *>(ctl.data() + CTL_TOT_WORD);
+        for (int f = 0; f < 5; f++) total->n_stage[f] = (int64_t)tot[f] + (c->frame_no > 0 ? l.n_stage[f] : 0);
+        total->n_gmm = (int64_t)tot[5] + (c->frame_no > 0 ? l.n_gmm : 0);
+    }
+    return COG_OK;
+}
+
+cog_status cog_sync(cog_ctx *c)
+{
+    if (!c) return COG_ERR_INVALID_ARG;
+    if (c->sticky != COG_OK) return c->sticky;
+    std::vector<uint32_t> ctl;
+    return read_ctl(c, ctl);
+}
+
+// The exported image carries the host-side frame counter and trained flag in
+// otherwise unused control words so that an import resumes exactly.
+static const int CTL_FRAME_WORD = CTL_ERR_WORD + 2;   // uint64
+static const int CTL_TRAINED_WORD = CTL_ERR_WORD + 4;
+
+cog_status cog_export_state(cog_ctx *c, void *dst_host, size_t bytes)
+{
+    cog_status s = check_ctx(c);
+    if (s) return s;
+    if (!dst_host || bytes < c->L.total)
+        return set_err(c, COG_ERR_INVALID_ARG, "destination smaller than %zu bytes", c->L.total);
+    cudaError_t e = cudaMemcpyAsync(dst_host, c->state, c->L.total, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cog_export_state");
+    uint32_t *w = (uint32_t *)((uint8_t *)dst_host + c->L.ctl);
+    uint64_t fn = (uint64_t)c->frame_no;
+    memcpy(w + CTL_FRAME_WORD, &fn, 8);
+    w[CTL_TRAINED_WORD] = c->trained ? 1u : 0u;
+    return COG_OK;
+}
+
+cog_status cog_import_state(cog_ctx *c, const void *src_host, size_t bytes)
+{
+    cog_status s = check_ctx(c);
+    if (s) return s;
+    if (!src_host || bytes < c->L.total)
+        return set_err(c, COG_ERR_INVALID_ARG, "source smaller than %zu bytes", c->L.total);
+    cudaError_t e = cudaMemcpyAsync(c->state, src_host, c->L.total, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cog_import_state");
+    const uint32_t *w = (const uint32_t *)((const uint8_t *)src_host + c->L.ctl);
+    uint64_t fn;
+    memcpy(&fn, w + CTL_FRAME_WORD, 8);
+    c->frame_no = (int64_t)fn;
+    c->trained = w[CTL_TRAINED_WORD] != 0;
+    return COG_OK;
+}
+
+cog_status cog_info(cog_ctx *c, int64_t *frames_applied, void **state_dev)
+{
+    if (!c) return COG_ERR_INVALID_ARG;
+    if (frames_applied) *frames_applied = c->frame_no;
+    if (state_dev) *state_dev = c->state;
+    return COG_OK;
+}
+
+const char *cog_last_error_string(cog_ctx *c)
+{
+    return c ? c->err : g_create_err;
+}
+
+cog_status cog_destroy(cog_ctx *c)
+{
+    if (!c) return COG_ERR_INVALID_ARG;
+    cog_status s = c->sticky;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess && s == COG_OK) s = COG_ERR_CUDA;
+    if (c->stage_in) cudaFree(c->stage_in);
+    if (c->owns) cudaFree(c->state);
+    delete c;
+    return s;
+}
+
+}  // extern "C"

@@ -1,0 +1,299 @@
+// cog_device.cuh -- device-side building blocks of the CoG kernels:
+// storage-type conversion, 128-bit vector access to the state planes, the
+// per-pixel mixture record, and the Stauffer-Grimson step of Eq. 2 that the
+// cascade's last stage, the plain-mixture baseline and the training warm-up
+// share.  All arithmetic is FP32 whatever the storage type.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "cog_internal.h"
+
+namespace cog {
+
+// ----------------------------------------------------------------- storage
+template <typename T> struct Store;
+
+template <> struct Store<float> {
+    static constexpr int bytes = 4;
+    __device__ __forceinline__ static float to_f(float x) { return x; }
+    __device__ __forceinline__ static float from_f(float x) { return x; }
+    __device__ __forceinline__ static uint32_t bits(float x) { return __float_as_uint(x); }
+    __device__ __forceinline__ static float unbits(uint32_t b) { return __uint_as_float(b); }
+};
+template <> struct Store<__half> {
+    static constexpr int bytes = 2;
+    __device__ __forceinline__ static float to_f(__half x) { return __half2float(x); }
+    __device__ __forceinline__ static __half from_f(float x) { return __float2half_rn(x); }
+    __device__ __forceinline__ static uint32_t bits(float x) { return __half_as_ushort(__float2half_rn(x)); }
+    __device__ __forceinline__ static float unbits(uint32_t b) { return __half2float(__ushort_as_half((unsigned short)b)); }
+};
+template <> struct Store<__nv_bfloat16> {
+    static constexpr int bytes = 2;
+    __device__ __forceinline__ static float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
+    __device__ __forceinline__ static __nv_bfloat16 from_f(float x) { return __float2bfloat16_rn(x); }
+    __device__ __forceinline__ static uint32_t bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+    __device__ __forceinline__ static float unbits(uint32_t b) { return __bfloat162float(__ushort_as_bfloat16((unsigned short)b)); }
+};
+
+__device__ __forceinline__ uint32_t u4get(const uint4 &v, int i)
+{
+    return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ void u4set(uint4 &v, int i, uint32_t x)
+{
+    if (i == 0) v.x = x; else if (i == 1) v.y = x; else if (i == 2) v.z = x; else v.w = x;
+}
+
+// Eight consecutive values of a plane (8 x T = 16 or 32 bytes, aligned).
+template <typename T> struct Vec8 {
+    static constexpr int NV = (8 * Store<T>::bytes) / 16;   // uint4 per 8 values
+    uint4 u[NV];
+    __device__ __forceinline__ void load(const T *p) {
+#pragma unroll
+        for (int i = 0; i < NV; i++) u[i] = reinterpret_cast<const uint4 *>(p)[i];
+    }
+    __device__ __forceinline__ void store(T *p) const {
+#pragma unroll
+        for (int i = 0; i < NV; i++) reinterpret_cast<uint4 *>(p)[i] = u[i];
+    }
+    __device__ __forceinline__ float get(int i) const {
+        if (Store<T>::bytes == 4) return Store<T>::unbits(u4get(u[i >> 2], i & 3));
+        uint32_t w = u4get(u[i >> 3], (i >> 1) & 3);
+        return Store<T>::unbits((i & 1) ? (w >> 16) : (w & 0xffffu));
+    }
+    __device__ __forceinline__ void set(int i, float x) {
+        uint32_t b = Store<T>::bits(x);
+        if (Store<T>::bytes == 4) { u4set(u[i >> 2], i & 3, b); return; }
+        uint32_t w = u4get(u[i >> 3], (i >> 1) & 3);
+        w = (i & 1) ? ((w & 0xffffu) | (b << 16)) : ((w & 0xffff0000u) | b);
+        u4set(u[i >> 3], (i >> 1) & 3, w);
+    }
+};
+
+// ------------------------------------------------------------ mixture record
+// Per-pixel record: K components of (w, mu0, mu1, mu2, v0, v1, v2), stored
+// contiguously and padded to a 16-byte multiple so one survivor's record is
+// fetched with whole 128-bit loads.
+template <typename T, int K> struct Rec {
+    static constexpr int NE = 7 * K;
+    static constexpr int NV = (NE * Store<T>::bytes + 15) / 16;
+    static constexpr int BYTES = NV * 16;
+};
+
+template <int K> struct Mix {
+    float w[K], mu[K][3], v[K][3];
+};
+
+template <typename T, int K>
+__device__ __forceinline__ float rec_elem(const uint4 *u, int e)
+{
+    if (Store<T>::bytes == 4) return Store<T>::unbits(u4get(u[e >> 2], e & 3));
+    uint32_t w = u4get(u[e >> 3], (e >> 1) & 3);
+    return Store<T>::unbits((e & 1) ? (w >> 16) : (w & 0xffffu));
+}
+
+template <typename T, int K>
+__device__ __forceinline__ void rec_load(const uint8_t *gmm, int64_t p, Mix<K> &m)
+{
+    constexpr int NV = Rec<T, K>::NV;
+    uint4 u[NV];
+    const uint4 *src = reinterpret_cast<const uint4 *>(gmm + p * Rec<T, K>::BYTES);
+#pragma unroll
+    for (int i = 0; i < NV; i++) u[i] = src[i];
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        m.w[k] = rec_elem<T, K>(u, 7 * k);
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            m.mu[k][c] = rec_elem<T, K>(u, 7 * k + 1 + c);
+            m.v[k][c] = rec_elem<T, K>(u, 7 * k + 4 + c);
+        }
+    }
+}
+
+template <typename T, int K>
+__device__ __forceinline__ void rec_store(uint8_t *gmm, int64_t p, const Mix<K> &m)
+{
+    constexpr int NV = Rec<T, K>::NV;
+    constexpr int NE = Rec<T, K>::NE;
+    uint4 u[NV];
+#pragma unroll
+    for (int i = 0; i < NV; i++) u[i] = make_uint4(0, 0, 0, 0);
+#pragma unroll
+    for (int e = 0; e < NE; e++) {
+        const int k = e / 7, f = e % 7;
+        const float x = f == 0 ? m.w[k] : (f < 4 ? m.mu[k][f - 1] : m.v[k][f - 4]);
+        const uint32_t b = Store<T>::bits(x);
+        if (Store<T>::bytes == 4) {
+            u4set(u[e >> 2], e & 3, b);
+        } else {
+            uint32_t w = u4get(u[e >> 3], (e >> 1) & 3);
+            w |= (e & 1) ? (b << 16) : b;
+            u4set(u[e >> 3], (e >> 1) & 3, w);
+        }
+    }
+    uint4 *dst = reinterpret_cast<uint4 *>(gmm + p * Rec<T, K>::BYTES);
+#pragma unroll
+    for (int i = 0; i < NV; i++) dst[i] = u[i];
+}
+
+__device__ __forceinline__ float clampf(float x, float lo, float hi)
+{
+    return x < lo ? lo : (x > hi ? hi : x);
+}
+
+// ----------------------------------------------------- Eq. 2 mixture step
+// Ordered Gaussians (Stauffer-Grimson with diagonal covariance):
+//   rank key w^2 / mean variance, descending, ties to the lower index;
+//   match = first component in rank order with max_c (I-mu)^2/(lam^2 v) < 1;
+//   background iff a match exists and the weight ranked before it is <= T
+//   (decided on the state before the update);
+//   update at rate a (rho = a): weights (1-a) w + a [k = match], the matched
+//   mean and variance move toward I; with no match the lowest-ranked
+//   component restarts at (I, var_init, w_init); weights renormalised.
+struct MixOut {
+    int match;   // matched component or -1
+    int tgt;     // matched or restarted component
+    int fg;      // 1 = foreground
+    float tm;    // match statistic of the matched component (pre-update)
+};
+
+template <int K>
+__device__ __forceinline__ MixOut mix_step(Mix<K> &m, const float I[3], float a, const DevParams &dp)
+{
+    float r[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        const float vbar = (m.v[k][0] + m.v[k][1] + m.v[k][2]) / 3.0f;
+        r[k] = m.w[k] * m.w[k] / vbar;
+    }
+    int pos[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        int c = 0;
+#pragma unroll
+        for (int j = 0; j < K; j++)
+            if (j != k) c += (r[j] > r[k]) || (r[j] == r[k] && j < k);
+        pos[k] = c;
+    }
+    MixOut o;
+    o.match = -1;
+    o.tm = 0.f;
+    int mpos = K;
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        float tk = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const float d = I[c] - m.mu[k][c];
+            const float t = d * d / (dp.lam2 * m.v[k][c]);
+            tk = t > tk ? t : tk;
+        }
+        if (tk < 1.f && pos[k] < mpos) { mpos = pos[k]; o.match = k; o.tm = tk; }
+    }
+    if (o.match >= 0) {
+        float S = 0.f;
+#pragma unroll
+        for (int k = 0; k < K; k++)
+            if (pos[k] < mpos) S += m.w[k];
+        o.fg = !(S <= dp.T_bg);
+    } else {
+        o.fg = 1;
+    }
+    const float b = 1.f - a;
+    if (o.match >= 0) {
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            m.w[k] = b * m.w[k] + (k == o.match ? a : 0.f);
+            if (k == o.match) {
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    m.mu[k][c] = m.mu[k][c] + a * (I[c] - m.mu[k][c]);
+                    const float d = I[c] - m.mu[k][c];
+                    m.v[k][c] = clampf(b * m.v[k][c] + a * d * d, dp.var_min, dp.var_max);
+                }
+            }
+        }
+        o.tgt = o.match;
+    } else {
+        o.tgt = 0;
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            m.w[k] = b * m.w[k];
+            if (pos[k] == K - 1) {
+                o.tgt = k;
+                m.w[k] = dp.w_init;
+#pragma unroll
+                for (int c = 0; c < 3; c++) { m.mu[k][c] = I[c]; m.v[k][c] = dp.var_init; }
+            }
+        }
+    }
+    float sum = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; k++) sum += m.w[k];
+#pragma unroll
+    for (int k = 0; k < K; k++) m.w[k] = m.w[k] / sum;
+    return o;
+}
+
+// Abrupt illumination change (Sec. 2, end of "Cascade of Gaussians"): the
+// foreground decision becomes background, the matched or new mode takes
+// weight w_illum and the others share the rest in proportion.
+template <int K>
+__device__ __forceinline__ void illum_response(Mix<K> &m, int tgt, float w_illum)
+{
+    float so = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; k++) if (k != tgt) so += m.w[k];
+    if (so > 0.f) {
+#pragma unroll
+        for (int k = 0; k < K; k++)
+            m.w[k] = (k == tgt) ? w_illum : m.w[k] * (1.f - w_illum) / so;
+    } else {
+#pragma unroll
+        for (int k = 0; k < K; k++) if (k == tgt) m.w[k] = 1.f;
+    }
+}
+
+// ------------------------------------------------------------ bulk copies
+// One-shot TMA bulk copy global -> shared completing on an mbarrier.
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+// Bounded wait on phase `parity`; returns false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok = 0;
+    for (uint32_t it = 0; it < (1u << 22) && !ok; it++) {
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+    }
+    return ok != 0;
+}
+
+}  // namespace cog

@@ -1,0 +1,49 @@
+// cog_inst.cuh -- instantiates the per-storage-type kernels for K = 1..8.
+// Included once per storage type (COG_T, COG_SUFFIX) so the three types
+// compile as separate translation units in parallel.
+#include "cog_apply.cuh"
+#include "cog_mixture.cuh"
+
+#define COG_CAT2(a, b) a##b
+#define COG_CAT(a, b) COG_CAT2(a, b)
+
+namespace cog {
+
+#define COG_KSWITCH(CALL)                 \
+    switch (K) {                          \
+    case 1: return CALL(1);               \
+    case 2: return CALL(2);               \
+    case 3: return CALL(3);               \
+    case 4: return CALL(4);               \
+    case 5: return CALL(5);               \
+    case 6: return CALL(6);               \
+    case 7: return CALL(7);               \
+    case 8: return CALL(8);               \
+    default: return cudaErrorInvalidValue; \
+    }
+
+cudaError_t COG_CAT(launch_apply_, COG_SUFFIX)(int K, const ApplyArgs &a, cudaStream_t st)
+{
+#define CALL_A(k) launch_apply_t<COG_T, k>(a, st)
+    COG_KSWITCH(CALL_A)
+#undef CALL_A
+}
+
+cudaError_t COG_CAT(launch_plain_, COG_SUFFIX)(int K, const DevParams &dp, const StatePtrs &s,
+                                               const uint8_t *frame, uint8_t *mask, cudaStream_t st)
+{
+#define CALL_P(k) launch_plain_t<COG_T, k>(dp, s, frame, mask, st)
+    COG_KSWITCH(CALL_P)
+#undef CALL_P
+}
+
+cudaError_t COG_CAT(launch_warmup_, COG_SUFFIX)(int K, const DevParams &dp, const StatePtrs &s,
+                                                const uint8_t *frames, int N, int r1, int r2,
+                                                cudaStream_t st)
+{
+#define CALL_W(k) launch_warmup_t<COG_T, k>(dp, s, frames, N, r1, r2, st)
+    COG_KSWITCH(CALL_W)
+#undef CALL_W
+}
+
+}  // namespace cog

@@ -1,0 +1,82 @@
+// cog_internal.h -- definitions shared by the library's translation units:
+// the kernel parameter block, the state layout and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/cog.h"
+
+namespace cog {
+
+constexpr int PX_ALIGN = 4096;   // pixel padding of every state plane
+constexpr int KMAX = 8;
+
+// Control block (first 4096 bytes of the state), in 32-bit words.
+//   [0, 768)   per-frame counters: 3 rotating buffers x 8 fields x 32 slots;
+//              fields 0..4 = pixels labelled at each stage, 5 = pixels that
+//              reached the mixture stage.  Frame n accumulates into buffer
+//              n % 3, reads buffer (n - 1) % 3 for its illumination flag, and
+//              its block 0 clears buffer (n + 1) % 3.
+//   [768, 800) running totals, 8 x uint64 (fields as above), lagging one frame
+//   [800]      device error word
+constexpr int CTL_SLOTS = 32;
+constexpr int CTL_FIELDS = 8;
+constexpr int CTL_BUF_WORDS = CTL_SLOTS * CTL_FIELDS;
+constexpr int CTL_TOT_WORD = 3 * CTL_BUF_WORDS;     // 768
+constexpr int CTL_ERR_WORD = CTL_TOT_WORD + 32;     // 800
+constexpr int CTL_BYTES = 4096;
+
+// device error codes (bit flags in the error word)
+constexpr uint32_t DERR_TMA_TIMEOUT = 1u;
+
+// Everything a kernel needs, passed by value.
+struct DevParams {
+    int64_t P;          // pixels
+    int K;
+    unsigned flags;
+    float alpha, lam2, T_bg, w_init, var_init, var_min, var_max;
+    float tau_fd, eta, c_halt, w_illum;
+    int q_null;
+    int illum_permille;
+};
+
+struct StatePtrs {
+    uint32_t *ctl;
+    uint32_t *jl;       // previous frame RGB + label byte
+    void *conf;         // confidence plane
+    uint16_t *qab;      // qa | qb << 8
+    void *rga;          // 6 planes: m0 m1 m2 v0 v1 v2
+    int64_t rga_plane;  // elements between planes
+    uint8_t *gmm;       // mixture records
+    uint8_t *kde;       // prior, [P][3][256]
+};
+
+struct Layout {
+    size_t total, ctl, jl, conf, qab, rga, rga_plane_bytes, gmm, rec_bytes, kde, elem;
+    int64_t P, Pp;
+};
+
+int elem_bytes(int dtype);
+int rec_bytes(int dtype, int K);
+bool make_layout(const cog_params &p, Layout &L);
+
+struct ApplyArgs {
+    DevParams dp;
+    StatePtrs s;
+    const uint8_t *frame;
+    uint8_t *mask;
+    uint8_t *stagemap;   // may be null
+    uint32_t frame_no;   // frames applied since training
+};
+
+// launchers (return the launch error)
+cudaError_t launch_apply(int dtype, int K, const ApplyArgs &a, cudaStream_t st);
+cudaError_t launch_plain_gmm(int dtype, int K, const DevParams &dp, const StatePtrs &s,
+                             const uint8_t *frame, uint8_t *mask, cudaStream_t st);
+cudaError_t launch_kde_train(const DevParams &dp, const StatePtrs &s, const uint8_t *frames,
+                             int n_frames, const uint32_t *g, int R, cudaStream_t st);
+cudaError_t launch_warmup(int dtype, int K, const DevParams &dp, const StatePtrs &s,
+                          const uint8_t *frames, int n_frames, int r1, int r2, cudaStream_t st);
+
+}  // namespace cog

@@ -1,0 +1,72 @@
+"""Host-only checks of the C ABI: the library loads without a GPU, exports
+every function include/cog.h declares, and validates parameters."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def cog():
+    from paper_1705_09339_gb300.build import build
+    build()
+    from paper_1705_09339_gb300 import cog
+    return cog
+
+
+def _declared(header):
+    src = open(os.path.join(ROOT, "include", header)).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(cog_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_function(cog):
+    names = _declared("cog.h")
+    assert "cog_apply" in names and "cog_train_prior" in names and len(names) >= 15
+    for n in names:
+        assert hasattr(cog.lib, n), n
+
+
+def test_struct_sizes_match_header(cog):
+    import ctypes as C
+    assert C.sizeof(cog.cog_params) == 4 * 21
+    assert C.sizeof(cog.cog_stats) == 8 * 6 + 8
+    assert C.sizeof(cog.cog_layout) == 8 * 11
+
+
+def test_default_params_and_layout(cog):
+    p = cog.cog_default_params(1920, 1080, 5, state_dtype="f16")
+    assert (p.alpha, p.lambda_, p.T_bg) == (pytest.approx(0.01), 2.5, pytest.approx(0.7))
+    assert p.flags == cog.COG_ALL and p.kde_bw == 4
+    L = cog.cog_state_layout(p)
+    P = 1920 * 1080
+    Pp = (P + 4095) // 4096 * 4096
+    assert L.rec_bytes == 80 and L.elem_bytes == 2
+    assert L.kde + P * 768 <= L.total
+    for off in (L.jl, L.conf, L.qab, L.rga, L.gmm, L.kde):
+        assert off % 256 == 0
+    assert L.gmm - L.rga >= 6 * Pp * 2
+    assert cog.cog_state_bytes(p) == L.total
+    p32 = cog.cog_default_params(160, 120, 3)
+    assert cog.cog_state_layout(p32).rec_bytes == 96
+
+
+@pytest.mark.parametrize("field,value", [("K", 0), ("K", 9), ("width", 0), ("alpha", 0.0), ("alpha", 1.5),
+                                         ("var_min", 0.0), ("kde_bw", 0), ("kde_bw", 33), ("r2", -1),
+                                         ("illum_permille", 1001), ("flags", 16), ("state_dtype", 3),
+                                         ("w_illum", 1.0), ("T_bg", 1.5)])
+def test_invalid_params_rejected(cog, field, value):
+    p = cog.cog_default_params(64, 48, 3)
+    setattr(p, field, value)
+    with pytest.raises(cog.CogError) as e:
+        cog.cog_state_bytes(p)
+    assert e.value.status == cog.COG_ERR_INVALID_ARG
+    assert cog.cog_last_error_string(None)
+
+
+def test_null_context_calls_fail_cleanly(cog):
+    assert cog.lib.cog_sync(None) == cog.COG_ERR_INVALID_ARG
+    assert cog.lib.cog_destroy(None) == cog.COG_ERR_INVALID_ARG
+    assert cog.lib.cog_apply(None, None, None, None, None) == cog.COG_ERR_INVALID_ARG
