@@ -128,7 +128,7 @@ cog_status cog_state_layout(const cog_params *p, cog_layout *out);
 cog_status cog_create(const cog_params *p, void *cuda_stream, void *state_dev, cog_ctx **out);
 
 /* Training phase (Sec. 2): frames_dev holds n_frames >= 2 frames back to
- * back (n_frames x height x width x 3 bytes, 16-byte aligned).  Builds the
+ * back (n_frames x height x width x 3 bytes, any alignment).  Builds the
  * per-pixel, per-channel kernel-density prior over the frames (Sec. 2,
  * "Scene Prior"), the residue-class confidence weights (Sec. 2,
  * "Determining Learning Rate Hyper-parameters"), and warms the mixture of
@@ -141,10 +141,14 @@ cog_status cog_train_prior(cog_ctx *ctx, const uint8_t *frames_dev, int32_t n_fr
  * stage 0 frame difference, stage 1 running Gaussian average, stage 2 the
  * ordered Gaussians of Eq. 2 with the scene prior and the confidence of
  * Sec. 2 "Confidence Measure"; only the level that labels a pixel adapts.
- * frame_dev: height x width x 3 bytes, 16-byte aligned.  mask_dev: one byte
- * per pixel (255 = foreground), 8-byte aligned.  stagemap_dev: NULL, or one
- * COG_ST_* byte per pixel, 8-byte aligned.  stats_host: NULL, or receives
- * this frame's counts (the call then synchronises the stream).
+ * frame_dev: height x width x 3 bytes (any alignment; 16-byte aligned
+ * frames are staged by TMA bulk copies).  mask_dev: one byte per pixel
+ * (255 = foreground).  stagemap_dev: NULL, or one COG_ST_* byte per pixel.
+ * 8-byte aligned mask and stage map take vector stores.  stats_host: NULL,
+ * or receives this frame's counts (the call then synchronises the stream).
+ * The environment variable COG_PREFETCH, read by cog_create, selects when
+ * the running-average planes are fetched: 0 (default) decided per frame
+ * from the previous frame's occupancy, 1 always early, 2 only on demand.
  * COG_ERR_STATE before cog_train_prior. */
 cog_status cog_apply(cog_ctx *ctx, const uint8_t *frame_dev, uint8_t *mask_dev,
                      uint8_t *stagemap_dev, cog_stats *stats_host);

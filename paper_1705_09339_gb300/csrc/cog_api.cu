@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -64,6 +65,7 @@ struct cog_ctx {
     cog_status sticky;
     char err[512];
     uint8_t *stage_in, *stage_out;   // cog_apply_host staging buffers
+    uint32_t prefetch;               // stage-1 early-fetch policy (COG_PREFETCH)
 };
 
 static thread_local char g_create_err[512];
@@ -226,6 +228,9 @@ cog_status cog_create(const cog_params *p, void *cuda_stream, void *state_dev, c
     s.kde = c->state + c->L.kde;
     c->sticky = COG_OK;
     c->err[0] = 0;
+    // stage-1 early-fetch policy: 0 = decided per frame from the previous
+    // frame's occupancy (default), 1 = always, 2 = never
+    if (const char *pf = getenv("COG_PREFETCH")) c->prefetch = (uint32_t)atoi(pf) % 3;
     *out = c;
     return COG_OK;
 }
@@ -242,7 +247,6 @@ cog_status cog_train_prior(cog_ctx *c, const uint8_t *frames_dev, int32_t n_fram
     cog_status s = check_ctx(c);
     if (s) return s;
     if (!frames_dev) return set_err(c, COG_ERR_INVALID_ARG, "frames_dev is NULL");
-    if ((uintptr_t)frames_dev & 15) return set_err(c, COG_ERR_INVALID_ARG, "frames_dev must be 16-byte aligned");
     if (n_frames < 2) return set_err(c, COG_ERR_INVALID_ARG, "need at least 2 training frames");
     const int bw = c->p.kde_bw, R = 3 * bw;
     uint32_t g[100];
@@ -309,9 +313,6 @@ cog_status cog_apply(cog_ctx *c, const uint8_t *frame_dev, uint8_t *mask_dev, ui
     if (s) return s;
     if (!c->trained) return set_err(c, COG_ERR_STATE, "cog_apply before cog_train_prior");
     if (!frame_dev || !mask_dev) return set_err(c, COG_ERR_INVALID_ARG, "frame_dev and mask_dev are required");
-    if ((uintptr_t)frame_dev & 15) return set_err(c, COG_ERR_INVALID_ARG, "frame_dev must be 16-byte aligned");
-    if ((uintptr_t)mask_dev & 7) return set_err(c, COG_ERR_INVALID_ARG, "mask_dev must be 8-byte aligned");
-    if ((uintptr_t)stagemap_dev & 7) return set_err(c, COG_ERR_INVALID_ARG, "stagemap_dev must be 8-byte aligned");
     ApplyArgs a;
     a.dp = c->dp;
     a.s = c->sp;
@@ -319,6 +320,9 @@ cog_status cog_apply(cog_ctx *c, const uint8_t *frame_dev, uint8_t *mask_dev, ui
     a.mask = mask_dev;
     a.stagemap = stagemap_dev;
     a.frame_no = (uint32_t)(c->frame_no % 3);
+    a.frame_al16 = ((uintptr_t)frame_dev & 15) == 0;
+    a.out_al8 = ((uintptr_t)mask_dev & 7) == 0 && ((uintptr_t)stagemap_dev & 7) == 0;
+    a.prefetch = c->prefetch;
     cudaError_t e;
     switch (c->p.state_dtype) {
     case COG_F32: e = launch_apply_f32(c->p.K, a, c->stream); break;

@@ -67,7 +67,10 @@ struct ApplyArgs {
     const uint8_t *frame;
     uint8_t *mask;
     uint8_t *stagemap;   // may be null
-    uint32_t frame_no;   // frames applied since training
+    uint32_t frame_no;   // frames applied since training (mod 3)
+    uint32_t frame_al16; // frame pointer 16-byte aligned: staged by TMA
+    uint32_t out_al8;    // mask (and stage map) 8-byte aligned: vector stores
+    uint32_t prefetch;   // 0 = by occupancy, 1 = always, 2 = never fetch stage-1 planes early
 };
 
 // launchers (return the launch error)

@@ -7,21 +7,67 @@
 
 namespace cog {
 
-// One thread per pixel: frame bytes, record, mixture step, record, mask.
+// One thread per pixel.  The CTA's tile of mixture records (256 x 16-byte-
+// multiple records, contiguous) and its frame bytes arrive by TMA bulk
+// copies; each thread runs the mixture step from shared memory and writes
+// its record back there; one thread stores the tile's records with a TMA
+// bulk store.  Every byte moves in whole, coalesced transfers.
+constexpr int PLAIN_TPB = 256;
+
 template <typename T, int K>
-__global__ void __launch_bounds__(256) plain_gmm_kernel(const DevParams dp, uint8_t *gmm,
-                                                        const uint8_t *frame, uint8_t *mask)
+__host__ __device__ constexpr int plain_smem_bytes()
 {
-    const int64_t p = (int64_t)blockIdx.x * 256 + threadIdx.x;
-    if (p >= dp.P) return;
-    float I[3];
+    return PLAIN_TPB * Rec<T, K>::BYTES + PLAIN_TPB * 3 + PLAIN_TPB;
+}
+
+template <typename T, int K>
+__global__ void __launch_bounds__(PLAIN_TPB) plain_gmm_kernel(const DevParams dp, uint8_t *gmm,
+                                                              const uint8_t *frame, uint8_t *mask,
+                                                              uint32_t frame_al16, uint32_t *err)
+{
+    constexpr int RB = Rec<T, K>::BYTES;
+    extern __shared__ __align__(128) uint8_t smem[];
+    uint8_t *rec_s = smem;
+    uint8_t *frame_s = smem + PLAIN_TPB * RB;
+    uint8_t *mask_s = frame_s + PLAIN_TPB * 3;
+    __shared__ __align__(8) uint64_t bar;
+    const int tid = threadIdx.x;
+    const int64_t p0 = (int64_t)blockIdx.x * PLAIN_TPB;
+    const int npx = (int)min((int64_t)PLAIN_TPB, dp.P - p0);
+    const int fbytes = npx * 3, fbulk = frame_al16 ? (fbytes & ~15) : 0;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        mbar_expect_tx(&bar, (uint32_t)(npx * RB + fbulk));
+        bulk_g2s(rec_s, gmm + p0 * RB, (uint32_t)(npx * RB), &bar);
+        if (fbulk) bulk_g2s(frame_s, frame + p0 * 3, (uint32_t)fbulk, &bar);
+    }
+    for (int i = fbulk + tid; i < fbytes; i += PLAIN_TPB) frame_s[i] = frame[p0 * 3 + i];
+    __syncthreads();
+    const bool timed_out = !mbar_wait(&bar, 0);
+    if (__syncthreads_or(timed_out)) {
+        if (tid == 0) atomicOr(err, DERR_TMA_TIMEOUT);
+        return;
+    }
+    if (tid < npx) {
+        float I[3];
 #pragma unroll
-    for (int c = 0; c < 3; c++) I[c] = (float)frame[p * 3 + c];
-    Mix<K> m;
-    rec_load<T, K>(gmm, p, m);
-    const MixOut o = mix_step<K>(m, I, dp.alpha, dp);
-    rec_store<T, K>(gmm, p, m);
-    mask[p] = o.fg ? 255 : 0;
+        for (int c = 0; c < 3; c++) I[c] = (float)frame_s[tid * 3 + c];
+        Mix<K> m;
+        rec_load<T, K>(rec_s, tid, m);
+        const MixOut o = mix_step<K>(m, I, dp.alpha, dp);
+        rec_store<T, K>(rec_s, tid, m);
+        mask_s[tid] = o.fg ? 255 : 0;
+    }
+    fence_async_smem();
+    __syncthreads();
+    const bool mask_bulk = ((uintptr_t)(mask + p0) & 15) == 0 && (npx & 15) == 0;
+    if (tid == 0) {
+        bulk_s2g(gmm + p0 * RB, rec_s, (uint32_t)(npx * RB));
+        if (mask_bulk) bulk_s2g(mask + p0, mask_s, (uint32_t)npx);
+        bulk_commit();
+        bulk_wait_read0();   // shared memory must outlive the bulk reads
+    }
+    if (!mask_bulk && tid < npx) mask[p0 + tid] = mask_s[tid];
 }
 
 // Training (Sec. 2): per pixel, in one pass over the N frames,
@@ -106,8 +152,15 @@ template <typename T, int K>
 cudaError_t launch_plain_t(const DevParams &dp, const StatePtrs &s, const uint8_t *frame,
                            uint8_t *mask, cudaStream_t st)
 {
-    const int64_t grid = (dp.P + 255) / 256;
-    plain_gmm_kernel<T, K><<<(unsigned)grid, 256, 0, st>>>(dp, s.gmm, frame, mask);
+    constexpr int smem = plain_smem_bytes<T, K>();
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(plain_gmm_kernel<T, K>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+    }
+    const int64_t grid = (dp.P + PLAIN_TPB - 1) / PLAIN_TPB;
+    plain_gmm_kernel<T, K><<<(unsigned)grid, PLAIN_TPB, smem, st>>>(
+        dp, s.gmm, frame, mask, ((uintptr_t)frame & 15) == 0, s.ctl + CTL_ERR_WORD);
     return cudaGetLastError();
 }
 
