@@ -96,17 +96,19 @@ typedef struct cog_stats {
 /* Byte offsets of the state buffer's planes (for export/import decoding).
  * P = width*height; Pp = P rounded up to a multiple of 4096. */
 typedef struct cog_layout {
-    uint64_t total;          /* bytes of the whole state buffer                         */
-    uint64_t ctl;            /* control block (counters), 4096 bytes                    */
-    uint64_t jl;             /* uint32[Pp]: previous frame R,G,B in bytes 0..2, label 3 */
-    uint64_t conf;           /* dtype[Pp]: confidence C                                 */
-    uint64_t qab;            /* uint16[Pp]: residue weights qa | qb << 8 (of 255)       */
-    uint64_t rga;            /* 6 planes dtype[Pp]: m0 m1 m2 v0 v1 v2                   */
-    uint64_t rga_plane;      /* bytes between consecutive running-average planes        */
-    uint64_t gmm;            /* per-pixel records of rec_bytes: K x (w, mu0..2, v0..2)  */
-    uint64_t rec_bytes;      /* K*7*sizeof(dtype) rounded up to 16                      */
-    uint64_t kde;            /* uint8[P][3][256]: peak-normalised prior                 */
-    uint64_t elem_bytes;     /* sizeof(dtype)                                           */
+    uint64_t total;          /* bytes of the whole state buffer                          */
+    uint64_t ctl;            /* control block (counters), 4096 bytes                     */
+    uint64_t jl;             /* uint32[Pp]: previous frame R,G,B in bytes 0..2, label 3  */
+    uint64_t conf;           /* dtype[Pp]: confidence C                                  */
+    uint64_t s1;             /* stage-1 records, s1_bytes each: m0 m1 m2 v0 v1 v2 as     */
+                             /* dtype, then uint16 qa | qb << 8 (16-bit dtypes) or       */
+                             /* uint32 (FP32), zero padding                              */
+    uint64_t s1_bytes;       /* 16 (FP16/BF16) or 32 (FP32)                              */
+    uint64_t gmm;            /* per-pixel records of rec_bytes: K x (w, mu0..2, v0..2)   */
+    uint64_t rec_bytes;      /* K*7*sizeof(dtype) rounded up to 16                       */
+    uint64_t queue;          /* scratch: survivor queue, 16 bytes x Pp                   */
+    uint64_t kde;            /* uint8[P][3][256]: peak-normalised prior                  */
+    uint64_t elem_bytes;     /* sizeof(dtype)                                            */
 } cog_layout;
 
 typedef struct cog_ctx cog_ctx;
@@ -144,11 +146,11 @@ cog_status cog_train_prior(cog_ctx *ctx, const uint8_t *frames_dev, int32_t n_fr
  * frame_dev: height x width x 3 bytes (any alignment; 16-byte aligned
  * frames are staged by TMA bulk copies).  mask_dev: one byte per pixel
  * (255 = foreground).  stagemap_dev: NULL, or one COG_ST_* byte per pixel.
- * 8-byte aligned mask and stage map take vector stores.  stats_host: NULL,
- * or receives this frame's counts (the call then synchronises the stream).
- * The environment variable COG_PREFETCH, read by cog_create, selects when
- * the running-average planes are fetched: 0 (default) decided per frame
- * from the previous frame's occupancy, 1 always early, 2 only on demand.
+ * 8-byte aligned frames, masks and stage maps take vector accesses.
+ * stats_host: NULL, or receives this frame's counts (the call then
+ * synchronises the stream).  Two kernels run per frame: stages 0 and 1 over
+ * every pixel, then the mixture stage over the pixels left (compacted into
+ * the state's survivor queue).
  * COG_ERR_STATE before cog_train_prior. */
 cog_status cog_apply(cog_ctx *ctx, const uint8_t *frame_dev, uint8_t *mask_dev,
                      uint8_t *stagemap_dev, cog_stats *stats_host);
@@ -180,6 +182,15 @@ cog_status cog_import_state(cog_ctx *ctx, const void *src_host, size_t bytes);
 
 /* Number of frames applied since training, and the device state pointer. */
 cog_status cog_info(cog_ctx *ctx, int64_t *frames_applied, void **state_dev);
+
+/* Per-kernel timing.  cog_profile_begin makes the next max_frames calls
+ * of cog_apply record CUDA events on the context's stream around each of
+ * its two kernels (stages 0-1, then the mixture stage); cog_profile_end
+ * synchronises and returns the summed milliseconds of each kernel and the
+ * number of frames recorded, then releases the events.  Both synchronise
+ * the stream. */
+cog_status cog_profile_begin(cog_ctx *ctx, int32_t max_frames);
+cog_status cog_profile_end(cog_ctx *ctx, double *stage01_ms, double *stage2_ms, int64_t *frames);
 
 /* Human-readable description of the context's last error ("" if none).
  * With ctx == NULL: the last error of a failed cog_create on this thread. */

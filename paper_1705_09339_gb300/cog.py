@@ -46,8 +46,8 @@ class cog_stats(C.Structure):
 
 
 class cog_layout(C.Structure):
-    _fields_ = [(n, C.c_uint64) for n in ("total", "ctl", "jl", "conf", "qab", "rga", "rga_plane", "gmm",
-                                          "rec_bytes", "kde", "elem_bytes")]
+    _fields_ = [(n, C.c_uint64) for n in ("total", "ctl", "jl", "conf", "s1", "s1_bytes", "gmm", "rec_bytes",
+                                          "queue", "kde", "elem_bytes")]
 
 
 class CogError(RuntimeError):
@@ -76,6 +76,8 @@ def _load() -> C.CDLL:
         "cog_export_state": (C.c_int, [vp, vp, sz]),
         "cog_import_state": (C.c_int, [vp, vp, sz]),
         "cog_info": (C.c_int, [vp, P(C.c_int64), P(vp)]),
+        "cog_profile_begin": (C.c_int, [vp, i32]),
+        "cog_profile_end": (C.c_int, [vp, P(C.c_double), P(C.c_double), P(C.c_int64)]),
         "cog_last_error_string": (C.c_char_p, [vp]),
         "cog_destroy": (C.c_int, [vp]),
     }
@@ -181,6 +183,17 @@ def cog_info(ctx):
     return n.value, s.value
 
 
+def cog_profile_begin(ctx, max_frames: int) -> None:
+    _check(lib.cog_profile_begin(ctx, max_frames), ctx)
+
+
+def cog_profile_end(ctx):
+    """Returns (stage01_ms, stage2_ms, frames) summed over the recorded frames."""
+    a, b, n = C.c_double(), C.c_double(), C.c_int64()
+    _check(lib.cog_profile_end(ctx, C.byref(a), C.byref(b), C.byref(n)), ctx)
+    return a.value, b.value, n.value
+
+
 def cog_last_error_string(ctx=None) -> str:
     m = lib.cog_last_error_string(ctx)
     return m.decode() if m else ""
@@ -205,6 +218,20 @@ def _bf16_to_f32(u16: np.ndarray) -> np.ndarray:
     return (u16.astype(np.uint32) << 16).view(np.float32)
 
 
+def _s1_view(buf, L, P, p):
+    """Stage-1 records as (values [P, 6] float64, qab [P] uint16)."""
+    rb = int(L.s1_bytes)
+    raw = buf[L.s1:L.s1 + P * rb].reshape(P, rb)
+    if p.state_dtype == COG_F32:
+        vals = raw[:, :24].copy().view(np.float32).astype(np.float64)
+        qab = raw[:, 24:28].copy().view(np.uint32).reshape(P).astype(np.uint16)
+    else:
+        h = raw[:, :12].copy().view(np.uint16)
+        vals = (_bf16_to_f32(h) if p.state_dtype == COG_BF16 else h.view(np.float16)).astype(np.float64)
+        qab = raw[:, 12:14].copy().view(np.uint16).reshape(P)
+    return vals.reshape(P, 6), qab
+
+
 def decode_state(buf: np.ndarray, p: cog_params) -> dict:
     """FP64 copies of the model planes of an exported state image:
     w [P,K], mu [P,K,3], var [P,K,3], rga_m [P,3], rga_v [P,3], conf [P],
@@ -222,8 +249,7 @@ def decode_state(buf: np.ndarray, p: cog_params) -> dict:
     prev = np.stack([(jl >> (8 * c)) & 0xFF for c in range(3)], axis=1).astype(np.uint8)
     label = (jl >> 24).astype(np.uint8)
     conf = vals(L.conf, P)
-    qab = _plane(buf, L.qab, P, np.uint16)
-    rga = np.stack([vals(L.rga + i * L.rga_plane, P) for i in range(6)], axis=1)
+    s1, qab = _s1_view(buf, L, P, p)
     rec_elems = L.rec_bytes // L.elem_bytes
     if p.state_dtype == COG_BF16:
         recs = _bf16_to_f32(_plane(buf, L.gmm, Pp * rec_elems, np.uint16)).astype(np.float64)
@@ -232,8 +258,17 @@ def decode_state(buf: np.ndarray, p: cog_params) -> dict:
     recs = recs.reshape(Pp, rec_elems)[:P, :7 * K].reshape(P, K, 7)
     kde = buf[L.kde:L.kde + P * 768].reshape(P, 3, 256)
     return dict(w=recs[:, :, 0].copy(), mu=recs[:, :, 1:4].copy(), var=recs[:, :, 4:7].copy(),
-                rga_m=rga[:, :3].copy(), rga_v=rga[:, 3:].copy(), conf=conf, label=label, prev=prev,
+                rga_m=s1[:, :3].copy(), rga_v=s1[:, 3:].copy(), conf=conf, label=label, prev=prev,
                 kde=kde, qa=(qab & 0xFF).astype(np.uint8), qb=(qab >> 8).astype(np.uint8))
+
+
+def _to_storage(arr, dtype) -> np.ndarray:
+    """float64 values -> raw little-endian storage words (uint16/float32)."""
+    arr = np.asarray(arr, np.float64)
+    if dtype == COG_BF16:
+        f = arr.astype(np.float32).view(np.uint32)
+        return ((f + 0x7FFF + ((f >> 16) & 1)) >> 16).astype(np.uint16)
+    return arr.astype(_NP_DT[dtype])
 
 
 def encode_state(buf: np.ndarray, p: cog_params, st: dict) -> np.ndarray:
@@ -243,30 +278,26 @@ def encode_state(buf: np.ndarray, p: cog_params, st: dict) -> np.ndarray:
     P, K = p.width * p.height, p.K
     Pp = (P + 4095) // 4096 * 4096
     out = buf.copy()
-
-    def put(off, arr):
-        arr = np.asarray(arr, np.float64).reshape(-1)
-        if p.state_dtype == COG_BF16:
-            f = arr.astype(np.float32).view(np.uint32)
-            r = ((f + 0x7FFF + ((f >> 16) & 1)) >> 16).astype(np.uint16)
-            out[off:off + r.nbytes] = r.view(np.uint8)
-        else:
-            r = arr.astype(_NP_DT[p.state_dtype])
-            out[off:off + r.nbytes] = r.view(np.uint8)
-
     jl = (st["prev"][:, 0].astype(np.uint32) | (st["prev"][:, 1].astype(np.uint32) << 8)
           | (st["prev"][:, 2].astype(np.uint32) << 16) | (st["label"].astype(np.uint32) << 24))
     out[L.jl:L.jl + 4 * P] = jl.view(np.uint8)
-    put(L.conf, st["conf"])
-    qab = st["qa"].astype(np.uint16) | (st["qb"].astype(np.uint16) << 8)
-    out[L.qab:L.qab + 2 * P] = qab.view(np.uint8)
-    for c in range(3):
-        put(L.rga + c * L.rga_plane, st["rga_m"][:, c])
-        put(L.rga + (3 + c) * L.rga_plane, st["rga_v"][:, c])
+    c = _to_storage(st["conf"], p.state_dtype)
+    out[L.conf:L.conf + c.nbytes] = c.view(np.uint8)
+    rb = int(L.s1_bytes)
+    rec = np.zeros((P, rb), np.uint8)
+    v = _to_storage(np.concatenate([st["rga_m"], st["rga_v"]], axis=1), p.state_dtype).reshape(P, 6)
+    rec[:, :v.itemsize * 6] = v.view(np.uint8).reshape(P, -1)
+    qab = st["qa"].astype(np.uint32) | (st["qb"].astype(np.uint32) << 8)
+    if p.state_dtype == COG_F32:
+        rec[:, 24:28] = qab.astype(np.uint32).view(np.uint8).reshape(P, 4)
+    else:
+        rec[:, 12:14] = qab.astype(np.uint16).view(np.uint8).reshape(P, 2)
+    out[L.s1:L.s1 + P * rb] = rec.reshape(-1)
     rec_elems = L.rec_bytes // L.elem_bytes
     recs = np.zeros((Pp, rec_elems))
     r = np.concatenate([st["w"][:, :, None], st["mu"], st["var"]], axis=2).reshape(P, 7 * K)
     recs[:P, :7 * K] = r
-    put(L.gmm, recs)
+    g = _to_storage(recs, p.state_dtype)
+    out[L.gmm:L.gmm + g.nbytes] = g.view(np.uint8).reshape(-1)
     out[L.kde:L.kde + P * 768] = np.asarray(st["kde"], np.uint8).reshape(-1)
     return out

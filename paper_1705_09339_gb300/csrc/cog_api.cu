@@ -12,9 +12,9 @@
 #include "cog_internal.h"
 
 namespace cog {
-cudaError_t launch_apply_f32(int, const ApplyArgs &, cudaStream_t);
-cudaError_t launch_apply_f16(int, const ApplyArgs &, cudaStream_t);
-cudaError_t launch_apply_bf16(int, const ApplyArgs &, cudaStream_t);
+cudaError_t launch_apply_f32(int, const ApplyArgs &, cudaStream_t, const ApplyEvents *);
+cudaError_t launch_apply_f16(int, const ApplyArgs &, cudaStream_t, const ApplyEvents *);
+cudaError_t launch_apply_bf16(int, const ApplyArgs &, cudaStream_t, const ApplyEvents *);
 cudaError_t launch_plain_f32(int, const DevParams &, const StatePtrs &, const uint8_t *, uint8_t *, cudaStream_t);
 cudaError_t launch_plain_f16(int, const DevParams &, const StatePtrs &, const uint8_t *, uint8_t *, cudaStream_t);
 cudaError_t launch_plain_bf16(int, const DevParams &, const StatePtrs &, const uint8_t *, uint8_t *, cudaStream_t);
@@ -26,6 +26,8 @@ int elem_bytes(int dtype) { return dtype == COG_F32 ? 4 : 2; }
 
 int rec_bytes(int dtype, int K) { return (K * 7 * elem_bytes(dtype) + 15) / 16 * 16; }
 
+int s1_bytes(int dtype) { return dtype == COG_F32 ? 32 : 16; }
+
 static size_t up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 bool make_layout(const cog_params &p, Layout &L)
@@ -34,14 +36,14 @@ bool make_layout(const cog_params &p, Layout &L)
     L.Pp = (int64_t)up((size_t)L.P, PX_ALIGN);
     L.elem = (size_t)elem_bytes(p.state_dtype);
     L.rec_bytes = (size_t)rec_bytes(p.state_dtype, p.K);
+    L.s1_bytes = (size_t)s1_bytes(p.state_dtype);
     size_t o = 0;
     L.ctl = o;  o += CTL_BYTES;
     L.jl = o;   o = up(o + (size_t)L.Pp * 4, 256);
     L.conf = o; o = up(o + (size_t)L.Pp * L.elem, 256);
-    L.qab = o;  o = up(o + (size_t)L.Pp * 2, 256);
-    L.rga = o;  L.rga_plane_bytes = (size_t)L.Pp * L.elem;
-    o = up(o + 6 * L.rga_plane_bytes, 256);
+    L.s1 = o;   o = up(o + (size_t)L.Pp * L.s1_bytes, 256);
     L.gmm = o;  o = up(o + (size_t)L.Pp * L.rec_bytes, 256);
+    L.queue = o; o = up(o + (size_t)L.Pp * 16, 256);
     L.kde = o;  o = up(o + (size_t)L.P * 768, 256);
     L.total = o;
     return true;
@@ -65,7 +67,9 @@ struct cog_ctx {
     cog_status sticky;
     char err[512];
     uint8_t *stage_in, *stage_out;   // cog_apply_host staging buffers
-    uint32_t prefetch;               // stage-1 early-fetch policy (COG_PREFETCH)
+    int n_sm;                        // multiprocessors of the device
+    std::vector<ApplyEvents> prof;   // per-frame kernel timing events (profiling on)
+    int64_t prof_n;                  // frames recorded since profiling was enabled
 };
 
 static thread_local char g_create_err[512];
@@ -146,8 +150,8 @@ cog_status cog_state_layout(const cog_params *p, cog_layout *out)
     if (!out) return set_err(nullptr, COG_ERR_INVALID_ARG, "out is NULL");
     Layout L;
     make_layout(*p, L);
-    out->total = L.total; out->ctl = L.ctl; out->jl = L.jl; out->conf = L.conf; out->qab = L.qab;
-    out->rga = L.rga; out->rga_plane = L.rga_plane_bytes; out->gmm = L.gmm; out->rec_bytes = L.rec_bytes;
+    out->total = L.total; out->ctl = L.ctl; out->jl = L.jl; out->conf = L.conf; out->s1 = L.s1;
+    out->s1_bytes = L.s1_bytes; out->gmm = L.gmm; out->rec_bytes = L.rec_bytes; out->queue = L.queue;
     out->kde = L.kde; out->elem_bytes = L.elem;
     return COG_OK;
 }
@@ -221,16 +225,15 @@ cog_status cog_create(const cog_params *p, void *cuda_stream, void *state_dev, c
     s.ctl = (uint32_t *)(c->state + c->L.ctl);
     s.jl = (uint32_t *)(c->state + c->L.jl);
     s.conf = c->state + c->L.conf;
-    s.qab = (uint16_t *)(c->state + c->L.qab);
-    s.rga = c->state + c->L.rga;
-    s.rga_plane = c->L.Pp;
+    s.s1 = c->state + c->L.s1;
     s.gmm = c->state + c->L.gmm;
+    s.queue = (uint4 *)(c->state + c->L.queue);
     s.kde = c->state + c->L.kde;
     c->sticky = COG_OK;
     c->err[0] = 0;
-    // stage-1 early-fetch policy: 0 = decided per frame from the previous
-    // frame's occupancy (default), 1 = always, 2 = never
-    if (const char *pf = getenv("COG_PREFETCH")) c->prefetch = (uint32_t)atoi(pf) % 3;
+    if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
+        c->n_sm < 1)
+        c->n_sm = 1;
     *out = c;
     return COG_OK;
 }
@@ -320,14 +323,16 @@ cog_status cog_apply(cog_ctx *c, const uint8_t *frame_dev, uint8_t *mask_dev, ui
     a.mask = mask_dev;
     a.stagemap = stagemap_dev;
     a.frame_no = (uint32_t)(c->frame_no % 3);
-    a.frame_al16 = ((uintptr_t)frame_dev & 15) == 0;
-    a.out_al8 = ((uintptr_t)mask_dev & 7) == 0 && ((uintptr_t)stagemap_dev & 7) == 0;
-    a.prefetch = c->prefetch;
+    a.frame_al4 = ((uintptr_t)frame_dev & 3) == 0;
+    a.out_al4 = ((uintptr_t)mask_dev & 3) == 0 && ((uintptr_t)stagemap_dev & 3) == 0;
+    a.k2_grid = (uint32_t)c->n_sm;
+    const ApplyEvents *ev = nullptr;
+    if (!c->prof.empty() && c->prof_n < (int64_t)c->prof.size()) ev = &c->prof[(size_t)c->prof_n++];
     cudaError_t e;
     switch (c->p.state_dtype) {
-    case COG_F32: e = launch_apply_f32(c->p.K, a, c->stream); break;
-    case COG_F16: e = launch_apply_f16(c->p.K, a, c->stream); break;
-    default: e = launch_apply_bf16(c->p.K, a, c->stream); break;
+    case COG_F32: e = launch_apply_f32(c->p.K, a, c->stream, ev); break;
+    case COG_F16: e = launch_apply_f16(c->p.K, a, c->stream, ev); break;
+    default: e = launch_apply_bf16(c->p.K, a, c->stream, ev); break;
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "cog_apply launch");
     c->frame_no++;
@@ -413,7 +418,7 @@ cog_status cog_sync(cog_ctx *c)
 
 // The exported image carries the host-side frame counter and trained flag in
 // otherwise unused control words so that an import resumes exactly.
-static const int CTL_FRAME_WORD = CTL_ERR_WORD + 2;   // uint64
+static const int CTL_FRAME_WORD = CTL_ERR_WORD + 2;   // uint64 (words 802, 803)
 static const int CTL_TRAINED_WORD = CTL_ERR_WORD + 4;
 
 cog_status cog_export_state(cog_ctx *c, void *dst_host, size_t bytes)
@@ -457,6 +462,58 @@ cog_status cog_info(cog_ctx *c, int64_t *frames_applied, void **state_dev)
     return COG_OK;
 }
 
+static void free_profile(cog_ctx *c)
+{
+    for (auto &e : c->prof) {
+        cudaEventDestroy(e.e0);
+        cudaEventDestroy(e.e1);
+        cudaEventDestroy(e.e2);
+    }
+    c->prof.clear();
+    c->prof_n = 0;
+}
+
+cog_status cog_profile_begin(cog_ctx *c, int32_t max_frames)
+{
+    cog_status s = check_ctx(c);
+    if (s) return s;
+    if (max_frames < 0 || max_frames > (1 << 20)) return set_err(c, COG_ERR_INVALID_ARG, "max_frames out of range");
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cog_profile_begin");
+    free_profile(c);
+    c->prof.resize((size_t)max_frames);
+    for (auto &ev : c->prof) {
+        if (cudaEventCreate(&ev.e0) != cudaSuccess || cudaEventCreate(&ev.e1) != cudaSuccess ||
+            cudaEventCreate(&ev.e2) != cudaSuccess) {
+            cudaGetLastError();
+            c->prof.clear();
+            return set_err(c, COG_ERR_OOM, "cudaEventCreate failed");
+        }
+    }
+    return COG_OK;
+}
+
+cog_status cog_profile_end(cog_ctx *c, double *stage01_ms, double *stage2_ms, int64_t *frames)
+{
+    cog_status s = check_ctx(c);
+    if (s) return s;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cog_profile_end");
+    double a = 0, b = 0;
+    for (int64_t i = 0; i < c->prof_n; i++) {
+        float x = 0, y = 0;
+        cudaEventElapsedTime(&x, c->prof[(size_t)i].e0, c->prof[(size_t)i].e1);
+        cudaEventElapsedTime(&y, c->prof[(size_t)i].e1, c->prof[(size_t)i].e2);
+        a += x;
+        b += y;
+    }
+    if (stage01_ms) *stage01_ms = a;
+    if (stage2_ms) *stage2_ms = b;
+    if (frames) *frames = c->prof_n;
+    free_profile(c);
+    return COG_OK;
+}
+
 const char *cog_last_error_string(cog_ctx *c)
 {
     return c ? c->err : g_create_err;
@@ -468,6 +525,7 @@ cog_status cog_destroy(cog_ctx *c)
     cog_status s = c->sticky;
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess && s == COG_OK) s = COG_ERR_CUDA;
+    free_profile(c);
     if (c->stage_in) cudaFree(c->stage_in);
     if (c->owns) cudaFree(c->state);
     delete c;

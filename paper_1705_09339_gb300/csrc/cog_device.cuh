@@ -73,6 +73,51 @@ template <typename T> struct Vec8 {
     }
 };
 
+// N consecutive values of a plane held as raw 32-bit words, loaded and
+// stored with the widest aligned vector (N*sizeof(T) = 8, 16 or 32 bytes).
+template <typename T, int N> struct VecN {
+    static constexpr int BYTES = N * Store<T>::bytes;
+    static constexpr int NW = BYTES / 4;
+    uint32_t w[NW];
+    __device__ __forceinline__ void load(const T *p) {
+        if (BYTES % 16 == 0) {
+#pragma unroll
+            for (int i = 0; i < BYTES / 16; i++) {
+                const uint4 v = reinterpret_cast<const uint4 *>(p)[i];
+                w[4 * i] = v.x; w[4 * i + 1] = v.y; w[4 * i + 2] = v.z; w[4 * i + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < BYTES / 8; i++) {
+                const uint2 v = reinterpret_cast<const uint2 *>(p)[i];
+                w[2 * i] = v.x; w[2 * i + 1] = v.y;
+            }
+        }
+    }
+    __device__ __forceinline__ void store(T *p) const {
+        if (BYTES % 16 == 0) {
+#pragma unroll
+            for (int i = 0; i < BYTES / 16; i++)
+                reinterpret_cast<uint4 *>(p)[i] = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < BYTES / 8; i++)
+                reinterpret_cast<uint2 *>(p)[i] = make_uint2(w[2 * i], w[2 * i + 1]);
+        }
+    }
+    __device__ __forceinline__ float get(int i) const {
+        if (Store<T>::bytes == 4) return Store<T>::unbits(w[i]);
+        const uint32_t x = w[i >> 1];
+        return Store<T>::unbits((i & 1) ? (x >> 16) : (x & 0xffffu));
+    }
+    __device__ __forceinline__ void set(int i, float x) {
+        const uint32_t b = Store<T>::bits(x);
+        if (Store<T>::bytes == 4) { w[i] = b; return; }
+        const uint32_t o = w[i >> 1];
+        w[i >> 1] = (i & 1) ? ((o & 0xffffu) | (b << 16)) : ((o & 0xffff0000u) | b);
+    }
+};
+
 // ------------------------------------------------------------ mixture record
 // Per-pixel record: K components of (w, mu0, mu1, mu2, v0, v1, v2), stored
 // contiguously and padded to a 16-byte multiple so one survivor's record is
@@ -85,6 +130,44 @@ template <typename T, int K> struct Rec {
 
 template <int K> struct Mix {
     float w[K], mu[K][3], v[K][3];
+};
+
+// ----------------------------------------------------------- stage-1 record
+// Per-pixel running average and residue weights, one aligned block per
+// pixel: (m0, m1, m2, v0, v1, v2, qa | qb << 8), 16 bytes with 16-bit
+// storage, 32 with FP32.  Only pixels past stage 0 touch it, so a 32-byte
+// sector serves two pixels instead of sixteen planes' worth.
+template <typename T> struct S1Rec {
+    static constexpr int BYTES = Store<T>::bytes == 4 ? 32 : 16;
+    static constexpr int NV = BYTES / 16;
+    uint4 u[NV];
+    __device__ __forceinline__ void load(const uint8_t *base, int64_t p) {
+#pragma unroll
+        for (int i = 0; i < NV; i++) u[i] = reinterpret_cast<const uint4 *>(base + p * BYTES)[i];
+    }
+    __device__ __forceinline__ void store(uint8_t *base, int64_t p) const {
+#pragma unroll
+        for (int i = 0; i < NV; i++) reinterpret_cast<uint4 *>(base + p * BYTES)[i] = u[i];
+    }
+    __device__ __forceinline__ float get(int e) const {   // e: 0..2 mean, 3..5 variance
+        if (Store<T>::bytes == 4) return Store<T>::unbits(u4get(u[e >> 2], e & 3));
+        const uint32_t w = u4get(u[0], e >> 1);
+        return Store<T>::unbits((e & 1) ? (w >> 16) : (w & 0xffffu));
+    }
+    __device__ __forceinline__ void set(int e, float x) {
+        const uint32_t b = Store<T>::bits(x);
+        if (Store<T>::bytes == 4) { u4set(u[e >> 2], e & 3, b); return; }
+        uint32_t w = u4get(u[0], e >> 1);
+        w = (e & 1) ? ((w & 0xffffu) | (b << 16)) : ((w & 0xffff0000u) | b);
+        u4set(u[0], e >> 1, w);
+    }
+    __device__ __forceinline__ uint32_t qab() const {
+        return Store<T>::bytes == 4 ? u4get(u[NV - 1], 2) : (u[0].w & 0xffffu);
+    }
+    __device__ __forceinline__ void set_qab(uint32_t q) {
+        if (Store<T>::bytes == 4) { u4set(u[NV - 1], 2, q); u4set(u[NV - 1], 3, 0u); }
+        else u[0].w = q;
+    }
 };
 
 template <typename T, int K>
@@ -161,44 +244,65 @@ struct MixOut {
     float tm;    // match statistic of the matched component (pre-update)
 };
 
+// Decisions are taken in division-free form: the rank order compares
+// w_j^2 (v_k0+v_k1+v_k2) with w_k^2 (v_j0+v_j1+v_j2) (the mean's 1/3
+// cancels), and a channel matches when (I-mu)^2 < lam^2 v.  These differ
+// from the quotient forms only within rounding of the threshold.
 template <int K>
-__device__ __forceinline__ MixOut mix_step(Mix<K> &m, const float I[3], float a, const DevParams &dp)
+__device__ __forceinline__ void rank_positions(const Mix<K> &m, int pos[K])
 {
-    float r[K];
+    float wsq[K], vs[K];
 #pragma unroll
     for (int k = 0; k < K; k++) {
-        const float vbar = (m.v[k][0] + m.v[k][1] + m.v[k][2]) / 3.0f;
-        r[k] = m.w[k] * m.w[k] / vbar;
+        wsq[k] = m.w[k] * m.w[k];
+        vs[k] = m.v[k][0] + m.v[k][1] + m.v[k][2];
     }
-    int pos[K];
 #pragma unroll
     for (int k = 0; k < K; k++) {
         int c = 0;
 #pragma unroll
-        for (int j = 0; j < K; j++)
-            if (j != k) c += (r[j] > r[k]) || (r[j] == r[k] && j < k);
+        for (int j = 0; j < K; j++) {
+            if (j == k) continue;
+            const float a = wsq[j] * vs[k], b = wsq[k] * vs[j];
+            c += (a > b) || (a == b && j < k);
+        }
         pos[k] = c;
     }
+}
+
+template <int K>
+__device__ __forceinline__ MixOut mix_step(Mix<K> &m, const float I[3], float a, const DevParams &dp)
+{
+    int pos[K];
+    rank_positions<K>(m, pos);
     MixOut o;
     o.match = -1;
     o.tm = 0.f;
     int mpos = K;
 #pragma unroll
     for (int k = 0; k < K; k++) {
-        float tk = 0.f;
+        bool ok = true;
 #pragma unroll
         for (int c = 0; c < 3; c++) {
             const float d = I[c] - m.mu[k][c];
-            const float t = d * d / (dp.lam2 * m.v[k][c]);
-            tk = t > tk ? t : tk;
+            ok = ok && (d * d < dp.lam2 * m.v[k][c]);
         }
-        if (tk < 1.f && pos[k] < mpos) { mpos = pos[k]; o.match = k; o.tm = tk; }
+        if (ok && pos[k] < mpos) { mpos = pos[k]; o.match = k; }
     }
     if (o.match >= 0) {
         float S = 0.f;
 #pragma unroll
-        for (int k = 0; k < K; k++)
+        for (int k = 0; k < K; k++) {
             if (pos[k] < mpos) S += m.w[k];
+            if (k == o.match) {
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    const float d = I[c] - m.mu[k][c];
+                    const float t = __fdividef(d * d, dp.lam2 * m.v[k][c]);
+                    o.tm = t > o.tm ? t : o.tm;
+                }
+            }
+        }
         o.fg = !(S <= dp.T_bg);
     } else {
         o.fg = 1;
@@ -234,8 +338,9 @@ __device__ __forceinline__ MixOut mix_step(Mix<K> &m, const float I[3], float a,
     float sum = 0.f;
 #pragma unroll
     for (int k = 0; k < K; k++) sum += m.w[k];
+    const float inv = 1.f / sum;
 #pragma unroll
-    for (int k = 0; k < K; k++) m.w[k] = m.w[k] / sum;
+    for (int k = 0; k < K; k++) m.w[k] = m.w[k] * inv;
     return o;
 }
 

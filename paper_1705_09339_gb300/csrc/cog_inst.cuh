@@ -22,9 +22,10 @@ namespace cog {
     default: return cudaErrorInvalidValue; \
     }
 
-cudaError_t COG_CAT(launch_apply_, COG_SUFFIX)(int K, const ApplyArgs &a, cudaStream_t st)
+cudaError_t COG_CAT(launch_apply_, COG_SUFFIX)(int K, const ApplyArgs &a, cudaStream_t st,
+                                               const ApplyEvents *ev)
 {
-#define CALL_A(k) launch_apply_t<COG_T, k>(a, st)
+#define CALL_A(k) launch_apply_t<COG_T, k>(a, st, ev)
     COG_KSWITCH(CALL_A)
 #undef CALL_A
 }

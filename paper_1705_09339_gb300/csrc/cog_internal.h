@@ -17,14 +17,17 @@ constexpr int KMAX = 8;
 //              fields 0..4 = pixels labelled at each stage, 5 = pixels that
 //              reached the mixture stage.  Frame n accumulates into buffer
 //              n % 3, reads buffer (n - 1) % 3 for its illumination flag, and
-//              its block 0 clears buffer (n + 1) % 3.
+//              its first kernel's block 0 clears buffer (n + 1) % 3.
 //   [768, 800) running totals, 8 x uint64 (fields as above), lagging one frame
 //   [800]      device error word
+//   [802, 806) host bookkeeping carried by export/import
+//   [808, 811) survivor-queue length of frame n % 3 (rotates like the counters)
 constexpr int CTL_SLOTS = 32;
 constexpr int CTL_FIELDS = 8;
 constexpr int CTL_BUF_WORDS = CTL_SLOTS * CTL_FIELDS;
 constexpr int CTL_TOT_WORD = 3 * CTL_BUF_WORDS;     // 768
 constexpr int CTL_ERR_WORD = CTL_TOT_WORD + 32;     // 800
+constexpr int CTL_QCNT_WORD = CTL_ERR_WORD + 8;     // 808
 constexpr int CTL_BYTES = 4096;
 
 // device error codes (bit flags in the error word)
@@ -45,20 +48,20 @@ struct StatePtrs {
     uint32_t *ctl;
     uint32_t *jl;       // previous frame RGB + label byte
     void *conf;         // confidence plane
-    uint16_t *qab;      // qa | qb << 8
-    void *rga;          // 6 planes: m0 m1 m2 v0 v1 v2
-    int64_t rga_plane;  // elements between planes
+    uint8_t *s1;        // stage-1 records: m0 m1 m2 v0 v1 v2, qa | qb << 8
     uint8_t *gmm;       // mixture records
+    uint4 *queue;       // survivor queue (scratch, one entry per pixel at most)
     uint8_t *kde;       // prior, [P][3][256]
 };
 
 struct Layout {
-    size_t total, ctl, jl, conf, qab, rga, rga_plane_bytes, gmm, rec_bytes, kde, elem;
+    size_t total, ctl, jl, conf, s1, s1_bytes, gmm, rec_bytes, queue, kde, elem;
     int64_t P, Pp;
 };
 
 int elem_bytes(int dtype);
 int rec_bytes(int dtype, int K);
+int s1_bytes(int dtype);
 bool make_layout(const cog_params &p, Layout &L);
 
 struct ApplyArgs {
@@ -68,9 +71,15 @@ struct ApplyArgs {
     uint8_t *mask;
     uint8_t *stagemap;   // may be null
     uint32_t frame_no;   // frames applied since training (mod 3)
-    uint32_t frame_al16; // frame pointer 16-byte aligned: staged by TMA
-    uint32_t out_al8;    // mask (and stage map) 8-byte aligned: vector stores
-    uint32_t prefetch;   // 0 = by occupancy, 1 = always, 2 = never fetch stage-1 planes early
+    uint32_t frame_al4;  // frame pointer 4-byte aligned: 32-bit frame loads
+    uint32_t out_al4;    // mask (and stage map) 4-byte aligned: 32-bit stores
+    uint32_t k2_grid;    // CTAs of the persistent mixture-stage kernel
+};
+
+// Optional per-kernel timing: events recorded before the first kernel,
+// between the two kernels and after the second, on the launch stream.
+struct ApplyEvents {
+    cudaEvent_t e0, e1, e2;
 };
 
 // launchers (return the launch error)

@@ -119,33 +119,28 @@ __global__ void __launch_bounds__(128) warmup_kernel(const DevParams dp, const S
         fg = mix_step<K>(m, I, dp.alpha, dp).fg;
     }
     rec_store<T, K>(s.gmm, p, m);
-    // running average <- top-ranked component (ties to the lower index)
-    int best = 0;
-    float rb = -1.f;
-#pragma unroll
-    for (int k = 0; k < K; k++) {
-        const float vbar = (m.v[k][0] + m.v[k][1] + m.v[k][2]) / 3.0f;
-        const float r = m.w[k] * m.w[k] / vbar;
-        if (r > rb) { rb = r; best = k; }
-    }
-    T *rga = reinterpret_cast<T *>(s.rga);
-#pragma unroll
-    for (int k = 0; k < K; k++) {
-        if (k == best) {
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                rga[c * s.rga_plane + p] = Store<T>::from_f(m.mu[k][c]);
-                rga[(3 + c) * s.rga_plane + p] = Store<T>::from_f(m.v[k][c]);
-            }
-        }
-    }
-    reinterpret_cast<T *>(s.conf)[p] = Store<T>::from_f(0.5f);
-    s.jl[p] = prev[0] | (prev[1] << 8) | (prev[2] << 16) | ((uint32_t)fg << 24);
+    // running average <- top-ranked component (ties to the lower index),
+    // packed with the residue weights into the stage-1 record
     const uint32_t n = (uint32_t)(N - 1);
     uint32_t qa = (255u * n0 + n / 2) / n;
     uint32_t qb = (255u * n2 + n / 2) / n;
     if (qb > 255u - qa) qb = 255u - qa;
-    s.qab[p] = (uint16_t)(qa | (qb << 8));
+    int pos[K];
+    rank_positions<K>(m, pos);
+    S1Rec<T> r;
+#pragma unroll
+    for (int i = 0; i < S1Rec<T>::NV; i++) r.u[i] = make_uint4(0, 0, 0, 0);
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        if (pos[k] == 0) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) { r.set(c, m.mu[k][c]); r.set(3 + c, m.v[k][c]); }
+        }
+    }
+    r.set_qab(qa | (qb << 8));
+    r.store(s.s1, p);
+    reinterpret_cast<T *>(s.conf)[p] = Store<T>::from_f(0.5f);
+    s.jl[p] = prev[0] | (prev[1] << 8) | (prev[2] << 16) | ((uint32_t)fg << 24);
 }
 
 template <typename T, int K>

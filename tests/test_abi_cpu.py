@@ -45,12 +45,12 @@ def test_default_params_and_layout(cog):
     Pp = (P + 4095) // 4096 * 4096
     assert L.rec_bytes == 80 and L.elem_bytes == 2
     assert L.kde + P * 768 <= L.total
-    for off in (L.jl, L.conf, L.qab, L.rga, L.gmm, L.kde):
+    for off in (L.jl, L.conf, L.s1, L.gmm, L.queue, L.kde):
         assert off % 256 == 0
-    assert L.gmm - L.rga >= 6 * Pp * 2
+    assert L.s1_bytes == 16 and L.gmm - L.s1 >= Pp * 16 and L.kde - L.queue >= Pp * 16
     assert cog.cog_state_bytes(p) == L.total
     p32 = cog.cog_default_params(160, 120, 3)
-    assert cog.cog_state_layout(p32).rec_bytes == 96
+    assert cog.cog_state_layout(p32).rec_bytes == 96 and cog.cog_state_layout(p32).s1_bytes == 32
 
 
 @pytest.mark.parametrize("field,value", [("K", 0), ("K", 9), ("width", 0), ("alpha", 0.0), ("alpha", 1.5),
