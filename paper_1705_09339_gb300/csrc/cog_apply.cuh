@@ -34,6 +34,8 @@ namespace cog {
 constexpr int PPT = 4;         // pixels per thread in stage01_kernel
 constexpr int K1_TPB = 256;
 constexpr int K2_TPB = 128;
+constexpr int WPX = 32 * PPT;  // pixels per warp in stage01_kernel
+constexpr float R255 = 1.f / 255.f;
 
 // Read the previous frame's counters: illumination flag (lag one frame).
 __device__ __forceinline__ bool illum_flag_prev(const DevParams &dp, const uint32_t *ctl, uint32_t n, int lane)
@@ -43,16 +45,33 @@ __device__ __forceinline__ bool illum_flag_prev(const DevParams &dp, const uint3
     return (dp.flags & COG_ILLUM) && (uint64_t)g * 1000u > (uint64_t)dp.illum_permille * (uint64_t)dp.P;
 }
 
+// Stage-1 confidence term: a + b (1 - D/255) + g (1 - t_r).
+__device__ __forceinline__ float conf_stage1(uint32_t q, int D, float tr)
+{
+    const float wa = (float)(q & 0xffu) * R255, wb = (float)(q >> 8) * R255;
+    const float wg = (float)(255u - (q & 0xffu) - (q >> 8)) * R255;
+    return wa + wb * (1.f - (float)D * R255) + wg * (1.f - tr);
+}
+
 template <typename T, int TPB>
 __global__ void __launch_bounds__(TPB) stage01_kernel(const ApplyArgs A)
 {
     static_assert(PPT == 4, "frame and mask vector widths assume 4 pixels per thread");
-    __shared__ uint32_t wtot_s[TPB / 32], qbase_s, cnt_s[2];
+    constexpr int NW = TPB / 32;
+    // per warp: the stage-1 work list and what its pixels need, the results
+    // the owners collect, and the warp's survivor queue entries
+    __shared__ uint2 stash_s[NW][WPX];      // rgb | D << 24, C- bits
+    __shared__ uint8_t list_s[NW][WPX];     // pixel slot (lane * 4 + i)
+    __shared__ float resc_s[NW][WPX];       // new C of pixels decided at stage 1
+    __shared__ uint8_t resst_s[NW][WPX];    // 1: decided at stage 1, 2: survivor
+    __shared__ uint4 ent_s[NW][WPX];        // survivor queue entries
+    __shared__ uint32_t nent_s[NW], qbase_s, cnt_s[2];
     const DevParams &dp = A.dp;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t n = A.frame_no;
     uint32_t *ctl = A.s.ctl;
-    const int64_t p0 = ((int64_t)blockIdx.x * TPB + tid) * PPT;
+    const int64_t wbase = ((int64_t)blockIdx.x * TPB + warp * 32) * PPT;
+    const int64_t p0 = wbase + lane * PPT;
     const int nact = (int)max((int64_t)0, min((int64_t)PPT, dp.P - p0));
     const bool conf_on = dp.flags & COG_CONF;
 
@@ -106,7 +125,7 @@ __global__ void __launch_bounds__(TPB) stage01_kernel(const ApplyArgs A)
         return D;
     };
 
-    // ---- stage 0
+    // ---- stage 0; the pixels left go on the warp's stage-1 work list
     uint32_t need1 = 0;
 #pragma unroll
     for (int i = 0; i < PPT; i++) {
@@ -116,70 +135,110 @@ __global__ void __launch_bounds__(TPB) stage01_kernel(const ApplyArgs A)
             if (!((dp.flags & COG_FD) && bg_prev && (float)Dof(i) <= dp.tau_fd * (0.5f + Cm))) need1 |= 1u << i;
         }
     }
+    const int n1 = __popc(need1);
+    int incl = n1;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += t;
+    }
+    const int n1w = __shfl_sync(0xffffffffu, incl, 31);
+    {
+        int k = incl - n1;
+#pragma unroll
+        for (int i = 0; i < PPT; i++) {
+            if (!(need1 >> i & 1u)) continue;
+            const int slot = lane * PPT + i;
+            list_s[warp][k++] = (uint8_t)slot;
+            const uint32_t rgb = pix(i, 0) | (pix(i, 1) << 8) | (pix(i, 2) << 16);
+            stash_s[warp][slot] = make_uint2(rgb | ((uint32_t)Dof(i) << 24),
+                                             __float_as_uint(conf_on ? cv.get(i) : 0.5f));
+        }
+    }
+    __syncwarp();
 
-    // ---- stage 1: running Gaussian average (records of the pixels left)
-    S1Rec<T> r[PPT];
-#pragma unroll
-    for (int i = 0; i < PPT; i++)
-        if (need1 >> i & 1u) r[i].load(A.s.s1, p0 + i);
-    uint32_t need2 = 0, st1 = 0;     // st1: decided at stage 1
-    VecN<T, PPT> cn = cv;            // new confidence of the pixels decided here
-#pragma unroll
-    for (int i = 0; i < PPT; i++) {
-        if (i >= nact) continue;
-        const float Cm = conf_on ? cv.get(i) : 0.5f;
-        float ci = 1.f;               // stage 0: instantaneous confidence 1
-        if (need1 >> i & 1u) {
-            if (!(dp.flags & COG_RGA)) { need2 |= 1u << i; continue; }
-            float tr = 0.f;
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                const float d = (float)pix(i, c) - r[i].get(c);
-                const float t = __fdividef(d * d, dp.lam2 * r[i].get(3 + c));
-                tr = t > tr ? t : tr;
-            }
-            if (!(tr < 1.f)) { need2 |= 1u << i; continue; }
-            st1 |= 1u << i;
-            if (!(conf_on && Cm >= dp.c_halt)) {
-                const float ae = dp.alpha * (1.5f - Cm);
+    // ---- stage 1 over the compacted list: one pass per 32 pixels left
+    int ne = 0;
+    uint32_t n_rga = 0;
+    const uint32_t lt = (1u << lane) - 1u;
+    for (int j0 = 0; j0 < n1w; j0 += 32) {
+        const int j = j0 + lane;
+        bool surv = false;
+        uint4 ent = make_uint4(0, 0, 0, 0);
+        if (j < n1w) {
+            const int slot = list_s[warp][j];
+            const int64_t p = wbase + slot;
+            const uint2 sv = stash_s[warp][slot];
+            const int D = (int)(sv.x >> 24);
+            const float Cm = __uint_as_float(sv.y);
+            S1Rec<T> r;
+            r.load(A.s.s1, p);
+            if (dp.flags & COG_RGA) {
+                float tr = 0.f;
 #pragma unroll
                 for (int c = 0; c < 3; c++) {
-                    const float I = (float)pix(i, c);
-                    const float m = r[i].get(c) + ae * (I - r[i].get(c));
-                    const float d = I - m;
-                    r[i].set(c, m);
-                    r[i].set(3 + c, clampf((1.f - ae) * r[i].get(3 + c) + ae * d * d, dp.var_min, dp.var_max));
+                    const float d = (float)((sv.x >> (8 * c)) & 0xffu) - r.get(c);
+                    const float t = __fdividef(d * d, dp.lam2 * r.get(3 + c));
+                    tr = t > tr ? t : tr;
                 }
-                r[i].store(A.s.s1, p0 + i);
+                if (tr < 1.f) {
+                    if (!(conf_on && Cm >= dp.c_halt)) {
+                        const float ae = dp.alpha * (1.5f - Cm);
+#pragma unroll
+                        for (int c = 0; c < 3; c++) {
+                            const float I = (float)((sv.x >> (8 * c)) & 0xffu);
+                            const float m = r.get(c) + ae * (I - r.get(c));
+                            const float d = I - m;
+                            r.set(c, m);
+                            r.set(3 + c, clampf((1.f - ae) * r.get(3 + c) + ae * d * d, dp.var_min, dp.var_max));
+                        }
+                        r.store(A.s.s1, p);
+                    }
+                    resc_s[warp][slot] = (1.f - dp.eta) * Cm + dp.eta * conf_stage1(r.qab(), D, tr);
+                    resst_s[warp][slot] = 1;
+                    n_rga++;
+                } else {
+                    surv = true;
+                }
+            } else {
+                surv = true;
             }
-            const uint32_t q = r[i].qab();
-            const float wa = (float)(q & 0xffu) / 255.f, wb = (float)(q >> 8) / 255.f;
-            const float wg = (float)(255u - (q & 0xffu) - (q >> 8)) / 255.f;
-            ci = wa + wb * (1.f - (float)Dof(i) / 255.f) + wg * (1.f - tr);
+            if (surv) {
+                resst_s[warp][slot] = 2;
+                ent = make_uint4((uint32_t)p, sv.x, sv.y, r.qab());
+            }
         }
-        if (conf_on) cn.set(i, (1.f - dp.eta) * Cm + dp.eta * ci);
+        const uint32_t b = __ballot_sync(0xffffffffu, surv);
+        if (surv) ent_s[warp][ne + __popc(b & lt)] = ent;
+        ne += __popc(b);
     }
+    __syncwarp();
 
-    // ---- outputs of the pixels decided here; survivors get placeholders
-    //      (previous label, old confidence, mask 0) that the mixture stage
-    //      overwrites
-    uint32_t n_fd = 0, n_rga = 0;
+    // ---- outputs; survivors get placeholders (previous label, old C,
+    //      mask 0) that the mixture stage overwrites
+    uint32_t n_fd = 0;
     if (nact > 0) {
         uint4 jn = jl;
         uint32_t sm = 0;
+        VecN<T, PPT> cn = cv;
+        bool any_c = false;
 #pragma unroll
         for (int i = 0; i < PPT; i++) {
             if (i >= nact) continue;
-            const bool surv = need2 >> i & 1u;
-            const uint32_t st = surv ? (uint32_t)COG_ST_GMM_BG : ((st1 >> i & 1u) ? (uint32_t)COG_ST_RGA : (uint32_t)COG_ST_FD);
-            n_fd += st == COG_ST_FD;
-            n_rga += st == COG_ST_RGA;
+            const uint32_t r1 = (need1 >> i & 1u) ? resst_s[warp][lane * PPT + i] : 0u;
+            const bool surv = r1 == 2;
+            const uint32_t st = r1 == 0 ? (uint32_t)COG_ST_FD : (r1 == 1 ? (uint32_t)COG_ST_RGA : (uint32_t)COG_ST_GMM_BG);
+            n_fd += r1 == 0;
+            if (conf_on && !surv) {
+                cn.set(i, r1 == 0 ? (1.f - dp.eta) * cv.get(i) + dp.eta : resc_s[warp][lane * PPT + i]);
+                any_c = true;
+            }
             u4set(jn, i, pix(i, 0) | (pix(i, 1) << 8) | (pix(i, 2) << 16) | (surv ? (u4get(jl, i) & 0xff000000u) : 0u));
             sm |= st << (8 * i);
         }
         if (jn.x != jl.x || jn.y != jl.y || jn.z != jl.z || jn.w != jl.w)
             *reinterpret_cast<uint4 *>(A.s.jl + p0) = jn;
-        if (conf_on && need2 != ((1u << nact) - 1u)) cn.store(reinterpret_cast<T *>(A.s.conf) + p0);
+        if (any_c) cn.store(reinterpret_cast<T *>(A.s.conf) + p0);
         if (nact == PPT && A.out_al4) {
             *reinterpret_cast<uint32_t *>(A.mask + p0) = 0u;
             if (A.stagemap) *reinterpret_cast<uint32_t *>(A.stagemap + p0) = sm;
@@ -191,19 +250,12 @@ __global__ void __launch_bounds__(TPB) stage01_kernel(const ApplyArgs A)
         }
     }
 
-    // ---- compact the survivors into the frame's queue: warp scan, one
-    //      atomic per CTA
-    const int n2 = __popc(need2);
-    int incl = n2;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, incl, off);
-        if (lane >= off) incl += t;
-    }
-    if (lane == 31) wtot_s[warp] = (uint32_t)incl;
+    // ---- counters, then the CTA's survivors into the frame's queue (one
+    //      atomic per CTA, coalesced copies)
     const uint32_t vfd = __reduce_add_sync(0xffffffffu, n_fd);
     const uint32_t vrga = __reduce_add_sync(0xffffffffu, n_rga);
     if (lane == 0) {
+        nent_s[warp] = (uint32_t)ne;
         if (vfd) atomicAdd(&cnt_s[0], vfd);
         if (vrga) atomicAdd(&cnt_s[1], vrga);
     }
@@ -211,7 +263,7 @@ __global__ void __launch_bounds__(TPB) stage01_kernel(const ApplyArgs A)
     if (tid == 0) {
         uint32_t tot = 0;
 #pragma unroll
-        for (int w = 0; w < TPB / 32; w++) tot += wtot_s[w];
+        for (int w = 0; w < NW; w++) tot += nent_s[w];
         qbase_s = tot ? atomicAdd(ctl + CTL_QCNT_WORD + n % 3, tot) : 0u;
         const int slot = blockIdx.x & (CTL_SLOTS - 1);
         uint32_t *cur = ctl + (n % 3) * CTL_BUF_WORDS;
@@ -220,18 +272,99 @@ __global__ void __launch_bounds__(TPB) stage01_kernel(const ApplyArgs A)
         if (tot) atomicAdd(cur + 5 * CTL_SLOTS + slot, tot);
     }
     __syncthreads();
-    if (need2) {
-        uint32_t pos = qbase_s + (uint32_t)(incl - n2);
-        for (int w = 0; w < warp; w++) pos += wtot_s[w];
+    if (ne) {
+        uint32_t base = qbase_s;
+        for (int w = 0; w < warp; w++) base += nent_s[w];
+        for (int k = lane; k < ne; k += 32) A.s.queue[base + k] = ent_s[warp][k];
+    }
+}
+
+// ---- stage 2: one survivor of the queue, in two halves (loads, then the
+//      mixture step and its stores) so a thread keeps two survivors in flight
+template <typename T, int K> struct S2In {
+    uint4 e;
+    uint4 rec[Rec<T, K>::NV];
+    uint32_t qk[3];
+};
+
+template <typename T, int K>
+__device__ __forceinline__ void s2_load(const ApplyArgs &A, uint32_t q, S2In<T, K> &in)
+{
+    in.e = __ldcg(A.s.queue + q);
+    const int64_t p = in.e.x;
 #pragma unroll
-        for (int i = 0; i < PPT; i++) {
-            if (!(need2 >> i & 1u)) continue;
-            const float Cm = conf_on ? cv.get(i) : 0.5f;
-            const uint32_t rgb = pix(i, 0) | (pix(i, 1) << 8) | (pix(i, 2) << 16);
-            A.s.queue[pos++] = make_uint4((uint32_t)(p0 + i), rgb | ((uint32_t)Dof(i) << 24), __float_as_uint(Cm),
-                                          r[i].qab());
+    for (int c = 0; c < 3; c++) in.qk[c] = __ldg(A.s.kde + (p * 3 + c) * 256 + ((in.e.y >> (8 * c)) & 0xffu));
+    const uint4 *src = reinterpret_cast<const uint4 *>(A.s.gmm + p * Rec<T, K>::BYTES);
+#pragma unroll
+    for (int i = 0; i < Rec<T, K>::NV; i++) in.rec[i] = src[i];
+}
+
+template <typename T, int K>
+__device__ __forceinline__ int s2_finish(const ApplyArgs &A, const S2In<T, K> &in, bool flag)
+{
+    const DevParams &dp = A.dp;
+    const bool conf_on = dp.flags & COG_CONF;
+    const int64_t p = in.e.x;
+    const int D = (int)(in.e.y >> 24);
+    float I[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) I[c] = (float)((in.e.y >> (8 * c)) & 0xffu);
+    const float Cm = __uint_as_float(in.e.z);
+    const uint32_t qab = in.e.w & 0xffffu;
+    Mix<K> m;
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        m.w[k] = rec_elem<T, K>(in.rec, 7 * k);
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            m.mu[k][c] = rec_elem<T, K>(in.rec, 7 * k + 1 + c);
+            m.v[k][c] = rec_elem<T, K>(in.rec, 7 * k + 4 + c);
         }
     }
+    const float ae = dp.alpha * (1.5f - Cm);
+    const MixOut o = mix_step<K>(m, I, ae, dp);
+    int label = o.fg, st = o.fg ? COG_ST_FG : COG_ST_GMM_BG;
+    if (flag && o.fg) {
+        illum_response<K>(m, o.tgt, dp.w_illum);
+        label = 0;
+        st = COG_ST_ILLUM;
+    }
+    rec_store<T, K>(A.s.gmm, p, m);
+    if (!label) {   // transition update: the background mode seeds stage 1
+        S1Rec<T> r;
+#pragma unroll
+        for (int i = 0; i < S1Rec<T>::NV; i++) r.u[i] = make_uint4(0, 0, 0, 0);
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            if (k == o.tgt) {
+#pragma unroll
+                for (int c = 0; c < 3; c++) { r.set(c, m.mu[k][c]); r.set(3 + c, m.v[k][c]); }
+            }
+        }
+        r.set_qab(qab);
+        r.store(A.s.s1, p);
+    }
+    if (conf_on) {
+        uint32_t qmin = in.qk[0] < in.qk[1] ? in.qk[0] : in.qk[1];
+        qmin = in.qk[2] < qmin ? in.qk[2] : qmin;
+        const uint32_t qa = qab & 0xffu, qb = qab >> 8;
+        const float wa = (float)qa * R255, wb = (float)qb * R255;
+        const float wg = (float)(255u - qa - qb) * R255;
+        const float dhat = (float)D * R255;
+        const float Mh = o.match >= 0 ? (o.tm < 1.f ? o.tm : 1.f) : 1.f;
+        float ci;
+        if ((int)qmin < dp.q_null) {
+            const float den = wb + wg;
+            ci = den > 0.f ? (wb * (1.f - dhat) + wg * (1.f - Mh)) / den : 0.f;
+        } else {
+            ci = wa * ((float)qmin * R255) + wb * (1.f - dhat) + wg * (1.f - Mh);
+        }
+        reinterpret_cast<T *>(A.s.conf)[p] = Store<T>::from_f((1.f - dp.eta) * Cm + dp.eta * ci);
+    }
+    reinterpret_cast<uint8_t *>(A.s.jl)[p * 4 + 3] = (uint8_t)label;
+    A.mask[p] = label ? 255 : 0;
+    if (A.stagemap) A.stagemap[p] = (uint8_t)st;
+    return st;
 }
 
 template <typename T, int K, int TPB>
@@ -242,7 +375,6 @@ __global__ void __launch_bounds__(TPB) stage2_kernel(const ApplyArgs A)
     const int tid = threadIdx.x, lane = tid & 31;
     const uint32_t n = A.frame_no;
     uint32_t *ctl = A.s.ctl;
-    const bool conf_on = dp.flags & COG_CONF;
     if (tid < 32) {
         const bool f = illum_flag_prev(dp, ctl, n, lane);
         if (lane == 0) flag_s = f;
@@ -251,67 +383,19 @@ __global__ void __launch_bounds__(TPB) stage2_kernel(const ApplyArgs A)
     __syncthreads();
     const bool flag = flag_s;
     const uint32_t nq = __ldcg(ctl + CTL_QCNT_WORD + n % 3);
+    const uint32_t stride = gridDim.x * TPB;
     uint32_t cbg = 0, cfg = 0, cil = 0;
-    for (uint32_t q = blockIdx.x * TPB + tid; q < nq; q += gridDim.x * TPB) {
-        const uint4 e = __ldcg(A.s.queue + q);
-        const int64_t p = e.x;
-        const int D = (int)(e.y >> 24);
-        int Iv[3];
-        float I[3];
-#pragma unroll
-        for (int c = 0; c < 3; c++) { Iv[c] = (e.y >> (8 * c)) & 0xff; I[c] = (float)Iv[c]; }
-        const float Cm = __uint_as_float(e.z);
-        const uint32_t qab = e.w & 0xffffu;
-        // the record and the three prior bytes in one round trip
-        uint32_t qk[3];
-#pragma unroll
-        for (int c = 0; c < 3; c++) qk[c] = __ldg(A.s.kde + (p * 3 + c) * 256 + Iv[c]);
-        Mix<K> m;
-        rec_load<T, K>(A.s.gmm, p, m);
-        const float ae = dp.alpha * (1.5f - Cm);
-        const MixOut o = mix_step<K>(m, I, ae, dp);
-        int label = o.fg, st = o.fg ? COG_ST_FG : COG_ST_GMM_BG;
-        if (flag && o.fg) {
-            illum_response<K>(m, o.tgt, dp.w_illum);
-            label = 0;
-            st = COG_ST_ILLUM;
+    for (uint32_t q = blockIdx.x * TPB + tid; q < nq; q += 2 * stride) {
+        const bool two = q + stride < nq;
+        S2In<T, K> a, b;
+        s2_load<T, K>(A, q, a);
+        if (two) s2_load<T, K>(A, q + stride, b);
+        int st = s2_finish<T, K>(A, a, flag);
+        cbg += st == COG_ST_GMM_BG; cfg += st == COG_ST_FG; cil += st == COG_ST_ILLUM;
+        if (two) {
+            st = s2_finish<T, K>(A, b, flag);
+            cbg += st == COG_ST_GMM_BG; cfg += st == COG_ST_FG; cil += st == COG_ST_ILLUM;
         }
-        rec_store<T, K>(A.s.gmm, p, m);
-        if (!label) {   // transition update: the background mode seeds stage 1
-            S1Rec<T> r;
-#pragma unroll
-            for (int k = 0; k < K; k++) {
-                if (k == o.tgt) {
-#pragma unroll
-                    for (int c = 0; c < 3; c++) { r.set(c, m.mu[k][c]); r.set(3 + c, m.v[k][c]); }
-                }
-            }
-            r.set_qab(qab);
-            r.store(A.s.s1, p);
-        }
-        if (conf_on) {
-            uint32_t qmin = qk[0] < qk[1] ? qk[0] : qk[1];
-            qmin = qk[2] < qmin ? qk[2] : qmin;
-            const uint32_t qa = qab & 0xffu, qb = qab >> 8;
-            const float wa = (float)qa / 255.f, wb = (float)qb / 255.f;
-            const float wg = (float)(255u - qa - qb) / 255.f;
-            const float dhat = (float)D / 255.f;
-            const float Mh = o.match >= 0 ? (o.tm < 1.f ? o.tm : 1.f) : 1.f;
-            float ci;
-            if ((int)qmin < dp.q_null) {
-                const float den = wb + wg;
-                ci = den > 0.f ? (wb * (1.f - dhat) + wg * (1.f - Mh)) / den : 0.f;
-            } else {
-                ci = wa * ((float)qmin / 255.f) + wb * (1.f - dhat) + wg * (1.f - Mh);
-            }
-            reinterpret_cast<T *>(A.s.conf)[p] = Store<T>::from_f((1.f - dp.eta) * Cm + dp.eta * ci);
-        }
-        reinterpret_cast<uint8_t *>(A.s.jl)[p * 4 + 3] = (uint8_t)label;
-        A.mask[p] = label ? 255 : 0;
-        if (A.stagemap) A.stagemap[p] = (uint8_t)st;
-        cbg += st == COG_ST_GMM_BG;
-        cfg += st == COG_ST_FG;
-        cil += st == COG_ST_ILLUM;
     }
     cbg = __reduce_add_sync(0xffffffffu, cbg);
     cfg = __reduce_add_sync(0xffffffffu, cfg);
