@@ -164,6 +164,9 @@ def run_ours(args, rank, local_rank, world):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
+    torch.zeros(1, device=dev)          # create the context before setting its limit
+    if args.l2_fetch >= 0:
+        cog.cog_set_l2_fetch_bytes(args.l2_fetch)
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
     wl = workload("hd_dynamic", fg_frac=args.fg, seed=3 + rank)
@@ -280,6 +283,7 @@ def run_ours(args, rank, local_rank, world):
                                    f"{N_TRAIN} train frames, fg {args.fg:.3f}, one frame per step",
                        "width": W_, "height": H_, "K": K_, "state_dtype": "f16", "n_train": N_TRAIN,
                        "fg_frac": args.fg, "l2": "flushed (512 MB write) between timed steps",
+                       "l2_fetch_bytes": args.l2_fetch,
                        "parallelism": f"stream-sharded x{world} (one camera per GPU, no collective)"},
             "roofline": {"bound": "hbm", "achieved": round(ach_d, 1), "peak": hbm, "unit": "GB/s",
                          "frac": round(ach_d / hbm, 4), "traffic": tr_c, "peak_source": hbm_src,
@@ -392,6 +396,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fg", type=float, default=0.02)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--l2-fetch", type=int, default=32,
+                    help="L2 fetch granularity in bytes for the process (-1 keeps the driver default)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -192,6 +192,16 @@ cog_status cog_info(cog_ctx *ctx, int64_t *frames_applied, void **state_dev);
 cog_status cog_profile_begin(cog_ctx *ctx, int32_t max_frames);
 cog_status cog_profile_end(cog_ctx *ctx, double *stage01_ms, double *stage2_ms, int64_t *frames);
 
+/* Sets the L2 fetch granularity of the calling process's CUDA context on
+ * the current device (cudaLimitMaxL2FetchGranularity; 0 or a power of two
+ * up to 128 bytes).  The mixture stage gathers one 80-byte record and three
+ * prior bytes per survivor at random addresses; with the driver's default
+ * granularity each 32-byte miss pulls in neighbouring sectors that are never
+ * used.  32 keeps DRAM traffic at the sectors the cascade touches.  The
+ * limit applies to every kernel of the process on that device and ends with
+ * the process. */
+cog_status cog_set_l2_fetch_bytes(int32_t bytes);
+
 /* Human-readable description of the context's last error ("" if none).
  * With ctx == NULL: the last error of a failed cog_create on this thread. */
 const char *cog_last_error_string(cog_ctx *ctx);

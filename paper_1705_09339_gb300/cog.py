@@ -77,6 +77,7 @@ def _load() -> C.CDLL:
         "cog_import_state": (C.c_int, [vp, vp, sz]),
         "cog_info": (C.c_int, [vp, P(C.c_int64), P(vp)]),
         "cog_profile_begin": (C.c_int, [vp, i32]),
+        "cog_set_l2_fetch_bytes": (C.c_int, [i32]),
         "cog_profile_end": (C.c_int, [vp, P(C.c_double), P(C.c_double), P(C.c_int64)]),
         "cog_last_error_string": (C.c_char_p, [vp]),
         "cog_destroy": (C.c_int, [vp]),
@@ -181,6 +182,10 @@ def cog_info(ctx):
     n, s = C.c_int64(), C.c_void_p()
     _check(lib.cog_info(ctx, C.byref(n), C.byref(s)), ctx)
     return n.value, s.value
+
+
+def cog_set_l2_fetch_bytes(nbytes: int) -> None:
+    _check(lib.cog_set_l2_fetch_bytes(nbytes))
 
 
 def cog_profile_begin(ctx, max_frames: int) -> None:

@@ -462,6 +462,18 @@ cog_status cog_info(cog_ctx *c, int64_t *frames_applied, void **state_dev)
     return COG_OK;
 }
 
+cog_status cog_set_l2_fetch_bytes(int32_t bytes)
+{
+    if (bytes < 0 || bytes > 128 || (bytes & (bytes - 1)))
+        return set_err(nullptr, COG_ERR_INVALID_ARG, "bytes must be 0 or a power of two up to 128");
+    cudaError_t e = cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(nullptr, COG_ERR_CUDA, "cudaDeviceSetLimit: %s", cudaGetErrorString(e));
+    }
+    return COG_OK;
+}
+
 static void free_profile(cog_ctx *c)
 {
     for (auto &e : c->prof) {

@@ -96,34 +96,41 @@ __global__ void __launch_bounds__(TPB) stage01_kernel(const ApplyArgs A)
     // ---- all stage-0 loads at once: previous frame + label (16 B),
     //      confidence (8 or 16 B), frame bytes (12 B)
     uint4 jl = make_uint4(0, 0, 0, 0);
-    uint32_t fw[3] = {0, 0, 0};
+    uint32_t w0 = 0, w1 = 0, w2 = 0;
     VecN<T, PPT> cv;
     if (nact > 0) {
         jl = *reinterpret_cast<const uint4 *>(A.s.jl + p0);
         cv.load(reinterpret_cast<const T *>(A.s.conf) + p0);
         if (A.frame_al4 && nact == PPT) {
             const uint32_t *f4 = reinterpret_cast<const uint32_t *>(A.frame + p0 * 3);
-            fw[0] = f4[0]; fw[1] = f4[1]; fw[2] = f4[2];
+            w0 = f4[0]; w1 = f4[1]; w2 = f4[2];
         } else {
+            uint32_t fw[3] = {0, 0, 0};
 #pragma unroll
             for (int b3 = 0; b3 < PPT * 3; b3++)
                 if (b3 < nact * 3) fw[b3 >> 2] |= (uint32_t)A.frame[p0 * 3 + b3] << ((b3 & 3) * 8);
+            w0 = fw[0]; w1 = fw[1]; w2 = fw[2];
         }
     }
-    auto pix = [&](int i, int c) -> uint32_t {
-        const int b3 = i * 3 + c;
-        return (fw[b3 >> 2] >> ((b3 & 3) * 8)) & 0xffu;
-    };
-    auto Dof = [&](int i) -> int {
+    // the four pixels as (r | g << 8 | b << 16) words, the frame-difference
+    // statistic D = max_c |I_c - J_c| of each, computed once
+    uint32_t Iw[PPT];
+    Iw[0] = w0 & 0x00ffffffu;
+    Iw[1] = __byte_perm(w0, w1, 0x0543) & 0x00ffffffu;
+    Iw[2] = __byte_perm(w1, w2, 0x0432) & 0x00ffffffu;
+    Iw[3] = w2 >> 8;
+    int Dv[PPT];
+#pragma unroll
+    for (int i = 0; i < PPT; i++) {
         const uint32_t j = u4get(jl, i);
         int D = 0;
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            const int d = abs((int)pix(i, c) - (int)((j >> (8 * c)) & 0xffu));
+            const int d = abs((int)((Iw[i] >> (8 * c)) & 0xffu) - (int)((j >> (8 * c)) & 0xffu));
             D = d > D ? d : D;
         }
-        return D;
-    };
+        Dv[i] = D;
+    }
 
     // ---- stage 0; the pixels left go on the warp's stage-1 work list
     uint32_t need1 = 0;
@@ -132,7 +139,7 @@ __global__ void __launch_bounds__(TPB) stage01_kernel(const ApplyArgs A)
         if (i < nact) {
             const float Cm = conf_on ? cv.get(i) : 0.5f;
             const bool bg_prev = (u4get(jl, i) >> 24) == 0;
-            if (!((dp.flags & COG_FD) && bg_prev && (float)Dof(i) <= dp.tau_fd * (0.5f + Cm))) need1 |= 1u << i;
+            if (!((dp.flags & COG_FD) && bg_prev && (float)Dv[i] <= dp.tau_fd * (0.5f + Cm))) need1 |= 1u << i;
         }
     }
     const int n1 = __popc(need1);
@@ -143,15 +150,14 @@ __global__ void __launch_bounds__(TPB) stage01_kernel(const ApplyArgs A)
         if (lane >= off) incl += t;
     }
     const int n1w = __shfl_sync(0xffffffffu, incl, 31);
-    {
+    if (need1) {
         int k = incl - n1;
 #pragma unroll
         for (int i = 0; i < PPT; i++) {
             if (!(need1 >> i & 1u)) continue;
             const int slot = lane * PPT + i;
             list_s[warp][k++] = (uint8_t)slot;
-            const uint32_t rgb = pix(i, 0) | (pix(i, 1) << 8) | (pix(i, 2) << 16);
-            stash_s[warp][slot] = make_uint2(rgb | ((uint32_t)Dof(i) << 24),
+            stash_s[warp][slot] = make_uint2(Iw[i] | ((uint32_t)Dv[i] << 24),
                                              __float_as_uint(conf_on ? cv.get(i) : 0.5f));
         }
     }
@@ -218,23 +224,22 @@ __global__ void __launch_bounds__(TPB) stage01_kernel(const ApplyArgs A)
     //      mask 0) that the mixture stage overwrites
     uint32_t n_fd = 0;
     if (nact > 0) {
-        uint4 jn = jl;
+        uint4 jn;
         uint32_t sm = 0;
         VecN<T, PPT> cn = cv;
         bool any_c = false;
 #pragma unroll
         for (int i = 0; i < PPT; i++) {
-            if (i >= nact) continue;
             const uint32_t r1 = (need1 >> i & 1u) ? resst_s[warp][lane * PPT + i] : 0u;
+            const bool act = i < nact;
             const bool surv = r1 == 2;
-            const uint32_t st = r1 == 0 ? (uint32_t)COG_ST_FD : (r1 == 1 ? (uint32_t)COG_ST_RGA : (uint32_t)COG_ST_GMM_BG);
-            n_fd += r1 == 0;
-            if (conf_on && !surv) {
+            n_fd += act && r1 == 0;
+            if (conf_on && act && !surv) {
                 cn.set(i, r1 == 0 ? (1.f - dp.eta) * cv.get(i) + dp.eta : resc_s[warp][lane * PPT + i]);
                 any_c = true;
             }
-            u4set(jn, i, pix(i, 0) | (pix(i, 1) << 8) | (pix(i, 2) << 16) | (surv ? (u4get(jl, i) & 0xff000000u) : 0u));
-            sm |= st << (8 * i);
+            u4set(jn, i, act ? (Iw[i] | (surv ? (u4get(jl, i) & 0xff000000u) : 0u)) : u4get(jl, i));
+            sm |= (r1 == 0 ? (uint32_t)COG_ST_FD : (r1 == 1 ? (uint32_t)COG_ST_RGA : (uint32_t)COG_ST_GMM_BG)) << (8 * i);
         }
         if (jn.x != jl.x || jn.y != jl.y || jn.z != jl.z || jn.w != jl.w)
             *reinterpret_cast<uint4 *>(A.s.jl + p0) = jn;
