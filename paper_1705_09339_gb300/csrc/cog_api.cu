@@ -228,6 +228,7 @@ cog_status cog_create(const cog_params *p, void *cuda_stream, void *state_dev, c
     s.s1 = c->state + c->L.s1;
     s.gmm = c->state + c->L.gmm;
     s.queue = (uint4 *)(c->state + c->L.queue);
+    s.qseg_cap = c->L.Pp / QSEG;
     s.kde = c->state + c->L.kde;
     c->sticky = COG_OK;
     c->err[0] = 0;
@@ -326,6 +327,7 @@ cog_status cog_apply(cog_ctx *c, const uint8_t *frame_dev, uint8_t *mask_dev, ui
     a.frame_al4 = ((uintptr_t)frame_dev & 3) == 0;
     a.out_al4 = ((uintptr_t)mask_dev & 3) == 0 && ((uintptr_t)stagemap_dev & 3) == 0;
     a.k2_grid = (uint32_t)c->n_sm;
+    a.rec_bytes = (uint32_t)c->L.rec_bytes;
     const ApplyEvents *ev = nullptr;
     if (!c->prof.empty() && c->prof_n < (int64_t)c->prof.size()) ev = &c->prof[(size_t)c->prof_n++];
     cudaError_t e;

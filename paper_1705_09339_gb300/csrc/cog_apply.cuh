@@ -65,7 +65,6 @@ __global__ void __launch_bounds__(TPB) stage01_kernel(const ApplyArgs A)
     __shared__ float resc_s[NW][WPX];       // new C of pixels decided at stage 1
     __shared__ uint8_t resst_s[NW][WPX];    // 1: decided at stage 1, 2: survivor
     __shared__ uint4 ent_s[NW][WPX];        // survivor queue entries
-    __shared__ uint32_t nent_s[NW], qbase_s, cnt_s[2];
     const DevParams &dp = A.dp;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t n = A.frame_no;
@@ -75,13 +74,12 @@ __global__ void __launch_bounds__(TPB) stage01_kernel(const ApplyArgs A)
     const int nact = (int)max((int64_t)0, min((int64_t)PPT, dp.P - p0));
     const bool conf_on = dp.flags & COG_CONF;
 
-    if (tid < 2) cnt_s[tid] = 0;
     if (blockIdx.x == 0) {
         // rotate the per-frame counters: clear frame n+1's, add frame n-1's
         // to the running totals
         uint32_t *nxt = ctl + ((n + 1) % 3) * CTL_BUF_WORDS;
         for (int i = tid; i < CTL_BUF_WORDS; i += TPB) nxt[i] = 0;
-        if (tid == 0) ctl[CTL_QCNT_WORD + (n + 1) % 3] = 0;
+        if (tid < QSEG) ctl[CTL_QCNT_WORD + ((n + 1) % 3) * QSEG + tid] = 0;
         if (tid < 32) {
             const uint32_t *prev = ctl + ((n + 2) % 3) * CTL_BUF_WORDS;
             unsigned long long *tot = reinterpret_cast<unsigned long long *>(ctl + CTL_TOT_WORD);
@@ -212,6 +210,12 @@ __global__ void __launch_bounds__(TPB) stage01_kernel(const ApplyArgs A)
             if (surv) {
                 resst_s[warp][slot] = 2;
                 ent = make_uint4((uint32_t)p, sv.x, sv.y, r.qab());
+                // warm L2 with what the mixture stage will gather for this
+                // pixel: its record and its three prior bytes
+                const uint8_t *rec = A.s.gmm + p * A.rec_bytes;
+                for (uint32_t o = 0; o < A.rec_bytes; o += 32) prefetch_l2(rec + o);
+#pragma unroll
+                for (int c = 0; c < 3; c++) prefetch_l2(A.s.kde + (p * 3 + c) * 256 + ((sv.x >> (8 * c)) & 0xffu));
             }
         }
         const uint32_t b = __ballot_sync(0xffffffffu, surv);
@@ -255,32 +259,27 @@ __global__ void __launch_bounds__(TPB) stage01_kernel(const ApplyArgs A)
         }
     }
 
-    // ---- counters, then the CTA's survivors into the frame's queue (one
-    //      atomic per CTA, coalesced copies)
+    // ---- counters and the warp's survivors into its queue segment: one
+    //      atomic per warp and segment, no block-wide barrier
+    const uint32_t gwarp = blockIdx.x * NW + warp;
+    const uint32_t seg = gwarp & (QSEG - 1);
     const uint32_t vfd = __reduce_add_sync(0xffffffffu, n_fd);
     const uint32_t vrga = __reduce_add_sync(0xffffffffu, n_rga);
+    uint32_t base = 0;
     if (lane == 0) {
-        nent_s[warp] = (uint32_t)ne;
-        if (vfd) atomicAdd(&cnt_s[0], vfd);
-        if (vrga) atomicAdd(&cnt_s[1], vrga);
-    }
-    __syncthreads();
-    if (tid == 0) {
-        uint32_t tot = 0;
-#pragma unroll
-        for (int w = 0; w < NW; w++) tot += nent_s[w];
-        qbase_s = tot ? atomicAdd(ctl + CTL_QCNT_WORD + n % 3, tot) : 0u;
-        const int slot = blockIdx.x & (CTL_SLOTS - 1);
         uint32_t *cur = ctl + (n % 3) * CTL_BUF_WORDS;
-        if (cnt_s[0]) atomicAdd(cur + 0 * CTL_SLOTS + slot, cnt_s[0]);
-        if (cnt_s[1]) atomicAdd(cur + 1 * CTL_SLOTS + slot, cnt_s[1]);
-        if (tot) atomicAdd(cur + 5 * CTL_SLOTS + slot, tot);
+        const uint32_t slot = gwarp & (CTL_SLOTS - 1);
+        if (vfd) atomicAdd(cur + 0 * CTL_SLOTS + slot, vfd);
+        if (vrga) atomicAdd(cur + 1 * CTL_SLOTS + slot, vrga);
+        if (ne) {
+            atomicAdd(cur + 5 * CTL_SLOTS + slot, (uint32_t)ne);
+            base = atomicAdd(ctl + CTL_QCNT_WORD + (n % 3) * QSEG + seg, (uint32_t)ne);
+        }
     }
-    __syncthreads();
     if (ne) {
-        uint32_t base = qbase_s;
-        for (int w = 0; w < warp; w++) base += nent_s[w];
-        for (int k = lane; k < ne; k += 32) A.s.queue[base + k] = ent_s[warp][k];
+        base = __shfl_sync(0xffffffffu, base, 0);
+        uint4 *q = A.s.queue + seg * A.s.qseg_cap + base;
+        for (int k = lane; k < ne; k += 32) q[k] = ent_s[warp][k];
     }
 }
 
@@ -293,9 +292,9 @@ template <typename T, int K> struct S2In {
 };
 
 template <typename T, int K>
-__device__ __forceinline__ void s2_load(const ApplyArgs &A, uint32_t q, S2In<T, K> &in)
+__device__ __forceinline__ void s2_load(const ApplyArgs &A, int64_t qi, S2In<T, K> &in)
 {
-    in.e = __ldcg(A.s.queue + q);
+    in.e = __ldcg(A.s.queue + qi);
     const int64_t p = in.e.x;
 #pragma unroll
     for (int c = 0; c < 3; c++) in.qk[c] = __ldg(A.s.kde + (p * 3 + c) * 256 + ((in.e.y >> (8 * c)) & 0xffu));
@@ -375,26 +374,43 @@ __device__ __forceinline__ int s2_finish(const ApplyArgs &A, const S2In<T, K> &i
 template <typename T, int K, int TPB>
 __global__ void __launch_bounds__(TPB) stage2_kernel(const ApplyArgs A)
 {
-    __shared__ uint32_t flag_s, cnt_s[3];
+    __shared__ uint32_t flag_s, cnt_s[3], segp_s[QSEG + 1];
     const DevParams &dp = A.dp;
     const int tid = threadIdx.x, lane = tid & 31;
     const uint32_t n = A.frame_no;
     uint32_t *ctl = A.s.ctl;
     if (tid < 32) {
         const bool f = illum_flag_prev(dp, ctl, n, lane);
+        // exclusive prefix of the queue segments' lengths
+        const uint32_t len = __ldcg(ctl + CTL_QCNT_WORD + (n % 3) * QSEG + lane);
+        uint32_t incl = len;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += t;
+        }
+        segp_s[lane] = incl - len;
+        if (lane == 31) segp_s[QSEG] = incl;
         if (lane == 0) flag_s = f;
     }
     if (tid < 3) cnt_s[tid] = 0;
     __syncthreads();
     const bool flag = flag_s;
-    const uint32_t nq = __ldcg(ctl + CTL_QCNT_WORD + n % 3);
+    const uint32_t nq = segp_s[QSEG];
     const uint32_t stride = gridDim.x * TPB;
+    auto entry = [&](uint32_t q) -> int64_t {   // flat index -> queue slot
+        int lo = 0;
+#pragma unroll
+        for (int step = QSEG / 2; step >= 1; step >>= 1)
+            if (segp_s[lo + step] <= q) lo += step;
+        return (int64_t)lo * A.s.qseg_cap + (q - segp_s[lo]);
+    };
     uint32_t cbg = 0, cfg = 0, cil = 0;
     for (uint32_t q = blockIdx.x * TPB + tid; q < nq; q += 2 * stride) {
         const bool two = q + stride < nq;
         S2In<T, K> a, b;
-        s2_load<T, K>(A, q, a);
-        if (two) s2_load<T, K>(A, q + stride, b);
+        s2_load<T, K>(A, entry(q), a);
+        if (two) s2_load<T, K>(A, entry(q + stride), b);
         int st = s2_finish<T, K>(A, a, flag);
         cbg += st == COG_ST_GMM_BG; cfg += st == COG_ST_FG; cil += st == COG_ST_ILLUM;
         if (two) {

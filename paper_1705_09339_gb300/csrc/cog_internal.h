@@ -21,13 +21,16 @@ constexpr int KMAX = 8;
 //   [768, 800) running totals, 8 x uint64 (fields as above), lagging one frame
 //   [800]      device error word
 //   [802, 806) host bookkeeping carried by export/import
-//   [808, 811) survivor-queue length of frame n % 3 (rotates like the counters)
+//   [832, 928) survivor-queue segment lengths: 3 rotating frames x 32
+//              segments (frame n uses row n % 3; its first kernel's block 0
+//              clears row (n + 1) % 3)
 constexpr int CTL_SLOTS = 32;
 constexpr int CTL_FIELDS = 8;
 constexpr int CTL_BUF_WORDS = CTL_SLOTS * CTL_FIELDS;
 constexpr int CTL_TOT_WORD = 3 * CTL_BUF_WORDS;     // 768
 constexpr int CTL_ERR_WORD = CTL_TOT_WORD + 32;     // 800
-constexpr int CTL_QCNT_WORD = CTL_ERR_WORD + 8;     // 808
+constexpr int CTL_QCNT_WORD = CTL_ERR_WORD + 32;    // 832
+constexpr int QSEG = 32;                            // survivor-queue segments
 constexpr int CTL_BYTES = 4096;
 
 // device error codes (bit flags in the error word)
@@ -50,7 +53,8 @@ struct StatePtrs {
     void *conf;         // confidence plane
     uint8_t *s1;        // stage-1 records: m0 m1 m2 v0 v1 v2, qa | qb << 8
     uint8_t *gmm;       // mixture records
-    uint4 *queue;       // survivor queue (scratch, one entry per pixel at most)
+    uint4 *queue;       // survivor queue (scratch): QSEG segments of qseg_cap entries
+    int64_t qseg_cap;   // entries per segment (Pp / QSEG)
     uint8_t *kde;       // prior, [P][3][256]
 };
 
@@ -74,6 +78,7 @@ struct ApplyArgs {
     uint32_t frame_al4;  // frame pointer 4-byte aligned: 32-bit frame loads
     uint32_t out_al4;    // mask (and stage map) 4-byte aligned: 32-bit stores
     uint32_t k2_grid;    // CTAs of the persistent mixture-stage kernel
+    uint32_t rec_bytes;  // bytes of one mixture record (for L2 prefetches)
 };
 
 // Optional per-kernel timing: events recorded before the first kernel,
