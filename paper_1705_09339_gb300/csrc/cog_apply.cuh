@@ -210,12 +210,6 @@ __global__ void __launch_bounds__(TPB) stage01_kernel(const ApplyArgs A)
             if (surv) {
                 resst_s[warp][slot] = 2;
                 ent = make_uint4((uint32_t)p, sv.x, sv.y, r.qab());
-                // warm L2 with what the mixture stage will gather for this
-                // pixel: its record and its three prior bytes
-                const uint8_t *rec = A.s.gmm + p * A.rec_bytes;
-                for (uint32_t o = 0; o < A.rec_bytes; o += 32) prefetch_l2(rec + o);
-#pragma unroll
-                for (int c = 0; c < 3; c++) prefetch_l2(A.s.kde + (p * 3 + c) * 256 + ((sv.x >> (8 * c)) & 0xffu));
             }
         }
         const uint32_t b = __ballot_sync(0xffffffffu, surv);
