@@ -106,7 +106,8 @@ typedef struct cog_layout {
     uint64_t s1_bytes;       /* 16 (FP16/BF16) or 32 (FP32)                              */
     uint64_t gmm;            /* per-pixel records of rec_bytes: K x (w, mu0..2, v0..2)   */
     uint64_t rec_bytes;      /* K*7*sizeof(dtype) rounded up to 16                       */
-    uint64_t queue;          /* scratch: survivor queue, 16 bytes x Pp                   */
+    uint64_t queue;          /* scratch: survivor queue, 32 segments of whole 1024-entry */
+                             /* tiles, 16 bytes per entry                                */
     uint64_t kde;            /* uint8[P][3][256]: peak-normalised prior                  */
     uint64_t elem_bytes;     /* sizeof(dtype)                                            */
 } cog_layout;

@@ -43,7 +43,9 @@ bool make_layout(const cog_params &p, Layout &L)
     L.conf = o; o = up(o + (size_t)L.Pp * L.elem, 256);
     L.s1 = o;   o = up(o + (size_t)L.Pp * L.s1_bytes, 256);
     L.gmm = o;  o = up(o + (size_t)L.Pp * L.rec_bytes, 256);
-    L.queue = o; o = up(o + (size_t)L.Pp * 16, 256);
+    const int64_t ctas = (L.P + K1_TILE - 1) / K1_TILE;
+    L.qseg_cap = (ctas + QSEG - 1) / QSEG * K1_TILE;
+    L.queue = o; o = up(o + (size_t)(QSEG * L.qseg_cap) * 16, 256);
     L.kde = o;  o = up(o + (size_t)L.P * 768, 256);
     L.total = o;
     return true;
@@ -228,7 +230,7 @@ cog_status cog_create(const cog_params *p, void *cuda_stream, void *state_dev, c
     s.s1 = c->state + c->L.s1;
     s.gmm = c->state + c->L.gmm;
     s.queue = (uint4 *)(c->state + c->L.queue);
-    s.qseg_cap = c->L.Pp / QSEG;
+    s.qseg_cap = c->L.qseg_cap;
     s.kde = c->state + c->L.kde;
     c->sticky = COG_OK;
     c->err[0] = 0;
@@ -294,10 +296,9 @@ static void frame_stats(const std::vector<uint32_t> &ctl, int64_t frame, cog_sta
     memset(st, 0, sizeof *st);
     st->frame = (int32_t)frame;
     if (frame < 0) return;
-    const uint32_t *b = ctl.data() + (frame % 3) * CTL_BUF_WORDS;
     for (int f = 0; f < 6; f++) {
         int64_t v = 0;
-        for (int s = 0; s < CTL_SLOTS; s++) v += b[f * CTL_SLOTS + s];
+        for (int s = 0; s < CTL_SLOTS; s++) v += ctl[(size_t)ctl_slot((int)(frame % 3), f, s)];
         if (f < 5) st->n_stage[f] = v; else st->n_gmm = v;
     }
 }

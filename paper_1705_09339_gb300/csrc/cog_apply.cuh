@@ -35,13 +35,13 @@ constexpr int PPT = 4;         // pixels per thread in stage01_kernel
 constexpr int K1_TPB = 256;
 constexpr int K2_TPB = 128;
 constexpr int WPX = 32 * PPT;  // pixels per warp in stage01_kernel
+static_assert(K1_TPB * PPT == K1_TILE, "queue segments are sized in first-kernel tiles");
 constexpr float R255 = 1.f / 255.f;
 
 // Read the previous frame's counters: illumination flag (lag one frame).
 __device__ __forceinline__ bool illum_flag_prev(const DevParams &dp, const uint32_t *ctl, uint32_t n, int lane)
 {
-    const uint32_t *prev = ctl + ((n + 2) % 3) * CTL_BUF_WORDS;
-    const uint32_t g = __reduce_add_sync(0xffffffffu, __ldcg(prev + 5 * CTL_SLOTS + lane));
+    const uint32_t g = __reduce_add_sync(0xffffffffu, __ldcg(ctl + ctl_slot((n + 2) % 3, 5, lane)));
     return (dp.flags & COG_ILLUM) && (uint64_t)g * 1000u > (uint64_t)dp.illum_permille * (uint64_t)dp.P;
 }
 
@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(TPB) stage01_kernel(const ApplyArgs A)
     __shared__ float resc_s[NW][WPX];       // new C of pixels decided at stage 1
     __shared__ uint8_t resst_s[NW][WPX];    // 1: decided at stage 1, 2: survivor
     __shared__ uint4 ent_s[NW][WPX];        // survivor queue entries
+    __shared__ uint32_t nent_s[NW], qbase_s, cnt_s[2];
     const DevParams &dp = A.dp;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t n = A.frame_no;
@@ -74,18 +75,17 @@ __global__ void __launch_bounds__(TPB) stage01_kernel(const ApplyArgs A)
     const int nact = (int)max((int64_t)0, min((int64_t)PPT, dp.P - p0));
     const bool conf_on = dp.flags & COG_CONF;
 
+    if (tid < 2) cnt_s[tid] = 0;
     if (blockIdx.x == 0) {
         // rotate the per-frame counters: clear frame n+1's, add frame n-1's
         // to the running totals
-        uint32_t *nxt = ctl + ((n + 1) % 3) * CTL_BUF_WORDS;
-        for (int i = tid; i < CTL_BUF_WORDS; i += TPB) nxt[i] = 0;
-        if (tid < QSEG) ctl[CTL_QCNT_WORD + ((n + 1) % 3) * QSEG + tid] = 0;
+        for (int i = tid; i < CTL_FIELDS * CTL_SLOTS; i += TPB) ctl[ctl_slot((n + 1) % 3, i / CTL_SLOTS, i % CTL_SLOTS)] = 0;
+        if (tid < QSEG) ctl[ctl_qcnt((n + 1) % 3, tid)] = 0;
         if (tid < 32) {
-            const uint32_t *prev = ctl + ((n + 2) % 3) * CTL_BUF_WORDS;
             unsigned long long *tot = reinterpret_cast<unsigned long long *>(ctl + CTL_TOT_WORD);
 #pragma unroll
             for (int f = 0; f < 6; f++) {
-                const uint32_t v = __reduce_add_sync(0xffffffffu, __ldcg(prev + f * CTL_SLOTS + lane));
+                const uint32_t v = __reduce_add_sync(0xffffffffu, __ldcg(ctl + ctl_slot((n + 2) % 3, f, lane)));
                 if (lane == 0) tot[f] += v;
             }
         }
@@ -253,25 +253,31 @@ __global__ void __launch_bounds__(TPB) stage01_kernel(const ApplyArgs A)
         }
     }
 
-    // ---- counters and the warp's survivors into its queue segment: one
-    //      atomic per warp and segment, no block-wide barrier
-    const uint32_t gwarp = blockIdx.x * NW + warp;
-    const uint32_t seg = gwarp & (QSEG - 1);
+    // ---- counters, then the CTA's survivors into one queue segment: one
+    //      reservation per CTA, coalesced copies
     const uint32_t vfd = __reduce_add_sync(0xffffffffu, n_fd);
     const uint32_t vrga = __reduce_add_sync(0xffffffffu, n_rga);
-    uint32_t base = 0;
     if (lane == 0) {
-        uint32_t *cur = ctl + (n % 3) * CTL_BUF_WORDS;
-        const uint32_t slot = gwarp & (CTL_SLOTS - 1);
-        if (vfd) atomicAdd(cur + 0 * CTL_SLOTS + slot, vfd);
-        if (vrga) atomicAdd(cur + 1 * CTL_SLOTS + slot, vrga);
-        if (ne) {
-            atomicAdd(cur + 5 * CTL_SLOTS + slot, (uint32_t)ne);
-            base = atomicAdd(ctl + CTL_QCNT_WORD + (n % 3) * QSEG + seg, (uint32_t)ne);
-        }
+        nent_s[warp] = (uint32_t)ne;
+        if (vfd) atomicAdd(&cnt_s[0], vfd);
+        if (vrga) atomicAdd(&cnt_s[1], vrga);
     }
+    __syncthreads();
+    const uint32_t seg = blockIdx.x & (QSEG - 1);
+    if (tid == 0) {
+        uint32_t tot = 0;
+#pragma unroll
+        for (int w = 0; w < NW; w++) tot += nent_s[w];
+        qbase_s = tot ? atomicAdd(ctl + ctl_qcnt(n % 3, seg), tot) : 0u;
+        const int slot = blockIdx.x & (CTL_SLOTS - 1);
+        if (cnt_s[0]) atomicAdd(ctl + ctl_slot(n % 3, 0, slot), cnt_s[0]);
+        if (cnt_s[1]) atomicAdd(ctl + ctl_slot(n % 3, 1, slot), cnt_s[1]);
+        if (tot) atomicAdd(ctl + ctl_slot(n % 3, 5, slot), tot);
+    }
+    __syncthreads();
     if (ne) {
-        base = __shfl_sync(0xffffffffu, base, 0);
+        uint32_t base = qbase_s;
+        for (int w = 0; w < warp; w++) base += nent_s[w];
         uint4 *q = A.s.queue + seg * A.s.qseg_cap + base;
         for (int k = lane; k < ne; k += 32) q[k] = ent_s[warp][k];
     }
@@ -376,7 +382,7 @@ __global__ void __launch_bounds__(TPB) stage2_kernel(const ApplyArgs A)
     if (tid < 32) {
         const bool f = illum_flag_prev(dp, ctl, n, lane);
         // exclusive prefix of the queue segments' lengths
-        const uint32_t len = __ldcg(ctl + CTL_QCNT_WORD + (n % 3) * QSEG + lane);
+        const uint32_t len = __ldcg(ctl + ctl_qcnt(n % 3, lane));
         uint32_t incl = len;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -421,8 +427,7 @@ __global__ void __launch_bounds__(TPB) stage2_kernel(const ApplyArgs A)
         if (cil) atomicAdd(&cnt_s[2], cil);
     }
     __syncthreads();
-    if (tid < 3 && cnt_s[tid])
-        atomicAdd(ctl + (n % 3) * CTL_BUF_WORDS + (2 + tid) * CTL_SLOTS + (blockIdx.x & (CTL_SLOTS - 1)), cnt_s[tid]);
+    if (tid < 3 && cnt_s[tid]) atomicAdd(ctl + ctl_slot(n % 3, 2 + tid, blockIdx.x & (CTL_SLOTS - 1)), cnt_s[tid]);
 }
 
 template <typename T, int K>

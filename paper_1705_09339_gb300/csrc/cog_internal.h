@@ -12,26 +12,36 @@ namespace cog {
 constexpr int PX_ALIGN = 4096;   // pixel padding of every state plane
 constexpr int KMAX = 8;
 
-// Control block (first 4096 bytes of the state), in 32-bit words.
-//   [0, 768)   per-frame counters: 3 rotating buffers x 8 fields x 32 slots;
-//              fields 0..4 = pixels labelled at each stage, 5 = pixels that
-//              reached the mixture stage.  Frame n accumulates into buffer
-//              n % 3, reads buffer (n - 1) % 3 for its illumination flag, and
-//              its first kernel's block 0 clears buffer (n + 1) % 3.
-//   [768, 800) running totals, 8 x uint64 (fields as above), lagging one frame
-//   [800]      device error word
-//   [802, 806) host bookkeeping carried by export/import
-//   [832, 928) survivor-queue segment lengths: 3 rotating frames x 32
-//              segments (frame n uses row n % 3; its first kernel's block 0
-//              clears row (n + 1) % 3)
+// Control block (first CTL_BYTES of the state), in 32-bit words.  Every
+// atomic counter sits on its own 128-byte line (CTL_PAD words apart) so that
+// the per-CTA atomics of a frame spread over L2 slices instead of queueing
+// on one line.
+//   ctl_slot(b, f, s)  per-frame counters: 3 rotating buffers b x 8 fields f
+//              x 32 slots s; fields 0..4 = pixels labelled at each stage,
+//              5 = pixels that reached the mixture stage.  Frame n
+//              accumulates into buffer n % 3, reads buffer (n - 1) % 3 for its
+//              illumination flag, and its first kernel's block 0 clears buffer
+//              (n + 1) % 3.
+//   CTL_TOT_WORD       running totals, 8 x uint64 (fields as above), lagging
+//                      one frame
+//   CTL_ERR_WORD       device error word; the next words hold host
+//                      bookkeeping carried by export/import
+//   ctl_qcnt(b, g)     survivor-queue segment lengths: 3 rotating frames x
+//                      QSEG segments
 constexpr int CTL_SLOTS = 32;
 constexpr int CTL_FIELDS = 8;
-constexpr int CTL_BUF_WORDS = CTL_SLOTS * CTL_FIELDS;
-constexpr int CTL_TOT_WORD = 3 * CTL_BUF_WORDS;     // 768
-constexpr int CTL_ERR_WORD = CTL_TOT_WORD + 32;     // 800
-constexpr int CTL_QCNT_WORD = CTL_ERR_WORD + 32;    // 832
+constexpr int CTL_PAD = 32;
 constexpr int QSEG = 32;                            // survivor-queue segments
-constexpr int CTL_BYTES = 4096;
+constexpr int K1_TILE = 1024;                       // pixels per CTA of the stage-0/1 kernel
+__host__ __device__ constexpr int ctl_slot(int buf, int f, int s)
+{
+    return ((buf * CTL_FIELDS + f) * CTL_SLOTS + s) * CTL_PAD;
+}
+constexpr int CTL_TOT_WORD = 3 * CTL_FIELDS * CTL_SLOTS * CTL_PAD;   // 24576
+constexpr int CTL_ERR_WORD = CTL_TOT_WORD + 32;
+constexpr int CTL_QCNT_WORD = CTL_ERR_WORD + 32;
+__host__ __device__ constexpr int ctl_qcnt(int buf, int seg) { return CTL_QCNT_WORD + (buf * QSEG + seg) * CTL_PAD; }
+constexpr int CTL_BYTES = ((CTL_QCNT_WORD + 3 * QSEG * CTL_PAD) * 4 + 4095) / 4096 * 4096;
 
 // device error codes (bit flags in the error word)
 constexpr uint32_t DERR_TMA_TIMEOUT = 1u;
@@ -54,13 +64,17 @@ struct StatePtrs {
     uint8_t *s1;        // stage-1 records: m0 m1 m2 v0 v1 v2, qa | qb << 8
     uint8_t *gmm;       // mixture records
     uint4 *queue;       // survivor queue (scratch): QSEG segments of qseg_cap entries
-    int64_t qseg_cap;   // entries per segment (Pp / QSEG)
+    int64_t qseg_cap;   // entries per segment: every CTA of the first kernel
+                        // puts up to K1_TILE survivors into segment
+                        // blockIdx % QSEG, so a segment holds
+                        // ceil(CTAs / QSEG) whole tiles
     uint8_t *kde;       // prior, [P][3][256]
 };
 
 struct Layout {
     size_t total, ctl, jl, conf, s1, s1_bytes, gmm, rec_bytes, queue, kde, elem;
     int64_t P, Pp;
+    int64_t qseg_cap;   // survivor-queue entries per segment
 };
 
 int elem_bytes(int dtype);

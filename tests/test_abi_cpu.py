@@ -48,6 +48,14 @@ def test_default_params_and_layout(cog):
     for off in (L.jl, L.conf, L.s1, L.gmm, L.queue, L.kde):
         assert off % 256 == 0
     assert L.s1_bytes == 16 and L.gmm - L.s1 >= Pp * 16 and L.kde - L.queue >= Pp * 16
+    # every first-kernel CTA (1024 pixels) may enqueue all its pixels into
+    # segment cta % 32: each segment holds ceil(ctas / 32) whole tiles
+    for (w, h) in [(1, 1), (64, 64), (1920, 1080), (4096, 1), (33 * 1024, 1)]:
+        pp = cog.cog_default_params(w, h, 3)
+        Lq = cog.cog_state_layout(pp)
+        ctas = (w * h + 1023) // 1024
+        cap = (ctas + 31) // 32 * 1024
+        assert Lq.kde - Lq.queue >= 32 * cap * 16
     assert cog.cog_state_bytes(p) == L.total
     p32 = cog.cog_default_params(160, 120, 3)
     assert cog.cog_state_layout(p32).rec_bytes == 96 and cog.cog_state_layout(p32).s1_bytes == 32
