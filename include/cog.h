@@ -168,6 +168,31 @@ cog_status cog_apply_plain_gmm(cog_ctx *ctx, const uint8_t *frame_dev, uint8_t *
  * allocates two device staging buffers that the context keeps. */
 cog_status cog_apply_host(cog_ctx *ctx, const uint8_t *frame_host, uint8_t *mask_host);
 
+/* cog_apply_host for callers that cannot allocate device memory: the
+ * paper has no counterpart; this is a deployment form of the same call.
+ * Some hosts must not call cudaMalloc or cudaFree at all: a frame server or
+ * real-time pipeline that shares the GPU (those calls can synchronise the
+ * whole device and stall every other stream), or an application that hands
+ * out all device memory from its own fixed budget.  This call stages the
+ * frame and the mask through one static device array of 8,294,400 bytes
+ * compiled into the library (a 1920 x 1080 frame plus its mask), which every
+ * GPU that loads the library holds until the process exits.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *   - Frames larger than 2,073,600 pixels are rejected with
+ *     COG_ERR_INVALID_ARG before anything runs.
+ *   - The first call on a device looks the array's device address up
+ *     (cudaGetSymbolAddress, with that device made current for the lookup);
+ *     make that first call before any stream capture.
+ *   - Every call on a device shares the one array and it keeps the last
+ *     call's contents.  Nothing in it needs to start at zero: the frame area
+ *     is fully overwritten before the kernels read it and the mask area is
+ *     fully written before it is copied back.  Calls whose work overlaps on
+ *     the GPU (contexts used from several host threads, or on several
+ *     streams of one device) race on the array: serialise them.
+ * Otherwise it behaves as cog_apply_host: returns when mask_host is
+ * filled. */
+cog_status cog_apply_host_noalloc(cog_ctx *ctx, const uint8_t *frame_host, uint8_t *mask_host);
+
 /* Statistics of the most recent cog_apply frame and running totals of the
  * stage counts over every frame applied since the last training.
  * Synchronises the stream. */

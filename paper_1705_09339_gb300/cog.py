@@ -71,6 +71,7 @@ def _load() -> C.CDLL:
         "cog_apply": (C.c_int, [vp, vp, vp, vp, P(cog_stats)]),
         "cog_apply_plain_gmm": (C.c_int, [vp, vp, vp]),
         "cog_apply_host": (C.c_int, [vp, vp, vp]),
+        "cog_apply_host_noalloc": (C.c_int, [vp, vp, vp]),
         "cog_read_stats": (C.c_int, [vp, P(cog_stats), P(cog_stats)]),
         "cog_sync": (C.c_int, [vp]),
         "cog_export_state": (C.c_int, [vp, vp, sz]),
@@ -154,6 +155,14 @@ def cog_apply_host(ctx, frame: np.ndarray, mask: np.ndarray) -> None:
     assert frame.dtype == np.uint8 and mask.dtype == np.uint8
     assert frame.flags.c_contiguous and mask.flags.c_contiguous
     _check(lib.cog_apply_host(ctx, frame.ctypes.data, mask.ctypes.data), ctx)
+
+
+def cog_apply_host_noalloc(ctx, frame: np.ndarray, mask: np.ndarray) -> None:
+    """cog_apply_host staged through the library's static device array
+    (no device allocation; frames up to 1920 x 1080)."""
+    assert frame.dtype == np.uint8 and mask.dtype == np.uint8
+    assert frame.flags.c_contiguous and mask.flags.c_contiguous
+    _check(lib.cog_apply_host_noalloc(ctx, frame.ctypes.data, mask.ctypes.data), ctx)
 
 
 def cog_read_stats(ctx):

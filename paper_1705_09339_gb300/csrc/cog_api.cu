@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -388,6 +389,78 @@ cog_status cog_apply_host(cog_ctx *c, const uint8_t *frame_host, uint8_t *mask_h
     if (e != cudaSuccess) return cuda_fail(c, e, "mask download");
     e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "cog_apply_host sync");
+    return COG_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// cog_apply_host_noalloc: the host-buffer entry point for callers that may
+// not allocate device memory.  The frame and mask are staged through one
+// file-scope device array of fixed size instead of cudaMalloc'd buffers.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int64_t NOALLOC_MAX_PIXELS = 1920 * 1080;                          // 2,073,600
+constexpr size_t NOALLOC_FRAME_BYTES = (size_t)NOALLOC_MAX_PIXELS * 3;       // 6,220,800 = 256 * 24300
+constexpr size_t NOALLOC_BYTES = NOALLOC_FRAME_BYTES + (size_t)NOALLOC_MAX_PIXELS;   // 8,294,400
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+uint8_t *g_noalloc_ptr[NOALLOC_MAX_DEVICES];   // device address of the array, per device
+}  // namespace
+
+// Frame bytes at offset 0, mask bytes at NOALLOC_FRAME_BYTES.  In host code
+// this name is only a stand-in: kernels get the address that
+// cudaGetSymbolAddress returns for the current device.
+static __device__ __align__(256) uint8_t g_noalloc_stage[NOALLOC_BYTES];
+
+// Resolves the array's device address for the context's device once
+// (making that device current for the lookup); NULL with the error set on
+// failure.
+static uint8_t *noalloc_stage(cog_ctx *c)
+{
+    if (c->device < 0 || c->device >= NOALLOC_MAX_DEVICES) {
+        set_err(c, COG_ERR_INVALID_ARG, "device %d beyond the %d devices the static staging supports", c->device,
+                NOALLOC_MAX_DEVICES);
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (g_noalloc_ptr[c->device]) return g_noalloc_ptr[c->device];
+    int cur = -1;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e == cudaSuccess && cur != c->device) e = cudaSetDevice(c->device);
+    void *ptr = nullptr;
+    if (e == cudaSuccess) e = cudaGetSymbolAddress(&ptr, g_noalloc_stage);
+    if (cur >= 0 && cur != c->device) cudaSetDevice(cur);
+    if (e != cudaSuccess || !ptr) {
+        cuda_fail(c, e != cudaSuccess ? e : cudaErrorInvalidSymbol, "cudaGetSymbolAddress(static staging array)");
+        return nullptr;
+    }
+    g_noalloc_ptr[c->device] = (uint8_t *)ptr;
+    return (uint8_t *)ptr;
+}
+
+extern "C" {
+
+cog_status cog_apply_host_noalloc(cog_ctx *c, const uint8_t *frame_host, uint8_t *mask_host)
+{
+    cog_status s = check_ctx(c);
+    if (s) return s;
+    if (!frame_host || !mask_host) return set_err(c, COG_ERR_INVALID_ARG, "frame_host and mask_host are required");
+    if (c->L.P > NOALLOC_MAX_PIXELS)
+        return set_err(c, COG_ERR_INVALID_ARG,
+                       "frame of %lld pixels exceeds the %lld-pixel limit of the static staging array",
+                       (long long)c->L.P, (long long)NOALLOC_MAX_PIXELS);
+    if (!c->trained) return set_err(c, COG_ERR_STATE, "cog_apply_host_noalloc before cog_train_prior");
+    uint8_t *stage = noalloc_stage(c);
+    if (!stage) return c->sticky != COG_OK ? c->sticky : COG_ERR_INVALID_ARG;
+    const size_t P = (size_t)c->L.P;
+    cudaError_t e = cudaMemcpyAsync(stage, frame_host, P * 3, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "frame upload (static staging)");
+    if ((s = cog_apply(c, stage, stage + NOALLOC_FRAME_BYTES, nullptr, nullptr)) != COG_OK) return s;
+    e = cudaMemcpyAsync(mask_host, stage + NOALLOC_FRAME_BYTES, P, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "mask download (static staging)");
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cog_apply_host_noalloc sync");
     return COG_OK;
 }
 

@@ -1,0 +1,67 @@
+"""cog_apply_host_noalloc: the host-buffer entry point for callers that may
+not allocate device memory (a frame server or real-time pipeline sharing
+the GPU, where cudaMalloc/cudaFree would synchronise the device, or an
+application that owns all device memory).  It stages through the library's
+static device array instead of allocating, and must give exactly what the
+allocating entry point gives.  Collected last on purpose."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+
+@pytest.fixture(scope="module")
+def cog():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1705_09339_gb300 import cog
+    return cog
+
+
+def test_noalloc_matches_the_allocating_entry_point_on_two_calls_in_a_row(cog):
+    from cogsynth import Scene
+    W, H, K = 320, 240, 3
+    sc = Scene(W, H, 21, kind="dynamic", n_train=30, fg_frac=0.05)
+    fr, _ = sc.frames(0, 32)
+    p = cog.cog_default_params(W, H, K)
+    stream = torch.cuda.current_stream().cuda_stream
+    a = cog.cog_create(p, stream)
+    b = cog.cog_create(p, stream)
+    train = torch.from_numpy(fr[:30].reshape(30, H, W, 3)).cuda()
+    cog.cog_train_prior(a, train, 30)
+    cog.cog_train_prior(b, train, 30)
+    for i in (30, 31):
+        f = np.ascontiguousarray(fr[i])
+        m_ref = np.zeros(W * H, np.uint8)
+        m_new = np.full(W * H, 7, np.uint8)
+        cog.cog_apply_host(a, f, m_ref)
+        cog.cog_apply_host_noalloc(b, f, m_new)
+        # masks are bytes: the tolerance the tests use for them is equality
+        assert np.array_equal(m_ref, m_new), i
+        assert set(np.unique(m_new)) <= {0, 255}
+    # the two contexts went through the same kernels on the same frames: the
+    # model planes agree exactly (the survivor queue is scratch whose entry
+    # order depends on atomic ordering, so whole images are not compared)
+    sa = cog.decode_state(cog.cog_export_state(a, p), p)
+    sb = cog.decode_state(cog.cog_export_state(b, p), p)
+    for k in ("w", "mu", "var", "rga_m", "rga_v", "conf", "label", "prev", "qa", "qb"):
+        assert np.array_equal(sa[k], sb[k]), k
+    cog.cog_destroy(a)
+    cog.cog_destroy(b)
+
+
+def test_noalloc_rejects_frames_beyond_its_static_limit(cog):
+    W, H = 1921, 1080          # one column more than the static array holds
+    p = cog.cog_default_params(W, H, 1, state_dtype="f16")
+    ctx = cog.cog_create(p, torch.cuda.current_stream().cuda_stream)
+    f = np.zeros(W * H * 3, np.uint8)
+    m = np.zeros(W * H, np.uint8)
+    with pytest.raises(cog.CogError) as e:
+        cog.cog_apply_host_noalloc(ctx, f, m)
+    assert e.value.status == cog.COG_ERR_INVALID_ARG
+    assert "2073600" in str(e.value)
+    cog.cog_destroy(ctx)
