@@ -33,7 +33,7 @@ namespace cog {
 
 constexpr int PPT = 4;         // pixels per thread in stage01_kernel
 constexpr int K1_TPB = 256;
-constexpr int K2_TPB = 128;
+constexpr int K2_TPB = 64;
 constexpr int WPX = 32 * PPT;  // pixels per warp in stage01_kernel
 static_assert(K1_TPB * PPT == K1_TILE, "queue segments are sized in first-kernel tiles");
 constexpr float R255 = 1.f / 255.f;
@@ -53,92 +53,72 @@ __device__ __forceinline__ float conf_stage1(uint32_t q, int D, float tr)
     return wa + wb * (1.f - (float)D * R255) + wg * (1.f - tr);
 }
 
-template <typename T, int TPB>
-__global__ void __launch_bounds__(TPB) stage01_kernel(const ApplyArgs A)
-{
-    static_assert(PPT == 4, "frame and mask vector widths assume 4 pixels per thread");
-    constexpr int NW = TPB / 32;
-    // per warp: the stage-1 work list and what its pixels need, the results
-    // the owners collect, and the warp's survivor queue entries
-    __shared__ uint2 stash_s[NW][WPX];      // rgb | D << 24, C- bits
-    __shared__ uint8_t list_s[NW][WPX];     // pixel slot (lane * 4 + i)
-    __shared__ float resc_s[NW][WPX];       // new C of pixels decided at stage 1
-    __shared__ uint8_t resst_s[NW][WPX];    // 1: decided at stage 1, 2: survivor
-    __shared__ uint4 ent_s[NW][WPX];        // survivor queue entries
-    __shared__ uint32_t nent_s[NW], qbase_s, cnt_s[2];
-    const DevParams &dp = A.dp;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t n = A.frame_no;
-    uint32_t *ctl = A.s.ctl;
-    const int64_t wbase = ((int64_t)blockIdx.x * TPB + warp * 32) * PPT;
-    const int64_t p0 = wbase + lane * PPT;
-    const int nact = (int)max((int64_t)0, min((int64_t)PPT, dp.P - p0));
-    const bool conf_on = dp.flags & COG_CONF;
+// Shared memory of one warp of stage01_kernel: the stage-1 work list and
+// what its pixels need, the results the owners collect, and the warp's
+// survivor queue entries.
+struct K1Warp {
+    uint2 stash[WPX];      // rgb | D << 24, C- bits
+    uint8_t list[WPX];     // pixel slot (lane * 4 + i)
+    uint8_t resst[WPX];    // 1: decided at stage 1, 2: survivor
+    float resc[WPX];       // new C of pixels decided at stage 1
+    uint4 ent[WPX];        // survivor queue entries
+};
 
-    if (tid < 2) cnt_s[tid] = 0;
-    if (blockIdx.x == 0) {
-        // rotate the per-frame counters: clear frame n+1's, add frame n-1's
-        // to the running totals
-        for (int i = tid; i < CTL_FIELDS * CTL_SLOTS; i += TPB) ctl[ctl_slot((n + 1) % 3, i / CTL_SLOTS, i % CTL_SLOTS)] = 0;
-        if (tid < QSEG) ctl[ctl_qcnt((n + 1) % 3, tid)] = 0;
-        if (tid < 32) {
-            unsigned long long *tot = reinterpret_cast<unsigned long long *>(ctl + CTL_TOT_WORD);
-#pragma unroll
-            for (int f = 0; f < 6; f++) {
-                const uint32_t v = __reduce_add_sync(0xffffffffu, __ldcg(ctl + ctl_slot((n + 2) % 3, f, lane)));
-                if (lane == 0) tot[f] += v;
-            }
-        }
-    }
+// One warp's 128 pixels through stages 0 and 1.  FULL: every pixel of the
+// warp lies inside the frame (all warps but the last one's).  Returns the
+// warp's survivor count; counts of the pixels decided here are added to
+// n_fd / n_rga (per lane).
+template <typename T, bool FULL>
+__device__ __forceinline__ int k1_warp(const ApplyArgs &A, K1Warp &W, uint32_t wbase, int lane,
+                                       uint32_t &n_fd, uint32_t &n_rga)
+{
+    const DevParams &dp = A.dp;
+    const bool conf_on = dp.flags & COG_CONF;
+    const uint32_t p0 = wbase + (uint32_t)lane * PPT;
+    const int nact = FULL ? PPT : (int)min((int64_t)PPT, max((int64_t)0, dp.P - (int64_t)p0));
 
     // ---- all stage-0 loads at once: previous frame + label (16 B),
     //      confidence (8 or 16 B), frame bytes (12 B)
     uint4 jl = make_uint4(0, 0, 0, 0);
     uint32_t w0 = 0, w1 = 0, w2 = 0;
     VecN<T, PPT> cv;
-    if (nact > 0) {
+    if (FULL || nact > 0) {
         jl = *reinterpret_cast<const uint4 *>(A.s.jl + p0);
         cv.load(reinterpret_cast<const T *>(A.s.conf) + p0);
-        if (A.frame_al4 && nact == PPT) {
-            const uint32_t *f4 = reinterpret_cast<const uint32_t *>(A.frame + p0 * 3);
+        if (A.frame_al4 && (FULL || nact == PPT)) {
+            const uint32_t *f4 = reinterpret_cast<const uint32_t *>(A.frame + (size_t)p0 * 3);
             w0 = f4[0]; w1 = f4[1]; w2 = f4[2];
         } else {
             uint32_t fw[3] = {0, 0, 0};
 #pragma unroll
             for (int b3 = 0; b3 < PPT * 3; b3++)
-                if (b3 < nact * 3) fw[b3 >> 2] |= (uint32_t)A.frame[p0 * 3 + b3] << ((b3 & 3) * 8);
+                if (b3 < nact * 3) fw[b3 >> 2] |= (uint32_t)A.frame[(size_t)p0 * 3 + b3] << ((b3 & 3) * 8);
             w0 = fw[0]; w1 = fw[1]; w2 = fw[2];
         }
     }
-    // the four pixels as (r | g << 8 | b << 16) words, the frame-difference
-    // statistic D = max_c |I_c - J_c| of each, computed once
-    uint32_t Iw[PPT];
+    // the four pixels as (r | g << 8 | b << 16) words, and per-channel
+    // absolute differences to the previous frame (byte-wise)
+    uint32_t Iw[PPT], ad[PPT];
     Iw[0] = w0 & 0x00ffffffu;
     Iw[1] = __byte_perm(w0, w1, 0x0543) & 0x00ffffffu;
     Iw[2] = __byte_perm(w1, w2, 0x0432) & 0x00ffffffu;
     Iw[3] = w2 >> 8;
-    int Dv[PPT];
 #pragma unroll
-    for (int i = 0; i < PPT; i++) {
-        const uint32_t j = u4get(jl, i);
-        int D = 0;
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            const int d = abs((int)((Iw[i] >> (8 * c)) & 0xffu) - (int)((j >> (8 * c)) & 0xffu));
-            D = d > D ? d : D;
-        }
-        Dv[i] = D;
-    }
+    for (int i = 0; i < PPT; i++) ad[i] = __vabsdiffu4(Iw[i], u4get(jl, i) & 0x00ffffffu);
 
-    // ---- stage 0; the pixels left go on the warp's stage-1 work list
+    // ---- stage 0: D = max_c |I_c - J_c| <= tau_fd (0.5 + C-) on a
+    //      background pixel.  D is an integer, so the test is D <= floor(tau)
+    //      applied to every channel at once.
     uint32_t need1 = 0;
+    const bool fd_on = dp.flags & COG_FD;
 #pragma unroll
     for (int i = 0; i < PPT; i++) {
-        if (i < nact) {
-            const float Cm = conf_on ? cv.get(i) : 0.5f;
-            const bool bg_prev = (u4get(jl, i) >> 24) == 0;
-            if (!((dp.flags & COG_FD) && bg_prev && (float)Dv[i] <= dp.tau_fd * (0.5f + Cm))) need1 |= 1u << i;
-        }
+        if (!FULL && i >= nact) continue;
+        const float Cm = conf_on ? cv.get(i) : 0.5f;
+        const float tau = dp.tau_fd * (0.5f + Cm);
+        const uint32_t t = tau >= 255.f ? 255u : (uint32_t)tau;      // floor, tau >= 0
+        const bool pass = fd_on && (u4get(jl, i) >> 24) == 0 && __vcmpgtu4(ad[i], t * 0x01010101u) == 0u;
+        if (!pass) need1 |= 1u << i;
     }
     const int n1 = __popc(need1);
     int incl = n1;
@@ -154,25 +134,25 @@ __global__ void __launch_bounds__(TPB) stage01_kernel(const ApplyArgs A)
         for (int i = 0; i < PPT; i++) {
             if (!(need1 >> i & 1u)) continue;
             const int slot = lane * PPT + i;
-            list_s[warp][k++] = (uint8_t)slot;
-            stash_s[warp][slot] = make_uint2(Iw[i] | ((uint32_t)Dv[i] << 24),
-                                             __float_as_uint(conf_on ? cv.get(i) : 0.5f));
+            W.list[k++] = (uint8_t)slot;
+            const uint32_t m2 = __vmaxu4(ad[i], ad[i] >> 8);
+            const uint32_t D = __vmaxu4(m2, m2 >> 8) & 0xffu;
+            W.stash[slot] = make_uint2(Iw[i] | (D << 24), __float_as_uint(conf_on ? cv.get(i) : 0.5f));
         }
     }
     __syncwarp();
 
     // ---- stage 1 over the compacted list: one pass per 32 pixels left
     int ne = 0;
-    uint32_t n_rga = 0;
     const uint32_t lt = (1u << lane) - 1u;
     for (int j0 = 0; j0 < n1w; j0 += 32) {
         const int j = j0 + lane;
         bool surv = false;
         uint4 ent = make_uint4(0, 0, 0, 0);
         if (j < n1w) {
-            const int slot = list_s[warp][j];
-            const int64_t p = wbase + slot;
-            const uint2 sv = stash_s[warp][slot];
+            const int slot = W.list[j];
+            const uint32_t p = wbase + slot;
+            const uint2 sv = W.stash[slot];
             const int D = (int)(sv.x >> 24);
             const float Cm = __uint_as_float(sv.y);
             S1Rec<T> r;
@@ -198,8 +178,8 @@ __global__ void __launch_bounds__(TPB) stage01_kernel(const ApplyArgs A)
                         }
                         r.store(A.s.s1, p);
                     }
-                    resc_s[warp][slot] = (1.f - dp.eta) * Cm + dp.eta * conf_stage1(r.qab(), D, tr);
-                    resst_s[warp][slot] = 1;
+                    W.resc[slot] = (1.f - dp.eta) * Cm + dp.eta * conf_stage1(r.qab(), D, tr);
+                    W.resst[slot] = 1;
                     n_rga++;
                 } else {
                     surv = true;
@@ -208,41 +188,39 @@ __global__ void __launch_bounds__(TPB) stage01_kernel(const ApplyArgs A)
                 surv = true;
             }
             if (surv) {
-                resst_s[warp][slot] = 2;
-                ent = make_uint4((uint32_t)p, sv.x, sv.y, r.qab());
+                W.resst[slot] = 2;
+                ent = make_uint4(p, sv.x, sv.y, r.qab());
             }
         }
         const uint32_t b = __ballot_sync(0xffffffffu, surv);
-        if (surv) ent_s[warp][ne + __popc(b & lt)] = ent;
+        if (surv) W.ent[ne + __popc(b & lt)] = ent;
         ne += __popc(b);
     }
     __syncwarp();
 
-    // ---- outputs; survivors get placeholders (previous label, old C,
-    //      mask 0) that the mixture stage overwrites
-    uint32_t n_fd = 0;
-    if (nact > 0) {
+    // ---- outputs: the previous frame becomes this frame with label 0 (the
+    //      mixture stage sets its survivors' labels), the mask 0 (likewise),
+    //      the confidence of the pixels decided here
+    if (FULL || nact > 0) {
         uint4 jn;
         uint32_t sm = 0;
         VecN<T, PPT> cn = cv;
         bool any_c = false;
 #pragma unroll
         for (int i = 0; i < PPT; i++) {
-            const uint32_t r1 = (need1 >> i & 1u) ? resst_s[warp][lane * PPT + i] : 0u;
-            const bool act = i < nact;
-            const bool surv = r1 == 2;
+            const bool act = FULL || i < nact;
+            const uint32_t r1 = (need1 >> i & 1u) ? W.resst[lane * PPT + i] : 0u;
             n_fd += act && r1 == 0;
-            if (conf_on && act && !surv) {
-                cn.set(i, r1 == 0 ? (1.f - dp.eta) * cv.get(i) + dp.eta : resc_s[warp][lane * PPT + i]);
+            if (conf_on && act && r1 != 2) {
+                cn.set(i, r1 == 0 ? (1.f - dp.eta) * cv.get(i) + dp.eta : W.resc[lane * PPT + i]);
                 any_c = true;
             }
-            u4set(jn, i, act ? (Iw[i] | (surv ? (u4get(jl, i) & 0xff000000u) : 0u)) : u4get(jl, i));
+            u4set(jn, i, act ? Iw[i] : u4get(jl, i));
             sm |= (r1 == 0 ? (uint32_t)COG_ST_FD : (r1 == 1 ? (uint32_t)COG_ST_RGA : (uint32_t)COG_ST_GMM_BG)) << (8 * i);
         }
-        if (jn.x != jl.x || jn.y != jl.y || jn.z != jl.z || jn.w != jl.w)
-            *reinterpret_cast<uint4 *>(A.s.jl + p0) = jn;
+        *reinterpret_cast<uint4 *>(A.s.jl + p0) = jn;
         if (any_c) cn.store(reinterpret_cast<T *>(A.s.conf) + p0);
-        if (nact == PPT && A.out_al4) {
+        if ((FULL || nact == PPT) && A.out_al4) {
             *reinterpret_cast<uint32_t *>(A.mask + p0) = 0u;
             if (A.stagemap) *reinterpret_cast<uint32_t *>(A.stagemap + p0) = sm;
         } else {
@@ -252,6 +230,41 @@ __global__ void __launch_bounds__(TPB) stage01_kernel(const ApplyArgs A)
             }
         }
     }
+    return ne;
+}
+
+template <typename T, int TPB>
+__global__ void __launch_bounds__(TPB) stage01_kernel(const ApplyArgs A)
+{
+    static_assert(PPT == 4, "frame and mask vector widths assume 4 pixels per thread");
+    constexpr int NW = TPB / 32;
+    __shared__ K1Warp W_s[NW];
+    __shared__ uint32_t nent_s[NW], qbase_s, cnt_s[2];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t n = A.frame_no;
+    uint32_t *ctl = A.s.ctl;
+    const uint32_t wbase = ((uint32_t)blockIdx.x * TPB + warp * 32) * PPT;
+
+    if (tid < 2) cnt_s[tid] = 0;
+    if (blockIdx.x == 0) {
+        // rotate the per-frame counters: clear frame n+1's, add frame n-1's
+        // to the running totals
+        for (int i = tid; i < CTL_FIELDS * CTL_SLOTS; i += TPB) ctl[ctl_slot((n + 1) % 3, i / CTL_SLOTS, i % CTL_SLOTS)] = 0;
+        if (tid < QSEG) ctl[ctl_qcnt((n + 1) % 3, tid)] = 0;
+        if (tid < 32) {
+            unsigned long long *tot = reinterpret_cast<unsigned long long *>(ctl + CTL_TOT_WORD);
+#pragma unroll
+            for (int f = 0; f < 6; f++) {
+                const uint32_t v = __reduce_add_sync(0xffffffffu, __ldcg(ctl + ctl_slot((n + 2) % 3, f, lane)));
+                if (lane == 0) tot[f] += v;
+            }
+        }
+    }
+
+    uint32_t n_fd = 0, n_rga = 0;
+    int ne;
+    if ((int64_t)wbase + WPX <= A.dp.P) ne = k1_warp<T, true>(A, W_s[warp], wbase, lane, n_fd, n_rga);
+    else ne = k1_warp<T, false>(A, W_s[warp], wbase, lane, n_fd, n_rga);
 
     // ---- counters, then the CTA's survivors into one queue segment: one
     //      reservation per CTA, coalesced copies
@@ -279,12 +292,12 @@ __global__ void __launch_bounds__(TPB) stage01_kernel(const ApplyArgs A)
         uint32_t base = qbase_s;
         for (int w = 0; w < warp; w++) base += nent_s[w];
         uint4 *q = A.s.queue + seg * A.s.qseg_cap + base;
-        for (int k = lane; k < ne; k += 32) q[k] = ent_s[warp][k];
+        for (int k = lane; k < ne; k += 32) q[k] = W_s[warp].ent[k];
     }
 }
 
-// ---- stage 2: one survivor of the queue, in two halves (loads, then the
-//      mixture step and its stores) so a thread keeps two survivors in flight
+// ---- stage 2: one survivor of the queue, in two halves (its loads, then
+//      the mixture step and its stores)
 template <typename T, int K> struct S2In {
     uint4 e;
     uint4 rec[Rec<T, K>::NV];
@@ -406,17 +419,11 @@ __global__ void __launch_bounds__(TPB) stage2_kernel(const ApplyArgs A)
         return (int64_t)lo * A.s.qseg_cap + (q - segp_s[lo]);
     };
     uint32_t cbg = 0, cfg = 0, cil = 0;
-    for (uint32_t q = blockIdx.x * TPB + tid; q < nq; q += 2 * stride) {
-        const bool two = q + stride < nq;
-        S2In<T, K> a, b;
+    for (uint32_t q = blockIdx.x * TPB + tid; q < nq; q += stride) {
+        S2In<T, K> a;
         s2_load<T, K>(A, entry(q), a);
-        if (two) s2_load<T, K>(A, entry(q + stride), b);
-        int st = s2_finish<T, K>(A, a, flag);
+        const int st = s2_finish<T, K>(A, a, flag);
         cbg += st == COG_ST_GMM_BG; cfg += st == COG_ST_FG; cil += st == COG_ST_ILLUM;
-        if (two) {
-            st = s2_finish<T, K>(A, b, flag);
-            cbg += st == COG_ST_GMM_BG; cfg += st == COG_ST_FG; cil += st == COG_ST_ILLUM;
-        }
     }
     cbg = __reduce_add_sync(0xffffffffu, cbg);
     cfg = __reduce_add_sync(0xffffffffu, cfg);
