@@ -32,10 +32,13 @@
 namespace cog {
 
 constexpr int PPT = 4;         // pixels per thread in stage01_kernel
-constexpr int K1_TPB = 256;
+constexpr int K1_TPB = 128;
 constexpr int K2_TPB = 64;
 constexpr int WPX = 32 * PPT;  // pixels per warp in stage01_kernel
-static_assert(K1_TPB * PPT == K1_TILE, "queue segments are sized in first-kernel tiles");
+// Queue segments: warp w of the first kernel puts up to WPX survivors into
+// segment w % QSEG.  The layout sizes a segment for ceil(CTAs / QSEG) tiles
+// of K1_TILE pixels, which holds every warp that maps to it.
+static_assert(K1_TPB * PPT * 2 == K1_TILE && WPX * 32 % K1_TILE == 0, "queue segment sizing");
 constexpr float R255 = 1.f / 255.f;
 
 // Read the previous frame's counters: illumination flag (lag one frame).
@@ -234,7 +237,7 @@ __device__ __forceinline__ int k1_warp(const ApplyArgs &A, K1Warp &W, uint32_t w
 }
 
 template <typename T, int TPB>
-__global__ void __launch_bounds__(TPB) stage01_kernel(const ApplyArgs A)
+__global__ void __launch_bounds__(TPB, 10) stage01_kernel(const ApplyArgs A)
 {
     static_assert(PPT == 4, "frame and mask vector widths assume 4 pixels per thread");
     constexpr int NW = TPB / 32;
@@ -244,6 +247,11 @@ __global__ void __launch_bounds__(TPB) stage01_kernel(const ApplyArgs A)
     const uint32_t n = A.frame_no;
     uint32_t *ctl = A.s.ctl;
     const uint32_t wbase = ((uint32_t)blockIdx.x * TPB + warp * 32) * PPT;
+    // programmatic dependent launch: let the mixture stage's CTAs be
+    // scheduled as this grid drains, and wait for the previous frame's
+    // kernels before touching the state they write
+    grid_launch_dependents();
+    grid_wait_prior();
 
     if (tid < 2) cnt_s[tid] = 0;
     if (blockIdx.x == 0) {
@@ -266,31 +274,23 @@ __global__ void __launch_bounds__(TPB) stage01_kernel(const ApplyArgs A)
     if ((int64_t)wbase + WPX <= A.dp.P) ne = k1_warp<T, true>(A, W_s[warp], wbase, lane, n_fd, n_rga);
     else ne = k1_warp<T, false>(A, W_s[warp], wbase, lane, n_fd, n_rga);
 
-    // ---- counters, then the CTA's survivors into one queue segment: one
-    //      reservation per CTA, coalesced copies
+    // per-warp reservation (padded counters)
+    const uint32_t gwarp = blockIdx.x * NW + warp;
+    const uint32_t seg = gwarp & (QSEG - 1);
     const uint32_t vfd = __reduce_add_sync(0xffffffffu, n_fd);
     const uint32_t vrga = __reduce_add_sync(0xffffffffu, n_rga);
+    uint32_t base = 0;
     if (lane == 0) {
-        nent_s[warp] = (uint32_t)ne;
-        if (vfd) atomicAdd(&cnt_s[0], vfd);
-        if (vrga) atomicAdd(&cnt_s[1], vrga);
+        const uint32_t slot = gwarp & (CTL_SLOTS - 1);
+        if (vfd) atomicAdd(ctl + ctl_slot(n % 3, 0, slot), vfd);
+        if (vrga) atomicAdd(ctl + ctl_slot(n % 3, 1, slot), vrga);
+        if (ne) {
+            atomicAdd(ctl + ctl_slot(n % 3, 5, slot), (uint32_t)ne);
+            base = atomicAdd(ctl + ctl_qcnt(n % 3, seg), (uint32_t)ne);
+        }
     }
-    __syncthreads();
-    const uint32_t seg = blockIdx.x & (QSEG - 1);
-    if (tid == 0) {
-        uint32_t tot = 0;
-#pragma unroll
-        for (int w = 0; w < NW; w++) tot += nent_s[w];
-        qbase_s = tot ? atomicAdd(ctl + ctl_qcnt(n % 3, seg), tot) : 0u;
-        const int slot = blockIdx.x & (CTL_SLOTS - 1);
-        if (cnt_s[0]) atomicAdd(ctl + ctl_slot(n % 3, 0, slot), cnt_s[0]);
-        if (cnt_s[1]) atomicAdd(ctl + ctl_slot(n % 3, 1, slot), cnt_s[1]);
-        if (tot) atomicAdd(ctl + ctl_slot(n % 3, 5, slot), tot);
-    }
-    __syncthreads();
     if (ne) {
-        uint32_t base = qbase_s;
-        for (int w = 0; w < warp; w++) base += nent_s[w];
+        base = __shfl_sync(0xffffffffu, base, 0);
         uint4 *q = A.s.queue + seg * A.s.qseg_cap + base;
         for (int k = lane; k < ne; k += 32) q[k] = W_s[warp].ent[k];
     }
@@ -392,6 +392,8 @@ __global__ void __launch_bounds__(TPB) stage2_kernel(const ApplyArgs A)
     const int tid = threadIdx.x, lane = tid & 31;
     const uint32_t n = A.frame_no;
     uint32_t *ctl = A.s.ctl;
+    grid_launch_dependents();
+    grid_wait_prior();     // the queue and counters come from stage01_kernel
     if (tid < 32) {
         const bool f = illum_flag_prev(dp, ctl, n, lane);
         // exclusive prefix of the queue segments' lengths
@@ -437,13 +439,31 @@ __global__ void __launch_bounds__(TPB) stage2_kernel(const ApplyArgs A)
     if (tid < 3 && cnt_s[tid]) atomicAdd(ctl + ctl_slot(n % 3, 2 + tid, blockIdx.x & (CTL_SLOTS - 1)), cnt_s[tid]);
 }
 
+// Launch with programmatic stream serialization: the kernel may be
+// scheduled before the preceding kernel on the stream finishes; it waits in
+// grid_wait_prior() for that kernel's results.
+template <typename Kern>
+cudaError_t launch_pdl(Kern kern, int64_t grid, int block, cudaStream_t st, const ApplyArgs &a)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
 template <typename T, int K>
 cudaError_t launch_apply_t(const ApplyArgs &a, cudaStream_t st, const ApplyEvents *ev)
 {
     const int64_t g1 = (a.dp.P + K1_TPB * PPT - 1) / (K1_TPB * PPT);
     if (ev) cudaEventRecord(ev->e0, st);
-    stage01_kernel<T, K1_TPB><<<(unsigned)g1, K1_TPB, 0, st>>>(a);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_pdl(stage01_kernel<T, K1_TPB>, g1, K1_TPB, st, a);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev->e1, st);
     static int per_sm = 0;
@@ -454,8 +474,7 @@ cudaError_t launch_apply_t(const ApplyArgs &a, cudaStream_t st, const ApplyEvent
     }
     const int64_t need = (a.dp.P + K2_TPB - 1) / K2_TPB;
     const int64_t g2 = min((int64_t)a.k2_grid * per_sm, need);
-    stage2_kernel<T, K, K2_TPB><<<(unsigned)max((int64_t)1, g2), K2_TPB, 0, st>>>(a);
-    e = cudaGetLastError();
+    e = launch_pdl(stage2_kernel<T, K, K2_TPB>, max((int64_t)1, g2), K2_TPB, st, a);
     if (ev) cudaEventRecord(ev->e2, st);
     return e;
 }
