@@ -193,6 +193,28 @@ cog_status cog_apply_host(cog_ctx *ctx, const uint8_t *frame_host, uint8_t *mask
  * filled. */
 cog_status cog_apply_host_noalloc(cog_ctx *ctx, const uint8_t *frame_host, uint8_t *mask_host);
 
+/* Batches: one frame for each of many streams per step (cameras of uneven
+ * resolution, K and storage type), run as one captured CUDA graph.  Streams
+ * sharing a storage type and K form a group that one stage-0/1 launch and
+ * one mixture-stage launch cover; groups run as parallel graph branches.
+ * cog_batch_create: ctxs are n >= 1 distinct trained contexts on the
+ * current device; cuda_stream must be a created stream (graphs cannot be
+ * captured on the legacy default stream).  It allocates the batch's
+ * descriptor tables.  While a context belongs to a batch, apply it only
+ * through the batch.
+ * cog_batch_apply: frames_dev[i] / masks_dev[i] are stream i's frame and
+ * mask buffers (as cog_apply).  Asynchronous on the batch's stream.  The
+ * graph is captured on the first call and replayed afterwards; changed
+ * buffer pointers only update device-side descriptors.
+ * cog_batch_sync waits for the batch's stream (then cog_read_stats works
+ * per context).  cog_batch_destroy frees the batch, not its contexts. */
+typedef struct cog_batch cog_batch;
+cog_status cog_batch_create(cog_ctx *const *ctxs, int32_t n, void *cuda_stream, cog_batch **out);
+cog_status cog_batch_apply(cog_batch *batch, const uint8_t *const *frames_dev, uint8_t *const *masks_dev);
+cog_status cog_batch_sync(cog_batch *batch);
+const char *cog_batch_last_error_string(cog_batch *batch);
+cog_status cog_batch_destroy(cog_batch *batch);
+
 /* Statistics of the most recent cog_apply frame and running totals of the
  * stage counts over every frame applied since the last training.
  * Synchronises the stream. */

@@ -82,6 +82,11 @@ def _load() -> C.CDLL:
         "cog_profile_end": (C.c_int, [vp, P(C.c_double), P(C.c_double), P(C.c_int64)]),
         "cog_last_error_string": (C.c_char_p, [vp]),
         "cog_destroy": (C.c_int, [vp]),
+        "cog_batch_create": (C.c_int, [P(vp), i32, vp, P(vp)]),
+        "cog_batch_apply": (C.c_int, [vp, P(vp), P(vp)]),
+        "cog_batch_sync": (C.c_int, [vp]),
+        "cog_batch_last_error_string": (C.c_char_p, [vp]),
+        "cog_batch_destroy": (C.c_int, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -215,6 +220,34 @@ def cog_last_error_string(ctx=None) -> str:
 
 def cog_destroy(ctx) -> None:
     _check(lib.cog_destroy(ctx))
+
+
+def _bcheck(status: int, b=None):
+    if status != COG_OK:
+        msg = lib.cog_batch_last_error_string(b)
+        raise CogError(status, msg.decode() if msg else "")
+
+
+def cog_batch_create(ctxs, stream: int):
+    arr = (C.c_void_p * len(ctxs))(*[c.value if isinstance(c, C.c_void_p) else c for c in ctxs])
+    b = C.c_void_p()
+    _bcheck(lib.cog_batch_create(arr, len(ctxs), stream, C.byref(b)))
+    return b
+
+
+def cog_batch_apply(b, frames, masks) -> None:
+    n = len(frames)
+    fa = (C.c_void_p * n)(*[_ptr(f) for f in frames])
+    ma = (C.c_void_p * n)(*[_ptr(m) for m in masks])
+    _bcheck(lib.cog_batch_apply(b, fa, ma), b)
+
+
+def cog_batch_sync(b) -> None:
+    _bcheck(lib.cog_batch_sync(b), b)
+
+
+def cog_batch_destroy(b) -> None:
+    _bcheck(lib.cog_batch_destroy(b))
 
 
 # ----------------------------------------------------------------------------

@@ -23,6 +23,13 @@ cudaError_t launch_warmup_f32(int, const DevParams &, const StatePtrs &, const u
 cudaError_t launch_warmup_f16(int, const DevParams &, const StatePtrs &, const uint8_t *, int, int, int, cudaStream_t);
 cudaError_t launch_warmup_bf16(int, const DevParams &, const StatePtrs &, const uint8_t *, int, int, int, cudaStream_t);
 
+cudaError_t launch_batch_f32(int, const BatchGroupDev &, uint32_t, uint32_t, cudaStream_t);
+cudaError_t launch_batch_f16(int, const BatchGroupDev &, uint32_t, uint32_t, cudaStream_t);
+cudaError_t launch_batch_bf16(int, const BatchGroupDev &, uint32_t, uint32_t, cudaStream_t);
+int k2_blocks_per_sm_f32(int);
+int k2_blocks_per_sm_f16(int);
+int k2_blocks_per_sm_bf16(int);
+
 int elem_bytes(int dtype) { return dtype == COG_F32 ? 4 : 2; }
 
 int rec_bytes(int dtype, int K) { return (K * 7 * elem_bytes(dtype) + 15) / 16 * 16; }
@@ -617,6 +624,264 @@ cog_status cog_destroy(cog_ctx *c)
     if (c->stage_in) cudaFree(c->stage_in);
     if (c->owns) cudaFree(c->state);
     delete c;
+    return s;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches: one frame for each of many streams per step, as one captured
+// CUDA graph (per storage type and K, one stage-0/1 launch and one mixture
+// launch over all the group's streams; groups run as parallel branches).
+// ---------------------------------------------------------------------------
+struct BatchGroupHost {
+    int dtype = 0, K = 0;
+    std::vector<int> members;          // indices into cog_batch::ctxs
+    std::vector<ApplyArgs> descs;      // host copy of the device descriptors
+    BatchGroupDev dev{};
+    uint32_t k1_ctas = 0, k2_ctas = 0;
+    void *dmem = nullptr;              // descs | frame_no | k1_pre | k2_pre
+    ApplyArgs *pinned = nullptr;       // upload staging
+};
+
+struct cog_batch {
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::vector<cog_ctx *> ctxs;
+    std::vector<BatchGroupHost> groups;
+    std::vector<const uint8_t *> frames;
+    std::vector<uint8_t *> masks;
+    std::vector<cudaStream_t> aux;     // one per group after the first (graph branches)
+    std::vector<cudaEvent_t> fork, join;
+    cudaEvent_t uploaded = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cog_status sticky = COG_OK;
+    char err[512] = {0};
+};
+
+static cog_status batch_err(cog_batch *b, cog_status s, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(b ? b->err : g_create_err, 512, fmt, ap);
+    va_end(ap);
+    if (b && s == COG_ERR_CUDA) b->sticky = s;
+    return s;
+}
+
+static void batch_free(cog_batch *b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (auto &g : b->groups) {
+        if (g.dmem) cudaFree(g.dmem);
+        if (g.pinned) cudaFreeHost(g.pinned);
+    }
+    for (auto s : b->aux) cudaStreamDestroy(s);
+    for (auto e : b->fork) cudaEventDestroy(e);
+    for (auto e : b->join) cudaEventDestroy(e);
+    if (b->uploaded) cudaEventDestroy(b->uploaded);
+    delete b;
+}
+
+extern "C" {
+
+cog_status cog_batch_create(cog_ctx *const *ctxs, int32_t n, void *cuda_stream, cog_batch **out)
+{
+    if (!out || !ctxs || n < 1) return batch_err(nullptr, COG_ERR_INVALID_ARG, "need ctxs, n >= 1 and out");
+    *out = nullptr;
+    for (int i = 0; i < n; i++) {
+        if (!ctxs[i]) return batch_err(nullptr, COG_ERR_INVALID_ARG, "ctxs[%d] is NULL", i);
+        if (ctxs[i]->sticky != COG_OK) return batch_err(nullptr, ctxs[i]->sticky, "ctxs[%d] has a sticky error", i);
+        if (!ctxs[i]->trained) return batch_err(nullptr, COG_ERR_STATE, "ctxs[%d] is not trained", i);
+        if (ctxs[i]->device != ctxs[0]->device)
+            return batch_err(nullptr, COG_ERR_INVALID_ARG, "all contexts of a batch must be on one device");
+        for (int j = 0; j < i; j++)
+            if (ctxs[j] == ctxs[i]) return batch_err(nullptr, COG_ERR_INVALID_ARG, "context %d appears twice", i);
+    }
+    cog_batch *b = new (std::nothrow) cog_batch();
+    if (!b) return batch_err(nullptr, COG_ERR_OOM, "host allocation failed");
+    b->stream = (cudaStream_t)cuda_stream;
+    b->device = ctxs[0]->device;
+    b->ctxs.assign(ctxs, ctxs + n);
+    b->frames.assign(n, nullptr);
+    b->masks.assign(n, nullptr);
+    for (int i = 0; i < n; i++) {
+        int gi = -1;
+        for (size_t g = 0; g < b->groups.size(); g++)
+            if (b->groups[g].dtype == ctxs[i]->p.state_dtype && b->groups[g].K == ctxs[i]->p.K) gi = (int)g;
+        if (gi < 0) {
+            b->groups.emplace_back();
+            gi = (int)b->groups.size() - 1;
+            b->groups[gi].dtype = ctxs[i]->p.state_dtype;
+            b->groups[gi].K = ctxs[i]->p.K;
+        }
+        b->groups[gi].members.push_back(i);
+    }
+    cudaError_t e = cudaEventCreateWithFlags(&b->uploaded, cudaEventDisableTiming);
+    for (auto &g : b->groups) {
+        if (e != cudaSuccess) break;
+        const int m = (int)g.members.size();
+        int64_t psum = 0;
+        for (int i : g.members) psum += ctxs[i]->L.P;
+        const int per_sm = g.dtype == COG_F32 ? k2_blocks_per_sm_f32(g.K)
+                         : (g.dtype == COG_F16 ? k2_blocks_per_sm_f16(g.K) : k2_blocks_per_sm_bf16(g.K));
+        const int64_t k2_total = (int64_t)ctxs[0]->n_sm * per_sm;
+        std::vector<uint32_t> k1(m + 1, 0), k2(m + 1, 0);
+        for (int j = 0; j < m; j++) {
+            const cog_ctx *c = ctxs[g.members[j]];
+            const int64_t t1 = (c->L.P + k1_tile_pixels() - 1) / k1_tile_pixels();
+            const int64_t need2 = (c->L.P + k2_block_threads() - 1) / k2_block_threads();
+            int64_t t2 = (int64_t)((double)k2_total * (double)c->L.P / (double)psum + 0.5);
+            t2 = t2 < 1 ? 1 : (t2 > need2 ? need2 : t2);
+            k1[j + 1] = k1[j] + (uint32_t)t1;
+            k2[j + 1] = k2[j] + (uint32_t)t2;
+            ApplyArgs a{};
+            a.dp = c->dp;
+            a.s = c->sp;
+            a.frame_no = (uint32_t)(c->frame_no % 3);
+            a.k2_grid = (uint32_t)c->n_sm;
+            a.rec_bytes = (uint32_t)c->L.rec_bytes;
+            g.descs.push_back(a);
+        }
+        g.k1_ctas = k1[m];
+        g.k2_ctas = k2[m];
+        const size_t bytes = sizeof(ApplyArgs) * m + 4 * (size_t)m + 8 * (size_t)(m + 1) + 64;
+        if ((e = cudaMalloc(&g.dmem, bytes)) != cudaSuccess) break;
+        if ((e = cudaMallocHost((void **)&g.pinned, sizeof(ApplyArgs) * m)) != cudaSuccess) break;
+        uint8_t *d = (uint8_t *)g.dmem;
+        g.dev.descs = (ApplyArgs *)d;
+        g.dev.frame_no = (uint32_t *)(d + sizeof(ApplyArgs) * m);
+        g.dev.k1_pre = (const uint32_t *)(d + sizeof(ApplyArgs) * m + 4 * m);
+        g.dev.k2_pre = g.dev.k1_pre + (m + 1);
+        g.dev.n = m;
+        std::vector<uint32_t> fno(m);
+        for (int j = 0; j < m; j++) fno[j] = (uint32_t)ctxs[g.members[j]]->frame_no;
+        e = cudaMemcpyAsync(g.dev.frame_no, fno.data(), 4 * m, cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync((void *)g.dev.k1_pre, k1.data(), 4 * (m + 1), cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync((void *)g.dev.k2_pre, k2.data(), 4 * (m + 1), cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    }
+    for (size_t g = 1; g < b->groups.size() && e == cudaSuccess; g++) {
+        cudaStream_t s;
+        cudaEvent_t f, j;
+        if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) break;
+        b->aux.push_back(s);
+        if ((e = cudaEventCreateWithFlags(&f, cudaEventDisableTiming)) != cudaSuccess) break;
+        b->fork.push_back(f);
+        if ((e = cudaEventCreateWithFlags(&j, cudaEventDisableTiming)) != cudaSuccess) break;
+        b->join.push_back(j);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        batch_err(nullptr, e == cudaErrorMemoryAllocation ? COG_ERR_OOM : COG_ERR_CUDA, "cog_batch_create: %s",
+                  cudaGetErrorString(e));
+        cog_status s = e == cudaErrorMemoryAllocation ? COG_ERR_OOM : COG_ERR_CUDA;
+        batch_free(b);
+        return s;
+    }
+    *out = b;
+    return COG_OK;
+}
+
+static cudaError_t batch_capture(cog_batch *b)
+{
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    for (size_t gi = 0; gi < b->groups.size() && e == cudaSuccess; gi++) {
+        BatchGroupHost &g = b->groups[gi];
+        cudaStream_t st = b->stream;
+        if (gi > 0) {
+            st = b->aux[gi - 1];
+            if ((e = cudaEventRecord(b->fork[gi - 1], b->stream)) != cudaSuccess) break;
+            if ((e = cudaStreamWaitEvent(st, b->fork[gi - 1], 0)) != cudaSuccess) break;
+        }
+        switch (g.dtype) {
+        case COG_F32: e = launch_batch_f32(g.K, g.dev, g.k1_ctas, g.k2_ctas, st); break;
+        case COG_F16: e = launch_batch_f16(g.K, g.dev, g.k1_ctas, g.k2_ctas, st); break;
+        default: e = launch_batch_bf16(g.K, g.dev, g.k1_ctas, g.k2_ctas, st); break;
+        }
+        if (e == cudaSuccess) e = launch_batch_advance(g.dev, st);
+        if (e == cudaSuccess && gi > 0) {
+            if ((e = cudaEventRecord(b->join[gi - 1], st)) == cudaSuccess)
+                e = cudaStreamWaitEvent(b->stream, b->join[gi - 1], 0);
+        }
+    }
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    return e;
+}
+
+cog_status cog_batch_apply(cog_batch *b, const uint8_t *const *frames_dev, uint8_t *const *masks_dev)
+{
+    if (!b) return COG_ERR_INVALID_ARG;
+    if (b->sticky != COG_OK) return b->sticky;
+    if (!frames_dev || !masks_dev) return batch_err(b, COG_ERR_INVALID_ARG, "frames_dev and masks_dev are required");
+    const int n = (int)b->ctxs.size();
+    for (int i = 0; i < n; i++) {
+        if (!frames_dev[i] || !masks_dev[i]) return batch_err(b, COG_ERR_INVALID_ARG, "stream %d: NULL buffer", i);
+        if (b->ctxs[i]->sticky != COG_OK) return batch_err(b, b->ctxs[i]->sticky, "stream %d: sticky error", i);
+    }
+    cudaError_t e = cudaSuccess;
+    for (auto &g : b->groups) {
+        bool dirty = false;
+        for (size_t j = 0; j < g.members.size(); j++) {
+            const int i = g.members[j];
+            if (b->frames[i] == frames_dev[i] && b->masks[i] == masks_dev[i]) continue;
+            ApplyArgs &a = g.descs[j];
+            a.frame = frames_dev[i];
+            a.mask = masks_dev[i];
+            a.stagemap = nullptr;
+            a.frame_al4 = ((uintptr_t)frames_dev[i] & 3) == 0;
+            a.out_al4 = ((uintptr_t)masks_dev[i] & 3) == 0;
+            b->frames[i] = frames_dev[i];
+            b->masks[i] = masks_dev[i];
+            dirty = true;
+        }
+        if (!dirty) continue;
+        // the device keeps frame_no current; the host copy matches it at
+        // this point in stream order
+        for (size_t j = 0; j < g.members.size(); j++)
+            g.descs[j].frame_no = (uint32_t)(b->ctxs[g.members[j]]->frame_no % 3);
+        if ((e = cudaEventSynchronize(b->uploaded)) != cudaSuccess) break;
+        memcpy(g.pinned, g.descs.data(), sizeof(ApplyArgs) * g.descs.size());
+        if ((e = cudaMemcpyAsync(g.dev.descs, g.pinned, sizeof(ApplyArgs) * g.descs.size(), cudaMemcpyHostToDevice,
+                                 b->stream)) != cudaSuccess)
+            break;
+        if ((e = cudaEventRecord(b->uploaded, b->stream)) != cudaSuccess) break;
+    }
+    if (e == cudaSuccess && !b->exec) e = batch_capture(b);
+    if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, b->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return batch_err(b, COG_ERR_CUDA, "cog_batch_apply: %s", cudaGetErrorString(e));
+    }
+    for (cog_ctx *c : b->ctxs) c->frame_no++;
+    return COG_OK;
+}
+
+cog_status cog_batch_sync(cog_batch *b)
+{
+    if (!b) return COG_ERR_INVALID_ARG;
+    if (b->sticky != COG_OK) return b->sticky;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return batch_err(b, COG_ERR_CUDA, "cog_batch_sync: %s", cudaGetErrorString(e));
+    return COG_OK;
+}
+
+const char *cog_batch_last_error_string(cog_batch *b) { return b ? b->err : g_create_err; }
+
+cog_status cog_batch_destroy(cog_batch *b)
+{
+    if (!b) return COG_ERR_INVALID_ARG;
+    cog_status s = b->sticky;
+    batch_free(b);
     return s;
 }
 

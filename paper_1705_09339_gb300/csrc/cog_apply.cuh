@@ -236,25 +236,19 @@ __device__ __forceinline__ int k1_warp(const ApplyArgs &A, K1Warp &W, uint32_t w
     return ne;
 }
 
+// One CTA of the stage-0/1 pass over stream A: tile `cta` of its frame.
 template <typename T, int TPB>
-__global__ void __launch_bounds__(TPB, 10) stage01_kernel(const ApplyArgs A)
+__device__ __forceinline__ void k1_cta(const ApplyArgs &A, uint32_t cta)
 {
     static_assert(PPT == 4, "frame and mask vector widths assume 4 pixels per thread");
     constexpr int NW = TPB / 32;
     __shared__ K1Warp W_s[NW];
-    __shared__ uint32_t nent_s[NW], qbase_s, cnt_s[2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t n = A.frame_no;
     uint32_t *ctl = A.s.ctl;
-    const uint32_t wbase = ((uint32_t)blockIdx.x * TPB + warp * 32) * PPT;
-    // programmatic dependent launch: let the mixture stage's CTAs be
-    // scheduled as this grid drains, and wait for the previous frame's
-    // kernels before touching the state they write
-    grid_launch_dependents();
-    grid_wait_prior();
+    const uint32_t wbase = (cta * TPB + warp * 32) * PPT;
 
-    if (tid < 2) cnt_s[tid] = 0;
-    if (blockIdx.x == 0) {
+    if (cta == 0) {
         // rotate the per-frame counters: clear frame n+1's, add frame n-1's
         // to the running totals
         for (int i = tid; i < CTL_FIELDS * CTL_SLOTS; i += TPB) ctl[ctl_slot((n + 1) % 3, i / CTL_SLOTS, i % CTL_SLOTS)] = 0;
@@ -275,7 +269,7 @@ __global__ void __launch_bounds__(TPB, 10) stage01_kernel(const ApplyArgs A)
     else ne = k1_warp<T, false>(A, W_s[warp], wbase, lane, n_fd, n_rga);
 
     // per-warp reservation (padded counters)
-    const uint32_t gwarp = blockIdx.x * NW + warp;
+    const uint32_t gwarp = cta * NW + warp;
     const uint32_t seg = gwarp & (QSEG - 1);
     const uint32_t vfd = __reduce_add_sync(0xffffffffu, n_fd);
     const uint32_t vrga = __reduce_add_sync(0xffffffffu, n_rga);
@@ -294,6 +288,17 @@ __global__ void __launch_bounds__(TPB, 10) stage01_kernel(const ApplyArgs A)
         uint4 *q = A.s.queue + seg * A.s.qseg_cap + base;
         for (int k = lane; k < ne; k += 32) q[k] = W_s[warp].ent[k];
     }
+}
+
+template <typename T, int TPB>
+__global__ void __launch_bounds__(TPB, 10) stage01_kernel(const ApplyArgs A)
+{
+    // programmatic dependent launch: let the mixture stage's CTAs be
+    // scheduled as this grid drains, and wait for the previous frame's
+    // kernels before touching the state they write
+    grid_launch_dependents();
+    grid_wait_prior();
+    k1_cta<T, TPB>(A, blockIdx.x);
 }
 
 // ---- stage 2: one survivor of the queue, in two halves (its loads, then
@@ -384,16 +389,15 @@ __device__ __forceinline__ int s2_finish(const ApplyArgs &A, const S2In<T, K> &i
     return st;
 }
 
+// One of ncta CTAs walking stream A's survivor queue.
 template <typename T, int K, int TPB>
-__global__ void __launch_bounds__(TPB) stage2_kernel(const ApplyArgs A)
+__device__ __forceinline__ void k2_cta(const ApplyArgs &A, uint32_t cta, uint32_t ncta)
 {
     __shared__ uint32_t flag_s, cnt_s[3], segp_s[QSEG + 1];
     const DevParams &dp = A.dp;
     const int tid = threadIdx.x, lane = tid & 31;
     const uint32_t n = A.frame_no;
     uint32_t *ctl = A.s.ctl;
-    grid_launch_dependents();
-    grid_wait_prior();     // the queue and counters come from stage01_kernel
     if (tid < 32) {
         const bool f = illum_flag_prev(dp, ctl, n, lane);
         // exclusive prefix of the queue segments' lengths
@@ -412,7 +416,7 @@ __global__ void __launch_bounds__(TPB) stage2_kernel(const ApplyArgs A)
     __syncthreads();
     const bool flag = flag_s;
     const uint32_t nq = segp_s[QSEG];
-    const uint32_t stride = gridDim.x * TPB;
+    const uint32_t stride = ncta * TPB;
     auto entry = [&](uint32_t q) -> int64_t {   // flat index -> queue slot
         int lo = 0;
 #pragma unroll
@@ -421,7 +425,7 @@ __global__ void __launch_bounds__(TPB) stage2_kernel(const ApplyArgs A)
         return (int64_t)lo * A.s.qseg_cap + (q - segp_s[lo]);
     };
     uint32_t cbg = 0, cfg = 0, cil = 0;
-    for (uint32_t q = blockIdx.x * TPB + tid; q < nq; q += stride) {
+    for (uint32_t q = cta * TPB + tid; q < nq; q += stride) {
         S2In<T, K> a;
         s2_load<T, K>(A, entry(q), a);
         const int st = s2_finish<T, K>(A, a, flag);
@@ -436,7 +440,45 @@ __global__ void __launch_bounds__(TPB) stage2_kernel(const ApplyArgs A)
         if (cil) atomicAdd(&cnt_s[2], cil);
     }
     __syncthreads();
-    if (tid < 3 && cnt_s[tid]) atomicAdd(ctl + ctl_slot(n % 3, 2 + tid, blockIdx.x & (CTL_SLOTS - 1)), cnt_s[tid]);
+    if (tid < 3 && cnt_s[tid]) atomicAdd(ctl + ctl_slot(n % 3, 2 + tid, cta & (CTL_SLOTS - 1)), cnt_s[tid]);
+}
+
+template <typename T, int K, int TPB>
+__global__ void __launch_bounds__(TPB) stage2_kernel(const ApplyArgs A)
+{
+    grid_launch_dependents();
+    grid_wait_prior();     // the queue and counters come from stage01_kernel
+    k2_cta<T, K, TPB>(A, blockIdx.x, gridDim.x);
+}
+
+// ---- batched: many streams of one storage type and K in one launch each
+__device__ __forceinline__ int batch_stream(const uint32_t *pre, int n, uint32_t x)
+{
+    int lo = 0, hi = n;            // largest s < n with pre[s] <= x
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(pre + mid) <= x) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <typename T, int TPB>
+__global__ void __launch_bounds__(TPB, 10) stage01_batch_kernel(const BatchGroupDev G)
+{
+    grid_launch_dependents();
+    grid_wait_prior();
+    const int s = batch_stream(G.k1_pre, G.n, blockIdx.x);
+    k1_cta<T, TPB>(G.descs[s], blockIdx.x - G.k1_pre[s]);
+}
+
+template <typename T, int K, int TPB>
+__global__ void __launch_bounds__(TPB) stage2_batch_kernel(const BatchGroupDev G)
+{
+    grid_launch_dependents();
+    grid_wait_prior();
+    const int s = batch_stream(G.k2_pre, G.n, blockIdx.x);
+    k2_cta<T, K, TPB>(G.descs[s], blockIdx.x - G.k2_pre[s], G.k2_pre[s + 1] - G.k2_pre[s]);
 }
 
 // Launch with programmatic stream serialization: the kernel may be
@@ -479,4 +521,42 @@ cudaError_t launch_apply_t(const ApplyArgs &a, cudaStream_t st, const ApplyEvent
     return e;
 }
 
+}  // namespace cog
+
+namespace cog {
+
+template <typename T, int K>
+cudaError_t launch_batch_t(const BatchGroupDev &g, uint32_t k1_ctas, uint32_t k2_ctas, cudaStream_t st)
+{
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.stream = st;
+    cfg.gridDim = dim3(k1_ctas);
+    cfg.blockDim = dim3(K1_TPB);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, stage01_batch_kernel<T, K1_TPB>, g);
+    if (e != cudaSuccess) return e;
+    cfg.gridDim = dim3(k2_ctas);
+    cfg.blockDim = dim3(K2_TPB);
+    return cudaLaunchKernelEx(&cfg, stage2_batch_kernel<T, K, K2_TPB>, g);
+}
+
+template <typename T, int K>
+int k2_blocks_per_sm_t()
+{
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, stage2_batch_kernel<T, K, K2_TPB>, K2_TPB, 0) !=
+            cudaSuccess || b < 1)
+        b = 4;
+    return b;
+}
+
+}  // namespace cog
+
+namespace cog {
+inline int k1_tile_pixels_impl() { return K1_TPB * PPT; }
+inline int k2_block_threads_impl() { return K2_TPB; }
 }  // namespace cog

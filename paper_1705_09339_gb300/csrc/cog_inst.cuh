@@ -30,6 +30,28 @@ cudaError_t COG_CAT(launch_apply_, COG_SUFFIX)(int K, const ApplyArgs &a, cudaSt
 #undef CALL_A
 }
 
+cudaError_t COG_CAT(launch_batch_, COG_SUFFIX)(int K, const BatchGroupDev &g, uint32_t k1, uint32_t k2,
+                                               cudaStream_t st)
+{
+#define CALL_B(k) launch_batch_t<COG_T, k>(g, k1, k2, st)
+    COG_KSWITCH(CALL_B)
+#undef CALL_B
+}
+
+int COG_CAT(k2_blocks_per_sm_, COG_SUFFIX)(int K)
+{
+    switch (K) {
+    case 1: return k2_blocks_per_sm_t<COG_T, 1>();
+    case 2: return k2_blocks_per_sm_t<COG_T, 2>();
+    case 3: return k2_blocks_per_sm_t<COG_T, 3>();
+    case 4: return k2_blocks_per_sm_t<COG_T, 4>();
+    case 5: return k2_blocks_per_sm_t<COG_T, 5>();
+    case 6: return k2_blocks_per_sm_t<COG_T, 6>();
+    case 7: return k2_blocks_per_sm_t<COG_T, 7>();
+    default: return k2_blocks_per_sm_t<COG_T, 8>();
+    }
+}
+
 cudaError_t COG_CAT(launch_plain_, COG_SUFFIX)(int K, const DevParams &dp, const StatePtrs &s,
                                                const uint8_t *frame, uint8_t *mask, cudaStream_t st)
 {

@@ -95,6 +95,24 @@ struct ApplyArgs {
     uint32_t rec_bytes;  // bytes of one mixture record (for L2 prefetches)
 };
 
+// A batch group: streams sharing one storage type and K, run by one launch
+// of each kernel.  Descriptors live in device memory so that a captured
+// graph stays valid while frame buffers change.
+struct BatchGroupDev {
+    ApplyArgs *descs;        // [n], frame_no field = frames applied % 3
+    uint32_t *frame_no;      // [n] frames applied (full count)
+    const uint32_t *k1_pre;  // [n + 1] prefix of first-kernel CTAs per stream
+    const uint32_t *k2_pre;  // [n + 1] prefix of mixture-stage CTAs per stream
+    int n;
+};
+
+cudaError_t launch_batch_group(int dtype, int K, const BatchGroupDev &g, uint32_t k1_ctas, uint32_t k2_ctas,
+                               cudaStream_t st);
+cudaError_t launch_batch_advance(const BatchGroupDev &g, cudaStream_t st);
+int k1_tile_pixels();
+int k2_block_threads();
+int k2_blocks_per_sm(int dtype, int K);
+
 // Optional per-kernel timing: events recorded before the first kernel,
 // between the two kernels and after the second, on the launch stream.
 struct ApplyEvents {

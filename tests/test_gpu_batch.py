@@ -1,0 +1,90 @@
+"""The batched path (many streams per step in one captured graph) gives
+exactly what per-stream cog_apply gives, through graph replays, mixed
+sizes, K and storage types, and changing frame buffers."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+
+@pytest.fixture(scope="module")
+def cog():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1705_09339_gb300 import cog
+    return cog
+
+
+SPECS = [(160, 120, 3, "f32"), (320, 240, 5, "f16"), (97, 61, 3, "f32"), (640, 480, 5, "f16"),
+         (33, 1, 5, "f16"), (200, 100, 3, "bf16"), (160, 120, 5, "f16")]
+
+
+def _streams(n_train=20, n_test=6):
+    from cogsynth import Scene
+    out = []
+    for i, (w, h, k, dt) in enumerate(SPECS):
+        sc = Scene(w, h, 40 + i, kind="dynamic", n_train=n_train, fg_frac=0.05, switch_at=3)
+        fr, _ = sc.frames(0, n_train + n_test)
+        out.append((w, h, k, dt, fr))
+    return out
+
+
+def _ctx(cog, w, h, k, dt, fr, n_train, stream):
+    p = cog.cog_default_params(w, h, k, state_dtype=dt)
+    c = cog.cog_create(p, stream)
+    t = torch.from_numpy(fr[:n_train].reshape(n_train, h, w, 3)).cuda()
+    cog.cog_train_prior(c, t, n_train)
+    cog.cog_sync(c)
+    return c, p
+
+
+def test_batch_equals_single_stream_apply(cog):
+    NT, NF = 20, 6
+    data = _streams(NT, NF)
+    s = torch.cuda.Stream()
+    single = [_ctx(cog, w, h, k, dt, fr, NT, s.cuda_stream) for (w, h, k, dt, fr) in data]
+    batched = [_ctx(cog, w, h, k, dt, fr, NT, s.cuda_stream) for (w, h, k, dt, fr) in data]
+    b = cog.cog_batch_create([c for c, _ in batched], s.cuda_stream)
+    # two sets of device frame buffers, alternated between steps
+    bufs = [[torch.empty((h, w, 3), dtype=torch.uint8, device="cuda") for (w, h, _, _, _) in data] for _ in range(2)]
+    mb = [torch.empty((h, w), dtype=torch.uint8, device="cuda") for (w, h, _, _, _) in data]
+    ms = [torch.empty((h, w), dtype=torch.uint8, device="cuda") for (w, h, _, _, _) in data]
+    for t in range(NF):
+        with torch.cuda.stream(s):
+            for i, (w, h, k, dt, fr) in enumerate(data):
+                bufs[t % 2][i].copy_(torch.from_numpy(fr[NT + t].reshape(h, w, 3)))
+            s.synchronize()
+            for i, (c, _) in enumerate(single):
+                cog.cog_apply(c, bufs[t % 2][i], ms[i])
+            cog.cog_batch_apply(b, bufs[t % 2], mb)
+            cog.cog_batch_sync(b)
+            for c, _ in single:
+                cog.cog_sync(c)
+        for i in range(len(data)):
+            assert torch.equal(mb[i], ms[i]), (t, i)
+    for (ca, pa), (cb, pb) in zip(single, batched):
+        sa = cog.decode_state(cog.cog_export_state(ca, pa), pa)
+        sb = cog.decode_state(cog.cog_export_state(cb, pb), pb)
+        for key in ("w", "mu", "var", "rga_m", "rga_v", "conf", "label", "prev"):
+            assert np.array_equal(sa[key], sb[key]), key
+        la, ta = cog.cog_read_stats(ca)
+        lb, tb = cog.cog_read_stats(cb)
+        assert la == lb and ta == tb
+    cog.cog_batch_destroy(b)
+    for c, _ in single + batched:
+        cog.cog_destroy(c)
+
+
+def test_batch_argument_errors(cog):
+    with pytest.raises(cog.CogError):
+        cog.cog_batch_create([], torch.cuda.Stream().cuda_stream)
+    p = cog.cog_default_params(32, 32, 3)
+    c = cog.cog_create(p, None)
+    with pytest.raises(cog.CogError) as e:          # untrained
+        cog.cog_batch_create([c], torch.cuda.Stream().cuda_stream)
+    assert e.value.status == cog.COG_ERR_STATE
+    cog.cog_destroy(c)
