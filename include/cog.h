@@ -231,6 +231,14 @@ cog_status cog_import_state(cog_ctx *ctx, const void *src_host, size_t bytes);
 /* Number of frames applied since training, and the device state pointer. */
 cog_status cog_info(cog_ctx *ctx, int64_t *frames_applied, void **state_dev);
 
+/* Launch shape of the context's two cascade kernels (the autotuner's
+ * knobs; results do not depend on them): k1_threads in {64, 128, 256}
+ * threads per stage-0/1 CTA (4 pixels per thread), k2_threads in {64, 128}
+ * per mixture-stage CTA, k2_ctas_per_sm mixture-stage CTAs per SM (0: as
+ * many as fit).  Defaults 128, 64, 0.  A batch uses each group's first
+ * member's shape, read at cog_batch_create. */
+cog_status cog_set_launch(cog_ctx *ctx, int32_t k1_threads, int32_t k2_threads, int32_t k2_ctas_per_sm);
+
 /* Per-kernel timing.  cog_profile_begin makes the next max_frames calls
  * of cog_apply record CUDA events on the context's stream around each of
  * its two kernels (stages 0-1, then the mixture stage); cog_profile_end

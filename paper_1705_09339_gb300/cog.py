@@ -78,6 +78,7 @@ def _load() -> C.CDLL:
         "cog_import_state": (C.c_int, [vp, vp, sz]),
         "cog_info": (C.c_int, [vp, P(C.c_int64), P(vp)]),
         "cog_profile_begin": (C.c_int, [vp, i32]),
+        "cog_set_launch": (C.c_int, [vp, i32, i32, i32]),
         "cog_set_l2_fetch_bytes": (C.c_int, [i32]),
         "cog_profile_end": (C.c_int, [vp, P(C.c_double), P(C.c_double), P(C.c_int64)]),
         "cog_last_error_string": (C.c_char_p, [vp]),
@@ -200,6 +201,10 @@ def cog_info(ctx):
 
 def cog_set_l2_fetch_bytes(nbytes: int) -> None:
     _check(lib.cog_set_l2_fetch_bytes(nbytes))
+
+
+def cog_set_launch(ctx, k1_threads: int = 128, k2_threads: int = 64, k2_ctas_per_sm: int = 0) -> None:
+    _check(lib.cog_set_launch(ctx, k1_threads, k2_threads, k2_ctas_per_sm), ctx)
 
 
 def cog_profile_begin(ctx, max_frames: int) -> None:

@@ -13,9 +13,9 @@
 #include "cog_internal.h"
 
 namespace cog {
-cudaError_t launch_apply_f32(int, const ApplyArgs &, cudaStream_t, const ApplyEvents *);
-cudaError_t launch_apply_f16(int, const ApplyArgs &, cudaStream_t, const ApplyEvents *);
-cudaError_t launch_apply_bf16(int, const ApplyArgs &, cudaStream_t, const ApplyEvents *);
+cudaError_t launch_apply_f32(int, const ApplyArgs &, const LaunchCfg &, cudaStream_t, const ApplyEvents *);
+cudaError_t launch_apply_f16(int, const ApplyArgs &, const LaunchCfg &, cudaStream_t, const ApplyEvents *);
+cudaError_t launch_apply_bf16(int, const ApplyArgs &, const LaunchCfg &, cudaStream_t, const ApplyEvents *);
 cudaError_t launch_plain_f32(int, const DevParams &, const StatePtrs &, const uint8_t *, uint8_t *, cudaStream_t);
 cudaError_t launch_plain_f16(int, const DevParams &, const StatePtrs &, const uint8_t *, uint8_t *, cudaStream_t);
 cudaError_t launch_plain_bf16(int, const DevParams &, const StatePtrs &, const uint8_t *, uint8_t *, cudaStream_t);
@@ -23,12 +23,12 @@ cudaError_t launch_warmup_f32(int, const DevParams &, const StatePtrs &, const u
 cudaError_t launch_warmup_f16(int, const DevParams &, const StatePtrs &, const uint8_t *, int, int, int, cudaStream_t);
 cudaError_t launch_warmup_bf16(int, const DevParams &, const StatePtrs &, const uint8_t *, int, int, int, cudaStream_t);
 
-cudaError_t launch_batch_f32(int, const BatchGroupDev &, uint32_t, uint32_t, cudaStream_t);
-cudaError_t launch_batch_f16(int, const BatchGroupDev &, uint32_t, uint32_t, cudaStream_t);
-cudaError_t launch_batch_bf16(int, const BatchGroupDev &, uint32_t, uint32_t, cudaStream_t);
-int k2_blocks_per_sm_f32(int);
-int k2_blocks_per_sm_f16(int);
-int k2_blocks_per_sm_bf16(int);
+cudaError_t launch_batch_f32(int, const BatchGroupDev &, const LaunchCfg &, uint32_t, uint32_t, cudaStream_t);
+cudaError_t launch_batch_f16(int, const BatchGroupDev &, const LaunchCfg &, uint32_t, uint32_t, cudaStream_t);
+cudaError_t launch_batch_bf16(int, const BatchGroupDev &, const LaunchCfg &, uint32_t, uint32_t, cudaStream_t);
+int k2_blocks_per_sm_f32(int, const LaunchCfg &);
+int k2_blocks_per_sm_f16(int, const LaunchCfg &);
+int k2_blocks_per_sm_bf16(int, const LaunchCfg &);
 
 int elem_bytes(int dtype) { return dtype == COG_F32 ? 4 : 2; }
 
@@ -78,6 +78,7 @@ struct cog_ctx {
     char err[512];
     uint8_t *stage_in, *stage_out;   // cog_apply_host staging buffers
     int n_sm;                        // multiprocessors of the device
+    LaunchCfg launch;                // kernel launch shape (cog_set_launch)
     std::vector<ApplyEvents> prof;   // per-frame kernel timing events (profiling on)
     int64_t prof_n;                  // frames recorded since profiling was enabled
 };
@@ -341,9 +342,9 @@ cog_status cog_apply(cog_ctx *c, const uint8_t *frame_dev, uint8_t *mask_dev, ui
     if (!c->prof.empty() && c->prof_n < (int64_t)c->prof.size()) ev = &c->prof[(size_t)c->prof_n++];
     cudaError_t e;
     switch (c->p.state_dtype) {
-    case COG_F32: e = launch_apply_f32(c->p.K, a, c->stream, ev); break;
-    case COG_F16: e = launch_apply_f16(c->p.K, a, c->stream, ev); break;
-    default: e = launch_apply_bf16(c->p.K, a, c->stream, ev); break;
+    case COG_F32: e = launch_apply_f32(c->p.K, a, c->launch, c->stream, ev); break;
+    case COG_F16: e = launch_apply_f16(c->p.K, a, c->launch, c->stream, ev); break;
+    default: e = launch_apply_bf16(c->p.K, a, c->launch, c->stream, ev); break;
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "cog_apply launch");
     c->frame_no++;
@@ -568,6 +569,19 @@ static void free_profile(cog_ctx *c)
     c->prof_n = 0;
 }
 
+cog_status cog_set_launch(cog_ctx *c, int32_t k1_threads, int32_t k2_threads, int32_t k2_ctas_per_sm)
+{
+    if (!c) return COG_ERR_INVALID_ARG;
+    if (k1_threads != 64 && k1_threads != 128 && k1_threads != 256)
+        return set_err(c, COG_ERR_INVALID_ARG, "k1_threads must be 64, 128 or 256");
+    if (k2_threads != 64 && k2_threads != 128) return set_err(c, COG_ERR_INVALID_ARG, "k2_threads must be 64 or 128");
+    if (k2_ctas_per_sm < 0 || k2_ctas_per_sm > 64) return set_err(c, COG_ERR_INVALID_ARG, "k2_ctas_per_sm out of range");
+    c->launch.k1_tpb = k1_threads;
+    c->launch.k2_tpb = k2_threads;
+    c->launch.k2_per_sm = k2_ctas_per_sm;
+    return COG_OK;
+}
+
 cog_status cog_profile_begin(cog_ctx *c, int32_t max_frames)
 {
     cog_status s = check_ctx(c);
@@ -636,6 +650,7 @@ cog_status cog_destroy(cog_ctx *c)
 // ---------------------------------------------------------------------------
 struct BatchGroupHost {
     int dtype = 0, K = 0;
+    LaunchCfg launch;                  // the first member's launch shape
     std::vector<int> members;          // indices into cog_batch::ctxs
     std::vector<ApplyArgs> descs;      // host copy of the device descriptors
     BatchGroupDev dev{};
@@ -716,6 +731,7 @@ cog_status cog_batch_create(cog_ctx *const *ctxs, int32_t n, void *cuda_stream, 
             gi = (int)b->groups.size() - 1;
             b->groups[gi].dtype = ctxs[i]->p.state_dtype;
             b->groups[gi].K = ctxs[i]->p.K;
+            b->groups[gi].launch = ctxs[i]->launch;
         }
         b->groups[gi].members.push_back(i);
     }
@@ -725,14 +741,15 @@ cog_status cog_batch_create(cog_ctx *const *ctxs, int32_t n, void *cuda_stream, 
         const int m = (int)g.members.size();
         int64_t psum = 0;
         for (int i : g.members) psum += ctxs[i]->L.P;
-        const int per_sm = g.dtype == COG_F32 ? k2_blocks_per_sm_f32(g.K)
-                         : (g.dtype == COG_F16 ? k2_blocks_per_sm_f16(g.K) : k2_blocks_per_sm_bf16(g.K));
+        const int per_sm = g.dtype == COG_F32 ? k2_blocks_per_sm_f32(g.K, g.launch)
+                         : (g.dtype == COG_F16 ? k2_blocks_per_sm_f16(g.K, g.launch) : k2_blocks_per_sm_bf16(g.K, g.launch));
         const int64_t k2_total = (int64_t)ctxs[0]->n_sm * per_sm;
         std::vector<uint32_t> k1(m + 1, 0), k2(m + 1, 0);
         for (int j = 0; j < m; j++) {
             const cog_ctx *c = ctxs[g.members[j]];
-            const int64_t t1 = (c->L.P + k1_tile_pixels() - 1) / k1_tile_pixels();
-            const int64_t need2 = (c->L.P + k2_block_threads() - 1) / k2_block_threads();
+            const int64_t tile = (int64_t)g.launch.k1_tpb * 4;
+            const int64_t t1 = (c->L.P + tile - 1) / tile;
+            const int64_t need2 = (c->L.P + g.launch.k2_tpb - 1) / g.launch.k2_tpb;
             int64_t t2 = (int64_t)((double)k2_total * (double)c->L.P / (double)psum + 0.5);
             t2 = t2 < 1 ? 1 : (t2 > need2 ? need2 : t2);
             k1[j + 1] = k1[j] + (uint32_t)t1;
@@ -801,9 +818,9 @@ static cudaError_t batch_capture(cog_batch *b)
             if ((e = cudaStreamWaitEvent(st, b->fork[gi - 1], 0)) != cudaSuccess) break;
         }
         switch (g.dtype) {
-        case COG_F32: e = launch_batch_f32(g.K, g.dev, g.k1_ctas, g.k2_ctas, st); break;
-        case COG_F16: e = launch_batch_f16(g.K, g.dev, g.k1_ctas, g.k2_ctas, st); break;
-        default: e = launch_batch_bf16(g.K, g.dev, g.k1_ctas, g.k2_ctas, st); break;
+        case COG_F32: e = launch_batch_f32(g.K, g.dev, g.launch, g.k1_ctas, g.k2_ctas, st); break;
+        case COG_F16: e = launch_batch_f16(g.K, g.dev, g.launch, g.k1_ctas, g.k2_ctas, st); break;
+        default: e = launch_batch_bf16(g.K, g.dev, g.launch, g.k1_ctas, g.k2_ctas, st); break;
         }
         if (e == cudaSuccess) e = launch_batch_advance(g.dev, st);
         if (e == cudaSuccess && gi > 0) {

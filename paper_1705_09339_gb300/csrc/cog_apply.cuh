@@ -32,13 +32,13 @@
 namespace cog {
 
 constexpr int PPT = 4;         // pixels per thread in stage01_kernel
-constexpr int K1_TPB = 128;
+constexpr int K1_TPB = 128;    // default launch shape (the autotuner may pick others)
 constexpr int K2_TPB = 64;
 constexpr int WPX = 32 * PPT;  // pixels per warp in stage01_kernel
 // Queue segments: warp w of the first kernel puts up to WPX survivors into
 // segment w % QSEG.  The layout sizes a segment for ceil(CTAs / QSEG) tiles
 // of K1_TILE pixels, which holds every warp that maps to it.
-static_assert(K1_TPB * PPT * 2 == K1_TILE && WPX * 32 % K1_TILE == 0, "queue segment sizing");
+static_assert(WPX * 32 % K1_TILE == 0, "queue segment sizing assumes 128-pixel warps");
 constexpr float R255 = 1.f / 255.f;
 
 // Read the previous frame's counters: illumination flag (lag one frame).
@@ -291,7 +291,7 @@ __device__ __forceinline__ void k1_cta(const ApplyArgs &A, uint32_t cta)
 }
 
 template <typename T, int TPB>
-__global__ void __launch_bounds__(TPB, 10) stage01_kernel(const ApplyArgs A)
+__global__ void __launch_bounds__(TPB, 1280 / TPB) stage01_kernel(const ApplyArgs A)
 {
     // programmatic dependent launch: let the mixture stage's CTAs be
     // scheduled as this grid drains, and wait for the previous frame's
@@ -464,7 +464,7 @@ __device__ __forceinline__ int batch_stream(const uint32_t *pre, int n, uint32_t
 }
 
 template <typename T, int TPB>
-__global__ void __launch_bounds__(TPB, 10) stage01_batch_kernel(const BatchGroupDev G)
+__global__ void __launch_bounds__(TPB, 1280 / TPB) stage01_batch_kernel(const BatchGroupDev G)
 {
     grid_launch_dependents();
     grid_wait_prior();
@@ -500,33 +500,60 @@ cudaError_t launch_pdl(Kern kern, int64_t grid, int block, cudaStream_t st, cons
     return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
-template <typename T, int K>
-cudaError_t launch_apply_t(const ApplyArgs &a, cudaStream_t st, const ApplyEvents *ev)
+// ---- launch shapes: first-kernel CTA size in {64, 128, 256}, mixture-stage
+//      CTA size in {64, 128}, mixture-stage CTAs per SM (0: as many as fit)
+template <typename T>
+void (*k1_single(int tpb))(ApplyArgs)
 {
-    const int64_t g1 = (a.dp.P + K1_TPB * PPT - 1) / (K1_TPB * PPT);
+    return tpb == 64 ? stage01_kernel<T, 64> : (tpb == 256 ? stage01_kernel<T, 256> : stage01_kernel<T, 128>);
+}
+template <typename T, int K>
+void (*k2_single(int tpb))(ApplyArgs)
+{
+    return tpb == 128 ? stage2_kernel<T, K, 128> : stage2_kernel<T, K, 64>;
+}
+template <typename T>
+void (*k1_batch(int tpb))(BatchGroupDev)
+{
+    return tpb == 64 ? stage01_batch_kernel<T, 64>
+                     : (tpb == 256 ? stage01_batch_kernel<T, 256> : stage01_batch_kernel<T, 128>);
+}
+template <typename T, int K>
+void (*k2_batch(int tpb))(BatchGroupDev)
+{
+    return tpb == 128 ? stage2_batch_kernel<T, K, 128> : stage2_batch_kernel<T, K, 64>;
+}
+
+template <typename KernT>
+int blocks_per_sm(KernT k, int tpb)
+{
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, tpb, 0) != cudaSuccess || b < 1) b = 1;
+    return b;
+}
+
+template <typename T, int K>
+cudaError_t launch_apply_t(const ApplyArgs &a, const LaunchCfg &lc, cudaStream_t st, const ApplyEvents *ev)
+{
+    const int64_t g1 = (a.dp.P + lc.k1_tpb * PPT - 1) / (lc.k1_tpb * PPT);
     if (ev) cudaEventRecord(ev->e0, st);
-    cudaError_t e = launch_pdl(stage01_kernel<T, K1_TPB>, g1, K1_TPB, st, a);
+    cudaError_t e = launch_pdl(k1_single<T>(lc.k1_tpb), g1, lc.k1_tpb, st, a);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev->e1, st);
-    static int per_sm = 0;
-    if (!per_sm) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage2_kernel<T, K, K2_TPB>, K2_TPB, 0) !=
-                cudaSuccess || per_sm < 1)
-            per_sm = 4;
-    }
-    const int64_t need = (a.dp.P + K2_TPB - 1) / K2_TPB;
-    const int64_t g2 = min((int64_t)a.k2_grid * per_sm, need);
-    e = launch_pdl(stage2_kernel<T, K, K2_TPB>, max((int64_t)1, g2), K2_TPB, st, a);
+    static int per_sm[2] = {0, 0};      // by mixture-stage CTA size (64, 128)
+    int &ps = per_sm[lc.k2_tpb == 128];
+    if (!ps) ps = blocks_per_sm(k2_single<T, K>(lc.k2_tpb), lc.k2_tpb);
+    const int use = lc.k2_per_sm > 0 && lc.k2_per_sm < ps ? lc.k2_per_sm : ps;
+    const int64_t need = (a.dp.P + lc.k2_tpb - 1) / lc.k2_tpb;
+    const int64_t g2 = min((int64_t)a.k2_grid * use, need);
+    e = launch_pdl(k2_single<T, K>(lc.k2_tpb), max((int64_t)1, g2), lc.k2_tpb, st, a);
     if (ev) cudaEventRecord(ev->e2, st);
     return e;
 }
 
-}  // namespace cog
-
-namespace cog {
-
 template <typename T, int K>
-cudaError_t launch_batch_t(const BatchGroupDev &g, uint32_t k1_ctas, uint32_t k2_ctas, cudaStream_t st)
+cudaError_t launch_batch_t(const BatchGroupDev &g, const LaunchCfg &lc, uint32_t k1_ctas, uint32_t k2_ctas,
+                           cudaStream_t st)
 {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
@@ -536,27 +563,19 @@ cudaError_t launch_batch_t(const BatchGroupDev &g, uint32_t k1_ctas, uint32_t k2
     cfg.numAttrs = 1;
     cfg.stream = st;
     cfg.gridDim = dim3(k1_ctas);
-    cfg.blockDim = dim3(K1_TPB);
-    cudaError_t e = cudaLaunchKernelEx(&cfg, stage01_batch_kernel<T, K1_TPB>, g);
+    cfg.blockDim = dim3(lc.k1_tpb);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k1_batch<T>(lc.k1_tpb), g);
     if (e != cudaSuccess) return e;
     cfg.gridDim = dim3(k2_ctas);
-    cfg.blockDim = dim3(K2_TPB);
-    return cudaLaunchKernelEx(&cfg, stage2_batch_kernel<T, K, K2_TPB>, g);
+    cfg.blockDim = dim3(lc.k2_tpb);
+    return cudaLaunchKernelEx(&cfg, k2_batch<T, K>(lc.k2_tpb), g);
 }
 
 template <typename T, int K>
-int k2_blocks_per_sm_t()
+int k2_blocks_per_sm_t(const LaunchCfg &lc)
 {
-    int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, stage2_batch_kernel<T, K, K2_TPB>, K2_TPB, 0) !=
-            cudaSuccess || b < 1)
-        b = 4;
-    return b;
+    const int ps = blocks_per_sm(k2_batch<T, K>(lc.k2_tpb), lc.k2_tpb);
+    return lc.k2_per_sm > 0 && lc.k2_per_sm < ps ? lc.k2_per_sm : ps;
 }
 
-}  // namespace cog
-
-namespace cog {
-inline int k1_tile_pixels_impl() { return K1_TPB * PPT; }
-inline int k2_block_threads_impl() { return K2_TPB; }
 }  // namespace cog

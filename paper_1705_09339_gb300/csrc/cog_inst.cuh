@@ -22,33 +22,33 @@ namespace cog {
     default: return cudaErrorInvalidValue; \
     }
 
-cudaError_t COG_CAT(launch_apply_, COG_SUFFIX)(int K, const ApplyArgs &a, cudaStream_t st,
+cudaError_t COG_CAT(launch_apply_, COG_SUFFIX)(int K, const ApplyArgs &a, const LaunchCfg &lc, cudaStream_t st,
                                                const ApplyEvents *ev)
 {
-#define CALL_A(k) launch_apply_t<COG_T, k>(a, st, ev)
+#define CALL_A(k) launch_apply_t<COG_T, k>(a, lc, st, ev)
     COG_KSWITCH(CALL_A)
 #undef CALL_A
 }
 
-cudaError_t COG_CAT(launch_batch_, COG_SUFFIX)(int K, const BatchGroupDev &g, uint32_t k1, uint32_t k2,
-                                               cudaStream_t st)
+cudaError_t COG_CAT(launch_batch_, COG_SUFFIX)(int K, const BatchGroupDev &g, const LaunchCfg &lc, uint32_t k1,
+                                               uint32_t k2, cudaStream_t st)
 {
-#define CALL_B(k) launch_batch_t<COG_T, k>(g, k1, k2, st)
+#define CALL_B(k) launch_batch_t<COG_T, k>(g, lc, k1, k2, st)
     COG_KSWITCH(CALL_B)
 #undef CALL_B
 }
 
-int COG_CAT(k2_blocks_per_sm_, COG_SUFFIX)(int K)
+int COG_CAT(k2_blocks_per_sm_, COG_SUFFIX)(int K, const LaunchCfg &lc)
 {
     switch (K) {
-    case 1: return k2_blocks_per_sm_t<COG_T, 1>();
-    case 2: return k2_blocks_per_sm_t<COG_T, 2>();
-    case 3: return k2_blocks_per_sm_t<COG_T, 3>();
-    case 4: return k2_blocks_per_sm_t<COG_T, 4>();
-    case 5: return k2_blocks_per_sm_t<COG_T, 5>();
-    case 6: return k2_blocks_per_sm_t<COG_T, 6>();
-    case 7: return k2_blocks_per_sm_t<COG_T, 7>();
-    default: return k2_blocks_per_sm_t<COG_T, 8>();
+    case 1: return k2_blocks_per_sm_t<COG_T, 1>(lc);
+    case 2: return k2_blocks_per_sm_t<COG_T, 2>(lc);
+    case 3: return k2_blocks_per_sm_t<COG_T, 3>(lc);
+    case 4: return k2_blocks_per_sm_t<COG_T, 4>(lc);
+    case 5: return k2_blocks_per_sm_t<COG_T, 5>(lc);
+    case 6: return k2_blocks_per_sm_t<COG_T, 6>(lc);
+    case 7: return k2_blocks_per_sm_t<COG_T, 7>(lc);
+    default: return k2_blocks_per_sm_t<COG_T, 8>(lc);
     }
 }
 

@@ -106,12 +106,14 @@ struct BatchGroupDev {
     int n;
 };
 
-cudaError_t launch_batch_group(int dtype, int K, const BatchGroupDev &g, uint32_t k1_ctas, uint32_t k2_ctas,
-                               cudaStream_t st);
+// Launch shape of the two cascade kernels.
+struct LaunchCfg {
+    int k1_tpb = 128;   // stage-0/1 CTA size: 64, 128 or 256 (4 pixels per thread)
+    int k2_tpb = 64;    // mixture-stage CTA size: 64 or 128
+    int k2_per_sm = 0;  // mixture-stage CTAs per SM (0: as many as fit)
+};
+
 cudaError_t launch_batch_advance(const BatchGroupDev &g, cudaStream_t st);
-int k1_tile_pixels();
-int k2_block_threads();
-int k2_blocks_per_sm(int dtype, int K);
 
 // Optional per-kernel timing: events recorded before the first kernel,
 // between the two kernels and after the second, on the launch stream.
