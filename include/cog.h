@@ -211,6 +211,13 @@ cog_status cog_apply_host_noalloc(cog_ctx *ctx, const uint8_t *frame_host, uint8
 typedef struct cog_batch cog_batch;
 cog_status cog_batch_create(cog_ctx *const *ctxs, int32_t n, void *cuda_stream, cog_batch **out);
 cog_status cog_batch_apply(cog_batch *batch, const uint8_t *const *frames_dev, uint8_t *const *masks_dev);
+/* As cog_batch_apply for the streams with active_host[i] != 0 only (a
+ * host array of n flags); the other streams skip the step (their buffers
+ * may be NULL, their state and frame count do not change).  The same
+ * captured graph serves every subset: the flags live in device memory.
+ * This is the step of a continuous-batching server. */
+cog_status cog_batch_apply_active(cog_batch *batch, const uint8_t *const *frames_dev, uint8_t *const *masks_dev,
+                                  const uint8_t *active_host);
 cog_status cog_batch_sync(cog_batch *batch);
 const char *cog_batch_last_error_string(cog_batch *batch);
 cog_status cog_batch_destroy(cog_batch *batch);

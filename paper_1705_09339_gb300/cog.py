@@ -85,6 +85,7 @@ def _load() -> C.CDLL:
         "cog_destroy": (C.c_int, [vp]),
         "cog_batch_create": (C.c_int, [P(vp), i32, vp, P(vp)]),
         "cog_batch_apply": (C.c_int, [vp, P(vp), P(vp)]),
+        "cog_batch_apply_active": (C.c_int, [vp, P(vp), P(vp), vp]),
         "cog_batch_sync": (C.c_int, [vp]),
         "cog_batch_last_error_string": (C.c_char_p, [vp]),
         "cog_batch_destroy": (C.c_int, [vp]),
@@ -245,6 +246,16 @@ def cog_batch_apply(b, frames, masks) -> None:
     fa = (C.c_void_p * n)(*[_ptr(f) for f in frames])
     ma = (C.c_void_p * n)(*[_ptr(m) for m in masks])
     _bcheck(lib.cog_batch_apply(b, fa, ma), b)
+
+
+def cog_batch_apply_active(b, frames, masks, active) -> None:
+    """active: sequence of n truthy flags; frames/masks of inactive streams
+    may be None."""
+    n = len(frames)
+    fa = (C.c_void_p * n)(*[_ptr(f) for f in frames])
+    ma = (C.c_void_p * n)(*[_ptr(m) for m in masks])
+    act = np.ascontiguousarray(np.asarray(active, dtype=np.uint8))
+    _bcheck(lib.cog_batch_apply_active(b, fa, ma, act.ctypes.data), b)
 
 
 def cog_batch_sync(b) -> None:

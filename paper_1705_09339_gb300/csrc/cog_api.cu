@@ -655,8 +655,10 @@ struct BatchGroupHost {
     std::vector<ApplyArgs> descs;      // host copy of the device descriptors
     BatchGroupDev dev{};
     uint32_t k1_ctas = 0, k2_ctas = 0;
-    void *dmem = nullptr;              // descs | frame_no | k1_pre | k2_pre
+    void *dmem = nullptr;              // descs | frame_no | k1_pre | k2_pre | active
     ApplyArgs *pinned = nullptr;       // upload staging
+    uint32_t *pinned_active = nullptr; // upload staging of the active flags
+    std::vector<uint32_t> active;      // host copy of the active flags
 };
 
 struct cog_batch {
@@ -692,6 +694,7 @@ static void batch_free(cog_batch *b)
     for (auto &g : b->groups) {
         if (g.dmem) cudaFree(g.dmem);
         if (g.pinned) cudaFreeHost(g.pinned);
+        if (g.pinned_active) cudaFreeHost(g.pinned_active);
     }
     for (auto s : b->aux) cudaStreamDestroy(s);
     for (auto e : b->fork) cudaEventDestroy(e);
@@ -764,15 +767,18 @@ cog_status cog_batch_create(cog_ctx *const *ctxs, int32_t n, void *cuda_stream, 
         }
         g.k1_ctas = k1[m];
         g.k2_ctas = k2[m];
-        const size_t bytes = sizeof(ApplyArgs) * m + 4 * (size_t)m + 8 * (size_t)(m + 1) + 64;
+        const size_t bytes = sizeof(ApplyArgs) * m + 4 * (size_t)m + 8 * (size_t)(m + 1) + 4 * (size_t)m + 64;
         if ((e = cudaMalloc(&g.dmem, bytes)) != cudaSuccess) break;
         if ((e = cudaMallocHost((void **)&g.pinned, sizeof(ApplyArgs) * m)) != cudaSuccess) break;
+        if ((e = cudaMallocHost((void **)&g.pinned_active, 4 * (size_t)m)) != cudaSuccess) break;
         uint8_t *d = (uint8_t *)g.dmem;
         g.dev.descs = (ApplyArgs *)d;
         g.dev.frame_no = (uint32_t *)(d + sizeof(ApplyArgs) * m);
         g.dev.k1_pre = (const uint32_t *)(d + sizeof(ApplyArgs) * m + 4 * m);
         g.dev.k2_pre = g.dev.k1_pre + (m + 1);
+        g.dev.active = g.dev.k2_pre + (m + 1);
         g.dev.n = m;
+        g.active.assign(m, 1u);
         std::vector<uint32_t> fno(m);
         for (int j = 0; j < m; j++) fno[j] = (uint32_t)ctxs[g.members[j]]->frame_no;
         e = cudaMemcpyAsync(g.dev.frame_no, fno.data(), 4 * m, cudaMemcpyHostToDevice, b->stream);
@@ -780,6 +786,8 @@ cog_status cog_batch_create(cog_ctx *const *ctxs, int32_t n, void *cuda_stream, 
             e = cudaMemcpyAsync((void *)g.dev.k1_pre, k1.data(), 4 * (m + 1), cudaMemcpyHostToDevice, b->stream);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync((void *)g.dev.k2_pre, k2.data(), 4 * (m + 1), cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync((void *)g.dev.active, g.active.data(), 4 * m, cudaMemcpyHostToDevice, b->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     }
     for (size_t g = 1; g < b->groups.size() && e == cudaSuccess; g++) {
@@ -835,21 +843,26 @@ static cudaError_t batch_capture(cog_batch *b)
     return e;
 }
 
-cog_status cog_batch_apply(cog_batch *b, const uint8_t *const *frames_dev, uint8_t *const *masks_dev)
+static cog_status batch_apply(cog_batch *b, const uint8_t *const *frames_dev, uint8_t *const *masks_dev,
+                              const uint8_t *active_host)
 {
     if (!b) return COG_ERR_INVALID_ARG;
     if (b->sticky != COG_OK) return b->sticky;
     if (!frames_dev || !masks_dev) return batch_err(b, COG_ERR_INVALID_ARG, "frames_dev and masks_dev are required");
     const int n = (int)b->ctxs.size();
     for (int i = 0; i < n; i++) {
-        if (!frames_dev[i] || !masks_dev[i]) return batch_err(b, COG_ERR_INVALID_ARG, "stream %d: NULL buffer", i);
+        const bool on = !active_host || active_host[i];
+        if (on && (!frames_dev[i] || !masks_dev[i])) return batch_err(b, COG_ERR_INVALID_ARG, "stream %d: NULL buffer", i);
         if (b->ctxs[i]->sticky != COG_OK) return batch_err(b, b->ctxs[i]->sticky, "stream %d: sticky error", i);
     }
     cudaError_t e = cudaSuccess;
     for (auto &g : b->groups) {
-        bool dirty = false;
+        bool dirty = false, adirty = false;
         for (size_t j = 0; j < g.members.size(); j++) {
             const int i = g.members[j];
+            const uint32_t on = (!active_host || active_host[i]) ? 1u : 0u;
+            if (on != g.active[j]) { g.active[j] = on; adirty = true; }
+            if (!on) continue;
             if (b->frames[i] == frames_dev[i] && b->masks[i] == masks_dev[i]) continue;
             ApplyArgs &a = g.descs[j];
             a.frame = frames_dev[i];
@@ -861,16 +874,24 @@ cog_status cog_batch_apply(cog_batch *b, const uint8_t *const *frames_dev, uint8
             b->masks[i] = masks_dev[i];
             dirty = true;
         }
-        if (!dirty) continue;
+        if (!dirty && !adirty) continue;
         // the device keeps frame_no current; the host copy matches it at
         // this point in stream order
         for (size_t j = 0; j < g.members.size(); j++)
             g.descs[j].frame_no = (uint32_t)(b->ctxs[g.members[j]]->frame_no % 3);
         if ((e = cudaEventSynchronize(b->uploaded)) != cudaSuccess) break;
-        memcpy(g.pinned, g.descs.data(), sizeof(ApplyArgs) * g.descs.size());
-        if ((e = cudaMemcpyAsync(g.dev.descs, g.pinned, sizeof(ApplyArgs) * g.descs.size(), cudaMemcpyHostToDevice,
-                                 b->stream)) != cudaSuccess)
-            break;
+        if (dirty) {
+            memcpy(g.pinned, g.descs.data(), sizeof(ApplyArgs) * g.descs.size());
+            if ((e = cudaMemcpyAsync(g.dev.descs, g.pinned, sizeof(ApplyArgs) * g.descs.size(),
+                                     cudaMemcpyHostToDevice, b->stream)) != cudaSuccess)
+                break;
+        }
+        if (adirty) {
+            memcpy(g.pinned_active, g.active.data(), 4 * g.active.size());
+            if ((e = cudaMemcpyAsync((void *)g.dev.active, g.pinned_active, 4 * g.active.size(),
+                                     cudaMemcpyHostToDevice, b->stream)) != cudaSuccess)
+                break;
+        }
         if ((e = cudaEventRecord(b->uploaded, b->stream)) != cudaSuccess) break;
     }
     if (e == cudaSuccess && !b->exec) e = batch_capture(b);
@@ -879,8 +900,21 @@ cog_status cog_batch_apply(cog_batch *b, const uint8_t *const *frames_dev, uint8
         cudaGetLastError();
         return batch_err(b, COG_ERR_CUDA, "cog_batch_apply: %s", cudaGetErrorString(e));
     }
-    for (cog_ctx *c : b->ctxs) c->frame_no++;
+    for (int i = 0; i < n; i++)
+        if (!active_host || active_host[i]) b->ctxs[i]->frame_no++;
     return COG_OK;
+}
+
+cog_status cog_batch_apply(cog_batch *b, const uint8_t *const *frames_dev, uint8_t *const *masks_dev)
+{
+    return batch_apply(b, frames_dev, masks_dev, nullptr);
+}
+
+cog_status cog_batch_apply_active(cog_batch *b, const uint8_t *const *frames_dev, uint8_t *const *masks_dev,
+                                  const uint8_t *active_host)
+{
+    if (!active_host) return batch_err(b, COG_ERR_INVALID_ARG, "active_host is required");
+    return batch_apply(b, frames_dev, masks_dev, active_host);
 }
 
 cog_status cog_batch_sync(cog_batch *b)

@@ -469,6 +469,7 @@ __global__ void __launch_bounds__(TPB, 1280 / TPB) stage01_batch_kernel(const Ba
     grid_launch_dependents();
     grid_wait_prior();
     const int s = batch_stream(G.k1_pre, G.n, blockIdx.x);
+    if (!G.active[s]) return;      // no frame for this stream in this step
     k1_cta<T, TPB>(G.descs[s], blockIdx.x - G.k1_pre[s]);
 }
 
@@ -478,6 +479,7 @@ __global__ void __launch_bounds__(TPB) stage2_batch_kernel(const BatchGroupDev G
     grid_launch_dependents();
     grid_wait_prior();
     const int s = batch_stream(G.k2_pre, G.n, blockIdx.x);
+    if (!G.active[s]) return;
     k2_cta<T, K, TPB>(G.descs[s], blockIdx.x - G.k2_pre[s], G.k2_pre[s + 1] - G.k2_pre[s]);
 }
 

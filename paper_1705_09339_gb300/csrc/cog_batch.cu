@@ -9,7 +9,7 @@ __global__ void batch_advance_kernel(const BatchGroupDev g)
 {
     asm volatile("griddepcontrol.wait;" ::: "memory");   // after the mixture stage
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s < g.n) {
+    if (s < g.n && g.active[s]) {
         const uint32_t f = g.frame_no[s] + 1;
         g.frame_no[s] = f;
         g.descs[s].frame_no = f % 3;

@@ -103,6 +103,7 @@ struct BatchGroupDev {
     uint32_t *frame_no;      // [n] frames applied (full count)
     const uint32_t *k1_pre;  // [n + 1] prefix of first-kernel CTAs per stream
     const uint32_t *k2_pre;  // [n + 1] prefix of mixture-stage CTAs per stream
+    const uint32_t *active;  // [n] 1 = the stream has a frame this step
     int n;
 };
 

@@ -1,0 +1,75 @@
+"""The continuous-batching server: every camera's masks in the mix equal
+what the same camera gives alone; admission refuses cameras that do not fit
+in free device memory."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+
+@pytest.fixture(scope="module")
+def cog():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1705_09339_gb300 import cog
+    return cog
+
+
+CAMS = [(160, 120, 3, "f16"), (320, 240, 5, "f16"), (640, 480, 5, "f16"), (97, 61, 3, "f32"), (200, 150, 5, "bf16")]
+
+
+def test_each_camera_same_alone_and_in_the_mix(cog):
+    import random
+    import time
+
+    from cogsynth import Scene
+    from cogsynth.gpu import GpuScene
+    from paper_1705_09339_gb300.serve import FrameServer
+    NT, NF = 30, 14
+    srv = FrameServer(reserve_bytes=1 << 30, keep_masks=True)
+    data = []
+    for i, (w, h, k, dt) in enumerate(CAMS):
+        sc = Scene(w, h, 900 + i, kind="dynamic", n_train=NT, fg_frac=0.05, switch_at=4)
+        gs = GpuScene(sc)
+        tr = gs.render(0, NT)
+        te = gs.render(NT, NF)
+        cam = srv.admit(w, h, k, dt, tr)
+        assert cam is not None
+        data.append((cam, tr, [te[j].cpu().pin_memory() for j in range(NF)]))
+    srv.start()
+    # frames of all cameras arrive interleaved at random moments
+    order = [(i, j) for i in range(len(CAMS)) for j in range(NF)]
+    order.sort(key=lambda x: (x[1] + random.Random(x[0] * 100 + x[1]).random(), x[0]))
+    for i, j in order:
+        srv.submit(data[i][0], data[i][2][j])
+        if j % 3 == 0:
+            time.sleep(0.001)
+    stats = srv.stop()
+    assert stats["frames"] == len(CAMS) * NF and stats["latency_ms"]["p99"] > 0
+    for i, (w, h, k, dt) in enumerate(CAMS):
+        cam, tr, frames = data[i]
+        got = sorted(srv.results[cam.id], key=lambda x: x[0])
+        assert [s for s, _ in got] == list(range(NF))
+        p = cog.cog_default_params(w, h, k, state_dtype=dt)
+        c = cog.cog_create(p, torch.cuda.current_stream().cuda_stream)
+        cog.cog_train_prior(c, tr, NT)
+        m = torch.empty((h, w), dtype=torch.uint8, device="cuda")
+        for j in range(NF):
+            cog.cog_apply(c, frames[j].cuda(), m)
+            assert np.array_equal(m.cpu().numpy(), got[j][1]), (i, j)
+        cog.cog_destroy(c)
+    srv.close()
+
+
+def test_admission_by_free_memory(cog):
+    from paper_1705_09339_gb300.serve import FrameServer
+    free, total = torch.cuda.mem_get_info()
+    srv = FrameServer(reserve_bytes=free)          # nothing fits above this reserve
+    tr = torch.zeros((2, 48, 64, 3), dtype=torch.uint8, device="cuda")
+    assert srv.admit(64, 48, 3, "f16", tr) is None
+    assert len(srv.refused) == 1
+    srv.close()
