@@ -40,6 +40,29 @@ N_TEST_MAX = 2000
 FALLBACK_HBM = 6800.0
 
 
+def stream_seed(base: int, rank: int) -> int:
+    """Each rank owns its own camera stream (weak scaling, no exchange)."""
+    return base + rank
+
+
+def max_over_ranks(values, world: int, device=None):
+    """Max of per-rank timings (the slowest rank defines the job's time).
+    The only collective the benchmark uses; it carries no pixel data."""
+    if world <= 1:
+        return list(values)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_mpixel_per_s(pixels_per_step: int, steps: int, ms_max: float, world: int) -> float:
+    """Whole-job throughput: every rank processed its own stream's pixels in
+    at most ms_max milliseconds."""
+    return world * pixels_per_step * steps / (ms_max / 1e3) / 1e6
+
+
 def rank_info():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
             int(os.environ.get("WORLD_SIZE", 1)))
@@ -169,7 +192,7 @@ def run_ours(args, rank, local_rank, world):
         cog.cog_set_l2_fetch_bytes(args.l2_fetch)
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
-    wl = workload("hd_dynamic", fg_frac=args.fg, seed=3 + rank)
+    wl = workload("hd_dynamic", fg_frac=args.fg, seed=stream_seed(3, rank))
     sc = wl["scene"]
     P = sc.P
     n_test = args.warmup + 2 * args.steps
@@ -242,10 +265,7 @@ def run_ours(args, rank, local_rank, world):
               n_gmm=tot1["n_gmm"] - tot0["n_gmm"], frames=args.steps)
     st_prof = dict(n_stage=[b - a for a, b in zip(tot1["n_stage"], tot2["n_stage"])],
                    n_gmm=tot2["n_gmm"] - tot1["n_gmm"], frames=args.steps)
-    if world > 1:
-        t = torch.tensor([ms_c, ms_g], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_c, ms_g = t.tolist()
+    ms_c, ms_g = max_over_ranks([ms_c, ms_g], world, dev)
 
     # end to end through the C ABI with host buffers (pinned)
     n_e2e = min(args.steps, 100)
@@ -265,17 +285,14 @@ def run_ours(args, rank, local_rank, world):
     for i in range(n_e2e):
         cog.cog_apply_host(ctx_e, hf[i], hm[i])
     t_e2e = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = t.item()
+    t_e2e = max_over_ranks([t_e2e], world, dev)[0]
     cog.cog_destroy(ctx_e)
 
     result = None
     if rank == 0:
         hbm, hbm_src = peaks()
-        value = world * P * args.steps / (ms_c / 1e3) / 1e6
-        value_g = world * P * args.steps / (ms_g / 1e3) / 1e6
+        value = job_mpixel_per_s(P, args.steps, ms_c, world)
+        value_g = job_mpixel_per_s(P, args.steps, ms_g, world)
         bytes_c = sum(cog_bytes(st, P, 2, K_))
         b1, b2 = cog_bytes(st_prof, P, 2, K_)
         bytes_g = plain_bytes(args.steps, P, 2, K_)
@@ -421,10 +438,7 @@ def run_batch(args, rank, local_rank, world):
         cog.cog_batch_sync(b)
     ms = sum(a.elapsed_time(e) for a, e in ev)
     ms_g = sum(a.elapsed_time(e) for a, e in evg)
-    if world > 1:
-        t = torch.tensor([ms, ms_g], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_g = t.tolist()
+    ms, ms_g = max_over_ranks([ms, ms_g], world, dev)
     tot1 = [cog.cog_read_stats(c)[1] for c in ctxs]
     bytes_c = bytes_g = 0
     occ = np.zeros(5)
