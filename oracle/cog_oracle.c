@@ -44,6 +44,7 @@ static int check_params(const orc_params *pr)
     if (pr->K < 1 || pr->K > KMAX) return -1;
     if (!(pr->var_min > 0.0) || pr->var_max < pr->var_min) return -1;
     if (pr->kde_bw < 1 || pr->kde_bw > 32) return -1;
+    if ((pr->flags & ORC_SAMPLE) && pr->skip_period < 1) return -1;
     return 0;
 }
 
@@ -132,7 +133,7 @@ typedef struct {
 } px_out;
 
 static px_out cascade_pixel(const orc_params *pr, orc_state *s, int64_t p,
-                            const uint8_t *I, int illum_flag)
+                            const uint8_t *I, int illum_flag, int64_t n)
 {
     const int K = pr->K;
     const double lam2 = pr->lambda * pr->lambda;
@@ -152,6 +153,18 @@ static px_out cascade_pixel(const orc_params *pr, orc_state *s, int64_t p,
     const double a_eff = pr->alpha * (1.5 - Cm);
     const int halt = (fl & ORC_CONF) && Cm >= pr->c_halt;
     if ((fl & ORC_CONF) && near_rel(Cm, pr->c_halt)) o.near |= ORC_NEAR_HALT;
+
+    /* Confidence-based temporal sampling (Sec. 2, "Confidence based temporal
+     * sampling"): a pixel whose confidence has saturated is looked at only
+     * every skip_period frames, in 64-pixel blocks with staggered phases;
+     * in between it keeps its label and nothing about it changes. */
+    if ((fl & ORC_SAMPLE) && (fl & ORC_CONF)) {
+        if (near_rel(Cm, pr->c_skip)) o.near |= ORC_NEAR_SKIP;
+        if (Cm >= pr->c_skip && (n + (p >> 6)) % pr->skip_period != 0) {
+            o.stage = ORC_ST_SKIP;
+            return o;
+        }
+    }
 
     int D = 0;
     for (int c = 0; c < 3; c++) {
@@ -332,25 +345,27 @@ int orc_apply(const orc_params *pr, orc_state *s, const uint8_t *frame,
     /* the counter of the previous frame decides this frame's flag */
     const int flag = (pr->flags & ORC_ILLUM) &&
                      s->illum[0] * 1000 > (int64_t)pr->illum_permille * P;
+    const int64_t n = s->illum[1];
     int64_t n_gmm = 0;
-    int64_t n_st[5] = {0, 0, 0, 0, 0};
-    int64_t n0 = 0, n1 = 0, n2 = 0, n3 = 0, n4 = 0;
+    int64_t n_st[6] = {0, 0, 0, 0, 0, 0};
+    int64_t n0 = 0, n1 = 0, n2 = 0, n3 = 0, n4 = 0, n5 = 0;
 #ifdef _OPENMP
-#pragma omp parallel for schedule(static) reduction(+ : n_gmm, n0, n1, n2, n3, n4)
+#pragma omp parallel for schedule(static) reduction(+ : n_gmm, n0, n1, n2, n3, n4, n5)
 #endif
     for (int64_t p = 0; p < P; p++) {
-        px_out o = cascade_pixel(pr, s, p, frame + p * 3, flag);
+        px_out o = cascade_pixel(pr, s, p, frame + p * 3, flag, n);
         n_gmm += o.reached_gmm;
         n0 += o.stage == 0; n1 += o.stage == 1; n2 += o.stage == 2;
-        n3 += o.stage == 3; n4 += o.stage == 4;
+        n3 += o.stage == 3; n4 += o.stage == 4; n5 += o.stage == 5;
         mask[p] = s->label[p] ? 255 : 0;
         if (stage) stage[p] = (uint8_t)o.stage;
         if (near) near[p] = o.near;
     }
-    n_st[0] = n0; n_st[1] = n1; n_st[2] = n2; n_st[3] = n3; n_st[4] = n4;
+    n_st[0] = n0; n_st[1] = n1; n_st[2] = n2; n_st[3] = n3; n_st[4] = n4; n_st[5] = n5;
     s->illum[0] = n_gmm;
+    s->illum[1] = n + 1;
     if (st) {
-        for (int i = 0; i < 5; i++) st->n_stage[i] = n_st[i];
+        for (int i = 0; i < 6; i++) st->n_stage[i] = n_st[i];
         st->n_gmm = n_gmm;
         st->illum_flag = flag;
         st->pad = 0;
@@ -396,6 +411,7 @@ int orc_train(const orc_params *pr, const uint8_t *frames, int N, orc_state *s)
         s->label[p] = 0;
     }
     s->illum[0] = 0;
+    s->illum[1] = 0;
     /* frames 1..N-1 run the cascade with every rejection stage and every
      * modulation off, i.e. the plain mixture at rate alpha */
     orc_params pw = *pr;
@@ -424,6 +440,7 @@ int orc_train(const orc_params *pr, const uint8_t *frames, int N, orc_state *s)
         s->conf[p] = 0.5;
     }
     s->illum[0] = 0;
+    s->illum[1] = 0;
     return 0;
 }
 

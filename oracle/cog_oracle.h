@@ -45,6 +45,7 @@ extern "C" {
 #define ORC_RGA   2u   /* stage 1: running Gaussian average                             */
 #define ORC_CONF  4u   /* confidence-driven rates, thresholds and halting                */
 #define ORC_ILLUM 8u   /* abrupt-illumination counter and response                       */
+#define ORC_SAMPLE 16u /* confidence-based temporal sampling                             */
 
 /* near-threshold record bits (one byte per pixel and frame) */
 #define ORC_NEAR_FD    1u  /* D vs tau_fd (0.5 + C)            */
@@ -53,6 +54,7 @@ extern "C" {
 #define ORC_NEAR_BGSET 8u  /* weight ranked before match vs T  */
 #define ORC_NEAR_RANK 16u  /* two adjacent rank keys nearly tie */
 #define ORC_NEAR_HALT 32u  /* C vs c_halt                      */
+#define ORC_NEAR_SKIP 64u  /* C vs c_skip                      */
 
 /* stage codes written to the stage map */
 #define ORC_ST_FD     0
@@ -60,6 +62,7 @@ extern "C" {
 #define ORC_ST_GMM_BG 2
 #define ORC_ST_FG     3
 #define ORC_ST_ILLUM  4
+#define ORC_ST_SKIP   5   /* not sampled this frame: label carried       */
 
 typedef struct {
     int width, height;  /* pixels are numbered p = y*width + x          */
@@ -73,10 +76,13 @@ typedef struct {
     double eta;         /* confidence smoothing rate                    */
     double c_halt;      /* confidence at which RGA updates stop         */
     double w_illum;     /* weight given on an illumination change       */
+    double c_skip;      /* sampling: confidence at which a pixel is only
+                           processed every skip_period frames           */
     int q_null;         /* prior nullified below this level (of 255)    */
     int kde_bw;         /* kernel bandwidth in grey levels              */
     int r1, r2;         /* residue class bounds                         */
     int illum_permille; /* illumination threshold, per mille of pixels  */
+    int skip_period;    /* sampling period S (>= 1)                     */
     unsigned flags;     /* ORC_* switches                               */
 } orc_params;
 
@@ -93,12 +99,13 @@ typedef struct {
     uint8_t *kde;    /* [P][3][256]  peak-normalised prior q_c[v]       */
     uint8_t *qa;     /* [P]          static-class weight, of 255        */
     uint8_t *qb;     /* [P]          dynamic-class weight, of 255       */
-    int64_t *illum;  /* [1]          pixels that reached the GMM stage in
-                                     the previous frame                 */
+    int64_t *illum;  /* [2]          [0]: pixels that reached the GMM stage in
+                                     the previous frame; [1]: frames applied
+                                     since training                     */
 } orc_state;
 
 typedef struct {
-    int64_t n_stage[5];   /* pixels per ORC_ST_* code                */
+    int64_t n_stage[6];   /* pixels per ORC_ST_* code                */
     int64_t n_gmm;        /* pixels that reached the GMM stage       */
     int32_t illum_flag;   /* flag used for this frame                */
     int32_t pad;

@@ -16,8 +16,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "cog_oracle.c")
 _LIB = os.path.join(_HERE, "libcog_oracle.so")
 
-ORC_FD, ORC_RGA, ORC_CONF, ORC_ILLUM = 1, 2, 4, 8
-NEAR_BITS = {"fd": 1, "rga": 2, "match": 4, "bgset": 8, "rank": 16, "halt": 32}
+ORC_FD, ORC_RGA, ORC_CONF, ORC_ILLUM, ORC_SAMPLE = 1, 2, 4, 8, 16
+NEAR_BITS = {"fd": 1, "rga": 2, "match": 4, "bgset": 8, "rank": 16, "halt": 32, "skip": 64}
 
 _lock = threading.Lock()
 _lib = None
@@ -46,9 +46,9 @@ class _Params(C.Structure):
         ("alpha", C.c_double), ("lambda_", C.c_double), ("T_bg", C.c_double),
         ("w_init", C.c_double), ("var_init", C.c_double), ("var_min", C.c_double),
         ("var_max", C.c_double), ("tau_fd", C.c_double), ("eta", C.c_double),
-        ("c_halt", C.c_double), ("w_illum", C.c_double),
+        ("c_halt", C.c_double), ("w_illum", C.c_double), ("c_skip", C.c_double),
         ("q_null", C.c_int), ("kde_bw", C.c_int), ("r1", C.c_int), ("r2", C.c_int),
-        ("illum_permille", C.c_int), ("flags", C.c_uint),
+        ("illum_permille", C.c_int), ("skip_period", C.c_int), ("flags", C.c_uint),
     ]
 
 
@@ -59,7 +59,7 @@ class _State(C.Structure):
 
 
 class _Stats(C.Structure):
-    _fields_ = [("n_stage", C.c_int64 * 5), ("n_gmm", C.c_int64),
+    _fields_ = [("n_stage", C.c_int64 * 6), ("n_gmm", C.c_int64),
                 ("illum_flag", C.c_int32), ("pad", C.c_int32)]
 
 
@@ -92,15 +92,18 @@ def default_params(width: int, height: int, K: int = 3) -> dict:
     none; these are the readings recorded in the design notes)."""
     return dict(width=width, height=height, K=K, alpha=0.01, lambda_=2.5, T_bg=0.7,
                 w_init=0.05, var_init=225.0, var_min=4.0, var_max=900.0, tau_fd=8.0,
-                eta=0.125, c_halt=0.9, w_illum=0.75, q_null=13, kde_bw=4, r1=10, r2=30,
-                illum_permille=700, flags=ORC_FD | ORC_RGA | ORC_CONF | ORC_ILLUM)
+                eta=0.125, c_halt=0.9, w_illum=0.75, c_skip=0.95, q_null=13, kde_bw=4, r1=10, r2=30,
+                illum_permille=700, skip_period=4, flags=ORC_FD | ORC_RGA | ORC_CONF | ORC_ILLUM)
+
+
+_OPTIONAL = {"c_skip": 0.95, "skip_period": 4}
 
 
 def _params(p: dict) -> _Params:
     q = _Params()
     for name, _ in _Params._fields_:
         key = "lambda" if name == "lambda_" and "lambda" in p else name
-        setattr(q, name, p[key])
+        setattr(q, name, p[key] if key in p else _OPTIONAL[key])
     return q
 
 
@@ -128,7 +131,7 @@ class OracleState:
         self.kde = np.zeros((P, 3, 256), np.uint8)
         self.qa = np.zeros(P, np.uint8)
         self.qb = np.zeros(P, np.uint8)
-        self.illum = np.zeros(1, np.int64)
+        self.illum = np.zeros(2, np.int64)
 
     def _c(self) -> _State:
         s = _State()

@@ -408,3 +408,68 @@ def test_near_threshold_record():
     _hand_state(o)
     _, _, near, _ = o.apply(np.array([[104, 100, 98]], np.uint8))
     assert near[0] == 0
+
+
+# ------------------------------------------------------ temporal sampling
+from oracle import ORC_SAMPLE  # noqa: E402
+
+
+def test_sampling_saturated_pixel_follows_its_block_phase():
+    # Sec. 2 "Confidence based temporal sampling": once C >= c_skip a pixel
+    # is looked at only on frames n with (n + p/64) % S == 0; before that it
+    # is processed on every frame.  Two blocks (x = 0 and x = 64) have phases
+    # one frame apart.
+    S = 4
+    p = default_params(128, 1, 3)
+    p.update(flags=ORC_FD | ORC_CONF | ORC_SAMPLE, c_skip=0.95, skip_period=S)
+    o = Oracle(p)
+    o.train(np.full((10, 128, 3), 90, np.uint8))
+    seen_skip = False
+    for n in range(60):
+        before = o.state.copy()
+        _, st, _, stats = o.apply(np.full((128, 3), 90, np.uint8))
+        for x, blk in ((0, 0), (64, 1)):
+            Cm = before.conf[x]
+            if Cm >= 0.95 and (n + blk) % S != 0:
+                assert st[x] == 5
+                seen_skip = True
+                # skipped: every piece of state is unchanged
+                assert o.state.conf[x] == Cm and o.state.label[x] == before.label[x]
+                assert np.array_equal(o.state.prev[x], before.prev[x])
+            else:
+                assert st[x] == 0
+        assert stats["n_stage"][5] == int((st == 5).sum())
+    assert seen_skip
+    # every pixel of a block shares its phase
+    assert np.array_equal(st[:64], np.full(64, st[0])) and np.array_equal(st[64:], np.full(64, st[64]))
+
+
+def test_sampling_delays_detection_by_less_than_one_period():
+    S = 4
+    p = default_params(1, 1, 3)
+    p.update(flags=ORC_FD | ORC_RGA | ORC_CONF | ORC_SAMPLE, c_skip=0.95, skip_period=S)
+    o = Oracle(p)
+    o.train(np.full((10, 1, 3), 90, np.uint8))
+    n = 0
+    while not (o.state.conf[0] >= 0.95 and (n + 1) % S == 1):   # saturated, next frame off phase
+        o.apply(np.full((1, 3), 90, np.uint8))
+        n += 1
+    # an object arrives on an off-phase frame: the label is carried until the
+    # block's next phase frame, where the object is detected
+    labels = []
+    for k in range(S):
+        m, st, _, _ = o.apply(np.full((1, 3), 200, np.uint8))
+        labels.append((int(m[0]), int(st[0]), (n + k) % S))
+    first = next(i for i, (lab, _, _) in enumerate(labels) if lab == 255)
+    assert labels[first][2] == 0 and first <= S - 1
+    assert all(s == 5 for _, s, _ in labels[:first])
+
+
+def test_sampling_needs_confidence_below_threshold_processed_every_frame():
+    p = default_params(1, 1, 3)
+    p.update(flags=ORC_FD | ORC_CONF | ORC_SAMPLE, c_skip=0.999, skip_period=4)
+    o = Oracle(p)
+    o.train(np.full((10, 1, 3), 90, np.uint8))
+    for n in range(20):           # C stays below 0.999 for these frames
+        _, st, _, _ = o.apply(np.full((1, 3), 90, np.uint8))
+        assert st[0] == 0
