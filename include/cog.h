@@ -53,7 +53,8 @@ typedef enum { COG_F32 = 0, COG_F16 = 1, COG_BF16 = 2 } cog_dtype;
 #define COG_RGA   2u  /* stage 1: running Gaussian average                              */
 #define COG_CONF  4u  /* confidence-driven learning rate, thresholds and halting        */
 #define COG_ILLUM 8u  /* abrupt-illumination counter and response                       */
-#define COG_ALL   15u
+#define COG_SAMPLE 16u /* confidence-based temporal sampling (needs COG_CONF)            */
+#define COG_ALL   15u /* the cascade: every stage and modulation, no sampling            */
 
 /* Stage codes written to a stage map (the cascade level that labelled the
  * pixel; the paper's per-level occupancy figure). */
@@ -62,6 +63,7 @@ typedef enum { COG_F32 = 0, COG_F16 = 1, COG_BF16 = 2 } cog_dtype;
 #define COG_ST_GMM_BG 2
 #define COG_ST_FG     3
 #define COG_ST_ILLUM  4
+#define COG_ST_SKIP   5   /* not sampled this frame: label carried (COG_SAMPLE) */
 
 typedef struct cog_params {
     int32_t width, height;   /* frame size in pixels, each >= 1                           */
@@ -82,12 +84,17 @@ typedef struct cog_params {
     int32_t r1, r2;          /* residue class bounds (static <= r1 < oscillating <= r2)   */
     int32_t illum_permille;  /* illumination change when > this per mille of pixels       */
     uint32_t flags;          /* COG_* switches                                            */
+    float c_skip;            /* COG_SAMPLE: pixels with C >= c_skip are looked at only    */
+                             /* every skip_period frames (Sec. 2, "Confidence based       */
+                             /* temporal sampling"), in 64-pixel blocks with staggered    */
+                             /* phases: frame n processes block b when (n + b) % S == 0   */
+    int32_t skip_period;     /* S >= 1                                                    */
 } cog_params;
 
 /* Per-frame statistics (the stage occupancy n_i of the paper's speed-up
  * model, Sec. 3.2). */
 typedef struct cog_stats {
-    int64_t n_stage[5];      /* pixels labelled at each COG_ST_* level   */
+    int64_t n_stage[6];      /* pixels labelled at each COG_ST_* level   */
     int64_t n_gmm;           /* pixels that reached the mixture stage    */
     int32_t illum_flag;      /* illumination response active this frame  */
     int32_t frame;           /* index of the frame these counts describe */

@@ -20,7 +20,7 @@ COG_OK, COG_ERR_INVALID_ARG, COG_ERR_OOM, COG_ERR_CUDA, COG_ERR_STATE, COG_ERR_T
 STATUS_NAMES = ["COG_OK", "COG_ERR_INVALID_ARG", "COG_ERR_OOM", "COG_ERR_CUDA", "COG_ERR_STATE",
                 "COG_ERR_TIMEOUT", "COG_ERR_DEVICE"]
 COG_F32, COG_F16, COG_BF16 = 0, 1, 2
-COG_FD, COG_RGA, COG_CONF, COG_ILLUM = 1, 2, 4, 8
+COG_FD, COG_RGA, COG_CONF, COG_ILLUM, COG_SAMPLE = 1, 2, 4, 8, 16
 COG_ALL = 15
 DTYPES = {"f32": COG_F32, "f16": COG_F16, "bf16": COG_BF16}
 
@@ -32,12 +32,13 @@ class cog_params(C.Structure):
         ("var_init", C.c_float), ("var_min", C.c_float), ("var_max", C.c_float), ("tau_fd", C.c_float),
         ("eta_conf", C.c_float), ("c_halt", C.c_float), ("w_illum", C.c_float),
         ("q_null", C.c_int32), ("kde_bw", C.c_int32), ("r1", C.c_int32), ("r2", C.c_int32),
-        ("illum_permille", C.c_int32), ("flags", C.c_uint32),
+        ("illum_permille", C.c_int32), ("flags", C.c_uint32), ("c_skip", C.c_float),
+        ("skip_period", C.c_int32),
     ]
 
 
 class cog_stats(C.Structure):
-    _fields_ = [("n_stage", C.c_int64 * 5), ("n_gmm", C.c_int64), ("illum_flag", C.c_int32),
+    _fields_ = [("n_stage", C.c_int64 * 6), ("n_gmm", C.c_int64), ("illum_flag", C.c_int32),
                 ("frame", C.c_int32)]
 
     def as_dict(self) -> dict:

@@ -122,7 +122,8 @@ static const char *check_params(const cog_params *p)
     if (p->kde_bw < 1 || p->kde_bw > 32) return "kde_bw must be in 1..32";
     if (p->r1 < 0 || p->r2 < p->r1) return "need 0 <= r1 <= r2";
     if (p->illum_permille < 0 || p->illum_permille > 1000) return "illum_permille must be in 0..1000";
-    if (p->flags & ~COG_ALL) return "unknown flag bits";
+    if (p->flags & ~(COG_ALL | COG_SAMPLE)) return "unknown flag bits";
+    if (p->skip_period < 1) return "skip_period must be >= 1";
     return nullptr;
 }
 
@@ -153,6 +154,8 @@ void cog_default_params(cog_params *p, int32_t width, int32_t height, int32_t K)
     p->r2 = 30;
     p->illum_permille = 700;
     p->flags = COG_ALL;
+    p->c_skip = 0.95f;
+    p->skip_period = 4;
 }
 
 cog_status cog_state_layout(const cog_params *p, cog_layout *out)
@@ -232,6 +235,8 @@ cog_status cog_create(const cog_params *p, void *cuda_stream, void *state_dev, c
     d.w_illum = p->w_illum;
     d.q_null = p->q_null;
     d.illum_permille = p->illum_permille;
+    d.c_skip = p->c_skip;
+    d.skip_period = p->skip_period;
     StatePtrs &s = c->sp;
     s.ctl = (uint32_t *)(c->state + c->L.ctl);
     s.jl = (uint32_t *)(c->state + c->L.jl);
@@ -305,10 +310,12 @@ static void frame_stats(const std::vector<uint32_t> &ctl, int64_t frame, cog_sta
     memset(st, 0, sizeof *st);
     st->frame = (int32_t)frame;
     if (frame < 0) return;
-    for (int f = 0; f < 6; f++) {
+    for (int f = 0; f < 7; f++) {
         int64_t v = 0;
         for (int s = 0; s < CTL_SLOTS; s++) v += ctl[(size_t)ctl_slot((int)(frame % 3), f, s)];
-        if (f < 5) st->n_stage[f] = v; else st->n_gmm = v;
+        if (f < 5) st->n_stage[f] = v;
+        else if (f == 5) st->n_gmm = v;
+        else st->n_stage[5] = v;
     }
 }
 
@@ -334,6 +341,7 @@ cog_status cog_apply(cog_ctx *c, const uint8_t *frame_dev, uint8_t *mask_dev, ui
     a.mask = mask_dev;
     a.stagemap = stagemap_dev;
     a.frame_no = (uint32_t)(c->frame_no % 3);
+    a.frame_idx = (uint32_t)c->frame_no;
     a.frame_al4 = ((uintptr_t)frame_dev & 3) == 0;
     a.out_al4 = ((uintptr_t)mask_dev & 3) == 0 && ((uintptr_t)stagemap_dev & 3) == 0;
     a.k2_grid = (uint32_t)c->n_sm;
@@ -488,6 +496,7 @@ cog_status cog_read_stats(cog_ctx *c, cog_stats *last, cog_stats *total)
         const uint64_t *tot = reinterpret_cast<const uint64_t *>(ctl.data() + CTL_TOT_WORD);
         for (int f = 0; f < 5; f++) total->n_stage[f] = (int64_t)tot[f] + (c->frame_no > 0 ? l.n_stage[f] : 0);
         total->n_gmm = (int64_t)tot[5] + (c->frame_no > 0 ? l.n_gmm : 0);
+        total->n_stage[5] = (int64_t)tot[6] + (c->frame_no > 0 ? l.n_stage[5] : 0);
     }
     return COG_OK;
 }
@@ -761,6 +770,7 @@ cog_status cog_batch_create(cog_ctx *const *ctxs, int32_t n, void *cuda_stream, 
             a.dp = c->dp;
             a.s = c->sp;
             a.frame_no = (uint32_t)(c->frame_no % 3);
+    a.frame_idx = (uint32_t)c->frame_no;
             a.k2_grid = (uint32_t)c->n_sm;
             a.rec_bytes = (uint32_t)c->L.rec_bytes;
             g.descs.push_back(a);
@@ -877,8 +887,10 @@ static cog_status batch_apply(cog_batch *b, const uint8_t *const *frames_dev, ui
         if (!dirty && !adirty) continue;
         // the device keeps frame_no current; the host copy matches it at
         // this point in stream order
-        for (size_t j = 0; j < g.members.size(); j++)
+        for (size_t j = 0; j < g.members.size(); j++) {
             g.descs[j].frame_no = (uint32_t)(b->ctxs[g.members[j]]->frame_no % 3);
+            g.descs[j].frame_idx = (uint32_t)b->ctxs[g.members[j]]->frame_no;
+        }
         if ((e = cudaEventSynchronize(b->uploaded)) != cudaSuccess) break;
         if (dirty) {
             memcpy(g.pinned, g.descs.data(), sizeof(ApplyArgs) * g.descs.size());

@@ -73,22 +73,35 @@ struct K1Warp {
 // n_fd / n_rga (per lane).
 template <typename T, bool FULL>
 __device__ __forceinline__ int k1_warp(const ApplyArgs &A, K1Warp &W, uint32_t wbase, int lane,
-                                       uint32_t &n_fd, uint32_t &n_rga)
+                                       uint32_t &n_fd, uint32_t &n_rga, uint32_t &n_skip)
 {
     const DevParams &dp = A.dp;
     const bool conf_on = dp.flags & COG_CONF;
     const uint32_t p0 = wbase + (uint32_t)lane * PPT;
     const int nact = FULL ? PPT : (int)min((int64_t)PPT, max((int64_t)0, dp.P - (int64_t)p0));
+    const uint32_t act_bits = (1u << nact) - 1u;
 
-    // ---- all stage-0 loads at once: previous frame + label (16 B),
-    //      confidence (8 or 16 B), frame bytes (12 B)
+    // ---- stage-0 loads: previous frame + label (16 B), confidence (8 or
+    //      16 B), frame bytes (12 B).  With temporal sampling, a 64-pixel
+    //      block off its phase reads its frame bytes only if some pixel in
+    //      the group has not saturated (Sec. 2, "Confidence based temporal
+    //      sampling"; a group of 4 never straddles two blocks).
     uint4 jl = make_uint4(0, 0, 0, 0);
     uint32_t w0 = 0, w1 = 0, w2 = 0;
     VecN<T, PPT> cv;
+    uint32_t skip = 0;
     if (FULL || nact > 0) {
         jl = *reinterpret_cast<const uint4 *>(A.s.jl + p0);
         cv.load(reinterpret_cast<const T *>(A.s.conf) + p0);
-        if (A.frame_al4 && (FULL || nact == PPT)) {
+        const bool sampling = (dp.flags & COG_SAMPLE) && conf_on;
+        if (sampling && (A.frame_idx + (p0 >> 6)) % (uint32_t)dp.skip_period != 0u) {
+#pragma unroll
+            for (int i = 0; i < PPT; i++)
+                if ((FULL || i < nact) && cv.get(i) >= dp.c_skip) skip |= 1u << i;
+        }
+        if (skip == act_bits) {
+            // every pixel of the group keeps its label this frame
+        } else if (A.frame_al4 && (FULL || nact == PPT)) {
             const uint32_t *f4 = reinterpret_cast<const uint32_t *>(A.frame + (size_t)p0 * 3);
             w0 = f4[0]; w1 = f4[1]; w2 = f4[2];
         } else {
@@ -116,7 +129,7 @@ __device__ __forceinline__ int k1_warp(const ApplyArgs &A, K1Warp &W, uint32_t w
     const bool fd_on = dp.flags & COG_FD;
 #pragma unroll
     for (int i = 0; i < PPT; i++) {
-        if (!FULL && i >= nact) continue;
+        if ((!FULL && i >= nact) || (skip >> i & 1u)) continue;
         const float Cm = conf_on ? cv.get(i) : 0.5f;
         const float tau = dp.tau_fd * (0.5f + Cm);
         const uint32_t t = tau >= 255.f ? 255u : (uint32_t)tau;      // floor, tau >= 0
@@ -203,32 +216,39 @@ __device__ __forceinline__ int k1_warp(const ApplyArgs &A, K1Warp &W, uint32_t w
 
     // ---- outputs: the previous frame becomes this frame with label 0 (the
     //      mixture stage sets its survivors' labels), the mask 0 (likewise),
-    //      the confidence of the pixels decided here
+    //      the confidence of the pixels decided here; a pixel skipped by the
+    //      temporal sampling keeps everything and shows its carried label
     if (FULL || nact > 0) {
         uint4 jn;
-        uint32_t sm = 0;
+        uint32_t sm = 0, mk = 0;
         VecN<T, PPT> cn = cv;
         bool any_c = false;
 #pragma unroll
         for (int i = 0; i < PPT; i++) {
             const bool act = FULL || i < nact;
+            const bool sk = skip >> i & 1u;
             const uint32_t r1 = (need1 >> i & 1u) ? W.resst[lane * PPT + i] : 0u;
-            n_fd += act && r1 == 0;
-            if (conf_on && act && r1 != 2) {
+            n_fd += act && !sk && r1 == 0;
+            n_skip += sk;
+            if (conf_on && act && !sk && r1 != 2) {
                 cn.set(i, r1 == 0 ? (1.f - dp.eta) * cv.get(i) + dp.eta : W.resc[lane * PPT + i]);
                 any_c = true;
             }
-            u4set(jn, i, act ? Iw[i] : u4get(jl, i));
-            sm |= (r1 == 0 ? (uint32_t)COG_ST_FD : (r1 == 1 ? (uint32_t)COG_ST_RGA : (uint32_t)COG_ST_GMM_BG)) << (8 * i);
+            u4set(jn, i, act && !sk ? Iw[i] : u4get(jl, i));
+            if (sk) mk |= ((u4get(jl, i) >> 24) ? 255u : 0u) << (8 * i);
+            sm |= (sk ? (uint32_t)COG_ST_SKIP
+                      : (r1 == 0 ? (uint32_t)COG_ST_FD : (r1 == 1 ? (uint32_t)COG_ST_RGA : (uint32_t)COG_ST_GMM_BG)))
+                  << (8 * i);
         }
-        *reinterpret_cast<uint4 *>(A.s.jl + p0) = jn;
+        if (jn.x != jl.x || jn.y != jl.y || jn.z != jl.z || jn.w != jl.w)
+            *reinterpret_cast<uint4 *>(A.s.jl + p0) = jn;
         if (any_c) cn.store(reinterpret_cast<T *>(A.s.conf) + p0);
         if ((FULL || nact == PPT) && A.out_al4) {
-            *reinterpret_cast<uint32_t *>(A.mask + p0) = 0u;
+            *reinterpret_cast<uint32_t *>(A.mask + p0) = mk;
             if (A.stagemap) *reinterpret_cast<uint32_t *>(A.stagemap + p0) = sm;
         } else {
             for (int i = 0; i < nact; i++) {
-                A.mask[p0 + i] = 0;
+                A.mask[p0 + i] = (uint8_t)(mk >> (8 * i));
                 if (A.stagemap) A.stagemap[p0 + i] = (uint8_t)(sm >> (8 * i));
             }
         }
@@ -256,28 +276,30 @@ __device__ __forceinline__ void k1_cta(const ApplyArgs &A, uint32_t cta)
         if (tid < 32) {
             unsigned long long *tot = reinterpret_cast<unsigned long long *>(ctl + CTL_TOT_WORD);
 #pragma unroll
-            for (int f = 0; f < 6; f++) {
+            for (int f = 0; f < 7; f++) {
                 const uint32_t v = __reduce_add_sync(0xffffffffu, __ldcg(ctl + ctl_slot((n + 2) % 3, f, lane)));
                 if (lane == 0) tot[f] += v;
             }
         }
     }
 
-    uint32_t n_fd = 0, n_rga = 0;
+    uint32_t n_fd = 0, n_rga = 0, n_skip = 0;
     int ne;
-    if ((int64_t)wbase + WPX <= A.dp.P) ne = k1_warp<T, true>(A, W_s[warp], wbase, lane, n_fd, n_rga);
-    else ne = k1_warp<T, false>(A, W_s[warp], wbase, lane, n_fd, n_rga);
+    if ((int64_t)wbase + WPX <= A.dp.P) ne = k1_warp<T, true>(A, W_s[warp], wbase, lane, n_fd, n_rga, n_skip);
+    else ne = k1_warp<T, false>(A, W_s[warp], wbase, lane, n_fd, n_rga, n_skip);
 
     // per-warp reservation (padded counters)
     const uint32_t gwarp = cta * NW + warp;
     const uint32_t seg = gwarp & (QSEG - 1);
     const uint32_t vfd = __reduce_add_sync(0xffffffffu, n_fd);
     const uint32_t vrga = __reduce_add_sync(0xffffffffu, n_rga);
+    const uint32_t vskip = __reduce_add_sync(0xffffffffu, n_skip);
     uint32_t base = 0;
     if (lane == 0) {
         const uint32_t slot = gwarp & (CTL_SLOTS - 1);
         if (vfd) atomicAdd(ctl + ctl_slot(n % 3, 0, slot), vfd);
         if (vrga) atomicAdd(ctl + ctl_slot(n % 3, 1, slot), vrga);
+        if (vskip) atomicAdd(ctl + ctl_slot(n % 3, 6, slot), vskip);
         if (ne) {
             atomicAdd(ctl + ctl_slot(n % 3, 5, slot), (uint32_t)ne);
             base = atomicAdd(ctl + ctl_qcnt(n % 3, seg), (uint32_t)ne);

@@ -13,6 +13,7 @@ __global__ void batch_advance_kernel(const BatchGroupDev g)
         const uint32_t f = g.frame_no[s] + 1;
         g.frame_no[s] = f;
         g.descs[s].frame_no = f % 3;
+        g.descs[s].frame_idx = f;
     }
 }
 

@@ -18,7 +18,8 @@ constexpr int KMAX = 8;
 // on one line.
 //   ctl_slot(b, f, s)  per-frame counters: 3 rotating buffers b x 8 fields f
 //              x 32 slots s; fields 0..4 = pixels labelled at each stage,
-//              5 = pixels that reached the mixture stage.  Frame n
+//              5 = pixels that reached the mixture stage, 6 = pixels skipped
+//              by the temporal sampling.  Frame n
 //              accumulates into buffer n % 3, reads buffer (n - 1) % 3 for its
 //              illumination flag, and its first kernel's block 0 clears buffer
 //              (n + 1) % 3.
@@ -55,6 +56,8 @@ struct DevParams {
     float tau_fd, eta, c_halt, w_illum;
     int q_null;
     int illum_permille;
+    float c_skip;
+    int skip_period;
 };
 
 struct StatePtrs {
@@ -89,6 +92,7 @@ struct ApplyArgs {
     uint8_t *mask;
     uint8_t *stagemap;   // may be null
     uint32_t frame_no;   // frames applied since training (mod 3)
+    uint32_t frame_idx;  // frames applied since training (sampling phase)
     uint32_t frame_al4;  // frame pointer 4-byte aligned: 32-bit frame loads
     uint32_t out_al4;    // mask (and stage map) 4-byte aligned: 32-bit stores
     uint32_t k2_grid;    // CTAs of the persistent mixture-stage kernel

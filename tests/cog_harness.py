@@ -8,9 +8,9 @@ import numpy as np
 # actually receives so the two compute with identical constants
 BASE = dict(alpha=0.01, lambda_=2.5, T_bg=0.7, w_init=0.05, var_init=225.0, var_min=4.0,
             var_max=900.0, tau_fd=8.0, eta=0.125, c_halt=0.9, w_illum=0.75, q_null=13, kde_bw=4,
-            r1=10, r2=30, illum_permille=700, flags=15)
+            r1=10, r2=30, illum_permille=700, flags=15, c_skip=0.95, skip_period=4)
 FLOATS = ("alpha", "lambda_", "T_bg", "w_init", "var_init", "var_min", "var_max", "tau_fd", "eta",
-          "c_halt", "w_illum")
+          "c_halt", "w_illum", "c_skip")
 
 
 def params(W, H, K, **over):
@@ -176,4 +176,4 @@ def set_oracle_state(o, st):
     s = o.state
     for k in ("w", "mu", "var", "rga_m", "rga_v", "conf", "label", "prev", "kde", "qa", "qb"):
         getattr(s, k)[...] = st[k]
-    s.illum[0] = 0
+    s.illum[:] = 0

@@ -137,6 +137,22 @@ def test_vga_dynamic_stream_with_light_switch():
         assert e[k] <= TOL, (k, e[k])
 
 
+def test_temporal_sampling_stream_matches_oracle():
+    # confidence-based temporal sampling on: saturated pixels are looked at
+    # every 4 frames in 64-pixel phase blocks; both sides must skip the same
+    # pixels on the same frames
+    (gm, gsm, gst, gs), (om, osm, near, ost, os_) = _stream(160, 120, 3, 200, 120, "rects", flags=31)
+    agree, unexplained, ever = compare_stream(gm, gsm, om, osm, near)
+    assert unexplained == 0
+    assert agree >= 0.9999
+    skipped = sum(s["n_stage"][5] for s in ost)
+    assert skipped > 0.2 * 160 * 120 * 120          # sampling really engages
+    assert sum(s["n_stage"][5] for s in gst) == pytest.approx(skipped, rel=1e-3)
+    e = state_errors(gs, os_, ~ever)
+    for k in ("w", "mu", "var", "rga_m", "rga_v", "conf"):
+        assert e[k] <= TOL, (k, e[k])
+
+
 # --------------------------------------------------- seeded random states
 @pytest.mark.parametrize("K", [1, 3, 5, 8])
 @pytest.mark.parametrize("flags", [15, 0, 1 | 2, 4 | 8])
