@@ -375,6 +375,11 @@ int orc_apply(const orc_params *pr, orc_state *s, const uint8_t *frame,
 
 int orc_train(const orc_params *pr, const uint8_t *frames, int N, orc_state *s)
 {
+    return orc_train_near(pr, frames, N, s, NULL);
+}
+
+int orc_train_near(const orc_params *pr, const uint8_t *frames, int N, orc_state *s, uint8_t *near)
+{
     if (check_params(pr) || !frames || !s || N < 2) return -1;
     const int64_t P = (int64_t)pr->width * pr->height;
     const int K = pr->K;
@@ -417,22 +422,33 @@ int orc_train(const orc_params *pr, const uint8_t *frames, int N, orc_state *s)
     orc_params pw = *pr;
     pw.flags = 0;
     uint8_t *mask = (uint8_t *)malloc((size_t)P);
-    if (!mask) return -1;
-    for (int t = 1; t < N; t++)
-        orc_apply(&pw, s, frames + (int64_t)t * P * 3, mask, NULL, NULL, NULL);
+    uint8_t *nf = near ? (uint8_t *)malloc((size_t)P) : NULL;
+    if (!mask || (near && !nf)) { free(mask); free(nf); return -1; }
+    if (near) memset(near, 0, (size_t)P);
+    for (int t = 1; t < N; t++) {
+        orc_apply(&pw, s, frames + (int64_t)t * P * 3, mask, NULL, nf, NULL);
+        if (near)
+            for (int64_t p = 0; p < P; p++) near[p] |= nf[p];
+    }
     free(mask);
+    free(nf);
 
     /* running average <- the top-ranked mode; C <- 0.5; the label and the
      * previous frame are those of the last training frame */
     for (int64_t p = 0; p < P; p++) {
         const double *w = s->w + p * K, *var = s->var + p * K * 3;
         int best = 0;
-        double rb = -1.0;
+        double rb = -1.0, r[KMAX];
         for (int k = 0; k < K; k++) {
             double vbar = (var[k * 3 + 0] + var[k * 3 + 1] + var[k * 3 + 2]) / 3.0;
-            double r = w[k] * w[k] / vbar;
-            if (r > rb) { rb = r; best = k; }
+            r[k] = w[k] * w[k] / vbar;
+            if (r[k] > rb) { rb = r[k]; best = k; }
         }
+        /* the top mode seeds the running average: a near-tie with another
+         * key is a near decision too */
+        if (near)
+            for (int k = 0; k < K; k++)
+                if (k != best && r[k] != rb && fabs(r[k] - rb) <= NEAR_REL * rb) near[p] |= ORC_NEAR_RANK;
         for (int c = 0; c < 3; c++) {
             s->rga_m[p * 3 + c] = s->mu[(p * K + best) * 3 + c];
             s->rga_v[p * 3 + c] = s->var[(p * K + best) * 3 + c];

@@ -119,6 +119,12 @@ int orc_kde_weights(int bw, int64_t *g, int cap);
  * mixture warm-up, running-average and confidence initialisation. */
 int orc_train(const orc_params *pr, const uint8_t *frames, int N, orc_state *s);
 
+/* orc_train that also records, per pixel, the OR of the near-threshold bits
+ * (ORC_NEAR_*) of every warm-up decision over frames 1..N-1, plus
+ * ORC_NEAR_RANK when the top-ranked mode that seeds the running average
+ * nearly ties another; near[P] may be NULL. */
+int orc_train_near(const orc_params *pr, const uint8_t *frames, int N, orc_state *s, uint8_t *near);
+
 /* One test frame through the cascade.  frame[P][3]; mask[P] (0/255);
  * stage[P] and near[P] are optional (NULL skips them). */
 int orc_apply(const orc_params *pr, orc_state *s, const uint8_t *frame,

@@ -73,6 +73,9 @@ def _load():
             lib.orc_kde_weights.restype = C.c_int
             lib.orc_train.argtypes = [C.POINTER(_Params), C.c_void_p, C.c_int, C.POINTER(_State)]
             lib.orc_train.restype = C.c_int
+            lib.orc_train_near.argtypes = [C.POINTER(_Params), C.c_void_p, C.c_int, C.POINTER(_State),
+                                           C.c_void_p]
+            lib.orc_train_near.restype = C.c_int
             lib.orc_apply.argtypes = [C.POINTER(_Params), C.POINTER(_State), C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(_Stats)]
             lib.orc_apply.restype = C.c_int
@@ -159,11 +162,16 @@ class Oracle:
         self._cp = _params(self.p)
         self.lib = _load()
 
-    def train(self, frames: np.ndarray) -> None:
+    def train(self, frames: np.ndarray, want_near: bool = False):
+        """Training over frames [N, P, 3].  With want_near, returns the OR
+        of the near-threshold bits of every warm-up decision per pixel."""
         f = np.ascontiguousarray(frames, dtype=np.uint8).reshape(-1, self.P, 3)
         s = self.state._c()
-        if self.lib.orc_train(C.byref(self._cp), f.ctypes.data, f.shape[0], C.byref(s)) != 0:
+        near = np.zeros(self.P, np.uint8) if want_near else None
+        if self.lib.orc_train_near(C.byref(self._cp), f.ctypes.data, f.shape[0], C.byref(s),
+                                   near.ctypes.data if want_near else None) != 0:
             raise ValueError("orc_train rejected its arguments")
+        return near
 
     def apply(self, frame: np.ndarray, want_stage: bool = True, want_near: bool = True):
         f = np.ascontiguousarray(frame, dtype=np.uint8).reshape(self.P, 3)

@@ -410,6 +410,23 @@ def test_near_threshold_record():
     assert near[0] == 0
 
 
+def test_training_near_record():
+    # two training frames; frame 1 differs from frame 0 by d on one channel,
+    # and component 0 starts at (I_0, v_init).  With lambda^2 v_init = 256
+    # the warm-up's match statistic is d^2 / 256: exactly 1 for d = 16 (a
+    # decision on the threshold, recorded), 0.39 for d = 10 (not recorded)
+    v = 256 / 6.25
+    o = one_pixel(var_init=v)
+    near = o.train(np.array([[[100, 100, 100]], [[116, 100, 100]]], np.uint8), want_near=True)
+    assert near[0] & 4
+    o = one_pixel(var_init=v)
+    near = o.train(np.array([[[100, 100, 100]], [[110, 100, 100]]], np.uint8), want_near=True)
+    assert near[0] == 0
+    # constant training: every decision is far from its threshold
+    o = one_pixel()
+    assert (o.train(np.full((30, 1, 3), 90, np.uint8), want_near=True) == 0).all()
+
+
 # ------------------------------------------------------ temporal sampling
 from oracle import ORC_SAMPLE  # noqa: E402
 
