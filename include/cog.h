@@ -151,10 +151,10 @@ cog_status cog_train_prior(cog_ctx *ctx, const uint8_t *frames_dev, int32_t n_fr
  * stage 0 frame difference, stage 1 running Gaussian average, stage 2 the
  * ordered Gaussians of Eq. 2 with the scene prior and the confidence of
  * Sec. 2 "Confidence Measure"; only the level that labels a pixel adapts.
- * frame_dev: height x width x 3 bytes (any alignment; 16-byte aligned
- * frames are staged by TMA bulk copies).  mask_dev: one byte per pixel
- * (255 = foreground).  stagemap_dev: NULL, or one COG_ST_* byte per pixel.
- * 8-byte aligned frames, masks and stage maps take vector accesses.
+ * frame_dev: height x width x 3 bytes (any alignment).  mask_dev: one byte
+ * per pixel (255 = foreground).  stagemap_dev: NULL, or one COG_ST_* byte
+ * per pixel.  4-byte aligned frames, masks and stage maps take 32-bit
+ * accesses.
  * stats_host: NULL, or receives this frame's counts (the call then
  * synchronises the stream).  Two kernels run per frame: stages 0 and 1 over
  * every pixel, then the mixture stage over the pixels left (compacted into
@@ -162,6 +162,36 @@ cog_status cog_train_prior(cog_ctx *ctx, const uint8_t *frames_dev, int32_t n_fr
  * COG_ERR_STATE before cog_train_prior. */
 cog_status cog_apply(cog_ctx *ctx, const uint8_t *frame_dev, uint8_t *mask_dev,
                      uint8_t *stagemap_dev, cog_stats *stats_host);
+
+/* n_frames consecutive frames through the cascade, for video that is
+ * already recorded (Sec. 2, "Cascade of Gaussians CoG", applied frame after
+ * frame; the paper has no multi-frame form: this is a scheduling of the
+ * same per-frame step).  Results -- masks, stage maps, counts, model state,
+ * the illumination flags of the counter at the end of that section -- are
+ * identical to n_frames calls of cog_apply with the same buffers.
+ * frames_dev: n_frames x height x width x 3 bytes, back to back.
+ * masks_dev: n_frames x height x width bytes; stagemaps_dev: NULL or the
+ * same size.  Any alignment; 4-byte aligned buffers with height x width a
+ * multiple of 4 take 32-bit accesses.  stats_host: NULL, or n_frames
+ * entries, one per frame (the call then synchronises the stream).
+ * Frames go in launches of up to 32 frames: one cooperative launch keeps
+ * every pixel's stage-0/1 state on chip across its frames.  The launch
+ * assumes no frame after its first is flagged as an illumination change,
+ * checks that against the counts of the whole frame, and if it was wrong
+ * undoes the launch's state changes and runs again with the flag fixed
+ * (at most 33 runs; one when no frame is flagged).  The first call
+ * allocates the context's clip scratch: counters plus an undo log of about
+ * 30 + the mixture record's bytes per pixel.  Stream-ordered like
+ * cog_apply; a grid-wide wait that gives up after 2 s sets the device
+ * error word (COG_ERR_DEVICE from the next synchronising call).
+ * COG_ERR_STATE before cog_train_prior; COG_ERR_OOM if the scratch cannot
+ * be allocated. */
+cog_status cog_apply_clip(cog_ctx *ctx, const uint8_t *frames_dev, int32_t n_frames, uint8_t *masks_dev,
+                          uint8_t *stagemaps_dev, cog_stats *stats_host);
+
+/* Runs the last launch of cog_apply_clip needed (1 = no illumination flag
+ * was mispredicted; 0 before any clip).  Synchronises the stream. */
+cog_status cog_clip_runs(cog_ctx *ctx, int32_t *runs);
 
 /* The comparison baseline: one frame of the plain Stauffer-Grimson mixture
  * (Eq. 2 at rate alpha, no cascade, no prior, no confidence) on this

@@ -70,6 +70,8 @@ def _load() -> C.CDLL:
         "cog_create": (C.c_int, [P(cog_params), vp, vp, P(vp)]),
         "cog_train_prior": (C.c_int, [vp, vp, i32]),
         "cog_apply": (C.c_int, [vp, vp, vp, vp, P(cog_stats)]),
+        "cog_apply_clip": (C.c_int, [vp, vp, i32, vp, vp, P(cog_stats)]),
+        "cog_clip_runs": (C.c_int, [vp, P(i32)]),
         "cog_apply_plain_gmm": (C.c_int, [vp, vp, vp]),
         "cog_apply_host": (C.c_int, [vp, vp, vp]),
         "cog_apply_host_noalloc": (C.c_int, [vp, vp, vp]),
@@ -153,6 +155,21 @@ def cog_apply(ctx, frame, mask, stagemap=None, want_stats: bool = False):
     st = cog_stats() if want_stats else None
     _check(lib.cog_apply(ctx, _ptr(frame), _ptr(mask), _ptr(stagemap), C.byref(st) if st else None), ctx)
     return st.as_dict() if st else None
+
+
+def cog_apply_clip(ctx, frames, n_frames: int, masks, stagemaps=None, want_stats: bool = False):
+    """n_frames consecutive frames ([n, H, W, 3] bytes) through the cascade;
+    identical to n_frames cog_apply calls.  Returns per-frame stats dicts
+    when asked."""
+    st = (cog_stats * n_frames)() if want_stats else None
+    _check(lib.cog_apply_clip(ctx, _ptr(frames), int(n_frames), _ptr(masks), _ptr(stagemaps), st), ctx)
+    return [s.as_dict() for s in st] if st is not None else None
+
+
+def cog_clip_runs(ctx) -> int:
+    r = C.c_int32(0)
+    _check(lib.cog_clip_runs(ctx, C.byref(r)), ctx)
+    return r.value
 
 
 def cog_apply_plain_gmm(ctx, frame, mask) -> None:

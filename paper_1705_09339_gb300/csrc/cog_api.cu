@@ -26,6 +26,9 @@ cudaError_t launch_warmup_bf16(int, const DevParams &, const StatePtrs &, const 
 cudaError_t launch_batch_f32(int, const BatchGroupDev &, const LaunchCfg &, uint32_t, uint32_t, cudaStream_t);
 cudaError_t launch_batch_f16(int, const BatchGroupDev &, const LaunchCfg &, uint32_t, uint32_t, cudaStream_t);
 cudaError_t launch_batch_bf16(int, const BatchGroupDev &, const LaunchCfg &, uint32_t, uint32_t, cudaStream_t);
+cudaError_t launch_clip_f32(int, const ClipArgs &, int, cudaStream_t);
+cudaError_t launch_clip_f16(int, const ClipArgs &, int, cudaStream_t);
+cudaError_t launch_clip_bf16(int, const ClipArgs &, int, cudaStream_t);
 int k2_blocks_per_sm_f32(int, const LaunchCfg &);
 int k2_blocks_per_sm_f16(int, const LaunchCfg &);
 int k2_blocks_per_sm_bf16(int, const LaunchCfg &);
@@ -81,6 +84,8 @@ struct cog_ctx {
     LaunchCfg launch;                // kernel launch shape (cog_set_launch)
     std::vector<ApplyEvents> prof;   // per-frame kernel timing events (profiling on)
     int64_t prof_n;                  // frames recorded since profiling was enabled
+    uint8_t *clip_mem;               // cog_apply_clip scratch (allocated on first use)
+    size_t clip_bytes;
 };
 
 static thread_local char g_create_err[512];
@@ -365,6 +370,123 @@ cog_status cog_apply(cog_ctx *c, const uint8_t *frame_dev, uint8_t *mask_dev, ui
     return COG_OK;
 }
 
+// Scratch of the clip path: per-frame counter banks and sync words, then
+// the undo log (clip-start copies of the stage-0/1 planes, original mixture
+// records, one touched bit per pixel).
+struct ClipScratch {
+    size_t cnt, sync, jl, conf, s1, gmm, touched, total;
+};
+static ClipScratch clip_layout(const Layout &L)
+{
+    ClipScratch z;
+    size_t o = 0;
+    z.cnt = o;     o = up(o + (size_t)CLIP_CNT_WORDS * 4, 256);
+    z.sync = o;    o = up(o + (size_t)CLIP_SYNC_WORDS * 4, 256);
+    z.jl = o;      o = up(o + (size_t)L.Pp * 4, 256);
+    z.conf = o;    o = up(o + (size_t)L.Pp * L.elem, 256);
+    z.s1 = o;      o = up(o + (size_t)L.Pp * L.s1_bytes, 256);
+    z.gmm = o;     o = up(o + (size_t)L.Pp * L.rec_bytes, 256);
+    z.touched = o; o = up(o + (size_t)L.Pp / 8, 256);
+    z.total = o;
+    return z;
+}
+
+cog_status cog_apply_clip(cog_ctx *c, const uint8_t *frames_dev, int32_t n_frames, uint8_t *masks_dev,
+                          uint8_t *stagemaps_dev, cog_stats *stats_host)
+{
+    cog_status s = check_ctx(c);
+    if (s) return s;
+    if (!c->trained) return set_err(c, COG_ERR_STATE, "cog_apply_clip before cog_train_prior");
+    if (!frames_dev || !masks_dev) return set_err(c, COG_ERR_INVALID_ARG, "frames_dev and masks_dev are required");
+    if (n_frames < 1) return set_err(c, COG_ERR_INVALID_ARG, "n_frames must be >= 1");
+    const ClipScratch z = clip_layout(c->L);
+    cudaError_t e;
+    if (!c->clip_mem) {
+        e = cudaMalloc((void **)&c->clip_mem, z.total);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            c->clip_mem = nullptr;
+            return set_err(c, COG_ERR_OOM, "cudaMalloc of %zu clip scratch bytes: %s", z.total, cudaGetErrorString(e));
+        }
+        c->clip_bytes = z.total;
+    }
+    const int64_t P = c->L.P;
+    ClipArgs a;
+    memset(&a, 0, sizeof a);
+    a.dp = c->dp;
+    a.s = c->sp;
+    a.undo_jl = (uint32_t *)(c->clip_mem + z.jl);
+    a.undo_conf = c->clip_mem + z.conf;
+    a.undo_s1 = c->clip_mem + z.s1;
+    a.undo_gmm = c->clip_mem + z.gmm;
+    a.touched = (uint32_t *)(c->clip_mem + z.touched);
+    a.cnt = (uint32_t *)(c->clip_mem + z.cnt);
+    a.sync = (uint32_t *)(c->clip_mem + z.sync);
+    a.frame_al4 = ((uintptr_t)frames_dev & 3) == 0 && (P & 3) == 0;
+    a.out_al4 = ((uintptr_t)masks_dev & 3) == 0 && ((uintptr_t)stagemaps_dev & 3) == 0 && (P & 3) == 0;
+    for (int32_t f0 = 0; f0 < n_frames; f0 += CLIP_TMAX) {
+        const int32_t T = n_frames - f0 < CLIP_TMAX ? n_frames - f0 : CLIP_TMAX;
+        a.frames = frames_dev + (int64_t)f0 * P * 3;
+        a.masks = masks_dev + (int64_t)f0 * P;
+        a.stagemaps = stagemaps_dev ? stagemaps_dev + (int64_t)f0 * P : nullptr;
+        a.T = (uint32_t)T;
+        a.frame_idx0 = (uint32_t)c->frame_no;
+        a.frame_mod3 = (uint32_t)(c->frame_no % 3);
+        e = cudaMemsetAsync(c->clip_mem, 0, z.jl, c->stream);   // counter banks and sync words
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync(clip counters)");
+        switch (c->p.state_dtype) {
+        case COG_F32: e = launch_clip_f32(c->p.K, a, c->n_sm, c->stream); break;
+        case COG_F16: e = launch_clip_f16(c->p.K, a, c->n_sm, c->stream); break;
+        default: e = launch_clip_bf16(c->p.K, a, c->n_sm, c->stream); break;
+        }
+        if (e != cudaSuccess) return cuda_fail(c, e, "cog_apply_clip launch");
+        const int64_t first = c->frame_no;
+        c->frame_no += T;
+        if (stats_host) {
+            std::vector<uint32_t> cnt(CLIP_CNT_WORDS), sync(CLIP_SYNC_WORDS);
+            e = cudaMemcpyAsync(cnt.data(), a.cnt, cnt.size() * 4, cudaMemcpyDeviceToHost, c->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(sync.data(), a.sync, sync.size() * 4, cudaMemcpyDeviceToHost, c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "reading the clip counters");
+            std::vector<uint32_t> ctl;
+            if ((s = read_ctl(c, ctl)) != COG_OK) return s;
+            const int bank = (int)sync[CLIP_RUNS_WORD + 1];
+            const uint32_t flags = sync[CLIP_RUNS_WORD + 2];
+            for (int t = 0; t < T; t++) {
+                cog_stats &st = stats_host[f0 + t];
+                memset(&st, 0, sizeof st);
+                st.frame = (int32_t)(first + t);
+                for (int f = 0; f < 7; f++) {
+                    int64_t v = 0;
+                    for (int q = 0; q < CLIP_SLOTS; q++) v += cnt[(size_t)clip_cnt_word(bank, t, f, q)];
+                    if (f < 5) st.n_stage[f] = v;
+                    else if (f == 5) st.n_gmm = v;
+                    else st.n_stage[5] = v;
+                }
+                st.illum_flag = (int32_t)((flags >> t) & 1u);
+            }
+        }
+    }
+    return COG_OK;
+}
+
+cog_status cog_clip_runs(cog_ctx *c, int32_t *runs)
+{
+    cog_status s = check_ctx(c);
+    if (s) return s;
+    if (!runs) return set_err(c, COG_ERR_INVALID_ARG, "runs is NULL");
+    *runs = 0;
+    if (!c->clip_mem) return COG_OK;
+    const ClipScratch z = clip_layout(c->L);
+    uint32_t v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, c->clip_mem + z.sync + CLIP_RUNS_WORD * 4, 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cog_clip_runs");
+    *runs = (int32_t)v;
+    return COG_OK;
+}
+
 cog_status cog_apply_plain_gmm(cog_ctx *c, const uint8_t *frame_dev, uint8_t *mask_dev)
 {
     cog_status s = check_ctx(c);
@@ -645,6 +767,7 @@ cog_status cog_destroy(cog_ctx *c)
     if (e != cudaSuccess && s == COG_OK) s = COG_ERR_CUDA;
     free_profile(c);
     if (c->stage_in) cudaFree(c->stage_in);
+    if (c->clip_mem) cudaFree(c->clip_mem);
     if (c->owns) cudaFree(c->state);
     delete c;
     return s;

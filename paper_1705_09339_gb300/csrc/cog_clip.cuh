@@ -1,0 +1,632 @@
+// cog_clip.cuh -- the cascade over a clip of consecutive frames in one
+// launch, with each pixel's stage-0/1 state held on chip from the first
+// frame of the clip to the last.
+//
+// Per pixel, frame after frame, the work is exactly that of the per-frame
+// kernels (Sec. 2, "Cascade of Gaussians CoG": frame difference, running
+// Gaussian average, ordered Gaussians of Eq. 2 with the scene prior, the
+// confidence of "Confidence Measure"), with identical arithmetic and the
+// same rounding to the storage type after every frame, so masks, stage maps,
+// counts and state match frame-by-frame cog_apply bit for bit.
+//
+// The one coupling across pixels is the illumination counter (last
+// paragraph of "Cascade of Gaussians CoG"): frame n's response depends on
+// how many pixels of the whole frame n-1 reached the mixture stage.  The
+// clip kernel speculates that no frame after the first is flagged, counts
+// every frame's mixture-stage pixels, and after a grid-wide barrier checks
+// the speculation.  If frame m's flag was wrong, every CTA restores the
+// clip-start state from the undo log written during the pass and the clip
+// runs again with frames 0..m fixed; each run fixes at least one more
+// frame, so at most T+1 runs are needed (one in the common case).
+//
+// GB300 mapping.  A warp owns G x 128 consecutive pixels (G = 2) for the whole
+// clip: their previous frame + label and confidence in registers, their
+// stage-1 records in shared memory; it streams the clip's frame bytes with
+// one frame of register prefetch.  Stage-1 work and mixture-stage survivors
+// are compacted within the warp (no block barriers); survivors read and
+// write their mixture records in place in HBM, the first touch of a record
+// in a clip saving the original to the undo log.  Warps take pixel tiles
+// from a dynamic counter.  The grid is cooperative (all CTAs resident), so
+// the barriers between the pass, the check and a rerun cannot deadlock;
+// every wait is bounded by the global timer and reports a device error.
+#pragma once
+
+#include "cog_apply.cuh"
+
+namespace cog {
+
+constexpr int CLIP_TPB = 128;
+
+// Shared memory of one warp: stage-1 records of its G x 128 pixels and the
+// per-frame work lists (indices are pixel slots within the tile).
+template <typename T, int G> struct alignas(16) ClipWarp {
+    static constexpr int WT = G * 128;
+    uint8_t s1[WT * S1Rec<T>::BYTES];
+    uint2 stash[WT];       // rgb | D << 24, C- bits
+    float resc[WT];        // new confidence of pixels decided at stage 1 or 2
+    uint8_t list[WT];      // stage-1 work list
+    uint8_t surv[WT];      // mixture-stage survivors
+    uint8_t resst[WT];     // stage code of pixels past stage 0
+    uint32_t touched[WT / 32];   // mixture record saved to the undo log
+};
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier of a cooperative launch: every CTA arrives once per
+// barrier; `target` = (barriers so far) x gridDim.x.  Gives up after two
+// seconds, sets the device error word and returns false in every thread of
+// the CTA.
+__device__ __forceinline__ bool clip_grid_sync(uint32_t *bar, uint32_t target, uint32_t *err)
+{
+    __syncthreads();
+    int bad = 0;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(bar, 1u);
+        const uint64_t t0 = global_ns();
+        for (uint32_t it = 0; ld_acquire_gpu(bar) < target; it++) {
+            __nanosleep(128);
+            if ((it & 255u) == 0 && (global_ns() - t0 > 2000000000ull || it > (1u << 26))) {
+                atomicOr(err, DERR_GRID_TIMEOUT);
+                bad = 1;
+                break;
+            }
+        }
+        __threadfence();
+    }
+    return !__syncthreads_or(bad);
+}
+
+// Stage 0 of one group of 4 pixels (frame words w0..w2): skip bits, the
+// pixels as rgb words, and the mask of pixels that go on to stage 1.
+template <typename T>
+__device__ __forceinline__ void clip_stage0(const DevParams &dp, const uint4 &jl, const VecN<T, PPT> &cv,
+                                            uint32_t w0, uint32_t w1, uint32_t w2, int nact, bool phase_off,
+                                            uint32_t Iw[PPT], uint32_t ad[PPT], uint32_t &skip, uint32_t &need1)
+{
+    const bool conf_on = dp.flags & COG_CONF;
+    skip = 0;
+    if (phase_off) {
+#pragma unroll
+        for (int i = 0; i < PPT; i++)
+            if (i < nact && cv.get(i) >= dp.c_skip) skip |= 1u << i;
+    }
+    Iw[0] = w0 & 0x00ffffffu;
+    Iw[1] = __byte_perm(w0, w1, 0x0543) & 0x00ffffffu;
+    Iw[2] = __byte_perm(w1, w2, 0x0432) & 0x00ffffffu;
+    Iw[3] = w2 >> 8;
+#pragma unroll
+    for (int i = 0; i < PPT; i++) ad[i] = __vabsdiffu4(Iw[i], u4get(jl, i) & 0x00ffffffu);
+    need1 = 0;
+    const bool fd_on = dp.flags & COG_FD;
+#pragma unroll
+    for (int i = 0; i < PPT; i++) {
+        if (i >= nact || (skip >> i & 1u)) continue;
+        const float Cm = conf_on ? cv.get(i) : 0.5f;
+        const float tau = dp.tau_fd * (0.5f + Cm);
+        const uint32_t t = tau >= 255.f ? 255u : (uint32_t)tau;
+        const bool pass = fd_on && (u4get(jl, i) >> 24) == 0 && __vcmpgtu4(ad[i], t * 0x01010101u) == 0u;
+        if (!pass) need1 |= 1u << i;
+    }
+}
+
+__device__ __forceinline__ void load_frame_words(const uint8_t *f, int64_t p0, int nact, bool al4, uint32_t &w0,
+                                                 uint32_t &w1, uint32_t &w2)
+{
+    if (nact == PPT && al4) {
+        const uint32_t *f4 = reinterpret_cast<const uint32_t *>(f + p0 * 3);
+        w0 = __ldcs(f4); w1 = __ldcs(f4 + 1); w2 = __ldcs(f4 + 2);
+    } else {
+        uint32_t fw[3] = {0, 0, 0};
+#pragma unroll
+        for (int b3 = 0; b3 < PPT * 3; b3++)
+            if (b3 < nact * 3) fw[b3 >> 2] |= (uint32_t)f[p0 * 3 + b3] << ((b3 & 3) * 8);
+        w0 = fw[0]; w1 = fw[1]; w2 = fw[2];
+    }
+}
+
+// One warp's tile of G x 128 pixels through the T frames of the clip.
+// cnt_s: the CTA's per-frame counters [CLIP_TMAX][CTL_FIELDS].
+template <typename T, int K, int G>
+__device__ __forceinline__ void clip_tile(const ClipArgs &A, ClipWarp<T, G> &W, uint32_t wbase, int lane,
+                                          uint32_t flags, uint32_t *cnt_s)
+{
+    const DevParams &dp = A.dp;
+    const bool conf_on = dp.flags & COG_CONF;
+    const bool sampling = (dp.flags & COG_SAMPLE) && conf_on;
+    constexpr int WT = G * 128;
+    constexpr int SB = S1Rec<T>::BYTES;
+    const int64_t P = dp.P;
+
+    uint4 jl[G];
+    VecN<T, PPT> cv[G];
+    int nact[G];
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+        const int64_t p0 = (int64_t)wbase + g * 128 + lane * PPT;
+        nact[g] = (int)min((int64_t)PPT, max((int64_t)0, P - p0));
+        jl[g] = make_uint4(0, 0, 0, 0);
+        if (nact[g] > 0) {
+            jl[g] = *reinterpret_cast<const uint4 *>(A.s.jl + p0);
+            cv[g].load(reinterpret_cast<const T *>(A.s.conf) + p0);
+            *reinterpret_cast<uint4 *>(A.undo_jl + p0) = jl[g];
+            cv[g].store(reinterpret_cast<T *>(A.undo_conf) + p0);
+        } else {
+#pragma unroll
+            for (int i = 0; i < VecN<T, PPT>::NW; i++) cv[g].w[i] = 0;
+        }
+    }
+    // stage-1 records of the tile (planes are padded to whole 4096-pixel
+    // blocks, so the tile never runs past the allocation)
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(A.s.s1 + (int64_t)wbase * SB);
+        uint4 *und = reinterpret_cast<uint4 *>(A.undo_s1 + (int64_t)wbase * SB);
+        uint4 *dst = reinterpret_cast<uint4 *>(W.s1);
+#pragma unroll
+        for (int k = lane; k < WT * SB / 16; k += 32) {
+            const uint4 v = src[k];
+            dst[k] = v;
+            und[k] = v;
+        }
+    }
+    if (lane < WT / 32) W.touched[lane] = 0;
+    __syncwarp();
+
+    uint32_t nw[G][3];
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+        const int64_t p0 = (int64_t)wbase + g * 128 + lane * PPT;
+        nw[g][0] = nw[g][1] = nw[g][2] = 0;
+        if (nact[g] > 0) load_frame_words(A.frames, p0, nact[g], A.frame_al4, nw[g][0], nw[g][1], nw[g][2]);
+    }
+    const uint32_t lt = (1u << lane) - 1u;
+
+    for (uint32_t t = 0; t < A.T; t++) {
+        uint32_t cw[G][3];
+#pragma unroll
+        for (int g = 0; g < G; g++) { cw[g][0] = nw[g][0]; cw[g][1] = nw[g][1]; cw[g][2] = nw[g][2]; }
+        if (t + 1 < A.T) {
+            const uint8_t *fn = A.frames + (int64_t)(t + 1) * P * 3;
+#pragma unroll
+            for (int g = 0; g < G; g++) {
+                const int64_t p0 = (int64_t)wbase + g * 128 + lane * PPT;
+                if (nact[g] > 0) load_frame_words(fn, p0, nact[g], A.frame_al4, nw[g][0], nw[g][1], nw[g][2]);
+            }
+        }
+        const uint32_t fidx = A.frame_idx0 + t;
+        const bool flag = (flags >> t) & 1u;
+
+        // ---- stage 0 and the stage-1 work list
+        uint32_t Iw[G][PPT], skip[G], need1[G];
+        int n1 = 0;
+#pragma unroll
+        for (int g = 0; g < G; g++) {
+            const uint32_t p0 = wbase + g * 128 + lane * PPT;
+            const bool off = sampling && (fidx + (p0 >> 6)) % (uint32_t)dp.skip_period != 0u;
+            uint32_t ad[PPT];
+            clip_stage0<T>(dp, jl[g], cv[g], cw[g][0], cw[g][1], cw[g][2], nact[g], off, Iw[g], ad, skip[g],
+                           need1[g]);
+            n1 += __popc(need1[g]);
+            if (need1[g]) {
+#pragma unroll
+                for (int i = 0; i < PPT; i++) {
+                    if (!(need1[g] >> i & 1u)) continue;
+                    const int slot = g * 128 + lane * PPT + i;
+                    const uint32_t m2 = __vmaxu4(ad[i], ad[i] >> 8);
+                    const uint32_t D = __vmaxu4(m2, m2 >> 8) & 0xffu;
+                    W.stash[slot] = make_uint2(Iw[g][i] | (D << 24), __float_as_uint(conf_on ? cv[g].get(i) : 0.5f));
+                }
+            }
+        }
+        int incl = n1;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += v;
+        }
+        const int n1w = __shfl_sync(0xffffffffu, incl, 31);
+        {
+            int k = incl - n1;
+#pragma unroll
+            for (int g = 0; g < G; g++)
+#pragma unroll
+                for (int i = 0; i < PPT; i++)
+                    if (need1[g] >> i & 1u) W.list[k++] = (uint8_t)(g * 128 + lane * PPT + i);
+        }
+        __syncwarp();
+
+        // ---- stage 1 over the compacted list
+        int ns = 0;
+        for (int j0 = 0; j0 < n1w; j0 += 32) {
+            const int j = j0 + lane;
+            bool surv = false;
+            int slot = 0;
+            if (j < n1w) {
+                slot = W.list[j];
+                const uint2 sv = W.stash[slot];
+                const int D = (int)(sv.x >> 24);
+                const float Cm = __uint_as_float(sv.y);
+                S1Rec<T> r;
+#pragma unroll
+                for (int i = 0; i < S1Rec<T>::NV; i++) r.u[i] = reinterpret_cast<const uint4 *>(W.s1 + slot * SB)[i];
+                surv = true;
+                if (dp.flags & COG_RGA) {
+                    float tr = 0.f;
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        const float d = (float)((sv.x >> (8 * c)) & 0xffu) - r.get(c);
+                        const float tt = __fdividef(d * d, dp.lam2 * r.get(3 + c));
+                        tr = tt > tr ? tt : tr;
+                    }
+                    if (tr < 1.f) {
+                        surv = false;
+                        if (!(conf_on && Cm >= dp.c_halt)) {
+                            const float ae = dp.alpha * (1.5f - Cm);
+#pragma unroll
+                            for (int c = 0; c < 3; c++) {
+                                const float I = (float)((sv.x >> (8 * c)) & 0xffu);
+                                const float m = r.get(c) + ae * (I - r.get(c));
+                                const float d = I - m;
+                                r.set(c, m);
+                                r.set(3 + c, clampf((1.f - ae) * r.get(3 + c) + ae * d * d, dp.var_min, dp.var_max));
+                            }
+#pragma unroll
+                            for (int i = 0; i < S1Rec<T>::NV; i++) reinterpret_cast<uint4 *>(W.s1 + slot * SB)[i] = r.u[i];
+                        }
+                        W.resc[slot] = (1.f - dp.eta) * Cm + dp.eta * conf_stage1(r.qab(), D, tr);
+                        W.resst[slot] = COG_ST_RGA;
+                    }
+                }
+            }
+            const uint32_t b = __ballot_sync(0xffffffffu, surv);
+            if (surv) W.surv[ns + __popc(b & lt)] = (uint8_t)slot;
+            ns += __popc(b);
+        }
+        __syncwarp();
+
+        // ---- stage 2: mixture step of the survivors, records in place
+        for (int j0 = 0; j0 < ns; j0 += 32) {
+            const int j = j0 + lane;
+            if (j < ns) {
+                const int slot = W.surv[j];
+                const int64_t p = (int64_t)wbase + slot;
+                const uint2 sv = W.stash[slot];
+                uint4 raw[Rec<T, K>::NV];
+                const uint4 *src = reinterpret_cast<const uint4 *>(A.s.gmm + p * Rec<T, K>::BYTES);
+#pragma unroll
+                for (int i = 0; i < Rec<T, K>::NV; i++) raw[i] = src[i];
+                uint32_t qk[3];
+#pragma unroll
+                for (int c = 0; c < 3; c++) qk[c] = __ldg(A.s.kde + (p * 3 + c) * 256 + ((sv.x >> (8 * c)) & 0xffu));
+                const uint32_t bit = 1u << (slot & 31);
+                if (!(W.touched[slot >> 5] & bit)) {
+                    uint4 *u = reinterpret_cast<uint4 *>(A.undo_gmm + p * Rec<T, K>::BYTES);
+#pragma unroll
+                    for (int i = 0; i < Rec<T, K>::NV; i++) u[i] = raw[i];
+                    atomicOr(&W.touched[slot >> 5], bit);
+                }
+                const int D = (int)(sv.x >> 24);
+                float I[3];
+#pragma unroll
+                for (int c = 0; c < 3; c++) I[c] = (float)((sv.x >> (8 * c)) & 0xffu);
+                const float Cm = __uint_as_float(sv.y);
+                S1Rec<T> r;
+#pragma unroll
+                for (int i = 0; i < S1Rec<T>::NV; i++) r.u[i] = reinterpret_cast<const uint4 *>(W.s1 + slot * SB)[i];
+                const uint32_t qab = r.qab();
+                Mix<K> m;
+#pragma unroll
+                for (int k = 0; k < K; k++) {
+                    m.w[k] = rec_elem<T, K>(raw, 7 * k);
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        m.mu[k][c] = rec_elem<T, K>(raw, 7 * k + 1 + c);
+                        m.v[k][c] = rec_elem<T, K>(raw, 7 * k + 4 + c);
+                    }
+                }
+                const float ae = dp.alpha * (1.5f - Cm);
+                const MixOut o = mix_step<K>(m, I, ae, dp);
+                int label = o.fg, st = o.fg ? COG_ST_FG : COG_ST_GMM_BG;
+                if (flag && o.fg) {
+                    illum_response<K>(m, o.tgt, dp.w_illum);
+                    label = 0;
+                    st = COG_ST_ILLUM;
+                }
+                rec_store<T, K>(A.s.gmm, p, m);
+                if (!label) {   // transition update: the background mode seeds stage 1
+                    S1Rec<T> rn;
+#pragma unroll
+                    for (int i = 0; i < S1Rec<T>::NV; i++) rn.u[i] = make_uint4(0, 0, 0, 0);
+#pragma unroll
+                    for (int k = 0; k < K; k++) {
+                        if (k == o.tgt) {
+#pragma unroll
+                            for (int c = 0; c < 3; c++) { rn.set(c, m.mu[k][c]); rn.set(3 + c, m.v[k][c]); }
+                        }
+                    }
+                    rn.set_qab(qab);
+#pragma unroll
+                    for (int i = 0; i < S1Rec<T>::NV; i++) reinterpret_cast<uint4 *>(W.s1 + slot * SB)[i] = rn.u[i];
+                }
+                if (conf_on) {
+                    uint32_t qmin = qk[0] < qk[1] ? qk[0] : qk[1];
+                    qmin = qk[2] < qmin ? qk[2] : qmin;
+                    const uint32_t qa = qab & 0xffu, qb = qab >> 8;
+                    const float wa = (float)qa * R255, wb = (float)qb * R255;
+                    const float wg = (float)(255u - qa - qb) * R255;
+                    const float dhat = (float)D * R255;
+                    const float Mh = o.match >= 0 ? (o.tm < 1.f ? o.tm : 1.f) : 1.f;
+                    float ci;
+                    if ((int)qmin < dp.q_null) {
+                        const float den = wb + wg;
+                        ci = den > 0.f ? (wb * (1.f - dhat) + wg * (1.f - Mh)) / den : 0.f;
+                    } else {
+                        ci = wa * ((float)qmin * R255) + wb * (1.f - dhat) + wg * (1.f - Mh);
+                    }
+                    W.resc[slot] = (1.f - dp.eta) * Cm + dp.eta * ci;
+                }
+                W.resst[slot] = (uint8_t)st;
+            }
+        }
+        __syncwarp();
+
+        // ---- outputs of frame t; registers carry the pixels to frame t+1
+        uint32_t c_fd = 0, c_rga = 0, c_bg = 0, c_fg = 0, c_il = 0, c_sk = 0;
+        uint8_t *mk_out = A.masks + (int64_t)t * P;
+        uint8_t *sm_out = A.stagemaps ? A.stagemaps + (int64_t)t * P : nullptr;
+#pragma unroll
+        for (int g = 0; g < G; g++) {
+            if (nact[g] <= 0) continue;
+            const int64_t p0 = (int64_t)wbase + g * 128 + lane * PPT;
+            uint32_t mk = 0, sm = 0;
+#pragma unroll
+            for (int i = 0; i < PPT; i++) {
+                if (i >= nact[g]) continue;
+                const int slot = g * 128 + lane * PPT + i;
+                const bool sk = skip[g] >> i & 1u;
+                const uint32_t st = sk ? (uint32_t)COG_ST_SKIP
+                                       : ((need1[g] >> i & 1u) ? (uint32_t)W.resst[slot] : (uint32_t)COG_ST_FD);
+                c_fd += st == COG_ST_FD; c_rga += st == COG_ST_RGA; c_bg += st == COG_ST_GMM_BG;
+                c_fg += st == COG_ST_FG; c_il += st == COG_ST_ILLUM; c_sk += sk;
+                const uint32_t old = u4get(jl[g], i);
+                uint32_t label;
+                if (sk) {
+                    label = old >> 24;
+                } else {
+                    label = st == COG_ST_FG;
+                    u4set(jl[g], i, Iw[g][i] | (label << 24));
+                    if (conf_on)
+                        cv[g].set(i, st == COG_ST_FD ? (1.f - dp.eta) * cv[g].get(i) + dp.eta : W.resc[slot]);
+                }
+                mk |= (label ? 255u : 0u) << (8 * i);
+                sm |= st << (8 * i);
+            }
+            if (nact[g] == PPT && A.out_al4) {
+                __stcs(reinterpret_cast<uint32_t *>(mk_out + p0), mk);
+                if (sm_out) __stcs(reinterpret_cast<uint32_t *>(sm_out + p0), sm);
+            } else {
+                for (int i = 0; i < nact[g]; i++) {
+                    mk_out[p0 + i] = (uint8_t)(mk >> (8 * i));
+                    if (sm_out) sm_out[p0 + i] = (uint8_t)(sm >> (8 * i));
+                }
+            }
+        }
+        const uint32_t v[6] = {__reduce_add_sync(0xffffffffu, c_fd), __reduce_add_sync(0xffffffffu, c_rga),
+                               __reduce_add_sync(0xffffffffu, c_bg), __reduce_add_sync(0xffffffffu, c_fg),
+                               __reduce_add_sync(0xffffffffu, c_il), __reduce_add_sync(0xffffffffu, c_sk)};
+        if (lane == 0) {
+            uint32_t *cs = cnt_s + t * CTL_FIELDS;
+#pragma unroll
+            for (int f = 0; f < 5; f++) if (v[f]) atomicAdd(cs + f, v[f]);
+            if (v[2] + v[3] + v[4]) atomicAdd(cs + 5, v[2] + v[3] + v[4]);
+            if (v[5]) atomicAdd(cs + 6, v[5]);
+        }
+        __syncwarp();
+    }
+
+    // ---- the tile's state after the clip, in place
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+        if (nact[g] <= 0) continue;
+        const int64_t p0 = (int64_t)wbase + g * 128 + lane * PPT;
+        *reinterpret_cast<uint4 *>(A.s.jl + p0) = jl[g];
+        if (conf_on) cv[g].store(reinterpret_cast<T *>(A.s.conf) + p0);
+    }
+    {
+        uint4 *dst = reinterpret_cast<uint4 *>(A.s.s1 + (int64_t)wbase * SB);
+        const uint4 *src = reinterpret_cast<const uint4 *>(W.s1);
+#pragma unroll
+        for (int k = lane; k < WT * SB / 16; k += 32) dst[k] = src[k];
+    }
+    if (lane < WT / 32) A.touched[wbase / 32 + lane] = W.touched[lane];
+    __syncwarp();
+}
+
+// Undo one warp tile: planes from the clip-start copies, and the mixture
+// records the failed run touched.
+template <typename T, int K, int G>
+__device__ __forceinline__ void clip_restore_tile(const ClipArgs &A, uint32_t wbase, int lane)
+{
+    constexpr int WT = G * 128;
+    constexpr int SB = S1Rec<T>::BYTES;
+    const int64_t P = A.dp.P;
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+        const int64_t p0 = (int64_t)wbase + g * 128 + lane * PPT;
+        if (p0 >= P) continue;
+        *reinterpret_cast<uint4 *>(A.s.jl + p0) = *reinterpret_cast<const uint4 *>(A.undo_jl + p0);
+        VecN<T, PPT> c;
+        c.load(reinterpret_cast<const T *>(A.undo_conf) + p0);
+        c.store(reinterpret_cast<T *>(A.s.conf) + p0);
+    }
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(A.undo_s1 + (int64_t)wbase * SB);
+        uint4 *dst = reinterpret_cast<uint4 *>(A.s.s1 + (int64_t)wbase * SB);
+        for (int k = lane; k < WT * SB / 16; k += 32) dst[k] = src[k];
+    }
+    for (int j = 0; j < WT; j += 32) {
+        const uint32_t word = __ldcg(A.touched + wbase / 32 + j / 32);
+        if (word >> lane & 1u) {
+            const int64_t p = (int64_t)wbase + j + lane;
+            const uint4 *src = reinterpret_cast<const uint4 *>(A.undo_gmm + p * Rec<T, K>::BYTES);
+            uint4 *dst = reinterpret_cast<uint4 *>(A.s.gmm + p * Rec<T, K>::BYTES);
+#pragma unroll
+            for (int i = 0; i < Rec<T, K>::NV; i++) dst[i] = src[i];
+        }
+    }
+}
+
+template <typename T, int K, int G>
+__global__ void __launch_bounds__(CLIP_TPB) clip_kernel(const ClipArgs A)
+{
+    constexpr int NW = CLIP_TPB / 32;
+    extern __shared__ __align__(16) uint8_t clip_smem[];
+    ClipWarp<T, G> *W = reinterpret_cast<ClipWarp<T, G> *>(clip_smem);
+    __shared__ uint32_t cnt_s[CLIP_TMAX * CTL_FIELDS];
+    __shared__ uint32_t flags_s, tile_s[NW], tf_s;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const DevParams &dp = A.dp;
+    uint32_t *ctl = A.s.ctl;
+    uint32_t *err = ctl + CTL_ERR_WORD;
+    uint32_t *bar = A.sync;
+    const uint32_t n0 = A.frame_mod3;
+
+    if (warp == 0) {   // frame 0's flag comes from the frame before the clip
+        const bool f = illum_flag_prev(dp, ctl, n0, lane);
+        if (lane == 0) flags_s = f ? 1u : 0u;
+    }
+    __syncthreads();
+    uint32_t flags = flags_s;
+    uint32_t nsync = 0;
+    uint32_t run = 0;
+    for (;; run++) {
+        const int bank = (int)(run % 3);
+        for (int i = tid; i < CLIP_TMAX * CTL_FIELDS; i += CLIP_TPB) cnt_s[i] = 0;
+        if (blockIdx.x == 0 && run >= 1) {
+            // the bank and tile counter of the run after this one were last
+            // read before the barrier that ended the previous run
+            const int nb = (int)((run + 1) % 3);
+            for (int i = tid; i < CLIP_TMAX * CTL_FIELDS * CLIP_SLOTS; i += CLIP_TPB)
+                A.cnt[clip_cnt_word(nb, i / (CTL_FIELDS * CLIP_SLOTS), (i / CLIP_SLOTS) % CTL_FIELDS, i % CLIP_SLOTS)] = 0;
+            if (tid == 0) A.sync[CLIP_TILE_WORD + 32 * nb] = 0;
+        }
+        __syncthreads();
+        // ---- the pass: warps take tiles until none is left
+        for (;;) {
+            uint32_t wt = 0;
+            if (lane == 0) wt = atomicAdd(A.sync + CLIP_TILE_WORD + 32 * bank, 1u);
+            wt = __shfl_sync(0xffffffffu, wt, 0);
+            if (wt >= A.n_tiles) break;
+            clip_tile<T, K, G>(A, W[warp], wt * (uint32_t)(G * 128), lane, flags, cnt_s);
+        }
+        __syncthreads();
+        for (int i = tid; i < (int)A.T * CTL_FIELDS; i += CLIP_TPB)
+            if (cnt_s[i]) atomicAdd(A.cnt + clip_cnt_word(bank, i / CTL_FIELDS, i % CTL_FIELDS, blockIdx.x % CLIP_SLOTS), cnt_s[i]);
+        if (!clip_grid_sync(bar, ++nsync * gridDim.x, err)) return;
+        // ---- check the speculated flags against the counts
+        if (warp == 0) {
+            uint32_t ng = 0;
+            if (lane < (int)A.T)
+                for (int s = 0; s < CLIP_SLOTS; s++) ng += __ldcg(A.cnt + clip_cnt_word(bank, lane, 5, s));
+            // frame lane + 1 is flagged when frame lane sent more than the
+            // threshold share of the frame to the mixture stage
+            const bool f = (dp.flags & COG_ILLUM) && lane + 1 < (int)A.T &&
+                           (uint64_t)ng * 1000u > (uint64_t)dp.illum_permille * (uint64_t)dp.P;
+            const uint32_t tf = (__ballot_sync(0xffffffffu, f) << 1) | (flags & 1u);
+            if (lane == 0) tf_s = tf;
+        }
+        __syncthreads();
+        const uint32_t tf = tf_s;
+        const uint32_t diff = (tf ^ flags) & (A.T >= 32 ? 0xffffffffu : ((1u << A.T) - 1u));
+        if (!diff) break;
+        if (run >= A.T) {   // cannot happen: each run fixes one more frame
+            if (blockIdx.x == 0 && tid == 0) atomicOr(err, DERR_CLIP_RUNS);
+            return;
+        }
+        // frames before the first wrong flag were right; the flag of that
+        // frame is now known; later ones take this run's counts as a guess
+        flags = tf;
+        for (uint32_t wt = blockIdx.x * NW + warp; wt < A.n_tiles; wt += gridDim.x * NW)
+            clip_restore_tile<T, K, G>(A, wt * (uint32_t)(G * 128), lane);
+        if (!clip_grid_sync(bar, ++nsync * gridDim.x, err)) return;
+    }
+
+    // ---- the control block as frame-by-frame application leaves it after
+    //      the clip's last frame
+    if (blockIdx.x == 0 && warp == 0) {
+        const int bank = (int)(run % 3);
+        unsigned long long *tot = reinterpret_cast<unsigned long long *>(ctl + CTL_TOT_WORD);
+        const uint32_t nl = (n0 + A.T - 1) % 3;
+        uint32_t last = 0;
+#pragma unroll 1
+        for (int f = 0; f < 7; f++) {
+            uint64_t add = __reduce_add_sync(0xffffffffu, __ldcg(ctl + ctl_slot((n0 + 2) % 3, f, lane)));
+            uint32_t v = 0;
+            if (lane < (int)A.T)
+                for (int s = 0; s < CLIP_SLOTS; s++) v += __ldcg(A.cnt + clip_cnt_word(bank, lane, f, s));
+            add += __reduce_add_sync(0xffffffffu, lane + 1 < (int)A.T ? v : 0u);
+            const uint32_t vl = __shfl_sync(0xffffffffu, v, (int)A.T - 1);
+            if (lane == 0) tot[f] += add;
+            if (lane == f) last = vl;
+        }
+        __syncwarp();
+        for (int i = lane; i < 3 * CTL_FIELDS * CTL_SLOTS; i += 32)
+            ctl[ctl_slot(i / (CTL_FIELDS * CTL_SLOTS), (i / CTL_SLOTS) % CTL_FIELDS, i % CTL_SLOTS)] = 0;
+        for (int i = lane; i < 3 * QSEG; i += 32) ctl[ctl_qcnt(i / QSEG, i % QSEG)] = 0;
+        __syncwarp();
+        if (lane < 7) ctl[ctl_slot((int)nl, lane, 0)] = last;
+        if (lane == 0) {
+            A.sync[CLIP_RUNS_WORD] = run + 1;
+            A.sync[CLIP_RUNS_WORD + 1] = (uint32_t)bank;
+            A.sync[CLIP_RUNS_WORD + 2] = flags;
+        }
+    }
+}
+
+template <typename T, int K, int G>
+size_t clip_smem_bytes()
+{
+    return sizeof(ClipWarp<T, G>) * (CLIP_TPB / 32);
+}
+
+template <typename T, int K, int G>
+int clip_blocks_per_sm()
+{
+    static int b = -1;
+    if (b < 0) {
+        const size_t sm = clip_smem_bytes<T, K, G>();
+        cudaFuncSetAttribute(clip_kernel<T, K, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, clip_kernel<T, K, G>, CLIP_TPB, sm) != cudaSuccess)
+            b = 0;
+    }
+    return b;
+}
+
+template <typename T, int K>
+cudaError_t launch_clip_t(const ClipArgs &a0, int n_sm, cudaStream_t st)
+{
+    constexpr int G = 2;
+    ClipArgs a = a0;
+    a.n_tiles = (uint32_t)((a.dp.P + G * 128 - 1) / (G * 128));
+    const int bps = clip_blocks_per_sm<T, K, G>();
+    if (bps < 1) return cudaErrorInvalidConfiguration;
+    const int64_t want = (a.n_tiles + CLIP_TPB / 32 - 1) / (CLIP_TPB / 32);
+    const int grid = (int)min((int64_t)bps * n_sm, max((int64_t)1, want));
+    void *args[] = {(void *)&a};
+    return cudaLaunchCooperativeKernel((const void *)clip_kernel<T, K, G>, dim3(grid), dim3(CLIP_TPB), args,
+                                       clip_smem_bytes<T, K, G>(), st);
+}
+
+}  // namespace cog

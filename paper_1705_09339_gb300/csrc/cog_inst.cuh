@@ -3,6 +3,7 @@
 // compile as separate translation units in parallel.
 #include "cog_apply.cuh"
 #include "cog_mixture.cuh"
+#include "cog_clip.cuh"
 
 #define COG_CAT2(a, b) a##b
 #define COG_CAT(a, b) COG_CAT2(a, b)
@@ -50,6 +51,13 @@ int COG_CAT(k2_blocks_per_sm_, COG_SUFFIX)(int K, const LaunchCfg &lc)
     case 7: return k2_blocks_per_sm_t<COG_T, 7>(lc);
     default: return k2_blocks_per_sm_t<COG_T, 8>(lc);
     }
+}
+
+cudaError_t COG_CAT(launch_clip_, COG_SUFFIX)(int K, const ClipArgs &a, int n_sm, cudaStream_t st)
+{
+#define CALL_C(k) launch_clip_t<COG_T, k>(a, n_sm, st)
+    COG_KSWITCH(CALL_C)
+#undef CALL_C
 }
 
 cudaError_t COG_CAT(launch_plain_, COG_SUFFIX)(int K, const DevParams &dp, const StatePtrs &s,

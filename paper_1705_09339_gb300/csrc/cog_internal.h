@@ -120,6 +120,45 @@ struct LaunchCfg {
 
 cudaError_t launch_batch_advance(const BatchGroupDev &g, cudaStream_t st);
 
+// ---- clip of consecutive frames in one cooperative launch
+constexpr int CLIP_TMAX = 32;          // frames per launch (their flags fit one word)
+constexpr int CLIP_SLOTS = 8;          // counter slots per (frame, field)
+constexpr uint32_t DERR_GRID_TIMEOUT = 2u;   // a grid-wide wait of the clip kernel gave up
+constexpr uint32_t DERR_CLIP_RUNS = 4u;      // the clip kernel's reruns did not converge
+// per-frame counters of a run: 3 banks (runs rotate) x CLIP_TMAX frames x
+// CTL_FIELDS fields x CLIP_SLOTS slots, each slot on its own 128-byte line
+__host__ __device__ constexpr int clip_cnt_word(int bank, int t, int f, int s)
+{
+    return (((bank * CLIP_TMAX + t) * CTL_FIELDS + f) * CLIP_SLOTS + s) * CTL_PAD;
+}
+constexpr int CLIP_CNT_WORDS = 3 * CLIP_TMAX * CTL_FIELDS * CLIP_SLOTS * CTL_PAD;
+// sync words: [0] barrier arrivals; [CLIP_TILE_WORD + 32 b] tile counter of
+// bank b; [CLIP_RUNS_WORD] runs used, [+1] bank of the final run, [+2] the
+// flags the final run used
+constexpr int CLIP_TILE_WORD = 32;
+constexpr int CLIP_RUNS_WORD = 128;
+constexpr int CLIP_SYNC_WORDS = 256;
+
+struct ClipArgs {
+    DevParams dp;
+    StatePtrs s;
+    const uint8_t *frames;    // [T][P][3]
+    uint8_t *masks;           // [T][P]
+    uint8_t *stagemaps;       // [T][P] or null
+    uint32_t *undo_jl;        // clip-start copies of the planes
+    void *undo_conf;
+    uint8_t *undo_s1;
+    uint8_t *undo_gmm;        // original mixture records of touched pixels
+    uint32_t *touched;        // 1 bit per pixel: record saved in undo_gmm
+    uint32_t *cnt;            // CLIP_CNT_WORDS
+    uint32_t *sync;           // CLIP_SYNC_WORDS
+    uint32_t T;               // frames in this clip, 1..CLIP_TMAX
+    uint32_t frame_idx0;      // frames applied before the clip (sampling phase)
+    uint32_t frame_mod3;      // the same count mod 3 (control-block buffers)
+    uint32_t frame_al4, out_al4;
+    uint32_t n_tiles;         // set by the launcher
+};
+
 // Optional per-kernel timing: events recorded before the first kernel,
 // between the two kernels and after the second, on the launch stream.
 struct ApplyEvents {

@@ -78,3 +78,5 @@ def test_null_context_calls_fail_cleanly(cog):
     assert cog.lib.cog_sync(None) == cog.COG_ERR_INVALID_ARG
     assert cog.lib.cog_destroy(None) == cog.COG_ERR_INVALID_ARG
     assert cog.lib.cog_apply(None, None, None, None, None) == cog.COG_ERR_INVALID_ARG
+    assert cog.lib.cog_apply_clip(None, None, 4, None, None, None) == cog.COG_ERR_INVALID_ARG
+    assert cog.lib.cog_clip_runs(None, None) == cog.COG_ERR_INVALID_ARG
