@@ -19,14 +19,16 @@
 // runs again with frames 0..m fixed; each run fixes at least one more
 // frame, so at most T+1 runs are needed (one in the common case).
 //
-// GB300 mapping.  A warp owns G x 128 consecutive pixels (G = 2) for the whole
+// GB300 mapping.  A warp owns G x 128 consecutive pixels for the whole
 // clip: their previous frame + label and confidence in registers, their
 // stage-1 records in shared memory; it streams the clip's frame bytes with
-// one frame of register prefetch.  Stage-1 work and mixture-stage survivors
-// are compacted within the warp (no block barriers); survivors read and
-// write their mixture records in place in HBM, the first touch of a record
-// in a clip saving the original to the undo log.  Warps take pixel tiles
-// from a dynamic counter.  The grid is cooperative (all CTAs resident), so
+// one frame of register prefetch.  Stage-1 work is compacted within the
+// warp; the mixture-stage survivors of all the CTA's warps are compacted
+// into one shared queue per frame and run one per thread (a warp-level
+// queue would run the long mixture step for a few lanes of every warp).
+// Survivors read and write their mixture records in place in HBM, the
+// first touch of a record in a clip saving the original to the undo log.
+// CTAs take tiles of NW x G x 128 pixels from a dynamic counter.  The grid is cooperative (all CTAs resident), so
 // the barriers between the pass, the check and a rerun cannot deadlock;
 // every wait is bounded by the global timer and reports a device error.
 #pragma once
@@ -36,6 +38,9 @@
 namespace cog {
 
 constexpr int CLIP_TPB = 128;
+constexpr int CLIP_G = 2;        // 128-pixel groups per warp tile
+constexpr int CLIP_MINB = 3;     // CTAs per SM the register budget must allow
+#define CLIP_S2_INLINE __forceinline__
 
 // Shared memory of one warp: stage-1 records of its G x 128 pixels and the
 // per-frame work lists (indices are pixel slots within the tile).
@@ -45,9 +50,16 @@ template <typename T, int G> struct alignas(16) ClipWarp {
     uint2 stash[WT];       // rgb | D << 24, C- bits
     float resc[WT];        // new confidence of pixels decided at stage 1 or 2
     uint8_t list[WT];      // stage-1 work list
-    uint8_t surv[WT];      // mixture-stage survivors
     uint8_t resst[WT];     // stage code of pixels past stage 0
     uint32_t touched[WT / 32];   // mixture record saved to the undo log
+};
+
+// The CTA's mixture-stage queue of one frame: survivors of all its warps,
+// (warp << 8 | slot), processed densely by all its threads; counts
+// double-buffered by frame parity.
+template <int NW, int WT> struct ClipQueue {
+    uint16_t q[NW * WT];
+    uint32_t n[2];
 };
 
 __device__ __forceinline__ uint64_t global_ns()
@@ -137,12 +149,108 @@ __device__ __forceinline__ void load_frame_words(const uint8_t *f, int64_t p0, i
     }
 }
 
-// One warp's tile of G x 128 pixels through the T frames of the clip.
-// cnt_s: the CTA's per-frame counters [CLIP_TMAX][CTL_FIELDS].
+// The mixture stage of one survivor (pixel p, slot `slot` of warp area V)
+// in frame t: Eq. 2 on its record in place (the first touch in the clip
+// saves the original to the undo log), the illumination response when the
+// frame is flagged, the transition update of its stage-1 record, and its
+// confidence; its stage code goes to V.resst.  Kept out of line so that
+// the mixture's registers do not add to the per-frame state the caller
+// keeps live across it.
 template <typename T, int K, int G>
-__device__ __forceinline__ void clip_tile(const ClipArgs &A, ClipWarp<T, G> &W, uint32_t wbase, int lane,
-                                          uint32_t flags, uint32_t *cnt_s)
+__device__ CLIP_S2_INLINE void clip_s2(const ClipArgs &A, ClipWarp<T, G> &V, int64_t p, int slot, bool flag)
 {
+    const DevParams &dp = A.dp;
+    const bool conf_on = dp.flags & COG_CONF;
+    constexpr int SB = S1Rec<T>::BYTES;
+    const uint2 sv = V.stash[slot];
+    uint4 raw[Rec<T, K>::NV];
+    const uint4 *src = reinterpret_cast<const uint4 *>(A.s.gmm + p * Rec<T, K>::BYTES);
+#pragma unroll
+    for (int i = 0; i < Rec<T, K>::NV; i++) raw[i] = src[i];
+    uint32_t qk[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) qk[c] = __ldg(A.s.kde + (p * 3 + c) * 256 + ((sv.x >> (8 * c)) & 0xffu));
+    const uint32_t bit = 1u << (slot & 31);
+    if (!(V.touched[slot >> 5] & bit)) {
+        uint4 *u = reinterpret_cast<uint4 *>(A.undo_gmm + p * Rec<T, K>::BYTES);
+#pragma unroll
+        for (int i = 0; i < Rec<T, K>::NV; i++) u[i] = raw[i];
+        atomicOr(&V.touched[slot >> 5], bit);
+    }
+    const int D = (int)(sv.x >> 24);
+    float I[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) I[c] = (float)((sv.x >> (8 * c)) & 0xffu);
+    const float Cm = __uint_as_float(sv.y);
+    S1Rec<T> r;
+#pragma unroll
+    for (int i = 0; i < S1Rec<T>::NV; i++) r.u[i] = reinterpret_cast<const uint4 *>(V.s1 + slot * SB)[i];
+    const uint32_t qab = r.qab();
+    Mix<K> m;
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        m.w[k] = rec_elem<T, K>(raw, 7 * k);
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            m.mu[k][c] = rec_elem<T, K>(raw, 7 * k + 1 + c);
+            m.v[k][c] = rec_elem<T, K>(raw, 7 * k + 4 + c);
+        }
+    }
+    const float ae = dp.alpha * (1.5f - Cm);
+    const MixOut o = mix_step<K>(m, I, ae, dp);
+    int label = o.fg, st = o.fg ? COG_ST_FG : COG_ST_GMM_BG;
+    if (flag && o.fg) {
+        illum_response<K>(m, o.tgt, dp.w_illum);
+        label = 0;
+        st = COG_ST_ILLUM;
+    }
+    rec_store<T, K>(A.s.gmm, p, m);
+    if (!label) {   // transition update: the background mode seeds stage 1
+        S1Rec<T> rn;
+#pragma unroll
+        for (int i = 0; i < S1Rec<T>::NV; i++) rn.u[i] = make_uint4(0, 0, 0, 0);
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            if (k == o.tgt) {
+#pragma unroll
+                for (int c = 0; c < 3; c++) { rn.set(c, m.mu[k][c]); rn.set(3 + c, m.v[k][c]); }
+            }
+        }
+        rn.set_qab(qab);
+#pragma unroll
+        for (int i = 0; i < S1Rec<T>::NV; i++) reinterpret_cast<uint4 *>(V.s1 + slot * SB)[i] = rn.u[i];
+    }
+    if (conf_on) {
+        uint32_t qmin = qk[0] < qk[1] ? qk[0] : qk[1];
+        qmin = qk[2] < qmin ? qk[2] : qmin;
+        const uint32_t qa = qab & 0xffu, qb = qab >> 8;
+        const float wa = (float)qa * R255, wb = (float)qb * R255;
+        const float wg = (float)(255u - qa - qb) * R255;
+        const float dhat = (float)D * R255;
+        const float Mh = o.match >= 0 ? (o.tm < 1.f ? o.tm : 1.f) : 1.f;
+        float ci;
+        if ((int)qmin < dp.q_null) {
+            const float den = wb + wg;
+            ci = den > 0.f ? (wb * (1.f - dhat) + wg * (1.f - Mh)) / den : 0.f;
+        } else {
+            ci = wa * ((float)qmin * R255) + wb * (1.f - dhat) + wg * (1.f - Mh);
+        }
+        V.resc[slot] = (1.f - dp.eta) * Cm + dp.eta * ci;
+    }
+    V.resst[slot] = (uint8_t)st;
+}
+
+// One CTA tile (NW warps x G x 128 pixels) through the T frames of the
+// clip.  Each warp runs stages 0 and 1 of its own pixels; the survivors of
+// all warps go through the mixture stage together, one per thread; then
+// each warp writes its pixels' outputs.  cnt_s: the CTA's per-frame
+// counters [CLIP_TMAX][CTL_FIELDS].
+template <typename T, int K, int G, int NW>
+__device__ __forceinline__ void clip_tile(const ClipArgs &A, ClipWarp<T, G> *Ws, ClipQueue<NW, G * 128> &Q,
+                                          uint32_t cbase, int warp, int lane, uint32_t flags, uint32_t *cnt_s)
+{
+    ClipWarp<T, G> &W = Ws[warp];
+    const uint32_t wbase = cbase + (uint32_t)warp * (G * 128);
     const DevParams &dp = A.dp;
     const bool conf_on = dp.flags & COG_CONF;
     const bool sampling = (dp.flags & COG_SAMPLE) && conf_on;
@@ -182,7 +290,8 @@ __device__ __forceinline__ void clip_tile(const ClipArgs &A, ClipWarp<T, G> &W, 
         }
     }
     if (lane < WT / 32) W.touched[lane] = 0;
-    __syncwarp();
+    if (threadIdx.x == 0) { Q.n[0] = 0; Q.n[1] = 0; }
+    __syncthreads();
 
     uint32_t nw[G][3];
 #pragma unroll
@@ -247,8 +356,7 @@ __device__ __forceinline__ void clip_tile(const ClipArgs &A, ClipWarp<T, G> &W, 
         }
         __syncwarp();
 
-        // ---- stage 1 over the compacted list
-        int ns = 0;
+        // ---- stage 1 over the compacted list; survivors join the CTA queue
         for (int j0 = 0; j0 < n1w; j0 += 32) {
             const int j = j0 + lane;
             bool surv = false;
@@ -291,96 +399,24 @@ __device__ __forceinline__ void clip_tile(const ClipArgs &A, ClipWarp<T, G> &W, 
                 }
             }
             const uint32_t b = __ballot_sync(0xffffffffu, surv);
-            if (surv) W.surv[ns + __popc(b & lt)] = (uint8_t)slot;
-            ns += __popc(b);
+            uint32_t base = 0;
+            if (lane == 0 && b) base = atomicAdd(&Q.n[t & 1], (uint32_t)__popc(b));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (surv) Q.q[base + __popc(b & lt)] = (uint16_t)((warp << 8) | slot);
         }
-        __syncwarp();
+        __syncthreads();
+        if (threadIdx.x == 0) Q.n[(t + 1) & 1] = 0;   // last read in the previous frame
 
-        // ---- stage 2: mixture step of the survivors, records in place
-        for (int j0 = 0; j0 < ns; j0 += 32) {
-            const int j = j0 + lane;
-            if (j < ns) {
-                const int slot = W.surv[j];
-                const int64_t p = (int64_t)wbase + slot;
-                const uint2 sv = W.stash[slot];
-                uint4 raw[Rec<T, K>::NV];
-                const uint4 *src = reinterpret_cast<const uint4 *>(A.s.gmm + p * Rec<T, K>::BYTES);
-#pragma unroll
-                for (int i = 0; i < Rec<T, K>::NV; i++) raw[i] = src[i];
-                uint32_t qk[3];
-#pragma unroll
-                for (int c = 0; c < 3; c++) qk[c] = __ldg(A.s.kde + (p * 3 + c) * 256 + ((sv.x >> (8 * c)) & 0xffu));
-                const uint32_t bit = 1u << (slot & 31);
-                if (!(W.touched[slot >> 5] & bit)) {
-                    uint4 *u = reinterpret_cast<uint4 *>(A.undo_gmm + p * Rec<T, K>::BYTES);
-#pragma unroll
-                    for (int i = 0; i < Rec<T, K>::NV; i++) u[i] = raw[i];
-                    atomicOr(&W.touched[slot >> 5], bit);
-                }
-                const int D = (int)(sv.x >> 24);
-                float I[3];
-#pragma unroll
-                for (int c = 0; c < 3; c++) I[c] = (float)((sv.x >> (8 * c)) & 0xffu);
-                const float Cm = __uint_as_float(sv.y);
-                S1Rec<T> r;
-#pragma unroll
-                for (int i = 0; i < S1Rec<T>::NV; i++) r.u[i] = reinterpret_cast<const uint4 *>(W.s1 + slot * SB)[i];
-                const uint32_t qab = r.qab();
-                Mix<K> m;
-#pragma unroll
-                for (int k = 0; k < K; k++) {
-                    m.w[k] = rec_elem<T, K>(raw, 7 * k);
-#pragma unroll
-                    for (int c = 0; c < 3; c++) {
-                        m.mu[k][c] = rec_elem<T, K>(raw, 7 * k + 1 + c);
-                        m.v[k][c] = rec_elem<T, K>(raw, 7 * k + 4 + c);
-                    }
-                }
-                const float ae = dp.alpha * (1.5f - Cm);
-                const MixOut o = mix_step<K>(m, I, ae, dp);
-                int label = o.fg, st = o.fg ? COG_ST_FG : COG_ST_GMM_BG;
-                if (flag && o.fg) {
-                    illum_response<K>(m, o.tgt, dp.w_illum);
-                    label = 0;
-                    st = COG_ST_ILLUM;
-                }
-                rec_store<T, K>(A.s.gmm, p, m);
-                if (!label) {   // transition update: the background mode seeds stage 1
-                    S1Rec<T> rn;
-#pragma unroll
-                    for (int i = 0; i < S1Rec<T>::NV; i++) rn.u[i] = make_uint4(0, 0, 0, 0);
-#pragma unroll
-                    for (int k = 0; k < K; k++) {
-                        if (k == o.tgt) {
-#pragma unroll
-                            for (int c = 0; c < 3; c++) { rn.set(c, m.mu[k][c]); rn.set(3 + c, m.v[k][c]); }
-                        }
-                    }
-                    rn.set_qab(qab);
-#pragma unroll
-                    for (int i = 0; i < S1Rec<T>::NV; i++) reinterpret_cast<uint4 *>(W.s1 + slot * SB)[i] = rn.u[i];
-                }
-                if (conf_on) {
-                    uint32_t qmin = qk[0] < qk[1] ? qk[0] : qk[1];
-                    qmin = qk[2] < qmin ? qk[2] : qmin;
-                    const uint32_t qa = qab & 0xffu, qb = qab >> 8;
-                    const float wa = (float)qa * R255, wb = (float)qb * R255;
-                    const float wg = (float)(255u - qa - qb) * R255;
-                    const float dhat = (float)D * R255;
-                    const float Mh = o.match >= 0 ? (o.tm < 1.f ? o.tm : 1.f) : 1.f;
-                    float ci;
-                    if ((int)qmin < dp.q_null) {
-                        const float den = wb + wg;
-                        ci = den > 0.f ? (wb * (1.f - dhat) + wg * (1.f - Mh)) / den : 0.f;
-                    } else {
-                        ci = wa * ((float)qmin * R255) + wb * (1.f - dhat) + wg * (1.f - Mh);
-                    }
-                    W.resc[slot] = (1.f - dp.eta) * Cm + dp.eta * ci;
-                }
-                W.resst[slot] = (uint8_t)st;
+        // ---- stage 2: the CTA's survivors, one per thread, records in place
+        {
+            const uint32_t ns = Q.n[t & 1];
+            for (uint32_t q = threadIdx.x; q < ns; q += NW * 32) {
+                const uint32_t e = Q.q[q];
+                const int slot = (int)(e & 0xffu);
+                clip_s2<T, K, G>(A, Ws[e >> 8], (int64_t)cbase + (e >> 8) * (G * 128) + slot, slot, flag);
             }
         }
-        __syncwarp();
+        __syncthreads();
 
         // ---- outputs of frame t; registers carry the pixels to frame t+1
         uint32_t c_fd = 0, c_rga = 0, c_bg = 0, c_fg = 0, c_il = 0, c_sk = 0;
@@ -489,13 +525,14 @@ __device__ __forceinline__ void clip_restore_tile(const ClipArgs &A, uint32_t wb
 }
 
 template <typename T, int K, int G>
-__global__ void __launch_bounds__(CLIP_TPB) clip_kernel(const ClipArgs A)
+__global__ void __launch_bounds__(CLIP_TPB, CLIP_MINB) clip_kernel(const __grid_constant__ ClipArgs A)
 {
     constexpr int NW = CLIP_TPB / 32;
     extern __shared__ __align__(16) uint8_t clip_smem[];
     ClipWarp<T, G> *W = reinterpret_cast<ClipWarp<T, G> *>(clip_smem);
+    __shared__ ClipQueue<NW, G * 128> Q;
     __shared__ uint32_t cnt_s[CLIP_TMAX * CTL_FIELDS];
-    __shared__ uint32_t flags_s, tile_s[NW], tf_s;
+    __shared__ uint32_t flags_s, tile_s, tf_s;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const DevParams &dp = A.dp;
     uint32_t *ctl = A.s.ctl;
@@ -523,13 +560,14 @@ __global__ void __launch_bounds__(CLIP_TPB) clip_kernel(const ClipArgs A)
             if (tid == 0) A.sync[CLIP_TILE_WORD + 32 * nb] = 0;
         }
         __syncthreads();
-        // ---- the pass: warps take tiles until none is left
+        // ---- the pass: CTAs take tiles until none is left
         for (;;) {
-            uint32_t wt = 0;
-            if (lane == 0) wt = atomicAdd(A.sync + CLIP_TILE_WORD + 32 * bank, 1u);
-            wt = __shfl_sync(0xffffffffu, wt, 0);
-            if (wt >= A.n_tiles) break;
-            clip_tile<T, K, G>(A, W[warp], wt * (uint32_t)(G * 128), lane, flags, cnt_s);
+            if (tid == 0) tile_s = atomicAdd(A.sync + CLIP_TILE_WORD + 32 * bank, 1u);
+            __syncthreads();
+            const uint32_t ct = tile_s;
+            __syncthreads();
+            if (ct >= A.n_tiles) break;
+            clip_tile<T, K, G, NW>(A, W, Q, ct * (uint32_t)(NW * G * 128), warp, lane, flags, cnt_s);
         }
         __syncthreads();
         for (int i = tid; i < (int)A.T * CTL_FIELDS; i += CLIP_TPB)
@@ -558,7 +596,7 @@ __global__ void __launch_bounds__(CLIP_TPB) clip_kernel(const ClipArgs A)
         // frames before the first wrong flag were right; the flag of that
         // frame is now known; later ones take this run's counts as a guess
         flags = tf;
-        for (uint32_t wt = blockIdx.x * NW + warp; wt < A.n_tiles; wt += gridDim.x * NW)
+        for (uint32_t wt = blockIdx.x * NW + warp; wt < A.n_tiles * NW; wt += gridDim.x * NW)
             clip_restore_tile<T, K, G>(A, wt * (uint32_t)(G * 128), lane);
         if (!clip_grid_sync(bar, ++nsync * gridDim.x, err)) return;
     }
@@ -601,29 +639,29 @@ size_t clip_smem_bytes()
     return sizeof(ClipWarp<T, G>) * (CLIP_TPB / 32);
 }
 
+// CTAs of the clip kernel that fit on one SM (asked every launch: a launch
+// covers up to 32 frames, and the answer must match the device current now)
 template <typename T, int K, int G>
 int clip_blocks_per_sm()
 {
-    static int b = -1;
-    if (b < 0) {
-        const size_t sm = clip_smem_bytes<T, K, G>();
-        cudaFuncSetAttribute(clip_kernel<T, K, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, clip_kernel<T, K, G>, CLIP_TPB, sm) != cudaSuccess)
-            b = 0;
-    }
+    int b = 0;
+    const size_t sm = clip_smem_bytes<T, K, G>();
+    if (cudaFuncSetAttribute(clip_kernel<T, K, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, clip_kernel<T, K, G>, CLIP_TPB, sm) != cudaSuccess)
+        b = 0;
     return b;
 }
 
 template <typename T, int K>
 cudaError_t launch_clip_t(const ClipArgs &a0, int n_sm, cudaStream_t st)
 {
-    constexpr int G = 2;
+    constexpr int G = CLIP_G;
+    constexpr int CT = CLIP_TPB / 32 * G * 128;   // pixels per CTA tile
     ClipArgs a = a0;
-    a.n_tiles = (uint32_t)((a.dp.P + G * 128 - 1) / (G * 128));
+    a.n_tiles = (uint32_t)((a.dp.P + CT - 1) / CT);
     const int bps = clip_blocks_per_sm<T, K, G>();
     if (bps < 1) return cudaErrorInvalidConfiguration;
-    const int64_t want = (a.n_tiles + CLIP_TPB / 32 - 1) / (CLIP_TPB / 32);
-    const int grid = (int)min((int64_t)bps * n_sm, max((int64_t)1, want));
+    const int grid = (int)min((int64_t)bps * n_sm, (int64_t)a.n_tiles);
     void *args[] = {(void *)&a};
     return cudaLaunchCooperativeKernel((const void *)clip_kernel<T, K, G>, dim3(grid), dim3(CLIP_TPB), args,
                                        clip_smem_bytes<T, K, G>(), st);
