@@ -223,6 +223,15 @@ static px_out cascade_pixel(const orc_params *pr, orc_state *s, int64_t p,
         o.reached_gmm = 1;
         double r[KMAX];
         int ord[KMAX];
+        /* ORC_MODE1: stage 1's copy of the rank-1 mode flows back into the
+         * mixture on the transition */
+        if (fl & ORC_MODE1) {
+            const int k1 = s->top[p];
+            for (int c = 0; c < 3; c++) {
+                mu[k1 * 3 + c] = rm[c];
+                var[k1 * 3 + c] = rv[c];
+            }
+        }
         /* 1. rank key omega^2 / mean variance, descending, ties by index */
         for (int k = 0; k < K; k++) {
             double vbar = (var[k * 3 + 0] + var[k * 3 + 1] + var[k * 3 + 2]) / 3.0;
@@ -307,8 +316,24 @@ static px_out cascade_pixel(const orc_params *pr, orc_state *s, int64_t p,
             o.stage = ORC_ST_ILLUM;
         }
         /* 6. transition update: the background mode seeds the running
-         *    average (only the active level adapts) */
-        if (label == 0) {
+         *    average (only the active level adapts); with ORC_MODE1 the
+         *    copy follows the mixture's new rank-1 mode, whatever the label */
+        if (fl & ORC_MODE1) {
+            int k1 = 0;
+            double rb = -1.0, r2[KMAX];
+            for (int k = 0; k < K; k++) {
+                double vbar = (var[k * 3 + 0] + var[k * 3 + 1] + var[k * 3 + 2]) / 3.0;
+                r2[k] = w[k] * w[k] / vbar;
+                if (r2[k] > rb) { rb = r2[k]; k1 = k; }
+            }
+            for (int k = 0; k < K; k++)
+                if (k != k1 && r2[k] != rb && fabs(r2[k] - rb) <= NEAR_REL * rb) o.near |= ORC_NEAR_RANK;
+            s->top[p] = (uint8_t)k1;
+            for (int c = 0; c < 3; c++) {
+                rm[c] = mu[k1 * 3 + c];
+                rv[c] = var[k1 * 3 + c];
+            }
+        } else if (label == 0) {
             for (int c = 0; c < 3; c++) {
                 rm[c] = mu[tgt * 3 + c];
                 rv[c] = var[tgt * 3 + c];
@@ -453,6 +478,7 @@ int orc_train_near(const orc_params *pr, const uint8_t *frames, int N, orc_state
             s->rga_m[p * 3 + c] = s->mu[(p * K + best) * 3 + c];
             s->rga_v[p * 3 + c] = s->var[(p * K + best) * 3 + c];
         }
+        s->top[p] = (uint8_t)best;
         s->conf[p] = 0.5;
     }
     s->illum[0] = 0;

@@ -20,7 +20,12 @@
  *   - confidence C = a P + b dI + g M: Sec. 2, "Confidence Measure";
  *   - cascade CHP -> running Gaussian average -> ordered Gaussians, prior
  *     nullified, active-level-only adaptation, illumination counter:
- *     Sec. 2, "Cascade of Gaussians CoG".
+ *     Sec. 2, "Cascade of Gaussians CoG";
+ *   - ORC_MODE1, the Fig. 1 reading of the cascade (CHP -> mode 1 -> the
+ *     other modes): stage 1 tests and adapts a copy of the mixture's
+ *     rank-1 mode; on the transition to stage 2 the copy is written back
+ *     into that mode ("during a transition the parameters are updated",
+ *     Sec. 2), Eq. 2 runs, and the copy then follows the new rank-1 mode.
  * The readings taken where the text is silent or garbled are listed in the
  * repository's design notes and restated beside the code below.
  *
@@ -46,6 +51,7 @@ extern "C" {
 #define ORC_CONF  4u   /* confidence-driven rates, thresholds and halting                */
 #define ORC_ILLUM 8u   /* abrupt-illumination counter and response                       */
 #define ORC_SAMPLE 16u /* confidence-based temporal sampling                             */
+#define ORC_MODE1 32u  /* stage 1 is the mixture's rank-1 mode (Fig. 1 reading)        */
 
 /* near-threshold record bits (one byte per pixel and frame) */
 #define ORC_NEAR_FD    1u  /* D vs tau_fd (0.5 + C)            */
@@ -102,6 +108,8 @@ typedef struct {
     int64_t *illum;  /* [2]          [0]: pixels that reached the GMM stage in
                                      the previous frame; [1]: frames applied
                                      since training                     */
+    uint8_t *top;    /* [P]          with ORC_MODE1: the mixture component the
+                                     running average mirrors            */
 } orc_state;
 
 typedef struct {

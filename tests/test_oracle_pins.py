@@ -490,3 +490,75 @@ def test_sampling_needs_confidence_below_threshold_processed_every_frame():
     for n in range(20):           # C stays below 0.999 for these frames
         _, st, _, _ = o.apply(np.full((1, 3), 90, np.uint8))
         assert st[0] == 0
+
+
+# ------------------------------------------------ stage 1 as the rank-1 mode
+from oracle import ORC_MODE1  # noqa: E402
+
+
+def test_mode1_writes_the_stage1_copy_back_on_the_transition():
+    # hand state: keys .015625 (comp0), .0225 (comp1), .000625 (comp2), so the
+    # rank-1 mode is comp1 (50, 4).  Stage 1 has moved its copy to
+    # (52, 50, 50) / 5.  I = (150, 150, 150) fails stage 1 (t = 98^2 / 31.25)
+    # and matches no mode (comp0: 50^2/100 = 25; comp2: 50^2/400 = 6.25), so
+    # the weights decay, the lowest-ranked comp2 restarts at I, and comp1 --
+    # unmatched -- keeps exactly the written-back copy (52, 50, 50) / 5.
+    # Without the flag it would still read (50, 50, 50) / 4.
+    for flags, mu1, v1 in ((ORC_RGA | ORC_MODE1, [52, 50, 50], 5.0), (ORC_RGA, [50, 50, 50], 4.0)):
+        o = one_pixel(flags=flags, **HAND)
+        _hand_state(o, label=1)
+        o.state.top[0] = 1
+        o.state.rga_m[0] = [52, 50, 50]
+        o.state.rga_v[0] = [5, 5, 5]
+        m, st, _, _ = o.apply(np.array([[150, 150, 150]], np.uint8))
+        assert st[0] == 3 and m[0] == 255
+        assert list(o.state.mu[0, 1]) == mu1 and list(o.state.var[0, 1]) == [v1] * 3
+        assert list(o.state.mu[0, 2]) == [150, 150, 150]
+    # with the flag the copy then follows the new rank-1 mode: weights
+    # (.375, .225, .05)/.65 give keys .333/16, .12/5, .0059/100 -> comp1
+    o = one_pixel(flags=ORC_RGA | ORC_MODE1, **HAND)
+    _hand_state(o, label=1)
+    o.state.top[0] = 1
+    o.state.rga_m[0] = [52, 50, 50]
+    o.state.rga_v[0] = [5, 5, 5]
+    o.apply(np.array([[150, 150, 150]], np.uint8))
+    assert o.state.top[0] == 1
+    assert list(o.state.rga_m[0]) == [52, 50, 50] and list(o.state.rga_v[0]) == [5, 5, 5]
+
+
+def test_mode1_copy_is_the_rank1_mode_after_every_stage2_visit():
+    from cogsynth import Scene
+    W, H, K = 24, 16, 3
+    sc = Scene(W, H, 11, kind="dynamic", n_train=30, fg_frac=0.1, switch_at=20)
+    p = default_params(W, H, K)
+    p["flags"] = ALL | ORC_MODE1
+    o = Oracle(p)
+    tr, _ = sc.frames(0, 30)
+    o.train(tr)
+    s = o.state
+    for t in range(30, 80):
+        f, _ = sc.render(t)
+        _, st, _, _ = o.apply(f)
+        for q in np.nonzero(st >= 2)[0]:
+            key = s.w[q] ** 2 / s.var[q].mean(axis=1)
+            k1 = int(np.argmax(key))            # first maximum = lowest index on ties
+            assert s.top[q] == k1
+            assert np.array_equal(s.rga_m[q], s.mu[q, k1]) and np.array_equal(s.rga_v[q], s.var[q, k1])
+
+
+def test_mode1_alone_is_the_plain_mixture():
+    # with stage 1 off the copy is only ever set from the mixture, so the
+    # write-back is the identity and the result is the plain mixture
+    from cogsynth import Scene
+    sc = Scene(32, 20, 5, kind="dynamic", n_train=25, fg_frac=0.05, switch_at=10)
+    p = default_params(32, 20, 3)
+    p["flags"] = ORC_MODE1
+    o = Oracle(p)
+    tr, _ = sc.frames(0, 25)
+    o.train(tr)
+    w, mu, var = o.state.w.copy(), o.state.mu.copy(), o.state.var.copy()
+    for t in range(25, 60):
+        f, _ = sc.render(t)
+        m1, _, _, _ = o.apply(f)
+        assert np.array_equal(m1, o.plain_gmm(w, mu, var, f))
+        assert np.array_equal(mu, o.state.mu) and np.array_equal(var, o.state.var)
