@@ -221,6 +221,8 @@ def run_ours(args, rank, local_rank, world):
     p_cog = cog.cog_default_params(W_, H_, K_, state_dtype="f16")
     if args.sample:
         p_cog.flags |= cog.COG_SAMPLE
+    if args.mode1:
+        p_cog.flags |= cog.COG_MODE1
     p_gmm = cog.cog_default_params(W_, H_, K_, state_dtype="f16")
     tuned = None
     if args.autotune:
@@ -330,8 +332,9 @@ def run_ours(args, rank, local_rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{W_}x{H_} RGB u8 dynamic-background stream, K={K_}, FP16 state / FP32 math, "
                                    f"{N_TRAIN} train frames, fg {args.fg:.3f}, one frame per step"
-                                   + (", temporal sampling on" if args.sample else ""),
-                       "temporal_sampling": bool(args.sample),
+                                   + (", temporal sampling on" if args.sample else "")
+                                   + (", stage 1 = the mixture's rank-1 mode (Fig. 1 reading)" if args.mode1 else ""),
+                       "temporal_sampling": bool(args.sample), "mode1": bool(args.mode1),
                        "width": W_, "height": H_, "K": K_, "state_dtype": "f16", "n_train": N_TRAIN,
                        "fg_frac": args.fg, "l2": "flushed (512 MB write) between timed steps",
                        "l2_fetch_bytes": args.l2_fetch,
@@ -822,6 +825,8 @@ def main():
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--sample", action="store_true",
                     help="hd: confidence-based temporal sampling on (saturated pixels every 4 frames)")
+    ap.add_argument("--mode1", action="store_true",
+                    help="hd: COG_MODE1, stage 1 as the mixture's rank-1 mode (the Fig. 1 reading)")
     ap.add_argument("--l2-fetch", type=int, default=32,
                     help="L2 fetch granularity in bytes for the process (-1 keeps the driver default)")
     args = ap.parse_args()

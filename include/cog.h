@@ -54,6 +54,11 @@ typedef enum { COG_F32 = 0, COG_F16 = 1, COG_BF16 = 2 } cog_dtype;
 #define COG_CONF  4u  /* confidence-driven learning rate, thresholds and halting        */
 #define COG_ILLUM 8u  /* abrupt-illumination counter and response                       */
 #define COG_SAMPLE 16u /* confidence-based temporal sampling (needs COG_CONF)            */
+#define COG_MODE1 32u  /* stage 1 is a copy of the mixture's rank-1 mode (Fig. 1 reading:
+                          CHP -> mode 1 -> the other modes); on a pixel's transition to
+                          stage 2 the copy is written back into that mode (Sec. 2: the
+                          parameters are updated during a transition), Eq. 2 runs, and
+                          the copy then follows the mode that ranks first            */
 #define COG_ALL   15u /* the cascade: every stage and modulation, no sampling            */
 
 /* Stage codes written to a stage map (the cascade level that labelled the

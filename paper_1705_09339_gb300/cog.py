@@ -20,7 +20,7 @@ COG_OK, COG_ERR_INVALID_ARG, COG_ERR_OOM, COG_ERR_CUDA, COG_ERR_STATE, COG_ERR_T
 STATUS_NAMES = ["COG_OK", "COG_ERR_INVALID_ARG", "COG_ERR_OOM", "COG_ERR_CUDA", "COG_ERR_STATE",
                 "COG_ERR_TIMEOUT", "COG_ERR_DEVICE"]
 COG_F32, COG_F16, COG_BF16 = 0, 1, 2
-COG_FD, COG_RGA, COG_CONF, COG_ILLUM, COG_SAMPLE = 1, 2, 4, 8, 16
+COG_FD, COG_RGA, COG_CONF, COG_ILLUM, COG_SAMPLE, COG_MODE1 = 1, 2, 4, 8, 16, 32
 COG_ALL = 15
 DTYPES = {"f32": COG_F32, "f16": COG_F16, "bf16": COG_BF16}
 
@@ -300,23 +300,26 @@ def _bf16_to_f32(u16: np.ndarray) -> np.ndarray:
 
 
 def _s1_view(buf, L, P, p):
-    """Stage-1 records as (values [P, 6] float64, qab [P] uint16)."""
+    """Stage-1 records as (values [P, 6] float64, qab [P] uint16, top [P]
+    uint8: the mixture component the record mirrors under COG_MODE1)."""
     rb = int(L.s1_bytes)
     raw = buf[L.s1:L.s1 + P * rb].reshape(P, rb)
     if p.state_dtype == COG_F32:
         vals = raw[:, :24].copy().view(np.float32).astype(np.float64)
         qab = raw[:, 24:28].copy().view(np.uint32).reshape(P).astype(np.uint16)
+        top = raw[:, 28].copy()
     else:
         h = raw[:, :12].copy().view(np.uint16)
         vals = (_bf16_to_f32(h) if p.state_dtype == COG_BF16 else h.view(np.float16)).astype(np.float64)
         qab = raw[:, 12:14].copy().view(np.uint16).reshape(P)
-    return vals.reshape(P, 6), qab
+        top = raw[:, 14].copy()
+    return vals.reshape(P, 6), qab, top
 
 
 def decode_state(buf: np.ndarray, p: cog_params) -> dict:
     """FP64 copies of the model planes of an exported state image:
     w [P,K], mu [P,K,3], var [P,K,3], rga_m [P,3], rga_v [P,3], conf [P],
-    label [P], prev [P,3], kde [P,3,256], qa [P], qb [P]."""
+    label [P], prev [P,3], kde [P,3,256], qa [P], qb [P], top [P]."""
     L = cog_state_layout(p)
     P, K = p.width * p.height, p.K
     Pp = (P + 4095) // 4096 * 4096
@@ -330,7 +333,7 @@ def decode_state(buf: np.ndarray, p: cog_params) -> dict:
     prev = np.stack([(jl >> (8 * c)) & 0xFF for c in range(3)], axis=1).astype(np.uint8)
     label = (jl >> 24).astype(np.uint8)
     conf = vals(L.conf, P)
-    s1, qab = _s1_view(buf, L, P, p)
+    s1, qab, top = _s1_view(buf, L, P, p)
     rec_elems = L.rec_bytes // L.elem_bytes
     if p.state_dtype == COG_BF16:
         recs = _bf16_to_f32(_plane(buf, L.gmm, Pp * rec_elems, np.uint16)).astype(np.float64)
@@ -340,7 +343,7 @@ def decode_state(buf: np.ndarray, p: cog_params) -> dict:
     kde = buf[L.kde:L.kde + P * 768].reshape(P, 3, 256)
     return dict(w=recs[:, :, 0].copy(), mu=recs[:, :, 1:4].copy(), var=recs[:, :, 4:7].copy(),
                 rga_m=s1[:, :3].copy(), rga_v=s1[:, 3:].copy(), conf=conf, label=label, prev=prev,
-                kde=kde, qa=(qab & 0xFF).astype(np.uint8), qb=(qab >> 8).astype(np.uint8))
+                kde=kde, qa=(qab & 0xFF).astype(np.uint8), qb=(qab >> 8).astype(np.uint8), top=top)
 
 
 def _to_storage(arr, dtype) -> np.ndarray:
@@ -369,10 +372,13 @@ def encode_state(buf: np.ndarray, p: cog_params, st: dict) -> np.ndarray:
     v = _to_storage(np.concatenate([st["rga_m"], st["rga_v"]], axis=1), p.state_dtype).reshape(P, 6)
     rec[:, :v.itemsize * 6] = v.view(np.uint8).reshape(P, -1)
     qab = st["qa"].astype(np.uint32) | (st["qb"].astype(np.uint32) << 8)
+    top = np.asarray(st.get("top", np.zeros(P)), np.uint8)
     if p.state_dtype == COG_F32:
         rec[:, 24:28] = qab.astype(np.uint32).view(np.uint8).reshape(P, 4)
+        rec[:, 28] = top
     else:
         rec[:, 12:14] = qab.astype(np.uint16).view(np.uint8).reshape(P, 2)
+        rec[:, 14] = top
     out[L.s1:L.s1 + P * rb] = rec.reshape(-1)
     rec_elems = L.rec_bytes // L.elem_bytes
     recs = np.zeros((Pp, rec_elems))

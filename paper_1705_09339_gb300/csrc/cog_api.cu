@@ -127,7 +127,7 @@ static const char *check_params(const cog_params *p)
     if (p->kde_bw < 1 || p->kde_bw > 32) return "kde_bw must be in 1..32";
     if (p->r1 < 0 || p->r2 < p->r1) return "need 0 <= r1 <= r2";
     if (p->illum_permille < 0 || p->illum_permille > 1000) return "illum_permille must be in 0..1000";
-    if (p->flags & ~(COG_ALL | COG_SAMPLE)) return "unknown flag bits";
+    if (p->flags & ~(COG_ALL | COG_SAMPLE | COG_MODE1)) return "unknown flag bits";
     if (p->skip_period < 1) return "skip_period must be >= 1";
     return nullptr;
 }

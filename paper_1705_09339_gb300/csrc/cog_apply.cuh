@@ -329,6 +329,7 @@ template <typename T, int K> struct S2In {
     uint4 e;
     uint4 rec[Rec<T, K>::NV];
     uint32_t qk[3];
+    S1Rec<T> s1;   // COG_MODE1 only: the stage-1 copy of the rank-1 mode
 };
 
 template <typename T, int K>
@@ -341,6 +342,7 @@ __device__ __forceinline__ void s2_load(const ApplyArgs &A, int64_t qi, S2In<T, 
     const uint4 *src = reinterpret_cast<const uint4 *>(A.s.gmm + p * Rec<T, K>::BYTES);
 #pragma unroll
     for (int i = 0; i < Rec<T, K>::NV; i++) in.rec[i] = src[i];
+    if (A.dp.flags & COG_MODE1) in.s1.load(A.s.s1, p);
 }
 
 template <typename T, int K>
@@ -365,6 +367,8 @@ __device__ __forceinline__ int s2_finish(const ApplyArgs &A, const S2In<T, K> &i
             m.v[k][c] = rec_elem<T, K>(in.rec, 7 * k + 4 + c);
         }
     }
+    const bool mode1 = dp.flags & COG_MODE1;
+    if (mode1) mode1_write_back<T, K>(m, in.s1);
     const float ae = dp.alpha * (1.5f - Cm);
     const MixOut o = mix_step<K>(m, I, ae, dp);
     int label = o.fg, st = o.fg ? COG_ST_FG : COG_ST_GMM_BG;
@@ -374,7 +378,11 @@ __device__ __forceinline__ int s2_finish(const ApplyArgs &A, const S2In<T, K> &i
         st = COG_ST_ILLUM;
     }
     rec_store<T, K>(A.s.gmm, p, m);
-    if (!label) {   // transition update: the background mode seeds stage 1
+    if (mode1) {
+        S1Rec<T> r = in.s1;
+        mode1_recache<T, K>(m, r);
+        r.store(A.s.s1, p);
+    } else if (!label) {   // transition update: the background mode seeds stage 1
         S1Rec<T> r;
 #pragma unroll
         for (int i = 0; i < S1Rec<T>::NV; i++) r.u[i] = make_uint4(0, 0, 0, 0);
@@ -556,6 +564,12 @@ int blocks_per_sm(KernT k, int tpb)
     return b;
 }
 
+namespace {
+// Mixture-stage CTAs that fit on one SM, by CTA size (64, 128) and K; one
+// table per translation unit (storage type), filled on first use.
+int k2_occupancy[2][KMAX + 1];
+}
+
 template <typename T, int K>
 cudaError_t launch_apply_t(const ApplyArgs &a, const LaunchCfg &lc, cudaStream_t st, const ApplyEvents *ev)
 {
@@ -564,8 +578,7 @@ cudaError_t launch_apply_t(const ApplyArgs &a, const LaunchCfg &lc, cudaStream_t
     cudaError_t e = launch_pdl(k1_single<T>(lc.k1_tpb), g1, lc.k1_tpb, st, a);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev->e1, st);
-    static int per_sm[2] = {0, 0};      // by mixture-stage CTA size (64, 128)
-    int &ps = per_sm[lc.k2_tpb == 128];
+    int &ps = k2_occupancy[lc.k2_tpb == 128][K];
     if (!ps) ps = blocks_per_sm(k2_single<T, K>(lc.k2_tpb), lc.k2_tpb);
     const int use = lc.k2_per_sm > 0 && lc.k2_per_sm < ps ? lc.k2_per_sm : ps;
     const int64_t need = (a.dp.P + lc.k2_tpb - 1) / lc.k2_tpb;

@@ -196,6 +196,8 @@ __device__ CLIP_S2_INLINE void clip_s2(const ClipArgs &A, ClipWarp<T, G> &V, int
             m.v[k][c] = rec_elem<T, K>(raw, 7 * k + 4 + c);
         }
     }
+    const bool mode1 = dp.flags & COG_MODE1;
+    if (mode1) mode1_write_back<T, K>(m, r);
     const float ae = dp.alpha * (1.5f - Cm);
     const MixOut o = mix_step<K>(m, I, ae, dp);
     int label = o.fg, st = o.fg ? COG_ST_FG : COG_ST_GMM_BG;
@@ -205,7 +207,11 @@ __device__ CLIP_S2_INLINE void clip_s2(const ClipArgs &A, ClipWarp<T, G> &V, int
         st = COG_ST_ILLUM;
     }
     rec_store<T, K>(A.s.gmm, p, m);
-    if (!label) {   // transition update: the background mode seeds stage 1
+    if (mode1) {
+        mode1_recache<T, K>(m, r);
+#pragma unroll
+        for (int i = 0; i < S1Rec<T>::NV; i++) reinterpret_cast<uint4 *>(V.s1 + slot * SB)[i] = r.u[i];
+    } else if (!label) {   // transition update: the background mode seeds stage 1
         S1Rec<T> rn;
 #pragma unroll
         for (int i = 0; i < S1Rec<T>::NV; i++) rn.u[i] = make_uint4(0, 0, 0, 0);

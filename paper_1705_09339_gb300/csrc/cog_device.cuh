@@ -165,8 +165,16 @@ template <typename T> struct S1Rec {
         return Store<T>::bytes == 4 ? u4get(u[NV - 1], 2) : (u[0].w & 0xffffu);
     }
     __device__ __forceinline__ void set_qab(uint32_t q) {
-        if (Store<T>::bytes == 4) { u4set(u[NV - 1], 2, q); u4set(u[NV - 1], 3, 0u); }
-        else u[0].w = q;
+        if (Store<T>::bytes == 4) u4set(u[NV - 1], 2, q);
+        else u[0].w = (u[0].w & 0xffff0000u) | q;
+    }
+    // COG_MODE1: the mixture component this record mirrors
+    __device__ __forceinline__ int top() const {
+        return Store<T>::bytes == 4 ? (int)(u4get(u[NV - 1], 3) & 0xffu) : (int)((u[0].w >> 16) & 0xffu);
+    }
+    __device__ __forceinline__ void set_top(int k) {
+        if (Store<T>::bytes == 4) u4set(u[NV - 1], 3, (uint32_t)k);
+        else u[0].w = (u[0].w & 0x0000ffffu) | ((uint32_t)k << 16);
     }
 };
 
@@ -342,6 +350,37 @@ __device__ __forceinline__ MixOut mix_step(Mix<K> &m, const float I[3], float a,
 #pragma unroll
     for (int k = 0; k < K; k++) m.w[k] = m.w[k] * inv;
     return o;
+}
+
+// COG_MODE1 (the Fig. 1 reading: stage 1 is the mixture's rank-1 mode).
+// On the transition to stage 2 the stage-1 copy is written back into the
+// component it mirrors; after the update the copy follows the component
+// that now ranks first (ties to the lower index), whatever the label.
+template <typename T, int K>
+__device__ __forceinline__ void mode1_write_back(Mix<K> &m, const S1Rec<T> &r)
+{
+    const int k1 = r.top();
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        if (k == k1) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) { m.mu[k][c] = r.get(c); m.v[k][c] = r.get(3 + c); }
+        }
+    }
+}
+template <typename T, int K>
+__device__ __forceinline__ void mode1_recache(const Mix<K> &m, S1Rec<T> &r)
+{
+    int pos[K];
+    rank_positions<K>(m, pos);
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        if (pos[k] == 0) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) { r.set(c, m.mu[k][c]); r.set(3 + c, m.v[k][c]); }
+            r.set_top(k);
+        }
+    }
 }
 
 // Abrupt illumination change (Sec. 2, end of "Cascade of Gaussians"): the

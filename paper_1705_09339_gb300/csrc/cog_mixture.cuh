@@ -135,6 +135,7 @@ __global__ void __launch_bounds__(128) warmup_kernel(const DevParams dp, const S
         if (pos[k] == 0) {
 #pragma unroll
             for (int c = 0; c < 3; c++) { r.set(c, m.mu[k][c]); r.set(3 + c, m.v[k][c]); }
+            r.set_top(k);
         }
     }
     r.set_qab(qa | (qb << 8));

@@ -120,10 +120,10 @@ def state_errors(g, o, mask):
 def oracle_state(o):
     s = o.state
     return dict(w=s.w, mu=s.mu, var=s.var, rga_m=s.rga_m, rga_v=s.rga_v, conf=s.conf, label=s.label,
-                prev=s.prev, kde=s.kde, qa=s.qa, qb=s.qb)
+                prev=s.prev, kde=s.kde, qa=s.qa, qb=s.qb, top=s.top)
 
 
-def random_state(rng, P, K, dtype="f32", fg_frac=0.2):
+def random_state(rng, P, K, dtype="f32", fg_frac=0.2, mode1=False):
     """A seeded model state with the value ranges the method produces,
     rounded to the storage type so both sides start from the same values."""
     q = {"f32": np.float32, "f16": np.float16, "bf16": None}[dtype]
@@ -151,8 +151,15 @@ def random_state(rng, P, K, dtype="f32", fg_frac=0.2):
     kde[rng.random((P, 3, 256)) < 0.3] = rng.integers(0, 13)
     prev = rng.integers(0, 256, (P, 3)).astype(np.uint8)
     label = (rng.random(P) < fg_frac).astype(np.uint8)
-    return dict(w=r(w), mu=r(mu), var=r(var), rga_m=r(rga_m), rga_v=r(rga_v), conf=r(conf),
-                label=label, prev=prev, kde=kde, qa=qa.astype(np.uint8), qb=qb.astype(np.uint8))
+    # COG_MODE1 keeps the stage-1 record equal to the rank-1 mode it mirrors
+    key = w ** 2 / var.mean(axis=2)
+    top = np.argmax(key, axis=1).astype(np.uint8)
+    st = dict(w=r(w), mu=r(mu), var=r(var), rga_m=r(rga_m), rga_v=r(rga_v), conf=r(conf),
+              label=label, prev=prev, kde=kde, qa=qa.astype(np.uint8), qb=qb.astype(np.uint8), top=top)
+    if mode1:
+        st["rga_m"] = st["mu"][np.arange(P), top].copy()
+        st["rga_v"] = st["var"][np.arange(P), top].copy()
+    return st
 
 
 def random_frame(rng, st, mix=(0.4, 0.3, 0.3)):
@@ -174,6 +181,6 @@ def random_frame(rng, st, mix=(0.4, 0.3, 0.3)):
 
 def set_oracle_state(o, st):
     s = o.state
-    for k in ("w", "mu", "var", "rga_m", "rga_v", "conf", "label", "prev", "kde", "qa", "qb"):
+    for k in ("w", "mu", "var", "rga_m", "rga_v", "conf", "label", "prev", "kde", "qa", "qb", "top"):
         getattr(s, k)[...] = st[k]
     s.illum[:] = 0

@@ -63,7 +63,7 @@ def test_default_params_and_layout(cog):
 
 @pytest.mark.parametrize("field,value", [("K", 0), ("K", 9), ("width", 0), ("alpha", 0.0), ("alpha", 1.5),
                                          ("var_min", 0.0), ("kde_bw", 0), ("kde_bw", 33), ("r2", -1),
-                                         ("illum_permille", 1001), ("flags", 32), ("state_dtype", 3), ("skip_period", 0),
+                                         ("illum_permille", 1001), ("flags", 64), ("state_dtype", 3), ("skip_period", 0),
                                          ("w_illum", 1.0), ("T_bg", 1.5)])
 def test_invalid_params_rejected(cog, field, value):
     p = cog.cog_default_params(64, 48, 3)

@@ -93,6 +93,16 @@ def test_accuracy_per_config(name):
     pm, _, _ = p.apply(frames_d[NT:], stats=False, plain=True)
     p.close()
     rep["plain_gmm_f16_misclass_vs_truth"] = _misclass(pm, gt)
+    # the Fig. 1 reading (COG_MODE1): oracle and FP16 GPU, reported
+    o1 = oracle_run(params(W, H, K, flags=15 | 32))
+    o1.train(frames[:NT])
+    m1 = np.stack([o1.apply(frames[NT + t], want_stage=False, want_near=False)[0] for t in range(NF)])
+    g1 = GpuRun(params(W, H, K, flags=15 | 32), "f16")
+    g1.train(frames_d[:NT])
+    gm1, _, _ = g1.apply(frames_d[NT:], stats=False)
+    g1.close()
+    rep["mode1"] = {"oracle_misclass_vs_truth": _misclass(m1, gt), "f16_misclass_vs_truth": _misclass(gm1, gt),
+                    "f16_mask_agreement_with_oracle": float((gm1 == m1).mean())}
     rep["cog_f16_vs_plain_misclass_ratio"] = rep["f16"]["misclass_vs_truth"] / max(1e-12, rep["plain_gmm_f16_misclass_vs_truth"])
     REPORT[name] = rep
     if c["kind"] == "dynamic":

@@ -156,13 +156,13 @@ def test_temporal_sampling_stream_matches_oracle():
 
 # --------------------------------------------------- seeded random states
 @pytest.mark.parametrize("K", [1, 3, 5, 8])
-@pytest.mark.parametrize("flags", [15, 0, 1 | 2, 4 | 8])
+@pytest.mark.parametrize("flags", [15, 0, 1 | 2, 4 | 8, 15 | 32, 2 | 32])
 def test_seeded_state_steps_match_oracle(K, flags):
     rng = np.random.default_rng(100 + K * 16 + flags)
     W, H = 53, 41
     P = W * H
     d = params(W, H, K, flags=flags)
-    st = random_state(rng, P, K)
+    st = random_state(rng, P, K, mode1=bool(flags & 32))
     g = GpuRun(d)
     g.train(np.zeros((2, P, 3), np.uint8))
     g.set_state(st)
@@ -177,11 +177,14 @@ def test_seeded_state_steps_match_oracle(K, flags):
         bad = (gm[0] != om) | (gsm[0] != osm)
         assert not (bad & ~ever).any(), (step, np.nonzero(bad & ~ever)[0][:10])
         assert gst[0]["illum_flag"] == ost["illum_flag"]
-    e = state_errors(g.state(), oracle_state(o), ~ever)
+    gst = g.state()
+    e = state_errors(gst, oracle_state(o), ~ever)
     g.close()
     for k in ("w", "mu", "var", "rga_m", "rga_v", "conf"):
         assert e[k] <= TOL, (k, e[k])
     assert e["label"] == 0 and e["prev"] == 0
+    if flags & 32:
+        assert np.array_equal(gst["top"][~ever], o.state.top[~ever])
 
 
 @pytest.mark.parametrize("dtype,tol", [("f16", 2e-3), ("bf16", 1.6e-2)])
@@ -332,3 +335,16 @@ def test_caller_owned_state_and_host_buffers():
     assert n == 10 and ptr == buf.data_ptr()
     cog.cog_destroy(ctx)
     ref.close()
+
+
+def test_mode1_stream_matches_oracle():
+    # the Fig. 1 reading (stage 1 = the mixture's rank-1 mode, written back on
+    # the transition) on the 160x120 workload, FP32
+    W, H, K = 160, 120, 3
+    (gm, gsm, gst, gs), (om, osm, near, ost, os_) = _stream(W, H, K, 200, 300, "rects", flags=15 | 32)
+    agree, unexplained, ever = compare_stream(gm, gsm, om, osm, near)
+    assert unexplained == 0 and agree >= 0.9999
+    e = state_errors(gs, os_, ~ever)
+    for k in ("w", "mu", "var", "rga_m", "rga_v", "conf"):
+        assert e[k] <= TOL, (k, e[k])
+    assert np.array_equal(gs["top"][~ever], os_["top"][~ever])
