@@ -57,14 +57,12 @@ __device__ __forceinline__ float conf_stage1(uint32_t q, int D, float tr)
 }
 
 // Shared memory of one warp of stage01_kernel: the stage-1 work list and
-// what its pixels need, the results the owners collect, and the warp's
-// survivor queue entries.
+// what its pixels need, and the results the owners collect.
 struct K1Warp {
     uint2 stash[WPX];      // rgb | D << 24, C- bits
     uint8_t list[WPX];     // pixel slot (lane * 4 + i)
     uint8_t resst[WPX];    // 1: decided at stage 1, 2: survivor
     float resc[WPX];       // new C of pixels decided at stage 1
-    uint4 ent[WPX];        // survivor queue entries
 };
 
 // One warp's 128 pixels through stages 0 and 1.  FULL: every pixel of the
@@ -72,7 +70,7 @@ struct K1Warp {
 // warp's survivor count; counts of the pixels decided here are added to
 // n_fd / n_rga (per lane).
 template <typename T, bool FULL>
-__device__ __forceinline__ int k1_warp(const ApplyArgs &A, K1Warp &W, uint32_t wbase, int lane,
+__device__ __forceinline__ int k1_warp(const ApplyArgs &A, K1Warp &W, uint32_t wbase, int lane, uint32_t seg,
                                        uint32_t &n_fd, uint32_t &n_rga, uint32_t &n_skip)
 {
     const DevParams &dp = A.dp;
@@ -208,8 +206,14 @@ __device__ __forceinline__ int k1_warp(const ApplyArgs &A, K1Warp &W, uint32_t w
                 ent = make_uint4(p, sv.x, sv.y, r.qab());
             }
         }
+        // survivors of this pass go straight to the frame's queue segment
         const uint32_t b = __ballot_sync(0xffffffffu, surv);
-        if (surv) W.ent[ne + __popc(b & lt)] = ent;
+        if (b) {
+            uint32_t base = 0;
+            if (lane == 0) base = atomicAdd(A.s.ctl + ctl_qcnt(A.frame_no % 3, seg), (uint32_t)__popc(b));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (surv) A.s.queue[(int64_t)seg * A.s.qseg_cap + base + __popc(b & lt)] = ent;
+        }
         ne += __popc(b);
     }
     __syncwarp();
@@ -283,32 +287,24 @@ __device__ __forceinline__ void k1_cta(const ApplyArgs &A, uint32_t cta)
         }
     }
 
-    uint32_t n_fd = 0, n_rga = 0, n_skip = 0;
-    int ne;
-    if ((int64_t)wbase + WPX <= A.dp.P) ne = k1_warp<T, true>(A, W_s[warp], wbase, lane, n_fd, n_rga, n_skip);
-    else ne = k1_warp<T, false>(A, W_s[warp], wbase, lane, n_fd, n_rga, n_skip);
-
-    // per-warp reservation (padded counters)
+    // warp w puts its survivors into queue segment w % QSEG
     const uint32_t gwarp = cta * NW + warp;
     const uint32_t seg = gwarp & (QSEG - 1);
+    uint32_t n_fd = 0, n_rga = 0, n_skip = 0;
+    int ne;
+    if ((int64_t)wbase + WPX <= A.dp.P) ne = k1_warp<T, true>(A, W_s[warp], wbase, lane, seg, n_fd, n_rga, n_skip);
+    else ne = k1_warp<T, false>(A, W_s[warp], wbase, lane, seg, n_fd, n_rga, n_skip);
+
+    // per-warp counts (padded counters)
     const uint32_t vfd = __reduce_add_sync(0xffffffffu, n_fd);
     const uint32_t vrga = __reduce_add_sync(0xffffffffu, n_rga);
     const uint32_t vskip = __reduce_add_sync(0xffffffffu, n_skip);
-    uint32_t base = 0;
     if (lane == 0) {
         const uint32_t slot = gwarp & (CTL_SLOTS - 1);
         if (vfd) atomicAdd(ctl + ctl_slot(n % 3, 0, slot), vfd);
         if (vrga) atomicAdd(ctl + ctl_slot(n % 3, 1, slot), vrga);
         if (vskip) atomicAdd(ctl + ctl_slot(n % 3, 6, slot), vskip);
-        if (ne) {
-            atomicAdd(ctl + ctl_slot(n % 3, 5, slot), (uint32_t)ne);
-            base = atomicAdd(ctl + ctl_qcnt(n % 3, seg), (uint32_t)ne);
-        }
-    }
-    if (ne) {
-        base = __shfl_sync(0xffffffffu, base, 0);
-        uint4 *q = A.s.queue + seg * A.s.qseg_cap + base;
-        for (int k = lane; k < ne; k += 32) q[k] = W_s[warp].ent[k];
+        if (ne) atomicAdd(ctl + ctl_slot(n % 3, 5, slot), (uint32_t)ne);
     }
 }
 
