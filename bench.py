@@ -128,18 +128,42 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was
-    taken on the current kernel sources; else None."""
+def ncu_counts(kernel: str):
+    """Per-launch ncu counts of the committed summary (DRAM bytes, warp
+    instructions), if they were taken on the current kernel sources."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             d = json.load(f)
         e = d.get(kernel)
         if e and e.get("source_hash") == source_hash():
-            return float(e["dram_bytes_per_launch"])
+            return e
     except Exception:
         pass
     return None
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was
+    taken on the current kernel sources; else None."""
+    e = ncu_counts(kernel)
+    return float(e["dram_bytes_per_launch"]) if e else None
+
+
+# warp-instruction issue peak of the GPU: 152 SMs x 4 schedulers x one warp
+# instruction per clock at the 2070 MHz maximum SM clock
+ISSUE_PEAK = 152 * 4 * 2.070e9
+
+
+def issue_rate(kernel: str, ms_per_launch: float):
+    """Warp instructions per second the kernel issued (ncu count per launch
+    over the live CUDA-event time) against the scheduler peak; None when the
+    committed counts are not for the current sources."""
+    e = ncu_counts(kernel)
+    if not e or "warp_instructions_per_launch" not in e or ms_per_launch <= 0:
+        return None
+    a = float(e["warp_instructions_per_launch"]) / (ms_per_launch / 1e3)
+    return {"achieved": round(a / 1e12, 4), "peak": round(ISSUE_PEAK / 1e12, 4), "unit": "Twarp-inst/s",
+            "frac": round(a / ISSUE_PEAK, 4), "warp_instructions_per_launch": e["warp_instructions_per_launch"]}
 
 
 # ---------------------------------------------------------------- clocks
@@ -344,7 +368,8 @@ def run_ours(args, rank, local_rank, world):
             "roofline": {"bound": "hbm", "achieved": round(ach_d, 1), "peak": hbm, "unit": "GB/s",
                          "frac": round(ach_d / hbm, 4), "traffic": tr_c, "peak_source": hbm_src,
                          "kernel": dom, "ms_per_launch": round(ms_d / args.steps, 5),
-                         "algorithmic_bytes_per_launch": b_d // args.steps},
+                         "algorithmic_bytes_per_launch": b_d // args.steps,
+                         "issue": issue_rate(dom, ms_d / args.steps)},
             "kernels": {"stage01_kernel": {"ms_per_launch": round(ms_k1 / args.steps, 5),
                                            "achieved_gbs": round(ach_1, 1),
                                            "algorithmic_bytes_per_launch": b1 // args.steps},
@@ -509,7 +534,8 @@ def run_clip(args, rank, local_rank, world):
             "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
                          "frac": round(ach / hbm, 4), "traffic": tr, "peak_source": hbm_src,
                          "kernel": "clip_kernel", "ms_per_launch": round(ms_c / args.steps, 5),
-                         "algorithmic_bytes_per_launch": b_clip // args.steps},
+                         "algorithmic_bytes_per_launch": b_clip // args.steps,
+                         "issue": issue_rate("clip_kernel", ms_c / args.steps)},
             "per_frame_cog": {"value": round(job_mpixel_per_s(P, frames, ms_f, world), 1), "unit": UNIT,
                               "ms_per_frame": round(ms_f / frames, 5),
                               "masks_identical_to_clip": same},
