@@ -198,6 +198,18 @@ cog_status cog_apply_clip(cog_ctx *ctx, const uint8_t *frames_dev, int32_t n_fra
  * was mispredicted; 0 before any clip).  Synchronises the stream. */
 cog_status cog_clip_runs(cog_ctx *ctx, int32_t *runs);
 
+/* Self-test of failure detection; the paper has no counterpart.  Runs the
+ * bounded grid-wide wait that cog_apply_clip's barriers use on a count that
+ * nothing completes, with a limit of limit_ms (1..2000) instead of 2 s, on
+ * the current device.  The wait must give up: *error_word receives the
+ * device error bits it set (2 = a grid-wide wait timed out) and
+ * *elapsed_ms the kernel's duration.  Uses two static device words (no
+ * allocation) and its own stream; returns COG_OK when the kernel ran to
+ * completion, COG_ERR_CUDA otherwise, COG_ERR_INVALID_ARG for bad
+ * arguments.  Calls that overlap on one device share the words: serialise
+ * them. */
+cog_status cog_selftest_bounded_wait(int32_t limit_ms, uint32_t *error_word, double *elapsed_ms);
+
 /* The comparison baseline: one frame of the plain Stauffer-Grimson mixture
  * (Eq. 2 at rate alpha, no cascade, no prior, no confidence) on this
  * context's mixture state.  Same buffer rules as cog_apply. */

@@ -72,6 +72,7 @@ def _load() -> C.CDLL:
         "cog_apply": (C.c_int, [vp, vp, vp, vp, P(cog_stats)]),
         "cog_apply_clip": (C.c_int, [vp, vp, i32, vp, vp, P(cog_stats)]),
         "cog_clip_runs": (C.c_int, [vp, P(i32)]),
+        "cog_selftest_bounded_wait": (C.c_int, [i32, P(C.c_uint32), P(C.c_double)]),
         "cog_apply_plain_gmm": (C.c_int, [vp, vp, vp]),
         "cog_apply_host": (C.c_int, [vp, vp, vp]),
         "cog_apply_host_noalloc": (C.c_int, [vp, vp, vp]),
@@ -170,6 +171,14 @@ def cog_clip_runs(ctx) -> int:
     r = C.c_int32(0)
     _check(lib.cog_clip_runs(ctx, C.byref(r)), ctx)
     return r.value
+
+
+def cog_selftest_bounded_wait(limit_ms: int):
+    """Runs the bounded grid-wide wait on a count nothing completes;
+    returns (device error bits it set, kernel milliseconds)."""
+    w, ms = C.c_uint32(0), C.c_double(0.0)
+    _check(lib.cog_selftest_bounded_wait(int(limit_ms), C.byref(w), C.byref(ms)))
+    return w.value, ms.value
 
 
 def cog_apply_plain_gmm(ctx, frame, mask) -> None:

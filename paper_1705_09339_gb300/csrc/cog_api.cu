@@ -29,6 +29,7 @@ cudaError_t launch_batch_bf16(int, const BatchGroupDev &, const LaunchCfg &, uin
 cudaError_t launch_clip_f32(int, const ClipArgs &, int, cudaStream_t);
 cudaError_t launch_clip_f16(int, const ClipArgs &, int, cudaStream_t);
 cudaError_t launch_clip_bf16(int, const ClipArgs &, int, cudaStream_t);
+cudaError_t run_wait_selftest(uint64_t limit_ns, uint32_t *error_word, float *elapsed_ms);
 int k2_blocks_per_sm_f32(int, const LaunchCfg &);
 int k2_blocks_per_sm_f16(int, const LaunchCfg &);
 int k2_blocks_per_sm_bf16(int, const LaunchCfg &);
@@ -484,6 +485,18 @@ cog_status cog_clip_runs(cog_ctx *c, int32_t *runs)
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "cog_clip_runs");
     *runs = (int32_t)v;
+    return COG_OK;
+}
+
+cog_status cog_selftest_bounded_wait(int32_t limit_ms, uint32_t *error_word, double *elapsed_ms)
+{
+    if (limit_ms < 1 || limit_ms > 2000 || !error_word || !elapsed_ms)
+        return set_err(nullptr, COG_ERR_INVALID_ARG, "limit_ms must be in 1..2000 and the outputs non-NULL");
+    float ms = 0.f;
+    *error_word = 0;
+    cudaError_t e = run_wait_selftest((uint64_t)limit_ms * 1000000ull, error_word, &ms);
+    if (e != cudaSuccess) return set_err(nullptr, COG_ERR_CUDA, "bounded-wait self-test: %s", cudaGetErrorString(e));
+    *elapsed_ms = ms;
     return COG_OK;
 }
 

@@ -77,10 +77,12 @@ __device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t *p)
 }
 
 // Grid-wide barrier of a cooperative launch: every CTA arrives once per
-// barrier; `target` = (barriers so far) x gridDim.x.  Gives up after two
-// seconds, sets the device error word and returns false in every thread of
-// the CTA.
-__device__ __forceinline__ bool clip_grid_sync(uint32_t *bar, uint32_t target, uint32_t *err)
+// barrier; `target` = (barriers so far) x gridDim.x.  Gives up after
+// limit_ns (or 2^26 polls), sets DERR_GRID_TIMEOUT in the device error word
+// and returns false in every thread of the CTA.
+constexpr uint64_t CLIP_WAIT_NS = 2000000000ull;
+__device__ __forceinline__ bool clip_grid_sync(uint32_t *bar, uint32_t target, uint32_t *err,
+                                               uint64_t limit_ns = CLIP_WAIT_NS)
 {
     __syncthreads();
     int bad = 0;
@@ -90,7 +92,7 @@ __device__ __forceinline__ bool clip_grid_sync(uint32_t *bar, uint32_t target, u
         const uint64_t t0 = global_ns();
         for (uint32_t it = 0; ld_acquire_gpu(bar) < target; it++) {
             __nanosleep(128);
-            if ((it & 255u) == 0 && (global_ns() - t0 > 2000000000ull || it > (1u << 26))) {
+            if ((it & 255u) == 0 && (global_ns() - t0 > limit_ns || it > (1u << 26))) {
                 atomicOr(err, DERR_GRID_TIMEOUT);
                 bad = 1;
                 break;
@@ -100,6 +102,7 @@ __device__ __forceinline__ bool clip_grid_sync(uint32_t *bar, uint32_t target, u
     }
     return !__syncthreads_or(bad);
 }
+
 
 // Stage 0 of one group of 4 pixels (frame words w0..w2): skip bits, the
 // pixels as rgb words, and the mask of pixels that go on to stage 1.

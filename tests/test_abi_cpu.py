@@ -80,3 +80,8 @@ def test_null_context_calls_fail_cleanly(cog):
     assert cog.lib.cog_apply(None, None, None, None, None) == cog.COG_ERR_INVALID_ARG
     assert cog.lib.cog_apply_clip(None, None, 4, None, None, None) == cog.COG_ERR_INVALID_ARG
     assert cog.lib.cog_clip_runs(None, None) == cog.COG_ERR_INVALID_ARG
+    import ctypes as C
+    w, ms = C.c_uint32(0), C.c_double(0.0)
+    for bad in (0, 2001):
+        assert cog.lib.cog_selftest_bounded_wait(bad, C.byref(w), C.byref(ms)) == cog.COG_ERR_INVALID_ARG
+    assert cog.lib.cog_selftest_bounded_wait(10, None, None) == cog.COG_ERR_INVALID_ARG
