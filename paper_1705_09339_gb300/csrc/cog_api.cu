@@ -895,7 +895,7 @@ cog_status cog_batch_create(cog_ctx *const *ctxs, int32_t n, void *cuda_stream, 
         std::vector<uint32_t> k1(m + 1, 0), k2(m + 1, 0);
         for (int j = 0; j < m; j++) {
             const cog_ctx *c = ctxs[g.members[j]];
-            const int64_t tile = (int64_t)g.launch.k1_tpb * 4;
+            const int64_t tile = (int64_t)g.launch.k1_tpb * K1_PX_PER_THREAD;
             const int64_t t1 = (c->L.P + tile - 1) / tile;
             const int64_t need2 = (c->L.P + g.launch.k2_tpb - 1) / g.launch.k2_tpb;
             int64_t t2 = (int64_t)((double)k2_total * (double)c->L.P / (double)psum + 0.5);

@@ -31,15 +31,19 @@
 
 namespace cog {
 
-constexpr int PPT = 4;         // pixels per thread in stage01_kernel
+constexpr int PPT = 4;         // pixels per group (one 32-bit mask word)
+constexpr int K1_G = K1_PX_PER_THREAD / PPT;   // groups per thread in stage01_kernel
 constexpr int K1_TPB = 128;    // default launch shape (the autotuner may pick others)
 constexpr int K2_TPB = 64;
-constexpr int WPX = 32 * PPT;  // pixels per warp in stage01_kernel
+constexpr int WPX = 32 * PPT * K1_G;   // pixels per warp in stage01_kernel
+static_assert(K1_G * PPT == K1_PX_PER_THREAD && WPX <= 256, "slots of a warp's pixels are bytes");
 // Queue segments: warp w of the first kernel puts up to WPX survivors into
 // segment w % QSEG.  The layout sizes a segment for ceil(CTAs / QSEG) tiles
 // of K1_TILE pixels, which holds every warp that maps to it.
-static_assert(WPX * 32 % K1_TILE == 0, "queue segment sizing assumes 128-pixel warps");
+static_assert(WPX * 32 % K1_TILE == 0, "queue segment sizing assumes whole K1 tiles per segment");
 constexpr float R255 = 1.f / 255.f;
+// Register budget of stage01_kernel: threads per SM it must fit
+constexpr int K1_THREADS_PER_SM = 1280;
 
 // Read the previous frame's counters: illumination flag (lag one frame).
 __device__ __forceinline__ bool illum_flag_prev(const DevParams &dp, const uint32_t *ctl, uint32_t n, int lane)
@@ -65,76 +69,149 @@ struct K1Warp {
     float resc[WPX];       // new C of pixels decided at stage 1
 };
 
-// One warp's 128 pixels through stages 0 and 1.  FULL: every pixel of the
-// warp lies inside the frame (all warps but the last one's).  Returns the
-// warp's survivor count; counts of the pixels decided here are added to
-// n_fd / n_rga (per lane).
+// One group of PPT consecutive pixels of a thread in stage01_kernel: its
+// loaded state, its frame words and its stage-0 outcome.
+template <typename T> struct K1Group {
+    uint4 jl;                 // previous frame + label of the 4 pixels
+    VecN<T, PPT> cv;          // confidence
+    uint32_t Iw[PPT];         // this frame's pixels as r | g << 8 | b << 16
+    uint32_t ad[PPT];         // per-channel |I - J|, byte-wise
+    uint32_t skip, need1;     // bits: skipped by sampling, past stage 0
+    int nact;                 // pixels of the group inside the frame
+};
+
+// Stage-0 loads of one group: previous frame + label (16 B), confidence (8
+// or 16 B), frame bytes (12 B).  With temporal sampling, a 64-pixel block
+// off its phase reads its frame bytes only if some pixel in the group has
+// not saturated (Sec. 2, "Confidence based temporal sampling"; a group of 4
+// never straddles two blocks).
 template <typename T, bool FULL>
-__device__ __forceinline__ int k1_warp(const ApplyArgs &A, K1Warp &W, uint32_t wbase, int lane, uint32_t seg,
-                                       uint32_t &n_fd, uint32_t &n_rga, uint32_t &n_skip)
+__device__ __forceinline__ void k1_group_load(const ApplyArgs &A, K1Group<T> &G, uint32_t p0)
 {
     const DevParams &dp = A.dp;
-    const bool conf_on = dp.flags & COG_CONF;
-    const uint32_t p0 = wbase + (uint32_t)lane * PPT;
-    const int nact = FULL ? PPT : (int)min((int64_t)PPT, max((int64_t)0, dp.P - (int64_t)p0));
-    const uint32_t act_bits = (1u << nact) - 1u;
-
-    // ---- stage-0 loads: previous frame + label (16 B), confidence (8 or
-    //      16 B), frame bytes (12 B).  With temporal sampling, a 64-pixel
-    //      block off its phase reads its frame bytes only if some pixel in
-    //      the group has not saturated (Sec. 2, "Confidence based temporal
-    //      sampling"; a group of 4 never straddles two blocks).
-    uint4 jl = make_uint4(0, 0, 0, 0);
+    G.nact = FULL ? PPT : (int)min((int64_t)PPT, max((int64_t)0, dp.P - (int64_t)p0));
+    G.jl = make_uint4(0, 0, 0, 0);
+    G.skip = 0;
     uint32_t w0 = 0, w1 = 0, w2 = 0;
-    VecN<T, PPT> cv;
-    uint32_t skip = 0;
-    if (FULL || nact > 0) {
-        jl = *reinterpret_cast<const uint4 *>(A.s.jl + p0);
-        cv.load(reinterpret_cast<const T *>(A.s.conf) + p0);
-        const bool sampling = (dp.flags & COG_SAMPLE) && conf_on;
+#pragma unroll
+    for (int i = 0; i < VecN<T, PPT>::NW; i++) G.cv.w[i] = 0;
+    if (FULL || G.nact > 0) {
+        G.jl = *reinterpret_cast<const uint4 *>(A.s.jl + p0);
+        G.cv.load(reinterpret_cast<const T *>(A.s.conf) + p0);
+        const bool sampling = (dp.flags & COG_SAMPLE) && (dp.flags & COG_CONF);
         if (sampling && (A.frame_idx + (p0 >> 6)) % (uint32_t)dp.skip_period != 0u) {
 #pragma unroll
             for (int i = 0; i < PPT; i++)
-                if ((FULL || i < nact) && cv.get(i) >= dp.c_skip) skip |= 1u << i;
+                if ((FULL || i < G.nact) && G.cv.get(i) >= dp.c_skip) G.skip |= 1u << i;
         }
-        if (skip == act_bits) {
+        if (G.skip == (1u << G.nact) - 1u) {
             // every pixel of the group keeps its label this frame
-        } else if (A.frame_al4 && (FULL || nact == PPT)) {
+        } else if (A.frame_al4 && (FULL || G.nact == PPT)) {
             const uint32_t *f4 = reinterpret_cast<const uint32_t *>(A.frame + (size_t)p0 * 3);
             w0 = f4[0]; w1 = f4[1]; w2 = f4[2];
         } else {
             uint32_t fw[3] = {0, 0, 0};
 #pragma unroll
             for (int b3 = 0; b3 < PPT * 3; b3++)
-                if (b3 < nact * 3) fw[b3 >> 2] |= (uint32_t)A.frame[(size_t)p0 * 3 + b3] << ((b3 & 3) * 8);
+                if (b3 < G.nact * 3) fw[b3 >> 2] |= (uint32_t)A.frame[(size_t)p0 * 3 + b3] << ((b3 & 3) * 8);
             w0 = fw[0]; w1 = fw[1]; w2 = fw[2];
         }
     }
-    // the four pixels as (r | g << 8 | b << 16) words, and per-channel
-    // absolute differences to the previous frame (byte-wise)
-    uint32_t Iw[PPT], ad[PPT];
-    Iw[0] = w0 & 0x00ffffffu;
-    Iw[1] = __byte_perm(w0, w1, 0x0543) & 0x00ffffffu;
-    Iw[2] = __byte_perm(w1, w2, 0x0432) & 0x00ffffffu;
-    Iw[3] = w2 >> 8;
-#pragma unroll
-    for (int i = 0; i < PPT; i++) ad[i] = __vabsdiffu4(Iw[i], u4get(jl, i) & 0x00ffffffu);
+    G.Iw[0] = w0 & 0x00ffffffu;
+    G.Iw[1] = __byte_perm(w0, w1, 0x0543) & 0x00ffffffu;
+    G.Iw[2] = __byte_perm(w1, w2, 0x0432) & 0x00ffffffu;
+    G.Iw[3] = w2 >> 8;
+}
 
-    // ---- stage 0: D = max_c |I_c - J_c| <= tau_fd (0.5 + C-) on a
-    //      background pixel.  D is an integer, so the test is D <= floor(tau)
-    //      applied to every channel at once.
-    uint32_t need1 = 0;
+// Stage 0 of one group: D = max_c |I_c - J_c| <= tau_fd (0.5 + C-) on a
+// background pixel.  D is an integer, so the test is D <= floor(tau)
+// applied to every channel at once.
+template <typename T, bool FULL>
+__device__ __forceinline__ void k1_group_stage0(const DevParams &dp, K1Group<T> &G)
+{
+    const bool conf_on = dp.flags & COG_CONF;
     const bool fd_on = dp.flags & COG_FD;
 #pragma unroll
+    for (int i = 0; i < PPT; i++) G.ad[i] = __vabsdiffu4(G.Iw[i], u4get(G.jl, i) & 0x00ffffffu);
+    G.need1 = 0;
+#pragma unroll
     for (int i = 0; i < PPT; i++) {
-        if ((!FULL && i >= nact) || (skip >> i & 1u)) continue;
-        const float Cm = conf_on ? cv.get(i) : 0.5f;
+        if ((!FULL && i >= G.nact) || (G.skip >> i & 1u)) continue;
+        const float Cm = conf_on ? G.cv.get(i) : 0.5f;
         const float tau = dp.tau_fd * (0.5f + Cm);
         const uint32_t t = tau >= 255.f ? 255u : (uint32_t)tau;      // floor, tau >= 0
-        const bool pass = fd_on && (u4get(jl, i) >> 24) == 0 && __vcmpgtu4(ad[i], t * 0x01010101u) == 0u;
-        if (!pass) need1 |= 1u << i;
+        const bool pass = fd_on && (u4get(G.jl, i) >> 24) == 0 && __vcmpgtu4(G.ad[i], t * 0x01010101u) == 0u;
+        if (!pass) G.need1 |= 1u << i;
     }
-    const int n1 = __popc(need1);
+}
+
+// Outputs of one group: the previous frame becomes this frame with label 0
+// (the mixture stage sets its survivors' labels), the mask 0 (likewise),
+// the confidence of the pixels decided here; a pixel skipped by the
+// temporal sampling keeps everything and shows its carried label.
+template <typename T, bool FULL>
+__device__ __forceinline__ void k1_group_out(const ApplyArgs &A, const K1Warp &W, const K1Group<T> &G, uint32_t p0,
+                                             int slot0, uint32_t &n_fd, uint32_t &n_skip)
+{
+    const DevParams &dp = A.dp;
+    const bool conf_on = dp.flags & COG_CONF;
+    if (!(FULL || G.nact > 0)) return;
+    uint4 jn;
+    uint32_t sm = 0, mk = 0;
+    VecN<T, PPT> cn = G.cv;
+    bool any_c = false;
+#pragma unroll
+    for (int i = 0; i < PPT; i++) {
+        const bool act = FULL || i < G.nact;
+        const bool sk = G.skip >> i & 1u;
+        const uint32_t r1 = (G.need1 >> i & 1u) ? W.resst[slot0 + i] : 0u;
+        n_fd += act && !sk && r1 == 0;
+        n_skip += sk;
+        if (conf_on && act && !sk && r1 != 2) {
+            cn.set(i, r1 == 0 ? (1.f - dp.eta) * G.cv.get(i) + dp.eta : W.resc[slot0 + i]);
+            any_c = true;
+        }
+        u4set(jn, i, act && !sk ? G.Iw[i] : u4get(G.jl, i));
+        if (sk) mk |= ((u4get(G.jl, i) >> 24) ? 255u : 0u) << (8 * i);
+        sm |= (sk ? (uint32_t)COG_ST_SKIP
+                  : (r1 == 0 ? (uint32_t)COG_ST_FD : (r1 == 1 ? (uint32_t)COG_ST_RGA : (uint32_t)COG_ST_GMM_BG)))
+              << (8 * i);
+    }
+    if (jn.x != G.jl.x || jn.y != G.jl.y || jn.z != G.jl.z || jn.w != G.jl.w)
+        *reinterpret_cast<uint4 *>(A.s.jl + p0) = jn;
+    if (any_c) cn.store(reinterpret_cast<T *>(A.s.conf) + p0);
+    if ((FULL || G.nact == PPT) && A.out_al4) {
+        *reinterpret_cast<uint32_t *>(A.mask + p0) = mk;
+        if (A.stagemap) *reinterpret_cast<uint32_t *>(A.stagemap + p0) = sm;
+    } else {
+        for (int i = 0; i < G.nact; i++) {
+            A.mask[p0 + i] = (uint8_t)(mk >> (8 * i));
+            if (A.stagemap) A.stagemap[p0 + i] = (uint8_t)(sm >> (8 * i));
+        }
+    }
+}
+
+// One warp's WPX pixels (K1_G groups of 128: each lane owns 4 consecutive
+// pixels of every group) through stages 0 and 1.  FULL: every pixel of the
+// warp lies inside the frame (all warps but the last one's).  Returns the
+// warp's survivor count; counts of the pixels decided here are added to
+// n_fd / n_rga / n_skip (per lane).
+template <typename T, bool FULL>
+__device__ __forceinline__ int k1_warp(const ApplyArgs &A, K1Warp &W, uint32_t wbase, int lane, uint32_t seg,
+                                       uint32_t &n_fd, uint32_t &n_rga, uint32_t &n_skip)
+{
+    const DevParams &dp = A.dp;
+    const bool conf_on = dp.flags & COG_CONF;
+    K1Group<T> grp[K1_G];
+#pragma unroll
+    for (int g = 0; g < K1_G; g++) k1_group_load<T, FULL>(A, grp[g], wbase + g * 128 + (uint32_t)lane * PPT);
+#pragma unroll
+    for (int g = 0; g < K1_G; g++) k1_group_stage0<T, FULL>(dp, grp[g]);
+
+    // ---- the stage-1 work list of the warp
+    int n1 = 0;
+#pragma unroll
+    for (int g = 0; g < K1_G; g++) n1 += __popc(grp[g].need1);
     int incl = n1;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
@@ -142,16 +219,21 @@ __device__ __forceinline__ int k1_warp(const ApplyArgs &A, K1Warp &W, uint32_t w
         if (lane >= off) incl += t;
     }
     const int n1w = __shfl_sync(0xffffffffu, incl, 31);
-    if (need1) {
+    {
         int k = incl - n1;
 #pragma unroll
-        for (int i = 0; i < PPT; i++) {
-            if (!(need1 >> i & 1u)) continue;
-            const int slot = lane * PPT + i;
-            W.list[k++] = (uint8_t)slot;
-            const uint32_t m2 = __vmaxu4(ad[i], ad[i] >> 8);
-            const uint32_t D = __vmaxu4(m2, m2 >> 8) & 0xffu;
-            W.stash[slot] = make_uint2(Iw[i] | (D << 24), __float_as_uint(conf_on ? cv.get(i) : 0.5f));
+        for (int g = 0; g < K1_G; g++) {
+            if (!grp[g].need1) continue;
+#pragma unroll
+            for (int i = 0; i < PPT; i++) {
+                if (!(grp[g].need1 >> i & 1u)) continue;
+                const int slot = g * 128 + lane * PPT + i;
+                W.list[k++] = (uint8_t)slot;
+                const uint32_t m2 = __vmaxu4(grp[g].ad[i], grp[g].ad[i] >> 8);
+                const uint32_t D = __vmaxu4(m2, m2 >> 8) & 0xffu;
+                W.stash[slot] = make_uint2(grp[g].Iw[i] | (D << 24),
+                                           __float_as_uint(conf_on ? grp[g].cv.get(i) : 0.5f));
+            }
         }
     }
     __syncwarp();
@@ -218,45 +300,9 @@ __device__ __forceinline__ int k1_warp(const ApplyArgs &A, K1Warp &W, uint32_t w
     }
     __syncwarp();
 
-    // ---- outputs: the previous frame becomes this frame with label 0 (the
-    //      mixture stage sets its survivors' labels), the mask 0 (likewise),
-    //      the confidence of the pixels decided here; a pixel skipped by the
-    //      temporal sampling keeps everything and shows its carried label
-    if (FULL || nact > 0) {
-        uint4 jn;
-        uint32_t sm = 0, mk = 0;
-        VecN<T, PPT> cn = cv;
-        bool any_c = false;
 #pragma unroll
-        for (int i = 0; i < PPT; i++) {
-            const bool act = FULL || i < nact;
-            const bool sk = skip >> i & 1u;
-            const uint32_t r1 = (need1 >> i & 1u) ? W.resst[lane * PPT + i] : 0u;
-            n_fd += act && !sk && r1 == 0;
-            n_skip += sk;
-            if (conf_on && act && !sk && r1 != 2) {
-                cn.set(i, r1 == 0 ? (1.f - dp.eta) * cv.get(i) + dp.eta : W.resc[lane * PPT + i]);
-                any_c = true;
-            }
-            u4set(jn, i, act && !sk ? Iw[i] : u4get(jl, i));
-            if (sk) mk |= ((u4get(jl, i) >> 24) ? 255u : 0u) << (8 * i);
-            sm |= (sk ? (uint32_t)COG_ST_SKIP
-                      : (r1 == 0 ? (uint32_t)COG_ST_FD : (r1 == 1 ? (uint32_t)COG_ST_RGA : (uint32_t)COG_ST_GMM_BG)))
-                  << (8 * i);
-        }
-        if (jn.x != jl.x || jn.y != jl.y || jn.z != jl.z || jn.w != jl.w)
-            *reinterpret_cast<uint4 *>(A.s.jl + p0) = jn;
-        if (any_c) cn.store(reinterpret_cast<T *>(A.s.conf) + p0);
-        if ((FULL || nact == PPT) && A.out_al4) {
-            *reinterpret_cast<uint32_t *>(A.mask + p0) = mk;
-            if (A.stagemap) *reinterpret_cast<uint32_t *>(A.stagemap + p0) = sm;
-        } else {
-            for (int i = 0; i < nact; i++) {
-                A.mask[p0 + i] = (uint8_t)(mk >> (8 * i));
-                if (A.stagemap) A.stagemap[p0 + i] = (uint8_t)(sm >> (8 * i));
-            }
-        }
-    }
+    for (int g = 0; g < K1_G; g++)
+        k1_group_out<T, FULL>(A, W, grp[g], wbase + g * 128 + (uint32_t)lane * PPT, g * 128 + lane * PPT, n_fd, n_skip);
     return ne;
 }
 
@@ -264,13 +310,13 @@ __device__ __forceinline__ int k1_warp(const ApplyArgs &A, K1Warp &W, uint32_t w
 template <typename T, int TPB>
 __device__ __forceinline__ void k1_cta(const ApplyArgs &A, uint32_t cta)
 {
-    static_assert(PPT == 4, "frame and mask vector widths assume 4 pixels per thread");
+    static_assert(PPT == 4, "frame and mask vector widths assume groups of 4 pixels");
     constexpr int NW = TPB / 32;
     __shared__ K1Warp W_s[NW];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t n = A.frame_no;
     uint32_t *ctl = A.s.ctl;
-    const uint32_t wbase = (cta * TPB + warp * 32) * PPT;
+    const uint32_t wbase = (cta * NW + warp) * WPX;
 
     if (cta == 0) {
         // rotate the per-frame counters: clear frame n+1's, add frame n-1's
@@ -309,7 +355,7 @@ __device__ __forceinline__ void k1_cta(const ApplyArgs &A, uint32_t cta)
 }
 
 template <typename T, int TPB>
-__global__ void __launch_bounds__(TPB, 1280 / TPB) stage01_kernel(const ApplyArgs A)
+__global__ void __launch_bounds__(TPB, K1_THREADS_PER_SM / TPB) stage01_kernel(const ApplyArgs A)
 {
     // programmatic dependent launch: let the mixture stage's CTAs be
     // scheduled as this grid drains, and wait for the previous frame's
@@ -490,7 +536,7 @@ __device__ __forceinline__ int batch_stream(const uint32_t *pre, int n, uint32_t
 }
 
 template <typename T, int TPB>
-__global__ void __launch_bounds__(TPB, 1280 / TPB) stage01_batch_kernel(const BatchGroupDev G)
+__global__ void __launch_bounds__(TPB, K1_THREADS_PER_SM / TPB) stage01_batch_kernel(const BatchGroupDev G)
 {
     grid_launch_dependents();
     grid_wait_prior();
@@ -569,7 +615,7 @@ int k2_occupancy[2][KMAX + 1];
 template <typename T, int K>
 cudaError_t launch_apply_t(const ApplyArgs &a, const LaunchCfg &lc, cudaStream_t st, const ApplyEvents *ev)
 {
-    const int64_t g1 = (a.dp.P + lc.k1_tpb * PPT - 1) / (lc.k1_tpb * PPT);
+    const int64_t g1 = (a.dp.P + lc.k1_tpb * K1_PX_PER_THREAD - 1) / (lc.k1_tpb * K1_PX_PER_THREAD);
     if (ev) cudaEventRecord(ev->e0, st);
     cudaError_t e = launch_pdl(k1_single<T>(lc.k1_tpb), g1, lc.k1_tpb, st, a);
     if (e != cudaSuccess) return e;

@@ -33,7 +33,8 @@ constexpr int CTL_SLOTS = 32;
 constexpr int CTL_FIELDS = 8;
 constexpr int CTL_PAD = 32;
 constexpr int QSEG = 32;                            // survivor-queue segments
-constexpr int K1_TILE = 1024;                       // pixels per CTA of the stage-0/1 kernel
+constexpr int K1_TILE = 1024;                       // queue sizing unit: pixels of a 128-thread CTA
+constexpr int K1_PX_PER_THREAD = 4;                 // pixels per thread of the stage-0/1 kernel
 __host__ __device__ constexpr int ctl_slot(int buf, int f, int s)
 {
     return ((buf * CTL_FIELDS + f) * CTL_SLOTS + s) * CTL_PAD;
