@@ -222,6 +222,18 @@ cog_status cog_apply_plain_gmm(cog_ctx *ctx, const uint8_t *frame_dev, uint8_t *
  * allocates two device staging buffers that the context keeps. */
 cog_status cog_apply_host(cog_ctx *ctx, const uint8_t *frame_host, uint8_t *mask_host);
 
+/* n_frames consecutive frames from host memory (frames_host: n_frames x
+ * height x width x 3 bytes; masks_host: n_frames x height x width bytes),
+ * each through the cascade as cog_apply, with the transfers pipelined: the
+ * upload of the next frame and the download of the previous mask run on the
+ * context's own copy streams while the current frame's kernels run, through
+ * two device slots.  Results are those of n_frames cog_apply_host calls.
+ * Page-locked host buffers let the copies overlap; pageable ones work.  The
+ * first call allocates the slots (2 x (4 bytes per pixel)) and creates two
+ * streams and six events that the context keeps.  Returns when every mask
+ * is in masks_host. */
+cog_status cog_apply_host_frames(cog_ctx *ctx, const uint8_t *frames_host, int32_t n_frames, uint8_t *masks_host);
+
 /* cog_apply_host for callers that cannot allocate device memory: the
  * paper has no counterpart; this is a deployment form of the same call.
  * Some hosts must not call cudaMalloc or cudaFree at all: a frame server or

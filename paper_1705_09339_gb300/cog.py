@@ -76,6 +76,7 @@ def _load() -> C.CDLL:
         "cog_apply_plain_gmm": (C.c_int, [vp, vp, vp]),
         "cog_apply_host": (C.c_int, [vp, vp, vp]),
         "cog_apply_host_noalloc": (C.c_int, [vp, vp, vp]),
+        "cog_apply_host_frames": (C.c_int, [vp, vp, i32, vp]),
         "cog_read_stats": (C.c_int, [vp, P(cog_stats), P(cog_stats)]),
         "cog_sync": (C.c_int, [vp]),
         "cog_export_state": (C.c_int, [vp, vp, sz]),
@@ -189,6 +190,14 @@ def cog_apply_host(ctx, frame: np.ndarray, mask: np.ndarray) -> None:
     assert frame.dtype == np.uint8 and mask.dtype == np.uint8
     assert frame.flags.c_contiguous and mask.flags.c_contiguous
     _check(lib.cog_apply_host(ctx, frame.ctypes.data, mask.ctypes.data), ctx)
+
+
+def cog_apply_host_frames(ctx, frames: np.ndarray, masks: np.ndarray) -> None:
+    """frames [n, H, W, 3] and masks [n, H, W] in host memory (pinned for
+    overlap); copies pipelined with the kernels."""
+    assert frames.dtype == np.uint8 and masks.dtype == np.uint8
+    assert frames.flags.c_contiguous and masks.flags.c_contiguous and frames.shape[0] == masks.shape[0]
+    _check(lib.cog_apply_host_frames(ctx, frames.ctypes.data, int(frames.shape[0]), masks.ctypes.data), ctx)
 
 
 def cog_apply_host_noalloc(ctx, frame: np.ndarray, mask: np.ndarray) -> None:

@@ -87,6 +87,11 @@ struct cog_ctx {
     int64_t prof_n;                  // frames recorded since profiling was enabled
     uint8_t *clip_mem;               // cog_apply_clip scratch (allocated on first use)
     size_t clip_bytes;
+    // cog_apply_host_frames pipeline (created on first use): two frame and
+    // two mask slots, an upload and a download stream, and per-slot events
+    uint8_t *pipe_mem;
+    cudaStream_t pipe_in, pipe_out;
+    cudaEvent_t ev_in[2], ev_done[2], ev_out[2];
 };
 
 static thread_local char g_create_err[512];
@@ -615,6 +620,60 @@ cog_status cog_apply_host_noalloc(cog_ctx *c, const uint8_t *frame_host, uint8_t
     return COG_OK;
 }
 
+// Frames from host memory, pipelined: the upload of frame i+1 and the
+// download of mask i-1 run on their own streams while frame i's kernels run
+// on the context's stream; events order each slot's reuse.
+cog_status cog_apply_host_frames(cog_ctx *c, const uint8_t *frames_host, int32_t n_frames, uint8_t *masks_host)
+{
+    cog_status s = check_ctx(c);
+    if (s) return s;
+    if (!c->trained) return set_err(c, COG_ERR_STATE, "cog_apply_host_frames before cog_train_prior");
+    if (!frames_host || !masks_host) return set_err(c, COG_ERR_INVALID_ARG, "frames_host and masks_host are required");
+    if (n_frames < 1) return set_err(c, COG_ERR_INVALID_ARG, "n_frames must be >= 1");
+    const size_t P = (size_t)c->L.P;
+    const size_t fb = up(P * 3, 256), mb = up(P, 256);
+    cudaError_t e;
+    if (!c->pipe_mem) {
+        e = cudaMalloc((void **)&c->pipe_mem, 2 * (fb + mb));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            c->pipe_mem = nullptr;
+            return set_err(c, COG_ERR_OOM, "pipeline staging allocation: %s", cudaGetErrorString(e));
+        }
+        bool ok = cudaStreamCreateWithFlags(&c->pipe_in, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&c->pipe_out, cudaStreamNonBlocking) == cudaSuccess;
+        for (int i = 0; i < 2 && ok; i++)
+            ok = cudaEventCreateWithFlags(&c->ev_in[i], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&c->ev_done[i], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&c->ev_out[i], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) return cuda_fail(c, cudaGetLastError(), "pipeline streams/events");
+    }
+    uint8_t *fslot[2] = {c->pipe_mem, c->pipe_mem + fb};
+    uint8_t *mslot[2] = {c->pipe_mem + 2 * fb, c->pipe_mem + 2 * fb + mb};
+    for (int32_t i = 0; i < n_frames; i++) {
+        const int k = i & 1;
+        if (i >= 2) e = cudaStreamWaitEvent(c->pipe_in, c->ev_done[k], 0);    // slot read by frame i-2
+        else e = cudaSuccess;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(fslot[k], frames_host + (size_t)i * P * 3, P * 3, cudaMemcpyHostToDevice, c->pipe_in);
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev_in[k], c->pipe_in);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->ev_in[k], 0);
+        if (e == cudaSuccess && i >= 2) e = cudaStreamWaitEvent(c->stream, c->ev_out[k], 0);   // mask slot copied out
+        if (e != cudaSuccess) return cuda_fail(c, e, "cog_apply_host_frames upload");
+        if ((s = cog_apply(c, fslot[k], mslot[k], nullptr, nullptr)) != COG_OK) return s;
+        e = cudaEventRecord(c->ev_done[k], c->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->pipe_out, c->ev_done[k], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(masks_host + (size_t)i * P, mslot[k], P, cudaMemcpyDeviceToHost, c->pipe_out);
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev_out[k], c->pipe_out);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cog_apply_host_frames download");
+    }
+    e = cudaStreamSynchronize(c->pipe_out);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cog_apply_host_frames sync");
+    return COG_OK;
+}
+
 cog_status cog_read_stats(cog_ctx *c, cog_stats *last, cog_stats *total)
 {
     cog_status s = check_ctx(c);
@@ -781,6 +840,18 @@ cog_status cog_destroy(cog_ctx *c)
     free_profile(c);
     if (c->stage_in) cudaFree(c->stage_in);
     if (c->clip_mem) cudaFree(c->clip_mem);
+    if (c->pipe_mem) {
+        cudaStreamSynchronize(c->pipe_in);
+        cudaStreamSynchronize(c->pipe_out);
+        cudaFree(c->pipe_mem);
+        for (int i = 0; i < 2; i++) {
+            cudaEventDestroy(c->ev_in[i]);
+            cudaEventDestroy(c->ev_done[i]);
+            cudaEventDestroy(c->ev_out[i]);
+        }
+        cudaStreamDestroy(c->pipe_in);
+        cudaStreamDestroy(c->pipe_out);
+    }
     if (c->owns) cudaFree(c->state);
     delete c;
     return s;

@@ -337,6 +337,37 @@ def test_caller_owned_state_and_host_buffers():
     ref.close()
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_frames_pipeline_equals_device_apply(pinned):
+    # cog_apply_host_frames overlaps uploads and downloads with the kernels
+    # through two device slots; results must equal cog_apply on device
+    # buffers frame by frame (also with a light switch inside the run)
+    from cogsynth import Scene
+    from paper_1705_09339_gb300 import cog
+    W, H, K, NT, NF = 320, 240, 5, 40, 37
+    sc = Scene(W, H, 7, kind="dynamic", n_train=NT, fg_frac=0.05, switch_at=20)
+    fr, _ = sc.frames(0, NT + NF)
+    d = params(W, H, K)
+    ref = GpuRun(d, "f16")
+    ref.train(fr[:NT])
+    rm, _, _ = ref.apply(fr[NT:])
+    g = GpuRun(d, "f16")
+    g.train(fr[:NT])
+    host = torch.from_numpy(np.ascontiguousarray(fr[NT:]).reshape(NF, H, W, 3))
+    masks = torch.zeros((NF, H, W), dtype=torch.uint8)
+    if pinned:
+        host, masks = host.pin_memory(), masks.pin_memory()
+    cog.cog_apply_host_frames(g.ctx, host.numpy(), masks.numpy())
+    assert np.array_equal(masks.numpy().reshape(NF, -1), rm)
+    sa, sb = ref.state(), g.state()
+    for k in sa:
+        assert np.array_equal(sa[k], sb[k]), k
+    # a second call continues the same stream
+    cog.cog_apply_host_frames(g.ctx, host.numpy()[:5].copy(), masks.numpy()[:5].copy())
+    assert cog.cog_info(g.ctx)[0] == NF + 5
+    ref.close(); g.close()
+
+
 def test_mode1_stream_matches_oracle():
     # the Fig. 1 reading (stage 1 = the mixture's rank-1 mode, written back on
     # the transition) on the 160x120 workload, FP32
