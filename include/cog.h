@@ -198,6 +198,41 @@ cog_status cog_apply_clip(cog_ctx *ctx, const uint8_t *frames_dev, int32_t n_fra
  * was mispredicted; 0 before any clip).  Synchronises the stream. */
 cog_status cog_clip_runs(cog_ctx *ctx, int32_t *runs);
 
+/* Native continuous-batching frame server; the paper has no counterpart
+ * (a deployment form of the batched step).  n trained contexts become the
+ * server's streams: while it exists they belong to it (call nothing else
+ * on them).  It allocates two device frame slots and two mask slots per
+ * stream, a batch over the contexts (cog_batch_create) and three streams,
+ * and starts a worker and a completion thread.
+ *   cog_server_submit: queues one frame of stream `stream` from host memory
+ *     (height x width x 3 bytes; page-locked for overlap) and the host
+ *     buffer that receives its mask; both must stay valid until the frame
+ *     is done (cog_server_drain).  Thread-safe; returns at once.
+ *   The worker takes, for every stream with a frame waiting and a free
+ *   slot, the oldest frame; uploads them; runs one batched step over those
+ *   streams only; downloads their masks.  Frames submitted meanwhile join
+ *   the next step, whose uploads overlap the running one.
+ *   cog_server_drain: waits up to timeout_ms until every submitted frame is
+ *     done; COG_ERR_TIMEOUT otherwise.
+ *   cog_server_read_stats: counts and the p50/p99/max latency from submission
+ *     to the mask being in host memory, and the seconds since creation.
+ *   cog_server_destroy: stops the threads; frames not yet started are
+ *     dropped (drain first to keep them).  Errors are sticky. */
+typedef struct cog_server cog_server;
+typedef struct {
+    int64_t submitted, frames, steps, pixels;
+    double p50_ms, p99_ms, max_ms, wall_s;
+} cog_server_stats;
+cog_status cog_server_create(cog_ctx *const *ctxs, int32_t n, cog_server **out);
+cog_status cog_server_submit(cog_server *s, int32_t stream, const uint8_t *frame_host, uint8_t *mask_host);
+cog_status cog_server_drain(cog_server *s, int32_t timeout_ms);
+cog_status cog_server_read_stats(cog_server *s, cog_server_stats *out);
+/* Per-frame record in completion order: submission time since creation and
+ * latency, both in ms; copies min(cap, done) entries, *n = frames done. */
+cog_status cog_server_read_latencies(cog_server *s, float *submit_ms, float *latency_ms, int64_t cap, int64_t *n);
+const char *cog_server_last_error_string(cog_server *s);
+cog_status cog_server_destroy(cog_server *s);
+
 /* Self-test of failure detection; the paper has no counterpart.  Runs the
  * bounded grid-wide wait that cog_apply_clip's barriers use on a count that
  * nothing completes, with a limit of limit_ms (1..2000) instead of 2 s, on

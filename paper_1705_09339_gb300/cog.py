@@ -46,6 +46,14 @@ class cog_stats(C.Structure):
                     frame=int(self.frame))
 
 
+class cog_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("frames", C.c_int64), ("steps", C.c_int64), ("pixels", C.c_int64),
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("max_ms", C.c_double), ("wall_s", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
 class cog_layout(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in ("total", "ctl", "jl", "conf", "s1", "s1_bytes", "gmm", "rec_bytes",
                                           "queue", "kde", "elem_bytes")]
@@ -94,6 +102,13 @@ def _load() -> C.CDLL:
         "cog_batch_sync": (C.c_int, [vp]),
         "cog_batch_last_error_string": (C.c_char_p, [vp]),
         "cog_batch_destroy": (C.c_int, [vp]),
+        "cog_server_create": (C.c_int, [P(vp), i32, P(vp)]),
+        "cog_server_submit": (C.c_int, [vp, i32, vp, vp]),
+        "cog_server_drain": (C.c_int, [vp, i32]),
+        "cog_server_read_stats": (C.c_int, [vp, P(cog_server_stats)]),
+        "cog_server_read_latencies": (C.c_int, [vp, vp, vp, C.c_int64, P(C.c_int64)]),
+        "cog_server_last_error_string": (C.c_char_p, [vp]),
+        "cog_server_destroy": (C.c_int, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -406,3 +421,55 @@ def encode_state(buf: np.ndarray, p: cog_params, st: dict) -> np.ndarray:
     out[L.gmm:L.gmm + g.nbytes] = g.view(np.uint8).reshape(-1)
     out[L.kde:L.kde + P * 768] = np.asarray(st["kde"], np.uint8).reshape(-1)
     return out
+
+
+# ----------------------------------------------------------------------------
+# Native frame server (continuous batching of many camera streams).
+# ----------------------------------------------------------------------------
+def _scheck(status: int, srv=None):
+    if status != COG_OK:
+        msg = lib.cog_server_last_error_string(srv)
+        raise CogError(status, msg.decode() if msg else "")
+
+
+def cog_server_create(ctxs) -> C.c_void_p:
+    arr = (C.c_void_p * len(ctxs))(*[c.value if isinstance(c, C.c_void_p) else c for c in ctxs])
+    srv = C.c_void_p()
+    _scheck(lib.cog_server_create(arr, len(ctxs), C.byref(srv)))
+    return srv
+
+
+def cog_server_submit(srv, stream: int, frame_host, mask_host) -> None:
+    """frame_host / mask_host: host tensors or numpy arrays (page-locked for
+    overlap) that stay alive until the frame is done."""
+    _scheck(lib.cog_server_submit(srv, int(stream), _host_ptr(frame_host), _host_ptr(mask_host)), srv)
+
+
+def cog_server_drain(srv, timeout_ms: int = 60000) -> None:
+    _scheck(lib.cog_server_drain(srv, int(timeout_ms)), srv)
+
+
+def cog_server_read_stats(srv) -> dict:
+    st = cog_server_stats()
+    _scheck(lib.cog_server_read_stats(srv, C.byref(st)), srv)
+    return st.as_dict()
+
+
+def cog_server_read_latencies(srv):
+    """(submission ms, latency ms) arrays of the frames done, in completion order."""
+    n = C.c_int64(0)
+    _scheck(lib.cog_server_read_latencies(srv, None, None, 0, C.byref(n)), srv)
+    t = np.empty(n.value, np.float32)
+    lat = np.empty(n.value, np.float32)
+    _scheck(lib.cog_server_read_latencies(srv, t.ctypes.data, lat.ctypes.data, n.value, C.byref(n)), srv)
+    return t, lat
+
+
+def cog_server_destroy(srv) -> None:
+    _scheck(lib.cog_server_destroy(srv))
+
+
+def _host_ptr(x) -> int:
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()

@@ -94,6 +94,10 @@ struct cog_ctx {
     cudaEvent_t ev_in[2], ev_done[2], ev_out[2];
 };
 
+namespace cog {
+int64_t ctx_pixels(const cog_ctx *c) { return c ? c->L.P : 0; }
+}  // namespace cog
+
 static thread_local char g_create_err[512];
 
 static cog_status set_err(cog_ctx *c, cog_status s, const char *fmt, ...)
@@ -872,8 +876,8 @@ struct BatchGroupHost {
     BatchGroupDev dev{};
     uint32_t k1_ctas = 0, k2_ctas = 0;
     void *dmem = nullptr;              // descs | frame_no | k1_pre | k2_pre | active
-    ApplyArgs *pinned = nullptr;       // upload staging
-    uint32_t *pinned_active = nullptr; // upload staging of the active flags
+    ApplyArgs *pinned[2] = {nullptr, nullptr};        // upload staging, by step parity
+    uint32_t *pinned_active[2] = {nullptr, nullptr};  // upload staging of the active flags
     std::vector<uint32_t> active;      // host copy of the active flags
 };
 
@@ -886,7 +890,8 @@ struct cog_batch {
     std::vector<uint8_t *> masks;
     std::vector<cudaStream_t> aux;     // one per group after the first (graph branches)
     std::vector<cudaEvent_t> fork, join;
-    cudaEvent_t uploaded = nullptr;
+    cudaEvent_t uploaded[2] = {nullptr, nullptr};   // uploads of the last step of each parity done
+    uint64_t step = 0;
     cudaGraphExec_t exec = nullptr;
     cog_status sticky = COG_OK;
     char err[512] = {0};
@@ -909,13 +914,16 @@ static void batch_free(cog_batch *b)
     if (b->exec) cudaGraphExecDestroy(b->exec);
     for (auto &g : b->groups) {
         if (g.dmem) cudaFree(g.dmem);
-        if (g.pinned) cudaFreeHost(g.pinned);
-        if (g.pinned_active) cudaFreeHost(g.pinned_active);
+        for (int k = 0; k < 2; k++) {
+            if (g.pinned[k]) cudaFreeHost(g.pinned[k]);
+            if (g.pinned_active[k]) cudaFreeHost(g.pinned_active[k]);
+        }
     }
     for (auto s : b->aux) cudaStreamDestroy(s);
     for (auto e : b->fork) cudaEventDestroy(e);
     for (auto e : b->join) cudaEventDestroy(e);
-    if (b->uploaded) cudaEventDestroy(b->uploaded);
+    for (int k = 0; k < 2; k++)
+        if (b->uploaded[k]) cudaEventDestroy(b->uploaded[k]);
     delete b;
 }
 
@@ -954,7 +962,8 @@ cog_status cog_batch_create(cog_ctx *const *ctxs, int32_t n, void *cuda_stream, 
         }
         b->groups[gi].members.push_back(i);
     }
-    cudaError_t e = cudaEventCreateWithFlags(&b->uploaded, cudaEventDisableTiming);
+    cudaError_t e = cudaEventCreateWithFlags(&b->uploaded[0], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->uploaded[1], cudaEventDisableTiming);
     for (auto &g : b->groups) {
         if (e != cudaSuccess) break;
         const int m = (int)g.members.size();
@@ -986,8 +995,11 @@ cog_status cog_batch_create(cog_ctx *const *ctxs, int32_t n, void *cuda_stream, 
         g.k2_ctas = k2[m];
         const size_t bytes = sizeof(ApplyArgs) * m + 4 * (size_t)m + 8 * (size_t)(m + 1) + 4 * (size_t)m + 64;
         if ((e = cudaMalloc(&g.dmem, bytes)) != cudaSuccess) break;
-        if ((e = cudaMallocHost((void **)&g.pinned, sizeof(ApplyArgs) * m)) != cudaSuccess) break;
-        if ((e = cudaMallocHost((void **)&g.pinned_active, 4 * (size_t)m)) != cudaSuccess) break;
+        for (int k = 0; k < 2 && e == cudaSuccess; k++) {
+            if ((e = cudaMallocHost((void **)&g.pinned[k], sizeof(ApplyArgs) * m)) != cudaSuccess) break;
+            e = cudaMallocHost((void **)&g.pinned_active[k], 4 * (size_t)m);
+        }
+        if (e != cudaSuccess) break;
         uint8_t *d = (uint8_t *)g.dmem;
         g.dev.descs = (ApplyArgs *)d;
         g.dev.frame_no = (uint32_t *)(d + sizeof(ApplyArgs) * m);
@@ -1073,6 +1085,10 @@ static cog_status batch_apply(cog_batch *b, const uint8_t *const *frames_dev, ui
         if (b->ctxs[i]->sticky != COG_OK) return batch_err(b, b->ctxs[i]->sticky, "stream %d: sticky error", i);
     }
     cudaError_t e = cudaSuccess;
+    // upload staging alternates by step: the buffers of this parity were
+    // last read by the uploads of two steps ago
+    const int par = (int)(b->step & 1);
+    bool staged = false;
     for (auto &g : b->groups) {
         bool dirty = false, adirty = false;
         for (size_t j = 0; j < g.members.size(); j++) {
@@ -1098,21 +1114,25 @@ static cog_status batch_apply(cog_batch *b, const uint8_t *const *frames_dev, ui
             g.descs[j].frame_no = (uint32_t)(b->ctxs[g.members[j]]->frame_no % 3);
             g.descs[j].frame_idx = (uint32_t)b->ctxs[g.members[j]]->frame_no;
         }
-        if ((e = cudaEventSynchronize(b->uploaded)) != cudaSuccess) break;
+        if (!staged) {
+            if ((e = cudaEventSynchronize(b->uploaded[par])) != cudaSuccess) break;
+            staged = true;
+        }
         if (dirty) {
-            memcpy(g.pinned, g.descs.data(), sizeof(ApplyArgs) * g.descs.size());
-            if ((e = cudaMemcpyAsync(g.dev.descs, g.pinned, sizeof(ApplyArgs) * g.descs.size(),
+            memcpy(g.pinned[par], g.descs.data(), sizeof(ApplyArgs) * g.descs.size());
+            if ((e = cudaMemcpyAsync(g.dev.descs, g.pinned[par], sizeof(ApplyArgs) * g.descs.size(),
                                      cudaMemcpyHostToDevice, b->stream)) != cudaSuccess)
                 break;
         }
         if (adirty) {
-            memcpy(g.pinned_active, g.active.data(), 4 * g.active.size());
-            if ((e = cudaMemcpyAsync((void *)g.dev.active, g.pinned_active, 4 * g.active.size(),
+            memcpy(g.pinned_active[par], g.active.data(), 4 * g.active.size());
+            if ((e = cudaMemcpyAsync((void *)g.dev.active, g.pinned_active[par], 4 * g.active.size(),
                                      cudaMemcpyHostToDevice, b->stream)) != cudaSuccess)
                 break;
         }
-        if ((e = cudaEventRecord(b->uploaded, b->stream)) != cudaSuccess) break;
     }
+    if (e == cudaSuccess && staged) e = cudaEventRecord(b->uploaded[par], b->stream);
+    b->step++;
     if (e == cudaSuccess && !b->exec) e = batch_capture(b);
     if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, b->stream);
     if (e != cudaSuccess) {

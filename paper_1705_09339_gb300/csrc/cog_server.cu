@@ -1,0 +1,360 @@
+// cog_server.cu -- native continuous-batching frame server (host code).
+//
+// Many camera streams share one GPU.  Callers submit host frames from any
+// thread; a worker thread repeatedly takes, for every stream that has a
+// frame waiting and a free device slot (two per stream), the oldest frame,
+// uploads those frames on a copy stream, runs one batched cascade step over
+// exactly those streams (cog_batch_apply_active: one replay of one captured
+// CUDA graph) and downloads their masks on a second copy stream.  Frames
+// that arrive while a step is on the GPU join the next step, whose uploads
+// overlap the running step.  A completion thread waits for each step's
+// downloads and records every frame's latency from submission to its mask
+// being in host memory.  Every wait is bounded by a condition-variable
+// timeout or by a CUDA event of work already enqueued.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "cog_internal.h"
+
+namespace {
+
+using clk = std::chrono::steady_clock;
+
+struct Pending {
+    const uint8_t *frame;   // host, height x width x 3
+    uint8_t *mask;          // host, height x width
+    clk::time_point t;      // submission
+    uint64_t seq;           // per-stream sequence number
+};
+
+struct Stream {
+    int64_t P = 0;
+    uint8_t *slot[2] = {nullptr, nullptr};   // device frame slots
+    uint8_t *mslot[2] = {nullptr, nullptr};  // device mask slots
+    std::deque<Pending> pending;
+    int inflight = 0;
+    uint64_t seq = 0;
+};
+
+struct Pick {
+    int stream;
+    Pending f;
+};
+
+struct Step {
+    cudaEvent_t done;
+    std::vector<Pick> picks;
+};
+
+}  // namespace
+
+struct cog_server {
+    int device = 0;
+    cog_batch *batch = nullptr;
+    cudaStream_t compute = nullptr, up = nullptr, down = nullptr;
+    cudaEvent_t copied = nullptr, applied = nullptr;
+    std::vector<Stream> streams;
+    std::mutex mu;                       // streams' queues, counts, statistics
+    std::condition_variable cv_work;     // work arrived or a slot freed
+    std::condition_variable cv_idle;     // a step completed
+    std::mutex dmu;
+    std::condition_variable cv_done;
+    std::deque<Step> done_q;
+    bool stop = false, worker_done = false;
+    std::thread worker, completer;
+    std::vector<float> lat_ms;
+    std::vector<float> sub_ms;           // submission time of each done frame, since creation
+    int64_t frames = 0, pixels = 0, steps = 0, submitted = 0;
+    clk::time_point t0;
+    cog_status sticky = COG_OK;
+    char err[512] = {0};
+};
+
+static thread_local char g_server_err[512];
+
+static cog_status server_err(cog_server *s, cog_status st, const char *fmt, ...)
+{
+    char *dst = s ? s->err : g_server_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 512, fmt, ap);
+    va_end(ap);
+    if (s && st != COG_OK && st != COG_ERR_INVALID_ARG) s->sticky = st;
+    return st;
+}
+
+static void server_worker(cog_server *s)
+{
+    cudaSetDevice(s->device);
+    const int n = (int)s->streams.size();
+    std::vector<const uint8_t *> frames(n, nullptr);
+    std::vector<uint8_t *> masks(n, nullptr);
+    std::vector<uint8_t> active(n, 0);
+    for (;;) {
+        std::vector<Pick> picks;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            for (;;) {
+                for (int i = 0; i < n; i++) {
+                    Stream &q = s->streams[i];
+                    if (!q.pending.empty() && q.inflight < 2) {
+                        picks.push_back({i, q.pending.front()});
+                        q.pending.pop_front();
+                        q.inflight++;
+                    }
+                }
+                if (!picks.empty() || s->stop || s->sticky != COG_OK) break;
+                s->cv_work.wait_for(lk, std::chrono::milliseconds(50));
+            }
+            if (picks.empty()) break;   // stopping, nothing left to start
+        }
+        cudaError_t e = cudaSuccess;
+        std::fill(active.begin(), active.end(), 0);
+        for (const Pick &k : picks) {
+            Stream &q = s->streams[k.stream];
+            const int sl = (int)(k.f.seq & 1);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(q.slot[sl], k.f.frame, (size_t)q.P * 3, cudaMemcpyHostToDevice, s->up);
+            frames[k.stream] = q.slot[sl];
+            masks[k.stream] = q.mslot[sl];
+            active[k.stream] = 1;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(s->copied, s->up);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s->compute, s->copied, 0);
+        cog_status st = COG_OK;
+        if (e == cudaSuccess) st = cog_batch_apply_active(s->batch, frames.data(), masks.data(), active.data());
+        if (e == cudaSuccess && st == COG_OK) e = cudaEventRecord(s->applied, s->compute);
+        if (e == cudaSuccess && st == COG_OK) e = cudaStreamWaitEvent(s->down, s->applied, 0);
+        for (const Pick &k : picks) {
+            Stream &q = s->streams[k.stream];
+            if (e == cudaSuccess && st == COG_OK)
+                e = cudaMemcpyAsync(k.f.mask, q.mslot[k.f.seq & 1], (size_t)q.P, cudaMemcpyDeviceToHost, s->down);
+        }
+        Step step;
+        step.picks = std::move(picks);
+        if (e == cudaSuccess && st == COG_OK) e = cudaEventCreateWithFlags(&step.done, cudaEventDisableTiming);
+        if (e == cudaSuccess && st == COG_OK) e = cudaEventRecord(step.done, s->down);
+        if (e != cudaSuccess || st != COG_OK) {
+            std::lock_guard<std::mutex> lk(s->mu);
+            if (st != COG_OK) server_err(s, st, "batched step: %s", cog_batch_last_error_string(s->batch));
+            else server_err(s, COG_ERR_CUDA, "batched step: %s", cudaGetErrorString(e));
+            for (const Pick &k : step.picks) s->streams[k.stream].inflight--;
+            s->cv_idle.notify_all();
+            break;
+        }
+        {
+            std::lock_guard<std::mutex> lk(s->dmu);
+            s->done_q.push_back(std::move(step));
+        }
+        s->cv_done.notify_one();
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->steps++;
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(s->dmu);
+        s->worker_done = true;
+    }
+    s->cv_done.notify_one();
+}
+
+static void server_completer(cog_server *s)
+{
+    cudaSetDevice(s->device);
+    for (;;) {
+        Step step;
+        {
+            std::unique_lock<std::mutex> lk(s->dmu);
+            while (s->done_q.empty() && !s->worker_done) s->cv_done.wait_for(lk, std::chrono::milliseconds(50));
+            if (s->done_q.empty()) break;
+            step = std::move(s->done_q.front());
+            s->done_q.pop_front();
+        }
+        const cudaError_t e = cudaEventSynchronize(step.done);
+        const clk::time_point now = clk::now();
+        cudaEventDestroy(step.done);
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            if (e != cudaSuccess) server_err(s, COG_ERR_CUDA, "step completion: %s", cudaGetErrorString(e));
+            for (const Pick &k : step.picks) {
+                Stream &q = s->streams[k.stream];
+                q.inflight--;
+                s->frames++;
+                s->pixels += q.P;
+                s->lat_ms.push_back(std::chrono::duration<float, std::milli>(now - k.f.t).count());
+                s->sub_ms.push_back(std::chrono::duration<float, std::milli>(k.f.t - s->t0).count());
+            }
+        }
+        s->cv_work.notify_one();
+        s->cv_idle.notify_all();
+    }
+}
+
+static void server_free(cog_server *s)
+{
+    for (Stream &q : s->streams)
+        for (int k = 0; k < 2; k++) {
+            if (q.slot[k]) cudaFree(q.slot[k]);
+            if (q.mslot[k]) cudaFree(q.mslot[k]);
+        }
+    if (s->batch) cog_batch_destroy(s->batch);
+    if (s->copied) cudaEventDestroy(s->copied);
+    if (s->applied) cudaEventDestroy(s->applied);
+    for (cudaStream_t st : {s->compute, s->up, s->down})
+        if (st) cudaStreamDestroy(st);
+    delete s;
+}
+
+extern "C" {
+
+cog_status cog_server_create(cog_ctx *const *ctxs, int32_t n, cog_server **out)
+{
+    if (!out) return server_err(nullptr, COG_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!ctxs || n < 1) return server_err(nullptr, COG_ERR_INVALID_ARG, "need n >= 1 contexts");
+    cog_server *s = new (std::nothrow) cog_server();
+    if (!s) return server_err(nullptr, COG_ERR_OOM, "host allocation failed");
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->up, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->down, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->copied, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->applied, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        server_err(nullptr, COG_ERR_CUDA, "server streams: %s", cudaGetErrorString(e));
+        server_free(s);
+        return COG_ERR_CUDA;
+    }
+    cog_status st = cog_batch_create(ctxs, n, s->compute, &s->batch);
+    if (st != COG_OK) {
+        server_err(nullptr, st, "batch: %s", cog_batch_last_error_string(nullptr));
+        s->batch = nullptr;
+        server_free(s);
+        return st;
+    }
+    s->streams.resize((size_t)n);
+    for (int i = 0; i < n && e == cudaSuccess; i++) {
+        const int64_t P = cog::ctx_pixels(ctxs[i]);
+        Stream &q = s->streams[i];
+        q.P = P;
+        for (int k = 0; k < 2 && e == cudaSuccess; k++) {
+            e = cudaMalloc((void **)&q.slot[k], (size_t)P * 3);
+            if (e == cudaSuccess) e = cudaMalloc((void **)&q.mslot[k], (size_t)P);
+        }
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        server_err(nullptr, COG_ERR_OOM, "server slots: %s", cudaGetErrorString(e));
+        server_free(s);
+        return COG_ERR_OOM;
+    }
+    s->t0 = clk::now();
+    s->worker = std::thread(server_worker, s);
+    s->completer = std::thread(server_completer, s);
+    *out = s;
+    return COG_OK;
+}
+
+cog_status cog_server_submit(cog_server *s, int32_t stream, const uint8_t *frame_host, uint8_t *mask_host)
+{
+    if (!s) return COG_ERR_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->sticky != COG_OK) return s->sticky;
+        if (stream < 0 || stream >= (int32_t)s->streams.size() || !frame_host || !mask_host)
+            return server_err(s, COG_ERR_INVALID_ARG, "stream index out of range or NULL buffer");
+        if (s->stop) return server_err(s, COG_ERR_STATE, "server is stopping");
+        Stream &q = s->streams[stream];
+        q.pending.push_back({frame_host, mask_host, clk::now(), q.seq++});
+        s->submitted++;
+    }
+    s->cv_work.notify_one();
+    return COG_OK;
+}
+
+cog_status cog_server_drain(cog_server *s, int32_t timeout_ms)
+{
+    if (!s || timeout_ms < 0) return COG_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    const clk::time_point until = clk::now() + std::chrono::milliseconds(timeout_ms);
+    while (s->frames < s->submitted && s->sticky == COG_OK) {
+        if (s->cv_idle.wait_until(lk, until) == std::cv_status::timeout && s->frames < s->submitted)
+            return server_err(s, COG_ERR_TIMEOUT, "drain: %lld of %lld frames done after %d ms",
+                              (long long)s->frames, (long long)s->submitted, timeout_ms);
+    }
+    return s->sticky;
+}
+
+cog_status cog_server_read_stats(cog_server *s, cog_server_stats *out)
+{
+    if (!s || !out) return COG_ERR_INVALID_ARG;
+    std::vector<float> lat;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        memset(out, 0, sizeof *out);
+        out->frames = s->frames;
+        out->steps = s->steps;
+        out->pixels = s->pixels;
+        out->submitted = s->submitted;
+        out->wall_s = std::chrono::duration<double>(clk::now() - s->t0).count();
+        lat = s->lat_ms;
+    }
+    if (!lat.empty()) {
+        std::sort(lat.begin(), lat.end());
+        auto pct = [&](double q) {
+            const double r = q * (double)(lat.size() - 1);
+            const size_t i = (size_t)r;
+            const double f = r - (double)i;
+            return i + 1 < lat.size() ? (1.0 - f) * lat[i] + f * lat[i + 1] : (double)lat[i];
+        };
+        out->p50_ms = pct(0.50);
+        out->p99_ms = pct(0.99);
+        out->max_ms = lat.back();
+    }
+    return s->sticky;
+}
+
+cog_status cog_server_read_latencies(cog_server *s, float *submit_ms, float *latency_ms, int64_t cap, int64_t *n)
+{
+    if (!s || !n || cap < 0 || (cap > 0 && (!submit_ms || !latency_ms))) return COG_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    const int64_t m = std::min<int64_t>(cap, (int64_t)s->lat_ms.size());
+    if (m > 0) {
+        memcpy(submit_ms, s->sub_ms.data(), sizeof(float) * (size_t)m);
+        memcpy(latency_ms, s->lat_ms.data(), sizeof(float) * (size_t)m);
+    }
+    *n = (int64_t)s->lat_ms.size();
+    return COG_OK;
+}
+
+const char *cog_server_last_error_string(cog_server *s)
+{
+    return s ? s->err : g_server_err;
+}
+
+cog_status cog_server_destroy(cog_server *s)
+{
+    if (!s) return COG_ERR_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    if (s->completer.joinable()) s->completer.join();
+    const cog_status st = s->sticky;
+    cudaStreamSynchronize(s->down);
+    server_free(s);
+    return st;
+}
+
+}  // extern "C"
