@@ -121,9 +121,6 @@ struct LaunchCfg {
 
 cudaError_t launch_batch_advance(const BatchGroupDev &g, cudaStream_t st);
 
-// pixels per frame of a context
-int64_t ctx_pixels(const cog_ctx *c);
-
 // ---- clip of consecutive frames in one cooperative launch
 constexpr int CLIP_TMAX = 32;          // frames per launch (their flags fit one word)
 constexpr int CLIP_SLOTS = 8;          // counter slots per (frame, field)

@@ -24,6 +24,10 @@
 
 #include "cog_internal.h"
 
+namespace cog {
+int64_t ctx_pixels(const cog_ctx *c);   // pixels per frame of a context (cog_api.cu)
+}
+
 namespace {
 
 using clk = std::chrono::steady_clock;
