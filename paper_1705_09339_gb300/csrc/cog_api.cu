@@ -30,6 +30,9 @@ cudaError_t launch_clip_f32(int, const ClipArgs &, int, cudaStream_t);
 cudaError_t launch_clip_f16(int, const ClipArgs &, int, cudaStream_t);
 cudaError_t launch_clip_bf16(int, const ClipArgs &, int, cudaStream_t);
 cudaError_t run_wait_selftest(uint64_t limit_ns, uint32_t *error_word, float *elapsed_ms);
+int k1_batch_blocks_per_sm_f32(const LaunchCfg &);
+int k1_batch_blocks_per_sm_f16(const LaunchCfg &);
+int k1_batch_blocks_per_sm_bf16(const LaunchCfg &);
 int k2_blocks_per_sm_f32(int, const LaunchCfg &);
 int k2_blocks_per_sm_f16(int, const LaunchCfg &);
 int k2_blocks_per_sm_bf16(int, const LaunchCfg &);
@@ -874,12 +877,41 @@ struct BatchGroupHost {
     std::vector<int> members;          // indices into cog_batch::ctxs
     std::vector<ApplyArgs> descs;      // host copy of the device descriptors
     BatchGroupDev dev{};
-    uint32_t k1_ctas = 0, k2_ctas = 0;
-    void *dmem = nullptr;              // descs | frame_no | k1_pre | k2_pre | active
+    uint32_t k1_ctas = 0, k2_ctas = 0; // fixed grids of the two batch kernels
+    std::vector<int64_t> tiles, pix;   // stage-0/1 tiles and pixels per member
+    void *dmem = nullptr;              // descs | frame_no | active | k1_pre | k2_pre
     ApplyArgs *pinned[2] = {nullptr, nullptr};        // upload staging, by step parity
-    uint32_t *pinned_active[2] = {nullptr, nullptr};  // upload staging of the active flags
+    uint32_t *pinned_active[2] = {nullptr, nullptr};  // upload staging of the step plan
     std::vector<uint32_t> active;      // host copy of the active flags
 };
+
+// The step plan of a group: active flags, the prefix of the active
+// members' stage-0/1 tiles, and the mixture-stage CTAs split among the
+// active members in proportion to their pixels (at least one each, never
+// more than the grid or than one per k2_tpb pixels).  out: n + 2 (n + 1).
+static void batch_plan(const BatchGroupHost &g, uint32_t *out)
+{
+    const int n = (int)g.members.size();
+    uint32_t *act = out, *k1 = out + n, *k2 = out + 2 * n + 1;
+    int64_t psum = 0, nact = 0;
+    for (int j = 0; j < n; j++)
+        if (g.active[j]) { psum += g.pix[j]; nact++; }
+    const int64_t spare = (int64_t)g.k2_ctas - nact;
+    k1[0] = 0;
+    k2[0] = 0;
+    for (int j = 0; j < n; j++) {
+        act[j] = g.active[j];
+        int64_t t1 = 0, t2 = 0;
+        if (g.active[j]) {
+            t1 = g.tiles[j];
+            t2 = 1 + (spare > 0 && psum > 0 ? spare * g.pix[j] / psum : 0);
+            const int64_t need = (g.pix[j] + g.launch.k2_tpb - 1) / g.launch.k2_tpb;
+            t2 = t2 > need ? need : t2;
+        }
+        k1[j + 1] = k1[j] + (uint32_t)t1;
+        k2[j + 1] = k2[j] + (uint32_t)t2;
+    }
+}
 
 struct cog_batch {
     cudaStream_t stream = nullptr;
@@ -969,19 +1001,18 @@ cog_status cog_batch_create(cog_ctx *const *ctxs, int32_t n, void *cuda_stream, 
         const int m = (int)g.members.size();
         int64_t psum = 0;
         for (int i : g.members) psum += ctxs[i]->L.P;
+        (void)psum;
         const int per_sm = g.dtype == COG_F32 ? k2_blocks_per_sm_f32(g.K, g.launch)
                          : (g.dtype == COG_F16 ? k2_blocks_per_sm_f16(g.K, g.launch) : k2_blocks_per_sm_bf16(g.K, g.launch));
-        const int64_t k2_total = (int64_t)ctxs[0]->n_sm * per_sm;
-        std::vector<uint32_t> k1(m + 1, 0), k2(m + 1, 0);
+        const int k1_bps = g.dtype == COG_F32 ? k1_batch_blocks_per_sm_f32(g.launch)
+                         : (g.dtype == COG_F16 ? k1_batch_blocks_per_sm_f16(g.launch) : k1_batch_blocks_per_sm_bf16(g.launch));
+        int64_t tiles_all = 0;
         for (int j = 0; j < m; j++) {
             const cog_ctx *c = ctxs[g.members[j]];
             const int64_t tile = (int64_t)g.launch.k1_tpb * K1_PX_PER_THREAD;
-            const int64_t t1 = (c->L.P + tile - 1) / tile;
-            const int64_t need2 = (c->L.P + g.launch.k2_tpb - 1) / g.launch.k2_tpb;
-            int64_t t2 = (int64_t)((double)k2_total * (double)c->L.P / (double)psum + 0.5);
-            t2 = t2 < 1 ? 1 : (t2 > need2 ? need2 : t2);
-            k1[j + 1] = k1[j] + (uint32_t)t1;
-            k2[j + 1] = k2[j] + (uint32_t)t2;
+            g.tiles.push_back((c->L.P + tile - 1) / tile);
+            g.pix.push_back(c->L.P);
+            tiles_all += g.tiles.back();
             ApplyArgs a{};
             a.dp = c->dp;
             a.s = c->sp;
@@ -991,32 +1022,33 @@ cog_status cog_batch_create(cog_ctx *const *ctxs, int32_t n, void *cuda_stream, 
             a.rec_bytes = (uint32_t)c->L.rec_bytes;
             g.descs.push_back(a);
         }
-        g.k1_ctas = k1[m];
-        g.k2_ctas = k2[m];
-        const size_t bytes = sizeof(ApplyArgs) * m + 4 * (size_t)m + 8 * (size_t)(m + 1) + 4 * (size_t)m + 64;
+        // fixed grids: a persistent stage-0/1 grid, and every mixture-stage
+        // CTA that fits (split among the active members each step)
+        const int64_t g1 = (int64_t)ctxs[0]->n_sm * (k1_bps > 0 ? k1_bps : 1);
+        g.k1_ctas = (uint32_t)(tiles_all < g1 ? tiles_all : g1);
+        g.k2_ctas = (uint32_t)((int64_t)ctxs[0]->n_sm * per_sm);
+        const size_t plan_words = (size_t)m + 2 * (size_t)(m + 1);
+        const size_t bytes = sizeof(ApplyArgs) * m + 4 * (size_t)m + 4 * plan_words + 64;
         if ((e = cudaMalloc(&g.dmem, bytes)) != cudaSuccess) break;
         for (int k = 0; k < 2 && e == cudaSuccess; k++) {
             if ((e = cudaMallocHost((void **)&g.pinned[k], sizeof(ApplyArgs) * m)) != cudaSuccess) break;
-            e = cudaMallocHost((void **)&g.pinned_active[k], 4 * (size_t)m);
+            e = cudaMallocHost((void **)&g.pinned_active[k], 4 * plan_words);
         }
         if (e != cudaSuccess) break;
         uint8_t *d = (uint8_t *)g.dmem;
         g.dev.descs = (ApplyArgs *)d;
         g.dev.frame_no = (uint32_t *)(d + sizeof(ApplyArgs) * m);
-        g.dev.k1_pre = (const uint32_t *)(d + sizeof(ApplyArgs) * m + 4 * m);
+        g.dev.active = (const uint32_t *)(d + sizeof(ApplyArgs) * m + 4 * m);
+        g.dev.k1_pre = g.dev.active + m;
         g.dev.k2_pre = g.dev.k1_pre + (m + 1);
-        g.dev.active = g.dev.k2_pre + (m + 1);
         g.dev.n = m;
         g.active.assign(m, 1u);
-        std::vector<uint32_t> fno(m);
+        std::vector<uint32_t> fno(m), plan(plan_words);
         for (int j = 0; j < m; j++) fno[j] = (uint32_t)ctxs[g.members[j]]->frame_no;
+        batch_plan(g, plan.data());
         e = cudaMemcpyAsync(g.dev.frame_no, fno.data(), 4 * m, cudaMemcpyHostToDevice, b->stream);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync((void *)g.dev.k1_pre, k1.data(), 4 * (m + 1), cudaMemcpyHostToDevice, b->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync((void *)g.dev.k2_pre, k2.data(), 4 * (m + 1), cudaMemcpyHostToDevice, b->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync((void *)g.dev.active, g.active.data(), 4 * m, cudaMemcpyHostToDevice, b->stream);
+            e = cudaMemcpyAsync((void *)g.dev.active, plan.data(), 4 * plan_words, cudaMemcpyHostToDevice, b->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     }
     for (size_t g = 1; g < b->groups.size() && e == cudaSuccess; g++) {
@@ -1125,8 +1157,9 @@ static cog_status batch_apply(cog_batch *b, const uint8_t *const *frames_dev, ui
                 break;
         }
         if (adirty) {
-            memcpy(g.pinned_active[par], g.active.data(), 4 * g.active.size());
-            if ((e = cudaMemcpyAsync((void *)g.dev.active, g.pinned_active[par], 4 * g.active.size(),
+            const size_t m = g.members.size();
+            batch_plan(g, g.pinned_active[par]);
+            if ((e = cudaMemcpyAsync((void *)g.dev.active, g.pinned_active[par], 4 * (m + 2 * (m + 1)),
                                      cudaMemcpyHostToDevice, b->stream)) != cudaSuccess)
                 break;
         }

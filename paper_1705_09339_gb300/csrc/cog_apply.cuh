@@ -535,23 +535,28 @@ __device__ __forceinline__ int batch_stream(const uint32_t *pre, int n, uint32_t
     return lo;
 }
 
+// A persistent grid walks the active streams' tiles (the step plan's
+// prefix gives inactive streams no tiles).
 template <typename T, int TPB>
 __global__ void __launch_bounds__(TPB, K1_THREADS_PER_SM / TPB) stage01_batch_kernel(const BatchGroupDev G)
 {
     grid_launch_dependents();
     grid_wait_prior();
-    const int s = batch_stream(G.k1_pre, G.n, blockIdx.x);
-    if (!G.active[s]) return;      // no frame for this stream in this step
-    k1_cta<T, TPB>(G.descs[s], blockIdx.x - G.k1_pre[s]);
+    const uint32_t total = __ldg(G.k1_pre + G.n);
+    for (uint32_t t = blockIdx.x; t < total; t += gridDim.x) {
+        const int s = batch_stream(G.k1_pre, G.n, t);
+        k1_cta<T, TPB>(G.descs[s], t - __ldg(G.k1_pre + s));
+    }
 }
 
+// The mixture-stage CTAs are split among the active streams only.
 template <typename T, int K, int TPB>
 __global__ void __launch_bounds__(TPB) stage2_batch_kernel(const BatchGroupDev G)
 {
     grid_launch_dependents();
     grid_wait_prior();
+    if (blockIdx.x >= __ldg(G.k2_pre + G.n)) return;
     const int s = batch_stream(G.k2_pre, G.n, blockIdx.x);
-    if (!G.active[s]) return;
     k2_cta<T, K, TPB>(G.descs[s], blockIdx.x - G.k2_pre[s], G.k2_pre[s + 1] - G.k2_pre[s]);
 }
 
@@ -655,6 +660,12 @@ int k2_blocks_per_sm_t(const LaunchCfg &lc)
 {
     const int ps = blocks_per_sm(k2_batch<T, K>(lc.k2_tpb), lc.k2_tpb);
     return lc.k2_per_sm > 0 && lc.k2_per_sm < ps ? lc.k2_per_sm : ps;
+}
+
+template <typename T>
+int k1_batch_blocks_per_sm_t(const LaunchCfg &lc)
+{
+    return blocks_per_sm(k1_batch<T>(lc.k1_tpb), lc.k1_tpb);
 }
 
 }  // namespace cog

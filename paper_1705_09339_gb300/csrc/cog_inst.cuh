@@ -60,6 +60,11 @@ cudaError_t COG_CAT(launch_clip_, COG_SUFFIX)(int K, const ClipArgs &a, int n_sm
 #undef CALL_C
 }
 
+int COG_CAT(k1_batch_blocks_per_sm_, COG_SUFFIX)(const LaunchCfg &lc)
+{
+    return k1_batch_blocks_per_sm_t<COG_T>(lc);
+}
+
 cudaError_t COG_CAT(launch_plain_, COG_SUFFIX)(int K, const DevParams &dp, const StatePtrs &s,
                                                const uint8_t *frame, uint8_t *mask, cudaStream_t st)
 {

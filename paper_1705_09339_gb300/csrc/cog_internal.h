@@ -102,13 +102,17 @@ struct ApplyArgs {
 
 // A batch group: streams sharing one storage type and K, run by one launch
 // of each kernel.  Descriptors live in device memory so that a captured
-// graph stays valid while frame buffers change.
+// graph stays valid while frame buffers change.  The host rewrites the
+// step plan (active flags and the two prefixes, one upload) whenever the
+// set of streams with a frame changes: only those streams get work.
 struct BatchGroupDev {
     ApplyArgs *descs;        // [n], frame_no field = frames applied % 3
     uint32_t *frame_no;      // [n] frames applied (full count)
-    const uint32_t *k1_pre;  // [n + 1] prefix of first-kernel CTAs per stream
-    const uint32_t *k2_pre;  // [n + 1] prefix of mixture-stage CTAs per stream
     const uint32_t *active;  // [n] 1 = the stream has a frame this step
+    const uint32_t *k1_pre;  // [n + 1] prefix of the active streams' stage-0/1 tiles
+                             //         (an inactive stream has width 0)
+    const uint32_t *k2_pre;  // [n + 1] prefix of the mixture-stage CTAs given to the
+                             //         active streams (in proportion to their pixels)
     int n;
 };
 

@@ -144,7 +144,10 @@ static void server_worker(cog_server *s)
         }
         Step step;
         step.picks = std::move(picks);
-        if (e == cudaSuccess && st == COG_OK) e = cudaEventCreateWithFlags(&step.done, cudaEventDisableTiming);
+        // a blocking-sync event lets the completion thread sleep in its wait
+        // instead of spinning a core
+        if (e == cudaSuccess && st == COG_OK)
+            e = cudaEventCreateWithFlags(&step.done, cudaEventDisableTiming | cudaEventBlockingSync);
         if (e == cudaSuccess && st == COG_OK) e = cudaEventRecord(step.done, s->down);
         if (e != cudaSuccess || st != COG_OK) {
             std::lock_guard<std::mutex> lk(s->mu);
