@@ -5,6 +5,6 @@ benchmark's CPU-baseline leg are its only users.  The product package never
 imports it.  See ``cog_oracle.h`` for what each routine follows in the paper.
 """
 from .oracle import (  # noqa: F401
-    ORC_CONF, ORC_FD, ORC_ILLUM, ORC_MODE1, ORC_RGA, ORC_SAMPLE, NEAR_BITS, Oracle, OracleState,
+    ORC_CONF, ORC_FD, ORC_ILLUM, ORC_MODE1, ORC_PERCHAN, ORC_RGA, ORC_SAMPLE, NEAR_BITS, Oracle, OracleState,
     build_oracle, default_params, kde_weights, oracle_threads,
 )

@@ -45,6 +45,7 @@ static int check_params(const orc_params *pr)
     if (!(pr->var_min > 0.0) || pr->var_max < pr->var_min) return -1;
     if (pr->kde_bw < 1 || pr->kde_bw > 32) return -1;
     if ((pr->flags & ORC_SAMPLE) && pr->skip_period < 1) return -1;
+    if ((pr->flags & ORC_PERCHAN) && (pr->flags & ORC_MODE1)) return -1;
     return 0;
 }
 
@@ -132,6 +133,108 @@ typedef struct {
     uint8_t near;
 } px_out;
 
+/* Stage 2 with per-channel independent mixtures (ORC_PERCHAN): channel c
+ * ranks its components by w_c^2 / v_c, takes the first in rank order with
+ * (I_c - mu_c)^2 / (lambda^2 v_c) < 1, is background iff the weight ranked
+ * before it is <= T, and updates its own weights (Eq. 2 per channel); a
+ * channel with no match restarts its lowest-ranked component.  The pixel is
+ * background iff every channel is.  Returns the label; *Mhat receives the
+ * largest per-channel match statistic (1 for an unmatched channel). */
+static int stage2_perchan(const orc_params *pr, orc_state *s, int64_t p, const uint8_t *I,
+                          double a_eff, int illum_flag, double *Mhat, uint8_t *near, int *illum)
+{
+    const int K = pr->K;
+    const double lam2 = pr->lambda * pr->lambda;
+    double *mu = s->mu + p * K * 3;
+    double *var = s->var + p * K * 3;
+    int chan_fg[3], tgt_c[3], label = 0;
+    *Mhat = 0.0;
+    for (int c = 0; c < 3; c++) {
+        double *w = s->wc + (p * 3 + c) * K;
+        double r[KMAX];
+        int ord[KMAX];
+        for (int k = 0; k < K; k++) r[k] = w[k] * w[k] / var[k * 3 + c];
+        for (int k = 0; k < K; k++) ord[k] = k;
+        for (int i = 1; i < K; i++) {            /* stable insertion sort */
+            int x = ord[i], j = i - 1;
+            while (j >= 0 && r[ord[j]] < r[x]) { ord[j + 1] = ord[j]; j--; }
+            ord[j + 1] = x;
+        }
+        for (int i = 0; i + 1 < K; i++) {
+            double ra = r[ord[i]], rb = r[ord[i + 1]];
+            double mx = ra > rb ? ra : rb;
+            if (ra != rb && fabs(ra - rb) <= NEAR_REL * mx) *near |= ORC_NEAR_RANK;
+        }
+        int m = -1, mpos = -1;
+        double tm = 0.0;
+        for (int j = 0; j < K; j++) {
+            int k = ord[j];
+            double d = I[c] - mu[k * 3 + c];
+            double tk = d * d / (lam2 * var[k * 3 + c]);
+            if (near_rel(tk, 1.0)) *near |= ORC_NEAR_MATCH;
+            if (tk < 1.0) { m = k; mpos = j; tm = tk; break; }
+        }
+        int fgc = 1;
+        if (m >= 0) {
+            double S = 0.0;
+            for (int j = 0; j < mpos; j++) S += w[ord[j]];
+            if (near_rel(S, pr->T_bg)) *near |= ORC_NEAR_BGSET;
+            fgc = (S <= pr->T_bg) ? 0 : 1;
+        }
+        const double Mc = (m >= 0) ? (tm < 1.0 ? tm : 1.0) : 1.0;
+        if (Mc > *Mhat) *Mhat = Mc;
+        int tgt;
+        if (m >= 0) {
+            for (int k = 0; k < K; k++) w[k] = (1.0 - a_eff) * w[k] + (k == m ? a_eff : 0.0);
+            double *pm = &mu[m * 3 + c], *pv = &var[m * 3 + c];
+            *pm = *pm + a_eff * (I[c] - *pm);
+            double d = I[c] - *pm;
+            *pv = clampd((1.0 - a_eff) * (*pv) + a_eff * d * d, pr->var_min, pr->var_max);
+            tgt = m;
+        } else {
+            for (int k = 0; k < K; k++) w[k] = (1.0 - a_eff) * w[k];
+            int low = ord[K - 1];
+            mu[low * 3 + c] = I[c];
+            var[low * 3 + c] = pr->var_init;
+            w[low] = pr->w_init;
+            tgt = low;
+        }
+        double sum = 0.0;
+        for (int k = 0; k < K; k++) sum += w[k];
+        for (int k = 0; k < K; k++) w[k] = w[k] / sum;
+        chan_fg[c] = fgc;
+        tgt_c[c] = tgt;
+        label |= fgc;
+    }
+    *illum = 0;
+    if (illum_flag && label) {
+        /* abrupt illumination change: every channel that decided foreground
+         * gives its matched or new component the weight w_illum */
+        for (int c = 0; c < 3; c++) {
+            if (!chan_fg[c]) continue;
+            double *w = s->wc + (p * 3 + c) * K;
+            double so = 0.0;
+            for (int k = 0; k < K; k++) if (k != tgt_c[c]) so += w[k];
+            if (so > 0.0) {
+                for (int k = 0; k < K; k++)
+                    if (k != tgt_c[c]) w[k] = w[k] * (1.0 - pr->w_illum) / so;
+                w[tgt_c[c]] = pr->w_illum;
+            } else {
+                w[tgt_c[c]] = 1.0;
+            }
+        }
+        label = 0;
+        *illum = 1;
+    }
+    if (label == 0) {   /* transition update, channel by channel */
+        for (int c = 0; c < 3; c++) {
+            s->rga_m[p * 3 + c] = mu[tgt_c[c] * 3 + c];
+            s->rga_v[p * 3 + c] = var[tgt_c[c] * 3 + c];
+        }
+    }
+    return label;
+}
+
 static px_out cascade_pixel(const orc_params *pr, orc_state *s, int64_t p,
                             const uint8_t *I, int illum_flag, int64_t n)
 {
@@ -216,6 +319,27 @@ static px_out cascade_pixel(const orc_params *pr, orc_state *s, int64_t p,
             c_inst = wa + wb * (1.0 - dhat) + wg * (1.0 - tr);
             goto finish;
         }
+    }
+
+    /* Stage 2 with per-channel mixtures */
+    if (fl & ORC_PERCHAN) {
+        o.reached_gmm = 1;
+        double Mhat;
+        int il;
+        label = stage2_perchan(pr, s, p, I, a_eff, illum_flag, &Mhat, &o.near, &il);
+        o.stage = il ? ORC_ST_ILLUM : (label ? ORC_ST_FG : ORC_ST_GMM_BG);
+        int qmin = 255;
+        for (int c = 0; c < 3; c++) {
+            int q = s->kde[(p * 3 + c) * 256 + I[c]];
+            if (q < qmin) qmin = q;
+        }
+        if (qmin < pr->q_null) {
+            double den = wb + wg;
+            c_inst = den > 0.0 ? (wb * (1.0 - dhat) + wg * (1.0 - Mhat)) / den : 0.0;
+        } else {
+            c_inst = wa * (qmin / 255.0) + wb * (1.0 - dhat) + wg * (1.0 - Mhat);
+        }
+        goto finish;
     }
 
     /* Stage 2: the ordered Gaussians (Eq. 2). */
@@ -424,7 +548,11 @@ int orc_train_near(const orc_params *pr, const uint8_t *frames, int N, orc_state
 
     /* mixture warm-up: component 0 takes the first frame with all the
      * weight; the others start empty (weight 0, mean 0, variance v_init) */
+    const int perchan = (pr->flags & ORC_PERCHAN) != 0;
     for (int64_t p = 0; p < P; p++) {
+        if (perchan)
+            for (int c = 0; c < 3; c++)
+                for (int k = 0; k < K; k++) s->wc[(p * 3 + c) * K + k] = k == 0 ? 1.0 : 0.0;
         for (int k = 0; k < K; k++) {
             s->w[p * K + k] = k == 0 ? 1.0 : 0.0;
             for (int c = 0; c < 3; c++) {
@@ -445,7 +573,7 @@ int orc_train_near(const orc_params *pr, const uint8_t *frames, int N, orc_state
     /* frames 1..N-1 run the cascade with every rejection stage and every
      * modulation off, i.e. the plain mixture at rate alpha */
     orc_params pw = *pr;
-    pw.flags = 0;
+    pw.flags = perchan ? ORC_PERCHAN : 0u;
     uint8_t *mask = (uint8_t *)malloc((size_t)P);
     uint8_t *nf = near ? (uint8_t *)malloc((size_t)P) : NULL;
     if (!mask || (near && !nf)) { free(mask); free(nf); return -1; }
@@ -461,6 +589,25 @@ int orc_train_near(const orc_params *pr, const uint8_t *frames, int N, orc_state
     /* running average <- the top-ranked mode; C <- 0.5; the label and the
      * previous frame are those of the last training frame */
     for (int64_t p = 0; p < P; p++) {
+        if (perchan) {
+            /* each channel's running average starts at its own top mode */
+            for (int c = 0; c < 3; c++) {
+                const double *w = s->wc + (p * 3 + c) * K, *var = s->var + p * K * 3;
+                int best = 0;
+                double rb = -1.0, r[KMAX];
+                for (int k = 0; k < K; k++) {
+                    r[k] = w[k] * w[k] / var[k * 3 + c];
+                    if (r[k] > rb) { rb = r[k]; best = k; }
+                }
+                if (near)
+                    for (int k = 0; k < K; k++)
+                        if (k != best && r[k] != rb && fabs(r[k] - rb) <= NEAR_REL * rb) near[p] |= ORC_NEAR_RANK;
+                s->rga_m[p * 3 + c] = s->mu[(p * K + best) * 3 + c];
+                s->rga_v[p * 3 + c] = s->var[(p * K + best) * 3 + c];
+            }
+            s->conf[p] = 0.5;
+            continue;
+        }
         const double *w = s->w + p * K, *var = s->var + p * K * 3;
         int best = 0;
         double rb = -1.0, r[KMAX];

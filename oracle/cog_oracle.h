@@ -21,6 +21,11 @@
  *   - cascade CHP -> running Gaussian average -> ordered Gaussians, prior
  *     nullified, active-level-only adaptation, illumination counter:
  *     Sec. 2, "Cascade of Gaussians CoG";
+ *   - ORC_PERCHAN, per-channel independent mixtures (the independence of
+ *     the R, G, B channels Sec. 2 assumes for the prior, applied to the
+ *     mixture): each channel ranks, matches and updates its own K 1-D
+ *     components with its own weights; a pixel is background iff every
+ *     channel is;
  *   - ORC_MODE1, the Fig. 1 reading of the cascade (CHP -> mode 1 -> the
  *     other modes): stage 1 tests and adapts a copy of the mixture's
  *     rank-1 mode; on the transition to stage 2 the copy is written back
@@ -52,6 +57,7 @@ extern "C" {
 #define ORC_ILLUM 8u   /* abrupt-illumination counter and response                       */
 #define ORC_SAMPLE 16u /* confidence-based temporal sampling                             */
 #define ORC_MODE1 32u  /* stage 1 is the mixture's rank-1 mode (Fig. 1 reading)        */
+#define ORC_PERCHAN 64u /* per-channel independent mixtures (own weights per channel)    */
 
 /* near-threshold record bits (one byte per pixel and frame) */
 #define ORC_NEAR_FD    1u  /* D vs tau_fd (0.5 + C)            */
@@ -110,6 +116,8 @@ typedef struct {
                                      since training                     */
     uint8_t *top;    /* [P]          with ORC_MODE1: the mixture component the
                                      running average mirrors            */
+    double  *wc;     /* [P][3][K]    with ORC_PERCHAN: each channel's own
+                                     mixture weights (w is then unused) */
 } orc_state;
 
 typedef struct {

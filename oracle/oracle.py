@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "cog_oracle.c")
 _LIB = os.path.join(_HERE, "libcog_oracle.so")
 
-ORC_FD, ORC_RGA, ORC_CONF, ORC_ILLUM, ORC_SAMPLE, ORC_MODE1 = 1, 2, 4, 8, 16, 32
+ORC_FD, ORC_RGA, ORC_CONF, ORC_ILLUM, ORC_SAMPLE, ORC_MODE1, ORC_PERCHAN = 1, 2, 4, 8, 16, 32, 64
 NEAR_BITS = {"fd": 1, "rga": 2, "match": 4, "bgset": 8, "rank": 16, "halt": 32, "skip": 64}
 
 _lock = threading.Lock()
@@ -55,7 +55,7 @@ class _Params(C.Structure):
 class _State(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in (
         "w", "mu", "var", "rga_m", "rga_v", "conf", "label", "prev", "kde",
-        "qa", "qb", "illum", "top")]
+        "qa", "qb", "illum", "top", "wc")]
 
 
 class _Stats(C.Structure):
@@ -136,6 +136,7 @@ class OracleState:
         self.qb = np.zeros(P, np.uint8)
         self.illum = np.zeros(2, np.int64)
         self.top = np.zeros(P, np.uint8)
+        self.wc = np.zeros((P, 3, K))
 
     def _c(self) -> _State:
         s = _State()

@@ -562,3 +562,83 @@ def test_mode1_alone_is_the_plain_mixture():
         m1, _, _, _ = o.apply(f)
         assert np.array_equal(m1, o.plain_gmm(w, mu, var, f))
         assert np.array_equal(mu, o.state.mu) and np.array_equal(var, o.state.var)
+
+
+# ------------------------------------------------ per-channel mixtures
+from oracle import ORC_PERCHAN  # noqa: E402
+
+
+def test_perchan_on_gray_input_is_the_shared_mixture():
+    # with R = G = B in every frame and every state, the three per-channel
+    # mixtures are copies of the shared-weight one: same keys, matches,
+    # updates and decisions, so masks, stage maps and means/variances agree
+    # and each channel's weights equal the shared weights
+    from cogsynth import Scene
+    W, H, K = 40, 24, 3
+    sc = Scene(W, H, 21, kind="dynamic", n_train=30, fg_frac=0.1, switch_at=15)
+    fr, _ = sc.frames(0, 70)
+    gray = np.repeat(fr[..., :1], 3, axis=-1)
+    runs = []
+    for extra in (0, ORC_PERCHAN):
+        p = default_params(W, H, K)
+        p["flags"] = ALL | extra
+        o = Oracle(p)
+        o.train(gray[:30])
+        out = [o.apply(gray[t])[:2] for t in range(30, 70)]
+        runs.append((o, out))
+    (a, oa), (b, ob) = runs
+    for (ma, sa), (mb, sb) in zip(oa, ob):
+        assert np.array_equal(ma, mb) and np.array_equal(sa, sb)
+    assert np.array_equal(a.state.mu, b.state.mu) and np.array_equal(a.state.var, b.state.var)
+    for c in range(3):
+        assert np.array_equal(b.state.wc[:, c, :], a.state.w)
+
+
+def test_perchan_channels_are_independent():
+    # with every other stage off each channel's mixture sees only its own
+    # values: changing channel 1 leaves channels 0 and 2 bit-identical
+    from cogsynth import Scene
+    W, H, K = 32, 20, 3
+    sc = Scene(W, H, 22, kind="dynamic", n_train=25, fg_frac=0.1, switch_at=12)
+    fr, _ = sc.frames(0, 60)
+    alt = fr.copy()
+    alt[..., 1] = 255 - alt[..., 1]
+    st = []
+    for f in (fr, alt):
+        p = default_params(W, H, K)
+        p["flags"] = ORC_PERCHAN
+        o = Oracle(p)
+        o.train(f[:25])
+        for t in range(25, 60):
+            o.apply(f[t])
+        st.append(o.state)
+    for c in (0, 2):
+        assert np.array_equal(st[0].wc[:, c], st[1].wc[:, c])
+        assert np.array_equal(st[0].mu[:, :, c], st[1].mu[:, :, c])
+        assert np.array_equal(st[0].var[:, :, c], st[1].var[:, :, c])
+    assert not np.array_equal(st[0].wc[:, 1], st[1].wc[:, 1])
+
+
+def test_hand_perchan_one_channel_behind_too_much_weight_is_foreground():
+    # every channel: comp0 (100, v 16), comp1 (50, v 4), comp2 (200, v 64);
+    # weights ch0 = ch2 = (.5, .3, .2), ch1 = (.2, .75, .05); I = (104, 100, 98)
+    # ch0: keys .015625 / .0225 / .000625 -> order 1, 0, 2; comp0 matches at
+    #      rank 2 (t = 16/100), S = .3 -> BG; w = (.625, .225, .15), mu0 = 101,
+    #      v0 = .75*16 + .25*3^2 = 14.25
+    # ch1: keys .0025 / .140625 / .0000390625 -> order 1, 0, 2; comp0 matches
+    #      (t = 0), S = .75 > .7 -> FG; w = (.4, .5625, .0375), mu0 = 100, v0 = 12
+    # ch2: as ch0 with t = 4/100: BG; mu0 = 99.5, v0 = .75*16 + .25*1.5^2 = 12.5625
+    # the pixel is FG (one channel is); no transition update
+    o = one_pixel(flags=ORC_PERCHAN, **HAND)
+    _hand_state(o)
+    o.state.wc[0, 0] = [0.5, 0.3, 0.2]
+    o.state.wc[0, 1] = [0.2, 0.75, 0.05]
+    o.state.wc[0, 2] = [0.5, 0.3, 0.2]
+    rga0 = o.state.rga_m[0].copy()
+    m, st, _, _ = o.apply(np.array([[104, 100, 98]], np.uint8))
+    assert m[0] == 255 and st[0] == 3
+    assert np.allclose(o.state.wc[0, 0], [0.625, 0.225, 0.15], rtol=0, atol=1e-15)
+    assert np.allclose(o.state.wc[0, 1], [0.4, 0.5625, 0.0375], rtol=0, atol=1e-15)
+    assert list(o.state.mu[0, 0]) == [101, 100, 99.5]
+    assert list(o.state.var[0, 0]) == [14.25, 12, 12.5625]
+    assert np.array_equal(o.state.rga_m[0], rga0)
