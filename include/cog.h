@@ -59,6 +59,12 @@ typedef enum { COG_F32 = 0, COG_F16 = 1, COG_BF16 = 2 } cog_dtype;
                           stage 2 the copy is written back into that mode (Sec. 2: the
                           parameters are updated during a transition), Eq. 2 runs, and
                           the copy then follows the mode that ranks first            */
+#define COG_PERCHAN 64u /* per-channel independent mixtures (Sec. 2 assumes independent
+                           R, G, B channels for the prior; here also for the mixture):
+                           each channel ranks, matches and updates its own K 1-D
+                           components with its own weights; a pixel is background iff
+                           every channel is.  Records hold K x 9 values.  Not with
+                           COG_MODE1; cog_apply_plain_gmm is not defined with it    */
 #define COG_ALL   15u /* the cascade: every stage and modulation, no sampling            */
 
 /* Stage codes written to a stage map (the cascade level that labelled the

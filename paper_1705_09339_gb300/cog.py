@@ -20,7 +20,7 @@ COG_OK, COG_ERR_INVALID_ARG, COG_ERR_OOM, COG_ERR_CUDA, COG_ERR_STATE, COG_ERR_T
 STATUS_NAMES = ["COG_OK", "COG_ERR_INVALID_ARG", "COG_ERR_OOM", "COG_ERR_CUDA", "COG_ERR_STATE",
                 "COG_ERR_TIMEOUT", "COG_ERR_DEVICE"]
 COG_F32, COG_F16, COG_BF16 = 0, 1, 2
-COG_FD, COG_RGA, COG_CONF, COG_ILLUM, COG_SAMPLE, COG_MODE1 = 1, 2, 4, 8, 16, 32
+COG_FD, COG_RGA, COG_CONF, COG_ILLUM, COG_SAMPLE, COG_MODE1, COG_PERCHAN = 1, 2, 4, 8, 16, 32, 64
 COG_ALL = 15
 DTYPES = {"f32": COG_F32, "f16": COG_F16, "bf16": COG_BF16}
 
@@ -352,7 +352,8 @@ def _s1_view(buf, L, P, p):
 def decode_state(buf: np.ndarray, p: cog_params) -> dict:
     """FP64 copies of the model planes of an exported state image:
     w [P,K], mu [P,K,3], var [P,K,3], rga_m [P,3], rga_v [P,3], conf [P],
-    label [P], prev [P,3], kde [P,3,256], qa [P], qb [P], top [P]."""
+    label [P], prev [P,3], kde [P,3,256], qa [P], qb [P], top [P]; with
+    COG_PERCHAN the weights are per channel: wc [P,3,K] instead of w."""
     L = cog_state_layout(p)
     P, K = p.width * p.height, p.K
     Pp = (P + 4095) // 4096 * 4096
@@ -372,11 +373,18 @@ def decode_state(buf: np.ndarray, p: cog_params) -> dict:
         recs = _bf16_to_f32(_plane(buf, L.gmm, Pp * rec_elems, np.uint16)).astype(np.float64)
     else:
         recs = _plane(buf, L.gmm, Pp * rec_elems, _NP_DT[p.state_dtype]).astype(np.float64)
-    recs = recs.reshape(Pp, rec_elems)[:P, :7 * K].reshape(P, K, 7)
     kde = buf[L.kde:L.kde + P * 768].reshape(P, 3, 256)
-    return dict(w=recs[:, :, 0].copy(), mu=recs[:, :, 1:4].copy(), var=recs[:, :, 4:7].copy(),
-                rga_m=s1[:, :3].copy(), rga_v=s1[:, 3:].copy(), conf=conf, label=label, prev=prev,
-                kde=kde, qa=(qab & 0xFF).astype(np.uint8), qb=(qab >> 8).astype(np.uint8), top=top)
+    out = dict(rga_m=s1[:, :3].copy(), rga_v=s1[:, 3:].copy(), conf=conf, label=label, prev=prev,
+               kde=kde, qa=(qab & 0xFF).astype(np.uint8), qb=(qab >> 8).astype(np.uint8), top=top)
+    if p.flags & COG_PERCHAN:
+        # per component (w0 w1 w2 mu0 mu1 mu2 v0 v1 v2); wc [P, 3, K]
+        recs = recs.reshape(Pp, rec_elems)[:P, :9 * K].reshape(P, K, 9)
+        out.update(wc=recs[:, :, 0:3].transpose(0, 2, 1).copy(), mu=recs[:, :, 3:6].copy(),
+                   var=recs[:, :, 6:9].copy())
+    else:
+        recs = recs.reshape(Pp, rec_elems)[:P, :7 * K].reshape(P, K, 7)
+        out.update(w=recs[:, :, 0].copy(), mu=recs[:, :, 1:4].copy(), var=recs[:, :, 4:7].copy())
+    return out
 
 
 def _to_storage(arr, dtype) -> np.ndarray:
@@ -415,8 +423,12 @@ def encode_state(buf: np.ndarray, p: cog_params, st: dict) -> np.ndarray:
     out[L.s1:L.s1 + P * rb] = rec.reshape(-1)
     rec_elems = L.rec_bytes // L.elem_bytes
     recs = np.zeros((Pp, rec_elems))
-    r = np.concatenate([st["w"][:, :, None], st["mu"], st["var"]], axis=2).reshape(P, 7 * K)
-    recs[:P, :7 * K] = r
+    if p.flags & COG_PERCHAN:
+        r = np.concatenate([st["wc"].transpose(0, 2, 1), st["mu"], st["var"]], axis=2).reshape(P, 9 * K)
+        recs[:P, :9 * K] = r
+    else:
+        r = np.concatenate([st["w"][:, :, None], st["mu"], st["var"]], axis=2).reshape(P, 7 * K)
+        recs[:P, :7 * K] = r
     g = _to_storage(recs, p.state_dtype)
     out[L.gmm:L.gmm + g.nbytes] = g.view(np.uint8).reshape(-1)
     out[L.kde:L.kde + P * 768] = np.asarray(st["kde"], np.uint8).reshape(-1)

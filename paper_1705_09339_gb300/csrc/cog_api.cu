@@ -33,13 +33,16 @@ cudaError_t run_wait_selftest(uint64_t limit_ns, uint32_t *error_word, float *el
 int k1_batch_blocks_per_sm_f32(const LaunchCfg &);
 int k1_batch_blocks_per_sm_f16(const LaunchCfg &);
 int k1_batch_blocks_per_sm_bf16(const LaunchCfg &);
-int k2_blocks_per_sm_f32(int, const LaunchCfg &);
-int k2_blocks_per_sm_f16(int, const LaunchCfg &);
-int k2_blocks_per_sm_bf16(int, const LaunchCfg &);
+int k2_blocks_per_sm_f32(int, const LaunchCfg &, bool);
+int k2_blocks_per_sm_f16(int, const LaunchCfg &, bool);
+int k2_blocks_per_sm_bf16(int, const LaunchCfg &, bool);
 
 int elem_bytes(int dtype) { return dtype == COG_F32 ? 4 : 2; }
 
-int rec_bytes(int dtype, int K) { return (K * 7 * elem_bytes(dtype) + 15) / 16 * 16; }
+int rec_bytes(int dtype, int K, bool perchan)
+{
+    return (K * (perchan ? 9 : 7) * elem_bytes(dtype) + 15) / 16 * 16;
+}
 
 int s1_bytes(int dtype) { return dtype == COG_F32 ? 32 : 16; }
 
@@ -50,7 +53,7 @@ bool make_layout(const cog_params &p, Layout &L)
     L.P = (int64_t)p.width * p.height;
     L.Pp = (int64_t)up((size_t)L.P, PX_ALIGN);
     L.elem = (size_t)elem_bytes(p.state_dtype);
-    L.rec_bytes = (size_t)rec_bytes(p.state_dtype, p.K);
+    L.rec_bytes = (size_t)rec_bytes(p.state_dtype, p.K, (p.flags & COG_PERCHAN) != 0);
     L.s1_bytes = (size_t)s1_bytes(p.state_dtype);
     size_t o = 0;
     L.ctl = o;  o += CTL_BYTES;
@@ -140,7 +143,8 @@ static const char *check_params(const cog_params *p)
     if (p->kde_bw < 1 || p->kde_bw > 32) return "kde_bw must be in 1..32";
     if (p->r1 < 0 || p->r2 < p->r1) return "need 0 <= r1 <= r2";
     if (p->illum_permille < 0 || p->illum_permille > 1000) return "illum_permille must be in 0..1000";
-    if (p->flags & ~(COG_ALL | COG_SAMPLE | COG_MODE1)) return "unknown flag bits";
+    if (p->flags & ~(COG_ALL | COG_SAMPLE | COG_MODE1 | COG_PERCHAN)) return "unknown flag bits";
+    if ((p->flags & COG_PERCHAN) && (p->flags & COG_MODE1)) return "COG_PERCHAN and COG_MODE1 do not combine";
     if (p->skip_period < 1) return "skip_period must be >= 1";
     return nullptr;
 }
@@ -514,6 +518,8 @@ cog_status cog_selftest_bounded_wait(int32_t limit_ms, uint32_t *error_word, dou
 
 cog_status cog_apply_plain_gmm(cog_ctx *c, const uint8_t *frame_dev, uint8_t *mask_dev)
 {
+    if (c && (c->p.flags & COG_PERCHAN))
+        return set_err(c, COG_ERR_INVALID_ARG, "the plain mixture uses shared weights; not defined with COG_PERCHAN");
     cog_status s = check_ctx(c);
     if (s) return s;
     if (!c->trained) return set_err(c, COG_ERR_STATE, "cog_apply_plain_gmm before cog_train_prior");
@@ -873,6 +879,7 @@ cog_status cog_destroy(cog_ctx *c)
 // ---------------------------------------------------------------------------
 struct BatchGroupHost {
     int dtype = 0, K = 0;
+    bool pc = false;                   // per-channel mixtures
     LaunchCfg launch;                  // the first member's launch shape
     std::vector<int> members;          // indices into cog_batch::ctxs
     std::vector<ApplyArgs> descs;      // host copy of the device descriptors
@@ -984,12 +991,15 @@ cog_status cog_batch_create(cog_ctx *const *ctxs, int32_t n, void *cuda_stream, 
     for (int i = 0; i < n; i++) {
         int gi = -1;
         for (size_t g = 0; g < b->groups.size(); g++)
-            if (b->groups[g].dtype == ctxs[i]->p.state_dtype && b->groups[g].K == ctxs[i]->p.K) gi = (int)g;
+            if (b->groups[g].dtype == ctxs[i]->p.state_dtype && b->groups[g].K == ctxs[i]->p.K &&
+                b->groups[g].pc == ((ctxs[i]->p.flags & COG_PERCHAN) != 0))
+                gi = (int)g;
         if (gi < 0) {
             b->groups.emplace_back();
             gi = (int)b->groups.size() - 1;
             b->groups[gi].dtype = ctxs[i]->p.state_dtype;
             b->groups[gi].K = ctxs[i]->p.K;
+            b->groups[gi].pc = (ctxs[i]->p.flags & COG_PERCHAN) != 0;
             b->groups[gi].launch = ctxs[i]->launch;
         }
         b->groups[gi].members.push_back(i);
@@ -1002,8 +1012,9 @@ cog_status cog_batch_create(cog_ctx *const *ctxs, int32_t n, void *cuda_stream, 
         int64_t psum = 0;
         for (int i : g.members) psum += ctxs[i]->L.P;
         (void)psum;
-        const int per_sm = g.dtype == COG_F32 ? k2_blocks_per_sm_f32(g.K, g.launch)
-                         : (g.dtype == COG_F16 ? k2_blocks_per_sm_f16(g.K, g.launch) : k2_blocks_per_sm_bf16(g.K, g.launch));
+        const int per_sm = g.dtype == COG_F32 ? k2_blocks_per_sm_f32(g.K, g.launch, g.pc)
+                         : (g.dtype == COG_F16 ? k2_blocks_per_sm_f16(g.K, g.launch, g.pc)
+                                               : k2_blocks_per_sm_bf16(g.K, g.launch, g.pc));
         const int k1_bps = g.dtype == COG_F32 ? k1_batch_blocks_per_sm_f32(g.launch)
                          : (g.dtype == COG_F16 ? k1_batch_blocks_per_sm_f16(g.launch) : k1_batch_blocks_per_sm_bf16(g.launch));
         int64_t tiles_all = 0;
@@ -1042,6 +1053,7 @@ cog_status cog_batch_create(cog_ctx *const *ctxs, int32_t n, void *cuda_stream, 
         g.dev.k1_pre = g.dev.active + m;
         g.dev.k2_pre = g.dev.k1_pre + (m + 1);
         g.dev.n = m;
+        g.dev.pc = g.pc ? 1 : 0;
         g.active.assign(m, 1u);
         std::vector<uint32_t> fno(m), plan(plan_words);
         for (int j = 0; j < m; j++) fno[j] = (uint32_t)ctxs[g.members[j]]->frame_no;

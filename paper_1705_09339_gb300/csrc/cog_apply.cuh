@@ -367,24 +367,91 @@ __global__ void __launch_bounds__(TPB, K1_THREADS_PER_SM / TPB) stage01_kernel(c
 
 // ---- stage 2: one survivor of the queue, in two halves (its loads, then
 //      the mixture step and its stores)
-template <typename T, int K> struct S2In {
+// Mixture record size: shared weights (K x 7 values) or per-channel
+// mixtures (K x 9, COG_PERCHAN).
+template <typename T, int K, bool PC> struct RecSel {
+    static constexpr int NV = PC ? RecPC<T, K>::NV : Rec<T, K>::NV;
+    static constexpr int BYTES = PC ? RecPC<T, K>::BYTES : Rec<T, K>::BYTES;
+};
+
+template <typename T, int K, bool PC = false> struct S2In {
     uint4 e;
-    uint4 rec[Rec<T, K>::NV];
+    uint4 rec[RecSel<T, K, PC>::NV];
     uint32_t qk[3];
     S1Rec<T> s1;   // COG_MODE1 only: the stage-1 copy of the rank-1 mode
 };
 
-template <typename T, int K>
-__device__ __forceinline__ void s2_load(const ApplyArgs &A, int64_t qi, S2In<T, K> &in)
+template <typename T, int K, bool PC = false>
+__device__ __forceinline__ void s2_load(const ApplyArgs &A, int64_t qi, S2In<T, K, PC> &in)
 {
     in.e = __ldcg(A.s.queue + qi);
     const int64_t p = in.e.x;
 #pragma unroll
     for (int c = 0; c < 3; c++) in.qk[c] = __ldg(A.s.kde + (p * 3 + c) * 256 + ((in.e.y >> (8 * c)) & 0xffu));
-    const uint4 *src = reinterpret_cast<const uint4 *>(A.s.gmm + p * Rec<T, K>::BYTES);
+    const uint4 *src = reinterpret_cast<const uint4 *>(A.s.gmm + p * RecSel<T, K, PC>::BYTES);
 #pragma unroll
-    for (int i = 0; i < Rec<T, K>::NV; i++) in.rec[i] = src[i];
-    if (A.dp.flags & COG_MODE1) in.s1.load(A.s.s1, p);
+    for (int i = 0; i < RecSel<T, K, PC>::NV; i++) in.rec[i] = src[i];
+    if (!PC && (A.dp.flags & COG_MODE1)) in.s1.load(A.s.s1, p);
+}
+
+// Confidence of a pixel decided at stage 2 (Sec. 2, "Confidence Measure"):
+// prior term from the three prior bytes unless the prior is nullified.
+__device__ __forceinline__ float conf_stage2(const DevParams &dp, const uint32_t qk[3], uint32_t qab, int D, float Cm,
+                                             float Mh)
+{
+    uint32_t qmin = qk[0] < qk[1] ? qk[0] : qk[1];
+    qmin = qk[2] < qmin ? qk[2] : qmin;
+    const uint32_t qa = qab & 0xffu, qb = qab >> 8;
+    const float wa = (float)qa * R255, wb = (float)qb * R255;
+    const float wg = (float)(255u - qa - qb) * R255;
+    const float dhat = (float)D * R255;
+    float ci;
+    if ((int)qmin < dp.q_null) {
+        const float den = wb + wg;
+        ci = den > 0.f ? (wb * (1.f - dhat) + wg * (1.f - Mh)) / den : 0.f;
+    } else {
+        ci = wa * ((float)qmin * R255) + wb * (1.f - dhat) + wg * (1.f - Mh);
+    }
+    return (1.f - dp.eta) * Cm + dp.eta * ci;
+}
+
+// Stage 2 with per-channel mixtures (COG_PERCHAN): returns the stage code.
+template <typename T, int K>
+__device__ __forceinline__ int s2_finish_pc(const ApplyArgs &A, const S2In<T, K, true> &in, bool flag)
+{
+    const DevParams &dp = A.dp;
+    const int64_t p = in.e.x;
+    const int D = (int)(in.e.y >> 24);
+    float I[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) I[c] = (float)((in.e.y >> (8 * c)) & 0xffu);
+    const float Cm = __uint_as_float(in.e.z);
+    const uint32_t qab = in.e.w & 0xffffu;
+    MixPC<K> m;
+    mixpc_unpack<T, K>(in.rec, m);
+    const MixOutPC o = mix_step_pc<K>(m, I, dp.alpha * (1.5f - Cm), dp);
+    int label = o.fg, st = o.fg ? COG_ST_FG : COG_ST_GMM_BG;
+    if (flag && o.fg) {
+        illum_response_pc<K>(m, o, dp.w_illum);
+        label = 0;
+        st = COG_ST_ILLUM;
+    }
+    uint4 u[RecPC<T, K>::NV];
+    mixpc_pack<T, K>(m, u);
+    uint4 *dst = reinterpret_cast<uint4 *>(A.s.gmm + p * RecPC<T, K>::BYTES);
+#pragma unroll
+    for (int i = 0; i < RecPC<T, K>::NV; i++) dst[i] = u[i];
+    if (!label) {
+        S1Rec<T> r;
+        s1_reseed_pc<T, K>(m, o, qab, r);
+        r.store(A.s.s1, p);
+    }
+    if (dp.flags & COG_CONF)
+        reinterpret_cast<T *>(A.s.conf)[p] = Store<T>::from_f(conf_stage2(dp, in.qk, qab, D, Cm, o.Mhat));
+    reinterpret_cast<uint8_t *>(A.s.jl)[p * 4 + 3] = (uint8_t)label;
+    A.mask[p] = label ? 255 : 0;
+    if (A.stagemap) A.stagemap[p] = (uint8_t)st;
+    return st;
 }
 
 template <typename T, int K>
@@ -439,21 +506,8 @@ __device__ __forceinline__ int s2_finish(const ApplyArgs &A, const S2In<T, K> &i
         r.store(A.s.s1, p);
     }
     if (conf_on) {
-        uint32_t qmin = in.qk[0] < in.qk[1] ? in.qk[0] : in.qk[1];
-        qmin = in.qk[2] < qmin ? in.qk[2] : qmin;
-        const uint32_t qa = qab & 0xffu, qb = qab >> 8;
-        const float wa = (float)qa * R255, wb = (float)qb * R255;
-        const float wg = (float)(255u - qa - qb) * R255;
-        const float dhat = (float)D * R255;
         const float Mh = o.match >= 0 ? (o.tm < 1.f ? o.tm : 1.f) : 1.f;
-        float ci;
-        if ((int)qmin < dp.q_null) {
-            const float den = wb + wg;
-            ci = den > 0.f ? (wb * (1.f - dhat) + wg * (1.f - Mh)) / den : 0.f;
-        } else {
-            ci = wa * ((float)qmin * R255) + wb * (1.f - dhat) + wg * (1.f - Mh);
-        }
-        reinterpret_cast<T *>(A.s.conf)[p] = Store<T>::from_f((1.f - dp.eta) * Cm + dp.eta * ci);
+        reinterpret_cast<T *>(A.s.conf)[p] = Store<T>::from_f(conf_stage2(dp, in.qk, qab, D, Cm, Mh));
     }
     reinterpret_cast<uint8_t *>(A.s.jl)[p * 4 + 3] = (uint8_t)label;
     A.mask[p] = label ? 255 : 0;
@@ -462,7 +516,7 @@ __device__ __forceinline__ int s2_finish(const ApplyArgs &A, const S2In<T, K> &i
 }
 
 // One of ncta CTAs walking stream A's survivor queue.
-template <typename T, int K, int TPB>
+template <typename T, int K, int TPB, bool PC = false>
 __device__ __forceinline__ void k2_cta(const ApplyArgs &A, uint32_t cta, uint32_t ncta)
 {
     __shared__ uint32_t flag_s, cnt_s[3], segp_s[QSEG + 1];
@@ -498,9 +552,11 @@ __device__ __forceinline__ void k2_cta(const ApplyArgs &A, uint32_t cta, uint32_
     };
     uint32_t cbg = 0, cfg = 0, cil = 0;
     for (uint32_t q = cta * TPB + tid; q < nq; q += stride) {
-        S2In<T, K> a;
-        s2_load<T, K>(A, entry(q), a);
-        const int st = s2_finish<T, K>(A, a, flag);
+        S2In<T, K, PC> a;
+        s2_load<T, K, PC>(A, entry(q), a);
+        int st;
+        if constexpr (PC) st = s2_finish_pc<T, K>(A, a, flag);
+        else st = s2_finish<T, K>(A, a, flag);
         cbg += st == COG_ST_GMM_BG; cfg += st == COG_ST_FG; cil += st == COG_ST_ILLUM;
     }
     cbg = __reduce_add_sync(0xffffffffu, cbg);
@@ -515,12 +571,12 @@ __device__ __forceinline__ void k2_cta(const ApplyArgs &A, uint32_t cta, uint32_
     if (tid < 3 && cnt_s[tid]) atomicAdd(ctl + ctl_slot(n % 3, 2 + tid, cta & (CTL_SLOTS - 1)), cnt_s[tid]);
 }
 
-template <typename T, int K, int TPB>
+template <typename T, int K, int TPB, bool PC = false>
 __global__ void __launch_bounds__(TPB) stage2_kernel(const ApplyArgs A)
 {
     grid_launch_dependents();
     grid_wait_prior();     // the queue and counters come from stage01_kernel
-    k2_cta<T, K, TPB>(A, blockIdx.x, gridDim.x);
+    k2_cta<T, K, TPB, PC>(A, blockIdx.x, gridDim.x);
 }
 
 // ---- batched: many streams of one storage type and K in one launch each
@@ -550,14 +606,14 @@ __global__ void __launch_bounds__(TPB, K1_THREADS_PER_SM / TPB) stage01_batch_ke
 }
 
 // The mixture-stage CTAs are split among the active streams only.
-template <typename T, int K, int TPB>
+template <typename T, int K, int TPB, bool PC = false>
 __global__ void __launch_bounds__(TPB) stage2_batch_kernel(const BatchGroupDev G)
 {
     grid_launch_dependents();
     grid_wait_prior();
     if (blockIdx.x >= __ldg(G.k2_pre + G.n)) return;
     const int s = batch_stream(G.k2_pre, G.n, blockIdx.x);
-    k2_cta<T, K, TPB>(G.descs[s], blockIdx.x - G.k2_pre[s], G.k2_pre[s + 1] - G.k2_pre[s]);
+    k2_cta<T, K, TPB, PC>(G.descs[s], blockIdx.x - G.k2_pre[s], G.k2_pre[s + 1] - G.k2_pre[s]);
 }
 
 // Launch with programmatic stream serialization: the kernel may be
@@ -587,8 +643,9 @@ void (*k1_single(int tpb))(ApplyArgs)
     return tpb == 64 ? stage01_kernel<T, 64> : (tpb == 256 ? stage01_kernel<T, 256> : stage01_kernel<T, 128>);
 }
 template <typename T, int K>
-void (*k2_single(int tpb))(ApplyArgs)
+void (*k2_single(int tpb, bool pc))(ApplyArgs)
 {
+    if (pc) return tpb == 128 ? stage2_kernel<T, K, 128, true> : stage2_kernel<T, K, 64, true>;
     return tpb == 128 ? stage2_kernel<T, K, 128> : stage2_kernel<T, K, 64>;
 }
 template <typename T>
@@ -598,8 +655,9 @@ void (*k1_batch(int tpb))(BatchGroupDev)
                      : (tpb == 256 ? stage01_batch_kernel<T, 256> : stage01_batch_kernel<T, 128>);
 }
 template <typename T, int K>
-void (*k2_batch(int tpb))(BatchGroupDev)
+void (*k2_batch(int tpb, bool pc))(BatchGroupDev)
 {
+    if (pc) return tpb == 128 ? stage2_batch_kernel<T, K, 128, true> : stage2_batch_kernel<T, K, 64, true>;
     return tpb == 128 ? stage2_batch_kernel<T, K, 128> : stage2_batch_kernel<T, K, 64>;
 }
 
@@ -614,7 +672,7 @@ int blocks_per_sm(KernT k, int tpb)
 namespace {
 // Mixture-stage CTAs that fit on one SM, by CTA size (64, 128) and K; one
 // table per translation unit (storage type), filled on first use.
-int k2_occupancy[2][KMAX + 1];
+int k2_occupancy[2][2][KMAX + 1];   // [per-channel][CTA size][K]
 }
 
 template <typename T, int K>
@@ -625,12 +683,13 @@ cudaError_t launch_apply_t(const ApplyArgs &a, const LaunchCfg &lc, cudaStream_t
     cudaError_t e = launch_pdl(k1_single<T>(lc.k1_tpb), g1, lc.k1_tpb, st, a);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev->e1, st);
-    int &ps = k2_occupancy[lc.k2_tpb == 128][K];
-    if (!ps) ps = blocks_per_sm(k2_single<T, K>(lc.k2_tpb), lc.k2_tpb);
+    const bool pc = a.dp.flags & COG_PERCHAN;
+    int &ps = k2_occupancy[pc][lc.k2_tpb == 128][K];
+    if (!ps) ps = blocks_per_sm(k2_single<T, K>(lc.k2_tpb, pc), lc.k2_tpb);
     const int use = lc.k2_per_sm > 0 && lc.k2_per_sm < ps ? lc.k2_per_sm : ps;
     const int64_t need = (a.dp.P + lc.k2_tpb - 1) / lc.k2_tpb;
     const int64_t g2 = min((int64_t)a.k2_grid * use, need);
-    e = launch_pdl(k2_single<T, K>(lc.k2_tpb), max((int64_t)1, g2), lc.k2_tpb, st, a);
+    e = launch_pdl(k2_single<T, K>(lc.k2_tpb, pc), max((int64_t)1, g2), lc.k2_tpb, st, a);
     if (ev) cudaEventRecord(ev->e2, st);
     return e;
 }
@@ -652,13 +711,13 @@ cudaError_t launch_batch_t(const BatchGroupDev &g, const LaunchCfg &lc, uint32_t
     if (e != cudaSuccess) return e;
     cfg.gridDim = dim3(k2_ctas);
     cfg.blockDim = dim3(lc.k2_tpb);
-    return cudaLaunchKernelEx(&cfg, k2_batch<T, K>(lc.k2_tpb), g);
+    return cudaLaunchKernelEx(&cfg, k2_batch<T, K>(lc.k2_tpb, g.pc != 0), g);
 }
 
 template <typename T, int K>
-int k2_blocks_per_sm_t(const LaunchCfg &lc)
+int k2_blocks_per_sm_t(const LaunchCfg &lc, bool pc)
 {
-    const int ps = blocks_per_sm(k2_batch<T, K>(lc.k2_tpb), lc.k2_tpb);
+    const int ps = blocks_per_sm(k2_batch<T, K>(lc.k2_tpb, pc), lc.k2_tpb);
     return lc.k2_per_sm > 0 && lc.k2_per_sm < ps ? lc.k2_per_sm : ps;
 }
 

@@ -159,26 +159,62 @@ __device__ __forceinline__ void load_frame_words(const uint8_t *f, int64_t p0, i
 // confidence; its stage code goes to V.resst.  Kept out of line so that
 // the mixture's registers do not add to the per-frame state the caller
 // keeps live across it.
-template <typename T, int K, int G>
+template <typename T, int K, int G, bool PC>
 __device__ CLIP_S2_INLINE void clip_s2(const ClipArgs &A, ClipWarp<T, G> &V, int64_t p, int slot, bool flag)
 {
     const DevParams &dp = A.dp;
     const bool conf_on = dp.flags & COG_CONF;
     constexpr int SB = S1Rec<T>::BYTES;
+    constexpr int RNV = RecSel<T, K, PC>::NV, RB = RecSel<T, K, PC>::BYTES;
     const uint2 sv = V.stash[slot];
-    uint4 raw[Rec<T, K>::NV];
-    const uint4 *src = reinterpret_cast<const uint4 *>(A.s.gmm + p * Rec<T, K>::BYTES);
+    uint4 raw[RNV];
+    const uint4 *src = reinterpret_cast<const uint4 *>(A.s.gmm + p * RB);
 #pragma unroll
-    for (int i = 0; i < Rec<T, K>::NV; i++) raw[i] = src[i];
+    for (int i = 0; i < RNV; i++) raw[i] = src[i];
     uint32_t qk[3];
 #pragma unroll
     for (int c = 0; c < 3; c++) qk[c] = __ldg(A.s.kde + (p * 3 + c) * 256 + ((sv.x >> (8 * c)) & 0xffu));
     const uint32_t bit = 1u << (slot & 31);
     if (!(V.touched[slot >> 5] & bit)) {
-        uint4 *u = reinterpret_cast<uint4 *>(A.undo_gmm + p * Rec<T, K>::BYTES);
+        uint4 *u = reinterpret_cast<uint4 *>(A.undo_gmm + p * RB);
 #pragma unroll
-        for (int i = 0; i < Rec<T, K>::NV; i++) u[i] = raw[i];
+        for (int i = 0; i < RNV; i++) u[i] = raw[i];
         atomicOr(&V.touched[slot >> 5], bit);
+    }
+    if constexpr (PC) {
+        // per-channel mixtures (COG_PERCHAN)
+        const int D = (int)(sv.x >> 24);
+        float I[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) I[c] = (float)((sv.x >> (8 * c)) & 0xffu);
+        const float Cm = __uint_as_float(sv.y);
+        S1Rec<T> r;
+#pragma unroll
+        for (int i = 0; i < S1Rec<T>::NV; i++) r.u[i] = reinterpret_cast<const uint4 *>(V.s1 + slot * SB)[i];
+        const uint32_t qab = r.qab();
+        MixPC<K> m;
+        mixpc_unpack<T, K>(raw, m);
+        const MixOutPC o = mix_step_pc<K>(m, I, dp.alpha * (1.5f - Cm), dp);
+        int label = o.fg, st = o.fg ? COG_ST_FG : COG_ST_GMM_BG;
+        if (flag && o.fg) {
+            illum_response_pc<K>(m, o, dp.w_illum);
+            label = 0;
+            st = COG_ST_ILLUM;
+        }
+        uint4 u[RecPC<T, K>::NV];
+        mixpc_pack<T, K>(m, u);
+        uint4 *dst = reinterpret_cast<uint4 *>(A.s.gmm + p * RB);
+#pragma unroll
+        for (int i = 0; i < RecPC<T, K>::NV; i++) dst[i] = u[i];
+        if (!label) {
+            S1Rec<T> rn;
+            s1_reseed_pc<T, K>(m, o, qab, rn);
+#pragma unroll
+            for (int i = 0; i < S1Rec<T>::NV; i++) reinterpret_cast<uint4 *>(V.s1 + slot * SB)[i] = rn.u[i];
+        }
+        if (conf_on) V.resc[slot] = conf_stage2(dp, qk, qab, D, Cm, o.Mhat);
+        V.resst[slot] = (uint8_t)st;
+        return;
     }
     const int D = (int)(sv.x >> 24);
     float I[3];
@@ -254,7 +290,7 @@ __device__ CLIP_S2_INLINE void clip_s2(const ClipArgs &A, ClipWarp<T, G> &V, int
 // all warps go through the mixture stage together, one per thread; then
 // each warp writes its pixels' outputs.  cnt_s: the CTA's per-frame
 // counters [CLIP_TMAX][CTL_FIELDS].
-template <typename T, int K, int G, int NW>
+template <typename T, int K, int G, int NW, bool PC>
 __device__ __forceinline__ void clip_tile(const ClipArgs &A, ClipWarp<T, G> *Ws, ClipQueue<NW, G * 128> &Q,
                                           uint32_t cbase, int warp, int lane, uint32_t flags, uint32_t *cnt_s)
 {
@@ -422,7 +458,7 @@ __device__ __forceinline__ void clip_tile(const ClipArgs &A, ClipWarp<T, G> *Ws,
             for (uint32_t q = threadIdx.x; q < ns; q += NW * 32) {
                 const uint32_t e = Q.q[q];
                 const int slot = (int)(e & 0xffu);
-                clip_s2<T, K, G>(A, Ws[e >> 8], (int64_t)cbase + (e >> 8) * (G * 128) + slot, slot, flag);
+                clip_s2<T, K, G, PC>(A, Ws[e >> 8], (int64_t)cbase + (e >> 8) * (G * 128) + slot, slot, flag);
             }
         }
         __syncthreads();
@@ -501,9 +537,10 @@ __device__ __forceinline__ void clip_tile(const ClipArgs &A, ClipWarp<T, G> *Ws,
 
 // Undo one warp tile: planes from the clip-start copies, and the mixture
 // records the failed run touched.
-template <typename T, int K, int G>
+template <typename T, int K, int G, bool PC>
 __device__ __forceinline__ void clip_restore_tile(const ClipArgs &A, uint32_t wbase, int lane)
 {
+    constexpr int RNV = RecSel<T, K, PC>::NV, RB = RecSel<T, K, PC>::BYTES;
     constexpr int WT = G * 128;
     constexpr int SB = S1Rec<T>::BYTES;
     const int64_t P = A.dp.P;
@@ -525,15 +562,15 @@ __device__ __forceinline__ void clip_restore_tile(const ClipArgs &A, uint32_t wb
         const uint32_t word = __ldcg(A.touched + wbase / 32 + j / 32);
         if (word >> lane & 1u) {
             const int64_t p = (int64_t)wbase + j + lane;
-            const uint4 *src = reinterpret_cast<const uint4 *>(A.undo_gmm + p * Rec<T, K>::BYTES);
-            uint4 *dst = reinterpret_cast<uint4 *>(A.s.gmm + p * Rec<T, K>::BYTES);
+            const uint4 *src = reinterpret_cast<const uint4 *>(A.undo_gmm + p * RB);
+            uint4 *dst = reinterpret_cast<uint4 *>(A.s.gmm + p * RB);
 #pragma unroll
-            for (int i = 0; i < Rec<T, K>::NV; i++) dst[i] = src[i];
+            for (int i = 0; i < RNV; i++) dst[i] = src[i];
         }
     }
 }
 
-template <typename T, int K, int G>
+template <typename T, int K, int G, bool PC>
 __global__ void __launch_bounds__(CLIP_TPB, CLIP_MINB) clip_kernel(const __grid_constant__ ClipArgs A)
 {
     constexpr int NW = CLIP_TPB / 32;
@@ -576,7 +613,7 @@ __global__ void __launch_bounds__(CLIP_TPB, CLIP_MINB) clip_kernel(const __grid_
             const uint32_t ct = tile_s;
             __syncthreads();
             if (ct >= A.n_tiles) break;
-            clip_tile<T, K, G, NW>(A, W, Q, ct * (uint32_t)(NW * G * 128), warp, lane, flags, cnt_s);
+            clip_tile<T, K, G, NW, PC>(A, W, Q, ct * (uint32_t)(NW * G * 128), warp, lane, flags, cnt_s);
         }
         __syncthreads();
         for (int i = tid; i < (int)A.T * CTL_FIELDS; i += CLIP_TPB)
@@ -606,7 +643,7 @@ __global__ void __launch_bounds__(CLIP_TPB, CLIP_MINB) clip_kernel(const __grid_
         // frame is now known; later ones take this run's counts as a guess
         flags = tf;
         for (uint32_t wt = blockIdx.x * NW + warp; wt < A.n_tiles * NW; wt += gridDim.x * NW)
-            clip_restore_tile<T, K, G>(A, wt * (uint32_t)(G * 128), lane);
+            clip_restore_tile<T, K, G, PC>(A, wt * (uint32_t)(G * 128), lane);
         if (!clip_grid_sync(bar, ++nsync * gridDim.x, err)) return;
     }
 
@@ -642,7 +679,7 @@ __global__ void __launch_bounds__(CLIP_TPB, CLIP_MINB) clip_kernel(const __grid_
     }
 }
 
-template <typename T, int K, int G>
+template <typename T, int G>
 size_t clip_smem_bytes()
 {
     return sizeof(ClipWarp<T, G>) * (CLIP_TPB / 32);
@@ -650,30 +687,38 @@ size_t clip_smem_bytes()
 
 // CTAs of the clip kernel that fit on one SM (asked every launch: a launch
 // covers up to 32 frames, and the answer must match the device current now)
-template <typename T, int K, int G>
+template <typename T, int K, int G, bool PC>
 int clip_blocks_per_sm()
 {
     int b = 0;
-    const size_t sm = clip_smem_bytes<T, K, G>();
-    if (cudaFuncSetAttribute(clip_kernel<T, K, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, clip_kernel<T, K, G>, CLIP_TPB, sm) != cudaSuccess)
+    const size_t sm = clip_smem_bytes<T, G>();
+    if (cudaFuncSetAttribute(clip_kernel<T, K, G, PC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, clip_kernel<T, K, G, PC>, CLIP_TPB, sm) != cudaSuccess)
         b = 0;
     return b;
 }
 
-template <typename T, int K>
-cudaError_t launch_clip_t(const ClipArgs &a0, int n_sm, cudaStream_t st)
+template <typename T, int K, bool PC>
+cudaError_t launch_clip_pc(const ClipArgs &a0, int n_sm, cudaStream_t st)
 {
     constexpr int G = CLIP_G;
     constexpr int CT = CLIP_TPB / 32 * G * 128;   // pixels per CTA tile
     ClipArgs a = a0;
     a.n_tiles = (uint32_t)((a.dp.P + CT - 1) / CT);
-    const int bps = clip_blocks_per_sm<T, K, G>();
+    const int bps = clip_blocks_per_sm<T, K, G, PC>();
     if (bps < 1) return cudaErrorInvalidConfiguration;
     const int grid = (int)min((int64_t)bps * n_sm, (int64_t)a.n_tiles);
     void *args[] = {(void *)&a};
-    return cudaLaunchCooperativeKernel((const void *)clip_kernel<T, K, G>, dim3(grid), dim3(CLIP_TPB), args,
-                                       clip_smem_bytes<T, K, G>(), st);
+    return cudaLaunchCooperativeKernel((const void *)clip_kernel<T, K, G, PC>, dim3(grid), dim3(CLIP_TPB), args,
+                                       clip_smem_bytes<T, G>(), st);
+}
+
+template <typename T, int K>
+cudaError_t launch_clip_t(const ClipArgs &a, int n_sm, cudaStream_t st)
+{
+    if (a.dp.flags & COG_PERCHAN) return launch_clip_pc<T, K, true>(a, n_sm, st);
+    return launch_clip_pc<T, K, false>(a, n_sm, st);
 }
 
 }  // namespace cog

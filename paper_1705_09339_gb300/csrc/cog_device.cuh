@@ -352,6 +352,196 @@ __device__ __forceinline__ MixOut mix_step(Mix<K> &m, const float I[3], float a,
     return o;
 }
 
+// --------------------------------------- per-channel mixtures (COG_PERCHAN)
+// Each channel has its own K one-dimensional components with their own
+// weights.  Record: per component (w0 w1 w2 mu0 mu1 mu2 v0 v1 v2), padded to
+// a 16-byte multiple.
+template <typename T, int K> struct RecPC {
+    static constexpr int NE = 9 * K;
+    static constexpr int NV = (NE * Store<T>::bytes + 15) / 16;
+    static constexpr int BYTES = NV * 16;
+};
+
+template <int K> struct MixPC {
+    float w[3][K], mu[3][K], v[3][K];
+};
+
+struct MixOutPC {
+    int fg;          // 1 = some channel is foreground (the pixel label)
+    int fg_c[3];     // per channel
+    int tgt[3];      // per channel: matched or restarted component
+    float Mhat;      // largest per-channel match statistic (1 if unmatched)
+};
+
+template <typename T, int K>
+__device__ __forceinline__ void mixpc_unpack(const uint4 *u, MixPC<K> &m)
+{
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            m.w[c][k] = rec_elem<T, K>(u, 9 * k + c);
+            m.mu[c][k] = rec_elem<T, K>(u, 9 * k + 3 + c);
+            m.v[c][k] = rec_elem<T, K>(u, 9 * k + 6 + c);
+        }
+    }
+}
+
+template <typename T, int K>
+__device__ __forceinline__ void mixpc_pack(const MixPC<K> &m, uint4 *u)
+{
+    constexpr int NV = RecPC<T, K>::NV;
+    constexpr int NE = RecPC<T, K>::NE;
+#pragma unroll
+    for (int i = 0; i < NV; i++) u[i] = make_uint4(0, 0, 0, 0);
+#pragma unroll
+    for (int e = 0; e < NE; e++) {
+        const int k = e / 9, f = e % 9, c = f % 3;
+        const float x = f < 3 ? m.w[c][k] : (f < 6 ? m.mu[c][k] : m.v[c][k]);
+        const uint32_t b = Store<T>::bits(x);
+        if (Store<T>::bytes == 4) {
+            u4set(u[e >> 2], e & 3, b);
+        } else {
+            uint32_t w = u4get(u[e >> 3], (e >> 1) & 3);
+            w |= (e & 1) ? (b << 16) : b;
+            u4set(u[e >> 3], (e >> 1) & 3, w);
+        }
+    }
+}
+
+// One channel's step of Eq. 2 on its own 1-D mixture, with the same
+// decisions and arithmetic as mix_step: rank by w^2 / v (cross-multiplied,
+// ties to the lower index), first match in rank order, background iff the
+// weight ranked before it is <= T, update at rate a, restart the
+// lowest-ranked component on no match, renormalise.
+template <int K>
+__device__ __forceinline__ void mix_step_channel(float (&w)[K], float (&mu)[K], float (&v)[K], float I, float a,
+                                                 const DevParams &dp, int &fg, int &tgt, float &M)
+{
+    int pos[K];
+    float wsq[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) wsq[k] = w[k] * w[k];
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        int cnt = 0;
+#pragma unroll
+        for (int j = 0; j < K; j++) {
+            if (j == k) continue;
+            const float x = wsq[j] * v[k], y = wsq[k] * v[j];
+            cnt += (x > y) || (x == y && j < k);
+        }
+        pos[k] = cnt;
+    }
+    int match = -1, mpos = K;
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        const float d = I - mu[k];
+        if (d * d < dp.lam2 * v[k] && pos[k] < mpos) { mpos = pos[k]; match = k; }
+    }
+    float tm = 0.f;
+    fg = 1;
+    if (match >= 0) {
+        float S = 0.f;
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            if (pos[k] < mpos) S += w[k];
+            if (k == match) {
+                const float d = I - mu[k];
+                tm = __fdividef(d * d, dp.lam2 * v[k]);
+            }
+        }
+        fg = !(S <= dp.T_bg);
+    }
+    M = match >= 0 ? (tm < 1.f ? tm : 1.f) : 1.f;
+    const float b = 1.f - a;
+    if (match >= 0) {
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            w[k] = b * w[k] + (k == match ? a : 0.f);
+            if (k == match) {
+                mu[k] = mu[k] + a * (I - mu[k]);
+                const float d = I - mu[k];
+                v[k] = clampf(b * v[k] + a * d * d, dp.var_min, dp.var_max);
+            }
+        }
+        tgt = match;
+    } else {
+        tgt = 0;
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            w[k] = b * w[k];
+            if (pos[k] == K - 1) {
+                tgt = k;
+                w[k] = dp.w_init;
+                mu[k] = I;
+                v[k] = dp.var_init;
+            }
+        }
+    }
+    float sum = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; k++) sum += w[k];
+    const float inv = 1.f / sum;
+#pragma unroll
+    for (int k = 0; k < K; k++) w[k] = w[k] * inv;
+}
+
+template <int K>
+__device__ __forceinline__ MixOutPC mix_step_pc(MixPC<K> &m, const float I[3], float a, const DevParams &dp)
+{
+    MixOutPC o;
+    o.fg = 0;
+    o.Mhat = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        float M;
+        mix_step_channel<K>(m.w[c], m.mu[c], m.v[c], I[c], a, dp, o.fg_c[c], o.tgt[c], M);
+        o.fg |= o.fg_c[c];
+        o.Mhat = M > o.Mhat ? M : o.Mhat;
+    }
+    return o;
+}
+
+// Abrupt illumination change with per-channel mixtures: every channel that
+// decided foreground gives its matched or new component the weight w_illum.
+template <int K>
+__device__ __forceinline__ void illum_response_pc(MixPC<K> &m, const MixOutPC &o, float w_illum)
+{
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        if (!o.fg_c[c]) continue;
+        float so = 0.f;
+#pragma unroll
+        for (int k = 0; k < K; k++) if (k != o.tgt[c]) so += m.w[c][k];
+        if (so > 0.f) {
+#pragma unroll
+            for (int k = 0; k < K; k++)
+                m.w[c][k] = (k == o.tgt[c]) ? w_illum : m.w[c][k] * (1.f - w_illum) / so;
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; k++) if (k == o.tgt[c]) m.w[c][k] = 1.f;
+        }
+    }
+}
+
+// Transition update with per-channel mixtures: each channel's stage-1
+// values take that channel's target component.
+template <typename T, int K>
+__device__ __forceinline__ void s1_reseed_pc(const MixPC<K> &m, const MixOutPC &o, uint32_t qab, S1Rec<T> &r)
+{
+#pragma unroll
+    for (int i = 0; i < S1Rec<T>::NV; i++) r.u[i] = make_uint4(0, 0, 0, 0);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            if (k == o.tgt[c]) { r.set(c, m.mu[c][k]); r.set(3 + c, m.v[c][k]); }
+        }
+    }
+    r.set_qab(qab);
+}
+
 // COG_MODE1 (the Fig. 1 reading: stage 1 is the mixture's rank-1 mode).
 // On the transition to stage 2 the stage-1 copy is written back into the
 // component it mirrors; after the update the copy follows the component

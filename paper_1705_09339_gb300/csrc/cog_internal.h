@@ -82,7 +82,7 @@ struct Layout {
 };
 
 int elem_bytes(int dtype);
-int rec_bytes(int dtype, int K);
+int rec_bytes(int dtype, int K, bool perchan);
 int s1_bytes(int dtype);
 bool make_layout(const cog_params &p, Layout &L);
 
@@ -114,6 +114,7 @@ struct BatchGroupDev {
     const uint32_t *k2_pre;  // [n + 1] prefix of the mixture-stage CTAs given to the
                              //         active streams (in proportion to their pixels)
     int n;
+    int pc;                  // 1: the group's streams use per-channel mixtures
 };
 
 // Launch shape of the two cascade kernels.

@@ -160,12 +160,91 @@ cudaError_t launch_plain_t(const DevParams &dp, const StatePtrs &s, const uint8_
     return cudaGetLastError();
 }
 
+// The same training with per-channel mixtures (COG_PERCHAN): each channel's
+// component 0 starts at (I_0c, var_init, 1), the per-channel step runs over
+// frames 1..N-1, and each channel's running average takes that channel's
+// top-ranked component.
+template <typename T, int K>
+__global__ void __launch_bounds__(128) warmup_pc_kernel(const DevParams dp, const StatePtrs s,
+                                                        const uint8_t *frames, int N, int r1, int r2)
+{
+    const int64_t p = (int64_t)blockIdx.x * 128 + threadIdx.x;
+    if (p >= dp.P) return;
+    const int64_t stride = dp.P * 3;
+    uint32_t prev[3];
+    MixPC<K> m;
+#pragma unroll
+    for (int c = 0; c < 3; c++) prev[c] = frames[p * 3 + c];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            m.w[c][k] = k == 0 ? 1.f : 0.f;
+            m.mu[c][k] = k == 0 ? (float)prev[c] : 0.f;
+            m.v[c][k] = dp.var_init;
+        }
+    }
+    uint32_t n0 = 0, n2 = 0;
+    int fg = 0;
+    const uint8_t *f = frames + p * 3;
+    for (int t = 1; t < N; t++) {
+        f += stride;
+        float I[3];
+        int R = 0;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const uint32_t v = f[c];
+            const int d = abs((int)v - (int)prev[c]);
+            R = d > R ? d : R;
+            prev[c] = v;
+            I[c] = (float)v;
+        }
+        n0 += R <= r1;
+        n2 += R > r2;
+        fg = mix_step_pc<K>(m, I, dp.alpha, dp).fg;
+    }
+    uint4 u[RecPC<T, K>::NV];
+    mixpc_pack<T, K>(m, u);
+    uint4 *dst = reinterpret_cast<uint4 *>(s.gmm + p * RecPC<T, K>::BYTES);
+#pragma unroll
+    for (int i = 0; i < RecPC<T, K>::NV; i++) dst[i] = u[i];
+    const uint32_t n = (uint32_t)(N - 1);
+    uint32_t qa = (255u * n0 + n / 2) / n;
+    uint32_t qb = (255u * n2 + n / 2) / n;
+    if (qb > 255u - qa) qb = 255u - qa;
+    S1Rec<T> r;
+#pragma unroll
+    for (int i = 0; i < S1Rec<T>::NV; i++) r.u[i] = make_uint4(0, 0, 0, 0);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        float wsq[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) wsq[k] = m.w[c][k] * m.w[c][k];
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            int cnt = 0;
+#pragma unroll
+            for (int j = 0; j < K; j++) {
+                if (j == k) continue;
+                const float x = wsq[j] * m.v[c][k], y = wsq[k] * m.v[c][j];
+                cnt += (x > y) || (x == y && j < k);
+            }
+            if (cnt == 0) { r.set(c, m.mu[c][k]); r.set(3 + c, m.v[c][k]); }
+        }
+    }
+    r.set_qab(qa | (qb << 8));
+    r.store(s.s1, p);
+    reinterpret_cast<T *>(s.conf)[p] = Store<T>::from_f(0.5f);
+    s.jl[p] = prev[0] | (prev[1] << 8) | (prev[2] << 16) | ((uint32_t)fg << 24);
+}
+
 template <typename T, int K>
 cudaError_t launch_warmup_t(const DevParams &dp, const StatePtrs &s, const uint8_t *frames, int N,
                             int r1, int r2, cudaStream_t st)
 {
     const int64_t grid = (dp.P + 127) / 128;
-    warmup_kernel<T, K><<<(unsigned)grid, 128, 0, st>>>(dp, s, frames, N, r1, r2);
+    if (dp.flags & COG_PERCHAN) warmup_pc_kernel<T, K><<<(unsigned)grid, 128, 0, st>>>(dp, s, frames, N, r1, r2);
+    else warmup_kernel<T, K><<<(unsigned)grid, 128, 0, st>>>(dp, s, frames, N, r1, r2);
     return cudaGetLastError();
 }
 

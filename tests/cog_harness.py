@@ -109,7 +109,9 @@ def compare_stream(gm, gs, om, os_, near):
 def state_errors(g, o, mask):
     """Largest relative error of each model field over the pixels in mask."""
     out = {}
-    for k in ("w", "mu", "var", "rga_m", "rga_v", "conf"):
+    for k in ("w", "mu", "var", "rga_m", "rga_v", "conf", "wc"):
+        if k not in g:
+            continue
         a, b = g[k][mask], o[k][mask]
         out[k] = float(rel_err(a, b).max()) if a.size else 0.0
     for k in ("label", "prev", "qa", "qb"):
@@ -120,10 +122,10 @@ def state_errors(g, o, mask):
 def oracle_state(o):
     s = o.state
     return dict(w=s.w, mu=s.mu, var=s.var, rga_m=s.rga_m, rga_v=s.rga_v, conf=s.conf, label=s.label,
-                prev=s.prev, kde=s.kde, qa=s.qa, qb=s.qb, top=s.top)
+                prev=s.prev, kde=s.kde, qa=s.qa, qb=s.qb, top=s.top, wc=s.wc)
 
 
-def random_state(rng, P, K, dtype="f32", fg_frac=0.2, mode1=False):
+def random_state(rng, P, K, dtype="f32", fg_frac=0.2, mode1=False, perchan=False):
     """A seeded model state with the value ranges the method produces,
     rounded to the storage type so both sides start from the same values."""
     q = {"f32": np.float32, "f16": np.float16, "bf16": None}[dtype]
@@ -159,6 +161,11 @@ def random_state(rng, P, K, dtype="f32", fg_frac=0.2, mode1=False):
     if mode1:
         st["rga_m"] = st["mu"][np.arange(P), top].copy()
         st["rga_v"] = st["var"][np.arange(P), top].copy()
+    if perchan:
+        wc = rng.gamma(0.7, size=(P, 3, K))
+        wc[rng.random((P, 3, K)) < 0.25] = 0.0
+        wc[:, :, 0] += 1e-3
+        st["wc"] = r(wc / wc.sum(axis=2, keepdims=True))
     return st
 
 
@@ -181,6 +188,7 @@ def random_frame(rng, st, mix=(0.4, 0.3, 0.3)):
 
 def set_oracle_state(o, st):
     s = o.state
-    for k in ("w", "mu", "var", "rga_m", "rga_v", "conf", "label", "prev", "kde", "qa", "qb", "top"):
-        getattr(s, k)[...] = st[k]
+    for k in ("w", "mu", "var", "rga_m", "rga_v", "conf", "label", "prev", "kde", "qa", "qb", "top", "wc"):
+        if k in st:
+            getattr(s, k)[...] = st[k]
     s.illum[:] = 0

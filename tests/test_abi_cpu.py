@@ -59,11 +59,16 @@ def test_default_params_and_layout(cog):
     assert cog.cog_state_bytes(p) == L.total
     p32 = cog.cog_default_params(160, 120, 3)
     assert cog.cog_state_layout(p32).rec_bytes == 96 and cog.cog_state_layout(p32).s1_bytes == 32
+    # per-channel mixtures: K x 9 values per record (K=5 FP16: 90 -> 96 bytes)
+    pc = cog.cog_default_params(1920, 1080, 5, state_dtype="f16")
+    pc.flags |= cog.COG_PERCHAN
+    assert cog.cog_state_layout(pc).rec_bytes == 96
 
 
 @pytest.mark.parametrize("field,value", [("K", 0), ("K", 9), ("width", 0), ("alpha", 0.0), ("alpha", 1.5),
                                          ("var_min", 0.0), ("kde_bw", 0), ("kde_bw", 33), ("r2", -1),
-                                         ("illum_permille", 1001), ("flags", 64), ("state_dtype", 3), ("skip_period", 0),
+                                         ("illum_permille", 1001), ("flags", 128), ("flags", 15 | 32 | 64),
+                                         ("state_dtype", 3), ("skip_period", 0),
                                          ("w_illum", 1.0), ("T_bg", 1.5)])
 def test_invalid_params_rejected(cog, field, value):
     p = cog.cog_default_params(64, 48, 3)

@@ -19,8 +19,10 @@ def cog():
     return cog
 
 
+# "+pc": per-channel mixtures (a group of its own in the batch)
 SPECS = [(160, 120, 3, "f32"), (320, 240, 5, "f16"), (97, 61, 3, "f32"), (640, 480, 5, "f16"),
-         (33, 1, 5, "f16"), (200, 100, 3, "bf16"), (160, 120, 5, "f16")]
+         (33, 1, 5, "f16"), (200, 100, 3, "bf16"), (160, 120, 5, "f16"), (128, 96, 5, "f16+pc"),
+         (64, 48, 3, "f32+pc")]
 
 
 def _streams(n_train=20, n_test=6):
@@ -34,7 +36,10 @@ def _streams(n_train=20, n_test=6):
 
 
 def _ctx(cog, w, h, k, dt, fr, n_train, stream):
-    p = cog.cog_default_params(w, h, k, state_dtype=dt)
+    base, _, pc = dt.partition("+")
+    p = cog.cog_default_params(w, h, k, state_dtype=base)
+    if pc:
+        p.flags |= cog.COG_PERCHAN
     c = cog.cog_create(p, stream)
     t = torch.from_numpy(fr[:n_train].reshape(n_train, h, w, 3)).cuda()
     cog.cog_train_prior(c, t, n_train)
@@ -69,8 +74,9 @@ def test_batch_equals_single_stream_apply(cog):
     for (ca, pa), (cb, pb) in zip(single, batched):
         sa = cog.decode_state(cog.cog_export_state(ca, pa), pa)
         sb = cog.decode_state(cog.cog_export_state(cb, pb), pb)
-        for key in ("w", "mu", "var", "rga_m", "rga_v", "conf", "label", "prev"):
-            assert np.array_equal(sa[key], sb[key]), key
+        for key in ("w", "wc", "mu", "var", "rga_m", "rga_v", "conf", "label", "prev"):
+            if key in sa:
+                assert np.array_equal(sa[key], sb[key]), key
         la, ta = cog.cog_read_stats(ca)
         lb, tb = cog.cog_read_stats(cb)
         assert la == lb and ta == tb

@@ -167,6 +167,20 @@ def test_clip_mode1_equals_frame_by_frame(dtype):
     a.close(); b.close()
 
 
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_clip_perchan_equals_frame_by_frame(dtype):
+    W, H, K, NT, NF = 200, 150, 5, 40, 50
+    fr = _scene(W, H, 12, NT, NF, kind="dynamic", fg_frac=0.05, switch_at=30)
+    d = params(W, H, K, flags=15 | 64)
+    a, b = _pair(d, dtype, fr[:NT])
+    am, asg, ast = a.apply(fr[NT:])
+    bm, bsg, bst = _clip(b, fr[NT:], [32, 18])
+    assert np.array_equal(am, bm) and np.array_equal(asg, bsg)
+    assert [s["illum_flag"] for s in ast] == [s["illum_flag"] for s in bst]
+    _same_state(a, b)
+    a.close(); b.close()
+
+
 def test_clip_fp32_matches_oracle():
     # the 160x120 workload through the clip path against the FP64 oracle
     from cogsynth import Scene

@@ -156,13 +156,13 @@ def test_temporal_sampling_stream_matches_oracle():
 
 # --------------------------------------------------- seeded random states
 @pytest.mark.parametrize("K", [1, 3, 5, 8])
-@pytest.mark.parametrize("flags", [15, 0, 1 | 2, 4 | 8, 15 | 32, 2 | 32])
+@pytest.mark.parametrize("flags", [15, 0, 1 | 2, 4 | 8, 15 | 32, 2 | 32, 15 | 64, 64])
 def test_seeded_state_steps_match_oracle(K, flags):
     rng = np.random.default_rng(100 + K * 16 + flags)
     W, H = 53, 41
     P = W * H
     d = params(W, H, K, flags=flags)
-    st = random_state(rng, P, K, mode1=bool(flags & 32))
+    st = random_state(rng, P, K, mode1=bool(flags & 32), perchan=bool(flags & 64))
     g = GpuRun(d)
     g.train(np.zeros((2, P, 3), np.uint8))
     g.set_state(st)
@@ -180,8 +180,9 @@ def test_seeded_state_steps_match_oracle(K, flags):
     gst = g.state()
     e = state_errors(gst, oracle_state(o), ~ever)
     g.close()
-    for k in ("w", "mu", "var", "rga_m", "rga_v", "conf"):
-        assert e[k] <= TOL, (k, e[k])
+    for k in ("w", "mu", "var", "rga_m", "rga_v", "conf", "wc"):
+        if k in e:
+            assert e[k] <= TOL, (k, e[k])
     assert e["label"] == 0 and e["prev"] == 0
     if flags & 32:
         assert np.array_equal(gst["top"][~ever], o.state.top[~ever])
@@ -379,3 +380,50 @@ def test_mode1_stream_matches_oracle():
     for k in ("w", "mu", "var", "rga_m", "rga_v", "conf"):
         assert e[k] <= TOL, (k, e[k])
     assert np.array_equal(gs["top"][~ever], os_["top"][~ever])
+
+
+def test_perchan_stream_matches_oracle():
+    # per-channel independent mixtures on the 160x120 workload, FP32
+    W, H, K = 160, 120, 3
+    (gm, gsm, gst, gs), (om, osm, near, ost, os_) = _stream(W, H, K, 200, 300, "rects", flags=15 | 64)
+    agree, unexplained, ever = compare_stream(gm, gsm, om, osm, near)
+    assert unexplained == 0 and agree >= 0.9999
+    e = state_errors(gs, os_, ~ever)
+    for k in ("wc", "mu", "var", "rga_m", "rga_v", "conf"):
+        assert e[k] <= TOL, (k, e[k])
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16"])
+def test_perchan_on_gray_input_equals_shared_weights_on_the_gpu(dtype):
+    # R = G = B: the per-channel kernels must reproduce the shared-weight
+    # kernels bit for bit (masks, stage maps, means, variances; each
+    # channel's weights equal to the shared weights)
+    from cogsynth import Scene
+    W, H, K, NT, NF = 96, 64, 5, 30, 40
+    sc = Scene(W, H, 23, kind="dynamic", n_train=NT, fg_frac=0.1, switch_at=20)
+    fr, _ = sc.frames(0, NT + NF)
+    gray = np.ascontiguousarray(np.repeat(fr[..., :1], 3, axis=-1))
+    a = GpuRun(params(W, H, K), dtype)
+    b = GpuRun(params(W, H, K, flags=15 | 64), dtype)
+    a.train(gray[:NT])
+    b.train(gray[:NT])
+    am, asg, _ = a.apply(gray[NT:])
+    bm, bsg, _ = b.apply(gray[NT:])
+    assert np.array_equal(am, bm) and np.array_equal(asg, bsg)
+    sa, sb = a.state(), b.state()
+    assert np.array_equal(sa["mu"], sb["mu"]) and np.array_equal(sa["var"], sb["var"])
+    for c in range(3):
+        assert np.array_equal(sb["wc"][:, c, :], sa["w"])
+    a.close(); b.close()
+
+
+def test_plain_gmm_refused_with_perchan():
+    from paper_1705_09339_gb300 import cog
+    g = GpuRun(params(32, 16, 3, flags=15 | 64))
+    g.train(np.zeros((2, 32 * 16, 3), np.uint8))
+    f = torch.zeros((16, 32, 3), dtype=torch.uint8, device="cuda")
+    m = torch.zeros((16, 32), dtype=torch.uint8, device="cuda")
+    with pytest.raises(cog.CogError) as e:
+        cog.cog_apply_plain_gmm(g.ctx, f, m)
+    assert e.value.status == cog.COG_ERR_INVALID_ARG
+    g.close()
