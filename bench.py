@@ -78,7 +78,7 @@ def peaks():
 
 
 # ---------------------------------------------------------------- byte model
-def cog_bytes(stats: dict, P: int, elem: int, K: int):
+def cog_bytes(stats: dict, P: int, elem: int, K: int, nv: int = 7):
     """Algorithmic bytes the cascade touches over a set of frames, from the
     per-stage occupancy counters and the per-stage byte table:
       every pixel (stage 0, first kernel): reads I, J, label, C and writes
@@ -96,7 +96,7 @@ def cog_bytes(stats: dict, P: int, elem: int, K: int):
     # a pixel skipped by the temporal sampling reads J, label and C and
     # writes its mask: 3 + 1 + e + 1
     k1 = (frames * P - skipped) * (9 + 2 * elem) + skipped * (5 + elem) + past0 * (2 + 12 * elem)
-    k2 = stats["n_gmm"] * (14 * K * elem + 96 + 6 * elem)
+    k2 = stats["n_gmm"] * (2 * nv * K * elem + 96 + 6 * elem)   # nv = 7, or 9 per-channel
     return int(k1), int(k2)
 
 
@@ -254,6 +254,8 @@ def run_ours(args, rank, local_rank, world):
         p_cog.flags |= cog.COG_SAMPLE
     if args.mode1:
         p_cog.flags |= cog.COG_MODE1
+    if args.perchan:
+        p_cog.flags |= cog.COG_PERCHAN
     p_gmm = cog.cog_default_params(W_, H_, K_, state_dtype="f16")
     tuned = None
     if args.autotune:
@@ -351,8 +353,9 @@ def run_ours(args, rank, local_rank, world):
         hbm, hbm_src = peaks()
         value = job_mpixel_per_s(P, args.steps, ms_c, world)
         value_g = job_mpixel_per_s(P, args.steps, ms_g, world)
-        bytes_c = sum(cog_bytes(st, P, 2, K_))
-        b1, b2 = cog_bytes(st_prof, P, 2, K_)
+        nv = 9 if args.perchan else 7
+        bytes_c = sum(cog_bytes(st, P, 2, K_, nv))
+        b1, b2 = cog_bytes(st_prof, P, 2, K_, nv)
         bytes_g = plain_bytes(args.steps, P, 2, K_)
         ach_c = bytes_c / (ms_c / 1e3) / 1e9
         ach_g = bytes_g / (ms_g / 1e3) / 1e9
@@ -371,8 +374,10 @@ def run_ours(args, rank, local_rank, world):
             "config": {"workload": f"{W_}x{H_} RGB u8 dynamic-background stream, K={K_}, FP16 state / FP32 math, "
                                    f"{N_TRAIN} train frames, fg {args.fg:.3f}, one frame per step"
                                    + (", temporal sampling on" if args.sample else "")
-                                   + (", stage 1 = the mixture's rank-1 mode (Fig. 1 reading)" if args.mode1 else ""),
+                                   + (", stage 1 = the mixture's rank-1 mode (Fig. 1 reading)" if args.mode1 else "")
+                                   + (", per-channel independent mixtures" if args.perchan else ""),
                        "temporal_sampling": bool(args.sample), "mode1": bool(args.mode1),
+                       "perchan": bool(args.perchan),
                        "width": W_, "height": H_, "K": K_, "state_dtype": "f16", "n_train": N_TRAIN,
                        "fg_frac": args.fg, "l2": "flushed (512 MB write) between timed steps",
                        "l2_fetch_bytes": args.l2_fetch,
@@ -875,6 +880,8 @@ def main():
                     help="hd: confidence-based temporal sampling on (saturated pixels every 4 frames)")
     ap.add_argument("--mode1", action="store_true",
                     help="hd: COG_MODE1, stage 1 as the mixture's rank-1 mode (the Fig. 1 reading)")
+    ap.add_argument("--perchan", action="store_true",
+                    help="hd: COG_PERCHAN, per-channel independent mixtures")
     ap.add_argument("--l2-fetch", type=int, default=32,
                     help="L2 fetch granularity in bytes for the process (-1 keeps the driver default)")
     args = ap.parse_args()

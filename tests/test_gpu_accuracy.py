@@ -103,6 +103,16 @@ def test_accuracy_per_config(name):
     g1.close()
     rep["mode1"] = {"oracle_misclass_vs_truth": _misclass(m1, gt), "f16_misclass_vs_truth": _misclass(gm1, gt),
                     "f16_mask_agreement_with_oracle": float((gm1 == m1).mean())}
+    # per-channel independent mixtures (COG_PERCHAN): oracle and FP16 GPU, reported
+    o2 = oracle_run(params(W, H, K, flags=15 | 64))
+    o2.train(frames[:NT])
+    m2 = np.stack([o2.apply(frames[NT + t], want_stage=False, want_near=False)[0] for t in range(NF)])
+    g2 = GpuRun(params(W, H, K, flags=15 | 64), "f16")
+    g2.train(frames_d[:NT])
+    gm2, _, _ = g2.apply(frames_d[NT:], stats=False)
+    g2.close()
+    rep["perchan"] = {"oracle_misclass_vs_truth": _misclass(m2, gt), "f16_misclass_vs_truth": _misclass(gm2, gt),
+                      "f16_mask_agreement_with_oracle": float((gm2 == m2).mean())}
     rep["cog_f16_vs_plain_misclass_ratio"] = rep["f16"]["misclass_vs_truth"] / max(1e-12, rep["plain_gmm_f16_misclass_vs_truth"])
     REPORT[name] = rep
     if c["kind"] == "dynamic":
