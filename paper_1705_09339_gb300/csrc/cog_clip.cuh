@@ -156,9 +156,9 @@ __device__ __forceinline__ void load_frame_words(const uint8_t *f, int64_t p0, i
 // in frame t: Eq. 2 on its record in place (the first touch in the clip
 // saves the original to the undo log), the illumination response when the
 // frame is flagged, the transition update of its stage-1 record, and its
-// confidence; its stage code goes to V.resst.  Kept out of line so that
-// the mixture's registers do not add to the per-frame state the caller
-// keeps live across it.
+// confidence; its stage code goes to V.resst.  (Inlined: an out-of-line
+// call, meant to keep the mixture's registers apart from the per-frame
+// state, measured slower.)
 template <typename T, int K, int G, bool PC>
 __device__ CLIP_S2_INLINE void clip_s2(const ClipArgs &A, ClipWarp<T, G> &V, int64_t p, int slot, bool flag)
 {
