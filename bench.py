@@ -336,9 +336,13 @@ def run_ours(args, rank, local_rank, world):
     if world > 1:
         dist.barrier()
     # the headline: frames streamed from host memory through the pipelined
-    # call (uploads and downloads overlap the kernels)
+    # call (uploads and downloads overlap the kernels); five calls over the
+    # pinned frames form one timed region (~20 ms), so that a single host
+    # hiccup does not decide the figure
+    E2E_REPS = 5
     t0 = time.perf_counter()
-    cog.cog_apply_host_frames(ctx_e, hf, hm)
+    for _ in range(E2E_REPS):
+        cog.cog_apply_host_frames(ctx_e, hf, hm)
     t_e2e = time.perf_counter() - t0
     # and the synchronous per-frame call, for comparison
     t0 = time.perf_counter()
@@ -405,8 +409,8 @@ def run_ours(args, rank, local_rank, world):
                                        "algorithmic_bytes_per_step": bytes_g // args.steps}},
             "speedup_vs_plain_gmm": round(ms_g / ms_c, 3),
             "stage_occupancy": {k: round(v, 5) for k, v in occ.items()},
-            "e2e": {"value": round(world * P * n_e2e / t_e2e / 1e6, 1), "unit": UNIT,
-                    "h2d_bytes_per_step": P * 3, "d2h_bytes_per_step": P, "steps": n_e2e,
+            "e2e": {"value": round(world * P * n_e2e * E2E_REPS / t_e2e / 1e6, 1), "unit": UNIT,
+                    "h2d_bytes_per_step": P * 3, "d2h_bytes_per_step": P, "steps": n_e2e * E2E_REPS,
                     "api": "cog_apply_host_frames (pinned host frames in, masks out; uploads and downloads "
                            "overlap the kernels; returns when every mask is on the host)",
                     "per_frame_sync_value": round(world * P * n_e2e / t_e2e_sync / 1e6, 1),
