@@ -312,6 +312,20 @@ def run_ours(args, rank, local_rank, world):
     timed(lambda i: cog.cog_apply(ctx, test[i], masks[i]), args.warmup + args.steps, args.steps)
     ms_k1, ms_k2, nprof = cog.cog_profile_end(ctx)
     _, tot2 = cog.cog_read_stats(ctx)
+    # the streaming floor at this size: the probe kernel moves stage 0's
+    # planes (16 B per pixel, no arithmetic) under the same flush and events
+    pr_jl = torch.randint(0, 2**31, (P,), dtype=torch.int32, device=dev)
+    pr_c = torch.randint(0, 2**15, (P,), dtype=torch.int16, device=dev)
+    pr_jo, pr_co = torch.empty_like(pr_jl), torch.empty_like(pr_c)
+    pr_m = torch.empty((P,), dtype=torch.uint8, device=dev)
+    probe = lambda i: cog.cog_probe_stream(pr_jl, pr_c, test[i], pr_jo, pr_co, pr_m, stream.cuda_stream)
+    ms_p = None
+    if P % 4 == 0 and (P * 3) % 16 == 0:   # the probe's frame words stay 16-byte aligned
+        timed(probe, 0, 3)
+        ev_p = timed(probe, args.warmup, args.steps)
+        torch.cuda.synchronize()
+        ms_p = sum(a.elapsed_time(b) for a, b in ev_p)
+    del pr_jl, pr_c, pr_jo, pr_co, pr_m
     ms_c = sum(a.elapsed_time(b) for a, b in ev_c)
     ms_g = sum(a.elapsed_time(b) for a, b in ev_g)
     st = dict(n_stage=[b - a for a, b in zip(tot0["n_stage"], tot1["n_stage"])],
@@ -392,7 +406,15 @@ def run_ours(args, rank, local_rank, world):
                          "frac": round(ach_d / hbm, 4), "traffic": tr_c, "peak_source": hbm_src,
                          "kernel": dom, "ms_per_launch": round(ms_d / args.steps, 5),
                          "algorithmic_bytes_per_launch": b_d // args.steps,
-                         "issue": issue_rate(dom, ms_d / args.steps)},
+                         "issue": issue_rate(dom, ms_d / args.steps),
+                         "floor": None if ms_p is None else {"kernel": "probe_stream_kernel (cog_probe_stream)",
+                                   "bytes_per_launch": 16 * P, "ms_per_launch": round(ms_p / args.steps, 5),
+                                   "achieved": round(16 * P * args.steps / (ms_p / 1e3) / 1e9, 1),
+                                   "frac_of_peak": round(16 * P * args.steps / (ms_p / 1e3) / 1e9 / hbm, 4),
+                                   "kernel_frac_of_floor": round(ach_d / (16 * P * args.steps / (ms_p / 1e3) / 1e9), 4),
+                                   "note": "stage 0's planes streamed with no arithmetic (9 B/px in, 7 out), "
+                                           "one launch per frame under the same L2 flush and events: the "
+                                           "bandwidth a pass of this size reaches at best"}},
             "kernels": {"stage01_kernel": {"ms_per_launch": round(ms_k1 / args.steps, 5),
                                            "achieved_gbs": round(ach_1, 1),
                                            "algorithmic_bytes_per_launch": b1 // args.steps},

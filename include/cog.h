@@ -251,6 +251,21 @@ cog_status cog_server_destroy(cog_server *s);
  * them. */
 cog_status cog_selftest_bounded_wait(int32_t limit_ms, uint32_t *error_word, double *elapsed_ms);
 
+/* Measurement aid; the paper has no counterpart.  One pass over the planes
+ * that stage 0 touches when every pixel passes it, with no arithmetic, to
+ * time the streaming floor of a kernel of that size: for every pixel p
+ *   jl_out[p]   = frame[3p] | frame[3p+1] << 8 | frame[3p+2] << 16
+ *                 | (jl_in[p] & 0xff000000)       (this frame, previous label)
+ *   conf_out[p] = conf_in[p]                      (16-bit confidence)
+ *   mask[p]     = jl_in[p] >> 24
+ * 9 bytes per pixel in, 7 out, one thread per 4 pixels in 128-thread CTAs as
+ * the stage-0/1 kernel.  P > 0 and a multiple of 4; every pointer 16-byte
+ * aligned, device memory owned by the caller, outputs disjoint from inputs.
+ * Launched on cuda_stream (a cudaStream_t) and not waited for.  Returns
+ * COG_ERR_INVALID_ARG for bad arguments, COG_ERR_CUDA for a launch error. */
+cog_status cog_probe_stream(const uint32_t *jl_in, const uint16_t *conf_in, const uint8_t *frame,
+                            uint32_t *jl_out, uint16_t *conf_out, uint8_t *mask, int64_t P, void *cuda_stream);
+
 /* The comparison baseline: one frame of the plain Stauffer-Grimson mixture
  * (Eq. 2 at rate alpha, no cascade, no prior, no confidence) on this
  * context's mixture state.  Same buffer rules as cog_apply. */

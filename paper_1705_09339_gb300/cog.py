@@ -81,6 +81,7 @@ def _load() -> C.CDLL:
         "cog_apply_clip": (C.c_int, [vp, vp, i32, vp, vp, P(cog_stats)]),
         "cog_clip_runs": (C.c_int, [vp, P(i32)]),
         "cog_selftest_bounded_wait": (C.c_int, [i32, P(C.c_uint32), P(C.c_double)]),
+        "cog_probe_stream": (C.c_int, [vp, vp, vp, vp, vp, vp, C.c_int64, vp]),
         "cog_apply_plain_gmm": (C.c_int, [vp, vp, vp]),
         "cog_apply_host": (C.c_int, [vp, vp, vp]),
         "cog_apply_host_noalloc": (C.c_int, [vp, vp, vp]),
@@ -195,6 +196,15 @@ def cog_selftest_bounded_wait(limit_ms: int):
     w, ms = C.c_uint32(0), C.c_double(0.0)
     _check(lib.cog_selftest_bounded_wait(int(limit_ms), C.byref(w), C.byref(ms)))
     return w.value, ms.value
+
+
+def cog_probe_stream(jl_in, conf_in, frame, jl_out, conf_out, mask, stream=None) -> None:
+    """Streaming probe over stage 0's planes (no arithmetic): jl_out = this
+    frame with jl_in's labels, conf_out = conf_in, mask = jl_in's labels.
+    jl: uint32 [P], conf: 16-bit [P], frame: uint8 [P, 3], mask: uint8 [P]."""
+    P = int(mask.numel())
+    _check(lib.cog_probe_stream(_ptr(jl_in), _ptr(conf_in), _ptr(frame), _ptr(jl_out), _ptr(conf_out),
+                                _ptr(mask), P, stream))
 
 
 def cog_apply_plain_gmm(ctx, frame, mask) -> None:

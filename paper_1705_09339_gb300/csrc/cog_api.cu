@@ -30,6 +30,8 @@ cudaError_t launch_clip_f32(int, const ClipArgs &, int, cudaStream_t);
 cudaError_t launch_clip_f16(int, const ClipArgs &, int, cudaStream_t);
 cudaError_t launch_clip_bf16(int, const ClipArgs &, int, cudaStream_t);
 cudaError_t run_wait_selftest(uint64_t limit_ns, uint32_t *error_word, float *elapsed_ms);
+cudaError_t launch_probe_stream(const uint32_t *jl_in, const uint16_t *conf_in, const uint8_t *frame,
+                                uint32_t *jl_out, uint16_t *conf_out, uint8_t *mask, int64_t P, cudaStream_t st);
 int k1_batch_blocks_per_sm_f32(const LaunchCfg &);
 int k1_batch_blocks_per_sm_f16(const LaunchCfg &);
 int k1_batch_blocks_per_sm_bf16(const LaunchCfg &);
@@ -513,6 +515,21 @@ cog_status cog_selftest_bounded_wait(int32_t limit_ms, uint32_t *error_word, dou
     cudaError_t e = run_wait_selftest((uint64_t)limit_ms * 1000000ull, error_word, &ms);
     if (e != cudaSuccess) return set_err(nullptr, COG_ERR_CUDA, "bounded-wait self-test: %s", cudaGetErrorString(e));
     *elapsed_ms = ms;
+    return COG_OK;
+}
+
+cog_status cog_probe_stream(const uint32_t *jl_in, const uint16_t *conf_in, const uint8_t *frame,
+                            uint32_t *jl_out, uint16_t *conf_out, uint8_t *mask, int64_t P, void *cuda_stream)
+{
+    if (P <= 0 || P % 4 != 0 || P / 4 > (int64_t)0x7fffffff * 128)
+        return set_err(nullptr, COG_ERR_INVALID_ARG, "P must be a positive multiple of 4");
+    const void *ptrs[6] = {jl_in, conf_in, frame, jl_out, conf_out, mask};
+    for (const void *q : ptrs)
+        if (!q || (reinterpret_cast<uintptr_t>(q) & 15u))
+            return set_err(nullptr, COG_ERR_INVALID_ARG, "every buffer must be non-NULL and 16-byte aligned");
+    cudaError_t e = launch_probe_stream(jl_in, conf_in, frame, jl_out, conf_out, mask, P,
+                                        static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return set_err(nullptr, COG_ERR_CUDA, "cog_probe_stream: %s", cudaGetErrorString(e));
     return COG_OK;
 }
 

@@ -90,3 +90,19 @@ def test_null_context_calls_fail_cleanly(cog):
     for bad in (0, 2001):
         assert cog.lib.cog_selftest_bounded_wait(bad, C.byref(w), C.byref(ms)) == cog.COG_ERR_INVALID_ARG
     assert cog.lib.cog_selftest_bounded_wait(10, None, None) == cog.COG_ERR_INVALID_ARG
+
+
+def test_probe_stream_rejects_bad_arguments(cog):
+    """The streaming probe validates its arguments before any launch."""
+    import numpy as np
+    bufs = [np.zeros(64, dtype=np.uint8) for _ in range(6)]
+    good = [b.ctypes.data + (-b.ctypes.data) % 16 for b in bufs]   # 16-byte aligned addresses
+    # (no valid call is made here: every case below fails validation)
+    for P in (0, -4, 6):
+        assert cog.lib.cog_probe_stream(*good, P, None) == cog.COG_ERR_INVALID_ARG
+    for i in range(6):
+        args = list(good)
+        args[i] = None
+        assert cog.lib.cog_probe_stream(*args, 8, None) == cog.COG_ERR_INVALID_ARG
+        args[i] = good[i] + 4
+        assert cog.lib.cog_probe_stream(*args, 8, None) == cog.COG_ERR_INVALID_ARG
