@@ -710,3 +710,206 @@ int orc_plain_gmm(const orc_params *pr, double *w_all, double *mu_all,
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Spatio-temporal grouping, training side (Sec. 2, "Clustering Similar */
+/* Background - Spatio-Temporal Grouping", steps 1-2): replay the       */
+/* mixture warm-up over the N training frames and, after each update at */
+/* frames 1..N-1, record the pixel's dominant mode (largest            */
+/* omega^2 / vbar, lowest index on ties): its mean variance vbar and    */
+/* its weight omega.  The features are the spreads of the two series    */
+/* over time, as population standard deviations, in the fixed-point    */
+/* codes sd_v * 64 and sd_w * 65536 (round half up, at most 65535).    */
+/* ------------------------------------------------------------------ */
+int orc_group_features(const orc_params *pr, const uint8_t *frames, int N,
+                       uint16_t *code_v, uint16_t *code_w)
+{
+    if (check_params(pr) || (pr->flags & ORC_PERCHAN) || !frames || !code_v || !code_w || N < 2) return -1;
+    const int64_t P = (int64_t)pr->width * pr->height;
+    const int K = pr->K;
+    double *w = (double *)malloc(sizeof(double) * (size_t)(P * K));
+    double *mu = (double *)malloc(sizeof(double) * (size_t)(P * K * 3));
+    double *var = (double *)malloc(sizeof(double) * (size_t)(P * K * 3));
+    double *sum = (double *)calloc((size_t)(P * 4), sizeof(double));   /* per pixel: sv, svv, sw, sww */
+    double *ref = (double *)malloc(sizeof(double) * (size_t)(P * 2));  /* first value of each series */
+    uint8_t *mask = (uint8_t *)malloc((size_t)P);
+    if (!w || !mu || !var || !sum || !ref || !mask) {
+        free(w); free(mu); free(var); free(sum); free(ref); free(mask);
+        return -1;
+    }
+    /* the warm-up's start: component 0 holds the first frame with all the
+     * weight, the others are empty */
+    for (int64_t p = 0; p < P; p++)
+        for (int k = 0; k < K; k++) {
+            w[p * K + k] = k == 0 ? 1.0 : 0.0;
+            for (int c = 0; c < 3; c++) {
+                mu[(p * K + k) * 3 + c] = k == 0 ? frames[p * 3 + c] : 0.0;
+                var[(p * K + k) * 3 + c] = pr->var_init;
+            }
+        }
+    orc_params pw = *pr;
+    pw.flags = 0u;
+    for (int t = 1; t < N; t++) {
+        orc_plain_gmm(&pw, w, mu, var, frames + (int64_t)t * P * 3, mask);
+        for (int64_t p = 0; p < P; p++) {
+            int best = 0;
+            double kb = -1.0, vb = 0.0;
+            for (int k = 0; k < K; k++) {
+                const double *v = var + (p * K + k) * 3;
+                const double vbar = (v[0] + v[1] + v[2]) / 3.0;
+                const double key = w[p * K + k] * w[p * K + k] / vbar;
+                if (key > kb) { kb = key; best = k; vb = vbar; }
+            }
+            const double om = w[p * K + best];
+            if (t == 1) { ref[p * 2] = vb; ref[p * 2 + 1] = om; }
+            /* sums of the series shifted by its first value (no cancellation) */
+            const double dv = vb - ref[p * 2], dw = om - ref[p * 2 + 1];
+            sum[p * 4 + 0] += dv;
+            sum[p * 4 + 1] += dv * dv;
+            sum[p * 4 + 2] += dw;
+            sum[p * 4 + 3] += dw * dw;
+        }
+    }
+    const double n = (double)(N - 1);
+    for (int64_t p = 0; p < P; p++) {
+        const double *s = sum + p * 4;
+        double vv = s[1] / n - (s[0] / n) * (s[0] / n);
+        double vw = s[3] / n - (s[2] / n) * (s[2] / n);
+        const double sdv = vv > 0.0 ? sqrt(vv) : 0.0, sdw = vw > 0.0 ? sqrt(vw) : 0.0;
+        const double cv = floor(sdv * 64.0 + 0.5), cw = floor(sdw * 65536.0 + 0.5);
+        code_v[p] = (uint16_t)(cv > 65535.0 ? 65535.0 : cv);
+        code_w[p] = (uint16_t)(cw > 65535.0 ? 65535.0 : cw);
+    }
+    free(w); free(mu); free(var); free(sum); free(ref); free(mask);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Spatio-temporal grouping, steps 4-6: K-means with K = 3 over the two */
+/* feature codes, each feature scaled by its standard deviation over   */
+/* all pixels; the cluster core of Eq. 3 (both features strictly within */
+/* the cluster's mean +- its standard deviation); the core's shared     */
+/* dominant mode.  Integer sums are exact, so the double arithmetic     */
+/* below is a fixed sequence of correctly rounded operations.           */
+/* ------------------------------------------------------------------ */
+static int nearest3(double qv, double qw, const double c[3][2], double sdv, double sdw)
+{
+    int best = 0;
+    double db = 0.0;
+    for (int j = 0; j < 3; j++) {
+        const double tv = (qv - c[j][0]) / sdv;
+        const double tw = (qw - c[j][1]) / sdw;
+        const double d = tv * tv + tw * tw;
+        if (j == 0 || d < db) { db = d; best = j; }
+    }
+    return best;
+}
+
+int orc_group_cluster(int64_t P, const uint16_t *code_v, const uint16_t *code_w, int max_iter,
+                      uint8_t *labels, orc_group_out *out)
+{
+    if (P < 1 || !code_v || !code_w || !labels || !out || max_iter < 1) return -1;
+    memset(out, 0, sizeof(*out));
+    /* feature scales over all pixels */
+    int64_t S1[2] = {0, 0}, S2[2] = {0, 0};
+    for (int64_t p = 0; p < P; p++) {
+        S1[0] += code_v[p];
+        S1[1] += code_w[p];
+        S2[0] += (int64_t)code_v[p] * code_v[p];
+        S2[1] += (int64_t)code_w[p] * code_w[p];
+    }
+    /* sd0: the spread of a feature (0 when constant); sd: its distance
+     * scale (1 when constant) */
+    double mean[2], sd0[2], sd[2];
+    for (int f = 0; f < 2; f++) {
+        mean[f] = (double)S1[f] / (double)P;
+        const double v = (double)S2[f] / (double)P - mean[f] * mean[f];
+        sd0[f] = v > 0.0 ? sqrt(v) : 0.0;
+        sd[f] = v > 0.0 ? sd0[f] : 1.0;
+    }
+    /* initial centroids on the diagonal: mean - sd0, mean, mean + sd0 */
+    double c[3][2];
+    for (int j = 0; j < 3; j++)
+        for (int f = 0; f < 2; f++) c[j][f] = mean[f] + (double)(j - 1) * sd0[f];
+    for (int64_t p = 0; p < P; p++) labels[p] = (uint8_t)nearest3((double)code_v[p], (double)code_w[p], c, sd[0], sd[1]);
+    /* Lloyd iterations: centroids <- member means (an empty cluster keeps
+     * its centroid), reassign, until no label changes */
+    out->iterations = max_iter;
+    out->converged = 0;
+    for (int it = 1; it <= max_iter; it++) {
+        int64_t n[3] = {0, 0, 0}, T[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+        for (int64_t p = 0; p < P; p++) {
+            n[labels[p]]++;
+            T[labels[p]][0] += code_v[p];
+            T[labels[p]][1] += code_w[p];
+        }
+        for (int j = 0; j < 3; j++)
+            if (n[j] > 0)
+                for (int f = 0; f < 2; f++) c[j][f] = (double)T[j][f] / (double)n[j];
+        int64_t changed = 0;
+        for (int64_t p = 0; p < P; p++) {
+            const uint8_t l = (uint8_t)nearest3((double)code_v[p], (double)code_w[p], c, sd[0], sd[1]);
+            changed += l != labels[p];
+            labels[p] = l;
+        }
+        if (changed == 0) {
+            out->iterations = it;
+            out->converged = 1;
+            break;
+        }
+    }
+    /* cluster statistics of the final labels and the cores of Eq. 3 */
+    for (int64_t p = 0; p < P; p++) {
+        const int j = labels[p];
+        out->n[j]++;
+        out->s1[j][0] += code_v[p];
+        out->s1[j][1] += code_w[p];
+        out->s2[j][0] += (int64_t)code_v[p] * code_v[p];
+        out->s2[j][1] += (int64_t)code_w[p] * code_w[p];
+    }
+    for (int j = 0; j < 3; j++)
+        for (int f = 0; f < 2; f++) {
+            if (out->n[j] == 0) continue;
+            const double m = (double)out->s1[j][f] / (double)out->n[j];
+            const double v = (double)out->s2[j][f] / (double)out->n[j] - m * m;
+            out->centroid[j][f] = m;
+            out->sd[j][f] = v > 0.0 ? sqrt(v) : 0.0;
+        }
+    for (int64_t p = 0; p < P; p++) {
+        const int j = labels[p];
+        const int core = fabs((double)code_v[p] - out->centroid[j][0]) < out->sd[j][0] &&
+                         fabs((double)code_w[p] - out->centroid[j][1]) < out->sd[j][1];
+        if (core) {
+            labels[p] = (uint8_t)(j | 0x80);
+            out->n_core[j]++;
+        }
+    }
+    return 0;
+}
+
+int orc_group_params(const orc_params *pr, const orc_state *s, const uint8_t *labels, orc_group_out *out)
+{
+    if (check_params(pr) || (pr->flags & ORC_PERCHAN) || !s || !labels || !out) return -1;
+    const int64_t P = (int64_t)pr->width * pr->height;
+    const int K = pr->K;
+    double acc[3][5];
+    int64_t n[3] = {0, 0, 0};
+    memset(acc, 0, sizeof(acc));
+    for (int64_t p = 0; p < P; p++) {
+        if (!(labels[p] & 0x80)) continue;
+        const int j = labels[p] & 3, k = s->top[p];
+        if (j > 2) return -1;
+        const double *v = s->var + (p * K + k) * 3;
+        acc[j][0] += s->w[p * K + k];
+        for (int c = 0; c < 3; c++) acc[j][1 + c] += s->mu[(p * K + k) * 3 + c];
+        acc[j][4] += (v[0] + v[1] + v[2]) / 3.0;
+        n[j]++;
+    }
+    for (int j = 0; j < 3; j++) {
+        if (!n[j]) continue;
+        out->w1[j] = acc[j][0] / (double)n[j];
+        for (int c = 0; c < 3; c++) out->mu1[j][c] = acc[j][1 + c] / (double)n[j];
+        out->v1[j] = acc[j][4] / (double)n[j];
+    }
+    return 0;
+}

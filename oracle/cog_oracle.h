@@ -155,6 +155,46 @@ int orc_plain_gmm(const orc_params *pr, double *w, double *mu, double *var,
 /* Number of OpenMP threads the oracle uses (1 without OpenMP). */
 int orc_threads(void);
 
+/* Spatio-temporal grouping features (Sec. 2, "Clustering Similar
+ * Background"): the mixture warm-up of orc_train replayed over
+ * frames[N][P][3]; after each update at frames 1..N-1 the dominant mode
+ * (largest omega^2 / vbar, lowest index on ties) gives its mean variance
+ * vbar and weight omega.  code_v[p] = round(64 sd(vbar)), code_w[p] =
+ * round(65536 sd(omega)), population standard deviations over the N-1
+ * updates, saturated at 65535.  Not defined with ORC_PERCHAN. */
+int orc_group_features(const orc_params *pr, const uint8_t *frames, int N,
+                       uint16_t *code_v, uint16_t *code_w);
+
+/* Grouping result: K-means labels and the Eq. 3 cores. */
+typedef struct {
+    int32_t iterations;     /* Lloyd steps until no label changed (max_iter if none) */
+    int32_t converged;      /* 1: the labels settled within max_iter                 */
+    int64_t n[3];           /* pixels per cluster                                    */
+    int64_t n_core[3];      /* of them inside the Eq. 3 band on both features       */
+    int64_t s1[3][2];       /* per cluster: sums of code_v, code_w                   */
+    int64_t s2[3][2];       /*              sums of their squares                    */
+    double centroid[3][2];  /* member means of the codes                             */
+    double sd[3][2];        /* member standard deviations of the codes               */
+    double w1[3];           /* orc_group_params: mean over the core of the dominant  */
+    double mu1[3][3];       /* mode's weight, means and mean variance                */
+    double v1[3];
+} orc_group_out;
+
+/* Steps 4-5: K-means, K = 3, over (code_v, code_w) scaled by their
+ * standard deviations over all P pixels (1 for a constant feature), first
+ * centroids at mean - sd, mean, mean + sd (sd = 0 for a constant feature:
+ * the centroids start on its one value), an empty cluster keeping its
+ * centroid, ties to the lower cluster; then each pixel whose two codes lie
+ * strictly within its cluster's mean +- standard deviation (Eq. 3) is a
+ * core pixel.  labels[p] = cluster | 0x80 for a core pixel. */
+int orc_group_cluster(int64_t P, const uint16_t *code_v, const uint16_t *code_w, int max_iter,
+                      uint8_t *labels, orc_group_out *out);
+
+/* Step 6: per cluster, the mean over its core pixels of the trained
+ * state's dominant mode (the one orc_train gave the running average):
+ * weight, per-channel means and mean variance, into out->w1, mu1, v1. */
+int orc_group_params(const orc_params *pr, const orc_state *s, const uint8_t *labels, orc_group_out *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -63,6 +63,20 @@ class _Stats(C.Structure):
                 ("illum_flag", C.c_int32), ("pad", C.c_int32)]
 
 
+class _GroupOut(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("converged", C.c_int32), ("n", C.c_int64 * 3),
+                ("n_core", C.c_int64 * 3), ("s1", (C.c_int64 * 2) * 3), ("s2", (C.c_int64 * 2) * 3),
+                ("centroid", (C.c_double * 2) * 3), ("sd", (C.c_double * 2) * 3),
+                ("w1", C.c_double * 3), ("mu1", (C.c_double * 3) * 3), ("v1", C.c_double * 3)]
+
+
+def _group_dict(g: _GroupOut) -> dict:
+    return dict(iterations=int(g.iterations), converged=int(g.converged), n=list(g.n), n_core=list(g.n_core),
+                s1=[list(r) for r in g.s1], s2=[list(r) for r in g.s2],
+                centroid=[list(r) for r in g.centroid], sd=[list(r) for r in g.sd],
+                w1=list(g.w1), mu1=[list(r) for r in g.mu1], v1=list(g.v1))
+
+
 def _load():
     global _lib
     with _lock:
@@ -82,12 +96,34 @@ def _load():
             lib.orc_plain_gmm.argtypes = [C.POINTER(_Params)] + [C.c_void_p] * 5
             lib.orc_plain_gmm.restype = C.c_int
             lib.orc_threads.restype = C.c_int
+            lib.orc_group_features.argtypes = [C.POINTER(_Params), C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]
+            lib.orc_group_features.restype = C.c_int
+            lib.orc_group_cluster.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
+                                              C.POINTER(_GroupOut)]
+            lib.orc_group_cluster.restype = C.c_int
+            lib.orc_group_params.argtypes = [C.POINTER(_Params), C.POINTER(_State), C.c_void_p,
+                                             C.POINTER(_GroupOut)]
+            lib.orc_group_params.restype = C.c_int
             _lib = lib
     return _lib
 
 
 def oracle_threads() -> int:
     return int(_load().orc_threads())
+
+
+def group_cluster(code_v: np.ndarray, code_w: np.ndarray, max_iter: int = 64):
+    """K-means (K = 3) over the two grouping codes and the Eq. 3 cores;
+    returns (labels: cluster | 0x80 for a core pixel, result dict)."""
+    cv = np.ascontiguousarray(code_v, dtype=np.uint16).ravel()
+    cw = np.ascontiguousarray(code_w, dtype=np.uint16).ravel()
+    assert cv.size == cw.size
+    labels = np.empty(cv.size, np.uint8)
+    g = _GroupOut()
+    if _load().orc_group_cluster(cv.size, cv.ctypes.data, cw.ctypes.data, int(max_iter), labels.ctypes.data,
+                                 C.byref(g)) != 0:
+        raise ValueError("orc_group_cluster rejected its arguments")
+    return labels, _group_dict(g)
 
 
 def default_params(width: int, height: int, K: int = 3) -> dict:
@@ -189,6 +225,29 @@ class Oracle:
             raise ValueError("orc_apply rejected its arguments")
         stats = dict(n_stage=list(st.n_stage), n_gmm=int(st.n_gmm), illum_flag=int(st.illum_flag))
         return mask, stage, near, stats
+
+    def group_features(self, frames: np.ndarray):
+        """Grouping features over training frames [N, P, 3]: (code_v,
+        code_w), the spreads of the dominant mode's mean variance and
+        weight over the warm-up, as uint16 codes."""
+        f = np.ascontiguousarray(frames, dtype=np.uint8).reshape(-1, self.P, 3)
+        cv = np.empty(self.P, np.uint16)
+        cw = np.empty(self.P, np.uint16)
+        if self.lib.orc_group_features(C.byref(self._cp), f.ctypes.data, f.shape[0], cv.ctypes.data,
+                                       cw.ctypes.data) != 0:
+            raise ValueError("orc_group_features rejected its arguments")
+        return cv, cw
+
+    def group_params(self, labels: np.ndarray) -> dict:
+        """Per cluster, the mean over its core pixels (labels & 0x80) of the
+        trained state's dominant mode: w1, mu1 [3][3], v1."""
+        lab = np.ascontiguousarray(labels, dtype=np.uint8).ravel()
+        g = _GroupOut()
+        s = self.state._c()
+        if self.lib.orc_group_params(C.byref(self._cp), C.byref(s), lab.ctypes.data, C.byref(g)) != 0:
+            raise ValueError("orc_group_params rejected its arguments")
+        d = _group_dict(g)
+        return dict(w1=d["w1"], mu1=d["mu1"], v1=d["v1"])
 
     def plain_gmm(self, w: np.ndarray, mu: np.ndarray, var: np.ndarray, frame: np.ndarray):
         for a in (w, mu, var):
