@@ -30,7 +30,9 @@
  *     other modes): stage 1 tests and adapts a copy of the mixture's
  *     rank-1 mode; on the transition to stage 2 the copy is written back
  *     into that mode ("during a transition the parameters are updated",
- *     Sec. 2), Eq. 2 runs, and the copy then follows the new rank-1 mode.
+ *     Sec. 2), Eq. 2 runs, and the copy then follows the new rank-1 mode;
+ *   - spatio-temporal grouping (training side): Sec. 2, "Clustering Similar
+ *     Background - Spatio-Temporal Grouping", its steps 1-6 and Eq. 3.
  * The readings taken where the text is silent or garbled are listed in the
  * repository's design notes and restated beside the code below.
  *
@@ -38,7 +40,9 @@
  * normalisation, the static-pixel variance decay, the step absorption time,
  * the constant-input confidence recursion, the flags-off == plain-GMM
  * identity and the illumination response are pinned by closed forms and
- * invariants in the CPU tests.  The overall behaviour of the full cascade on
+ * invariants in the CPU tests, and so are the grouping features (constant
+ * and two-level pixels worked by hand), the K-means fixed point and the
+ * Eq. 3 cores (brute force).  The overall behaviour of the full cascade on
  * natural video has no printed worked example in the paper: beyond those
  * pins it is "parity unpinned".
  */
