@@ -125,24 +125,24 @@ KERNEL_SOURCES = ("cog_internal.h", "cog_device.cuh", "cog_apply.cuh", "cog_mixt
                   "cog_inst.cuh", "cog_f32.cu", "cog_f16.cu", "cog_bf16.cu", "cog_kde.cu")
 
 
-def source_hash() -> str:
+def source_hash(sources=KERNEL_SOURCES) -> str:
     """Hash of the kernel sources; ncu counts taken on other sources are not used."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1705_09339_gb300", "csrc")
-    for f in KERNEL_SOURCES:
+    for f in sources:
         with open(os.path.join(d, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
 
 
-def ncu_counts(kernel: str):
+def ncu_counts(kernel: str, sources=KERNEL_SOURCES):
     """Per-launch ncu counts of the committed summary (DRAM bytes, warp
     instructions), if they were taken on the current kernel sources."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             d = json.load(f)
         e = d.get(kernel)
-        if e and e.get("source_hash") == source_hash():
+        if e and e.get("source_hash") == source_hash(sources):
             return e
     except Exception:
         pass
@@ -858,6 +858,96 @@ def cpu_baseline(sc, gpu_masks, args):
 
 
 # ---------------------------------------------------------------- reference arm
+# ------------------------------------------------------------- grouping
+GROUP_SOURCES = ("cog_internal.h", "cog_device.cuh", "cog_group.cu")
+
+
+def run_group(args, rank, local_rank, world):
+    """Spatio-temporal grouping (Sec. 2, steps 1-6 and Eq. 3) of the
+    1920x1080 dynamic stream's 500 training frames, K=5, FP16 state: one
+    step is one cog_group call (the warm-up replay that yields the two
+    feature codes, the K-means iterations and the Eq. 3 cores).  The
+    training frames (3.1 GB) exceed L2, so no flush is needed between steps."""
+    import torch
+    import torch.distributed as dist
+    from cogsynth import workload
+    from cogsynth.gpu import GpuScene
+    from paper_1705_09339_gb300 import cog
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    torch.zeros(1, device=dev)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    sc = workload("hd_dynamic", fg_frac=args.fg, seed=stream_seed(3, rank))["scene"]
+    P = sc.P
+    stream = torch.cuda.current_stream(dev)
+    train = GpuScene(sc, dev).render(0, N_TRAIN)
+    p = cog.cog_default_params(W_, H_, K_, state_dtype="f16")
+    ctx = cog.cog_create(p, stream.cuda_stream)
+    cog.cog_train_prior(ctx, train, N_TRAIN)
+    codes = torch.empty((2, P), dtype=torch.int16, device=dev)
+    labels = torch.empty(P, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        st = cog.cog_group(ctx, train, N_TRAIN, codes, labels)
+    clocks = Clocks(local_rank)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = []
+    for _ in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st = cog.cog_group(ctx, train, N_TRAIN, codes, labels)
+        b.record(stream)
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    (ms,) = max_over_ranks([ms], world, dev)
+    result = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            import oracle
+            idx = np.random.default_rng(0).choice(P, 2048, replace=False)
+            sub = train.reshape(N_TRAIN, P, 3)[:, torch.from_numpy(idx).to(dev)].cpu().numpy()
+            o = oracle.Oracle(dict(oracle.default_params(2048, 1, K_), flags=0))
+            t0 = time.perf_counter()
+            cv, cw = o.group_features(sub)
+            oracle.group_cluster(cv, cw)
+            t_cpu = time.perf_counter() - t0
+            cpu = {"value": round(2048 / t_cpu / 1e6, 6), "unit": "Mpixel/s", "cores": oracle.oracle_threads(),
+                   "kind": "oracle", "sample": "2048 random pixels' 500-frame training series: features "
+                                               "(FP64 warm-up replay) and K-means on them"}
+        e = ncu_counts("group_features_kernel", GROUP_SOURCES)
+        roof = {"bound": "alu", "kernel": "group_features_kernel", "unit": "Twarp-inst/s",
+                "peak": round(ISSUE_PEAK / 1e12, 4), "achieved": None, "frac": None, "traffic": None,
+                "note": "the warm-up replay issues instructions (FP32 mixture step per pixel and frame); "
+                        "peak = 152 SMs x 4 schedulers x 1 warp instruction per clock x 2070 MHz; the "
+                        "count is per launch from profiles/traffic.json over the whole cog_group time"}
+        if e and "warp_instructions_per_launch" in e:
+            a = float(e["warp_instructions_per_launch"]) / (ms / args.steps / 1e3)
+            roof.update(achieved=round(a / 1e12, 4), frac=round(a / ISSUE_PEAK, 4),
+                        traffic=e.get("dram_bytes_per_launch"))
+        result = {
+            "metric": "CoG spatio-temporal grouping Mpixel/s (500 training frames per pixel)",
+            "value": round(world * P * args.steps / (ms / 1e3) / 1e6, 2), "unit": "Mpixel/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{W_}x{H_} RGB u8 dynamic-background stream, {N_TRAIN} training frames, "
+                                   f"K={K_}, FP16 state: one cog_group per step",
+                       "l2": "training frames (3.1 GB) exceed L2; no flush"},
+            "groups": {k: st[k] for k in ("iterations", "converged", "n", "n_core", "centroid", "sd")},
+            "roofline": roof, "gpu_launches": 67 * args.steps, "e2e": None, "cpu_baseline": cpu, "clocks": clk,
+        }
+    cog.cog_destroy(ctx)
+    if world > 1:
+        dist.destroy_process_group()
+    return result
+
+
 def run_reference(args, rank, world):
     """The FP64 CPU oracle, as it stands, on the host cores: each step is
     one frame of a 20-row band (38,400 pixels) of the same stream."""
@@ -898,7 +988,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fg", type=float, default=0.02)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="hd", choices=["hd", "clip", "batch64", "serve"])
+    ap.add_argument("--workload", default="hd", choices=["hd", "clip", "batch64", "serve", "group"])
     ap.add_argument("--duration", type=float, default=20.0, help="serve: seconds of camera traffic")
     ap.add_argument("--cameras", type=int, default=256, help="serve: cameras")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
@@ -919,7 +1009,8 @@ def main():
     else:
         import __graft_entry__
         __graft_entry__.build()
-        r = {"batch64": run_batch, "serve": run_serve, "clip": run_clip}.get(args.workload, run_ours)(
+        r = {"batch64": run_batch, "serve": run_serve, "clip": run_clip,
+             "group": run_group}.get(args.workload, run_ours)(
             args, rank, local_rank, world)
     if r is not None and rank == 0:
         print(json.dumps(r), flush=True)

@@ -251,6 +251,48 @@ cog_status cog_server_destroy(cog_server *s);
  * them. */
 cog_status cog_selftest_bounded_wait(int32_t limit_ms, uint32_t *error_word, double *elapsed_ms);
 
+/* Spatio-temporal grouping (Sec. 2, "Clustering Similar Background -
+ * Spatio-Temporal Grouping", steps 1-6 and Eq. 3), a training-side
+ * analysis of which pixels share the mixture's update behaviour:
+ *   1-2  the warm-up of cog_train_prior is replayed over the same training
+ *        frames; after each update at frames 1..N-1 the dominant mode (rank
+ *        1 of omega^2 / vbar, lower index on ties) gives its mean variance
+ *        vbar and weight omega; per pixel the population standard
+ *        deviations of the two series are coded
+ *        code_v = round(64 sd_v), code_w = round(65536 sd_w), <= 65535;
+ *   3-4  K-means with K = 3 over (code_v, code_w), each scaled by its
+ *        standard deviation over all pixels (1 for a constant code), first
+ *        centroids at mean - sd, mean, mean + sd (sd = 0 for a constant
+ *        code), an empty cluster keeping its centroid, ties to the lower
+ *        cluster, until no label changes (at most 64 steps);
+ *   5    Eq. 3: a core pixel has both codes strictly within its cluster's
+ *        mean +- standard deviation;
+ *   6    per cluster, the mean over its core of the trained dominant mode
+ *        (the component cog_train_prior gave the running average).
+ * frames_dev: the n_frames >= 2 training frames given to cog_train_prior
+ * (n_frames x height x width x 3 bytes, device memory).  codes_dev: device
+ * uint16 [2][P] (code_v then code_w), 2-byte aligned; labels_dev: device
+ * uint8 [P], cluster 0..2 | 0x80 for a core pixel.  Both caller-owned.
+ * Call it after cog_train_prior and before cog_apply (step 6 reads the
+ * trained state).  Not defined with COG_PERCHAN (COG_ERR_INVALID_ARG);
+ * P must be below 2^30.  Runs on the context's stream and returns when
+ * stats_host is filled. */
+typedef struct cog_group_stats {
+    int32_t iterations;          /* K-means steps until no label changed (64 if none)  */
+    int32_t converged;           /* 1: the labels settled within 64 steps              */
+    int64_t n[3];                /* pixels per cluster                                 */
+    int64_t n_core[3];           /* of them core pixels (Eq. 3)                        */
+    int64_t code_sum[3][2];      /* per cluster: sums of code_v, code_w                */
+    int64_t code_sq_sum[3][2];   /*              and of their squares                  */
+    double centroid[3][2];       /* member means of the codes                          */
+    double sd[3][2];             /* member standard deviations of the codes            */
+    double w1[3];                /* core means of the dominant mode's weight,          */
+    double mu1[3][3];            /* per-channel means                                  */
+    double v1[3];                /* and mean variance                                  */
+} cog_group_stats;
+cog_status cog_group(cog_ctx *ctx, const uint8_t *frames_dev, int32_t n_frames, uint16_t *codes_dev,
+                     uint8_t *labels_dev, cog_group_stats *stats_host);
+
 /* Measurement aid; the paper has no counterpart.  One pass over the planes
  * that stage 0 touches when every pixel passes it, with no arithmetic, to
  * time the streaming floor of a kernel of that size: for every pixel p

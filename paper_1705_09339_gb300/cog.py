@@ -46,6 +46,18 @@ class cog_stats(C.Structure):
                     frame=int(self.frame))
 
 
+class cog_group_stats(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("converged", C.c_int32), ("n", C.c_int64 * 3),
+                ("n_core", C.c_int64 * 3), ("code_sum", (C.c_int64 * 2) * 3), ("code_sq_sum", (C.c_int64 * 2) * 3),
+                ("centroid", (C.c_double * 2) * 3), ("sd", (C.c_double * 2) * 3), ("w1", C.c_double * 3),
+                ("mu1", (C.c_double * 3) * 3), ("v1", C.c_double * 3)]
+
+    def as_dict(self) -> dict:
+        def conv(x):
+            return [conv(v) for v in x] if isinstance(x, C.Array) else x
+        return {n: conv(getattr(self, n)) for n, _ in self._fields_}
+
+
 class cog_server_stats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("frames", C.c_int64), ("steps", C.c_int64), ("pixels", C.c_int64),
                 ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("max_ms", C.c_double), ("wall_s", C.c_double)]
@@ -82,6 +94,7 @@ def _load() -> C.CDLL:
         "cog_clip_runs": (C.c_int, [vp, P(i32)]),
         "cog_selftest_bounded_wait": (C.c_int, [i32, P(C.c_uint32), P(C.c_double)]),
         "cog_probe_stream": (C.c_int, [vp, vp, vp, vp, vp, vp, C.c_int64, vp]),
+        "cog_group": (C.c_int, [vp, vp, i32, vp, vp, P(cog_group_stats)]),
         "cog_apply_plain_gmm": (C.c_int, [vp, vp, vp]),
         "cog_apply_host": (C.c_int, [vp, vp, vp]),
         "cog_apply_host_noalloc": (C.c_int, [vp, vp, vp]),
@@ -196,6 +209,15 @@ def cog_selftest_bounded_wait(limit_ms: int):
     w, ms = C.c_uint32(0), C.c_double(0.0)
     _check(lib.cog_selftest_bounded_wait(int(limit_ms), C.byref(w), C.byref(ms)))
     return w.value, ms.value
+
+
+def cog_group(ctx, frames, n_frames: int, codes, labels) -> dict:
+    """Spatio-temporal grouping on the training frames (uint8 [N, H, W, 3]
+    on the GPU): fills codes (uint16 [2, P]: code_v, code_w) and labels
+    (uint8 [P]: cluster | 0x80 for a core pixel); returns the statistics."""
+    st = cog_group_stats()
+    _check(lib.cog_group(ctx, _ptr(frames), int(n_frames), _ptr(codes), _ptr(labels), C.byref(st)), ctx)
+    return st.as_dict()
 
 
 def cog_probe_stream(jl_in, conf_in, frame, jl_out, conf_out, mask, stream=None) -> None:

@@ -30,6 +30,11 @@ cudaError_t launch_clip_f32(int, const ClipArgs &, int, cudaStream_t);
 cudaError_t launch_clip_f16(int, const ClipArgs &, int, cudaStream_t);
 cudaError_t launch_clip_bf16(int, const ClipArgs &, int, cudaStream_t);
 cudaError_t run_wait_selftest(uint64_t limit_ns, uint32_t *error_word, float *elapsed_ms);
+cudaError_t launch_group(int dtype, int K, const DevParams &dp, const StatePtrs &s, const uint8_t *frames, int N,
+                         uint16_t *codes, uint8_t *labels, int n_sm, cudaStream_t st);
+size_t group_ctl_offset();
+size_t group_ctl_bytes();
+void group_ctl_decode(const void *raw, cog_group_stats *out);
 cudaError_t launch_probe_stream(const uint32_t *jl_in, const uint16_t *conf_in, const uint8_t *frame,
                                 uint32_t *jl_out, uint16_t *conf_out, uint8_t *mask, int64_t P, cudaStream_t st);
 int k1_batch_blocks_per_sm_f32(const LaunchCfg &);
@@ -515,6 +520,31 @@ cog_status cog_selftest_bounded_wait(int32_t limit_ms, uint32_t *error_word, dou
     cudaError_t e = run_wait_selftest((uint64_t)limit_ms * 1000000ull, error_word, &ms);
     if (e != cudaSuccess) return set_err(nullptr, COG_ERR_CUDA, "bounded-wait self-test: %s", cudaGetErrorString(e));
     *elapsed_ms = ms;
+    return COG_OK;
+}
+
+cog_status cog_group(cog_ctx *c, const uint8_t *frames_dev, int32_t n_frames, uint16_t *codes_dev,
+                     uint8_t *labels_dev, cog_group_stats *stats_host)
+{
+    cog_status s = check_ctx(c);
+    if (s) return s;
+    if (!c->trained) return set_err(c, COG_ERR_STATE, "cog_group before cog_train_prior");
+    if (c->p.flags & COG_PERCHAN)
+        return set_err(c, COG_ERR_INVALID_ARG, "grouping uses the shared-weight mixture; not defined with COG_PERCHAN");
+    if (!frames_dev || !codes_dev || !labels_dev || !stats_host)
+        return set_err(c, COG_ERR_INVALID_ARG, "frames_dev, codes_dev, labels_dev and stats_host are required");
+    if (n_frames < 2) return set_err(c, COG_ERR_INVALID_ARG, "need at least 2 training frames");
+    if (reinterpret_cast<uintptr_t>(codes_dev) & 1u) return set_err(c, COG_ERR_INVALID_ARG, "codes_dev must be 2-byte aligned");
+    if (c->L.P >= (int64_t)1 << 30) return set_err(c, COG_ERR_INVALID_ARG, "grouping needs fewer than 2^30 pixels");
+    cudaError_t e = launch_group(c->p.state_dtype, c->p.K, c->dp, c->sp, frames_dev, n_frames, codes_dev, labels_dev,
+                                 c->n_sm, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "grouping launch");
+    std::vector<unsigned char> raw(group_ctl_bytes());
+    e = cudaMemcpyAsync(raw.data(), reinterpret_cast<const unsigned char *>(c->sp.ctl) + group_ctl_offset(), raw.size(),
+                        cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "grouping result");
+    group_ctl_decode(raw.data(), stats_host);
     return COG_OK;
 }
 

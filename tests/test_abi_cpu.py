@@ -34,6 +34,8 @@ def test_struct_sizes_match_header(cog):
     assert C.sizeof(cog.cog_params) == 4 * 23
     assert C.sizeof(cog.cog_stats) == 8 * 7 + 8
     assert C.sizeof(cog.cog_layout) == 8 * 11
+    # 2 int32, 3 + 3 + 6 + 6 int64, 6 + 6 + 3 + 9 + 3 double
+    assert C.sizeof(cog.cog_group_stats) == 8 + 8 * 18 + 8 * 27
 
 
 def test_default_params_and_layout(cog):
@@ -90,6 +92,12 @@ def test_null_context_calls_fail_cleanly(cog):
     for bad in (0, 2001):
         assert cog.lib.cog_selftest_bounded_wait(bad, C.byref(w), C.byref(ms)) == cog.COG_ERR_INVALID_ARG
     assert cog.lib.cog_selftest_bounded_wait(10, None, None) == cog.COG_ERR_INVALID_ARG
+
+
+def test_group_rejects_bad_arguments(cog):
+    import ctypes as C
+    st = cog.cog_group_stats()
+    assert cog.lib.cog_group(None, None, 10, None, None, C.byref(st)) == cog.COG_ERR_INVALID_ARG
 
 
 def test_probe_stream_rejects_bad_arguments(cog):
