@@ -123,6 +123,14 @@ def plain_bytes(frames: int, P: int, elem: int, K: int) -> int:
 # the ABI, the batch host code, the server and the self-test are left out)
 KERNEL_SOURCES = ("cog_internal.h", "cog_device.cuh", "cog_apply.cuh", "cog_mixture.cuh", "cog_clip.cuh",
                   "cog_inst.cuh", "cog_f32.cu", "cog_f16.cu", "cog_bf16.cu", "cog_kde.cu")
+# the sources each profiled kernel is compiled from: its counts stay valid
+# while these are unchanged
+APPLY_SOURCES = ("cog_internal.h", "cog_device.cuh", "cog_apply.cuh", "cog_inst.cuh", "cog_f32.cu", "cog_f16.cu",
+                 "cog_bf16.cu")
+SOURCES_OF = {"stage01_kernel": APPLY_SOURCES, "stage2_kernel": APPLY_SOURCES,
+              "plain_gmm_kernel": APPLY_SOURCES + ("cog_mixture.cuh",),
+              "clip_kernel": APPLY_SOURCES + ("cog_clip.cuh",),
+              "group_features_kernel": ("cog_internal.h", "cog_device.cuh", "cog_group.cu")}
 
 
 def source_hash(sources=KERNEL_SOURCES) -> str:
@@ -135,9 +143,10 @@ def source_hash(sources=KERNEL_SOURCES) -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_counts(kernel: str, sources=KERNEL_SOURCES):
+def ncu_counts(kernel: str):
     """Per-launch ncu counts of the committed summary (DRAM bytes, warp
-    instructions), if they were taken on the current kernel sources."""
+    instructions), if they were taken on the kernel's current sources."""
+    sources = SOURCES_OF.get(kernel, KERNEL_SOURCES)
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             d = json.load(f)
@@ -859,9 +868,6 @@ def cpu_baseline(sc, gpu_masks, args):
 
 # ---------------------------------------------------------------- reference arm
 # ------------------------------------------------------------- grouping
-GROUP_SOURCES = ("cog_internal.h", "cog_device.cuh", "cog_group.cu")
-
-
 def run_group(args, rank, local_rank, world):
     """Spatio-temporal grouping (Sec. 2, steps 1-6 and Eq. 3) of the
     1920x1080 dynamic stream's 500 training frames, K=5, FP16 state: one
@@ -921,7 +927,7 @@ def run_group(args, rank, local_rank, world):
             cpu = {"value": round(2048 / t_cpu / 1e6, 6), "unit": "Mpixel/s", "cores": oracle.oracle_threads(),
                    "kind": "oracle", "sample": "2048 random pixels' 500-frame training series: features "
                                                "(FP64 warm-up replay) and K-means on them"}
-        e = ncu_counts("group_features_kernel", GROUP_SOURCES)
+        e = ncu_counts("group_features_kernel")
         roof = {"bound": "alu", "kernel": "group_features_kernel", "unit": "Twarp-inst/s",
                 "peak": round(ISSUE_PEAK / 1e12, 4), "achieved": None, "frac": None, "traffic": None,
                 "note": "the warm-up replay issues instructions (FP32 mixture step per pixel and frame); "
