@@ -79,13 +79,24 @@ __global__ void __launch_bounds__(128) group_features_kernel(const DevParams dp,
 #pragma unroll
             for (int c = 0; c < 3; c++) I[c] = (float)f[c];
             mix_step<K>(m, I, dp.alpha, dp);
-            int pos[K];
-            rank_positions<K>(m, pos);
+            // the dominant mode: largest w^2 / vbar in the division-free
+            // form of rank_positions, the lower index on ties
+            int top = 0;
+            float wt = m.w[0] * m.w[0], vt = m.v[0][0] + m.v[0][1] + m.v[0][2];
+#pragma unroll
+            for (int k = 1; k < K; k++) {
+                const float wk = m.w[k] * m.w[k], vk = m.v[k][0] + m.v[k][1] + m.v[k][2];
+                if (wk * vt > wt * vk) {
+                    top = k;
+                    wt = wk;
+                    vt = vk;
+                }
+            }
             float vb = 0.f, om = 0.f;
 #pragma unroll
             for (int k = 0; k < K; k++)
-                if (pos[k] == 0) {
-                    vb = (m.v[k][0] + m.v[k][1] + m.v[k][2]) / 3.f;
+                if (k == top) {
+                    vb = vt / 3.f;
                     om = m.w[k];
                 }
             const float rn = 1.f / (float)t;

@@ -6,81 +6,130 @@
 //   q[v] = (255 k[v] + M/2) div M,  M = max_v k[v],
 // with g[d] = round(2^16 exp(-d^2 / (2 bw^2))) computed on the host.
 //
-// A CTA owns 16 pixels (48 channel histograms): shared-memory histograms
-// filled with shared atomics, the 256-level convolution from shared memory,
-// a warp max per histogram, and the quantised prior written as one
-// contiguous 12 KB block (the prior is stored [P][3][256]).
+// Layout: warp w owns the 32 channel histograms b = 32w .. 32w + 31 (b =
+// 3p + c, the prior's row order), so its lanes read 32 consecutive bytes of
+// every frame.  Each lane counts its own histogram in shared memory (uint16,
+// N < 65536) between KDE_PAD zero guards on each side (rows of KDE_ROW
+// entries put lane l's row in bank l), loads KDE_UNROLL frames before adding
+// them so that many loads are in flight, and keeps the smallest and largest
+// value it saw.  The density is zero more than 3bw levels from every
+// sample, so it is evaluated only on [min - 3bw, max + 3bw]: the warp then
+// takes its histograms one at a time, each lane on a level of the support,
+// so a histogram costs its support / 32 steps whatever its neighbours'
+// supports.  For the default bandwidth (3bw = 12) the 25 taps are unrolled
+// against the guarded row: one shared load and one multiply-add per tap.
 #include "cog_internal.h"
 
 namespace cog {
 
-constexpr int KDE_PX = 16;
-constexpr int KDE_TPB = 256;
-constexpr int KDE_NB = KDE_PX * 3;
-constexpr int KDE_SMEM = 2 * KDE_NB * 256 * 4;   // histograms + densities
+constexpr int KDE_WARPS = 2;
+constexpr int KDE_TPB = KDE_WARPS * 32;
+constexpr int KDE_PAD = 32;                       // zero guards around the 256 bins
+constexpr int KDE_ROW = 256 + 2 * KDE_PAD + 2;    // 161 words: lane l's row starts in bank l
+constexpr int KDE_UNROLL = 32;
+constexpr int KDE_SMEM = KDE_WARPS * 32 * KDE_ROW * 2 + KDE_WARPS * 256;   // rows + staging lines
 
 struct KdeW {
     uint32_t g[100];
     int R;
 };
 
-__global__ void __launch_bounds__(KDE_TPB) kde_kernel(int64_t P, const uint8_t *frames, int N,
-                                                      uint8_t *kde, const KdeW w)
+// k[v] = sum over |d| <= R of h[v + d] g[|d|], h zero outside [vmin, vmax]
+__device__ __forceinline__ uint32_t kde_density(const uint16_t *h, int v, int vmin, int vmax, const KdeW &w)
 {
-    extern __shared__ __align__(16) uint32_t ks[];
-    uint32_t *hist = ks;                    // [48][256]
-    uint32_t *dens = ks + KDE_NB * 256;     // [48][256]
-    __shared__ uint32_t Ms[KDE_NB];
-    const int tid = threadIdx.x;
-    const int64_t p0 = (int64_t)blockIdx.x * KDE_PX;
-    const int npx = (int)min((int64_t)KDE_PX, P - p0);
-    const int nb = npx * 3;
+    uint32_t acc = 0;
+    for (int d = -w.R; d <= w.R; d++) {
+        const int u = v + d;
+        if (u >= vmin && u <= vmax) acc += (uint32_t)h[u] * w.g[d < 0 ? -d : d];
+    }
+    return acc;
+}
 
-    for (int i = tid; i < KDE_NB * 256; i += KDE_TPB) hist[i] = 0;
-    __syncthreads();
-    const uint8_t *base = frames + p0 * 3;
-    const int64_t stride = P * 3;
-    const int total = N * nb;
-    for (int idx = tid; idx < total; idx += KDE_TPB) {
-        const int t = idx / nb;
-        const int b = idx - t * nb;
-        const uint32_t v = base[(int64_t)t * stride + b];
-        atomicAdd(&hist[b * 256 + v], 1u);
-    }
-    __syncthreads();
-    const int R = w.R;
-    for (int o = tid; o < nb * 256; o += KDE_TPB) {
-        const int b = o >> 8, v = o & 255;
-        const uint32_t *h = hist + b * 256;
-        const int lo = max(0, v - R), hi = min(255, v + R);
-        uint32_t acc = 0;
-        for (int u = lo; u <= hi; u++) acc += h[u] * w.g[abs(v - u)];
-        dens[o] = acc;
-    }
-    __syncthreads();
-    const int warp = tid >> 5, lane = tid & 31;
-    for (int b = warp; b < nb; b += KDE_TPB / 32) {
-        uint32_t mx = 0;
-        for (int v = lane; v < 256; v += 32) mx = max(mx, dens[b * 256 + v]);
-        mx = __reduce_max_sync(0xffffffffu, mx);
-        if (lane == 0) Ms[b] = mx;
-    }
-    __syncthreads();
-    uint32_t *out = reinterpret_cast<uint32_t *>(kde + p0 * 768);
-    for (int o4 = tid; o4 < nb * 64; o4 += KDE_TPB) {
-        const int b = o4 >> 6;
-        const uint64_t M = Ms[b];
-        const float rM = 1.0f / (float)M;
-        uint32_t word = 0;
+// The same density with the taps unrolled (R <= KDE_PAD): h points at bin 0
+// of a guarded row, so h[v + d] is zero wherever the histogram is.
+template <int R>
+__device__ __forceinline__ uint32_t kde_density_r(const uint16_t *h, int v, const KdeW &w)
+{
+    uint32_t acc = (uint32_t)h[v] * w.g[0];
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
-            const uint64_t num = 255ull * dens[o4 * 4 + j] + M / 2;
-            uint32_t q = (uint32_t)((float)num * rM);      // estimate, then exact fix-up
-            while (q > 0 && (uint64_t)q * M > num) q--;
-            while ((uint64_t)(q + 1) * M <= num) q++;
-            word |= q << (8 * j);
+    for (int d = 1; d <= R; d++) acc += ((uint32_t)h[v - d] + (uint32_t)h[v + d]) * w.g[d];
+    return acc;
+}
+
+// q = floor((255 k + M/2) / M), exactly: a float estimate, then corrected
+__device__ __forceinline__ uint32_t kde_quant(uint32_t k, uint64_t M, float rM)
+{
+    const uint64_t num = 255ull * k + M / 2;
+    uint32_t q = (uint32_t)((float)num * rM);
+    while (q > 0 && (uint64_t)q * M > num) q--;
+    while ((uint64_t)(q + 1) * M <= num) q++;
+    return q;
+}
+
+// RF: the unrolled tap count R (12), or 0 for any R (bounds-checked taps)
+template <int RF>
+__global__ void __launch_bounds__(KDE_TPB) kde_kernel(int64_t P, const uint8_t *frames, int N, uint8_t *kde,
+                                                      const KdeW w)
+{
+    extern __shared__ __align__(16) uint16_t kh[];   // [KDE_TPB][KDE_ROW]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t b = ((int64_t)blockIdx.x * KDE_WARPS + warp) * 32 + lane;
+    const bool act = b < P * 3;
+    uint16_t *row = kh + threadIdx.x * KDE_ROW;
+    for (int v = 0; v < KDE_ROW; v += 2) *reinterpret_cast<uint32_t *>(row + v) = 0u;
+    uint16_t *h = row + KDE_PAD;
+    int vmin = 255, vmax = 0;
+    const uint8_t *src = frames + b;
+    const int64_t stride = P * 3;
+    for (int t0 = 0; t0 < N; t0 += KDE_UNROLL) {
+        uint32_t x[KDE_UNROLL];
+#pragma unroll
+        for (int i = 0; i < KDE_UNROLL; i++) x[i] = act && t0 + i < N ? (uint32_t)__ldcs(src + (int64_t)(t0 + i) * stride) : 256u;
+#pragma unroll
+        for (int i = 0; i < KDE_UNROLL; i++)
+            if (x[i] < 256u) {
+                h[x[i]]++;
+                vmin = min(vmin, (int)x[i]);
+                vmax = max(vmax, (int)x[i]);
+            }
+    }
+    // the density: the warp takes its 32 histograms one after another, its
+    // lanes on consecutive levels of the support (conflict-free reads of
+    // one row), keeps the values in registers for the peak M, and writes
+    // the 256-byte row through a per-warp staging line
+    uint8_t *stage = reinterpret_cast<uint8_t *>(kh + KDE_TPB * KDE_ROW) + warp * 256;
+    const int lo_l = max(0, vmin - w.R), hi_l = act ? min(255, vmax + w.R) : -1;
+    __syncwarp();
+    for (int l = 0; l < 32; l++) {
+        const int64_t bl = b - lane + l;
+        if (bl >= P * 3) break;   // the same for every lane
+        const int LO = __shfl_sync(0xffffffffu, lo_l, l), HI = __shfl_sync(0xffffffffu, hi_l, l);
+        const int VMIN = __shfl_sync(0xffffffffu, vmin, l), VMAX = __shfl_sync(0xffffffffu, vmax, l);
+        const uint16_t *hl = kh + (warp * 32 + l) * KDE_ROW + KDE_PAD;
+        uint32_t kv[8], m = 0;
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const int v = LO + lane + 32 * i;
+            uint32_t k = 0;
+            if (LO + 32 * i <= HI && v <= HI) {
+                if constexpr (RF > 0) k = kde_density_r<RF>(hl, v, w);
+                else k = kde_density(hl, v, VMIN, VMAX, w);
+            }
+            kv[i] = k;
+            m = max(m, k);
         }
-        out[o4] = word;
+        const uint32_t M = __reduce_max_sync(0xffffffffu, m);
+        const float rM = 1.0f / (float)M;
+        *reinterpret_cast<uint2 *>(stage + 8 * lane) = make_uint2(0u, 0u);
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const int v = LO + lane + 32 * i;
+            if (LO + 32 * i <= HI && v <= HI) stage[v] = (uint8_t)kde_quant(kv[i], M, rM);
+        }
+        __syncwarp();
+        reinterpret_cast<uint2 *>(kde + bl * 256)[lane] = *reinterpret_cast<const uint2 *>(stage + 8 * lane);
+        __syncwarp();   // the staging line is rewritten for the next histogram
     }
 }
 
@@ -91,10 +140,12 @@ cudaError_t launch_kde_train(const DevParams &dp, const StatePtrs &s, const uint
     KdeW w;
     for (int d = 0; d < 100; d++) w.g[d] = d <= R ? g[d] : 0u;
     w.R = R;
-    cudaError_t e = cudaFuncSetAttribute(kde_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, KDE_SMEM);
+    if (n_frames >= 65536) return cudaErrorInvalidValue;   // uint16 counts
+    auto kern = R == 12 ? kde_kernel<12> : kde_kernel<0>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, KDE_SMEM);
     if (e != cudaSuccess) return e;
-    const int64_t grid = (dp.P + KDE_PX - 1) / KDE_PX;
-    kde_kernel<<<(unsigned)grid, KDE_TPB, KDE_SMEM, st>>>(dp.P, frames, n_frames, s.kde, w);
+    const int64_t grid = (dp.P * 3 + KDE_TPB - 1) / KDE_TPB;
+    kern<<<(unsigned)grid, KDE_TPB, KDE_SMEM, st>>>(dp.P, frames, n_frames, s.kde, w);
     return cudaGetLastError();
 }
 
