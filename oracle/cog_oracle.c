@@ -792,17 +792,27 @@ int orc_group_features(const orc_params *pr, const uint8_t *frames, int N,
 /* dominant mode.  Integer sums are exact, so the double arithmetic     */
 /* below is a fixed sequence of correctly rounded operations.           */
 /* ------------------------------------------------------------------ */
-static int nearest3(double qv, double qw, const double c[3][2], double sdv, double sdw)
+/* The assignment decision is taken in FP32 (a single-precision distance is
+ * what the GPU evaluates): centroids and reciprocal scales are rounded to
+ * float once per step, then per pixel t = (q - c) * (1/sd) and d = tv^2 +
+ * tw^2, each operation rounded to float, ties to the lower cluster. */
+static int nearest3(uint16_t qv, uint16_t qw, const float c[3][2], float iv, float iw)
 {
     int best = 0;
-    double db = 0.0;
+    float db = 0.0f;
     for (int j = 0; j < 3; j++) {
-        const double tv = (qv - c[j][0]) / sdv;
-        const double tw = (qw - c[j][1]) / sdw;
-        const double d = tv * tv + tw * tw;
+        const float tv = ((float)qv - c[j][0]) * iv;
+        const float tw = ((float)qw - c[j][1]) * iw;
+        const float d = tv * tv + tw * tw;
         if (j == 0 || d < db) { db = d; best = j; }
     }
     return best;
+}
+
+static void to_float(const double c[3][2], float cf[3][2])
+{
+    for (int j = 0; j < 3; j++)
+        for (int f = 0; f < 2; f++) cf[j][f] = (float)c[j][f];
 }
 
 int orc_group_cluster(int64_t P, const uint16_t *code_v, const uint16_t *code_w, int max_iter,
@@ -829,9 +839,12 @@ int orc_group_cluster(int64_t P, const uint16_t *code_v, const uint16_t *code_w,
     }
     /* initial centroids on the diagonal: mean - sd0, mean, mean + sd0 */
     double c[3][2];
+    float cf[3][2];
+    const float iv = (float)(1.0 / sd[0]), iw = (float)(1.0 / sd[1]);
     for (int j = 0; j < 3; j++)
         for (int f = 0; f < 2; f++) c[j][f] = mean[f] + (double)(j - 1) * sd0[f];
-    for (int64_t p = 0; p < P; p++) labels[p] = (uint8_t)nearest3((double)code_v[p], (double)code_w[p], c, sd[0], sd[1]);
+    to_float(c, cf);
+    for (int64_t p = 0; p < P; p++) labels[p] = (uint8_t)nearest3(code_v[p], code_w[p], cf, iv, iw);
     /* Lloyd iterations: centroids <- member means (an empty cluster keeps
      * its centroid), reassign, until no label changes */
     out->iterations = max_iter;
@@ -847,8 +860,9 @@ int orc_group_cluster(int64_t P, const uint16_t *code_v, const uint16_t *code_w,
             if (n[j] > 0)
                 for (int f = 0; f < 2; f++) c[j][f] = (double)T[j][f] / (double)n[j];
         int64_t changed = 0;
+        to_float(c, cf);
         for (int64_t p = 0; p < P; p++) {
-            const uint8_t l = (uint8_t)nearest3((double)code_v[p], (double)code_w[p], c, sd[0], sd[1]);
+            const uint8_t l = (uint8_t)nearest3(code_v[p], code_w[p], cf, iv, iw);
             changed += l != labels[p];
             labels[p] = l;
         }

@@ -187,7 +187,8 @@ typedef struct {
 /* Steps 4-5: K-means, K = 3, over (code_v, code_w) scaled by their
  * standard deviations over all P pixels (1 for a constant feature), first
  * centroids at mean - sd, mean, mean + sd (sd = 0 for a constant feature:
- * the centroids start on its one value), an empty cluster keeping its
+ * the centroids start on its one value; the distance itself in FP32 from
+ * float centroids and reciprocal scales), an empty cluster keeping its
  * centroid, ties to the lower cluster; then each pixel whose two codes lie
  * strictly within its cluster's mean +- standard deviation (Eq. 3) is a
  * core pixel.  labels[p] = cluster | 0x80 for a core pixel. */

@@ -12,14 +12,14 @@
 //              centroids at mean - sd, mean, mean + sd (sd = 0 for a
 //              constant code), an empty cluster keeping its centroid, ties
 //              to the lower cluster, until no label changes (at most
-//              GROUP_MAX_IT steps);
+//              GROUP_MAX_IT steps); the distance is evaluated in FP32;
 //   Eq. 3      core pixel: both codes strictly within the cluster's mean
 //              +- standard deviation;
 //   step 6     per cluster, the mean over its core of the trained state's
 //              dominant mode (weight, means, mean variance).
 // The clustering works on integer sums (exact with atomics in any order),
-// and every double operation is an explicitly rounded intrinsic, so the
-// labels are the same as any implementation of the same sequence of
+// and every floating-point operation is an explicitly rounded intrinsic, so
+// the labels are the same as any implementation of the same sequence of
 // correctly rounded operations on the same codes.
 #include <cmath>
 
@@ -143,16 +143,18 @@ __device__ __forceinline__ void group_scales(const GroupCtl *G, double P, double
     }
 }
 
-// Nearest of the three centroids in the scaled distance, ties to the lower.
-__device__ __forceinline__ int group_nearest(double qv, double qw, const double (*c)[2], const double sd[2])
+// Nearest of the three centroids in the scaled distance, ties to the lower,
+// decided in FP32: float centroids cf and reciprocal scales iv, iw (each
+// rounded once from double), every operation rounded separately.
+__device__ __forceinline__ int group_nearest(uint32_t qv, uint32_t qw, const float (*cf)[2], float iv, float iw)
 {
     int best = 0;
-    double db = 0.0;
+    float db = 0.f;
 #pragma unroll
     for (int j = 0; j < 3; j++) {
-        const double tv = __ddiv_rn(__dsub_rn(qv, c[j][0]), sd[0]);
-        const double tw = __ddiv_rn(__dsub_rn(qw, c[j][1]), sd[1]);
-        const double d = __dadd_rn(__dmul_rn(tv, tv), __dmul_rn(tw, tw));
+        const float tv = __fmul_rn(__fsub_rn((float)qv, cf[j][0]), iv);
+        const float tw = __fmul_rn(__fsub_rn((float)qw, cf[j][1]), iw);
+        const float d = __fadd_rn(__fmul_rn(tv, tv), __fmul_rn(tw, tw));
         if (j == 0 || d < db) {
             db = d;
             best = j;
@@ -178,7 +180,8 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x)
 __global__ void __launch_bounds__(GROUP_TPB) group_assign_kernel(int64_t P, const uint16_t *code_v, const uint16_t *code_w,
                                                                  uint8_t *labels, GroupCtl *G, int it)
 {
-    __shared__ double c_s[3][2], sd_s[2];
+    __shared__ double c_s[3][2];
+    __shared__ float cf_s[3][2], is_s[2];
     __shared__ int skip_s;
     __shared__ unsigned long long acc_s[16];   // n[3], s1[3][2], s2[3][2], changed
     const int tid = threadIdx.x;
@@ -186,8 +189,8 @@ __global__ void __launch_bounds__(GROUP_TPB) group_assign_kernel(int64_t P, cons
     if (tid == 0) {
         double mean[2], sd0[2], sd[2];
         group_scales(G, (double)P, mean, sd0, sd);
-        sd_s[0] = sd[0];
-        sd_s[1] = sd[1];
+        is_s[0] = __double2float_rn(__ddiv_rn(1.0, sd[0]));
+        is_s[1] = __double2float_rn(__ddiv_rn(1.0, sd[1]));
         int skip = 0;
         if (it == 0) {
             for (int j = 0; j < 3; j++)
@@ -200,6 +203,8 @@ __global__ void __launch_bounds__(GROUP_TPB) group_assign_kernel(int64_t P, cons
                     c_s[j][f] = in.n[j] ? __ddiv_rn(__ull2double_rn(in.s1[j][f]), __ull2double_rn(in.n[j])) : in.c[j][f];
         }
         skip_s = skip;
+        for (int j = 0; j < 3; j++)
+            for (int f = 0; f < 2; f++) cf_s[j][f] = __double2float_rn(c_s[j][f]);
     }
     if (tid < 16) acc_s[tid] = 0;
     __syncthreads();
@@ -221,7 +226,7 @@ __global__ void __launch_bounds__(GROUP_TPB) group_assign_kernel(int64_t P, cons
     unsigned long long ch = 0;
     for (int64_t p = (int64_t)blockIdx.x * GROUP_TPB + tid; p < P; p += (int64_t)gridDim.x * GROUP_TPB) {
         const uint32_t qv = code_v[p], qw = code_w[p];
-        const int l = group_nearest((double)qv, (double)qw, c_s, sd_s);
+        const int l = group_nearest(qv, qw, cf_s, is_s[0], is_s[1]);
         if (it > 0) ch += labels[p] != l;
         labels[p] = (uint8_t)l;
 #pragma unroll

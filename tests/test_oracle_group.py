@@ -112,7 +112,8 @@ def test_separated_blobs_are_recovered():
 def _bruteforce_check(v, w, labels, r):
     """Every pixel sits at the nearest final centroid (scaled distance), the
     centroids are their members' means, the cores follow Eq. 3; pixels
-    within rounding of a tie or a band edge are exempt."""
+    within rounding of a tie (the assignment is decided in FP32) or of a
+    band edge are exempt."""
     x = np.stack([v, w], 1).astype(np.float64)
     sd = x.std(axis=0)
     sd[sd == 0] = 1.0
@@ -121,7 +122,7 @@ def _bruteforce_check(v, w, labels, r):
     d = np.stack([(((x - cent[j]) / sd) ** 2).sum(1) if (cl == j).any() else np.full(len(x), np.inf)
                   for j in range(3)], 1)
     best = d.min(1)
-    clear = np.sort(d, 1)[:, 1] - best > 1e-9 * (1 + best)
+    clear = np.sort(d, 1)[:, 1] - best > 1e-5 * (1 + best)
     assert np.array_equal(d.argmin(1)[clear], cl[clear])
     for j in range(3):
         m = cl == j
