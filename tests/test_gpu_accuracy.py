@@ -4,7 +4,7 @@ For the 160x120 workload (K=3, 200 training + 300 test frames) and the
 640x480 dynamic workload (K=5, 500 training + 1000 test frames, with the +60
 light switch at test frame 600), the CUDA path runs with FP32, FP16 and BF16
 model state; the oracle runs once.  Reported (and written to
-gpurun_out/accuracy_report.json): mask agreement with the oracle, mismatches
+accuracy_report.json in the run's output folder): mask agreement with the oracle, mismatches
 not explained by near-threshold decisions, relative error of the final means
 and variances, and the misclassification rate against the generator's
 ground truth for the cascade (GPU) and the plain mixture (GPU, same frames).
