@@ -28,6 +28,15 @@ int orc_threads(void)
 #endif
 }
 
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 static int near_rel(double x, double thr)
 {
     return fabs(x - thr) <= NEAR_REL * fabs(thr);

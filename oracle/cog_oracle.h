@@ -156,8 +156,10 @@ int orc_apply(const orc_params *pr, orc_state *s, const uint8_t *frame,
 int orc_plain_gmm(const orc_params *pr, double *w, double *mu, double *var,
                   const uint8_t *frame, uint8_t *mask);
 
-/* Number of OpenMP threads the oracle uses (1 without OpenMP). */
+/* Number of OpenMP threads the oracle uses (1 without OpenMP), and a way
+ * to change it (n >= 1) for timing. */
 int orc_threads(void);
+void orc_set_threads(int n);
 
 /* Spatio-temporal grouping features (Sec. 2, "Clustering Similar
  * Background"): the mixture warm-up of orc_train replayed over

@@ -96,6 +96,8 @@ def _load():
             lib.orc_plain_gmm.argtypes = [C.POINTER(_Params)] + [C.c_void_p] * 5
             lib.orc_plain_gmm.restype = C.c_int
             lib.orc_threads.restype = C.c_int
+            lib.orc_set_threads.argtypes = [C.c_int]
+            lib.orc_set_threads.restype = None
             lib.orc_group_features.argtypes = [C.POINTER(_Params), C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]
             lib.orc_group_features.restype = C.c_int
             lib.orc_group_cluster.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
@@ -110,6 +112,11 @@ def _load():
 
 def oracle_threads() -> int:
     return int(_load().orc_threads())
+
+
+def set_threads(n: int) -> None:
+    """Threads for the oracle's parallel loops (timing only)."""
+    _load().orc_set_threads(int(n))
 
 
 def group_cluster(code_v: np.ndarray, code_w: np.ndarray, max_iter: int = 64):
