@@ -10,7 +10,7 @@
 // 3p + c, the prior's row order), so its lanes read 32 consecutive bytes of
 // every frame.  Each lane counts its own histogram in shared memory (uint16,
 // N < 65536) between KDE_PAD zero guards on each side (rows of KDE_ROW
-// entries put lane l's row in bank l), loads KDE_UNROLL frames before adding
+// entries start the 32 lanes' rows in 32 different banks), loads KDE_UNROLL frames before adding
 // them so that many loads are in flight, and keeps the smallest and largest
 // value it saw.  The density is zero more than 3bw levels from every
 // sample, so it is evaluated only on [min - 3bw, max + 3bw]: the warp then
@@ -24,8 +24,8 @@ namespace cog {
 
 constexpr int KDE_WARPS = 2;
 constexpr int KDE_TPB = KDE_WARPS * 32;
-constexpr int KDE_PAD = 32;                       // zero guards around the 256 bins
-constexpr int KDE_ROW = 256 + 2 * KDE_PAD + 2;    // 161 words: lane l's row starts in bank l
+constexpr int KDE_PAD = 12;                       // zero guards around the 256 bins (3bw at bw = 4)
+constexpr int KDE_ROW = 256 + 2 * KDE_PAD + 2;    // 141 words: lane l's row starts in bank 13 l mod 32
 constexpr int KDE_UNROLL = 32;
 constexpr int KDE_SMEM = KDE_WARPS * 32 * KDE_ROW * 2 + KDE_WARPS * 256;   // rows + staging lines
 
@@ -141,6 +141,7 @@ cudaError_t launch_kde_train(const DevParams &dp, const StatePtrs &s, const uint
     for (int d = 0; d < 100; d++) w.g[d] = d <= R ? g[d] : 0u;
     w.R = R;
     if (n_frames >= 65536) return cudaErrorInvalidValue;   // uint16 counts
+    static_assert(KDE_PAD >= 12, "the unrolled taps read 12 levels past the bins");
     auto kern = R == 12 ? kde_kernel<12> : kde_kernel<0>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, KDE_SMEM);
     if (e != cudaSuccess) return e;
