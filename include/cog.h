@@ -218,6 +218,13 @@ cog_status cog_clip_runs(cog_ctx *ctx, int32_t *runs);
  *   slot, the oldest frame; uploads them; runs one batched step over those
  *   streams only; downloads their masks.  Frames submitted meanwhile join
  *   the next step, whose uploads overlap the running one.
+ *   cog_server_add: a further trained context joins the running server as
+ *     stream *stream_out (the next index).  The worker takes it between
+ *     steps: once no step is on the GPU (at most 30 s) it rebuilds the batch
+ *     over all the contexts, so frames of the other streams wait for that
+ *     rebuild.  Allocates the new stream's slots; returns when it has
+ *     joined; COG_ERR_TIMEOUT after 60 s, COG_ERR_STATE if the server is
+ *     stopping.  A failed join leaves the server and its status unchanged.
  *   cog_server_drain: waits up to timeout_ms until every submitted frame is
  *     done; COG_ERR_TIMEOUT otherwise.
  *   cog_server_read_stats: counts and the p50/p99/max latency from submission
@@ -231,6 +238,7 @@ typedef struct {
 } cog_server_stats;
 cog_status cog_server_create(cog_ctx *const *ctxs, int32_t n, cog_server **out);
 cog_status cog_server_submit(cog_server *s, int32_t stream, const uint8_t *frame_host, uint8_t *mask_host);
+cog_status cog_server_add(cog_server *s, cog_ctx *ctx, int32_t *stream_out);
 cog_status cog_server_drain(cog_server *s, int32_t timeout_ms);
 cog_status cog_server_read_stats(cog_server *s, cog_server_stats *out);
 /* Per-frame record in completion order: submission time since creation and
@@ -264,7 +272,9 @@ cog_status cog_selftest_bounded_wait(int32_t limit_ms, uint32_t *error_word, dou
  *        standard deviation over all pixels (1 for a constant code), first
  *        centroids at mean - sd, mean, mean + sd (sd = 0 for a constant
  *        code), an empty cluster keeping its centroid, ties to the lower
- *        cluster, until no label changes (at most 64 steps);
+ *        cluster, until no label changes (at most 64 steps); the distance
+ *        is evaluated in FP32 from centroids and reciprocal scales rounded
+ *        to float once per step;
  *   5    Eq. 3: a core pixel has both codes strictly within its cluster's
  *        mean +- standard deviation;
  *   6    per cluster, the mean over its core of the trained dominant mode

@@ -10,7 +10,9 @@
 // overlap the running step.  A completion thread waits for each step's
 // downloads and records every frame's latency from submission to its mask
 // being in host memory.  Every wait is bounded by a condition-variable
-// timeout or by a CUDA event of work already enqueued.
+// timeout or by a CUDA event of work already enqueued.  A camera can join a
+// running server: between steps, once no step is on the GPU, the worker
+// rebuilds the batch over all the contexts.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -58,6 +60,17 @@ struct Step {
     std::vector<Pick> picks;
 };
 
+// A camera joining a running server: its context and device slots, handed
+// to the worker, which rebuilds the batch between steps.
+struct AddReq {
+    cog_ctx *ctx = nullptr;
+    Stream q;
+    int index = -1;
+    cog_status st = COG_OK;
+    bool done = false;
+    char msg[256] = {0};
+};
+
 }  // namespace
 
 struct cog_server {
@@ -66,7 +79,10 @@ struct cog_server {
     cudaStream_t compute = nullptr, up = nullptr, down = nullptr;
     cudaEvent_t copied = nullptr, applied = nullptr;
     std::vector<Stream> streams;
-    std::mutex mu;                       // streams' queues, counts, statistics
+    std::vector<cog_ctx *> ctxs;         // the batch's contexts, in stream order
+    std::deque<AddReq *> adds;           // cameras waiting to join (owned by their callers)
+    std::condition_variable cv_added;    // add requests handled
+    std::mutex mu;                       // streams' queues, counts, statistics, adds
     std::condition_variable cv_work;     // work arrived or a slot freed
     std::condition_variable cv_idle;     // a step completed
     std::mutex dmu;
@@ -95,10 +111,76 @@ static cog_status server_err(cog_server *s, cog_status st, const char *fmt, ...)
     return st;
 }
 
+static void fail_adds(cog_server *s, cog_status st, const char *why)
+{
+    for (AddReq *a : s->adds) {
+        a->st = st;
+        a->done = true;
+        snprintf(a->msg, sizeof a->msg, "%s", why);
+    }
+    s->adds.clear();
+    s->cv_added.notify_all();
+}
+
+// Joins the waiting cameras (called by the worker with s->mu held): waits,
+// at most 30 s, until no step is on the GPU, rebuilds the batch over the old
+// and the new contexts, and appends the new streams.  On failure the old
+// batch stays and the requests carry the error.
+static void server_join(cog_server *s, std::unique_lock<std::mutex> &lk)
+{
+    const clk::time_point until = clk::now() + std::chrono::seconds(30);
+    auto busy = [&] {
+        for (const Stream &q : s->streams)
+            if (q.inflight) return true;
+        return false;
+    };
+    while (busy() && s->sticky == COG_OK) {
+        if (s->cv_idle.wait_until(lk, until) == std::cv_status::timeout && busy()) {
+            fail_adds(s, COG_ERR_TIMEOUT, "the running steps did not finish within 30 s");
+            return;
+        }
+    }
+    if (s->sticky != COG_OK) {
+        fail_adds(s, s->sticky, "the server failed");
+        return;
+    }
+    std::vector<cog_ctx *> all = s->ctxs;
+    for (AddReq *a : s->adds) all.push_back(a->ctx);
+    cog_batch *nb = nullptr;
+    const cog_status st = cog_batch_create(all.data(), (int32_t)all.size(), s->compute, &nb);
+    if (st != COG_OK) {
+        fail_adds(s, st, cog_batch_last_error_string(nullptr));
+        return;
+    }
+    cog_batch_destroy(s->batch);   // idle: every step that used it has completed
+    s->batch = nb;
+    s->ctxs = all;
+    for (AddReq *a : s->adds) {
+        s->streams.push_back(std::move(a->q));
+        a->q = Stream();
+        a->index = (int)s->streams.size() - 1;
+        a->done = true;
+    }
+    s->adds.clear();
+    s->cv_added.notify_all();
+}
+
+// A failed join is the caller's error, not the server's: the message is
+// recorded without making the server's status sticky.
+static cog_status add_err(cog_server *s, cog_status st, const char *fmt, ...)
+{
+    std::lock_guard<std::mutex> lk(s->mu);
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(s->err, sizeof s->err, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
 static void server_worker(cog_server *s)
 {
     cudaSetDevice(s->device);
-    const int n = (int)s->streams.size();
+    int n = (int)s->streams.size();
     std::vector<const uint8_t *> frames(n, nullptr);
     std::vector<uint8_t *> masks(n, nullptr);
     std::vector<uint8_t> active(n, 0);
@@ -107,6 +189,13 @@ static void server_worker(cog_server *s)
         {
             std::unique_lock<std::mutex> lk(s->mu);
             for (;;) {
+                if (!s->adds.empty() && !s->stop) {
+                    server_join(s, lk);
+                    n = (int)s->streams.size();
+                    frames.resize(n, nullptr);
+                    masks.resize(n, nullptr);
+                    active.resize(n, 0);
+                }
                 for (int i = 0; i < n; i++) {
                     Stream &q = s->streams[i];
                     if (!q.pending.empty() && q.inflight < 2) {
@@ -166,6 +255,10 @@ static void server_worker(cog_server *s)
             std::lock_guard<std::mutex> lk(s->mu);
             s->steps++;
         }
+    }
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        fail_adds(s, s->sticky != COG_OK ? s->sticky : COG_ERR_STATE, "the server is stopping");
     }
     {
         std::lock_guard<std::mutex> lk(s->dmu);
@@ -248,6 +341,7 @@ cog_status cog_server_create(cog_ctx *const *ctxs, int32_t n, cog_server **out)
         server_free(s);
         return st;
     }
+    s->ctxs.assign(ctxs, ctxs + n);
     s->streams.resize((size_t)n);
     for (int i = 0; i < n && e == cudaSuccess; i++) {
         const int64_t P = cog::ctx_pixels(ctxs[i]);
@@ -285,6 +379,55 @@ cog_status cog_server_submit(cog_server *s, int32_t stream, const uint8_t *frame
         s->submitted++;
     }
     s->cv_work.notify_one();
+    return COG_OK;
+}
+
+cog_status cog_server_add(cog_server *s, cog_ctx *ctx, int32_t *stream_out)
+{
+    if (!s || !ctx || !stream_out) return COG_ERR_INVALID_ARG;
+    AddReq req;
+    req.ctx = ctx;
+    req.q.P = cog::ctx_pixels(ctx);
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 2 && e == cudaSuccess; k++) {
+        e = cudaMalloc((void **)&req.q.slot[k], (size_t)req.q.P * 3);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&req.q.mslot[k], (size_t)req.q.P);
+    }
+    auto free_slots = [&] {
+        for (int k = 0; k < 2; k++) {
+            if (req.q.slot[k]) cudaFree(req.q.slot[k]);
+            if (req.q.mslot[k]) cudaFree(req.q.mslot[k]);
+            req.q.slot[k] = req.q.mslot[k] = nullptr;
+        }
+    };
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_slots();
+        return add_err(s, COG_ERR_OOM, "slots of the joining camera: %s", cudaGetErrorString(e));
+    }
+    std::unique_lock<std::mutex> lk(s->mu);
+    if (s->stop || s->sticky != COG_OK) {
+        lk.unlock();
+        free_slots();
+        return add_err(s, COG_ERR_STATE, "the server is stopping or failed");
+    }
+    s->adds.push_back(&req);
+    s->cv_work.notify_all();
+    const clk::time_point until = clk::now() + std::chrono::seconds(60);
+    while (!req.done) {
+        if (s->cv_added.wait_until(lk, until) == std::cv_status::timeout && !req.done) {
+            s->adds.erase(std::remove(s->adds.begin(), s->adds.end(), &req), s->adds.end());
+            lk.unlock();
+            free_slots();
+            return add_err(s, COG_ERR_TIMEOUT, "the worker did not take the camera within 60 s");
+        }
+    }
+    lk.unlock();
+    if (req.st != COG_OK) {
+        free_slots();
+        return add_err(s, req.st, "camera join failed: %s", req.msg);
+    }
+    *stream_out = req.index;
     return COG_OK;
 }
 

@@ -51,10 +51,10 @@ class FrameServer:
     def admit(self, width: int, height: int, K: int, dtype: str, train_frames) -> Camera | None:
         """Admits a camera if its resident model and buffers fit in free
         device memory above the reserve, and trains it on train_frames (a
-        device uint8 tensor [N, H, W, 3]).  Returns None when refused."""
+        device uint8 tensor [N, H, W, 3]).  Returns None when refused.  A
+        camera admitted after start() joins the running server between two
+        of its steps."""
         torch = self.torch
-        if self.srv is not None:
-            raise RuntimeError("cameras are admitted before start()")
         cam = Camera(len(self.cameras), width, height, K, dtype)
         need = cog.cog_state_bytes(cam.params) + 2 * cam.P * 4 + (1 << 20)
         free, _ = torch.cuda.mem_get_info(self.dev)
@@ -67,6 +67,14 @@ class FrameServer:
         cog.cog_sync(cam.ctx)
         if not self.keep_masks:
             cam.mask_ring = [torch.empty((height, width), dtype=torch.uint8).pin_memory() for _ in range(self.RING)]
+        if self.srv is not None:
+            try:
+                idx = cog.cog_server_add(self.srv, cam.ctx)
+            except cog.CogError:
+                cog.cog_destroy(cam.ctx)
+                self.refused.append((width, height, K, dtype, need))
+                return None
+            assert idx == cam.id
         self.cameras.append(cam)
         return cam
 

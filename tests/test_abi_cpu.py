@@ -94,6 +94,12 @@ def test_null_context_calls_fail_cleanly(cog):
     assert cog.lib.cog_selftest_bounded_wait(10, None, None) == cog.COG_ERR_INVALID_ARG
 
 
+def test_server_add_rejects_bad_arguments(cog):
+    import ctypes as C
+    idx = C.c_int32(0)
+    assert cog.lib.cog_server_add(None, None, C.byref(idx)) == cog.COG_ERR_INVALID_ARG
+
+
 def test_group_rejects_bad_arguments(cog):
     import ctypes as C
     st = cog.cog_group_stats()

@@ -73,3 +73,51 @@ def test_admission_by_free_memory(cog):
     assert srv.admit(64, 48, 3, "f16", tr) is None
     assert len(srv.refused) == 1
     srv.close()
+
+
+def test_camera_joins_a_running_server(cog):
+    # two cameras serve; a third is admitted and trained while frames of the
+    # first two are on the GPU, joins between steps, and every camera's
+    # masks still equal what it gives alone
+    import time
+
+    from cogsynth import Scene
+    from cogsynth.gpu import GpuScene
+    from paper_1705_09339_gb300.serve import FrameServer
+    NT, NF = 30, 12
+    cams = [(160, 120, 3, "f16"), (97, 61, 5, "f32"), (200, 150, 5, "bf16")]
+    srv = FrameServer(reserve_bytes=1 << 30, keep_masks=True)
+    data = []
+    for i, (w, h, k, dt) in enumerate(cams):
+        sc = Scene(w, h, 700 + i, kind="dynamic", n_train=NT, fg_frac=0.05, switch_at=4)
+        gs = GpuScene(sc)
+        data.append((gs.render(0, NT), [f.cpu().pin_memory() for f in gs.render(NT, NF)]))
+    handles = [srv.admit(*cams[i], data[i][0]) for i in range(2)]
+    assert all(c is not None for c in handles)
+    srv.start()
+    for j in range(NF // 2):
+        for i in range(2):
+            srv.submit(handles[i], data[i][1][j])
+    late = srv.admit(*cams[2], data[2][0])          # joins while the first frames run
+    assert late is not None and late.id == 2
+    handles.append(late)
+    for j in range(NF):
+        if j >= NF // 2:
+            for i in range(2):
+                srv.submit(handles[i], data[i][1][j])
+        srv.submit(late, data[2][1][j])
+        time.sleep(0.0005)
+    stats = srv.stop()
+    assert stats["frames"] == 3 * NF and stats["cameras"] == 3
+    for i, (w, h, k, dt) in enumerate(cams):
+        got = sorted(srv.results[handles[i].id], key=lambda x: x[0])
+        assert [s for s, _ in got] == list(range(NF))
+        p = cog.cog_default_params(w, h, k, state_dtype=dt)
+        c = cog.cog_create(p, torch.cuda.current_stream().cuda_stream)
+        cog.cog_train_prior(c, data[i][0], NT)
+        m = torch.empty((h, w), dtype=torch.uint8, device="cuda")
+        for j in range(NF):
+            cog.cog_apply(c, data[i][1][j].cuda(), m)
+            assert np.array_equal(m.cpu().numpy(), got[j][1]), (i, j)
+        cog.cog_destroy(c)
+    srv.close()
