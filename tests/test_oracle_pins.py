@@ -329,6 +329,53 @@ def test_hand_gmm_match_behind_too_much_weight_is_foreground():
     assert list(o.state.var[0, 2]) == [48.0] * 3
 
 
+def test_hand_gmm_variance_clamped_at_the_top():
+    # comp0 widened to v = 1000 = var_max: keys .25/1000, .09/4, .04/64 ->
+    # order 1, 2, 0.  I = 179 on every channel: comp1 (50, 4) far; comp2
+    # (200, 64): 21^2 = 441 > 6.25*64 = 400, no match; comp0: 79^2 = 6241 <
+    # 6250 -> match at rank 3, weight before .3 + .2 = .5 <= .7 -> BG.
+    # mu0 = 100 + .25*79 = 119.75; v0 = .75*1000 + .25*59.25^2 = 1627.640625
+    # -> clamped to 1000; w = (.625, .225, .15)
+    o = one_pixel(flags=0, **HAND)
+    _hand_state(o)
+    o.state.var[0, 0] = [1000.0] * 3
+    m, st, _, _ = o.apply(np.array([[179, 179, 179]], np.uint8))
+    assert m[0] == 0 and st[0] == 2
+    assert list(o.state.mu[0, 0]) == [119.75] * 3
+    assert list(o.state.var[0, 0]) == [1000.0] * 3
+    np.testing.assert_allclose(o.state.w[0], [0.625, 0.225, 0.15], rtol=1e-15)
+
+
+def test_hand_equal_keys_rank_the_lower_index_first():
+    # two components with the same weight, mean and variance: equal keys, so
+    # component 0 ranks first and takes the match; component 1 only decays
+    o = one_pixel(K=2, flags=0, **HAND)
+    s = o.state
+    s.w[0] = [0.5, 0.5]
+    s.mu[0] = [[100, 100, 100], [100, 100, 100]]
+    s.var[0] = [[16, 16, 16], [16, 16, 16]]
+    s.conf[0], s.label[0], s.prev[0], s.kde[0] = 0.5, 0, [100, 100, 100], 200
+    m, _, _, _ = o.apply(np.array([[104, 104, 104]], np.uint8))
+    assert m[0] == 0
+    assert list(o.state.mu[0, 0]) == [101.0] * 3 and list(o.state.mu[0, 1]) == [100.0] * 3
+    np.testing.assert_allclose(o.state.w[0], [0.625, 0.375], rtol=1e-15)
+
+
+def test_hand_background_set_boundary_is_inclusive():
+    # T = 0.5 and weights (0.5, 0.5) with component 0 ranked first (smaller
+    # variance): a match at rank 2 has exactly T ranked before it -> BG
+    # (weight before <= T); with T just below 0.5 the same match is FG
+    for T, fg in ((0.5, 0), (0.4999, 255)):
+        o = one_pixel(K=2, flags=0, **dict(HAND, T_bg=T))
+        s = o.state
+        s.w[0] = [0.5, 0.5]
+        s.mu[0] = [[100, 100, 100], [200, 200, 200]]
+        s.var[0] = [[16, 16, 16], [64, 64, 64]]
+        s.conf[0], s.label[0], s.prev[0], s.kde[0] = 0.5, 0, [100, 100, 100], 200
+        m, _, _, _ = o.apply(np.array([[200, 200, 200]], np.uint8))
+        assert m[0] == fg, T
+
+
 def test_hand_rga_stage():
     # running average (100, 16): I = (104,100,98) -> t_r = .16 < 1 -> BG at stage 1,
     # same arithmetic as the matched mode above; the mixture is untouched
