@@ -376,6 +376,27 @@ def test_hand_background_set_boundary_is_inclusive():
         assert m[0] == fg, T
 
 
+def test_hand_illumination_response():
+    # the previous frame sent its one pixel to the mixture stage: 1 * 1000 >
+    # 700 * 1 flags this frame.  I = (0, 255, 0) matches nothing: decay
+    # (.375, .225, .15), comp2 restarts with w_init .05, renormalised to
+    # (15, 9, 2)/26; the foreground decision becomes an illumination change:
+    # comp2 takes w_illum = .75 and the others share .25 in proportion,
+    # 15/24 * .25 = .15625 and 9/24 * .25 = .09375; the label is background
+    o = one_pixel(flags=ORC_ILLUM, **HAND)
+    _hand_state(o)
+    o.state.illum[0] = 1
+    m, st, _, stats = o.apply(np.array([[0, 255, 0]], np.uint8))
+    assert m[0] == 0 and st[0] == 4 and stats["illum_flag"] == 1
+    np.testing.assert_allclose(o.state.w[0], [0.15625, 0.09375, 0.75], rtol=1e-15)
+    assert list(o.state.mu[0, 2]) == [0.0, 255.0, 0.0]
+    # and without the flag the same frame is plain foreground
+    o = one_pixel(flags=ORC_ILLUM, **HAND)
+    _hand_state(o)
+    m, st, _, stats = o.apply(np.array([[0, 255, 0]], np.uint8))
+    assert m[0] == 255 and st[0] == 3 and stats["illum_flag"] == 0
+
+
 def test_hand_rga_stage():
     # running average (100, 16): I = (104,100,98) -> t_r = .16 < 1 -> BG at stage 1,
     # same arithmetic as the matched mode above; the mixture is untouched
