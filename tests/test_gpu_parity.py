@@ -42,6 +42,23 @@ def test_generator_twin_bit_exact(kind):
 
 
 # -------------------------------------------------------------- training
+@pytest.mark.parametrize("bw", [1, 7])
+def test_prior_parity_other_bandwidths(bw):
+    # bandwidths other than 4 take the prior kernel's bounds-checked taps
+    from cogsynth import Scene
+    W, H, N = 37, 29, 23
+    sc = Scene(W, H, 5, kind="dynamic", n_train=N, fg_frac=0.05)
+    fr, _ = sc.frames(0, N)
+    d = params(W, H, 3, kde_bw=bw)
+    g = GpuRun(d)
+    g.train(fr)
+    gs = g.state()
+    g.close()
+    o = oracle_run(d)
+    o.train(fr)
+    assert np.array_equal(gs["kde"], oracle_state(o)["kde"])
+
+
 @pytest.mark.parametrize("W,H,K,N", [(160, 120, 3, 200), (37, 29, 5, 17), (1, 1, 1, 2), (91, 45, 8, 40)])
 def test_training_parity(W, H, K, N):
     from cogsynth import Scene

@@ -43,19 +43,21 @@ def test_kde_weights_semigroup_property():
     assert abs(g[6] * g[8] / 65536 - g[10]) <= 1.0
 
 
+@pytest.mark.parametrize("bw", [4, 1, 7])
 @pytest.mark.parametrize("v", [0, 3, 100, 250, 255])
-def test_kde_of_constant_training_is_the_normalised_kernel(v):
-    # all N training values equal v: k = N g[|u - v|], peak N g[0]
-    o = one_pixel()
+def test_kde_of_constant_training_is_the_normalised_kernel(v, bw):
+    # all N training values equal v: k = N g[|u - v|], peak N g[0]; the
+    # kernel's support is 3bw levels on each side
+    o = one_pixel(kde_bw=bw)
     frames = np.full((6, 1, 3), v, np.uint8)
     o.train(frames)
-    g = kde_weights(4)
+    g = [math.floor(65536.0 * math.exp(-d * d / (2.0 * bw * bw)) + 0.5) for d in range(3 * bw + 1)]
     for c in range(3):
         q = o.state.kde[0, c]
         for u in range(256):
             d = abs(u - v)
-            exp = (255 * int(g[d]) + int(g[0]) // 2) // int(g[0]) if d <= 12 else 0
-            assert q[u] == exp, (u, v)
+            exp = (255 * g[d] + g[0] // 2) // g[0] if d <= 3 * bw else 0
+            assert q[u] == exp, (u, v, bw)
 
 
 def test_kde_bruteforce_direct_sum_over_samples():
