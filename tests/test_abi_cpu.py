@@ -120,3 +120,18 @@ def test_probe_stream_rejects_bad_arguments(cog):
         assert cog.lib.cog_probe_stream(*args, 8, None) == cog.COG_ERR_INVALID_ARG
         args[i] = good[i] + 4
         assert cog.lib.cog_probe_stream(*args, 8, None) == cog.COG_ERR_INVALID_ARG
+
+
+def test_header_compiles_as_c99_and_cpp11(tmp_path):
+    """The C ABI header stands alone for C and C++ callers."""
+    import shutil
+    import subprocess
+    inc = os.path.join(ROOT, "include")
+    for cc, std, ext in (("gcc", "-std=c99", "c"), ("g++", "-std=c++11", "cpp")):
+        if not shutil.which(cc):
+            pytest.skip(f"{cc} not found")
+        src = tmp_path / f"h.{ext}"
+        src.write_text('#include "cog.h"\nint main(void) { cog_group_stats s; (void)s; return 0; }\n')
+        r = subprocess.run([cc, std, "-Wall", "-Wextra", "-Werror", "-I", inc, "-c", str(src), "-o",
+                            str(tmp_path / f"h_{ext}.o")], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
