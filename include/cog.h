@@ -224,7 +224,8 @@ cog_status cog_clip_runs(cog_ctx *ctx, int32_t *runs);
  *     over all the contexts, so frames of the other streams wait for that
  *     rebuild.  Allocates the new stream's slots; returns when it has
  *     joined; COG_ERR_TIMEOUT after 60 s, COG_ERR_STATE if the server is
- *     stopping.  A failed join leaves the server and its status unchanged.
+ *     stopping, COG_ERR_INVALID_ARG for a context the server already has.
+ *     A failed join leaves the server and its status unchanged.
  *   cog_server_drain: waits up to timeout_ms until every submitted frame is
  *     done; COG_ERR_TIMEOUT otherwise.
  *   cog_server_read_stats: counts and the p50/p99/max latency from submission

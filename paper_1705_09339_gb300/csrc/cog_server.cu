@@ -411,6 +411,13 @@ cog_status cog_server_add(cog_server *s, cog_ctx *ctx, int32_t *stream_out)
         free_slots();
         return add_err(s, COG_ERR_STATE, "the server is stopping or failed");
     }
+    bool dup = std::find(s->ctxs.begin(), s->ctxs.end(), ctx) != s->ctxs.end();
+    for (const AddReq *a : s->adds) dup = dup || a->ctx == ctx;
+    if (dup) {
+        lk.unlock();
+        free_slots();
+        return add_err(s, COG_ERR_INVALID_ARG, "the context already belongs to the server");
+    }
     s->adds.push_back(&req);
     s->cv_work.notify_all();
     const clk::time_point until = clk::now() + std::chrono::seconds(60);

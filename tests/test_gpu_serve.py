@@ -101,6 +101,8 @@ def test_camera_joins_a_running_server(cog):
     late = srv.admit(*cams[2], data[2][0])          # joins while the first frames run
     assert late is not None and late.id == 2
     handles.append(late)
+    with pytest.raises(cog.CogError):
+        cog.cog_server_add(srv.srv, late.ctx)       # already a stream of the server
     for j in range(NF):
         if j >= NF // 2:
             for i in range(2):
