@@ -712,3 +712,27 @@ def test_hand_perchan_one_channel_behind_too_much_weight_is_foreground():
     assert list(o.state.mu[0, 0]) == [101, 100, 99.5]
     assert list(o.state.var[0, 0]) == [14.25, 12, 12.5625]
     assert np.array_equal(o.state.rga_m[0], rga0)
+
+
+def test_oracle_results_do_not_depend_on_its_thread_count():
+    # OpenMP only distributes independent pixels (integer reductions): one
+    # thread and several give identical training, masks, stage maps and state
+    from cogsynth import Scene
+    import oracle
+    sc = Scene(48, 32, 11, kind="dynamic", n_train=20, fg_frac=0.1, switch_at=3)
+    fr, _ = sc.frames(0, 30)
+    out = []
+    n0 = oracle.oracle_threads()
+    try:
+        for th in (1, max(2, n0)):
+            oracle.set_threads(th)
+            o = Oracle(default_params(48, 32, 3))
+            o.train(fr[:20])
+            res = [o.apply(fr[t])[:2] for t in range(20, 30)]
+            out.append((res, o.state.w.copy(), o.state.var.copy(), o.state.kde.copy()))
+    finally:
+        oracle.set_threads(n0)
+    (r1, w1, v1, k1), (r2, w2, v2, k2) = out
+    for (m1, s1), (m2, s2) in zip(r1, r2):
+        assert np.array_equal(m1, m2) and np.array_equal(s1, s2)
+    assert np.array_equal(w1, w2) and np.array_equal(v1, v2) and np.array_equal(k1, k2)
