@@ -6,5 +6,6 @@ imports it.  See ``cog_oracle.h`` for what each routine follows in the paper.
 """
 from .oracle import (  # noqa: F401
     ORC_CONF, ORC_FD, ORC_ILLUM, ORC_MODE1, ORC_PERCHAN, ORC_RGA, ORC_SAMPLE, NEAR_BITS, Oracle, OracleState,
-    build_oracle, default_params, group_cluster, kde_weights, oracle_threads, set_threads,
+    build_oracle, default_params, group_assign, group_centroids, group_cluster, group_cores, group_init, kde_weights,
+    oracle_threads, set_threads,
 )

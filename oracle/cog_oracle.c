@@ -798,38 +798,58 @@ int orc_group_features(const orc_params *pr, const uint8_t *frames, int N,
 /* feature codes, each feature scaled by its standard deviation over   */
 /* all pixels; the cluster core of Eq. 3 (both features strictly within */
 /* the cluster's mean +- its standard deviation); the core's shared     */
-/* dominant mode.  Integer sums are exact, so the double arithmetic     */
-/* below is a fixed sequence of correctly rounded operations.           */
+/* dominant mode.  Sums of the integer codes are exact; distances are  */
+/* plain FP64, with a near-tie record for the assignment decision.      */
 /* ------------------------------------------------------------------ */
-/* The assignment decision is taken in FP32 (a single-precision distance is
- * what the GPU evaluates): centroids and reciprocal scales are rounded to
- * float once per step, then per pixel t = (q - c) * (1/sd) and d = tv^2 +
- * tw^2, each operation rounded to float, ties to the lower cluster. */
-static int nearest3(uint16_t qv, uint16_t qw, const float c[3][2], float iv, float iw)
+/* Scaled distance of the codes (qv, qw) to centroid c: both features
+ * divided by their spread over all pixels, squared and summed. */
+static double group_dist(double qv, double qw, const double c[2], const double sd[2])
 {
+    const double tv = (qv - c[0]) / sd[0], tw = (qw - c[1]) / sd[1];
+    return tv * tv + tw * tw;
+}
+
+/* An upper bound on how far a single-precision evaluation of group_dist
+ * can land from the exact distance, when the centroid and the reciprocal
+ * scales are rounded to single precision first and every operation is
+ * rounded (standard model: each rounding a relative error of at most
+ * u = 2^-24).  Per feature the scaled difference t is off by at most
+ * delta = u (|c| + 3 |q - c|) / sd (to first order, 1 % added for the
+ * second); squaring adds 2 |t| delta + delta^2; the two squares and their
+ * sum add 4 u d. */
+static double group_dist_fp32_err(double qv, double qw, const double c[2], const double sd[2])
+{
+    const double u = 1.0 / 16777216.0;
+    const double dv = 1.01 * u * (fabs(c[0]) + 3.0 * fabs(qv - c[0])) / sd[0];
+    const double dw = 1.01 * u * (fabs(c[1]) + 3.0 * fabs(qw - c[1])) / sd[1];
+    const double tv = fabs(qv - c[0]) / sd[0], tw = fabs(qw - c[1]) / sd[1];
+    return 2.0 * tv * dv + dv * dv + 2.0 * tw * dw + dw * dw + 4.0 * u * (tv * tv + tw * tw);
+}
+
+/* Nearest of the three centroids, ties to the lower cluster.  *near is set
+ * when the two smallest distances lie within 1e-5 relative of each other,
+ * or within twice the sum of their single-precision error bounds: a
+ * single-precision implementation may legitimately pick either there. */
+static int nearest3(uint16_t qv, uint16_t qw, const double c[3][2], const double sd[2], int *near)
+{
+    double d[3];
     int best = 0;
-    float db = 0.0f;
     for (int j = 0; j < 3; j++) {
-        const float tv = ((float)qv - c[j][0]) * iv;
-        const float tw = ((float)qw - c[j][1]) * iw;
-        const float d = tv * tv + tw * tw;
-        if (j == 0 || d < db) { db = d; best = j; }
+        d[j] = group_dist(qv, qw, c[j], sd);
+        if (d[j] < d[best]) best = j;
     }
+    int second = best == 0 ? 1 : 0;
+    for (int j = 0; j < 3; j++)
+        if (j != best && d[j] < d[second]) second = j;
+    const double gap = d[second] - d[best];
+    const double err = group_dist_fp32_err(qv, qw, c[best], sd) + group_dist_fp32_err(qv, qw, c[second], sd);
+    *near = gap <= 1e-5 * (1.0 + d[best]) || gap <= 2.0 * err;
     return best;
 }
 
-static void to_float(const double c[3][2], float cf[3][2])
+int orc_group_init(int64_t P, const uint16_t *code_v, const uint16_t *code_w, double c[3][2], double sd[2])
 {
-    for (int j = 0; j < 3; j++)
-        for (int f = 0; f < 2; f++) cf[j][f] = (float)c[j][f];
-}
-
-int orc_group_cluster(int64_t P, const uint16_t *code_v, const uint16_t *code_w, int max_iter,
-                      uint8_t *labels, orc_group_out *out)
-{
-    if (P < 1 || !code_v || !code_w || !labels || !out || max_iter < 1) return -1;
-    memset(out, 0, sizeof(*out));
-    /* feature scales over all pixels */
+    if (P < 1 || !code_v || !code_w || !c || !sd) return -1;
     int64_t S1[2] = {0, 0}, S2[2] = {0, 0};
     for (int64_t p = 0; p < P; p++) {
         S1[0] += code_v[p];
@@ -838,42 +858,71 @@ int orc_group_cluster(int64_t P, const uint16_t *code_v, const uint16_t *code_w,
         S2[1] += (int64_t)code_w[p] * code_w[p];
     }
     /* sd0: the spread of a feature (0 when constant); sd: its distance
-     * scale (1 when constant) */
-    double mean[2], sd0[2], sd[2];
+     * scale (1 when constant); first centroids on the diagonal at
+     * mean - sd0, mean, mean + sd0 */
     for (int f = 0; f < 2; f++) {
-        mean[f] = (double)S1[f] / (double)P;
-        const double v = (double)S2[f] / (double)P - mean[f] * mean[f];
-        sd0[f] = v > 0.0 ? sqrt(v) : 0.0;
-        sd[f] = v > 0.0 ? sd0[f] : 1.0;
+        const double mean = (double)S1[f] / (double)P;
+        const double v = (double)S2[f] / (double)P - mean * mean;
+        const double sd0 = v > 0.0 ? sqrt(v) : 0.0;
+        sd[f] = v > 0.0 ? sd0 : 1.0;
+        for (int j = 0; j < 3; j++) c[j][f] = mean + (double)(j - 1) * sd0;
     }
-    /* initial centroids on the diagonal: mean - sd0, mean, mean + sd0 */
-    double c[3][2];
-    float cf[3][2];
-    const float iv = (float)(1.0 / sd[0]), iw = (float)(1.0 / sd[1]);
+    return 0;
+}
+
+int orc_group_centroids(int64_t P, const uint16_t *code_v, const uint16_t *code_w, const uint8_t *labels,
+                        double c[3][2])
+{
+    if (P < 1 || !code_v || !code_w || !labels || !c) return -1;
+    int64_t n[3] = {0, 0, 0}, T[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    for (int64_t p = 0; p < P; p++) {
+        const int j = labels[p] & 0x7f;
+        if (j > 2) return -1;
+        n[j]++;
+        T[j][0] += code_v[p];
+        T[j][1] += code_w[p];
+    }
     for (int j = 0; j < 3; j++)
-        for (int f = 0; f < 2; f++) c[j][f] = mean[f] + (double)(j - 1) * sd0[f];
-    to_float(c, cf);
-    for (int64_t p = 0; p < P; p++) labels[p] = (uint8_t)nearest3(code_v[p], code_w[p], cf, iv, iw);
+        if (n[j] > 0)
+            for (int f = 0; f < 2; f++) c[j][f] = (double)T[j][f] / (double)n[j];
+    return 0;
+}
+
+int64_t orc_group_assign(int64_t P, const uint16_t *code_v, const uint16_t *code_w, const double c[3][2],
+                         const double sd[2], uint8_t *labels, uint8_t *near)
+{
+    if (P < 1 || !code_v || !code_w || !c || !sd || !labels || !(sd[0] > 0.0) || !(sd[1] > 0.0)) return -1;
+    int64_t n_near = 0;
+    for (int64_t p = 0; p < P; p++) {
+        int nr = 0;
+        labels[p] = (uint8_t)nearest3(code_v[p], code_w[p], c, sd, &nr);
+        if (near) near[p] = (uint8_t)nr;
+        n_near += nr;
+    }
+    return n_near;
+}
+
+int orc_group_cluster(int64_t P, const uint16_t *code_v, const uint16_t *code_w, int max_iter,
+                      uint8_t *labels, orc_group_out *out)
+{
+    if (P < 1 || !code_v || !code_w || !labels || !out || max_iter < 0) return -1;
+    memset(out, 0, sizeof(*out));
+    double c[3][2], sd[2];
+    orc_group_init(P, code_v, code_w, c, sd);
+    uint8_t *next = (uint8_t *)malloc((size_t)P);
+    if (!next) return -1;
+    out->n_near = orc_group_assign(P, code_v, code_w, c, sd, labels, NULL);
     /* Lloyd iterations: centroids <- member means (an empty cluster keeps
      * its centroid), reassign, until no label changes */
     out->iterations = max_iter;
     out->converged = 0;
     for (int it = 1; it <= max_iter; it++) {
-        int64_t n[3] = {0, 0, 0}, T[3][2] = {{0, 0}, {0, 0}, {0, 0}};
-        for (int64_t p = 0; p < P; p++) {
-            n[labels[p]]++;
-            T[labels[p]][0] += code_v[p];
-            T[labels[p]][1] += code_w[p];
-        }
-        for (int j = 0; j < 3; j++)
-            if (n[j] > 0)
-                for (int f = 0; f < 2; f++) c[j][f] = (double)T[j][f] / (double)n[j];
+        orc_group_centroids(P, code_v, code_w, labels, c);
+        out->n_near += orc_group_assign(P, code_v, code_w, c, sd, next, NULL);
         int64_t changed = 0;
-        to_float(c, cf);
         for (int64_t p = 0; p < P; p++) {
-            const uint8_t l = (uint8_t)nearest3(code_v[p], code_w[p], cf, iv, iw);
-            changed += l != labels[p];
-            labels[p] = l;
+            changed += next[p] != labels[p];
+            labels[p] = next[p];
         }
         if (changed == 0) {
             out->iterations = it;
@@ -881,9 +930,25 @@ int orc_group_cluster(int64_t P, const uint16_t *code_v, const uint16_t *code_w,
             break;
         }
     }
-    /* cluster statistics of the final labels and the cores of Eq. 3 */
+    free(next);
+    return orc_group_cores(P, code_v, code_w, labels, out);
+}
+
+int orc_group_cores(int64_t P, const uint16_t *code_v, const uint16_t *code_w, uint8_t *labels, orc_group_out *out)
+{
+    if (P < 1 || !code_v || !code_w || !labels || !out) return -1;
+    for (int j = 0; j < 3; j++) {
+        out->n[j] = out->n_core[j] = 0;
+        for (int f = 0; f < 2; f++) {
+            out->s1[j][f] = out->s2[j][f] = 0;
+            out->centroid[j][f] = out->sd[j][f] = 0.0;
+        }
+    }
+    /* cluster statistics of the labels and the cores of Eq. 3 */
     for (int64_t p = 0; p < P; p++) {
+        labels[p] &= 0x7f;
         const int j = labels[p];
+        if (j > 2) return -1;
         out->n[j]++;
         out->s1[j][0] += code_v[p];
         out->s1[j][1] += code_w[p];

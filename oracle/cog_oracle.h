@@ -184,18 +184,46 @@ typedef struct {
     double w1[3];           /* orc_group_params: mean over the core of the dominant  */
     double mu1[3][3];       /* mode's weight, means and mean variance                */
     double v1[3];
+    int64_t n_near;         /* assignments, over all steps, that were near a tie     */
 } orc_group_out;
 
 /* Steps 4-5: K-means, K = 3, over (code_v, code_w) scaled by their
  * standard deviations over all P pixels (1 for a constant feature), first
  * centroids at mean - sd, mean, mean + sd (sd = 0 for a constant feature:
- * the centroids start on its one value; the distance itself in FP32 from
- * float centroids and reciprocal scales), an empty cluster keeping its
- * centroid, ties to the lower cluster; then each pixel whose two codes lie
- * strictly within its cluster's mean +- standard deviation (Eq. 3) is a
- * core pixel.  labels[p] = cluster | 0x80 for a core pixel. */
+ * the centroids start on its one value), an empty cluster keeping its
+ * centroid, ties to the lower cluster, the distance in FP64; at most
+ * max_iter Lloyd steps after the first assignment (max_iter >= 0).  Then
+ * each pixel whose two codes lie strictly within its cluster's mean +-
+ * standard deviation (Eq. 3) is a core pixel.  labels[p] = cluster | 0x80
+ * for a core pixel.  The run is composed of the three steps below. */
 int orc_group_cluster(int64_t P, const uint16_t *code_v, const uint16_t *code_w, int max_iter,
                       uint8_t *labels, orc_group_out *out);
+
+/* The feature scales sd[2] (spread over all pixels, 1 for a constant
+ * feature) and the first centroids c[3][2]. */
+int orc_group_init(int64_t P, const uint16_t *code_v, const uint16_t *code_w, double c[3][2], double sd[2]);
+
+/* One Lloyd update: c[j] <- the mean codes of the pixels labelled j
+ * (labels & 0x7f); a cluster with no pixel keeps c[j]. */
+int orc_group_centroids(int64_t P, const uint16_t *code_v, const uint16_t *code_w, const uint8_t *labels,
+                        double c[3][2]);
+
+/* One assignment: labels[p] = the nearest centroid in the scaled FP64
+ * distance, ties to the lower cluster.  near (nullable) gets 1 where the
+ * two nearest distances are within 1e-5 relative of each other or within
+ * twice the bound on a single-precision evaluation's error of them (the
+ * centroid and scales rounded to single precision, every operation
+ * rounded): there the decision may go either way in an implementation that
+ * computes the distance in single precision.  Returns the number of near
+ * pixels, or -1 for bad arguments. */
+int64_t orc_group_assign(int64_t P, const uint16_t *code_v, const uint16_t *code_w, const double c[3][2],
+                         const double sd[2], uint8_t *labels, uint8_t *near);
+
+/* Step 5 on given labels (the core bit of labels is ignored and
+ * rewritten): per cluster the count, the sums of the codes and of their
+ * squares, the member means and standard deviations, and the Eq. 3 core
+ * (labels[p] |= 0x80, n_core). */
+int orc_group_cores(int64_t P, const uint16_t *code_v, const uint16_t *code_w, uint8_t *labels, orc_group_out *out);
 
 /* Step 6: per cluster, the mean over its core pixels of the trained
  * state's dominant mode (the one orc_train gave the running average):

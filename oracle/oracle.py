@@ -67,14 +67,15 @@ class _GroupOut(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("converged", C.c_int32), ("n", C.c_int64 * 3),
                 ("n_core", C.c_int64 * 3), ("s1", (C.c_int64 * 2) * 3), ("s2", (C.c_int64 * 2) * 3),
                 ("centroid", (C.c_double * 2) * 3), ("sd", (C.c_double * 2) * 3),
-                ("w1", C.c_double * 3), ("mu1", (C.c_double * 3) * 3), ("v1", C.c_double * 3)]
+                ("w1", C.c_double * 3), ("mu1", (C.c_double * 3) * 3), ("v1", C.c_double * 3),
+                ("n_near", C.c_int64)]
 
 
 def _group_dict(g: _GroupOut) -> dict:
     return dict(iterations=int(g.iterations), converged=int(g.converged), n=list(g.n), n_core=list(g.n_core),
                 s1=[list(r) for r in g.s1], s2=[list(r) for r in g.s2],
                 centroid=[list(r) for r in g.centroid], sd=[list(r) for r in g.sd],
-                w1=list(g.w1), mu1=[list(r) for r in g.mu1], v1=list(g.v1))
+                w1=list(g.w1), mu1=[list(r) for r in g.mu1], v1=list(g.v1), n_near=int(g.n_near))
 
 
 def _load():
@@ -103,6 +104,15 @@ def _load():
             lib.orc_group_cluster.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
                                               C.POINTER(_GroupOut)]
             lib.orc_group_cluster.restype = C.c_int
+            lib.orc_group_init.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+            lib.orc_group_init.restype = C.c_int
+            lib.orc_group_centroids.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+            lib.orc_group_centroids.restype = C.c_int
+            lib.orc_group_assign.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                             C.c_void_p, C.c_void_p]
+            lib.orc_group_assign.restype = C.c_int64
+            lib.orc_group_cores.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(_GroupOut)]
+            lib.orc_group_cores.restype = C.c_int
             lib.orc_group_params.argtypes = [C.POINTER(_Params), C.POINTER(_State), C.c_void_p,
                                              C.POINTER(_GroupOut)]
             lib.orc_group_params.restype = C.c_int
@@ -131,6 +141,60 @@ def group_cluster(code_v: np.ndarray, code_w: np.ndarray, max_iter: int = 64):
                                  C.byref(g)) != 0:
         raise ValueError("orc_group_cluster rejected its arguments")
     return labels, _group_dict(g)
+
+
+def _codes(code_v, code_w):
+    cv = np.ascontiguousarray(code_v, dtype=np.uint16).ravel()
+    cw = np.ascontiguousarray(code_w, dtype=np.uint16).ravel()
+    assert cv.size == cw.size and cv.size > 0
+    return cv, cw
+
+
+def group_init(code_v: np.ndarray, code_w: np.ndarray):
+    """Feature scales and first centroids of the K-means: (c[3][2], sd[2])."""
+    cv, cw = _codes(code_v, code_w)
+    c = np.zeros((3, 2), np.float64)
+    sd = np.zeros(2, np.float64)
+    if _load().orc_group_init(cv.size, cv.ctypes.data, cw.ctypes.data, c.ctypes.data, sd.ctypes.data) != 0:
+        raise ValueError("orc_group_init rejected its arguments")
+    return c, sd
+
+
+def group_centroids(code_v: np.ndarray, code_w: np.ndarray, labels: np.ndarray, c_prev: np.ndarray) -> np.ndarray:
+    """One Lloyd update from the given labels (a cluster with no pixel keeps
+    its centroid from c_prev)."""
+    cv, cw = _codes(code_v, code_w)
+    lab = np.ascontiguousarray(labels, dtype=np.uint8).ravel()
+    assert lab.size == cv.size
+    c = np.array(c_prev, dtype=np.float64).reshape(3, 2).copy()
+    if _load().orc_group_centroids(cv.size, cv.ctypes.data, cw.ctypes.data, lab.ctypes.data, c.ctypes.data) != 0:
+        raise ValueError("orc_group_centroids rejected its arguments")
+    return c
+
+
+def group_assign(code_v: np.ndarray, code_w: np.ndarray, c: np.ndarray, sd: np.ndarray):
+    """One FP64 assignment to the centroids c; returns (labels, near)."""
+    cv, cw = _codes(code_v, code_w)
+    cc = np.ascontiguousarray(c, dtype=np.float64).reshape(3, 2)
+    ss = np.ascontiguousarray(sd, dtype=np.float64).ravel()
+    labels = np.empty(cv.size, np.uint8)
+    near = np.empty(cv.size, np.uint8)
+    if _load().orc_group_assign(cv.size, cv.ctypes.data, cw.ctypes.data, cc.ctypes.data, ss.ctypes.data,
+                                labels.ctypes.data, near.ctypes.data) < 0:
+        raise ValueError("orc_group_assign rejected its arguments")
+    return labels, near.astype(bool)
+
+
+def group_cores(code_v: np.ndarray, code_w: np.ndarray, labels: np.ndarray):
+    """Cluster statistics and Eq. 3 cores of the given labels (core bits
+    ignored); returns (labels with core bits, result dict)."""
+    cv, cw = _codes(code_v, code_w)
+    lab = np.array(labels, dtype=np.uint8).ravel()
+    assert lab.size == cv.size
+    g = _GroupOut()
+    if _load().orc_group_cores(cv.size, cv.ctypes.data, cw.ctypes.data, lab.ctypes.data, C.byref(g)) != 0:
+        raise ValueError("orc_group_cores rejected its arguments")
+    return lab, _group_dict(g)
 
 
 def default_params(width: int, height: int, K: int = 3) -> dict:

@@ -17,7 +17,7 @@ import math
 import numpy as np
 import pytest
 
-from oracle import Oracle, default_params, group_cluster
+from oracle import Oracle, default_params, group_assign, group_centroids, group_cluster, group_init
 
 
 def _const_frames(values, N):
@@ -112,8 +112,7 @@ def test_separated_blobs_are_recovered():
 def _bruteforce_check(v, w, labels, r):
     """Every pixel sits at the nearest final centroid (scaled distance), the
     centroids are their members' means, the cores follow Eq. 3; pixels
-    within rounding of a tie (the assignment is decided in FP32) or of a
-    band edge are exempt."""
+    within FP64 rounding of a tie or of a band edge are exempt."""
     x = np.stack([v, w], 1).astype(np.float64)
     sd = x.std(axis=0)
     sd[sd == 0] = 1.0
@@ -122,7 +121,7 @@ def _bruteforce_check(v, w, labels, r):
     d = np.stack([(((x - cent[j]) / sd) ** 2).sum(1) if (cl == j).any() else np.full(len(x), np.inf)
                   for j in range(3)], 1)
     best = d.min(1)
-    clear = np.sort(d, 1)[:, 1] - best > 1e-5 * (1 + best)
+    clear = np.sort(d, 1)[:, 1] - best > 1e-9 * (1 + best)
     assert np.array_equal(d.argmin(1)[clear], cl[clear])
     for j in range(3):
         m = cl == j
@@ -147,6 +146,120 @@ def test_kmeans_fixed_point_and_cores_bruteforce(seed):
     labels, r = group_cluster(v, w)
     assert r["converged"] == 1
     _bruteforce_check(v, w, labels, r)
+
+
+def test_separated_blobs_have_no_near_assignment():
+    rng = np.random.default_rng(3)
+    v, w, _ = _blobs(rng, [(200, 300), (6000, 9000), (30000, 40000)], 50, 20)
+    _, r = group_cluster(v, w)
+    assert r["n_near"] == 0
+
+
+def test_init_closed_form():
+    # codes v = 0, 2 (mean 1, population sd 1), w constant 5 (scale 1,
+    # spread 0): centroids (0, 5), (1, 5), (2, 5)
+    c, sd = group_init(np.array([0, 2], np.uint16), np.array([5, 5], np.uint16))
+    assert sd.tolist() == [1.0, 1.0]
+    assert c.tolist() == [[0.0, 5.0], [1.0, 5.0], [2.0, 5.0]]
+
+
+def test_centroids_are_member_means_and_empty_keeps():
+    v = np.array([1, 3, 10, 20, 30], np.uint16)
+    w = np.array([4, 8, 0, 0, 3], np.uint16)
+    lab = np.array([0, 0, 2, 2, 0x82], np.uint8)     # a core bit does not change the cluster
+    c = group_centroids(v, w, lab, np.array([[7.0, 7.0], [-3.5, 11.25], [0.0, 0.0]]))
+    assert c.tolist() == [[2.0, 6.0], [-3.5, 11.25], [20.0, 1.0]]
+
+
+def test_assign_hand_worked_tie_and_margin():
+    # centroids (100, 100), (200, 100), (1000, 1000), unit scales: the
+    # pixel (150, 100) is 2500 from both of the first two (a tie: cluster
+    # 0, near); (149, 100) is 2401 against 2601 (clear, cluster 0);
+    # (151, 100) the mirror (clear, cluster 1); (999, 1000) clear, cluster 2
+    c = np.array([[100.0, 100.0], [200.0, 100.0], [1000.0, 1000.0]])
+    v = np.array([150, 149, 151, 999], np.uint16)
+    w = np.array([100, 100, 100, 1000], np.uint16)
+    lab, near = group_assign(v, w, c, np.array([1.0, 1.0]))
+    assert lab.tolist() == [0, 0, 1, 2]
+    assert near.tolist() == [True, False, False, False]
+
+
+def test_assign_scales_each_feature():
+    # with scales (100, 1) the w difference dominates: (500, 10) is
+    # (0.01^2 + 0) from (499, 10) and (0 + 3^2) from (500, 13)
+    c = np.array([[499.0, 10.0], [500.0, 13.0], [0.0, 0.0]])
+    lab, near = group_assign(np.array([500], np.uint16), np.array([10], np.uint16), c, np.array([100.0, 1.0]))
+    assert lab.tolist() == [0] and not near[0]
+    # with scales (1, 100): 1^2 from the first, 0.03^2 from the second
+    lab, _ = group_assign(np.array([500], np.uint16), np.array([10], np.uint16), c, np.array([1.0, 100.0]))
+    assert lab.tolist() == [1]
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_assign_bruteforce_and_single_precision_flips_are_near(seed):
+    # FP64 labels equal a brute-force argmin away from ties; every pixel
+    # whose decision a single-precision evaluation (centroid and reciprocal
+    # scales rounded to float32 once, each operation rounded, ties to the
+    # lower cluster) takes differently is in the near record.  Large codes
+    # with small scales stress the rounding of the centroids.
+    rng = np.random.default_rng(seed)
+    P = 200000
+    if seed % 2:
+        v = rng.integers(60000, 65536, P).astype(np.uint16)
+        w = rng.integers(0, 300, P).astype(np.uint16)
+        sd = np.array([rng.uniform(3, 20), rng.uniform(50, 90)])
+        c = np.stack([rng.uniform(60000, 65535, 3), rng.uniform(0, 300, 3)], 1)
+    else:
+        v = np.minimum(rng.gamma(2.0, 800.0, P), 65535).astype(np.uint16)
+        w = np.minimum(rng.gamma(1.5, 3000.0, P), 65535).astype(np.uint16)
+        sd = np.array([v.astype(float).std(), w.astype(float).std()])
+        c = np.stack([rng.uniform(0, 4000, 3), rng.uniform(0, 9000, 3)], 1)
+    lab, near = group_assign(v, w, c, sd)
+    x = np.stack([v, w], 1).astype(np.float64)
+    d = np.stack([(((x - c[j]) / sd) ** 2).sum(1) for j in range(3)], 1)
+    ds = np.sort(d, 1)
+    tie = ds[:, 1] - ds[:, 0] <= 1e-9 * (1 + ds[:, 0])
+    assert np.array_equal(lab[~tie], d.argmin(1)[~tie])
+    assert near[tie].all()
+    flips = _fp32_labels(v, w, c, sd) != lab
+    assert near[flips].all(), np.flatnonzero(flips & ~near)[:5]
+    assert near.mean() < 0.01
+
+
+def _fp32_labels(v, w, c, sd):
+    """The assignment evaluated in single precision: centroids and
+    reciprocal scales rounded to float32 once, each operation rounded, the
+    first minimum taken (ties to the lower cluster)."""
+    cf = c.astype(np.float32)
+    isd = (1.0 / sd).astype(np.float32)
+    d32 = np.empty((len(v), 3), np.float32)
+    for j in range(3):
+        tv = (v.astype(np.float32) - cf[j, 0]) * isd[0]
+        tw = (w.astype(np.float32) - cf[j, 1]) * isd[1]
+        d32[:, j] = tv * tv + tw * tw
+    return d32.argmin(1)
+
+
+def test_single_precision_near_ties_are_in_the_near_record():
+    # pixels on (or a hair off) the bisector of two centroids placed around
+    # a large code value: the rounding of the centroids to float32 flips
+    # many decisions, and every flip must be in the near record
+    rng = np.random.default_rng(0)
+    flips_seen = 0
+    for _ in range(300):
+        m = int(rng.integers(1000, 65000))
+        half = rng.uniform(0.5, 200)
+        eta = rng.uniform(-2e-3, 2e-3) * (m / 65535)
+        wc = rng.uniform(0, 60000)
+        c = np.array([[m - half, wc], [m + half + eta, wc + rng.uniform(-1e-3, 1e-3)], [0.0, 0.0]])
+        sd = np.array([rng.uniform(2, 50), rng.uniform(50, 3000)])
+        v = np.full(64, m, np.uint16)
+        w = rng.integers(0, 65536, 64).astype(np.uint16)
+        lab, near = group_assign(v, w, c, sd)
+        flips = _fp32_labels(v, w, c, sd) != lab
+        assert near[flips].all()
+        flips_seen += int(flips.sum())
+    assert flips_seen > 1000     # the construction does reach the rounding
 
 
 def test_constant_codes_form_one_cluster_with_empty_core():
