@@ -477,6 +477,60 @@ def run_ours(args, rank, local_rank, world):
     return result
 
 
+# ------------------------------------------------------------ profile case
+def run_profile_case(args, rank, local_rank, world):
+    """The small case that detailed ncu captures run: the same 1080p stream
+    and kernels as the default workload (K=5, FP16 state, default launch
+    shape, 500 training frames, freed after training), but one context and
+    only warmup + steps test frames on the device (about 2 GB held while
+    the cascade runs), each frame after the same 512 MB L2 flush.  Prints
+    the mean frame time and the stage occupancy; not a bench line."""
+    import torch
+    from cogsynth import workload
+    from cogsynth.gpu import GpuScene
+    from paper_1705_09339_gb300 import cog
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    torch.zeros(1, device=dev)
+    if args.l2_fetch >= 0:
+        cog.cog_set_l2_fetch_bytes(args.l2_fetch)
+    sc = workload("hd_dynamic", fg_frac=args.fg, seed=3)["scene"]
+    n_train, n_test = N_TRAIN, args.warmup + args.steps
+    stream = torch.cuda.current_stream(dev)
+    gs = GpuScene(sc, dev)
+    train = gs.render(0, n_train)
+    test = gs.render(n_train, n_test)
+    p = cog.cog_default_params(W_, H_, K_, state_dtype="f16")
+    if args.sample:
+        p.flags |= cog.COG_SAMPLE
+    ctx = cog.cog_create(p, stream.cuda_stream)
+    cog.cog_train_prior(ctx, train, n_train)
+    cog.cog_sync(ctx)
+    del train
+    torch.cuda.empty_cache()
+    masks = torch.empty((n_test, H_, W_), dtype=torch.uint8, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_test)]
+    for i in range(n_test):
+        if i == args.warmup:
+            cog.cog_sync(ctx)
+            _, tot0 = cog.cog_read_stats(ctx)
+        flush.zero_()
+        ev[i][0].record(stream)
+        cog.cog_apply(ctx, test[i], masks[i])
+        ev[i][1].record(stream)
+    cog.cog_sync(ctx)
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev[args.warmup:]]
+    _, tot1 = cog.cog_read_stats(ctx)
+    cog.cog_destroy(ctx)
+    occ = [(b - a) / (W_ * H_ * args.steps) for a, b in zip(tot0["n_stage"], tot1["n_stage"])]
+    return {"profile_case": f"{W_}x{H_} dynamic stream, K={K_}, FP16, {n_train} training frames",
+            "frames": args.steps, "ms_per_frame": round(sum(ms) / len(ms), 5),
+            "stage_occupancy": [round(x, 4) for x in occ]}
+
+
 # ---------------------------------------------------------------- clips
 CLIP_T = 32
 
@@ -1023,7 +1077,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fg", type=float, default=0.02)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="hd", choices=["hd", "clip", "batch64", "serve", "group"])
+    ap.add_argument("--workload", default="hd", choices=["hd", "clip", "batch64", "serve", "group", "profile"])
     ap.add_argument("--duration", type=float, default=20.0, help="serve: seconds of camera traffic")
     ap.add_argument("--cameras", type=int, default=256, help="serve: cameras")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
@@ -1045,7 +1099,7 @@ def main():
         import __graft_entry__
         __graft_entry__.build()
         r = {"batch64": run_batch, "serve": run_serve, "clip": run_clip,
-             "group": run_group}.get(args.workload, run_ours)(
+             "group": run_group, "profile": run_profile_case}.get(args.workload, run_ours)(
             args, rank, local_rank, world)
     if r is not None and rank == 0:
         print(json.dumps(r), flush=True)

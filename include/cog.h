@@ -275,7 +275,8 @@ cog_status cog_selftest_bounded_wait(int32_t limit_ms, uint32_t *error_word, dou
  *        code), an empty cluster keeping its centroid, ties to the lower
  *        cluster, until no label changes (at most 64 steps); the distance
  *        is evaluated in FP32 from centroids and reciprocal scales rounded
- *        to float once per step;
+ *        to float once per step, so a pixel within FP32 rounding of a tie
+ *        between its two nearest centroids may take either;
  *   5    Eq. 3: a core pixel has both codes strictly within its cluster's
  *        mean +- standard deviation;
  *   6    per cluster, the mean over its core of the trained dominant mode
@@ -303,6 +304,20 @@ typedef struct cog_group_stats {
 } cog_group_stats;
 cog_status cog_group(cog_ctx *ctx, const uint8_t *frames_dev, int32_t n_frames, uint16_t *codes_dev,
                      uint8_t *labels_dev, cog_group_stats *stats_host);
+
+/* Steps 3-6 of cog_group on the caller's codes (Sec. 2, "Clustering
+ * Similar Background", steps 4-6 and Eq. 3): the first assignment, then at
+ * most max_steps (0..64) Lloyd steps, stopping early once a step changes no
+ * label; then the Eq. 3 cores and step 6.  With max_steps = s the labels
+ * are those after step s (the core bit 0x80 added), which lets a caller
+ * follow the clustering step by step.  stats_host->iterations is the step
+ * that changed nothing, or max_steps if none did (converged = 0).
+ * codes_dev: device uint16 [2][P] as cog_group writes them, 2-byte
+ * aligned, read only; labels_dev: device uint8 [P].  Same state and
+ * argument rules as cog_group; max_steps outside 0..64 is
+ * COG_ERR_INVALID_ARG.  Returns when stats_host is filled. */
+cog_status cog_group_cluster(cog_ctx *ctx, const uint16_t *codes_dev, int32_t max_steps, uint8_t *labels_dev,
+                             cog_group_stats *stats_host);
 
 /* Measurement aid; the paper has no counterpart.  One pass over the planes
  * that stage 0 touches when every pixel passes it, with no arithmetic, to

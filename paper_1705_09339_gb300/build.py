@@ -20,7 +20,9 @@ BUILD = os.path.join(ROOT, "_build", platform.machine())
 LIB = os.path.join(PKG, "libcog.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+# host code: no FP contraction, so the host-side arithmetic (the grouping
+# statistics) rounds the same on x86 and Arm
+NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
                      "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
 
 

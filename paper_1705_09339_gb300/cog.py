@@ -95,6 +95,7 @@ def _load() -> C.CDLL:
         "cog_selftest_bounded_wait": (C.c_int, [i32, P(C.c_uint32), P(C.c_double)]),
         "cog_probe_stream": (C.c_int, [vp, vp, vp, vp, vp, vp, C.c_int64, vp]),
         "cog_group": (C.c_int, [vp, vp, i32, vp, vp, P(cog_group_stats)]),
+        "cog_group_cluster": (C.c_int, [vp, vp, i32, vp, P(cog_group_stats)]),
         "cog_apply_plain_gmm": (C.c_int, [vp, vp, vp]),
         "cog_apply_host": (C.c_int, [vp, vp, vp]),
         "cog_apply_host_noalloc": (C.c_int, [vp, vp, vp]),
@@ -218,6 +219,15 @@ def cog_group(ctx, frames, n_frames: int, codes, labels) -> dict:
     (uint8 [P]: cluster | 0x80 for a core pixel); returns the statistics."""
     st = cog_group_stats()
     _check(lib.cog_group(ctx, _ptr(frames), int(n_frames), _ptr(codes), _ptr(labels), C.byref(st)), ctx)
+    return st.as_dict()
+
+
+def cog_group_cluster(ctx, codes, max_steps: int, labels) -> dict:
+    """Grouping steps 3-6 on given codes (uint16 [2, P] on the GPU): the
+    first assignment and at most max_steps Lloyd steps, then the Eq. 3
+    cores; fills labels (uint8 [P]) and returns the statistics."""
+    st = cog_group_stats()
+    _check(lib.cog_group_cluster(ctx, _ptr(codes), int(max_steps), _ptr(labels), C.byref(st)), ctx)
     return st.as_dict()
 
 

@@ -31,18 +31,19 @@ cudaError_t launch_clip_f16(int, const ClipArgs &, int, cudaStream_t);
 cudaError_t launch_clip_bf16(int, const ClipArgs &, int, cudaStream_t);
 cudaError_t run_wait_selftest(uint64_t limit_ns, uint32_t *error_word, float *elapsed_ms);
 cudaError_t launch_group(int dtype, int K, const DevParams &dp, const StatePtrs &s, const uint8_t *frames, int N,
-                         uint16_t *codes, uint8_t *labels, int n_sm, cudaStream_t st);
+                         uint16_t *codes, uint8_t *labels, int max_steps, int n_sm, cudaStream_t st);
+int group_max_steps();
 size_t group_ctl_offset();
 size_t group_ctl_bytes();
-void group_ctl_decode(const void *raw, cog_group_stats *out);
+void group_ctl_decode(const void *raw, int max_steps, cog_group_stats *out);
 cudaError_t launch_probe_stream(const uint32_t *jl_in, const uint16_t *conf_in, const uint8_t *frame,
                                 uint32_t *jl_out, uint16_t *conf_out, uint8_t *mask, int64_t P, cudaStream_t st);
 int k1_batch_blocks_per_sm_f32(const LaunchCfg &);
 int k1_batch_blocks_per_sm_f16(const LaunchCfg &);
 int k1_batch_blocks_per_sm_bf16(const LaunchCfg &);
-int k2_blocks_per_sm_f32(int, const LaunchCfg &, bool);
-int k2_blocks_per_sm_f16(int, const LaunchCfg &, bool);
-int k2_blocks_per_sm_bf16(int, const LaunchCfg &, bool);
+int k2_blocks_per_sm_f32(int, const LaunchCfg &, int);
+int k2_blocks_per_sm_f16(int, const LaunchCfg &, int);
+int k2_blocks_per_sm_bf16(int, const LaunchCfg &, int);
 
 int elem_bytes(int dtype) { return dtype == COG_F32 ? 4 : 2; }
 
@@ -523,29 +524,57 @@ cog_status cog_selftest_bounded_wait(int32_t limit_ms, uint32_t *error_word, dou
     return COG_OK;
 }
 
-cog_status cog_group(cog_ctx *c, const uint8_t *frames_dev, int32_t n_frames, uint16_t *codes_dev,
+namespace {
+// Shared by cog_group (frames given: features first) and cog_group_cluster
+// (the caller's codes).
+cog_status group_run(cog_ctx *c, const uint8_t *frames_dev, int32_t n_frames, uint16_t *codes_dev, int32_t max_steps,
                      uint8_t *labels_dev, cog_group_stats *stats_host)
 {
-    cog_status s = check_ctx(c);
-    if (s) return s;
-    if (!c->trained) return set_err(c, COG_ERR_STATE, "cog_group before cog_train_prior");
-    if (c->p.flags & COG_PERCHAN)
-        return set_err(c, COG_ERR_INVALID_ARG, "grouping uses the shared-weight mixture; not defined with COG_PERCHAN");
-    if (!frames_dev || !codes_dev || !labels_dev || !stats_host)
-        return set_err(c, COG_ERR_INVALID_ARG, "frames_dev, codes_dev, labels_dev and stats_host are required");
-    if (n_frames < 2) return set_err(c, COG_ERR_INVALID_ARG, "need at least 2 training frames");
-    if (reinterpret_cast<uintptr_t>(codes_dev) & 1u) return set_err(c, COG_ERR_INVALID_ARG, "codes_dev must be 2-byte aligned");
-    if (c->L.P >= (int64_t)1 << 30) return set_err(c, COG_ERR_INVALID_ARG, "grouping needs fewer than 2^30 pixels");
     cudaError_t e = launch_group(c->p.state_dtype, c->p.K, c->dp, c->sp, frames_dev, n_frames, codes_dev, labels_dev,
-                                 c->n_sm, c->stream);
+                                 max_steps, c->n_sm, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "grouping launch");
     std::vector<unsigned char> raw(group_ctl_bytes());
     e = cudaMemcpyAsync(raw.data(), reinterpret_cast<const unsigned char *>(c->sp.ctl) + group_ctl_offset(), raw.size(),
                         cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "grouping result");
-    group_ctl_decode(raw.data(), stats_host);
+    group_ctl_decode(raw.data(), max_steps, stats_host);
     return COG_OK;
+}
+
+cog_status group_check(cog_ctx *c, const uint16_t *codes_dev, const uint8_t *labels_dev, const cog_group_stats *st)
+{
+    cog_status s = check_ctx(c);
+    if (s) return s;
+    if (!c->trained) return set_err(c, COG_ERR_STATE, "grouping before cog_train_prior");
+    if (c->p.flags & COG_PERCHAN)
+        return set_err(c, COG_ERR_INVALID_ARG, "grouping uses the shared-weight mixture; not defined with COG_PERCHAN");
+    if (!codes_dev || !labels_dev || !st)
+        return set_err(c, COG_ERR_INVALID_ARG, "codes_dev, labels_dev and stats_host are required");
+    if (reinterpret_cast<uintptr_t>(codes_dev) & 1u) return set_err(c, COG_ERR_INVALID_ARG, "codes_dev must be 2-byte aligned");
+    if (c->L.P >= (int64_t)1 << 30) return set_err(c, COG_ERR_INVALID_ARG, "grouping needs fewer than 2^30 pixels");
+    return COG_OK;
+}
+}  // namespace
+
+cog_status cog_group(cog_ctx *c, const uint8_t *frames_dev, int32_t n_frames, uint16_t *codes_dev,
+                     uint8_t *labels_dev, cog_group_stats *stats_host)
+{
+    cog_status s = group_check(c, codes_dev, labels_dev, stats_host);
+    if (s) return s;
+    if (!frames_dev) return set_err(c, COG_ERR_INVALID_ARG, "frames_dev is required");
+    if (n_frames < 2) return set_err(c, COG_ERR_INVALID_ARG, "need at least 2 training frames");
+    return group_run(c, frames_dev, n_frames, codes_dev, group_max_steps(), labels_dev, stats_host);
+}
+
+cog_status cog_group_cluster(cog_ctx *c, const uint16_t *codes_dev, int32_t max_steps, uint8_t *labels_dev,
+                             cog_group_stats *stats_host)
+{
+    cog_status s = group_check(c, codes_dev, labels_dev, stats_host);
+    if (s) return s;
+    if (max_steps < 0 || max_steps > group_max_steps())
+        return set_err(c, COG_ERR_INVALID_ARG, "max_steps must be in 0..%d", group_max_steps());
+    return group_run(c, nullptr, 0, const_cast<uint16_t *>(codes_dev), max_steps, labels_dev, stats_host);
 }
 
 cog_status cog_probe_stream(const uint32_t *jl_in, const uint16_t *conf_in, const uint8_t *frame,
@@ -926,7 +955,7 @@ cog_status cog_destroy(cog_ctx *c)
 // ---------------------------------------------------------------------------
 struct BatchGroupHost {
     int dtype = 0, K = 0;
-    bool pc = false;                   // per-channel mixtures
+    int mv = 0;                        // mixture variant (BatchGroupDev::mv)
     LaunchCfg launch;                  // the first member's launch shape
     std::vector<int> members;          // indices into cog_batch::ctxs
     std::vector<ApplyArgs> descs;      // host copy of the device descriptors
@@ -1039,14 +1068,14 @@ cog_status cog_batch_create(cog_ctx *const *ctxs, int32_t n, void *cuda_stream, 
         int gi = -1;
         for (size_t g = 0; g < b->groups.size(); g++)
             if (b->groups[g].dtype == ctxs[i]->p.state_dtype && b->groups[g].K == ctxs[i]->p.K &&
-                b->groups[g].pc == ((ctxs[i]->p.flags & COG_PERCHAN) != 0))
+                b->groups[g].mv == mix_variant(ctxs[i]->p.flags))
                 gi = (int)g;
         if (gi < 0) {
             b->groups.emplace_back();
             gi = (int)b->groups.size() - 1;
             b->groups[gi].dtype = ctxs[i]->p.state_dtype;
             b->groups[gi].K = ctxs[i]->p.K;
-            b->groups[gi].pc = (ctxs[i]->p.flags & COG_PERCHAN) != 0;
+            b->groups[gi].mv = mix_variant(ctxs[i]->p.flags);
             b->groups[gi].launch = ctxs[i]->launch;
         }
         b->groups[gi].members.push_back(i);
@@ -1059,9 +1088,9 @@ cog_status cog_batch_create(cog_ctx *const *ctxs, int32_t n, void *cuda_stream, 
         int64_t psum = 0;
         for (int i : g.members) psum += ctxs[i]->L.P;
         (void)psum;
-        const int per_sm = g.dtype == COG_F32 ? k2_blocks_per_sm_f32(g.K, g.launch, g.pc)
-                         : (g.dtype == COG_F16 ? k2_blocks_per_sm_f16(g.K, g.launch, g.pc)
-                                               : k2_blocks_per_sm_bf16(g.K, g.launch, g.pc));
+        const int per_sm = g.dtype == COG_F32 ? k2_blocks_per_sm_f32(g.K, g.launch, g.mv)
+                         : (g.dtype == COG_F16 ? k2_blocks_per_sm_f16(g.K, g.launch, g.mv)
+                                               : k2_blocks_per_sm_bf16(g.K, g.launch, g.mv));
         const int k1_bps = g.dtype == COG_F32 ? k1_batch_blocks_per_sm_f32(g.launch)
                          : (g.dtype == COG_F16 ? k1_batch_blocks_per_sm_f16(g.launch) : k1_batch_blocks_per_sm_bf16(g.launch));
         int64_t tiles_all = 0;
@@ -1100,7 +1129,7 @@ cog_status cog_batch_create(cog_ctx *const *ctxs, int32_t n, void *cuda_stream, 
         g.dev.k1_pre = g.dev.active + m;
         g.dev.k2_pre = g.dev.k1_pre + (m + 1);
         g.dev.n = m;
-        g.dev.pc = g.pc ? 1 : 0;
+        g.dev.mv = g.mv;
         g.active.assign(m, 1u);
         std::vector<uint32_t> fno(m), plan(plan_words);
         for (int j = 0; j < m; j++) fno[j] = (uint32_t)ctxs[g.members[j]]->frame_no;

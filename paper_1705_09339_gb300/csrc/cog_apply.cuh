@@ -13,12 +13,13 @@
 //
 // GB300 mapping.
 //   stage01_kernel: a light streaming kernel with no shared-memory staging
-//     and no barrier until its end.  A thread owns 8 consecutive pixels and
-//     issues all its stage-0 loads at once as 128/64-bit vectors (previous
-//     frame + label and confidence planes, frame bytes).  Pixels past stage
-//     0 fetch their 16-byte stage-1 record.  Pixels past stage 1 are
-//     compacted grid-wide: warp scan, CTA total, one atomic per CTA into the
-//     frame's survivor queue (16 bytes per survivor carrying everything the
+//     and one barrier at its end (the CTA's stage counts).  A thread owns 4
+//     consecutive pixels and issues all its stage-0 loads at once as
+//     128/64-bit vectors (previous frame + label and confidence planes,
+//     frame bytes), and writes its pixels' outputs at once.  Pixels past
+//     stage 0 are compacted per warp and fetch their 16-byte stage-1
+//     record.  Pixels past stage 1 go to the frame's survivor queue, one
+//     atomic per warp pass (16 bytes per survivor carrying everything the
 //     next stage needs).
 //   stage2_kernel: a persistent grid walks the queue; each survivor fetches
 //     its mixture record (one aligned block) and its three prior bytes in
@@ -55,268 +56,221 @@ __device__ __forceinline__ bool illum_flag_prev(const DevParams &dp, const uint3
 // Stage-1 confidence term: a + b (1 - D/255) + g (1 - t_r).
 __device__ __forceinline__ float conf_stage1(uint32_t q, int D, float tr)
 {
-    const float wa = (float)(q & 0xffu) * R255, wb = (float)(q >> 8) * R255;
-    const float wg = (float)(255u - (q & 0xffu) - (q >> 8)) * R255;
-    return wa + wb * (1.f - (float)D * R255) + wg * (1.f - tr);
+    const float wa = __fmul_rn((float)(q & 0xffu), R255), wb = __fmul_rn((float)(q >> 8), R255);
+    const float wg = __fmul_rn((float)(255u - (q & 0xffu) - (q >> 8)), R255);
+    const float dterm = __fsub_rn(1.f, __fmul_rn((float)D, R255));
+    return __fmaf_rn(wg, __fsub_rn(1.f, tr), __fmaf_rn(wb, dterm, wa));
 }
 
-// Shared memory of one warp of stage01_kernel: the stage-1 work list and
-// what its pixels need, and the results the owners collect.
-struct K1Warp {
-    uint2 stash[WPX];      // rgb | D << 24, C- bits
-    uint8_t list[WPX];     // pixel slot (lane * 4 + i)
-    uint8_t resst[WPX];    // 1: decided at stage 1, 2: survivor
-    float resc[WPX];       // new C of pixels decided at stage 1
+// Stage 1 of one pixel (Sec. 1, running Gaussian average; Sec. 3.2
+// halting): t_r = max_c (I_c - m_c)^2 / (lambda^2 v_c) against 1.  A
+// background pixel adapts (m, v) at alpha (1.5 - C-) unless halted (C- >=
+// c_halt); r is updated in place and *upd says whether it changed.  ix
+// holds I (r | g << 8 | b << 16).  Returns t_r (>= 1: on to stage 2).
+template <typename T>
+__device__ __forceinline__ float rga_step(const DevParams &dp, S1Rec<T> &r, uint32_t ix, float Cm, bool conf_on,
+                                          bool &upd)
+{
+    float m[3], v[3], I[3];
+    r.unpack(m, v);
+#pragma unroll
+    for (int c = 0; c < 3; c++) I[c] = (float)((ix >> (8 * c)) & 0xffu);
+    float tr = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const float t = eq2_chan_stat(I[c], m[c], v[c], dp.lam2);
+        tr = t > tr ? t : tr;
+    }
+    upd = tr < 1.f && !(conf_on && Cm >= dp.c_halt);
+    if (upd) {
+        const float ae = rate_eff(dp, Cm);
+#pragma unroll
+        for (int c = 0; c < 3; c++) eq2_chan_update(I[c], ae, __fsub_rn(1.f, ae), m[c], v[c], dp);
+        r.pack(m, v);
+    }
+    return tr;
+}
+
+// Shared memory of one CTA of stage01_kernel: its compacted stage-1 work
+// list (CPX = pixels of the CTA).  Entry j: ix = I (r | g << 8 | b << 16) |
+// D << 24 and cs = the pixel's C- bits; with 16-bit state cs also carries
+// the pixel's slot in the CTA (bits 16..31), with FP32 state the slot sits
+// in slot[j].
+template <typename T, int CPX> struct K1List {
+    uint32_t ix[CPX];
+    uint32_t cs[CPX];
+    uint16_t slot[Store<T>::bytes == 4 ? CPX : 1];
 };
 
-// One group of PPT consecutive pixels of a thread in stage01_kernel: its
-// loaded state, its frame words and its stage-0 outcome.
-template <typename T> struct K1Group {
-    uint4 jl;                 // previous frame + label of the 4 pixels
-    VecN<T, PPT> cv;          // confidence
+// A thread's PPT consecutive pixels in stage01_kernel: loaded state, frame
+// words, per-pixel D and the stage-0 outcome.
+template <typename T> struct K1Px {
+    uint4 jl;                 // previous frame + label
+    VecN<T, PPT> cv;          // confidence C-
     uint32_t Iw[PPT];         // this frame's pixels as r | g << 8 | b << 16
-    uint32_t ad[PPT];         // per-channel |I - J|, byte-wise
-    uint32_t skip, need1;     // bits: skipped by sampling, past stage 0
-    int nact;                 // pixels of the group inside the frame
+    uint32_t D[PPT];          // max_c |I_c - J_c|
+    uint32_t act;             // bits: pixel inside the frame
+    uint32_t skip;            // bits: not sampled this frame (COG_SAMPLE)
+    uint32_t need1;           // bits: past stage 0
 };
 
-// Stage-0 loads of one group: previous frame + label (16 B), confidence (8
-// or 16 B), frame bytes (12 B).  With temporal sampling, a 64-pixel block
-// off its phase reads its frame bytes only if some pixel in the group has
-// not saturated (Sec. 2, "Confidence based temporal sampling"; a group of 4
-// never straddles two blocks).
+// Loads and stage 0 of a thread's pixels p0 .. p0 + 3.
+//   Stage 0 (Sec. 2, CHP): a background pixel whose D = max_c |I_c - J_c|
+//   is at most tau_fd (0.5 + C-) keeps its label.  D is an integer, so the
+//   test is D <= floor(tau).
+//   Temporal sampling (Sec. 2, "Confidence based temporal sampling"): in a
+//   frame off its 64-pixel block's phase, a pixel with C- >= c_skip is not
+//   looked at (a group of 4 never straddles two blocks); a group whose
+//   pixels are all skipped reads no frame bytes.
 template <typename T, bool FULL>
-__device__ __forceinline__ void k1_group_load(const ApplyArgs &A, K1Group<T> &G, uint32_t p0)
+__device__ __forceinline__ void k1_stage0(const ApplyArgs &A, K1Px<T> &X, uint32_t p0)
 {
     const DevParams &dp = A.dp;
-    G.nact = FULL ? PPT : (int)min((int64_t)PPT, max((int64_t)0, dp.P - (int64_t)p0));
-    G.jl = make_uint4(0, 0, 0, 0);
-    G.skip = 0;
+    const bool conf_on = dp.flags & COG_CONF;
+    const int nact = FULL ? PPT : (int)min((int64_t)PPT, max((int64_t)0, dp.P - (int64_t)p0));
+    X.act = (1u << nact) - 1u;
+    X.skip = 0;
+    X.need1 = 0;
     uint32_t w0 = 0, w1 = 0, w2 = 0;
+    X.jl = make_uint4(0, 0, 0, 0);
 #pragma unroll
-    for (int i = 0; i < VecN<T, PPT>::NW; i++) G.cv.w[i] = 0;
-    if (FULL || G.nact > 0) {
-        G.jl = *reinterpret_cast<const uint4 *>(A.s.jl + p0);
-        G.cv.load(reinterpret_cast<const T *>(A.s.conf) + p0);
-        const bool sampling = (dp.flags & COG_SAMPLE) && (dp.flags & COG_CONF);
-        if (sampling && (A.frame_idx + (p0 >> 6)) % (uint32_t)dp.skip_period != 0u) {
+    for (int i = 0; i < VecN<T, PPT>::NW; i++) X.cv.w[i] = 0;
+    if (FULL || nact > 0) {
+        // the planes are padded to whole 4-pixel groups: vector loads stay in bounds
+        X.jl = *reinterpret_cast<const uint4 *>(A.s.jl + p0);
+        X.cv.load(reinterpret_cast<const T *>(A.s.conf) + p0);
+        if ((dp.flags & COG_SAMPLE) && conf_on && (A.frame_idx + (p0 >> 6)) % (uint32_t)dp.skip_period != 0u) {
 #pragma unroll
             for (int i = 0; i < PPT; i++)
-                if ((FULL || i < G.nact) && G.cv.get(i) >= dp.c_skip) G.skip |= 1u << i;
+                if (X.cv.get(i) >= dp.c_skip) X.skip |= 1u << i;
+            X.skip &= X.act;
         }
-        if (G.skip == (1u << G.nact) - 1u) {
+        if (X.skip == X.act) {
             // every pixel of the group keeps its label this frame
-        } else if (A.frame_al4 && (FULL || G.nact == PPT)) {
+        } else if (A.frame_al4 && (FULL || nact == PPT)) {
             const uint32_t *f4 = reinterpret_cast<const uint32_t *>(A.frame + (size_t)p0 * 3);
             w0 = f4[0]; w1 = f4[1]; w2 = f4[2];
         } else {
             uint32_t fw[3] = {0, 0, 0};
 #pragma unroll
             for (int b3 = 0; b3 < PPT * 3; b3++)
-                if (b3 < G.nact * 3) fw[b3 >> 2] |= (uint32_t)A.frame[(size_t)p0 * 3 + b3] << ((b3 & 3) * 8);
+                if (b3 < nact * 3) fw[b3 >> 2] |= (uint32_t)A.frame[(size_t)p0 * 3 + b3] << ((b3 & 3) * 8);
             w0 = fw[0]; w1 = fw[1]; w2 = fw[2];
         }
     }
-    G.Iw[0] = w0 & 0x00ffffffu;
-    G.Iw[1] = __byte_perm(w0, w1, 0x0543) & 0x00ffffffu;
-    G.Iw[2] = __byte_perm(w1, w2, 0x0432) & 0x00ffffffu;
-    G.Iw[3] = w2 >> 8;
-}
-
-// Stage 0 of one group: D = max_c |I_c - J_c| <= tau_fd (0.5 + C-) on a
-// background pixel.  D is an integer, so the test is D <= floor(tau)
-// applied to every channel at once.
-template <typename T, bool FULL>
-__device__ __forceinline__ void k1_group_stage0(const DevParams &dp, K1Group<T> &G)
-{
-    const bool conf_on = dp.flags & COG_CONF;
+    X.Iw[0] = w0 & 0x00ffffffu;
+    X.Iw[1] = __byte_perm(w0, w1, 0x0543) & 0x00ffffffu;
+    X.Iw[2] = __byte_perm(w1, w2, 0x0432) & 0x00ffffffu;
+    X.Iw[3] = w2 >> 8;
     const bool fd_on = dp.flags & COG_FD;
-#pragma unroll
-    for (int i = 0; i < PPT; i++) G.ad[i] = __vabsdiffu4(G.Iw[i], u4get(G.jl, i) & 0x00ffffffu);
-    G.need1 = 0;
+    uint32_t pass = 0;
 #pragma unroll
     for (int i = 0; i < PPT; i++) {
-        if ((!FULL && i >= G.nact) || (G.skip >> i & 1u)) continue;
-        const float Cm = conf_on ? G.cv.get(i) : 0.5f;
-        const float tau = dp.tau_fd * (0.5f + Cm);
-        const uint32_t t = tau >= 255.f ? 255u : (uint32_t)tau;      // floor, tau >= 0
-        const bool pass = fd_on && (u4get(G.jl, i) >> 24) == 0 && __vcmpgtu4(G.ad[i], t * 0x01010101u) == 0u;
-        if (!pass) G.need1 |= 1u << i;
+        const uint32_t j = u4get(X.jl, i);
+        // per-byte |I - J| (the top byte of both is 0), then the largest
+        const uint32_t ad = __vabsdiffu4(X.Iw[i], j & 0x00ffffffu);
+        X.D[i] = __vimax3_u32(ad & 0xffu, (ad >> 8) & 0xffu, ad >> 16);
+        const float Cm = conf_on ? X.cv.get(i) : 0.5f;
+        // floor(tau_fd (0.5 + C-)); the conversion saturates, tau >= 0
+        const uint32_t t = __float2uint_rz(__fmul_rn(dp.tau_fd, __fadd_rn(0.5f, Cm)));
+        pass |= (uint32_t)((j >> 24) == 0u && X.D[i] <= t) << i;
     }
+    if (!fd_on) pass = 0;
+    X.need1 = X.act & ~X.skip & ~pass;
 }
 
-// Outputs of one group: the previous frame becomes this frame with label 0
-// (the mixture stage sets its survivors' labels), the mask 0 (likewise),
-// the confidence of the pixels decided here; a pixel skipped by the
-// temporal sampling keeps everything and shows its carried label.
+// The thread's own outputs, written before stage 1 runs: the previous frame
+// becomes this frame with label 0, the mask 0 (the mixture stage sets its
+// survivors' labels and masks; a stage-1 background pixel keeps both), the
+// confidence of the pixels decided at stage 0 (the others keep C- until
+// stage 1 or 2 writes theirs); a skipped pixel keeps everything and shows
+// its carried label.  Returns the pixels decided at stage 0.
 template <typename T, bool FULL>
-__device__ __forceinline__ void k1_group_out(const ApplyArgs &A, const K1Warp &W, const K1Group<T> &G, uint32_t p0,
-                                             int slot0, uint32_t &n_fd, uint32_t &n_skip)
+__device__ __forceinline__ uint32_t k1_own_out(const ApplyArgs &A, const K1Px<T> &X, uint32_t p0)
 {
     const DevParams &dp = A.dp;
-    const bool conf_on = dp.flags & COG_CONF;
-    if (!(FULL || G.nact > 0)) return;
-    uint4 jn;
-    uint32_t sm = 0, mk = 0;
-    VecN<T, PPT> cn = G.cv;
-    bool any_c = false;
+    const uint32_t fd = X.act & ~X.skip & ~X.need1;
+    if (!(FULL || X.act)) return 0;
+    uint4 jn = make_uint4(X.Iw[0], X.Iw[1], X.Iw[2], X.Iw[3]);
+    uint32_t mk = 0;
+    const uint32_t keep = FULL ? X.skip : (X.skip | ~X.act);
+    if (keep) {
 #pragma unroll
-    for (int i = 0; i < PPT; i++) {
-        const bool act = FULL || i < G.nact;
-        const bool sk = G.skip >> i & 1u;
-        const uint32_t r1 = (G.need1 >> i & 1u) ? W.resst[slot0 + i] : 0u;
-        n_fd += act && !sk && r1 == 0;
-        n_skip += sk;
-        if (conf_on && act && !sk && r1 != 2) {
-            cn.set(i, r1 == 0 ? (1.f - dp.eta) * G.cv.get(i) + dp.eta : W.resc[slot0 + i]);
-            any_c = true;
+        for (int i = 0; i < PPT; i++) {
+            const uint32_t j = u4get(X.jl, i);
+            if (keep >> i & 1u) u4set(jn, i, j);
+            if (X.skip >> i & 1u) mk |= ((j >> 24) ? 255u : 0u) << (8 * i);
         }
-        u4set(jn, i, act && !sk ? G.Iw[i] : u4get(G.jl, i));
-        if (sk) mk |= ((u4get(G.jl, i) >> 24) ? 255u : 0u) << (8 * i);
-        sm |= (sk ? (uint32_t)COG_ST_SKIP
-                  : (r1 == 0 ? (uint32_t)COG_ST_FD : (r1 == 1 ? (uint32_t)COG_ST_RGA : (uint32_t)COG_ST_GMM_BG)))
-              << (8 * i);
     }
-    if (jn.x != G.jl.x || jn.y != G.jl.y || jn.z != G.jl.z || jn.w != G.jl.w)
-        *reinterpret_cast<uint4 *>(A.s.jl + p0) = jn;
-    if (any_c) cn.store(reinterpret_cast<T *>(A.s.conf) + p0);
-    if ((FULL || G.nact == PPT) && A.out_al4) {
+    *reinterpret_cast<uint4 *>(A.s.jl + p0) = jn;
+    if (dp.flags & COG_CONF) {
+        // C <- (1 - eta) C- + eta for the stage-0 pixels (c_inst = 1)
+        VecN<T, PPT> cn = X.cv;
+        if (Store<T>::bytes == 2) {
+#pragma unroll
+            for (int h = 0; h < PPT / 2; h++) {
+                if (!(fd >> (2 * h) & 3u)) continue;
+                const float2 c = Pair<T>::to_f2(X.cv.w[h]);
+                const float lo = (fd >> (2 * h) & 1u) ? conf_next(dp, c.x, 1.f) : c.x;
+                const float hi = (fd >> (2 * h + 1) & 1u) ? conf_next(dp, c.y, 1.f) : c.y;
+                cn.w[h] = Pair<T>::from_f2(lo, hi);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < PPT; i++)
+                if (fd >> i & 1u) cn.set(i, conf_next(dp, X.cv.get(i), 1.f));
+        }
+        cn.store(reinterpret_cast<T *>(A.s.conf) + p0);
+    }
+    uint32_t sm = 0;
+    if (A.stagemap) {
+#pragma unroll
+        for (int i = 0; i < PPT; i++)
+            sm |= ((X.skip >> i & 1u) ? (uint32_t)COG_ST_SKIP
+                                      : ((fd >> i & 1u) ? (uint32_t)COG_ST_FD : (uint32_t)COG_ST_GMM_BG)) << (8 * i);
+    }
+    if ((FULL || X.act == 0xfu) && A.out_al4) {
         *reinterpret_cast<uint32_t *>(A.mask + p0) = mk;
         if (A.stagemap) *reinterpret_cast<uint32_t *>(A.stagemap + p0) = sm;
     } else {
-        for (int i = 0; i < G.nact; i++) {
+        for (int i = 0; i < PPT; i++) {
+            if (!(X.act >> i & 1u)) continue;
             A.mask[p0 + i] = (uint8_t)(mk >> (8 * i));
             if (A.stagemap) A.stagemap[p0 + i] = (uint8_t)(sm >> (8 * i));
         }
     }
+    return fd;
 }
 
-// One warp's WPX pixels (K1_G groups of 128: each lane owns 4 consecutive
-// pixels of every group) through stages 0 and 1.  FULL: every pixel of the
-// warp lies inside the frame (all warps but the last one's).  Returns the
-// warp's survivor count; counts of the pixels decided here are added to
-// n_fd / n_rga / n_skip (per lane).
-template <typename T, bool FULL>
-__device__ __forceinline__ int k1_warp(const ApplyArgs &A, K1Warp &W, uint32_t wbase, int lane, uint32_t seg,
-                                       uint32_t &n_fd, uint32_t &n_rga, uint32_t &n_skip)
-{
-    const DevParams &dp = A.dp;
-    const bool conf_on = dp.flags & COG_CONF;
-    K1Group<T> grp[K1_G];
-#pragma unroll
-    for (int g = 0; g < K1_G; g++) k1_group_load<T, FULL>(A, grp[g], wbase + g * 128 + (uint32_t)lane * PPT);
-#pragma unroll
-    for (int g = 0; g < K1_G; g++) k1_group_stage0<T, FULL>(dp, grp[g]);
-
-    // ---- the stage-1 work list of the warp
-    int n1 = 0;
-#pragma unroll
-    for (int g = 0; g < K1_G; g++) n1 += __popc(grp[g].need1);
-    int incl = n1;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, incl, off);
-        if (lane >= off) incl += t;
-    }
-    const int n1w = __shfl_sync(0xffffffffu, incl, 31);
-    {
-        int k = incl - n1;
-#pragma unroll
-        for (int g = 0; g < K1_G; g++) {
-            if (!grp[g].need1) continue;
-#pragma unroll
-            for (int i = 0; i < PPT; i++) {
-                if (!(grp[g].need1 >> i & 1u)) continue;
-                const int slot = g * 128 + lane * PPT + i;
-                W.list[k++] = (uint8_t)slot;
-                const uint32_t m2 = __vmaxu4(grp[g].ad[i], grp[g].ad[i] >> 8);
-                const uint32_t D = __vmaxu4(m2, m2 >> 8) & 0xffu;
-                W.stash[slot] = make_uint2(grp[g].Iw[i] | (D << 24),
-                                           __float_as_uint(conf_on ? grp[g].cv.get(i) : 0.5f));
-            }
-        }
-    }
-    __syncwarp();
-
-    // ---- stage 1 over the compacted list: one pass per 32 pixels left
-    int ne = 0;
-    const uint32_t lt = (1u << lane) - 1u;
-    for (int j0 = 0; j0 < n1w; j0 += 32) {
-        const int j = j0 + lane;
-        bool surv = false;
-        uint4 ent = make_uint4(0, 0, 0, 0);
-        if (j < n1w) {
-            const int slot = W.list[j];
-            const uint32_t p = wbase + slot;
-            const uint2 sv = W.stash[slot];
-            const int D = (int)(sv.x >> 24);
-            const float Cm = __uint_as_float(sv.y);
-            S1Rec<T> r;
-            r.load(A.s.s1, p);
-            if (dp.flags & COG_RGA) {
-                float tr = 0.f;
-#pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    const float d = (float)((sv.x >> (8 * c)) & 0xffu) - r.get(c);
-                    const float t = __fdividef(d * d, dp.lam2 * r.get(3 + c));
-                    tr = t > tr ? t : tr;
-                }
-                if (tr < 1.f) {
-                    if (!(conf_on && Cm >= dp.c_halt)) {
-                        const float ae = dp.alpha * (1.5f - Cm);
-#pragma unroll
-                        for (int c = 0; c < 3; c++) {
-                            const float I = (float)((sv.x >> (8 * c)) & 0xffu);
-                            const float m = r.get(c) + ae * (I - r.get(c));
-                            const float d = I - m;
-                            r.set(c, m);
-                            r.set(3 + c, clampf((1.f - ae) * r.get(3 + c) + ae * d * d, dp.var_min, dp.var_max));
-                        }
-                        r.store(A.s.s1, p);
-                    }
-                    W.resc[slot] = (1.f - dp.eta) * Cm + dp.eta * conf_stage1(r.qab(), D, tr);
-                    W.resst[slot] = 1;
-                    n_rga++;
-                } else {
-                    surv = true;
-                }
-            } else {
-                surv = true;
-            }
-            if (surv) {
-                W.resst[slot] = 2;
-                ent = make_uint4(p, sv.x, sv.y, r.qab());
-            }
-        }
-        // survivors of this pass go straight to the frame's queue segment
-        const uint32_t b = __ballot_sync(0xffffffffu, surv);
-        if (b) {
-            uint32_t base = 0;
-            if (lane == 0) base = atomicAdd(A.s.ctl + ctl_qcnt(A.frame_no % 3, seg), (uint32_t)__popc(b));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (surv) A.s.queue[(int64_t)seg * A.s.qseg_cap + base + __popc(b & lt)] = ent;
-        }
-        ne += __popc(b);
-    }
-    __syncwarp();
-
-#pragma unroll
-    for (int g = 0; g < K1_G; g++)
-        k1_group_out<T, FULL>(A, W, grp[g], wbase + g * 128 + (uint32_t)lane * PPT, g * 128 + lane * PPT, n_fd, n_skip);
-    return ne;
-}
-
-// One CTA of the stage-0/1 pass over stream A: tile `cta` of its frame.
+// One CTA of the stage-0/1 pass over stream A: tile `cta` of its frame
+// (CPX = 4 TPB consecutive pixels, each thread owning 4 of them).
+//   1. every thread loads its pixels, runs stage 0 and writes its outputs;
+//   2. the pixels past stage 0 of the whole CTA are compacted into one
+//      shared list (warp ballots, then the warps' offsets), so stage 1 runs
+//      ceil(n / 32) warp passes for the CTA's n candidates, spread over its
+//      warps, instead of at least one partly idle pass per warp;
+//   3. a stage-1 lane writes its pixel's results itself (the owners' stores
+//      came before the barrier), and survivors go straight to the frame's
+//      queue segment of the warp (one atomic per warp pass);
+//   4. the stage counts are summed over the CTA and added to the frame's
+//      counters once.
 template <typename T, int TPB>
 __device__ __forceinline__ void k1_cta(const ApplyArgs &A, uint32_t cta)
 {
-    static_assert(PPT == 4, "frame and mask vector widths assume groups of 4 pixels");
-    constexpr int NW = TPB / 32;
-    __shared__ K1Warp W_s[NW];
+    static_assert(PPT == 4 && K1_G == 1, "frame and mask vector widths assume one group of 4 pixels per thread");
+    constexpr int NW = TPB / 32, CPX = TPB * PPT;
+    constexpr bool WIDE = Store<T>::bytes == 4;
+    static_assert(CPX <= 65536, "slots fit 16 bits");
+    __shared__ K1List<T, CPX> L;
+    __shared__ uint32_t wcnt_s[NW];
+    __shared__ uint32_t cnt_s[NW][4];
+    const DevParams &dp = A.dp;
+    const bool conf_on = dp.flags & COG_CONF;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t n = A.frame_no;
     uint32_t *ctl = A.s.ctl;
-    const uint32_t wbase = (cta * NW + warp) * WPX;
+    const uint32_t cbase = cta * CPX;
+    const uint32_t p0 = cbase + (uint32_t)tid * PPT;
 
     if (cta == 0) {
         // rotate the per-frame counters: clear frame n+1's, add frame n-1's
@@ -333,25 +287,112 @@ __device__ __forceinline__ void k1_cta(const ApplyArgs &A, uint32_t cta)
         }
     }
 
-    // warp w puts its survivors into queue segment w % QSEG
-    const uint32_t gwarp = cta * NW + warp;
-    const uint32_t seg = gwarp & (QSEG - 1);
-    uint32_t n_fd = 0, n_rga = 0, n_skip = 0;
-    int ne;
-    if ((int64_t)wbase + WPX <= A.dp.P) ne = k1_warp<T, true>(A, W_s[warp], wbase, lane, seg, n_fd, n_rga, n_skip);
-    else ne = k1_warp<T, false>(A, W_s[warp], wbase, lane, seg, n_fd, n_rga, n_skip);
-
-    // per-warp counts (padded counters)
-    const uint32_t vfd = __reduce_add_sync(0xffffffffu, n_fd);
-    const uint32_t vrga = __reduce_add_sync(0xffffffffu, n_rga);
-    const uint32_t vskip = __reduce_add_sync(0xffffffffu, n_skip);
-    if (lane == 0) {
-        const uint32_t slot = gwarp & (CTL_SLOTS - 1);
-        if (vfd) atomicAdd(ctl + ctl_slot(n % 3, 0, slot), vfd);
-        if (vrga) atomicAdd(ctl + ctl_slot(n % 3, 1, slot), vrga);
-        if (vskip) atomicAdd(ctl + ctl_slot(n % 3, 6, slot), vskip);
-        if (ne) atomicAdd(ctl + ctl_slot(n % 3, 5, slot), (uint32_t)ne);
+    // ---- 1. stage 0 and the owners' outputs
+    K1Px<T> X;
+    uint32_t fd;
+    if ((int64_t)cbase + CPX <= dp.P) {
+        k1_stage0<T, true>(A, X, p0);
+        fd = k1_own_out<T, true>(A, X, p0);
+    } else {
+        k1_stage0<T, false>(A, X, p0);
+        fd = k1_own_out<T, false>(A, X, p0);
     }
+
+    // ---- 2. the CTA's stage-1 list, candidates in pixel order
+    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t nw = 0, dst = 0;
+#pragma unroll
+    for (int i = 0; i < PPT; i++) {
+        const uint32_t b = __ballot_sync(0xffffffffu, X.need1 >> i & 1u);
+        nw += __popc(b);
+        dst += __popc(b & lt);
+    }
+    if (lane == 0) wcnt_s[warp] = nw;
+    __syncthreads();
+    uint32_t n1 = 0;
+#pragma unroll
+    for (int w = 0; w < NW; w++) {
+        const uint32_t c = wcnt_s[w];
+        dst += w < warp ? c : 0u;
+        n1 += c;
+    }
+#pragma unroll
+    for (int i = 0; i < PPT; i++) {
+        if (!(X.need1 >> i & 1u)) continue;
+        const uint32_t slot = (uint32_t)tid * PPT + i;
+        L.ix[dst] = X.Iw[i] | (X.D[i] << 24);
+        if (WIDE) {
+            L.cs[dst] = X.cv.w[i];
+            L.slot[dst] = (uint16_t)slot;
+        } else {
+            L.cs[dst] = ((X.cv.w[i >> 1] >> (16 * (i & 1))) & 0xffffu) | (slot << 16);
+        }
+        dst++;
+    }
+    __syncthreads();
+
+    // ---- 3. stage 1 (Sec. 1, running Gaussian average), 32 candidates per
+    //      warp pass; warp w's survivors go to queue segment (global warp) % QSEG
+    const uint32_t seg = (cta * NW + warp) & (QSEG - 1);
+    uint32_t n_rga = 0, ne = 0;
+    for (uint32_t j0 = (uint32_t)warp * 32; j0 < n1; j0 += TPB) {
+        const uint32_t j = j0 + (uint32_t)lane;
+        bool surv = false;
+        uint4 ent = make_uint4(0, 0, 0, 0);
+        if (j < n1) {
+            const uint32_t ix = L.ix[j], cs = L.cs[j];
+            const uint32_t p = cbase + (WIDE ? (uint32_t)L.slot[j] : (cs >> 16));
+            const int D = (int)(ix >> 24);
+            const float Cm = conf_on ? Store<T>::unbits(WIDE ? cs : (cs & 0xffffu)) : 0.5f;
+            S1Rec<T> r;
+            r.load(A.s.s1, p);
+            surv = true;
+            if (dp.flags & COG_RGA) {
+                bool upd;
+                const float tr = rga_step<T>(dp, r, ix, Cm, conf_on, upd);
+                if (tr < 1.f) {
+                    surv = false;
+                    if (upd) r.store(A.s.s1, p);
+                    if (conf_on)
+                        reinterpret_cast<T *>(A.s.conf)[p] =
+                            Store<T>::from_f(conf_next(dp, Cm, conf_stage1(r.qab(), D, tr)));
+                    if (A.stagemap) A.stagemap[p] = (uint8_t)COG_ST_RGA;
+                    n_rga++;
+                }
+            }
+            if (surv) ent = make_uint4(p, ix, __float_as_uint(Cm), r.qab());
+        }
+        const uint32_t b = __ballot_sync(0xffffffffu, surv);
+        if (b) {
+            uint32_t base = 0;
+            if (lane == 0) base = atomicAdd(A.s.ctl + ctl_qcnt(n % 3, seg), (uint32_t)__popc(b));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (surv) A.s.queue[(int64_t)seg * A.s.qseg_cap + base + __popc(b & lt)] = ent;
+        }
+        ne += __popc(b);
+    }
+
+    // ---- 4. the CTA's counts (fields: 0 stage 0, 1 stage 1, 6 skipped,
+    //      5 reached the mixture stage)
+    const uint32_t c0 = __reduce_add_sync(0xffffffffu, (uint32_t)__popc(fd));
+    const uint32_t c1 = __reduce_add_sync(0xffffffffu, n_rga);
+    const uint32_t c2 = __reduce_add_sync(0xffffffffu, (uint32_t)__popc(X.skip));
+    if (lane == 0) {
+        cnt_s[warp][0] = c0;
+        cnt_s[warp][1] = c1;
+        cnt_s[warp][2] = c2;
+        cnt_s[warp][3] = ne;
+    }
+    __syncthreads();
+    if (tid < 4) {
+        uint32_t v = 0;
+#pragma unroll
+        for (int w = 0; w < NW; w++) v += cnt_s[w][tid];
+        const int f = tid == 0 ? 0 : (tid == 1 ? 1 : (tid == 2 ? 6 : 5));
+        if (v) atomicAdd(ctl + ctl_slot(n % 3, f, cta & (CTL_SLOTS - 1)), v);
+    }
+    // (a persistent caller's next tile writes wcnt_s only after its own
+    // first barrier, which every thread reaches after the reads above)
 }
 
 template <typename T, int TPB>
@@ -381,7 +422,7 @@ template <typename T, int K, bool PC = false> struct S2In {
     S1Rec<T> s1;   // COG_MODE1 only: the stage-1 copy of the rank-1 mode
 };
 
-template <typename T, int K, bool PC = false>
+template <typename T, int K, bool PC = false, bool M1 = false>
 __device__ __forceinline__ void s2_load(const ApplyArgs &A, int64_t qi, S2In<T, K, PC> &in)
 {
     in.e = __ldcg(A.s.queue + qi);
@@ -391,7 +432,7 @@ __device__ __forceinline__ void s2_load(const ApplyArgs &A, int64_t qi, S2In<T, 
     const uint4 *src = reinterpret_cast<const uint4 *>(A.s.gmm + p * RecSel<T, K, PC>::BYTES);
 #pragma unroll
     for (int i = 0; i < RecSel<T, K, PC>::NV; i++) in.rec[i] = src[i];
-    if (!PC && (A.dp.flags & COG_MODE1)) in.s1.load(A.s.s1, p);
+    if (M1) in.s1.load(A.s.s1, p);
 }
 
 // Confidence of a pixel decided at stage 2 (Sec. 2, "Confidence Measure"):
@@ -402,17 +443,17 @@ __device__ __forceinline__ float conf_stage2(const DevParams &dp, const uint32_t
     uint32_t qmin = qk[0] < qk[1] ? qk[0] : qk[1];
     qmin = qk[2] < qmin ? qk[2] : qmin;
     const uint32_t qa = qab & 0xffu, qb = qab >> 8;
-    const float wa = (float)qa * R255, wb = (float)qb * R255;
-    const float wg = (float)(255u - qa - qb) * R255;
-    const float dhat = (float)D * R255;
+    const float wa = __fmul_rn((float)qa, R255), wb = __fmul_rn((float)qb, R255);
+    const float wg = __fmul_rn((float)(255u - qa - qb), R255);
+    const float dterm = __fsub_rn(1.f, __fmul_rn((float)D, R255)), mterm = __fsub_rn(1.f, Mh);
     float ci;
     if ((int)qmin < dp.q_null) {
-        const float den = wb + wg;
-        ci = den > 0.f ? (wb * (1.f - dhat) + wg * (1.f - Mh)) / den : 0.f;
+        const float den = __fadd_rn(wb, wg);
+        ci = den > 0.f ? __fdiv_rn(__fmaf_rn(wg, mterm, __fmul_rn(wb, dterm)), den) : 0.f;
     } else {
-        ci = wa * ((float)qmin * R255) + wb * (1.f - dhat) + wg * (1.f - Mh);
+        ci = __fmaf_rn(wg, mterm, __fmaf_rn(wb, dterm, __fmul_rn(wa, __fmul_rn((float)qmin, R255))));
     }
-    return (1.f - dp.eta) * Cm + dp.eta * ci;
+    return conf_next(dp, Cm, ci);
 }
 
 // Stage 2 with per-channel mixtures (COG_PERCHAN): returns the stage code.
@@ -429,7 +470,7 @@ __device__ __forceinline__ int s2_finish_pc(const ApplyArgs &A, const S2In<T, K,
     const uint32_t qab = in.e.w & 0xffffu;
     MixPC<K> m;
     mixpc_unpack<T, K>(in.rec, m);
-    const MixOutPC o = mix_step_pc<K>(m, I, dp.alpha * (1.5f - Cm), dp);
+    const MixOutPC o = mix_step_pc<K>(m, I, rate_eff(dp, Cm), dp);
     int label = o.fg, st = o.fg ? COG_ST_FG : COG_ST_GMM_BG;
     if (flag && o.fg) {
         illum_response_pc<K>(m, o, dp.w_illum);
@@ -454,8 +495,8 @@ __device__ __forceinline__ int s2_finish_pc(const ApplyArgs &A, const S2In<T, K,
     return st;
 }
 
-template <typename T, int K>
-__device__ __forceinline__ int s2_finish(const ApplyArgs &A, const S2In<T, K> &in, bool flag)
+template <typename T, int K, bool M1>
+__device__ __forceinline__ int s2_finish(const ApplyArgs &A, S2In<T, K> &in, bool flag)
 {
     const DevParams &dp = A.dp;
     const bool conf_on = dp.flags & COG_CONF;
@@ -466,44 +507,56 @@ __device__ __forceinline__ int s2_finish(const ApplyArgs &A, const S2In<T, K> &i
     for (int c = 0; c < 3; c++) I[c] = (float)((in.e.y >> (8 * c)) & 0xffu);
     const float Cm = __uint_as_float(in.e.z);
     const uint32_t qab = in.e.w & 0xffffu;
-    Mix<K> m;
+    const float ae = rate_eff(dp, Cm);
+    MixOut o;
+    int label, st;
+    if constexpr (M1) {
+        // stage 1 is a copy of the rank-1 mode: written back first, and
+        // re-taken from the updated mixture
+        Mix<K> m;
 #pragma unroll
-    for (int k = 0; k < K; k++) {
-        m.w[k] = rec_elem<T, K>(in.rec, 7 * k);
+        for (int k = 0; k < K; k++) {
+            m.w[k] = rec_elem<T, K>(in.rec, 7 * k);
 #pragma unroll
-        for (int c = 0; c < 3; c++) {
-            m.mu[k][c] = rec_elem<T, K>(in.rec, 7 * k + 1 + c);
-            m.v[k][c] = rec_elem<T, K>(in.rec, 7 * k + 4 + c);
+            for (int c = 0; c < 3; c++) {
+                m.mu[k][c] = rec_elem<T, K>(in.rec, 7 * k + 1 + c);
+                m.v[k][c] = rec_elem<T, K>(in.rec, 7 * k + 4 + c);
+            }
         }
-    }
-    const bool mode1 = dp.flags & COG_MODE1;
-    if (mode1) mode1_write_back<T, K>(m, in.s1);
-    const float ae = dp.alpha * (1.5f - Cm);
-    const MixOut o = mix_step<K>(m, I, ae, dp);
-    int label = o.fg, st = o.fg ? COG_ST_FG : COG_ST_GMM_BG;
-    if (flag && o.fg) {
-        illum_response<K>(m, o.tgt, dp.w_illum);
-        label = 0;
-        st = COG_ST_ILLUM;
-    }
-    rec_store<T, K>(A.s.gmm, p, m);
-    if (mode1) {
+        mode1_write_back<T, K>(m, in.s1);
+        o = mix_step<K>(m, I, ae, dp);
+        label = o.fg;
+        st = o.fg ? COG_ST_FG : COG_ST_GMM_BG;
+        if (flag && o.fg) {
+            illum_response<K>(m, o.tgt, dp.w_illum);
+            label = 0;
+            st = COG_ST_ILLUM;
+        }
+        rec_store<T, K>(A.s.gmm, p, m);
         S1Rec<T> r = in.s1;
         mode1_recache<T, K>(m, r);
         r.store(A.s.s1, p);
-    } else if (!label) {   // transition update: the background mode seeds stage 1
-        S1Rec<T> r;
-#pragma unroll
-        for (int i = 0; i < S1Rec<T>::NV; i++) r.u[i] = make_uint4(0, 0, 0, 0);
-#pragma unroll
-        for (int k = 0; k < K; k++) {
-            if (k == o.tgt) {
-#pragma unroll
-                for (int c = 0; c < 3; c++) { r.set(c, m.mu[k][c]); r.set(3 + c, m.v[k][c]); }
-            }
+    } else {
+        // the record stays in its stored form (fewer live registers)
+        float tmv[6];
+        o = mix_step_packed<T, K>(in.rec, I, ae, dp, flag, tmv);
+        label = o.fg;
+        st = o.fg ? COG_ST_FG : COG_ST_GMM_BG;
+        if (flag && o.fg) {   // illumination response (applied inside the step)
+            label = 0;
+            st = COG_ST_ILLUM;
         }
-        r.set_qab(qab);
-        r.store(A.s.s1, p);
+        uint4 *dst = reinterpret_cast<uint4 *>(A.s.gmm + p * Rec<T, K>::BYTES);
+#pragma unroll
+        for (int i = 0; i < Rec<T, K>::NV; i++) dst[i] = in.rec[i];
+        if (!label) {   // transition update: the background mode seeds stage 1
+            S1Rec<T> r;
+#pragma unroll
+            for (int i = 0; i < S1Rec<T>::NV; i++) r.u[i] = make_uint4(0, 0, 0, 0);
+            r.pack(tmv, tmv + 3);
+            r.set_qab(qab);
+            r.store(A.s.s1, p);
+        }
     }
     if (conf_on) {
         const float Mh = o.match >= 0 ? (o.tm < 1.f ? o.tm : 1.f) : 1.f;
@@ -515,8 +568,9 @@ __device__ __forceinline__ int s2_finish(const ApplyArgs &A, const S2In<T, K> &i
     return st;
 }
 
-// One of ncta CTAs walking stream A's survivor queue.
-template <typename T, int K, int TPB, bool PC = false>
+// One of ncta CTAs walking stream A's survivor queue.  V: the mixture
+// variant (mix_variant: 0 shared weights, 1 per-channel, 2 COG_MODE1).
+template <typename T, int K, int TPB, int V>
 __device__ __forceinline__ void k2_cta(const ApplyArgs &A, uint32_t cta, uint32_t ncta)
 {
     __shared__ uint32_t flag_s, cnt_s[3], segp_s[QSEG + 1];
@@ -552,11 +606,12 @@ __device__ __forceinline__ void k2_cta(const ApplyArgs &A, uint32_t cta, uint32_
     };
     uint32_t cbg = 0, cfg = 0, cil = 0;
     for (uint32_t q = cta * TPB + tid; q < nq; q += stride) {
+        constexpr bool PC = V == 1;
         S2In<T, K, PC> a;
-        s2_load<T, K, PC>(A, entry(q), a);
+        s2_load<T, K, PC, V == 2>(A, entry(q), a);
         int st;
         if constexpr (PC) st = s2_finish_pc<T, K>(A, a, flag);
-        else st = s2_finish<T, K>(A, a, flag);
+        else st = s2_finish<T, K, V == 2>(A, a, flag);
         cbg += st == COG_ST_GMM_BG; cfg += st == COG_ST_FG; cil += st == COG_ST_ILLUM;
     }
     cbg = __reduce_add_sync(0xffffffffu, cbg);
@@ -571,12 +626,12 @@ __device__ __forceinline__ void k2_cta(const ApplyArgs &A, uint32_t cta, uint32_
     if (tid < 3 && cnt_s[tid]) atomicAdd(ctl + ctl_slot(n % 3, 2 + tid, cta & (CTL_SLOTS - 1)), cnt_s[tid]);
 }
 
-template <typename T, int K, int TPB, bool PC = false>
+template <typename T, int K, int TPB, int V>
 __global__ void __launch_bounds__(TPB) stage2_kernel(const ApplyArgs A)
 {
     grid_launch_dependents();
     grid_wait_prior();     // the queue and counters come from stage01_kernel
-    k2_cta<T, K, TPB, PC>(A, blockIdx.x, gridDim.x);
+    k2_cta<T, K, TPB, V>(A, blockIdx.x, gridDim.x);
 }
 
 // ---- batched: many streams of one storage type and K in one launch each
@@ -606,14 +661,14 @@ __global__ void __launch_bounds__(TPB, K1_THREADS_PER_SM / TPB) stage01_batch_ke
 }
 
 // The mixture-stage CTAs are split among the active streams only.
-template <typename T, int K, int TPB, bool PC = false>
+template <typename T, int K, int TPB, int V>
 __global__ void __launch_bounds__(TPB) stage2_batch_kernel(const BatchGroupDev G)
 {
     grid_launch_dependents();
     grid_wait_prior();
     if (blockIdx.x >= __ldg(G.k2_pre + G.n)) return;
     const int s = batch_stream(G.k2_pre, G.n, blockIdx.x);
-    k2_cta<T, K, TPB, PC>(G.descs[s], blockIdx.x - G.k2_pre[s], G.k2_pre[s + 1] - G.k2_pre[s]);
+    k2_cta<T, K, TPB, V>(G.descs[s], blockIdx.x - G.k2_pre[s], G.k2_pre[s + 1] - G.k2_pre[s]);
 }
 
 // Launch with programmatic stream serialization: the kernel may be
@@ -643,10 +698,11 @@ void (*k1_single(int tpb))(ApplyArgs)
     return tpb == 64 ? stage01_kernel<T, 64> : (tpb == 256 ? stage01_kernel<T, 256> : stage01_kernel<T, 128>);
 }
 template <typename T, int K>
-void (*k2_single(int tpb, bool pc))(ApplyArgs)
+void (*k2_single(int tpb, int mv))(ApplyArgs)
 {
-    if (pc) return tpb == 128 ? stage2_kernel<T, K, 128, true> : stage2_kernel<T, K, 64, true>;
-    return tpb == 128 ? stage2_kernel<T, K, 128> : stage2_kernel<T, K, 64>;
+    if (mv == 1) return tpb == 128 ? stage2_kernel<T, K, 128, 1> : stage2_kernel<T, K, 64, 1>;
+    if (mv == 2) return tpb == 128 ? stage2_kernel<T, K, 128, 2> : stage2_kernel<T, K, 64, 2>;
+    return tpb == 128 ? stage2_kernel<T, K, 128, 0> : stage2_kernel<T, K, 64, 0>;
 }
 template <typename T>
 void (*k1_batch(int tpb))(BatchGroupDev)
@@ -655,10 +711,11 @@ void (*k1_batch(int tpb))(BatchGroupDev)
                      : (tpb == 256 ? stage01_batch_kernel<T, 256> : stage01_batch_kernel<T, 128>);
 }
 template <typename T, int K>
-void (*k2_batch(int tpb, bool pc))(BatchGroupDev)
+void (*k2_batch(int tpb, int mv))(BatchGroupDev)
 {
-    if (pc) return tpb == 128 ? stage2_batch_kernel<T, K, 128, true> : stage2_batch_kernel<T, K, 64, true>;
-    return tpb == 128 ? stage2_batch_kernel<T, K, 128> : stage2_batch_kernel<T, K, 64>;
+    if (mv == 1) return tpb == 128 ? stage2_batch_kernel<T, K, 128, 1> : stage2_batch_kernel<T, K, 64, 1>;
+    if (mv == 2) return tpb == 128 ? stage2_batch_kernel<T, K, 128, 2> : stage2_batch_kernel<T, K, 64, 2>;
+    return tpb == 128 ? stage2_batch_kernel<T, K, 128, 0> : stage2_batch_kernel<T, K, 64, 0>;
 }
 
 template <typename KernT>
@@ -672,7 +729,7 @@ int blocks_per_sm(KernT k, int tpb)
 namespace {
 // Mixture-stage CTAs that fit on one SM, by CTA size (64, 128) and K; one
 // table per translation unit (storage type), filled on first use.
-int k2_occupancy[2][2][KMAX + 1];   // [per-channel][CTA size][K]
+int k2_occupancy[3][2][KMAX + 1];   // [mixture variant][CTA size][K]
 }
 
 template <typename T, int K>
@@ -683,13 +740,13 @@ cudaError_t launch_apply_t(const ApplyArgs &a, const LaunchCfg &lc, cudaStream_t
     cudaError_t e = launch_pdl(k1_single<T>(lc.k1_tpb), g1, lc.k1_tpb, st, a);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev->e1, st);
-    const bool pc = a.dp.flags & COG_PERCHAN;
-    int &ps = k2_occupancy[pc][lc.k2_tpb == 128][K];
-    if (!ps) ps = blocks_per_sm(k2_single<T, K>(lc.k2_tpb, pc), lc.k2_tpb);
+    const int mv = mix_variant(a.dp.flags);
+    int &ps = k2_occupancy[mv][lc.k2_tpb == 128][K];
+    if (!ps) ps = blocks_per_sm(k2_single<T, K>(lc.k2_tpb, mv), lc.k2_tpb);
     const int use = lc.k2_per_sm > 0 && lc.k2_per_sm < ps ? lc.k2_per_sm : ps;
     const int64_t need = (a.dp.P + lc.k2_tpb - 1) / lc.k2_tpb;
     const int64_t g2 = min((int64_t)a.k2_grid * use, need);
-    e = launch_pdl(k2_single<T, K>(lc.k2_tpb, pc), max((int64_t)1, g2), lc.k2_tpb, st, a);
+    e = launch_pdl(k2_single<T, K>(lc.k2_tpb, mv), max((int64_t)1, g2), lc.k2_tpb, st, a);
     if (ev) cudaEventRecord(ev->e2, st);
     return e;
 }
@@ -711,13 +768,13 @@ cudaError_t launch_batch_t(const BatchGroupDev &g, const LaunchCfg &lc, uint32_t
     if (e != cudaSuccess) return e;
     cfg.gridDim = dim3(k2_ctas);
     cfg.blockDim = dim3(lc.k2_tpb);
-    return cudaLaunchKernelEx(&cfg, k2_batch<T, K>(lc.k2_tpb, g.pc != 0), g);
+    return cudaLaunchKernelEx(&cfg, k2_batch<T, K>(lc.k2_tpb, g.mv), g);
 }
 
 template <typename T, int K>
-int k2_blocks_per_sm_t(const LaunchCfg &lc, bool pc)
+int k2_blocks_per_sm_t(const LaunchCfg &lc, int mv)
 {
-    const int ps = blocks_per_sm(k2_batch<T, K>(lc.k2_tpb, pc), lc.k2_tpb);
+    const int ps = blocks_per_sm(k2_batch<T, K>(lc.k2_tpb, mv), lc.k2_tpb);
     return lc.k2_per_sm > 0 && lc.k2_per_sm < ps ? lc.k2_per_sm : ps;
 }
 

@@ -130,7 +130,7 @@ __device__ __forceinline__ void clip_stage0(const DevParams &dp, const uint4 &jl
     for (int i = 0; i < PPT; i++) {
         if (i >= nact || (skip >> i & 1u)) continue;
         const float Cm = conf_on ? cv.get(i) : 0.5f;
-        const float tau = dp.tau_fd * (0.5f + Cm);
+        const float tau = __fmul_rn(dp.tau_fd, __fadd_rn(0.5f, Cm));
         const uint32_t t = tau >= 255.f ? 255u : (uint32_t)tau;
         const bool pass = fd_on && (u4get(jl, i) >> 24) == 0 && __vcmpgtu4(ad[i], t * 0x01010101u) == 0u;
         if (!pass) need1 |= 1u << i;
@@ -194,7 +194,7 @@ __device__ CLIP_S2_INLINE void clip_s2(const ClipArgs &A, ClipWarp<T, G> &V, int
         const uint32_t qab = r.qab();
         MixPC<K> m;
         mixpc_unpack<T, K>(raw, m);
-        const MixOutPC o = mix_step_pc<K>(m, I, dp.alpha * (1.5f - Cm), dp);
+        const MixOutPC o = mix_step_pc<K>(m, I, rate_eff(dp, Cm), dp);
         int label = o.fg, st = o.fg ? COG_ST_FG : COG_ST_GMM_BG;
         if (flag && o.fg) {
             illum_response_pc<K>(m, o, dp.w_illum);
@@ -237,7 +237,7 @@ __device__ CLIP_S2_INLINE void clip_s2(const ClipArgs &A, ClipWarp<T, G> &V, int
     }
     const bool mode1 = dp.flags & COG_MODE1;
     if (mode1) mode1_write_back<T, K>(m, r);
-    const float ae = dp.alpha * (1.5f - Cm);
+    const float ae = rate_eff(dp, Cm);
     const MixOut o = mix_step<K>(m, I, ae, dp);
     int label = o.fg, st = o.fg ? COG_ST_FG : COG_ST_GMM_BG;
     if (flag && o.fg) {
@@ -266,21 +266,8 @@ __device__ CLIP_S2_INLINE void clip_s2(const ClipArgs &A, ClipWarp<T, G> &V, int
         for (int i = 0; i < S1Rec<T>::NV; i++) reinterpret_cast<uint4 *>(V.s1 + slot * SB)[i] = rn.u[i];
     }
     if (conf_on) {
-        uint32_t qmin = qk[0] < qk[1] ? qk[0] : qk[1];
-        qmin = qk[2] < qmin ? qk[2] : qmin;
-        const uint32_t qa = qab & 0xffu, qb = qab >> 8;
-        const float wa = (float)qa * R255, wb = (float)qb * R255;
-        const float wg = (float)(255u - qa - qb) * R255;
-        const float dhat = (float)D * R255;
         const float Mh = o.match >= 0 ? (o.tm < 1.f ? o.tm : 1.f) : 1.f;
-        float ci;
-        if ((int)qmin < dp.q_null) {
-            const float den = wb + wg;
-            ci = den > 0.f ? (wb * (1.f - dhat) + wg * (1.f - Mh)) / den : 0.f;
-        } else {
-            ci = wa * ((float)qmin * R255) + wb * (1.f - dhat) + wg * (1.f - Mh);
-        }
-        V.resc[slot] = (1.f - dp.eta) * Cm + dp.eta * ci;
+        V.resc[slot] = conf_stage2(dp, qk, qab, D, Cm, Mh);
     }
     V.resst[slot] = (uint8_t)st;
 }
@@ -416,29 +403,15 @@ __device__ __forceinline__ void clip_tile(const ClipArgs &A, ClipWarp<T, G> *Ws,
                 for (int i = 0; i < S1Rec<T>::NV; i++) r.u[i] = reinterpret_cast<const uint4 *>(W.s1 + slot * SB)[i];
                 surv = true;
                 if (dp.flags & COG_RGA) {
-                    float tr = 0.f;
-#pragma unroll
-                    for (int c = 0; c < 3; c++) {
-                        const float d = (float)((sv.x >> (8 * c)) & 0xffu) - r.get(c);
-                        const float tt = __fdividef(d * d, dp.lam2 * r.get(3 + c));
-                        tr = tt > tr ? tt : tr;
-                    }
+                    bool upd;
+                    const float tr = rga_step<T>(dp, r, sv.x, Cm, conf_on, upd);
                     if (tr < 1.f) {
                         surv = false;
-                        if (!(conf_on && Cm >= dp.c_halt)) {
-                            const float ae = dp.alpha * (1.5f - Cm);
-#pragma unroll
-                            for (int c = 0; c < 3; c++) {
-                                const float I = (float)((sv.x >> (8 * c)) & 0xffu);
-                                const float m = r.get(c) + ae * (I - r.get(c));
-                                const float d = I - m;
-                                r.set(c, m);
-                                r.set(3 + c, clampf((1.f - ae) * r.get(3 + c) + ae * d * d, dp.var_min, dp.var_max));
-                            }
+                        if (upd) {
 #pragma unroll
                             for (int i = 0; i < S1Rec<T>::NV; i++) reinterpret_cast<uint4 *>(W.s1 + slot * SB)[i] = r.u[i];
                         }
-                        W.resc[slot] = (1.f - dp.eta) * Cm + dp.eta * conf_stage1(r.qab(), D, tr);
+                        W.resc[slot] = conf_next(dp, Cm, conf_stage1(r.qab(), D, tr));
                         W.resst[slot] = COG_ST_RGA;
                     }
                 }
@@ -489,7 +462,7 @@ __device__ __forceinline__ void clip_tile(const ClipArgs &A, ClipWarp<T, G> *Ws,
                     label = st == COG_ST_FG;
                     u4set(jl[g], i, Iw[g][i] | (label << 24));
                     if (conf_on)
-                        cv[g].set(i, st == COG_ST_FD ? (1.f - dp.eta) * cv[g].get(i) + dp.eta : W.resc[slot]);
+                        cv[g].set(i, st == COG_ST_FD ? conf_next(dp, cv[g].get(i), 1.f) : W.resc[slot]);
                 }
                 mk |= (label ? 255u : 0u) << (8 * i);
                 sm |= st << (8 * i);

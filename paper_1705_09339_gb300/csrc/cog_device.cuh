@@ -38,6 +38,40 @@ template <> struct Store<__nv_bfloat16> {
     __device__ __forceinline__ static float unbits(uint32_t b) { return __bfloat162float(__ushort_as_bfloat16((unsigned short)b)); }
 };
 
+// Two 16-bit values in one word (low, high) to and from floats, with one
+// conversion per pair.
+template <typename T> struct Pair;
+template <> struct Pair<float> {   // unused: FP32 state is read by word
+    __device__ __forceinline__ static float2 to_f2(uint32_t) { return make_float2(0.f, 0.f); }
+    __device__ __forceinline__ static uint32_t from_f2(float, float) { return 0u; }
+};
+template <> struct Pair<__half> {
+    __device__ __forceinline__ static float2 to_f2(uint32_t w) {
+        __half2 h;
+        memcpy(&h, &w, 4);
+        return __half22float2(h);
+    }
+    __device__ __forceinline__ static uint32_t from_f2(float lo, float hi) {
+        const __half2 h = __floats2half2_rn(lo, hi);
+        uint32_t w;
+        memcpy(&w, &h, 4);
+        return w;
+    }
+};
+template <> struct Pair<__nv_bfloat16> {
+    __device__ __forceinline__ static float2 to_f2(uint32_t w) {
+        __nv_bfloat162 h;
+        memcpy(&h, &w, 4);
+        return __bfloat1622float2(h);
+    }
+    __device__ __forceinline__ static uint32_t from_f2(float lo, float hi) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+        uint32_t w;
+        memcpy(&w, &h, 4);
+        return w;
+    }
+};
+
 __device__ __forceinline__ uint32_t u4get(const uint4 &v, int i)
 {
     return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
@@ -168,6 +202,27 @@ template <typename T> struct S1Rec {
         if (Store<T>::bytes == 4) u4set(u[NV - 1], 2, q);
         else u[0].w = (u[0].w & 0xffff0000u) | q;
     }
+    // all six values at once: 16-bit storage converts pairs (m0 m1 | m2 v0
+    // | v1 v2), FP32 reads words
+    __device__ __forceinline__ void unpack(float m[3], float v[3]) const {
+        if (Store<T>::bytes == 4) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) { m[c] = get(c); v[c] = get(3 + c); }
+            return;
+        }
+        const float2 a = Pair<T>::to_f2(u[0].x), b = Pair<T>::to_f2(u[0].y), c = Pair<T>::to_f2(u[0].z);
+        m[0] = a.x; m[1] = a.y; m[2] = b.x; v[0] = b.y; v[1] = c.x; v[2] = c.y;
+    }
+    __device__ __forceinline__ void pack(const float m[3], const float v[3]) {
+        if (Store<T>::bytes == 4) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) { set(c, m[c]); set(3 + c, v[c]); }
+            return;
+        }
+        u[0].x = Pair<T>::from_f2(m[0], m[1]);
+        u[0].y = Pair<T>::from_f2(m[2], v[0]);
+        u[0].z = Pair<T>::from_f2(v[1], v[2]);
+    }
     // COG_MODE1: the mixture component this record mirrors
     __device__ __forceinline__ int top() const {
         return Store<T>::bytes == 4 ? (int)(u4get(u[NV - 1], 3) & 0xffu) : (int)((u[0].w >> 16) & 0xffu);
@@ -252,30 +307,78 @@ struct MixOut {
     float tm;    // match statistic of the matched component (pre-update)
 };
 
+// Eq. 2 arithmetic with every rounding written out, so that every kernel
+// that runs the mixture step (per frame, packed or not, clip, batch, plain
+// mixture, warm-up) rounds identically whatever the compiler would fuse.
+// A channel matches when (I - mu)^2 < lambda^2 v.
+__device__ __forceinline__ bool eq2_chan_match(float I, float mu, float v, float lam2)
+{
+    const float d = __fsub_rn(I, mu);
+    return __fmul_rn(d, d) < __fmul_rn(lam2, v);
+}
+// (I - mu)^2 / (lambda^2 v), the match statistic
+__device__ __forceinline__ float eq2_chan_stat(float I, float mu, float v, float lam2)
+{
+    const float d = __fsub_rn(I, mu);
+    return __fdividef(__fmul_rn(d, d), __fmul_rn(lam2, v));
+}
+// matched component: mu <- mu + a (I - mu), v <- (1 - a) v + a (I - mu_new)^2
+__device__ __forceinline__ void eq2_chan_update(float I, float a, float b, float &mu, float &v, const DevParams &dp)
+{
+    mu = __fmaf_rn(a, __fsub_rn(I, mu), mu);
+    const float d = __fsub_rn(I, mu);
+    v = clampf(__fmaf_rn(__fmul_rn(a, d), d, __fmul_rn(b, v)), dp.var_min, dp.var_max);
+}
+// rank key parts: w^2 and v0 + v1 + v2
+__device__ __forceinline__ float eq2_wsq(float w) { return __fmul_rn(w, w); }
+__device__ __forceinline__ float eq2_vsum(float v0, float v1, float v2) { return __fadd_rn(__fadd_rn(v0, v1), v2); }
+// j ranks before k
+__device__ __forceinline__ bool eq2_before(float wsq_j, float vs_j, float wsq_k, float vs_k, bool j_lower)
+{
+    const float x = __fmul_rn(wsq_j, vs_k), y = __fmul_rn(wsq_k, vs_j);
+    return x > y || (x == y && j_lower);
+}
+
+// The confidence-driven rate alpha (1.5 - C-) and the confidence update
+// C <- (1 - eta) C- + eta c_inst (Sec. 2, "Confidence Measure"), rounded
+// the same way everywhere.
+__device__ __forceinline__ float rate_eff(const DevParams &dp, float Cm)
+{
+    return __fmul_rn(dp.alpha, __fsub_rn(1.5f, Cm));
+}
+__device__ __forceinline__ float conf_next(const DevParams &dp, float Cm, float ci)
+{
+    return __fmaf_rn(__fsub_rn(1.f, dp.eta), Cm, __fmul_rn(dp.eta, ci));
+}
+
 // Decisions are taken in division-free form: the rank order compares
 // w_j^2 (v_k0+v_k1+v_k2) with w_k^2 (v_j0+v_j1+v_j2) (the mean's 1/3
 // cancels), and a channel matches when (I-mu)^2 < lam^2 v.  These differ
 // from the quotient forms only within rounding of the threshold.
 template <int K>
-__device__ __forceinline__ void rank_positions(const Mix<K> &m, int pos[K])
+__device__ __forceinline__ void rank_positions_k(const float wsq[K], const float vs[K], int pos[K])
 {
-    float wsq[K], vs[K];
-#pragma unroll
-    for (int k = 0; k < K; k++) {
-        wsq[k] = m.w[k] * m.w[k];
-        vs[k] = m.v[k][0] + m.v[k][1] + m.v[k][2];
-    }
 #pragma unroll
     for (int k = 0; k < K; k++) {
         int c = 0;
 #pragma unroll
         for (int j = 0; j < K; j++) {
             if (j == k) continue;
-            const float a = wsq[j] * vs[k], b = wsq[k] * vs[j];
-            c += (a > b) || (a == b && j < k);
+            c += eq2_before(wsq[j], vs[j], wsq[k], vs[k], j < k);
         }
         pos[k] = c;
     }
+}
+template <int K>
+__device__ __forceinline__ void rank_positions(const Mix<K> &m, int pos[K])
+{
+    float wsq[K], vs[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        wsq[k] = eq2_wsq(m.w[k]);
+        vs[k] = eq2_vsum(m.v[k][0], m.v[k][1], m.v[k][2]);
+    }
+    rank_positions_k<K>(wsq, vs, pos);
 }
 
 template <int K>
@@ -291,22 +394,18 @@ __device__ __forceinline__ MixOut mix_step(Mix<K> &m, const float I[3], float a,
     for (int k = 0; k < K; k++) {
         bool ok = true;
 #pragma unroll
-        for (int c = 0; c < 3; c++) {
-            const float d = I[c] - m.mu[k][c];
-            ok = ok && (d * d < dp.lam2 * m.v[k][c]);
-        }
+        for (int c = 0; c < 3; c++) ok = ok && eq2_chan_match(I[c], m.mu[k][c], m.v[k][c], dp.lam2);
         if (ok && pos[k] < mpos) { mpos = pos[k]; o.match = k; }
     }
     if (o.match >= 0) {
         float S = 0.f;
 #pragma unroll
         for (int k = 0; k < K; k++) {
-            if (pos[k] < mpos) S += m.w[k];
+            if (pos[k] < mpos) S = __fadd_rn(S, m.w[k]);
             if (k == o.match) {
 #pragma unroll
                 for (int c = 0; c < 3; c++) {
-                    const float d = I[c] - m.mu[k][c];
-                    const float t = __fdividef(d * d, dp.lam2 * m.v[k][c]);
+                    const float t = eq2_chan_stat(I[c], m.mu[k][c], m.v[k][c], dp.lam2);
                     o.tm = t > o.tm ? t : o.tm;
                 }
             }
@@ -315,18 +414,14 @@ __device__ __forceinline__ MixOut mix_step(Mix<K> &m, const float I[3], float a,
     } else {
         o.fg = 1;
     }
-    const float b = 1.f - a;
+    const float b = __fsub_rn(1.f, a);
     if (o.match >= 0) {
 #pragma unroll
         for (int k = 0; k < K; k++) {
-            m.w[k] = b * m.w[k] + (k == o.match ? a : 0.f);
+            m.w[k] = __fmaf_rn(b, m.w[k], k == o.match ? a : 0.f);
             if (k == o.match) {
 #pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    m.mu[k][c] = m.mu[k][c] + a * (I[c] - m.mu[k][c]);
-                    const float d = I[c] - m.mu[k][c];
-                    m.v[k][c] = clampf(b * m.v[k][c] + a * d * d, dp.var_min, dp.var_max);
-                }
+                for (int c = 0; c < 3; c++) eq2_chan_update(I[c], a, b, m.mu[k][c], m.v[k][c], dp);
             }
         }
         o.tgt = o.match;
@@ -334,7 +429,7 @@ __device__ __forceinline__ MixOut mix_step(Mix<K> &m, const float I[3], float a,
         o.tgt = 0;
 #pragma unroll
         for (int k = 0; k < K; k++) {
-            m.w[k] = b * m.w[k];
+            m.w[k] = __fmul_rn(b, m.w[k]);
             if (pos[k] == K - 1) {
                 o.tgt = k;
                 m.w[k] = dp.w_init;
@@ -345,10 +440,138 @@ __device__ __forceinline__ MixOut mix_step(Mix<K> &m, const float I[3], float a,
     }
     float sum = 0.f;
 #pragma unroll
-    for (int k = 0; k < K; k++) sum += m.w[k];
-    const float inv = 1.f / sum;
+    for (int k = 0; k < K; k++) sum = __fadd_rn(sum, m.w[k]);
+    const float inv = __frcp_rn(sum);
 #pragma unroll
-    for (int k = 0; k < K; k++) m.w[k] = m.w[k] * inv;
+    for (int k = 0; k < K; k++) m.w[k] = __fmul_rn(m.w[k], inv);
+    return o;
+}
+
+// The same step on a record kept in its stored form (K x 7 values of T in
+// 16-byte words, as Rec<T, K>): each value is converted when it is used and
+// written back when it changes, so the step needs about half the registers
+// of an unpacked mixture.  The arithmetic and its order are those of
+// mix_step, so both give the same record.  tgt_mv receives the updated (or
+// restarted) target component's means and variances.
+template <typename T, int K>
+__device__ __forceinline__ void rec_put(uint4 *u, int e, float x)
+{
+    const uint32_t b = Store<T>::bits(x);
+    if (Store<T>::bytes == 4) {
+        u4set(u[e >> 2], e & 3, b);
+    } else {
+        uint32_t w = u4get(u[e >> 3], (e >> 1) & 3);
+        w = (e & 1) ? ((w & 0xffffu) | (b << 16)) : ((w & 0xffff0000u) | b);
+        u4set(u[e >> 3], (e >> 1) & 3, w);
+    }
+}
+
+template <typename T, int K>
+__device__ __forceinline__ MixOut mix_step_packed(uint4 *u, const float I[3], float a, const DevParams &dp,
+                                                  bool illum, float tgt_mv[6])
+{
+    int pos[K];
+    uint32_t okb = 0;
+    {
+        float wsq[K], vs[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            wsq[k] = eq2_wsq(rec_elem<T, K>(u, 7 * k));
+            const float v0 = rec_elem<T, K>(u, 7 * k + 4), v1 = rec_elem<T, K>(u, 7 * k + 5),
+                        v2 = rec_elem<T, K>(u, 7 * k + 6);
+            vs[k] = eq2_vsum(v0, v1, v2);
+            const bool ok = eq2_chan_match(I[0], rec_elem<T, K>(u, 7 * k + 1), v0, dp.lam2) &&
+                            eq2_chan_match(I[1], rec_elem<T, K>(u, 7 * k + 2), v1, dp.lam2) &&
+                            eq2_chan_match(I[2], rec_elem<T, K>(u, 7 * k + 3), v2, dp.lam2);
+            okb |= (uint32_t)ok << k;
+        }
+        rank_positions_k<K>(wsq, vs, pos);
+    }
+    MixOut o;
+    o.match = -1;
+    o.tm = 0.f;
+    int mpos = K;
+#pragma unroll
+    for (int k = 0; k < K; k++)
+        if ((okb >> k & 1u) && pos[k] < mpos) { mpos = pos[k]; o.match = k; }
+    const int tgt = o.match >= 0 ? o.match : 0;
+    int tk = tgt;
+    if (o.match < 0) {
+#pragma unroll
+        for (int k = 0; k < K; k++) if (pos[k] == K - 1) tk = k;
+    }
+    o.tgt = tk;
+    // the target component's means and variances (before the update)
+    float mu[3] = {0.f, 0.f, 0.f}, v[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        if (k == tk) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) { mu[c] = rec_elem<T, K>(u, 7 * k + 1 + c); v[c] = rec_elem<T, K>(u, 7 * k + 4 + c); }
+        }
+    }
+    const float b = __fsub_rn(1.f, a);
+    float w[K];
+    if (o.match >= 0) {
+        float S = 0.f;
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const float wk = rec_elem<T, K>(u, 7 * k);
+            if (pos[k] < mpos) S = __fadd_rn(S, wk);
+            w[k] = __fmaf_rn(b, wk, k == o.match ? a : 0.f);
+        }
+        o.fg = !(S <= dp.T_bg);
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const float t = eq2_chan_stat(I[c], mu[c], v[c], dp.lam2);
+            o.tm = t > o.tm ? t : o.tm;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; c++) eq2_chan_update(I[c], a, b, mu[c], v[c], dp);
+    } else {
+        // the lowest-ranked component restarts (every component at the last
+        // rank position, as mix_step, should rounding ever tie two there)
+        o.fg = 1;
+        bool rep = false;
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const bool r = pos[k] == K - 1;
+            w[k] = r ? dp.w_init : __fmul_rn(b, rec_elem<T, K>(u, 7 * k));
+            rep = rep || (k == tk && r);
+        }
+        if (rep) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) { mu[c] = I[c]; v[c] = dp.var_init; }
+        }
+    }
+    float sum = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; k++) sum = __fadd_rn(sum, w[k]);
+    const float inv = __frcp_rn(sum);
+#pragma unroll
+    for (int k = 0; k < K; k++) w[k] = __fmul_rn(w[k], inv);
+    if (illum && o.fg) {
+        // the illumination response (illum_response) on the weights before
+        // they are rounded to the stored type, as the unpacked path does
+        float so = 0.f;
+#pragma unroll
+        for (int k = 0; k < K; k++) if (k != tk) so = __fadd_rn(so, w[k]);
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            if (so > 0.f) w[k] = (k == tk) ? dp.w_illum : __fdiv_rn(__fmul_rn(w[k], 1.f - dp.w_illum), so);
+            else if (k == tk) w[k] = 1.f;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        rec_put<T, K>(u, 7 * k, w[k]);
+        if (k == tk || (o.match < 0 && pos[k] == K - 1)) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) { rec_put<T, K>(u, 7 * k + 1 + c, mu[c]); rec_put<T, K>(u, 7 * k + 4 + c, v[c]); }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; c++) { tgt_mv[c] = mu[c]; tgt_mv[3 + c] = v[c]; }
     return o;
 }
 
@@ -421,56 +644,46 @@ __device__ __forceinline__ void mix_step_channel(float (&w)[K], float (&mu)[K], 
     int pos[K];
     float wsq[K];
 #pragma unroll
-    for (int k = 0; k < K; k++) wsq[k] = w[k] * w[k];
+    for (int k = 0; k < K; k++) wsq[k] = eq2_wsq(w[k]);
 #pragma unroll
     for (int k = 0; k < K; k++) {
         int cnt = 0;
 #pragma unroll
         for (int j = 0; j < K; j++) {
             if (j == k) continue;
-            const float x = wsq[j] * v[k], y = wsq[k] * v[j];
-            cnt += (x > y) || (x == y && j < k);
+            cnt += eq2_before(wsq[j], v[j], wsq[k], v[k], j < k);
         }
         pos[k] = cnt;
     }
     int match = -1, mpos = K;
 #pragma unroll
-    for (int k = 0; k < K; k++) {
-        const float d = I - mu[k];
-        if (d * d < dp.lam2 * v[k] && pos[k] < mpos) { mpos = pos[k]; match = k; }
-    }
+    for (int k = 0; k < K; k++)
+        if (eq2_chan_match(I, mu[k], v[k], dp.lam2) && pos[k] < mpos) { mpos = pos[k]; match = k; }
     float tm = 0.f;
     fg = 1;
     if (match >= 0) {
         float S = 0.f;
 #pragma unroll
         for (int k = 0; k < K; k++) {
-            if (pos[k] < mpos) S += w[k];
-            if (k == match) {
-                const float d = I - mu[k];
-                tm = __fdividef(d * d, dp.lam2 * v[k]);
-            }
+            if (pos[k] < mpos) S = __fadd_rn(S, w[k]);
+            if (k == match) tm = eq2_chan_stat(I, mu[k], v[k], dp.lam2);
         }
         fg = !(S <= dp.T_bg);
     }
     M = match >= 0 ? (tm < 1.f ? tm : 1.f) : 1.f;
-    const float b = 1.f - a;
+    const float b = __fsub_rn(1.f, a);
     if (match >= 0) {
 #pragma unroll
         for (int k = 0; k < K; k++) {
-            w[k] = b * w[k] + (k == match ? a : 0.f);
-            if (k == match) {
-                mu[k] = mu[k] + a * (I - mu[k]);
-                const float d = I - mu[k];
-                v[k] = clampf(b * v[k] + a * d * d, dp.var_min, dp.var_max);
-            }
+            w[k] = __fmaf_rn(b, w[k], k == match ? a : 0.f);
+            if (k == match) eq2_chan_update(I, a, b, mu[k], v[k], dp);
         }
         tgt = match;
     } else {
         tgt = 0;
 #pragma unroll
         for (int k = 0; k < K; k++) {
-            w[k] = b * w[k];
+            w[k] = __fmul_rn(b, w[k]);
             if (pos[k] == K - 1) {
                 tgt = k;
                 w[k] = dp.w_init;
@@ -481,10 +694,10 @@ __device__ __forceinline__ void mix_step_channel(float (&w)[K], float (&mu)[K], 
     }
     float sum = 0.f;
 #pragma unroll
-    for (int k = 0; k < K; k++) sum += w[k];
-    const float inv = 1.f / sum;
+    for (int k = 0; k < K; k++) sum = __fadd_rn(sum, w[k]);
+    const float inv = __frcp_rn(sum);
 #pragma unroll
-    for (int k = 0; k < K; k++) w[k] = w[k] * inv;
+    for (int k = 0; k < K; k++) w[k] = __fmul_rn(w[k], inv);
 }
 
 template <int K>
@@ -513,11 +726,11 @@ __device__ __forceinline__ void illum_response_pc(MixPC<K> &m, const MixOutPC &o
         if (!o.fg_c[c]) continue;
         float so = 0.f;
 #pragma unroll
-        for (int k = 0; k < K; k++) if (k != o.tgt[c]) so += m.w[c][k];
+        for (int k = 0; k < K; k++) if (k != o.tgt[c]) so = __fadd_rn(so, m.w[c][k]);
         if (so > 0.f) {
 #pragma unroll
             for (int k = 0; k < K; k++)
-                m.w[c][k] = (k == o.tgt[c]) ? w_illum : m.w[c][k] * (1.f - w_illum) / so;
+                m.w[c][k] = (k == o.tgt[c]) ? w_illum : __fdiv_rn(__fmul_rn(m.w[c][k], 1.f - w_illum), so);
         } else {
 #pragma unroll
             for (int k = 0; k < K; k++) if (k == o.tgt[c]) m.w[c][k] = 1.f;
@@ -581,11 +794,11 @@ __device__ __forceinline__ void illum_response(Mix<K> &m, int tgt, float w_illum
 {
     float so = 0.f;
 #pragma unroll
-    for (int k = 0; k < K; k++) if (k != tgt) so += m.w[k];
+    for (int k = 0; k < K; k++) if (k != tgt) so = __fadd_rn(so, m.w[k]);
     if (so > 0.f) {
 #pragma unroll
         for (int k = 0; k < K; k++)
-            m.w[k] = (k == tgt) ? w_illum : m.w[k] * (1.f - w_illum) / so;
+            m.w[k] = (k == tgt) ? w_illum : __fdiv_rn(__fmul_rn(m.w[k], 1.f - w_illum), so);
     } else {
 #pragma unroll
         for (int k = 0; k < K; k++) if (k == tgt) m.w[k] = 1.f;

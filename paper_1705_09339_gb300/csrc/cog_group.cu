@@ -12,15 +12,16 @@
 //              centroids at mean - sd, mean, mean + sd (sd = 0 for a
 //              constant code), an empty cluster keeping its centroid, ties
 //              to the lower cluster, until no label changes (at most
-//              GROUP_MAX_IT steps); the distance is evaluated in FP32;
+//              GROUP_MAX_IT steps, or the caller's limit); the distance is
+//              evaluated in FP32, so a pixel whose two nearest centroids
+//              are within FP32 rounding of a tie may go either way;
 //   Eq. 3      core pixel: both codes strictly within the cluster's mean
 //              +- standard deviation;
 //   step 6     per cluster, the mean over its core of the trained state's
 //              dominant mode (weight, means, mean variance).
 // The clustering works on integer sums (exact with atomics in any order),
 // and every floating-point operation is an explicitly rounded intrinsic, so
-// the labels are the same as any implementation of the same sequence of
-// correctly rounded operations on the same codes.
+// the result does not depend on the launch shape or the atomics' order.
 #include <cmath>
 
 #include "cog_device.cuh"
@@ -128,6 +129,30 @@ __global__ void __launch_bounds__(128) group_features_kernel(const DevParams dp,
     }
 }
 
+// Sums over all pixels of caller-given codes and their squares (the
+// features kernel accumulates the same sums as it writes its codes).
+__global__ void __launch_bounds__(GROUP_TPB) group_sums_kernel(int64_t P, const uint16_t *code_v, const uint16_t *code_w,
+                                                               GroupCtl *G)
+{
+    unsigned long long a[4] = {0, 0, 0, 0};
+    for (int64_t p = (int64_t)blockIdx.x * GROUP_TPB + threadIdx.x; p < P; p += (int64_t)gridDim.x * GROUP_TPB) {
+        const unsigned long long qv = code_v[p], qw = code_w[p];
+        a[0] += qv;
+        a[1] += qw;
+        a[2] += qv * qv;
+        a[3] += qw * qw;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) a[i] += __shfl_xor_sync(0xffffffffu, a[i], off);
+    if ((threadIdx.x & 31) == 0) {
+        if (a[0]) atomicAdd(&G->g1[0], a[0]);
+        if (a[1]) atomicAdd(&G->g1[1], a[1]);
+        if (a[2]) atomicAdd(&G->g2[0], a[2]);
+        if (a[3]) atomicAdd(&G->g2[1], a[3]);
+    }
+}
 
 // ------------------------------------------------------------------ K-means
 // Feature scales from the sums over all pixels: sd0 the spread (0 for a
@@ -264,13 +289,14 @@ __global__ void __launch_bounds__(GROUP_TPB) group_assign_kernel(int64_t P, cons
 // component's weight from the mixture record -- is summed per cluster.
 template <typename T, int K>
 __global__ void __launch_bounds__(GROUP_TPB) group_core_kernel(const StatePtrs s, int64_t P, const uint16_t *code_v,
-                                                               const uint16_t *code_w, uint8_t *labels, GroupCtl *G)
+                                                               const uint16_t *code_w, uint8_t *labels, GroupCtl *G,
+                                                               int max_steps)
 {
     __shared__ double mu_s[3][2], sg_s[3][2];
     __shared__ double par_s[3][5];
     __shared__ unsigned long long nc_s[3];
     const int tid = threadIdx.x;
-    const GroupBuf &fin = G->buf[GROUP_MAX_IT % 3];
+    const GroupBuf &fin = G->buf[max_steps % 3];
     if (tid == 0) {
         for (int j = 0; j < 3; j++)
             for (int f = 0; f < 2; f++) {
@@ -284,7 +310,7 @@ __global__ void __launch_bounds__(GROUP_TPB) group_core_kernel(const StatePtrs s
                 mu_s[j][f] = m;
                 sg_s[j][f] = sg;
             }
-        if (blockIdx.x == 0 && G->conv_iter == 0 && fin.changed == 0) G->conv_iter = GROUP_MAX_IT;
+        if (blockIdx.x == 0 && max_steps > 0 && G->conv_iter == 0 && fin.changed == 0) G->conv_iter = max_steps;
     }
     if (tid < 15) par_s[tid / 5][tid % 5] = 0.0;
     if (tid < 3) nc_s[tid] = 0;
@@ -318,58 +344,62 @@ __global__ void __launch_bounds__(GROUP_TPB) group_core_kernel(const StatePtrs s
 
 template <typename T, int K>
 cudaError_t launch_group_t(const DevParams &dp, const StatePtrs &s, const uint8_t *frames, int N, uint16_t *codes,
-                           uint8_t *labels, int n_sm, cudaStream_t st)
+                           uint8_t *labels, int max_steps, int n_sm, cudaStream_t st)
 {
     GroupCtl *G = reinterpret_cast<GroupCtl *>(s.ctl + CTL_GROUP_WORD);
     cudaError_t e = cudaMemsetAsync(G, 0, sizeof(GroupCtl), st);
     if (e != cudaSuccess) return e;
     uint16_t *cv = codes, *cw = codes + dp.P;
-    group_features_kernel<K><<<(unsigned)((dp.P + 127) / 128), 128, 0, st>>>(dp, frames, N, cv, cw, G);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int64_t need = (dp.P + GROUP_TPB - 1) / GROUP_TPB;
     const unsigned grid = (unsigned)min(need, (int64_t)n_sm * 8);
-    for (int it = 0; it <= GROUP_MAX_IT; it++) {
+    if (frames) group_features_kernel<K><<<(unsigned)((dp.P + 127) / 128), 128, 0, st>>>(dp, frames, N, cv, cw, G);
+    else group_sums_kernel<<<grid, GROUP_TPB, 0, st>>>(dp.P, cv, cw, G);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    for (int it = 0; it <= max_steps; it++) {
         group_assign_kernel<<<grid, GROUP_TPB, 0, st>>>(dp.P, cv, cw, labels, G, it);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    group_core_kernel<T, K><<<grid, GROUP_TPB, 0, st>>>(s, dp.P, cv, cw, labels, G);
+    group_core_kernel<T, K><<<grid, GROUP_TPB, 0, st>>>(s, dp.P, cv, cw, labels, G, max_steps);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_group_k(int K, const DevParams &dp, const StatePtrs &s, const uint8_t *frames, int N,
-                           uint16_t *codes, uint8_t *labels, int n_sm, cudaStream_t st)
+                           uint16_t *codes, uint8_t *labels, int max_steps, int n_sm, cudaStream_t st)
 {
     switch (K) {
-    case 1: return launch_group_t<T, 1>(dp, s, frames, N, codes, labels, n_sm, st);
-    case 2: return launch_group_t<T, 2>(dp, s, frames, N, codes, labels, n_sm, st);
-    case 3: return launch_group_t<T, 3>(dp, s, frames, N, codes, labels, n_sm, st);
-    case 4: return launch_group_t<T, 4>(dp, s, frames, N, codes, labels, n_sm, st);
-    case 5: return launch_group_t<T, 5>(dp, s, frames, N, codes, labels, n_sm, st);
-    case 6: return launch_group_t<T, 6>(dp, s, frames, N, codes, labels, n_sm, st);
-    case 7: return launch_group_t<T, 7>(dp, s, frames, N, codes, labels, n_sm, st);
-    default: return launch_group_t<T, 8>(dp, s, frames, N, codes, labels, n_sm, st);
+    case 1: return launch_group_t<T, 1>(dp, s, frames, N, codes, labels, max_steps, n_sm, st);
+    case 2: return launch_group_t<T, 2>(dp, s, frames, N, codes, labels, max_steps, n_sm, st);
+    case 3: return launch_group_t<T, 3>(dp, s, frames, N, codes, labels, max_steps, n_sm, st);
+    case 4: return launch_group_t<T, 4>(dp, s, frames, N, codes, labels, max_steps, n_sm, st);
+    case 5: return launch_group_t<T, 5>(dp, s, frames, N, codes, labels, max_steps, n_sm, st);
+    case 6: return launch_group_t<T, 6>(dp, s, frames, N, codes, labels, max_steps, n_sm, st);
+    case 7: return launch_group_t<T, 7>(dp, s, frames, N, codes, labels, max_steps, n_sm, st);
+    default: return launch_group_t<T, 8>(dp, s, frames, N, codes, labels, max_steps, n_sm, st);
     }
 }
 
+// frames == nullptr: cluster the caller's codes (no feature pass).
 cudaError_t launch_group(int dtype, int K, const DevParams &dp, const StatePtrs &s, const uint8_t *frames, int N,
-                         uint16_t *codes, uint8_t *labels, int n_sm, cudaStream_t st)
+                         uint16_t *codes, uint8_t *labels, int max_steps, int n_sm, cudaStream_t st)
 {
-    if (dtype == COG_F32) return launch_group_k<float>(K, dp, s, frames, N, codes, labels, n_sm, st);
-    if (dtype == COG_F16) return launch_group_k<__half>(K, dp, s, frames, N, codes, labels, n_sm, st);
-    return launch_group_k<__nv_bfloat16>(K, dp, s, frames, N, codes, labels, n_sm, st);
+    if (dtype == COG_F32) return launch_group_k<float>(K, dp, s, frames, N, codes, labels, max_steps, n_sm, st);
+    if (dtype == COG_F16) return launch_group_k<__half>(K, dp, s, frames, N, codes, labels, max_steps, n_sm, st);
+    return launch_group_k<__nv_bfloat16>(K, dp, s, frames, N, codes, labels, max_steps, n_sm, st);
 }
+
+int group_max_steps() { return GROUP_MAX_IT; }
 
 // The grouping result as the host reads it back.
 size_t group_ctl_offset() { return (size_t)CTL_GROUP_WORD * 4; }
 size_t group_ctl_bytes() { return sizeof(GroupCtl); }
-void group_ctl_decode(const void *raw, cog_group_stats *out)
+void group_ctl_decode(const void *raw, int max_steps, cog_group_stats *out)
 {
     const GroupCtl *G = static_cast<const GroupCtl *>(raw);
-    const GroupBuf &fin = G->buf[GROUP_MAX_IT % 3];
+    const GroupBuf &fin = G->buf[max_steps % 3];
     *out = cog_group_stats{};
     out->converged = G->conv_iter != 0;
-    out->iterations = G->conv_iter ? (int32_t)G->conv_iter : GROUP_MAX_IT;
+    out->iterations = G->conv_iter ? (int32_t)G->conv_iter : max_steps;
     for (int j = 0; j < 3; j++) {
         out->n[j] = (int64_t)fin.n[j];
         out->n_core[j] = (int64_t)G->n_core[j];

@@ -39,17 +39,17 @@ cudaError_t COG_CAT(launch_batch_, COG_SUFFIX)(int K, const BatchGroupDev &g, co
 #undef CALL_B
 }
 
-int COG_CAT(k2_blocks_per_sm_, COG_SUFFIX)(int K, const LaunchCfg &lc, bool pc)
+int COG_CAT(k2_blocks_per_sm_, COG_SUFFIX)(int K, const LaunchCfg &lc, int mv)
 {
     switch (K) {
-    case 1: return k2_blocks_per_sm_t<COG_T, 1>(lc, pc);
-    case 2: return k2_blocks_per_sm_t<COG_T, 2>(lc, pc);
-    case 3: return k2_blocks_per_sm_t<COG_T, 3>(lc, pc);
-    case 4: return k2_blocks_per_sm_t<COG_T, 4>(lc, pc);
-    case 5: return k2_blocks_per_sm_t<COG_T, 5>(lc, pc);
-    case 6: return k2_blocks_per_sm_t<COG_T, 6>(lc, pc);
-    case 7: return k2_blocks_per_sm_t<COG_T, 7>(lc, pc);
-    default: return k2_blocks_per_sm_t<COG_T, 8>(lc, pc);
+    case 1: return k2_blocks_per_sm_t<COG_T, 1>(lc, mv);
+    case 2: return k2_blocks_per_sm_t<COG_T, 2>(lc, mv);
+    case 3: return k2_blocks_per_sm_t<COG_T, 3>(lc, mv);
+    case 4: return k2_blocks_per_sm_t<COG_T, 4>(lc, mv);
+    case 5: return k2_blocks_per_sm_t<COG_T, 5>(lc, mv);
+    case 6: return k2_blocks_per_sm_t<COG_T, 6>(lc, mv);
+    case 7: return k2_blocks_per_sm_t<COG_T, 7>(lc, mv);
+    default: return k2_blocks_per_sm_t<COG_T, 8>(lc, mv);
     }
 }
 

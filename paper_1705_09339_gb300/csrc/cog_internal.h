@@ -114,8 +114,16 @@ struct BatchGroupDev {
     const uint32_t *k2_pre;  // [n + 1] prefix of the mixture-stage CTAs given to the
                              //         active streams (in proportion to their pixels)
     int n;
-    int pc;                  // 1: the group's streams use per-channel mixtures
+    int mv;                  // mixture variant of the group's streams: 0 shared
+                             // weights, 1 per-channel (COG_PERCHAN), 2 stage 1 as
+                             // the rank-1 mode (COG_MODE1)
 };
+
+// The mixture variant a stream's flags select (BatchGroupDev::mv).
+__host__ __device__ inline int mix_variant(unsigned flags)
+{
+    return (flags & COG_PERCHAN) ? 1 : ((flags & COG_MODE1) ? 2 : 0);
+}
 
 // Launch shape of the two cascade kernels.
 struct LaunchCfg {
