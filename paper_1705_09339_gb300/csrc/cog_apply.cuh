@@ -17,15 +17,16 @@
 //     consecutive pixels and issues all its stage-0 loads at once as
 //     128/64-bit vectors (previous frame + label and confidence planes,
 //     frame bytes), and writes its pixels' outputs at once.  Pixels past
-//     stage 0 are compacted per warp and fetch their 16-byte stage-1
+//     stage 0 are compacted per CTA and fetch their 16-byte stage-1
 //     record.  Pixels past stage 1 go to the frame's survivor queue, one
 //     atomic per warp pass (16 bytes per survivor carrying everything the
 //     next stage needs).
 //   stage2_kernel: a persistent grid walks the queue; each survivor fetches
 //     its mixture record (one aligned block) and its three prior bytes in
-//     one round trip, runs Eq. 2, and writes its record, label, mask and
-//     confidence back.  The mixture's register footprint and divergence no
-//     longer throttle the streaming stages.
+//     one round trip, runs Eq. 2 on the record in its stored form, and
+//     writes its record, label, mask and confidence back.  The mixture's
+//     register footprint and divergence no longer throttle the streaming
+//     stages.
 #pragma once
 
 #include "cog_device.cuh"
@@ -436,7 +437,8 @@ __device__ __forceinline__ void s2_load(const ApplyArgs &A, int64_t qi, S2In<T, 
 }
 
 // Confidence of a pixel decided at stage 2 (Sec. 2, "Confidence Measure"):
-// prior term from the three prior bytes unless the prior is nullified.
+// prior term from the smallest of the three prior bytes, unless the prior
+// is nullified (that minimum below q_null).
 __device__ __forceinline__ float conf_stage2(const DevParams &dp, const uint32_t qk[3], uint32_t qab, int D, float Cm,
                                              float Mh)
 {

@@ -42,10 +42,12 @@ def built():
     import __graft_entry__
     __graft_entry__.build()
     yield
-    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    os.makedirs(os.path.join(root, "gpurun_out"), exist_ok=True)
-    with open(os.path.join(root, "gpurun_out", "accuracy_report.json"), "w") as f:
-        json.dump(REPORT, f, indent=1)
+    # the per-config report goes where COG_REPORT_DIR points (nowhere if unset)
+    out = os.environ.get("COG_REPORT_DIR")
+    if out:
+        os.makedirs(out, exist_ok=True)
+        with open(os.path.join(out, "accuracy_report.json"), "w") as f:
+            json.dump(REPORT, f, indent=1)
 
 
 def _misclass(masks, gt):

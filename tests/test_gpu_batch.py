@@ -94,3 +94,67 @@ def test_batch_argument_errors(cog):
         cog.cog_batch_create([c], torch.cuda.Stream().cuda_stream)
     assert e.value.status == cog.COG_ERR_STATE
     cog.cog_destroy(c)
+
+
+def test_batch_matches_oracle_with_inactive_steps(cog):
+    # four small streams of mixed size, K = 3 and 5, FP32 state, through
+    # cog_batch_apply_active with each stream idle on some steps; every
+    # stream is compared with its own FP64 oracle run over the frames it
+    # actually received: masks identical on every pixel with no decision
+    # near a threshold so far, state within 1e-4 relative there
+    specs = [(97, 61, 3), (160, 120, 5), (33, 7, 5), (200, 100, 3)]
+    NT, NF = 40, 30
+    s = torch.cuda.Stream()      # a graph cannot be captured on the legacy default stream
+    with torch.cuda.stream(s):
+        _batch_vs_oracle(cog, specs, NT, NF, s)
+
+
+def _batch_vs_oracle(cog, specs, NT, NF, s):
+    from cog_harness import GpuRun, oracle_run, oracle_state, params, state_errors
+    from cogsynth import Scene
+    runs = []
+    for i, (w, h, k) in enumerate(specs):
+        sc = Scene(w, h, 90 + i, kind="dynamic", n_train=NT, fg_frac=0.05, switch_at=12 + 3 * i)
+        fr, _ = sc.frames(0, NT + NF)
+        d = params(w, h, k)
+        g = GpuRun(d, "f32")
+        g.train(fr[:NT])
+        runs.append((w, h, k, fr, d, g))
+    b = cog.cog_batch_create([r[5].ctx for r in runs], s.cuda_stream)
+    used = [0] * len(specs)
+    got = [[] for _ in specs]
+    for t in range(NF):
+        active = [int((t + i) % 4 != 3 or t < 2) for i in range(len(specs))]
+        frames, masks = [], []
+        for i, (w, h, k, fr, d, g) in enumerate(runs):
+            if active[i]:
+                frames.append(torch.from_numpy(fr[NT + used[i]].reshape(h, w, 3)).cuda())
+                masks.append(torch.empty((h, w), dtype=torch.uint8, device="cuda"))
+            else:
+                frames.append(None)
+                masks.append(None)
+        cog.cog_batch_apply_active(b, frames, masks, active)
+        cog.cog_batch_sync(b)
+        for i in range(len(specs)):
+            if active[i]:
+                got[i].append(masks[i].cpu().numpy().ravel())
+                used[i] += 1
+    cog.cog_batch_destroy(b)
+    for i, (w, h, k, fr, d, g) in enumerate(runs):
+        assert 0 < used[i] < NF
+        gs = g.state()
+        g.close()
+        o = oracle_run(d)
+        near0 = o.train(fr[:NT], want_near=True)
+        ever = near0 != 0
+        unexplained = 0
+        for j in range(used[i]):
+            m, _, near, _ = o.apply(fr[NT + j])
+            ever |= near != 0
+            unexplained += int(((got[i][j] != m) & ~ever).sum())
+        assert unexplained == 0, (i, unexplained)
+        e = state_errors(gs, oracle_state(o), ~ever)
+        for key in ("w", "mu", "var", "rga_m", "rga_v", "conf"):
+            assert e[key] <= 1e-4, (i, key, e[key])
+        for key in ("label", "prev", "qa", "qb"):
+            assert e[key] == 0, (i, key)

@@ -444,3 +444,41 @@ def test_plain_gmm_refused_with_perchan():
         cog.cog_apply_plain_gmm(g.ctx, f, m)
     assert e.value.status == cog.COG_ERR_INVALID_ARG
     g.close()
+
+
+def test_vga_full_workload_fp32_matches_oracle():
+    # the whole 640x480 dynamic-background workload as specified: 500
+    # training frames, 1000 test frames with the +60 light switch at test
+    # frame 600, K=5, FP32 state, free-running against the FP64 oracle
+    # (frames from the generator's GPU twin, bit-identical to its CPU side)
+    from cogsynth import workload
+    from cogsynth.gpu import GpuScene
+    wl = workload("vga_dynamic", fg_frac=0.03)
+    sc, K, NT, NF = wl["scene"], wl["K"], wl["n_train"], wl["n_test"]
+    W, H = sc.width, sc.height
+    fr = GpuScene(sc).render(0, NT + NF).cpu().numpy().reshape(NT + NF, W * H, 3)
+    d = params(W, H, K)
+    g = GpuRun(d, "f32")
+    g.train(fr[:NT])
+    gm, gsm, gst = g.apply(fr[NT:])
+    gs = g.state()
+    g.close()
+    o = oracle_run(d)
+    ever = o.train(fr[:NT], want_near=True) != 0
+    unexplained = agree = 0
+    flags_o = []
+    for t in range(NF):
+        m, s, near, st = o.apply(fr[NT + t])
+        ever |= near != 0
+        unexplained += int((((gm[t] != m) | (gsm[t] != s)) & ~ever).sum())
+        agree += int((gm[t] == m).sum())
+        flags_o.append(st["illum_flag"])
+    assert unexplained == 0
+    assert agree / gm.size >= 0.9999
+    assert [s["illum_flag"] for s in gst] == flags_o
+    assert flags_o[601] == 1
+    e = state_errors(gs, oracle_state(o), ~ever)
+    for k in ("w", "mu", "var", "rga_m", "rga_v", "conf"):
+        assert e[k] <= TOL, (k, e[k])
+    for k in ("label", "prev", "qa", "qb"):
+        assert e[k] == 0, k

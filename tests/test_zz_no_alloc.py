@@ -65,3 +65,37 @@ def test_noalloc_rejects_frames_beyond_its_static_limit(cog):
     assert e.value.status == cog.COG_ERR_INVALID_ARG
     assert "2073600" in str(e.value)
     cog.cog_destroy(ctx)
+
+
+def test_noalloc_allocates_no_device_memory(cog):
+    # A caller that cannot allocate must be able to rely on this: after one
+    # warm-up call (which looks the static array's device address up once
+    # per device and may load the library's kernels), further calls on a
+    # fresh context leave the device's free memory unchanged.  The check can
+    # see an allocation: the allocating entry point's first call on the same
+    # context creates its two staging buffers, and free memory drops.
+    W, H = 1920, 1080
+    p = cog.cog_default_params(W, H, 3, state_dtype="f16")
+    stream = torch.cuda.current_stream().cuda_stream
+    zeros = torch.zeros((4, H, W, 3), dtype=torch.uint8, device="cuda")
+    f = np.full(W * H * 3, 60, np.uint8)
+    m = np.zeros(W * H, np.uint8)
+    warm = cog.cog_create(p, stream)
+    cog.cog_train_prior(warm, zeros, 4)
+    cog.cog_apply_host_noalloc(warm, f, m)
+    ctx = cog.cog_create(p, stream)
+    cog.cog_train_prior(ctx, zeros, 4)
+    cog.cog_sync(ctx)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        cog.cog_apply_host_noalloc(ctx, f, m)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    cog.cog_apply_host(ctx, f, m)
+    torch.cuda.synchronize()
+    free2, _ = torch.cuda.mem_get_info()
+    assert free2 < free1, (free1, free2)
+    cog.cog_destroy(warm)
+    cog.cog_destroy(ctx)
