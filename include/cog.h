@@ -214,10 +214,11 @@ cog_status cog_clip_runs(cog_ctx *ctx, int32_t *runs);
  *     (height x width x 3 bytes; page-locked for overlap) and the host
  *     buffer that receives its mask; both must stay valid until the frame
  *     is done (cog_server_drain).  Thread-safe; returns at once.
- *   The worker takes, for every stream with a frame waiting and a free
- *   slot, the oldest frame; uploads them; runs one batched step over those
- *   streams only; downloads their masks.  Frames submitted meanwhile join
- *   the next step, whose uploads overlap the running one.
+ *   The worker takes, while fewer than three steps are on the GPU, for
+ *   every stream with a frame waiting and a free slot, the oldest frame;
+ *   uploads them; runs one batched step over those streams only; downloads
+ *   their masks.  Frames submitted meanwhile join the next step, whose
+ *   uploads overlap the running one.
  *   cog_server_add: a further trained context joins the running server as
  *     stream *stream_out (the next index).  The worker takes it between
  *     steps: once no step is on the GPU (at most 30 s) it rebuilds the batch
@@ -229,13 +230,21 @@ cog_status cog_clip_runs(cog_ctx *ctx, int32_t *runs);
  *   cog_server_drain: waits up to timeout_ms until every submitted frame is
  *     done; COG_ERR_TIMEOUT otherwise.
  *   cog_server_read_stats: counts and the p50/p99/max latency from submission
- *     to the mask being in host memory, and the seconds since creation.
+ *     to the mask being in host memory, and the seconds since creation; the
+ *     latency split into the wait (submission until the worker takes the
+ *     frame for a step) and the service (from then until the mask is in
+ *     host memory: upload, step, download, completion notice); and the host
+ *     time the worker spent issuing a step (copies, plan upload, graph
+ *     launch), whose tail shows the worker blocked in the CUDA runtime.
  *   cog_server_destroy: stops the threads; frames not yet started are
  *     dropped (drain first to keep them).  Errors are sticky. */
 typedef struct cog_server cog_server;
 typedef struct {
     int64_t submitted, frames, steps, pixels;
     double p50_ms, p99_ms, max_ms, wall_s;
+    double wait_p50_ms, wait_p99_ms;         /* submission -> taken for a step     */
+    double service_p50_ms, service_p99_ms;   /* taken -> mask in host memory       */
+    double enqueue_p99_ms, enqueue_max_ms;   /* per step: host time to issue it    */
 } cog_server_stats;
 cog_status cog_server_create(cog_ctx *const *ctxs, int32_t n, cog_server **out);
 cog_status cog_server_submit(cog_server *s, int32_t stream, const uint8_t *frame_host, uint8_t *mask_host);
@@ -245,6 +254,19 @@ cog_status cog_server_read_stats(cog_server *s, cog_server_stats *out);
 /* Per-frame record in completion order: submission time since creation and
  * latency, both in ms; copies min(cap, done) entries, *n = frames done. */
 cog_status cog_server_read_latencies(cog_server *s, float *submit_ms, float *latency_ms, int64_t cap, int64_t *n);
+/* The same with the wait of each frame (submission until the worker took it
+ * for a step) in wait_ms (nullable). */
+cog_status cog_server_read_timeline(cog_server *s, float *submit_ms, float *wait_ms, float *latency_ms, int64_t cap,
+                                    int64_t *n);
+/* Per-step record of the completed steps: the host time the worker spent
+ * issuing each step (enqueue_ms, in issue order) and, in parts_ms
+ * (nullable, 8 floats per step, in completion order), that time split into
+ * the frame uploads, the batched step (plan upload and graph launch) and
+ * the mask downloads with the completion event, then the step's GPU times
+ * from CUDA events: uploads, wait until the compute stream took the step,
+ * batched step, wait until the download stream took it, downloads.  Copies
+ * min(cap, completed) entries, *n = steps completed. */
+cog_status cog_server_read_steps(cog_server *s, float *enqueue_ms, float *parts_ms, int64_t cap, int64_t *n);
 const char *cog_server_last_error_string(cog_server *s);
 cog_status cog_server_destroy(cog_server *s);
 

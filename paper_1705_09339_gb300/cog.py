@@ -60,7 +60,9 @@ class cog_group_stats(C.Structure):
 
 class cog_server_stats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("frames", C.c_int64), ("steps", C.c_int64), ("pixels", C.c_int64),
-                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("max_ms", C.c_double), ("wall_s", C.c_double)]
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("max_ms", C.c_double), ("wall_s", C.c_double),
+                ("wait_p50_ms", C.c_double), ("wait_p99_ms", C.c_double), ("service_p50_ms", C.c_double),
+                ("service_p99_ms", C.c_double), ("enqueue_p99_ms", C.c_double), ("enqueue_max_ms", C.c_double)]
 
     def as_dict(self) -> dict:
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -123,6 +125,8 @@ def _load() -> C.CDLL:
         "cog_server_drain": (C.c_int, [vp, i32]),
         "cog_server_read_stats": (C.c_int, [vp, P(cog_server_stats)]),
         "cog_server_read_latencies": (C.c_int, [vp, vp, vp, C.c_int64, P(C.c_int64)]),
+        "cog_server_read_timeline": (C.c_int, [vp, vp, vp, vp, C.c_int64, P(C.c_int64)]),
+        "cog_server_read_steps": (C.c_int, [vp, vp, vp, C.c_int64, P(C.c_int64)]),
         "cog_server_last_error_string": (C.c_char_p, [vp]),
         "cog_server_destroy": (C.c_int, [vp]),
     }
@@ -526,6 +530,30 @@ def cog_server_read_latencies(srv):
     lat = np.empty(n.value, np.float32)
     _scheck(lib.cog_server_read_latencies(srv, t.ctypes.data, lat.ctypes.data, n.value, C.byref(n)), srv)
     return t, lat
+
+
+def cog_server_read_timeline(srv):
+    """(submission ms, wait ms, latency ms) arrays of the frames done, in
+    completion order; wait = submission until the worker took the frame."""
+    n = C.c_int64(0)
+    _scheck(lib.cog_server_read_timeline(srv, None, None, None, 0, C.byref(n)), srv)
+    t, w, lat = (np.empty(n.value, np.float32) for _ in range(3))
+    _scheck(lib.cog_server_read_timeline(srv, t.ctypes.data, w.ctypes.data, lat.ctypes.data, n.value, C.byref(n)),
+            srv)
+    return t, w, lat
+
+
+def cog_server_read_steps(srv):
+    """(enqueue ms [steps], parts ms [steps, 8]) of the completed steps: host
+    time per step; its split into uploads, batched step, downloads; then the
+    GPU times of uploads, compute wait, batched step, download wait,
+    downloads."""
+    n = C.c_int64(0)
+    _scheck(lib.cog_server_read_steps(srv, None, None, 0, C.byref(n)), srv)
+    e = np.empty(n.value, np.float32)
+    parts = np.empty((n.value, 8), np.float32)
+    _scheck(lib.cog_server_read_steps(srv, e.ctypes.data, parts.ctypes.data, n.value, C.byref(n)), srv)
+    return e, parts
 
 
 def cog_server_destroy(srv) -> None:

@@ -953,6 +953,9 @@ cog_status cog_destroy(cog_ctx *c)
 // CUDA graph (per storage type and K, one stage-0/1 launch and one mixture
 // launch over all the group's streams; groups run as parallel branches).
 // ---------------------------------------------------------------------------
+// Host staging sets for the per-step descriptor and plan uploads.
+constexpr int BATCH_STAGES = 8;
+
 struct BatchGroupHost {
     int dtype = 0, K = 0;
     int mv = 0;                        // mixture variant (BatchGroupDev::mv)
@@ -963,8 +966,8 @@ struct BatchGroupHost {
     uint32_t k1_ctas = 0, k2_ctas = 0; // fixed grids of the two batch kernels
     std::vector<int64_t> tiles, pix;   // stage-0/1 tiles and pixels per member
     void *dmem = nullptr;              // descs | frame_no | active | k1_pre | k2_pre
-    ApplyArgs *pinned[2] = {nullptr, nullptr};        // upload staging, by step parity
-    uint32_t *pinned_active[2] = {nullptr, nullptr};  // upload staging of the step plan
+    ApplyArgs *pinned[BATCH_STAGES] = {};              // upload staging, by step % BATCH_STAGES
+    uint32_t *pinned_active[BATCH_STAGES] = {};        // upload staging of the step plan
     std::vector<uint32_t> active;      // host copy of the active flags
 };
 
@@ -1005,7 +1008,7 @@ struct cog_batch {
     std::vector<uint8_t *> masks;
     std::vector<cudaStream_t> aux;     // one per group after the first (graph branches)
     std::vector<cudaEvent_t> fork, join;
-    cudaEvent_t uploaded[2] = {nullptr, nullptr};   // uploads of the last step of each parity done
+    cudaEvent_t uploaded[BATCH_STAGES] = {};        // uploads of the last step using each staging set done
     uint64_t step = 0;
     cudaGraphExec_t exec = nullptr;
     cog_status sticky = COG_OK;
@@ -1029,7 +1032,7 @@ static void batch_free(cog_batch *b)
     if (b->exec) cudaGraphExecDestroy(b->exec);
     for (auto &g : b->groups) {
         if (g.dmem) cudaFree(g.dmem);
-        for (int k = 0; k < 2; k++) {
+        for (int k = 0; k < BATCH_STAGES; k++) {
             if (g.pinned[k]) cudaFreeHost(g.pinned[k]);
             if (g.pinned_active[k]) cudaFreeHost(g.pinned_active[k]);
         }
@@ -1037,7 +1040,7 @@ static void batch_free(cog_batch *b)
     for (auto s : b->aux) cudaStreamDestroy(s);
     for (auto e : b->fork) cudaEventDestroy(e);
     for (auto e : b->join) cudaEventDestroy(e);
-    for (int k = 0; k < 2; k++)
+    for (int k = 0; k < BATCH_STAGES; k++)
         if (b->uploaded[k]) cudaEventDestroy(b->uploaded[k]);
     delete b;
 }
@@ -1080,8 +1083,9 @@ cog_status cog_batch_create(cog_ctx *const *ctxs, int32_t n, void *cuda_stream, 
         }
         b->groups[gi].members.push_back(i);
     }
-    cudaError_t e = cudaEventCreateWithFlags(&b->uploaded[0], cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->uploaded[1], cudaEventDisableTiming);
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < BATCH_STAGES && e == cudaSuccess; k++)
+        e = cudaEventCreateWithFlags(&b->uploaded[k], cudaEventDisableTiming);
     for (auto &g : b->groups) {
         if (e != cudaSuccess) break;
         const int m = (int)g.members.size();
@@ -1117,7 +1121,7 @@ cog_status cog_batch_create(cog_ctx *const *ctxs, int32_t n, void *cuda_stream, 
         const size_t plan_words = (size_t)m + 2 * (size_t)(m + 1);
         const size_t bytes = sizeof(ApplyArgs) * m + 4 * (size_t)m + 4 * plan_words + 64;
         if ((e = cudaMalloc(&g.dmem, bytes)) != cudaSuccess) break;
-        for (int k = 0; k < 2 && e == cudaSuccess; k++) {
+        for (int k = 0; k < BATCH_STAGES && e == cudaSuccess; k++) {
             if ((e = cudaMallocHost((void **)&g.pinned[k], sizeof(ApplyArgs) * m)) != cudaSuccess) break;
             e = cudaMallocHost((void **)&g.pinned_active[k], 4 * plan_words);
         }
@@ -1205,9 +1209,11 @@ static cog_status batch_apply(cog_batch *b, const uint8_t *const *frames_dev, ui
         if (b->ctxs[i]->sticky != COG_OK) return batch_err(b, b->ctxs[i]->sticky, "stream %d: sticky error", i);
     }
     cudaError_t e = cudaSuccess;
-    // upload staging alternates by step: the buffers of this parity were
-    // last read by the uploads of two steps ago
-    const int par = (int)(b->step & 1);
+    // upload staging rotates over BATCH_STAGES sets: the set of this step
+    // was last read by the uploads of BATCH_STAGES steps ago, long done
+    // while the host stays at most a few steps ahead of the GPU, so the
+    // wait below rarely blocks
+    const int par = (int)(b->step % BATCH_STAGES);
     bool staged = false;
     for (auto &g : b->groups) {
         bool dirty = false, adirty = false;

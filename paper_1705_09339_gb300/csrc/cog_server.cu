@@ -1,7 +1,8 @@
 // cog_server.cu -- native continuous-batching frame server (host code).
 //
 // Many camera streams share one GPU.  Callers submit host frames from any
-// thread; a worker thread repeatedly takes, for every stream that has a
+// thread; a worker thread repeatedly takes, while fewer than
+// MAX_STEPS_IN_FLIGHT steps are on the GPU, for every stream that has a
 // frame waiting and a free device slot (two per stream), the oldest frame,
 // uploads those frames on a copy stream, runs one batched cascade step over
 // exactly those streams (cog_batch_apply_active: one replay of one captured
@@ -34,6 +35,19 @@ namespace {
 
 using clk = std::chrono::steady_clock;
 
+// Steps on the GPU at once.  Every step carries fixed costs (copies issued,
+// plan upload, graph launch, completion), so a step per arriving frame
+// cannot keep up with thousands of frames per second.  With a few steps in
+// flight the GPU stays busy, and frames that arrive meanwhile gather into
+// the next, larger step.
+constexpr int MAX_STEPS_IN_FLIGHT = 3;
+
+// GPU-side timing of a step: events on the copy and compute streams
+//   0 uploads start, 1 uploads done (up stream),
+//   2 batched step starts, 3 batched step done (compute stream),
+//   4 downloads start, 5 downloads done (down stream)
+constexpr int STEP_TIMERS = 6;
+
 struct Pending {
     const uint8_t *frame;   // host, height x width x 3
     uint8_t *mask;          // host, height x width
@@ -53,10 +67,13 @@ struct Stream {
 struct Pick {
     int stream;
     Pending f;
+    clk::time_point t_pick;   // when the worker took the frame for a step
 };
 
 struct Step {
-    cudaEvent_t done;
+    cudaEvent_t done = nullptr;              // completion (from the server's event pool)
+    cudaEvent_t tm[STEP_TIMERS] = {};        // timing events (from the timing pool)
+    float host_parts[3] = {0.f, 0.f, 0.f};   // host time issuing uploads, batched step, downloads
     std::vector<Pick> picks;
 };
 
@@ -88,11 +105,18 @@ struct cog_server {
     std::mutex dmu;
     std::condition_variable cv_done;
     std::deque<Step> done_q;
+    std::vector<cudaEvent_t> ev_pool;    // step-completion events ready for reuse (under dmu)
+    std::vector<cudaEvent_t> tm_pool;    // timing events ready for reuse (under dmu)
+    std::vector<cudaEvent_t> ev_all;     // every event the pools ever made (freed with the server)
     bool stop = false, worker_done = false;
     std::thread worker, completer;
     std::vector<float> lat_ms;
     std::vector<float> sub_ms;           // submission time of each done frame, since creation
+    std::vector<float> wait_ms;          // submission -> taken by the worker, per done frame
+    std::vector<float> enq_ms;           // per step issued: host time to issue it
+    std::vector<float> step_parts_ms;    // per step completed: 3 host parts, then 5 GPU times
     int64_t frames = 0, pixels = 0, steps = 0, submitted = 0;
+    int steps_in_flight = 0;             // issued and not yet completed (under mu)
     clk::time_point t0;
     cog_status sticky = COG_OK;
     char err[512] = {0};
@@ -177,6 +201,27 @@ static cog_status add_err(cog_server *s, cog_status st, const char *fmt, ...)
     return st;
 }
 
+// An event from a pool (under dmu), or a new one recorded in ev_all.
+static cudaError_t pool_event(cog_server *s, std::vector<cudaEvent_t> &pool, unsigned flags, cudaEvent_t *out)
+{
+    {
+        std::lock_guard<std::mutex> lk(s->dmu);
+        if (!pool.empty()) {
+            *out = pool.back();
+            pool.pop_back();
+            return cudaSuccess;
+        }
+    }
+    const cudaError_t e = cudaEventCreateWithFlags(out, flags);
+    if (e != cudaSuccess) {
+        *out = nullptr;
+        return e;
+    }
+    std::lock_guard<std::mutex> lk(s->dmu);
+    s->ev_all.push_back(*out);
+    return cudaSuccess;
+}
+
 static void server_worker(cog_server *s)
 {
     cudaSetDevice(s->device);
@@ -196,20 +241,28 @@ static void server_worker(cog_server *s)
                     masks.resize(n, nullptr);
                     active.resize(n, 0);
                 }
-                for (int i = 0; i < n; i++) {
-                    Stream &q = s->streams[i];
-                    if (!q.pending.empty() && q.inflight < 2) {
-                        picks.push_back({i, q.pending.front()});
-                        q.pending.pop_front();
-                        q.inflight++;
+                if (s->steps_in_flight < MAX_STEPS_IN_FLIGHT) {
+                    for (int i = 0; i < n; i++) {
+                        Stream &q = s->streams[i];
+                        if (!q.pending.empty() && q.inflight < 2) {
+                            picks.push_back({i, q.pending.front(), clk::time_point{}});
+                            q.pending.pop_front();
+                            q.inflight++;
+                        }
                     }
                 }
                 if (!picks.empty() || s->stop || s->sticky != COG_OK) break;
                 s->cv_work.wait_for(lk, std::chrono::milliseconds(50));
             }
             if (picks.empty()) break;   // stopping, nothing left to start
+            s->steps_in_flight++;
         }
+        const clk::time_point t_pick = clk::now();
+        for (Pick &k : picks) k.t_pick = t_pick;
         cudaError_t e = cudaSuccess;
+        Step step;
+        for (int k = 0; k < STEP_TIMERS && e == cudaSuccess; k++) e = pool_event(s, s->tm_pool, cudaEventDefault, &step.tm[k]);
+        if (e == cudaSuccess) e = cudaEventRecord(step.tm[0], s->up);
         std::fill(active.begin(), active.end(), 0);
         for (const Pick &k : picks) {
             Stream &q = s->streams[k.stream];
@@ -220,29 +273,41 @@ static void server_worker(cog_server *s)
             masks[k.stream] = q.mslot[sl];
             active[k.stream] = 1;
         }
+        if (e == cudaSuccess) e = cudaEventRecord(step.tm[1], s->up);
         if (e == cudaSuccess) e = cudaEventRecord(s->copied, s->up);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s->compute, s->copied, 0);
+        if (e == cudaSuccess) e = cudaEventRecord(step.tm[2], s->compute);
+        const clk::time_point t_up = clk::now();
         cog_status st = COG_OK;
         if (e == cudaSuccess) st = cog_batch_apply_active(s->batch, frames.data(), masks.data(), active.data());
+        const clk::time_point t_app = clk::now();
+        if (e == cudaSuccess && st == COG_OK) e = cudaEventRecord(step.tm[3], s->compute);
         if (e == cudaSuccess && st == COG_OK) e = cudaEventRecord(s->applied, s->compute);
         if (e == cudaSuccess && st == COG_OK) e = cudaStreamWaitEvent(s->down, s->applied, 0);
+        if (e == cudaSuccess && st == COG_OK) e = cudaEventRecord(step.tm[4], s->down);
         for (const Pick &k : picks) {
             Stream &q = s->streams[k.stream];
             if (e == cudaSuccess && st == COG_OK)
                 e = cudaMemcpyAsync(k.f.mask, q.mslot[k.f.seq & 1], (size_t)q.P, cudaMemcpyDeviceToHost, s->down);
         }
-        Step step;
+        if (e == cudaSuccess && st == COG_OK) e = cudaEventRecord(step.tm[5], s->down);
         step.picks = std::move(picks);
         // a blocking-sync event lets the completion thread sleep in its wait
-        // instead of spinning a core
+        // instead of spinning a core; events come from pools that grow to
+        // the number of steps ever in flight at once and are reused
         if (e == cudaSuccess && st == COG_OK)
-            e = cudaEventCreateWithFlags(&step.done, cudaEventDisableTiming | cudaEventBlockingSync);
+            e = pool_event(s, s->ev_pool, cudaEventDisableTiming | cudaEventBlockingSync, &step.done);
         if (e == cudaSuccess && st == COG_OK) e = cudaEventRecord(step.done, s->down);
+        const clk::time_point t_end = clk::now();
+        step.host_parts[0] = std::chrono::duration<float, std::milli>(t_up - t_pick).count();
+        step.host_parts[1] = std::chrono::duration<float, std::milli>(t_app - t_up).count();
+        step.host_parts[2] = std::chrono::duration<float, std::milli>(t_end - t_app).count();
         if (e != cudaSuccess || st != COG_OK) {
             std::lock_guard<std::mutex> lk(s->mu);
             if (st != COG_OK) server_err(s, st, "batched step: %s", cog_batch_last_error_string(s->batch));
             else server_err(s, COG_ERR_CUDA, "batched step: %s", cudaGetErrorString(e));
             for (const Pick &k : step.picks) s->streams[k.stream].inflight--;
+            s->steps_in_flight--;
             s->cv_idle.notify_all();
             break;
         }
@@ -254,6 +319,7 @@ static void server_worker(cog_server *s)
         {
             std::lock_guard<std::mutex> lk(s->mu);
             s->steps++;
+            s->enq_ms.push_back(std::chrono::duration<float, std::milli>(t_end - t_pick).count());
         }
     }
     {
@@ -281,10 +347,23 @@ static void server_completer(cog_server *s)
         }
         const cudaError_t e = cudaEventSynchronize(step.done);
         const clk::time_point now = clk::now();
-        cudaEventDestroy(step.done);
+        // GPU times of the step: uploads, wait until the compute stream took
+        // it, batched step, wait until the download stream took it, downloads
+        float g[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        if (e == cudaSuccess)
+            for (int k = 0; k < 5; k++)
+                if (cudaEventElapsedTime(&g[k], step.tm[k], step.tm[k + 1]) != cudaSuccess) g[k] = -1.f;
+        {
+            std::lock_guard<std::mutex> lk(s->dmu);
+            s->ev_pool.push_back(step.done);
+            for (int k = 0; k < STEP_TIMERS; k++) s->tm_pool.push_back(step.tm[k]);
+        }
         {
             std::lock_guard<std::mutex> lk(s->mu);
             if (e != cudaSuccess) server_err(s, COG_ERR_CUDA, "step completion: %s", cudaGetErrorString(e));
+            s->steps_in_flight--;
+            s->step_parts_ms.insert(s->step_parts_ms.end(), step.host_parts, step.host_parts + 3);
+            s->step_parts_ms.insert(s->step_parts_ms.end(), g, g + 5);
             for (const Pick &k : step.picks) {
                 Stream &q = s->streams[k.stream];
                 q.inflight--;
@@ -292,6 +371,7 @@ static void server_completer(cog_server *s)
                 s->pixels += q.P;
                 s->lat_ms.push_back(std::chrono::duration<float, std::milli>(now - k.f.t).count());
                 s->sub_ms.push_back(std::chrono::duration<float, std::milli>(k.f.t - s->t0).count());
+                s->wait_ms.push_back(std::chrono::duration<float, std::milli>(k.t_pick - k.f.t).count());
             }
         }
         s->cv_work.notify_one();
@@ -307,6 +387,7 @@ static void server_free(cog_server *s)
             if (q.mslot[k]) cudaFree(q.mslot[k]);
         }
     if (s->batch) cog_batch_destroy(s->batch);
+    for (cudaEvent_t ev : s->ev_all) cudaEventDestroy(ev);
     if (s->copied) cudaEventDestroy(s->copied);
     if (s->applied) cudaEventDestroy(s->applied);
     for (cudaStream_t st : {s->compute, s->up, s->down})
@@ -451,10 +532,21 @@ cog_status cog_server_drain(cog_server *s, int32_t timeout_ms)
     return s->sticky;
 }
 
+// Linear-interpolated quantile q of v (sorted in place); 0 when empty.
+static double quantile(std::vector<float> &v, double q)
+{
+    if (v.empty()) return 0.0;
+    std::sort(v.begin(), v.end());
+    const double r = q * (double)(v.size() - 1);
+    const size_t i = (size_t)r;
+    const double f = r - (double)i;
+    return i + 1 < v.size() ? (1.0 - f) * v[i] + f * v[i + 1] : (double)v[i];
+}
+
 cog_status cog_server_read_stats(cog_server *s, cog_server_stats *out)
 {
     if (!s || !out) return COG_ERR_INVALID_ARG;
-    std::vector<float> lat;
+    std::vector<float> lat, wait, svc, enq;
     {
         std::lock_guard<std::mutex> lk(s->mu);
         memset(out, 0, sizeof *out);
@@ -464,23 +556,30 @@ cog_status cog_server_read_stats(cog_server *s, cog_server_stats *out)
         out->submitted = s->submitted;
         out->wall_s = std::chrono::duration<double>(clk::now() - s->t0).count();
         lat = s->lat_ms;
+        wait = s->wait_ms;
+        enq = s->enq_ms;
     }
-    if (!lat.empty()) {
-        std::sort(lat.begin(), lat.end());
-        auto pct = [&](double q) {
-            const double r = q * (double)(lat.size() - 1);
-            const size_t i = (size_t)r;
-            const double f = r - (double)i;
-            return i + 1 < lat.size() ? (1.0 - f) * lat[i] + f * lat[i + 1] : (double)lat[i];
-        };
-        out->p50_ms = pct(0.50);
-        out->p99_ms = pct(0.99);
-        out->max_ms = lat.back();
-    }
+    svc.resize(lat.size());
+    for (size_t i = 0; i < lat.size(); i++) svc[i] = lat[i] - wait[i];
+    out->p50_ms = quantile(lat, 0.50);
+    out->p99_ms = quantile(lat, 0.99);
+    out->max_ms = lat.empty() ? 0.0 : lat.back();
+    out->wait_p50_ms = quantile(wait, 0.50);
+    out->wait_p99_ms = quantile(wait, 0.99);
+    out->service_p50_ms = quantile(svc, 0.50);
+    out->service_p99_ms = quantile(svc, 0.99);
+    out->enqueue_p99_ms = quantile(enq, 0.99);
+    out->enqueue_max_ms = enq.empty() ? 0.0 : enq.back();
     return s->sticky;
 }
 
 cog_status cog_server_read_latencies(cog_server *s, float *submit_ms, float *latency_ms, int64_t cap, int64_t *n)
+{
+    return cog_server_read_timeline(s, submit_ms, nullptr, latency_ms, cap, n);
+}
+
+cog_status cog_server_read_timeline(cog_server *s, float *submit_ms, float *wait_ms, float *latency_ms, int64_t cap,
+                                    int64_t *n)
 {
     if (!s || !n || cap < 0 || (cap > 0 && (!submit_ms || !latency_ms))) return COG_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(s->mu);
@@ -488,8 +587,23 @@ cog_status cog_server_read_latencies(cog_server *s, float *submit_ms, float *lat
     if (m > 0) {
         memcpy(submit_ms, s->sub_ms.data(), sizeof(float) * (size_t)m);
         memcpy(latency_ms, s->lat_ms.data(), sizeof(float) * (size_t)m);
+        if (wait_ms) memcpy(wait_ms, s->wait_ms.data(), sizeof(float) * (size_t)m);
     }
     *n = (int64_t)s->lat_ms.size();
+    return COG_OK;
+}
+
+cog_status cog_server_read_steps(cog_server *s, float *enqueue_ms, float *parts_ms, int64_t cap, int64_t *n)
+{
+    if (!s || !n || cap < 0 || (cap > 0 && !enqueue_ms)) return COG_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    const int64_t done = (int64_t)(s->step_parts_ms.size() / 8);
+    const int64_t m = std::min<int64_t>(cap, done);
+    if (m > 0) {
+        memcpy(enqueue_ms, s->enq_ms.data(), sizeof(float) * (size_t)std::min<int64_t>(m, (int64_t)s->enq_ms.size()));
+        if (parts_ms) memcpy(parts_ms, s->step_parts_ms.data(), sizeof(float) * 8 * (size_t)m);
+    }
+    *n = done;
     return COG_OK;
 }
 

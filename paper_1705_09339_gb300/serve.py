@@ -100,7 +100,8 @@ class FrameServer:
         statistics."""
         cog.cog_server_drain(self.srv, timeout_ms)
         st = cog.cog_server_read_stats(self.srv)
-        self.timeline = cog.cog_server_read_latencies(self.srv)
+        self.timeline = cog.cog_server_read_timeline(self.srv)
+        self.steps = cog.cog_server_read_steps(self.srv)
         self._keep = []
         wall = st["wall_s"]
         return {"frames": st["frames"], "steps": st["steps"], "wall_s": round(wall, 3),
@@ -108,6 +109,14 @@ class FrameServer:
                 "latency_ms": {"p50": round(st["p50_ms"], 3) if st["frames"] else None,
                                "p99": round(st["p99_ms"], 3) if st["frames"] else None,
                                "max": round(st["max_ms"], 3) if st["frames"] else None},
+                # where the latency goes: waiting for the worker to take the
+                # frame, the frame's service (upload, step, download), and
+                # the host time the worker needed to issue a step
+                "latency_split_ms": {"wait_p50": round(st["wait_p50_ms"], 3), "wait_p99": round(st["wait_p99_ms"], 3),
+                                     "service_p50": round(st["service_p50_ms"], 3),
+                                     "service_p99": round(st["service_p99_ms"], 3),
+                                     "enqueue_p99": round(st["enqueue_p99_ms"], 3),
+                                     "enqueue_max": round(st["enqueue_max_ms"], 3)},
                 "cameras": len(self.cameras), "refused": len(self.refused)}
 
     def close(self):
