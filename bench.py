@@ -933,9 +933,12 @@ def run_serve(args, rank, local_rank, world):
     import gc
     gc.collect()
     gc.freeze()
+    # two warm-up frames per camera (both of its device slots, the batch
+    # graph's first launch), left out of the statistics; the Poisson stream
+    # then continues each camera's frames
+    srv.start(warmup_frames={cid: pools[cid][:2] for cid in pools})
     clocks = Clocks(local_rank)
     clocks.start()
-    srv.start()
     t0 = time.perf_counter()
     heap = [(t0 + float(rng.exponential(1 / 30)), c.id) for c in srv.cameras]
     heapq.heapify(heap)

@@ -214,7 +214,7 @@ cog_status cog_clip_runs(cog_ctx *ctx, int32_t *runs);
  *     (height x width x 3 bytes; page-locked for overlap) and the host
  *     buffer that receives its mask; both must stay valid until the frame
  *     is done (cog_server_drain).  Thread-safe; returns at once.
- *   The worker takes, while fewer than three steps are on the GPU, for
+ *   The worker takes, while fewer than four steps are on the GPU, for
  *   every stream with a frame waiting and a free slot, the oldest frame;
  *   uploads them; runs one batched step over those streams only; downloads
  *   their masks.  Frames submitted meanwhile join the next step, whose
@@ -267,6 +267,10 @@ cog_status cog_server_read_timeline(cog_server *s, float *submit_ms, float *wait
  * batched step, wait until the download stream took it, downloads.  Copies
  * min(cap, completed) entries, *n = steps completed. */
 cog_status cog_server_read_steps(cog_server *s, float *enqueue_ms, float *parts_ms, int64_t cap, int64_t *n);
+/* Clears the counters, latency and step records and restarts the clock of
+ * cog_server_read_stats (for example after warm-up frames).  Every submitted
+ * frame must be done (cog_server_drain): COG_ERR_STATE otherwise. */
+cog_status cog_server_reset_stats(cog_server *s);
 const char *cog_server_last_error_string(cog_server *s);
 cog_status cog_server_destroy(cog_server *s);
 

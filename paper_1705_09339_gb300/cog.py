@@ -127,6 +127,7 @@ def _load() -> C.CDLL:
         "cog_server_read_latencies": (C.c_int, [vp, vp, vp, C.c_int64, P(C.c_int64)]),
         "cog_server_read_timeline": (C.c_int, [vp, vp, vp, vp, C.c_int64, P(C.c_int64)]),
         "cog_server_read_steps": (C.c_int, [vp, vp, vp, C.c_int64, P(C.c_int64)]),
+        "cog_server_reset_stats": (C.c_int, [vp]),
         "cog_server_last_error_string": (C.c_char_p, [vp]),
         "cog_server_destroy": (C.c_int, [vp]),
     }
@@ -554,6 +555,10 @@ def cog_server_read_steps(srv):
     parts = np.empty((n.value, 8), np.float32)
     _scheck(lib.cog_server_read_steps(srv, e.ctypes.data, parts.ctypes.data, n.value, C.byref(n)), srv)
     return e, parts
+
+
+def cog_server_reset_stats(srv) -> None:
+    _scheck(lib.cog_server_reset_stats(srv), srv)
 
 
 def cog_server_destroy(srv) -> None:

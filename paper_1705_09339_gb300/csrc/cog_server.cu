@@ -11,7 +11,8 @@
 // overlap the running step.  A completion thread waits for each step's
 // downloads and records every frame's latency from submission to its mask
 // being in host memory.  Every wait is bounded by a condition-variable
-// timeout or by a CUDA event of work already enqueued.  A camera can join a
+// timeout or by a CUDA event of work already enqueued (polled, then waited
+// for in short naps).  A camera can join a
 // running server: between steps, once no step is on the GPU, the worker
 // rebuilds the batch over all the contexts.
 #include <algorithm>
@@ -40,7 +41,13 @@ using clk = std::chrono::steady_clock;
 // cannot keep up with thousands of frames per second.  With a few steps in
 // flight the GPU stays busy, and frames that arrive meanwhile gather into
 // the next, larger step.
-constexpr int MAX_STEPS_IN_FLIGHT = 3;
+constexpr int MAX_STEPS_IN_FLIGHT = 4;
+
+// The completion thread polls a step's event for up to this long before it
+// blocks: a blocking wait's wake-up costs about a millisecond, which with a
+// few steps in flight would bound the steps per second.  Past the spell
+// (an idle server) it sleeps in short naps instead of spinning a core.
+constexpr auto COMPLETION_SPIN = std::chrono::microseconds(3000);
 
 // GPU-side timing of a step: events on the copy and compute streams
 //   0 uploads start, 1 uploads done (up stream),
@@ -292,11 +299,9 @@ static void server_worker(cog_server *s)
         }
         if (e == cudaSuccess && st == COG_OK) e = cudaEventRecord(step.tm[5], s->down);
         step.picks = std::move(picks);
-        // a blocking-sync event lets the completion thread sleep in its wait
-        // instead of spinning a core; events come from pools that grow to
-        // the number of steps ever in flight at once and are reused
-        if (e == cudaSuccess && st == COG_OK)
-            e = pool_event(s, s->ev_pool, cudaEventDisableTiming | cudaEventBlockingSync, &step.done);
+        // events come from pools that grow to the number of steps ever in
+        // flight at once and are reused
+        if (e == cudaSuccess && st == COG_OK) e = pool_event(s, s->ev_pool, cudaEventDisableTiming, &step.done);
         if (e == cudaSuccess && st == COG_OK) e = cudaEventRecord(step.done, s->down);
         const clk::time_point t_end = clk::now();
         step.host_parts[0] = std::chrono::duration<float, std::milli>(t_up - t_pick).count();
@@ -345,7 +350,14 @@ static void server_completer(cog_server *s)
             step = std::move(s->done_q.front());
             s->done_q.pop_front();
         }
-        const cudaError_t e = cudaEventSynchronize(step.done);
+        // poll the step's event (a finished step is noticed within
+        // microseconds), then nap between polls once the spell is over
+        cudaError_t e;
+        const clk::time_point t_wait = clk::now();
+        while ((e = cudaEventQuery(step.done)) == cudaErrorNotReady) {
+            if (clk::now() - t_wait < COMPLETION_SPIN) std::this_thread::yield();
+            else std::this_thread::sleep_for(std::chrono::microseconds(50));
+        }
         const clk::time_point now = clk::now();
         // GPU times of the step: uploads, wait until the compute stream took
         // it, batched step, wait until the download stream took it, downloads
@@ -605,6 +617,22 @@ cog_status cog_server_read_steps(cog_server *s, float *enqueue_ms, float *parts_
     }
     *n = done;
     return COG_OK;
+}
+
+cog_status cog_server_reset_stats(cog_server *s)
+{
+    if (!s) return COG_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->frames != s->submitted || s->steps_in_flight)
+        return server_err(s, COG_ERR_STATE, "reset_stats: frames are still in flight (drain first)");
+    s->frames = s->pixels = s->steps = s->submitted = 0;
+    s->lat_ms.clear();
+    s->sub_ms.clear();
+    s->wait_ms.clear();
+    s->enq_ms.clear();
+    s->step_parts_ms.clear();
+    s->t0 = clk::now();
+    return s->sticky;
 }
 
 const char *cog_server_last_error_string(cog_server *s)

@@ -78,9 +78,18 @@ class FrameServer:
         self.cameras.append(cam)
         return cam
 
-    def start(self):
-        """Hands the admitted cameras to the native server and starts it."""
+    def start(self, warmup_frames=None):
+        """Hands the admitted cameras to the native server and starts it.
+        warmup_frames (optional): camera id -> list of host frames, served
+        first and left out of the statistics; they take each camera's first
+        steps (slot buffers, the batch graph's first launch)."""
         self.srv = cog.cog_server_create([c.ctx for c in self.cameras])
+        if warmup_frames:
+            for cam in self.cameras:
+                for f in warmup_frames.get(cam.id, []):
+                    self.submit(cam, f)
+            cog.cog_server_drain(self.srv, 120000)
+            cog.cog_server_reset_stats(self.srv)
 
     def submit(self, cam: Camera, frame_host, t_arrival: float | None = None):
         """Queues a host frame (pinned uint8 tensor [H, W, 3], alive until
