@@ -203,8 +203,12 @@ __device__ __forceinline__ uint32_t k1_own_out(const ApplyArgs &A, const K1Px<T>
             if (X.skip >> i & 1u) mk |= ((j >> 24) ? 255u : 0u) << (8 * i);
         }
     }
-    *reinterpret_cast<uint4 *>(A.s.jl + p0) = jn;
-    if (dp.flags & COG_CONF) {
+    // a thread whose pixels are all skipped by the temporal sampling changes
+    // nothing but its mask: its previous-frame and confidence words are
+    // not rewritten
+    const bool all_skipped = X.skip == X.act;
+    if (!all_skipped) *reinterpret_cast<uint4 *>(A.s.jl + p0) = jn;
+    if ((dp.flags & COG_CONF) && !all_skipped) {
         // C <- (1 - eta) C- + eta for the stage-0 pixels (c_inst = 1)
         VecN<T, PPT> cn = X.cv;
         if (Store<T>::bytes == 2) {
