@@ -53,6 +53,7 @@ static int check_params(const orc_params *pr)
     if (pr->K < 1 || pr->K > KMAX) return -1;
     if (!(pr->var_min > 0.0) || pr->var_max < pr->var_min) return -1;
     if (pr->kde_bw < 1 || pr->kde_bw > 32) return -1;
+    if (pr->kde_bits != 8 && pr->kde_bits != 4) return -1;
     if ((pr->flags & ORC_SAMPLE) && pr->skip_period < 1) return -1;
     if ((pr->flags & ORC_PERCHAN) && (pr->flags & ORC_MODE1)) return -1;
     return 0;
@@ -64,8 +65,9 @@ static int check_params(const orc_params *pr)
 /* Gaussian kernel K_sigma of bandwidth bw, independent R, G, B.  The     */
 /* density is evaluated on the 256 grey levels in integer arithmetic:     */
 /*   k[v] = sum_u h[u] g[v-u],  g[d] = round(2^16 exp(-d^2/(2 bw^2)))     */
-/* truncated at |d| <= 3 bw, then normalised to its peak:                */
-/*   q[v] = (255 k[v] + M/2) div M,  M = max_v k[v].                      */
+/* truncated at |d| <= 3 bw, then normalised to its peak and quantised */
+/* to Q = 2^kde_bits - 1 levels (255 for the 8-bit prior, 15 for 4-bit):  */
+/*   q[v] = (Q k[v] + M/2) div M,  M = max_v k[v].                        */
 /* ------------------------------------------------------------------ */
 int orc_kde_weights(int bw, int64_t *g, int cap)
 {
@@ -78,7 +80,7 @@ int orc_kde_weights(int bw, int64_t *g, int cap)
 }
 
 static void kde_one(const uint8_t *frames, int N, int64_t P, int64_t p, int c,
-                    const int64_t *g, int R, uint8_t *q)
+                    const int64_t *g, int R, int64_t Q, uint8_t *q)
 {
     int64_t h[256];
     int64_t k[256];
@@ -96,7 +98,25 @@ static void kde_one(const uint8_t *frames, int N, int64_t P, int64_t p, int c,
         if (acc > M) M = acc;
     }
     for (int v = 0; v < 256; v++)
-        q[v] = (uint8_t)((255 * k[v] + M / 2) / M);
+        q[v] = (uint8_t)((Q * k[v] + M / 2) / M);
+}
+
+/* The prior's value at the pixel's colour (Sec. 2, "Confidence Measure" and
+ * "Cascade of Gaussians CoG"): the smallest of the three channel levels as a
+ * fraction of the peak, q / Q.  The prior is nullified when that fraction
+ * is below q_null / 255 (q_null is on the 8-bit scale for either width),
+ * decided exactly in integers: 255 q < q_null Q. */
+static int prior_nullified(const orc_params *pr, const orc_state *s, int64_t p, const uint8_t *I,
+                           double *frac)
+{
+    const int Q = (1 << pr->kde_bits) - 1;
+    int qmin = Q;
+    for (int c = 0; c < 3; c++) {
+        int q = s->kde[(p * 3 + c) * 256 + I[c]];
+        if (q < qmin) qmin = q;
+    }
+    *frac = (double)qmin / Q;
+    return 255 * qmin < pr->q_null * Q;
 }
 
 /* ------------------------------------------------------------------ */
@@ -337,16 +357,12 @@ static px_out cascade_pixel(const orc_params *pr, orc_state *s, int64_t p,
         int il;
         label = stage2_perchan(pr, s, p, I, a_eff, illum_flag, &Mhat, &o.near, &il);
         o.stage = il ? ORC_ST_ILLUM : (label ? ORC_ST_FG : ORC_ST_GMM_BG);
-        int qmin = 255;
-        for (int c = 0; c < 3; c++) {
-            int q = s->kde[(p * 3 + c) * 256 + I[c]];
-            if (q < qmin) qmin = q;
-        }
-        if (qmin < pr->q_null) {
+        double qfrac;
+        if (prior_nullified(pr, s, p, I, &qfrac)) {
             double den = wb + wg;
             c_inst = den > 0.0 ? (wb * (1.0 - dhat) + wg * (1.0 - Mhat)) / den : 0.0;
         } else {
-            c_inst = wa * (qmin / 255.0) + wb * (1.0 - dhat) + wg * (1.0 - Mhat);
+            c_inst = wa * qfrac + wb * (1.0 - dhat) + wg * (1.0 - Mhat);
         }
         goto finish;
     }
@@ -474,17 +490,14 @@ static px_out cascade_pixel(const orc_params *pr, orc_state *s, int64_t p,
         }
         /* 7. confidence terms; the prior term drops out when the value lies
          *    in no dominant mode of the prior ("prior nullified") */
-        int qmin = 255;
-        for (int c = 0; c < 3; c++) {
-            int q = s->kde[(p * 3 + c) * 256 + I[c]];
-            if (q < qmin) qmin = q;
-        }
+        double qfrac;
+        const int nullified = prior_nullified(pr, s, p, I, &qfrac);
         double Mhat = (m >= 0) ? (tm < 1.0 ? tm : 1.0) : 1.0;
-        if (qmin < pr->q_null) {
+        if (nullified) {
             double den = wb + wg;
             c_inst = den > 0.0 ? (wb * (1.0 - dhat) + wg * (1.0 - Mhat)) / den : 0.0;
         } else {
-            c_inst = wa * (qmin / 255.0) + wb * (1.0 - dhat) + wg * (1.0 - Mhat);
+            c_inst = wa * qfrac + wb * (1.0 - dhat) + wg * (1.0 - Mhat);
         }
     }
 
@@ -551,7 +564,7 @@ int orc_train_near(const orc_params *pr, const uint8_t *frames, int N, orc_state
 #endif
     for (int64_t p = 0; p < P; p++) {
         for (int c = 0; c < 3; c++)
-            kde_one(frames, N, P, p, c, g, R, s->kde + (p * 3 + c) * 256);
+            kde_one(frames, N, P, p, c, g, R, (1 << pr->kde_bits) - 1, s->kde + (p * 3 + c) * 256);
         residue_one(pr, frames, N, P, p, s->qa + p, s->qb + p);
     }
 

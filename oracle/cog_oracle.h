@@ -94,12 +94,13 @@ typedef struct {
     double w_illum;     /* weight given on an illumination change       */
     double c_skip;      /* sampling: confidence at which a pixel is only
                            processed every skip_period frames           */
-    int q_null;         /* prior nullified below this level (of 255)    */
+    int q_null;         /* prior nullified below q_null / 255 of peak   */
     int kde_bw;         /* kernel bandwidth in grey levels              */
     int r1, r2;         /* residue class bounds                         */
     int illum_permille; /* illumination threshold, per mille of pixels  */
     int skip_period;    /* sampling period S (>= 1)                     */
     unsigned flags;     /* ORC_* switches                               */
+    int kde_bits;       /* prior levels: 8 (0..255) or 4 (0..15)        */
 } orc_params;
 
 /* Model state, all arrays owned by the caller. P = width*height. */
@@ -112,7 +113,8 @@ typedef struct {
     double  *conf;   /* [P]          confidence C                       */
     uint8_t *label;  /* [P]          previous label, 0 = BG, 1 = FG     */
     uint8_t *prev;   /* [P][3]       previous frame J                   */
-    uint8_t *kde;    /* [P][3][256]  peak-normalised prior q_c[v]       */
+    uint8_t *kde;    /* [P][3][256]  peak-normalised prior q_c[v], one
+                                     level per byte (0..2^kde_bits - 1)  */
     uint8_t *qa;     /* [P]          static-class weight, of 255        */
     uint8_t *qb;     /* [P]          dynamic-class weight, of 255       */
     int64_t *illum;  /* [2]          [0]: pixels that reached the GMM stage in

@@ -49,6 +49,7 @@ class _Params(C.Structure):
         ("c_halt", C.c_double), ("w_illum", C.c_double), ("c_skip", C.c_double),
         ("q_null", C.c_int), ("kde_bw", C.c_int), ("r1", C.c_int), ("r2", C.c_int),
         ("illum_permille", C.c_int), ("skip_period", C.c_int), ("flags", C.c_uint),
+        ("kde_bits", C.c_int),
     ]
 
 
@@ -203,10 +204,10 @@ def default_params(width: int, height: int, K: int = 3) -> dict:
     return dict(width=width, height=height, K=K, alpha=0.01, lambda_=2.5, T_bg=0.7,
                 w_init=0.05, var_init=225.0, var_min=4.0, var_max=900.0, tau_fd=8.0,
                 eta=0.125, c_halt=0.9, w_illum=0.75, c_skip=0.95, q_null=13, kde_bw=4, r1=10, r2=30,
-                illum_permille=700, skip_period=4, flags=ORC_FD | ORC_RGA | ORC_CONF | ORC_ILLUM)
+                illum_permille=700, skip_period=4, flags=ORC_FD | ORC_RGA | ORC_CONF | ORC_ILLUM, kde_bits=8)
 
 
-_OPTIONAL = {"c_skip": 0.95, "skip_period": 4}
+_OPTIONAL = {"c_skip": 0.95, "skip_period": 4, "kde_bits": 8}
 
 
 def _params(p: dict) -> _Params:

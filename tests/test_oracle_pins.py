@@ -80,6 +80,56 @@ def test_kde_bruteforce_direct_sum_over_samples():
             assert list(o.state.kde[0, c]) == exp
 
 
+@pytest.mark.parametrize("bw", [4, 1, 7])
+@pytest.mark.parametrize("v", [0, 100, 255])
+def test_kde4_of_constant_training_is_the_kernel_on_15_levels(v, bw):
+    # the 4-bit prior quantises the same density to 15 levels of its peak:
+    # all N values equal v gives (15 g[d] + g[0]/2) div g[0], d = |u - v|
+    o = one_pixel(kde_bw=bw, kde_bits=4)
+    o.train(np.full((5, 1, 3), v, np.uint8))
+    g = [math.floor(65536.0 * math.exp(-d * d / (2.0 * bw * bw)) + 0.5) for d in range(3 * bw + 1)]
+    for c in range(3):
+        q = o.state.kde[0, c]
+        for u in range(256):
+            d = abs(u - v)
+            assert q[u] == ((15 * g[d] + g[0] // 2) // g[0] if d <= 3 * bw else 0), (u, v, bw)
+
+
+def test_kde4_bruteforce_direct_sum_over_samples():
+    # as the 8-bit brute force, with 15 levels: q = (15 k + M/2) div M
+    rng = np.random.default_rng(11)
+    g = [int(x) for x in kde_weights(4)]
+    for trial in range(12):
+        N = int(rng.integers(2, 6))
+        frames = rng.integers(0, 256, (N, 1, 3), dtype=np.uint8)
+        if trial % 2 == 0:
+            frames = np.clip(frames // 6 + 100, 0, 255).astype(np.uint8)
+        o = one_pixel(kde_bits=4)
+        o.train(frames)
+        for c in range(3):
+            k = [sum(g[abs(v - int(frames[t, 0, c]))] if abs(v - int(frames[t, 0, c])) <= 12 else 0
+                     for t in range(N)) for v in range(256)]
+            M = max(k)
+            assert list(o.state.kde[0, c]) == [(15 * x + M // 2) // M for x in k]
+
+
+def test_kde4_and_kde8_round_the_same_density():
+    # both widths round k/M to the nearest level: q8 = 255 k/M + e8 and
+    # 17 q4 = 255 k/M + 17 e4 with |e| <= 1/2, so |17 q4 - q8| < 9; the top
+    # 8-bit level (k/M >= 254.5/255) lies inside the top 4-bit level
+    # (k/M >= 14.5/15)
+    rng = np.random.default_rng(5)
+    frames = rng.normal(128, 20, (40, 64, 3)).clip(0, 255).astype(np.uint8)
+    o8 = Oracle(default_params(64, 1, 3))
+    o4 = Oracle(dict(default_params(64, 1, 3), kde_bits=4))
+    o8.train(frames)
+    o4.train(frames)
+    q8 = o8.state.kde.astype(int)
+    q4 = o4.state.kde.astype(int)
+    assert q4.max() == 15 and np.all(np.abs(17 * q4 - q8) <= 8)
+    assert np.all(q4[q8 == 255] == 15) and np.all(q8[q4 < 15] < 255)
+
+
 # ---------------------------------------------------------------- residues
 def test_residue_classes_crafted_sequence():
     # Sec. 2 residue classes: R_t = max_c |I_t - I_{t-1}|; r1 = 10, r2 = 30.
@@ -450,6 +500,39 @@ def test_hand_confidence_terms():
     o.apply(np.array([[104, 100, 98]], np.uint8))
     c = (Fraction(1, 5) * (1 - Fraction(4, 255)) + Fraction(1, 5) * (1 - Fraction(4, 25))) / Fraction(2, 5)
     assert abs(o.state.conf[0] - float(Fraction(7, 16) + c / 8)) <= 1e-15
+
+
+def test_hand_confidence_prior_term_4bit():
+    # the 4-bit prior enters as the fraction q / 15 of its peak: level 12
+    # everywhere gives .6 * 12/15 in c, as the 8-bit level 204 = 17 * 12 does
+    c_rest = Fraction(1, 5) * (1 - Fraction(4, 255)) + Fraction(1, 5) * (1 - Fraction(4, 25))
+    for bits, level in ((4, 12), (8, 204)):
+        o = one_pixel(flags=ORC_CONF, kde_bits=bits, **HAND)
+        _hand_state(o)
+        o.state.kde[0] = level
+        o.apply(np.array([[104, 100, 98]], np.uint8))
+        c = Fraction(3, 5) * Fraction(12, 15) + c_rest
+        assert abs(o.state.conf[0] - float(Fraction(7, 16) + c / 8)) <= 1e-15, bits
+    # nullified iff q / 15 < q_null / 255, i.e. 17 q < q_null: level 1 stays
+    # at q_null = 17 (17 = 17) and drops at q_null = 18
+    for q_null, dropped in ((17, False), (18, True), (13, False)):
+        o = one_pixel(flags=ORC_CONF, kde_bits=4, q_null=q_null, **HAND)
+        _hand_state(o)
+        o.state.kde[0] = 1
+        o.apply(np.array([[104, 100, 98]], np.uint8))
+        c = c_rest / Fraction(2, 5) if dropped else Fraction(3, 5) * Fraction(1, 15) + c_rest
+        assert abs(o.state.conf[0] - float(Fraction(7, 16) + c / 8)) <= 1e-15, q_null
+    # level 0 is nullified at the default q_null = 13
+    o = one_pixel(flags=ORC_CONF, kde_bits=4, **HAND)
+    _hand_state(o)
+    o.state.kde[0] = 0
+    o.apply(np.array([[104, 100, 98]], np.uint8))
+    assert abs(o.state.conf[0] - float(Fraction(7, 16) + c_rest / Fraction(2, 5) / 8)) <= 1e-15
+
+
+def test_kde_bits_other_than_8_or_4_rejected():
+    with pytest.raises(Exception):
+        one_pixel(kde_bits=6).train(np.zeros((3, 1, 3), np.uint8))
 
 
 def test_confidence_modulates_rate_and_halts_rga():
