@@ -100,6 +100,10 @@ typedef struct cog_params {
                              /* temporal sampling"), in 64-pixel blocks with staggered    */
                              /* phases: frame n processes block b when (n + b) % S == 0   */
     int32_t skip_period;     /* S >= 1                                                    */
+    int32_t kde_bits;        /* scene-prior levels per channel value: 8 (q of 255, one     */
+                             /* byte each) or 4 (q of 15, two per byte: the even grey     */
+                             /* level in the low nibble); the prior enters as q / (2^bits */
+                             /* - 1) and is nullified below q_null / 255 either way       */
 } cog_params;
 
 /* Per-frame statistics (the stage occupancy n_i of the paper's speed-up
@@ -126,8 +130,10 @@ typedef struct cog_layout {
     uint64_t rec_bytes;      /* K*7*sizeof(dtype) rounded up to 16                       */
     uint64_t queue;          /* scratch: survivor queue, 32 segments of whole 1024-entry */
                              /* tiles, 16 bytes per entry                                */
-    uint64_t kde;            /* uint8[P][3][256]: peak-normalised prior                  */
+    uint64_t kde;            /* uint8[P][3][kde_row]: peak-normalised prior              */
     uint64_t elem_bytes;     /* sizeof(dtype)                                            */
+    uint64_t kde_row;        /* bytes per pixel and channel of the prior: 256 (8-bit) or */
+                             /* 128 (4-bit)                                              */
 } cog_layout;
 
 typedef struct cog_ctx cog_ctx;

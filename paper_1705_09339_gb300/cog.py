@@ -33,7 +33,7 @@ class cog_params(C.Structure):
         ("eta_conf", C.c_float), ("c_halt", C.c_float), ("w_illum", C.c_float),
         ("q_null", C.c_int32), ("kde_bw", C.c_int32), ("r1", C.c_int32), ("r2", C.c_int32),
         ("illum_permille", C.c_int32), ("flags", C.c_uint32), ("c_skip", C.c_float),
-        ("skip_period", C.c_int32),
+        ("skip_period", C.c_int32), ("kde_bits", C.c_int32),
     ]
 
 
@@ -70,7 +70,7 @@ class cog_server_stats(C.Structure):
 
 class cog_layout(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in ("total", "ctl", "jl", "conf", "s1", "s1_bytes", "gmm", "rec_bytes",
-                                          "queue", "kde", "elem_bytes")]
+                                          "queue", "kde", "elem_bytes", "kde_row")]
 
 
 class CogError(RuntimeError):
@@ -397,10 +397,23 @@ def _s1_view(buf, L, P, p):
     return vals.reshape(P, 6), qab, top
 
 
+def _prior_levels(rows: np.ndarray) -> np.ndarray:
+    """Prior rows [P, 3, kde_row] -> one level per grey value [P, 3, 256]
+    (4-bit rows hold level 2j in the low and 2j+1 in the high nibble of
+    byte j)."""
+    if rows.shape[2] == 256:
+        return rows
+    q = np.empty(rows.shape[:2] + (256,), np.uint8)
+    q[:, :, 0::2] = rows & 0xF
+    q[:, :, 1::2] = rows >> 4
+    return q
+
+
 def decode_state(buf: np.ndarray, p: cog_params) -> dict:
     """FP64 copies of the model planes of an exported state image:
     w [P,K], mu [P,K,3], var [P,K,3], rga_m [P,3], rga_v [P,3], conf [P],
-    label [P], prev [P,3], kde [P,3,256], qa [P], qb [P], top [P]; with
+    label [P], prev [P,3], kde [P,3,256] (levels of 255, or of 15 with
+    kde_bits = 4), qa [P], qb [P], top [P]; with
     COG_PERCHAN the weights are per channel: wc [P,3,K] instead of w."""
     L = cog_state_layout(p)
     P, K = p.width * p.height, p.K
@@ -421,7 +434,7 @@ def decode_state(buf: np.ndarray, p: cog_params) -> dict:
         recs = _bf16_to_f32(_plane(buf, L.gmm, Pp * rec_elems, np.uint16)).astype(np.float64)
     else:
         recs = _plane(buf, L.gmm, Pp * rec_elems, _NP_DT[p.state_dtype]).astype(np.float64)
-    kde = buf[L.kde:L.kde + P * 768].reshape(P, 3, 256)
+    kde = _prior_levels(buf[L.kde:L.kde + P * 3 * L.kde_row].reshape(P, 3, L.kde_row))
     out = dict(rga_m=s1[:, :3].copy(), rga_v=s1[:, 3:].copy(), conf=conf, label=label, prev=prev,
                kde=kde, qa=(qab & 0xFF).astype(np.uint8), qb=(qab >> 8).astype(np.uint8), top=top)
     if p.flags & COG_PERCHAN:
@@ -479,7 +492,10 @@ def encode_state(buf: np.ndarray, p: cog_params, st: dict) -> np.ndarray:
         recs[:P, :7 * K] = r
     g = _to_storage(recs, p.state_dtype)
     out[L.gmm:L.gmm + g.nbytes] = g.view(np.uint8).reshape(-1)
-    out[L.kde:L.kde + P * 768] = np.asarray(st["kde"], np.uint8).reshape(-1)
+    q = np.asarray(st["kde"], np.uint8).reshape(P, 3, 256)
+    if L.kde_row == 128:
+        q = (q[:, :, 0::2] & 0xF) | ((q[:, :, 1::2] & 0xF) << 4)
+    out[L.kde:L.kde + P * 3 * L.kde_row] = q.reshape(-1)
     return out
 
 

@@ -72,7 +72,8 @@ bool make_layout(const cog_params &p, Layout &L)
     const int64_t ctas = (L.P + K1_TILE - 1) / K1_TILE;
     L.qseg_cap = (ctas + QSEG - 1) / QSEG * K1_TILE;
     L.queue = o; o = up(o + (size_t)(QSEG * L.qseg_cap) * 16, 256);
-    L.kde = o;  o = up(o + (size_t)L.P * 768, 256);
+    L.kde_row = p.kde_bits == 4 ? 128 : 256;
+    L.kde = o;  o = up(o + (size_t)L.P * 3 * L.kde_row, 256);
     L.total = o;
     return true;
 }
@@ -149,6 +150,7 @@ static const char *check_params(const cog_params *p)
     if (!(p->w_illum > 0.f && p->w_illum < 1.f)) return "w_illum must be in (0, 1)";
     if (p->q_null < 0 || p->q_null > 256) return "q_null must be in 0..256";
     if (p->kde_bw < 1 || p->kde_bw > 32) return "kde_bw must be in 1..32";
+    if (p->kde_bits != 8 && p->kde_bits != 4) return "kde_bits must be 8 or 4";
     if (p->r1 < 0 || p->r2 < p->r1) return "need 0 <= r1 <= r2";
     if (p->illum_permille < 0 || p->illum_permille > 1000) return "illum_permille must be in 0..1000";
     if (p->flags & ~(COG_ALL | COG_SAMPLE | COG_MODE1 | COG_PERCHAN)) return "unknown flag bits";
@@ -186,6 +188,7 @@ void cog_default_params(cog_params *p, int32_t width, int32_t height, int32_t K)
     p->flags = COG_ALL;
     p->c_skip = 0.95f;
     p->skip_period = 4;
+    p->kde_bits = 8;
 }
 
 cog_status cog_state_layout(const cog_params *p, cog_layout *out)
@@ -196,7 +199,7 @@ cog_status cog_state_layout(const cog_params *p, cog_layout *out)
     make_layout(*p, L);
     out->total = L.total; out->ctl = L.ctl; out->jl = L.jl; out->conf = L.conf; out->s1 = L.s1;
     out->s1_bytes = L.s1_bytes; out->gmm = L.gmm; out->rec_bytes = L.rec_bytes; out->queue = L.queue;
-    out->kde = L.kde; out->elem_bytes = L.elem;
+    out->kde = L.kde; out->elem_bytes = L.elem; out->kde_row = L.kde_row;
     return COG_OK;
 }
 
@@ -267,6 +270,7 @@ cog_status cog_create(const cog_params *p, void *cuda_stream, void *state_dev, c
     d.illum_permille = p->illum_permille;
     d.c_skip = p->c_skip;
     d.skip_period = p->skip_period;
+    d.kde_bits = p->kde_bits;
     StatePtrs &s = c->sp;
     s.ctl = (uint32_t *)(c->state + c->L.ctl);
     s.jl = (uint32_t *)(c->state + c->L.jl);

@@ -433,7 +433,7 @@ __device__ __forceinline__ void s2_load(const ApplyArgs &A, int64_t qi, S2In<T, 
     in.e = __ldcg(A.s.queue + qi);
     const int64_t p = in.e.x;
 #pragma unroll
-    for (int c = 0; c < 3; c++) in.qk[c] = __ldg(A.s.kde + (p * 3 + c) * 256 + ((in.e.y >> (8 * c)) & 0xffu));
+    for (int c = 0; c < 3; c++) in.qk[c] = prior_level(A.s.kde, p, c, (in.e.y >> (8 * c)) & 0xffu, A.dp.kde_bits == 4);
     const uint4 *src = reinterpret_cast<const uint4 *>(A.s.gmm + p * RecSel<T, K, PC>::BYTES);
 #pragma unroll
     for (int i = 0; i < RecSel<T, K, PC>::NV; i++) in.rec[i] = src[i];
@@ -441,8 +441,8 @@ __device__ __forceinline__ void s2_load(const ApplyArgs &A, int64_t qi, S2In<T, 
 }
 
 // Confidence of a pixel decided at stage 2 (Sec. 2, "Confidence Measure"):
-// prior term from the smallest of the three prior bytes, unless the prior
-// is nullified (that minimum below q_null).
+// prior term from the smallest of the three prior levels (0..255 scale),
+// unless the prior is nullified (that minimum below q_null).
 __device__ __forceinline__ float conf_stage2(const DevParams &dp, const uint32_t qk[3], uint32_t qab, int D, float Cm,
                                              float Mh)
 {

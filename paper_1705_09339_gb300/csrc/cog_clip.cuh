@@ -173,7 +173,7 @@ __device__ CLIP_S2_INLINE void clip_s2(const ClipArgs &A, ClipWarp<T, G> &V, int
     for (int i = 0; i < RNV; i++) raw[i] = src[i];
     uint32_t qk[3];
 #pragma unroll
-    for (int c = 0; c < 3; c++) qk[c] = __ldg(A.s.kde + (p * 3 + c) * 256 + ((sv.x >> (8 * c)) & 0xffu));
+    for (int c = 0; c < 3; c++) qk[c] = prior_level(A.s.kde, p, c, (sv.x >> (8 * c)) & 0xffu, dp.kde_bits == 4);
     const uint32_t bit = 1u << (slot & 31);
     if (!(V.touched[slot >> 5] & bit)) {
         uint4 *u = reinterpret_cast<uint4 *>(A.undo_gmm + p * RB);

@@ -351,6 +351,18 @@ __device__ __forceinline__ float conf_next(const DevParams &dp, float Cm, float 
     return __fmaf_rn(__fsub_rn(1.f, dp.eta), Cm, __fmul_rn(dp.eta, ci));
 }
 
+// The scene prior's level for channel c of pixel p at grey level v, on the
+// 0..255 scale the confidence and the nullification test use (Sec. 2,
+// "Scene Prior in Background Model"): the stored byte of the 8-bit prior,
+// or 17 times the 4-bit level (q / 15 = 17 q / 255), read from the nibble
+// the level occupies (even v low, odd v high).
+__device__ __forceinline__ uint32_t prior_level(const uint8_t *kde, int64_t p, int c, uint32_t v, bool four_bit)
+{
+    if (!four_bit) return __ldg(kde + (p * 3 + c) * 256 + v);
+    const uint32_t b = __ldg(kde + (p * 3 + c) * 128 + (v >> 1));
+    return 17u * ((b >> ((v & 1u) << 2)) & 15u);
+}
+
 // Decisions are taken in division-free form: the rank order compares
 // w_j^2 (v_k0+v_k1+v_k2) with w_k^2 (v_j0+v_j1+v_j2) (the mean's 1/3
 // cancels), and a channel matches when (I-mu)^2 < lam^2 v.  These differ

@@ -59,6 +59,7 @@ struct DevParams {
     int illum_permille;
     float c_skip;
     int skip_period;
+    int kde_bits;       // 8: one prior level per byte; 4: two per byte
 };
 
 struct StatePtrs {
@@ -72,11 +73,11 @@ struct StatePtrs {
                         // puts up to K1_TILE survivors into segment
                         // blockIdx % QSEG, so a segment holds
                         // ceil(CTAs / QSEG) whole tiles
-    uint8_t *kde;       // prior, [P][3][256]
+    uint8_t *kde;       // prior, [P][3][256] levels, or [P][3][128] nibble pairs (4-bit)
 };
 
 struct Layout {
-    size_t total, ctl, jl, conf, s1, s1_bytes, gmm, rec_bytes, queue, kde, elem;
+    size_t total, ctl, jl, conf, s1, s1_bytes, gmm, rec_bytes, queue, kde, elem, kde_row;
     int64_t P, Pp;
     int64_t qseg_cap;   // survivor-queue entries per segment
 };

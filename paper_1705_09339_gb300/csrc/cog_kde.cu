@@ -3,8 +3,11 @@
 // with a Gaussian kernel of bandwidth bw, evaluated on the 256 grey levels in
 // exact integer arithmetic and normalised to its peak:
 //   h[u] = #{t : I_t = u},  k[v] = sum_{|v-u| <= 3bw} h[u] g[|v-u|],
-//   q[v] = (255 k[v] + M/2) div M,  M = max_v k[v],
-// with g[d] = round(2^16 exp(-d^2 / (2 bw^2))) computed on the host.
+//   q[v] = (Q k[v] + M/2) div M,  M = max_v k[v],
+// with g[d] = round(2^16 exp(-d^2 / (2 bw^2))) computed on the host and
+// Q = 255 for the 8-bit prior (one byte per level, 256-byte rows) or 15 for
+// the 4-bit one (two levels per byte, the even grey level in the low
+// nibble, 128-byte rows).
 //
 // Layout: warp w owns the 32 channel histograms b = 32w .. 32w + 31 (b =
 // 3p + c, the prior's row order), so its lanes read 32 consecutive bytes of
@@ -32,6 +35,7 @@ constexpr int KDE_SMEM = KDE_WARPS * 32 * KDE_ROW * 2 + KDE_WARPS * 256;   // ro
 struct KdeW {
     uint32_t g[100];
     int R;
+    uint32_t Q;   // top level: 255 (8-bit prior) or 15 (4-bit)
 };
 
 // k[v] = sum over |d| <= R of h[v + d] g[|d|], h zero outside [vmin, vmax]
@@ -56,10 +60,10 @@ __device__ __forceinline__ uint32_t kde_density_r(const uint16_t *h, int v, cons
     return acc;
 }
 
-// q = floor((255 k + M/2) / M), exactly: a float estimate, then corrected
-__device__ __forceinline__ uint32_t kde_quant(uint32_t k, uint64_t M, float rM)
+// q = floor((Q k + M/2) / M), exactly: a float estimate, then corrected
+__device__ __forceinline__ uint32_t kde_quant(uint32_t k, uint64_t M, float rM, uint32_t Q)
 {
-    const uint64_t num = 255ull * k + M / 2;
+    const uint64_t num = (uint64_t)Q * k + M / 2;
     uint32_t q = (uint32_t)((float)num * rM);
     while (q > 0 && (uint64_t)q * M > num) q--;
     while ((uint64_t)(q + 1) * M <= num) q++;
@@ -96,7 +100,8 @@ __global__ void __launch_bounds__(KDE_TPB) kde_kernel(int64_t P, const uint8_t *
     // the density: the warp takes its 32 histograms one after another, its
     // lanes on consecutive levels of the support (conflict-free reads of
     // one row), keeps the values in registers for the peak M, and writes
-    // the 256-byte row through a per-warp staging line
+    // the row (256 levels, or 128 bytes of level pairs) through a per-warp
+    // staging line
     uint8_t *stage = reinterpret_cast<uint8_t *>(kh + KDE_TPB * KDE_ROW) + warp * 256;
     const int lo_l = max(0, vmin - w.R), hi_l = act ? min(255, vmax + w.R) : -1;
     __syncwarp();
@@ -125,10 +130,17 @@ __global__ void __launch_bounds__(KDE_TPB) kde_kernel(int64_t P, const uint8_t *
 #pragma unroll
         for (int i = 0; i < 8; i++) {
             const int v = LO + lane + 32 * i;
-            if (LO + 32 * i <= HI && v <= HI) stage[v] = (uint8_t)kde_quant(kv[i], M, rM);
+            if (LO + 32 * i <= HI && v <= HI) stage[v] = (uint8_t)kde_quant(kv[i], M, rM, w.Q);
         }
         __syncwarp();
-        reinterpret_cast<uint2 *>(kde + bl * 256)[lane] = *reinterpret_cast<const uint2 *>(stage + 8 * lane);
+        const uint2 lv = *reinterpret_cast<const uint2 *>(stage + 8 * lane);   // levels 8 lane .. 8 lane + 7
+        if (w.Q == 255u) {
+            reinterpret_cast<uint2 *>(kde + bl * 256)[lane] = lv;
+        } else {
+            // levels < 16: byte j of the row is level 2j | level 2j+1 << 4
+            const uint32_t lo = lv.x | (lv.x >> 4), hi = lv.y | (lv.y >> 4);
+            reinterpret_cast<uint32_t *>(kde + bl * 128)[lane] = __byte_perm(lo, hi, 0x6420);
+        }
         __syncwarp();   // the staging line is rewritten for the next histogram
     }
 }
@@ -137,9 +149,11 @@ cudaError_t launch_kde_train(const DevParams &dp, const StatePtrs &s, const uint
                              int n_frames, const uint32_t *g, int R, cudaStream_t st)
 {
     if (R < 0 || R > 96) return cudaErrorInvalidValue;
+    if (dp.kde_bits != 8 && dp.kde_bits != 4) return cudaErrorInvalidValue;
     KdeW w;
     for (int d = 0; d < 100; d++) w.g[d] = d <= R ? g[d] : 0u;
     w.R = R;
+    w.Q = (1u << dp.kde_bits) - 1u;
     if (n_frames >= 65536) return cudaErrorInvalidValue;   // uint16 counts
     static_assert(KDE_PAD >= 12, "the unrolled taps read 12 levels past the bins");
     auto kern = R == 12 ? kde_kernel<12> : kde_kernel<0>;

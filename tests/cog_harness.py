@@ -8,7 +8,7 @@ import numpy as np
 # actually receives so the two compute with identical constants
 BASE = dict(alpha=0.01, lambda_=2.5, T_bg=0.7, w_init=0.05, var_init=225.0, var_min=4.0,
             var_max=900.0, tau_fd=8.0, eta=0.125, c_halt=0.9, w_illum=0.75, q_null=13, kde_bw=4,
-            r1=10, r2=30, illum_permille=700, flags=15, c_skip=0.95, skip_period=4)
+            r1=10, r2=30, illum_permille=700, flags=15, c_skip=0.95, skip_period=4, kde_bits=8)
 FLOATS = ("alpha", "lambda_", "T_bg", "w_init", "var_init", "var_min", "var_max", "tau_fd", "eta",
           "c_halt", "w_illum", "c_skip")
 
@@ -125,7 +125,7 @@ def oracle_state(o):
                 prev=s.prev, kde=s.kde, qa=s.qa, qb=s.qb, top=s.top, wc=s.wc)
 
 
-def random_state(rng, P, K, dtype="f32", fg_frac=0.2, mode1=False, perchan=False):
+def random_state(rng, P, K, dtype="f32", fg_frac=0.2, mode1=False, perchan=False, kde_bits=8):
     """A seeded model state with the value ranges the method produces,
     rounded to the storage type so both sides start from the same values."""
     q = {"f32": np.float32, "f16": np.float16, "bf16": None}[dtype]
@@ -149,8 +149,13 @@ def random_state(rng, P, K, dtype="f32", fg_frac=0.2, mode1=False, perchan=False
     conf = rng.uniform(0, 1, P)
     qa = rng.integers(0, 256, P)
     qb = np.minimum(rng.integers(0, 256, P), 255 - qa)
-    kde = rng.integers(0, 256, (P, 3, 256)).astype(np.uint8)
-    kde[rng.random((P, 3, 256)) < 0.3] = rng.integers(0, 13)
+    if kde_bits == 4:
+        # levels of 15; level 0 (17 * 0 < q_null = 13) is the nullified one
+        kde = rng.integers(0, 16, (P, 3, 256)).astype(np.uint8)
+        kde[rng.random((P, 3, 256)) < 0.3] = 0
+    else:
+        kde = rng.integers(0, 256, (P, 3, 256)).astype(np.uint8)
+        kde[rng.random((P, 3, 256)) < 0.3] = rng.integers(0, 13)
     prev = rng.integers(0, 256, (P, 3)).astype(np.uint8)
     label = (rng.random(P) < fg_frac).astype(np.uint8)
     # COG_MODE1 keeps the stage-1 record equal to the rank-1 mode it mirrors

@@ -31,9 +31,9 @@ def test_library_exports_every_declared_function(cog):
 
 def test_struct_sizes_match_header(cog):
     import ctypes as C
-    assert C.sizeof(cog.cog_params) == 4 * 23
+    assert C.sizeof(cog.cog_params) == 4 * 24
     assert C.sizeof(cog.cog_stats) == 8 * 7 + 8
-    assert C.sizeof(cog.cog_layout) == 8 * 11
+    assert C.sizeof(cog.cog_layout) == 8 * 12
     # 2 int32, 3 + 3 + 6 + 6 int64, 6 + 6 + 3 + 9 + 3 double
     assert C.sizeof(cog.cog_group_stats) == 8 + 8 * 18 + 8 * 27
 
@@ -46,7 +46,7 @@ def test_default_params_and_layout(cog):
     P = 1920 * 1080
     Pp = (P + 4095) // 4096 * 4096
     assert L.rec_bytes == 80 and L.elem_bytes == 2
-    assert L.kde + P * 768 <= L.total
+    assert L.kde_row == 256 and L.kde + P * 768 <= L.total
     for off in (L.jl, L.conf, L.s1, L.gmm, L.queue, L.kde):
         assert off % 256 == 0
     assert L.s1_bytes == 16 and L.gmm - L.s1 >= Pp * 16 and L.kde - L.queue >= Pp * 16
@@ -65,13 +65,18 @@ def test_default_params_and_layout(cog):
     pc = cog.cog_default_params(1920, 1080, 5, state_dtype="f16")
     pc.flags |= cog.COG_PERCHAN
     assert cog.cog_state_layout(pc).rec_bytes == 96
+    # the 4-bit prior: 128-byte rows, half the 8-bit prior's 768 bytes per pixel
+    p4 = cog.cog_default_params(1920, 1080, 5, state_dtype="f16", kde_bits=4)
+    L4 = cog.cog_state_layout(p4)
+    assert L4.kde_row == 128 and L4.kde == L.kde and L4.kde + P * 384 <= L4.total
+    assert L.total - L4.total >= P * 384 - 256
 
 
 @pytest.mark.parametrize("field,value", [("K", 0), ("K", 9), ("width", 0), ("alpha", 0.0), ("alpha", 1.5),
                                          ("var_min", 0.0), ("kde_bw", 0), ("kde_bw", 33), ("r2", -1),
                                          ("illum_permille", 1001), ("flags", 128), ("flags", 15 | 32 | 64),
                                          ("state_dtype", 3), ("skip_period", 0),
-                                         ("w_illum", 1.0), ("T_bg", 1.5)])
+                                         ("w_illum", 1.0), ("T_bg", 1.5), ("kde_bits", 0), ("kde_bits", 6)])
 def test_invalid_params_rejected(cog, field, value):
     p = cog.cog_default_params(64, 48, 3)
     setattr(p, field, value)
@@ -135,3 +140,34 @@ def test_header_compiles_as_c99_and_cpp11(tmp_path):
         r = subprocess.run([cc, std, "-Wall", "-Wextra", "-Werror", "-I", inc, "-c", str(src), "-o",
                             str(tmp_path / f"h_{ext}.o")], capture_output=True, text=True)
         assert r.returncode == 0, r.stderr
+
+
+def test_ctypes_structs_match_the_header(cog, tmp_path):
+    """Every struct the binding mirrors has the size and field offsets the
+    C compiler gives the header's declaration."""
+    import ctypes as C
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not found")
+    structs = {"cog_params": cog.cog_params, "cog_layout": cog.cog_layout, "cog_stats": cog.cog_stats,
+               "cog_group_stats": cog.cog_group_stats, "cog_server_stats": cog.cog_server_stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cog.h"', 'int main(void) {']
+    for name, ct in structs.items():
+        lines.append(f'    printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in ct._fields_:
+            cf = "lambda" if f == "lambda_" else f
+            lines.append(f'    printf("{name}.{f} %zu\\n", offsetof({name}, {cf}));')
+    lines += ['    return 0;', '}']
+    src = tmp_path / "sz.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "sz"
+    r = subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                 check=True).stdout.splitlines())
+    for name, ct in structs.items():
+        assert int(got[name]) == C.sizeof(ct), name
+        for f, _ in ct._fields_:
+            assert int(got[f"{name}.{f}"]) == getattr(ct, f).offset, (name, f)

@@ -19,10 +19,11 @@ def cog():
     return cog
 
 
-# "+pc": per-channel mixtures (a group of its own in the batch)
+# "+pc": per-channel mixtures (a group of its own in the batch); "+q4": the
+# 4-bit scene prior (in the same group as the 8-bit streams)
 SPECS = [(160, 120, 3, "f32"), (320, 240, 5, "f16"), (97, 61, 3, "f32"), (640, 480, 5, "f16"),
          (33, 1, 5, "f16"), (200, 100, 3, "bf16"), (160, 120, 5, "f16"), (128, 96, 5, "f16+pc"),
-         (64, 48, 3, "f32+pc")]
+         (64, 48, 3, "f32+pc"), (176, 144, 5, "f16+q4"), (45, 31, 3, "f32+pc+q4")]
 
 
 def _streams(n_train=20, n_test=6):
@@ -36,10 +37,12 @@ def _streams(n_train=20, n_test=6):
 
 
 def _ctx(cog, w, h, k, dt, fr, n_train, stream):
-    base, _, pc = dt.partition("+")
+    base, *opts = dt.split("+")
     p = cog.cog_default_params(w, h, k, state_dtype=base)
-    if pc:
+    if "pc" in opts:
         p.flags |= cog.COG_PERCHAN
+    if "q4" in opts:
+        p.kde_bits = 4
     c = cog.cog_create(p, stream)
     t = torch.from_numpy(fr[:n_train].reshape(n_train, h, w, 3)).cuda()
     cog.cog_train_prior(c, t, n_train)
@@ -101,8 +104,9 @@ def test_batch_matches_oracle_with_inactive_steps(cog):
     # cog_batch_apply_active with each stream idle on some steps; every
     # stream is compared with its own FP64 oracle run over the frames it
     # actually received: masks identical on every pixel with no decision
-    # near a threshold so far, state within 1e-4 relative there
-    specs = [(97, 61, 3), (160, 120, 5), (33, 7, 5), (200, 100, 3)]
+    # near a threshold so far, state within 1e-4 relative there; two of the
+    # streams keep the 4-bit prior
+    specs = [(97, 61, 3, 8), (160, 120, 5, 4), (33, 7, 5, 8), (200, 100, 3, 4)]
     NT, NF = 40, 30
     s = torch.cuda.Stream()      # a graph cannot be captured on the legacy default stream
     with torch.cuda.stream(s):
@@ -113,10 +117,10 @@ def _batch_vs_oracle(cog, specs, NT, NF, s):
     from cog_harness import GpuRun, oracle_run, oracle_state, params, state_errors
     from cogsynth import Scene
     runs = []
-    for i, (w, h, k) in enumerate(specs):
+    for i, (w, h, k, bits) in enumerate(specs):
         sc = Scene(w, h, 90 + i, kind="dynamic", n_train=NT, fg_frac=0.05, switch_at=12 + 3 * i)
         fr, _ = sc.frames(0, NT + NF)
-        d = params(w, h, k)
+        d = params(w, h, k, kde_bits=bits)
         g = GpuRun(d, "f32")
         g.train(fr[:NT])
         runs.append((w, h, k, fr, d, g))
