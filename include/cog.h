@@ -226,13 +226,25 @@ cog_status cog_clip_runs(cog_ctx *ctx, int32_t *runs);
  *   their masks.  Frames submitted meanwhile join the next step, whose
  *   uploads overlap the running one.
  *   cog_server_add: a further trained context joins the running server as
- *     stream *stream_out (the next index).  The worker takes it between
- *     steps: once no step is on the GPU (at most 30 s) it rebuilds the batch
- *     over all the contexts, so frames of the other streams wait for that
- *     rebuild.  Allocates the new stream's slots; returns when it has
- *     joined; COG_ERR_TIMEOUT after 60 s, COG_ERR_STATE if the server is
- *     stopping, COG_ERR_INVALID_ARG for a context the server already has.
- *     A failed join leaves the server and its status unchanged.
+ *     stream *stream_out: the lowest index a camera has left, else the next
+ *     index.  The worker takes it between steps: once no step is on the GPU
+ *     (at most 30 s) it rebuilds the batch over all the contexts, so frames
+ *     of the other streams wait for that rebuild.  Allocates the new
+ *     stream's slots; returns when it has joined; COG_ERR_TIMEOUT after
+ *     60 s, COG_ERR_STATE if the server is stopping, COG_ERR_INVALID_ARG for
+ *     a context the server already has.  A failed join leaves the server
+ *     and its status unchanged.
+ *   cog_server_remove: camera `stream` leaves the running server.  Frames
+ *     submitted for it from then on are refused (COG_ERR_INVALID_ARG); those
+ *     already submitted are completed.  Once none is waiting or on the GPU,
+ *     the worker rebuilds the batch without it between steps, as for a
+ *     join, and frees its slots; the call then returns and hands the context
+ *     back in *ctx_out (nullable): it belongs to the caller again (destroy
+ *     it, use it alone, or add it again).  The other cameras keep their
+ *     indices; the next join takes this one.  COG_ERR_INVALID_ARG for an
+ *     index that is not a serving camera or for the last camera (destroy the
+ *     server instead), COG_ERR_TIMEOUT after 60 s (the camera then stays),
+ *     COG_ERR_STATE if the server is stopping.
  *   cog_server_drain: waits up to timeout_ms until every submitted frame is
  *     done; COG_ERR_TIMEOUT otherwise.
  *   cog_server_read_stats: counts and the p50/p99/max latency from submission
@@ -255,6 +267,7 @@ typedef struct {
 cog_status cog_server_create(cog_ctx *const *ctxs, int32_t n, cog_server **out);
 cog_status cog_server_submit(cog_server *s, int32_t stream, const uint8_t *frame_host, uint8_t *mask_host);
 cog_status cog_server_add(cog_server *s, cog_ctx *ctx, int32_t *stream_out);
+cog_status cog_server_remove(cog_server *s, int32_t stream, cog_ctx **ctx_out);
 cog_status cog_server_drain(cog_server *s, int32_t timeout_ms);
 cog_status cog_server_read_stats(cog_server *s, cog_server_stats *out);
 /* Per-frame record in completion order: submission time since creation and

@@ -122,6 +122,7 @@ def _load() -> C.CDLL:
         "cog_server_create": (C.c_int, [P(vp), i32, P(vp)]),
         "cog_server_submit": (C.c_int, [vp, i32, vp, vp]),
         "cog_server_add": (C.c_int, [vp, vp, P(i32)]),
+        "cog_server_remove": (C.c_int, [vp, i32, P(vp)]),
         "cog_server_drain": (C.c_int, [vp, i32]),
         "cog_server_read_stats": (C.c_int, [vp, P(cog_server_stats)]),
         "cog_server_read_latencies": (C.c_int, [vp, vp, vp, C.c_int64, P(C.c_int64)]),
@@ -521,6 +522,14 @@ def cog_server_add(srv, ctx) -> int:
     idx = C.c_int32(-1)
     _scheck(lib.cog_server_add(srv, ctx, C.byref(idx)), srv)
     return idx.value
+
+
+def cog_server_remove(srv, stream: int) -> C.c_void_p:
+    """Camera `stream` leaves the running server once its submitted frames
+    are done; returns its context, which belongs to the caller again."""
+    ctx = C.c_void_p()
+    _scheck(lib.cog_server_remove(srv, int(stream), C.byref(ctx)), srv)
+    return ctx
 
 
 def cog_server_submit(srv, stream: int, frame_host, mask_host) -> None:

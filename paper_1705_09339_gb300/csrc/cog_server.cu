@@ -12,9 +12,11 @@
 // downloads and records every frame's latency from submission to its mask
 // being in host memory.  Every wait is bounded by a condition-variable
 // timeout or by a CUDA event of work already enqueued (polled, then waited
-// for in short naps).  A camera can join a
-// running server: between steps, once no step is on the GPU, the worker
-// rebuilds the batch over all the contexts.
+// for in short naps).  Cameras can join and leave a running server: between
+// steps, once no step is on the GPU, the worker rebuilds the batch over the
+// contexts that remain.  A leaving camera's submitted frames are completed
+// first; its stream index is given to the next camera that joins, so the
+// other cameras keep theirs.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -63,6 +65,8 @@ struct Pending {
 };
 
 struct Stream {
+    cog_ctx *ctx = nullptr;                  // nullptr: the camera left (index free)
+    bool leaving = false;                    // cog_server_remove called: no new frames
     int64_t P = 0;
     uint8_t *slot[2] = {nullptr, nullptr};   // device frame slots
     uint8_t *mslot[2] = {nullptr, nullptr};  // device mask slots
@@ -95,6 +99,16 @@ struct AddReq {
     char msg[256] = {0};
 };
 
+// A camera leaving: taken by the worker once its stream has no frame waiting
+// or on the GPU.
+struct LeaveReq {
+    int index = -1;
+    cog_ctx *ctx = nullptr;   // the context handed back
+    cog_status st = COG_OK;
+    bool done = false;
+    char msg[256] = {0};
+};
+
 }  // namespace
 
 struct cog_server {
@@ -104,8 +118,10 @@ struct cog_server {
     cudaEvent_t copied = nullptr, applied = nullptr;
     std::vector<Stream> streams;
     std::vector<cog_ctx *> ctxs;         // the batch's contexts, in stream order
+    std::vector<int> bpos;               // stream index -> position in the batch (-1: left)
     std::deque<AddReq *> adds;           // cameras waiting to join (owned by their callers)
-    std::condition_variable cv_added;    // add requests handled
+    std::deque<LeaveReq *> leaves;       // cameras waiting to leave (owned by their callers)
+    std::condition_variable cv_added;    // join and leave requests handled
     std::mutex mu;                       // streams' queues, counts, statistics, adds
     std::condition_variable cv_work;     // work arrived or a slot freed
     std::condition_variable cv_idle;     // a step completed
@@ -142,7 +158,16 @@ static cog_status server_err(cog_server *s, cog_status st, const char *fmt, ...)
     return st;
 }
 
-static void fail_adds(cog_server *s, cog_status st, const char *why)
+// A leave request whose stream has nothing waiting and nothing on the GPU.
+static bool leave_ready(const cog_server *s, const LeaveReq *l)
+{
+    const Stream &q = s->streams[l->index];
+    return q.pending.empty() && q.inflight == 0;
+}
+
+// Fails the waiting join requests and the leave requests in `which` (all
+// of them when null).  A leave that fails leaves its camera serving.
+static void fail_members(cog_server *s, cog_status st, const char *why, const std::vector<LeaveReq *> *which = nullptr)
 {
     for (AddReq *a : s->adds) {
         a->st = st;
@@ -150,49 +175,118 @@ static void fail_adds(cog_server *s, cog_status st, const char *why)
         snprintf(a->msg, sizeof a->msg, "%s", why);
     }
     s->adds.clear();
+    std::deque<LeaveReq *> keep;
+    for (LeaveReq *l : s->leaves) {
+        if (which && std::find(which->begin(), which->end(), l) == which->end()) {
+            keep.push_back(l);
+            continue;
+        }
+        l->st = st;
+        l->done = true;
+        snprintf(l->msg, sizeof l->msg, "%s", why);
+        s->streams[l->index].leaving = false;
+    }
+    s->leaves.swap(keep);
     s->cv_added.notify_all();
 }
 
-// Joins the waiting cameras (called by the worker with s->mu held): waits,
-// at most 30 s, until no step is on the GPU, rebuilds the batch over the old
-// and the new contexts, and appends the new streams.  On failure the old
-// batch stays and the requests carry the error.
-static void server_join(cog_server *s, std::unique_lock<std::mutex> &lk)
+// Stream index -> position in the batch, from the streams' contexts.
+static void rebuild_positions(cog_server *s)
 {
-    const clk::time_point until = clk::now() + std::chrono::seconds(30);
-    auto busy = [&] {
-        for (const Stream &q : s->streams)
-            if (q.inflight) return true;
-        return false;
+    s->ctxs.clear();
+    s->bpos.assign(s->streams.size(), -1);
+    for (size_t i = 0; i < s->streams.size(); i++)
+        if (s->streams[i].ctx) {
+            s->bpos[i] = (int)s->ctxs.size();
+            s->ctxs.push_back(s->streams[i].ctx);
+        }
+}
+
+// Takes the waiting joins and the leaves whose streams are drained (called
+// by the worker with s->mu held): waits, at most 30 s, until no step is on
+// the GPU, rebuilds the batch over the cameras that stay and those that
+// join, frees the leaving streams' slots and gives each joining camera the
+// lowest free stream index (else the next one).  On failure the old batch
+// and membership stay and the requests carry the error.
+static void server_rebuild(cog_server *s, std::unique_lock<std::mutex> &lk)
+{
+    // the requests are read again after every wait: a caller whose own
+    // time limit ran out meanwhile has withdrawn its request
+    auto ready = [&] {
+        std::vector<LeaveReq *> v;
+        for (LeaveReq *l : s->leaves)
+            if (leave_ready(s, l)) v.push_back(l);
+        return v;
     };
-    while (busy() && s->sticky == COG_OK) {
-        if (s->cv_idle.wait_until(lk, until) == std::cv_status::timeout && busy()) {
-            fail_adds(s, COG_ERR_TIMEOUT, "the running steps did not finish within 30 s");
+    if (s->adds.empty() && ready().empty()) return;
+    const clk::time_point until = clk::now() + std::chrono::seconds(30);
+    while (s->steps_in_flight > 0 && s->sticky == COG_OK) {
+        if (s->cv_idle.wait_until(lk, until) == std::cv_status::timeout && s->steps_in_flight > 0) {
+            const std::vector<LeaveReq *> go = ready();
+            fail_members(s, COG_ERR_TIMEOUT, "the running steps did not finish within 30 s", &go);
             return;
         }
     }
+    const std::vector<LeaveReq *> go = ready();
+    if (s->adds.empty() && go.empty()) return;
     if (s->sticky != COG_OK) {
-        fail_adds(s, s->sticky, "the server failed");
+        fail_members(s, s->sticky, "the server failed");
         return;
     }
-    std::vector<cog_ctx *> all = s->ctxs;
-    for (AddReq *a : s->adds) all.push_back(a->ctx);
+    // the new membership: streams that stay, then the joining cameras in
+    // the free indices, lowest first
+    std::vector<cog_ctx *> keep(s->streams.size(), nullptr);
+    for (size_t i = 0; i < s->streams.size(); i++) keep[i] = s->streams[i].ctx;
+    for (LeaveReq *l : go) keep[l->index] = nullptr;
+    std::vector<int> where;
+    for (AddReq *a : s->adds) {
+        int idx = -1;
+        for (size_t i = 0; i < keep.size() && idx < 0; i++)
+            if (!keep[i]) idx = (int)i;
+        if (idx < 0) {
+            idx = (int)keep.size();
+            keep.push_back(nullptr);
+        }
+        keep[idx] = a->ctx;
+        where.push_back(idx);
+    }
+    std::vector<cog_ctx *> all;
+    for (cog_ctx *c : keep)
+        if (c) all.push_back(c);
+    if (all.empty()) {
+        fail_members(s, COG_ERR_INVALID_ARG, "the last camera cannot leave", &go);
+        return;
+    }
     cog_batch *nb = nullptr;
     const cog_status st = cog_batch_create(all.data(), (int32_t)all.size(), s->compute, &nb);
     if (st != COG_OK) {
-        fail_adds(s, st, cog_batch_last_error_string(nullptr));
+        fail_members(s, st, cog_batch_last_error_string(nullptr), &go);
         return;
     }
     cog_batch_destroy(s->batch);   // idle: every step that used it has completed
     s->batch = nb;
-    s->ctxs = all;
-    for (AddReq *a : s->adds) {
-        s->streams.push_back(std::move(a->q));
+    for (LeaveReq *l : go) {
+        Stream &q = s->streams[l->index];
+        for (int k = 0; k < 2; k++) {
+            if (q.slot[k]) cudaFree(q.slot[k]);
+            if (q.mslot[k]) cudaFree(q.mslot[k]);
+        }
+        l->ctx = q.ctx;
+        q = Stream();
+        l->done = true;
+        s->leaves.erase(std::remove(s->leaves.begin(), s->leaves.end(), l), s->leaves.end());
+    }
+    if (s->streams.size() < keep.size()) s->streams.resize(keep.size());
+    for (size_t j = 0; j < s->adds.size(); j++) {
+        AddReq *a = s->adds[j];
+        s->streams[where[j]] = std::move(a->q);
+        s->streams[where[j]].ctx = a->ctx;
         a->q = Stream();
-        a->index = (int)s->streams.size() - 1;
+        a->index = where[j];
         a->done = true;
     }
     s->adds.clear();
+    rebuild_positions(s);
     s->cv_added.notify_all();
 }
 
@@ -232,22 +326,22 @@ static cudaError_t pool_event(cog_server *s, std::vector<cudaEvent_t> &pool, uns
 static void server_worker(cog_server *s)
 {
     cudaSetDevice(s->device);
-    int n = (int)s->streams.size();
-    std::vector<const uint8_t *> frames(n, nullptr);
-    std::vector<uint8_t *> masks(n, nullptr);
-    std::vector<uint8_t> active(n, 0);
+    // per batch position
+    std::vector<const uint8_t *> frames;
+    std::vector<uint8_t *> masks;
+    std::vector<uint8_t> active;
     for (;;) {
         std::vector<Pick> picks;
         {
             std::unique_lock<std::mutex> lk(s->mu);
             for (;;) {
-                if (!s->adds.empty() && !s->stop) {
-                    server_join(s, lk);
-                    n = (int)s->streams.size();
-                    frames.resize(n, nullptr);
-                    masks.resize(n, nullptr);
-                    active.resize(n, 0);
-                }
+                bool member = !s->adds.empty();
+                for (const LeaveReq *l : s->leaves) member = member || leave_ready(s, l);
+                if (member && !s->stop) server_rebuild(s, lk);
+                const int n = (int)s->streams.size();
+                frames.resize(s->ctxs.size(), nullptr);
+                masks.resize(s->ctxs.size(), nullptr);
+                active.resize(s->ctxs.size(), 0);
                 if (s->steps_in_flight < MAX_STEPS_IN_FLIGHT) {
                     for (int i = 0; i < n; i++) {
                         Stream &q = s->streams[i];
@@ -273,12 +367,12 @@ static void server_worker(cog_server *s)
         std::fill(active.begin(), active.end(), 0);
         for (const Pick &k : picks) {
             Stream &q = s->streams[k.stream];
-            const int sl = (int)(k.f.seq & 1);
+            const int sl = (int)(k.f.seq & 1), b = s->bpos[k.stream];
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(q.slot[sl], k.f.frame, (size_t)q.P * 3, cudaMemcpyHostToDevice, s->up);
-            frames[k.stream] = q.slot[sl];
-            masks[k.stream] = q.mslot[sl];
-            active[k.stream] = 1;
+            frames[b] = q.slot[sl];
+            masks[b] = q.mslot[sl];
+            active[b] = 1;
         }
         if (e == cudaSuccess) e = cudaEventRecord(step.tm[1], s->up);
         if (e == cudaSuccess) e = cudaEventRecord(s->copied, s->up);
@@ -329,7 +423,7 @@ static void server_worker(cog_server *s)
     }
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        fail_adds(s, s->sticky != COG_OK ? s->sticky : COG_ERR_STATE, "the server is stopping");
+        fail_members(s, s->sticky != COG_OK ? s->sticky : COG_ERR_STATE, "the server is stopping");
     }
     {
         std::lock_guard<std::mutex> lk(s->dmu);
@@ -439,6 +533,7 @@ cog_status cog_server_create(cog_ctx *const *ctxs, int32_t n, cog_server **out)
     for (int i = 0; i < n && e == cudaSuccess; i++) {
         const int64_t P = cog::ctx_pixels(ctxs[i]);
         Stream &q = s->streams[i];
+        q.ctx = ctxs[i];
         q.P = P;
         for (int k = 0; k < 2 && e == cudaSuccess; k++) {
             e = cudaMalloc((void **)&q.slot[k], (size_t)P * 3);
@@ -451,6 +546,7 @@ cog_status cog_server_create(cog_ctx *const *ctxs, int32_t n, cog_server **out)
         server_free(s);
         return COG_ERR_OOM;
     }
+    rebuild_positions(s);
     s->t0 = clk::now();
     s->worker = std::thread(server_worker, s);
     s->completer = std::thread(server_completer, s);
@@ -468,6 +564,8 @@ cog_status cog_server_submit(cog_server *s, int32_t stream, const uint8_t *frame
             return server_err(s, COG_ERR_INVALID_ARG, "stream index out of range or NULL buffer");
         if (s->stop) return server_err(s, COG_ERR_STATE, "server is stopping");
         Stream &q = s->streams[stream];
+        if (!q.ctx || q.leaving)
+            return server_err(s, COG_ERR_INVALID_ARG, "stream %d has left the server or is leaving", stream);
         q.pending.push_back({frame_host, mask_host, clk::now(), q.seq++});
         s->submitted++;
     }
@@ -528,6 +626,40 @@ cog_status cog_server_add(cog_server *s, cog_ctx *ctx, int32_t *stream_out)
         return add_err(s, req.st, "camera join failed: %s", req.msg);
     }
     *stream_out = req.index;
+    return COG_OK;
+}
+
+cog_status cog_server_remove(cog_server *s, int32_t stream, cog_ctx **ctx_out)
+{
+    if (!s) return COG_ERR_INVALID_ARG;
+    if (ctx_out) *ctx_out = nullptr;
+    LeaveReq req;
+    req.index = stream;
+    std::unique_lock<std::mutex> lk(s->mu);
+    if (s->stop || s->sticky != COG_OK) {
+        lk.unlock();
+        return add_err(s, COG_ERR_STATE, "the server is stopping or failed");
+    }
+    if (stream < 0 || stream >= (int32_t)s->streams.size() || !s->streams[stream].ctx ||
+        s->streams[stream].leaving) {
+        lk.unlock();
+        return add_err(s, COG_ERR_INVALID_ARG, "stream %d is not a camera of the server", stream);
+    }
+    s->streams[stream].leaving = true;
+    s->leaves.push_back(&req);
+    s->cv_work.notify_all();
+    const clk::time_point until = clk::now() + std::chrono::seconds(60);
+    while (!req.done) {
+        if (s->cv_added.wait_until(lk, until) == std::cv_status::timeout && !req.done) {
+            s->leaves.erase(std::remove(s->leaves.begin(), s->leaves.end(), &req), s->leaves.end());
+            s->streams[stream].leaving = false;
+            lk.unlock();
+            return add_err(s, COG_ERR_TIMEOUT, "stream %d did not leave within 60 s", stream);
+        }
+    }
+    lk.unlock();
+    if (req.st != COG_OK) return add_err(s, req.st, "camera leave failed: %s", req.msg);
+    if (ctx_out) *ctx_out = req.ctx;
     return COG_OK;
 }
 

@@ -10,8 +10,10 @@ on a copy stream; runs one batched cascade step over exactly those cameras
 (one replay of one captured CUDA graph); and downloads their masks.  Frames
 that arrive while a step is on the GPU join the next step, whose uploads
 overlap the running step.  A C++ completion thread stamps each frame's
-latency from submission to its mask being in host memory.  Python only
-admits cameras and submits frames.
+latency from submission to its mask being in host memory.  Cameras join and
+leave a running server between steps; a camera that leaves frees its HBM for
+the next admission, which takes its index.  Python only admits cameras,
+retires them and submits frames.
 """
 from __future__ import annotations
 
@@ -30,17 +32,20 @@ class Camera:
         self.ctx = None
         self.seq = 0             # frames submitted
         self.mask_ring = []      # pinned host masks reused when results are not kept
+        self.masks = []          # (seq, host mask) of every frame, when results are kept
 
 
 class FrameServer:
     RING = 4                     # host mask buffers per camera when results are not kept
+    # with keep_masks, results[camera index] lists (seq, mask) of the camera
+    # now at that index (a camera that left keeps its own in Camera.masks)
 
     def __init__(self, device=None, reserve_bytes: int = 4 << 30, keep_masks: bool = False):
         import torch
         self.torch = torch
         self.dev = torch.device(device or "cuda")
         self.reserve = reserve_bytes
-        self.cameras: list[Camera] = []
+        self.cameras: list[Camera | None] = []   # by stream index; None: the camera left
         self.refused: list[tuple] = []
         self.keep_masks = keep_masks
         self.results = collections.defaultdict(list)   # camera id -> (seq, mask) when keep_masks
@@ -55,7 +60,7 @@ class FrameServer:
         camera admitted after start() joins the running server between two
         of its steps."""
         torch = self.torch
-        cam = Camera(len(self.cameras), width, height, K, dtype)
+        cam = Camera(-1, width, height, K, dtype)
         need = cog.cog_state_bytes(cam.params) + 2 * cam.P * 4 + (1 << 20)
         free, _ = torch.cuda.mem_get_info(self.dev)
         if free - need < self.reserve:
@@ -74,15 +79,36 @@ class FrameServer:
                 cog.cog_destroy(cam.ctx)
                 self.refused.append((width, height, K, dtype, need))
                 return None
-            assert idx == cam.id
+            # the lowest index a camera has left, else the next one
+            free = [i for i, c in enumerate(self.cameras) if c is None]
+            assert idx == (free[0] if free else len(self.cameras))
+            cam.id = idx
+            if idx == len(self.cameras):
+                self.cameras.append(cam)
+            else:
+                self.cameras[idx] = cam
+            return cam
+        cam.id = len(self.cameras)
         self.cameras.append(cam)
         return cam
+
+    def leave(self, cam: Camera) -> None:
+        """cam leaves the running server once its submitted frames are done;
+        its model and buffers are freed and its index goes to the next
+        admission."""
+        assert self.srv is not None and self.cameras[cam.id] is cam
+        ctx = cog.cog_server_remove(self.srv, cam.id)
+        cog.cog_destroy(ctx)
+        cam.ctx = None
+        self.cameras[cam.id] = None
+        self.results.pop(cam.id, None)   # its masks stay in cam.masks
 
     def start(self, warmup_frames=None):
         """Hands the admitted cameras to the native server and starts it.
         warmup_frames (optional): camera id -> list of host frames, served
         first and left out of the statistics; they take each camera's first
         steps (slot buffers, the batch graph's first launch)."""
+        assert all(c is not None for c in self.cameras)
         self.srv = cog.cog_server_create([c.ctx for c in self.cameras])
         if warmup_frames:
             for cam in self.cameras:
@@ -98,6 +124,7 @@ class FrameServer:
         if self.keep_masks:
             mask = np.empty((cam.height, cam.width), np.uint8)
             self.results[cam.id].append((cam.seq, mask))
+            cam.masks.append((cam.seq, mask))
             self._keep.append(frame_host)
         else:
             mask = cam.mask_ring[cam.seq % self.RING]
@@ -126,12 +153,13 @@ class FrameServer:
                                      "service_p99": round(st["service_p99_ms"], 3),
                                      "enqueue_p99": round(st["enqueue_p99_ms"], 3),
                                      "enqueue_max": round(st["enqueue_max_ms"], 3)},
-                "cameras": len(self.cameras), "refused": len(self.refused)}
+                "cameras": sum(c is not None for c in self.cameras), "refused": len(self.refused)}
 
     def close(self):
         if self.srv is not None:
             cog.cog_server_destroy(self.srv)
             self.srv = None
         for c in self.cameras:
-            cog.cog_destroy(c.ctx)
+            if c is not None:
+                cog.cog_destroy(c.ctx)
         self.cameras = []

@@ -103,6 +103,7 @@ def test_server_add_rejects_bad_arguments(cog):
     import ctypes as C
     idx = C.c_int32(0)
     assert cog.lib.cog_server_add(None, None, C.byref(idx)) == cog.COG_ERR_INVALID_ARG
+    assert cog.lib.cog_server_remove(None, 0, None) == cog.COG_ERR_INVALID_ARG
 
 
 def test_group_rejects_bad_arguments(cog):

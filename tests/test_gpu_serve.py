@@ -1,6 +1,6 @@
 """The continuous-batching server: every camera's masks in the mix equal
-what the same camera gives alone; admission refuses cameras that do not fit
-in free device memory."""
+what the same camera gives alone, also when cameras join and leave a running
+server; admission refuses cameras that do not fit in free device memory."""
 import numpy as np
 import pytest
 
@@ -122,4 +122,76 @@ def test_camera_joins_a_running_server(cog):
             cog.cog_apply(c, data[i][1][j].cuda(), m)
             assert np.array_equal(m.cpu().numpy(), got[j][1]), (i, j)
         cog.cog_destroy(c)
+    srv.close()
+
+
+def test_camera_leaves_and_its_index_is_reused(cog):
+    # three cameras serve; the second leaves while its frames are on the GPU:
+    # every frame it was given is still completed, its index refuses frames
+    # until a fourth camera joins and takes it, and every camera's masks
+    # equal what it gives alone
+    from cogsynth import Scene
+    from cogsynth.gpu import GpuScene
+    from paper_1705_09339_gb300.serve import FrameServer
+    NT, NF = 30, 12
+    cams = [(160, 120, 3, "f16"), (97, 61, 5, "f32"), (200, 150, 5, "bf16"), (64, 48, 3, "f16")]
+    srv = FrameServer(reserve_bytes=1 << 30, keep_masks=True)
+    data = []
+    for i, (w, h, k, dt) in enumerate(cams):
+        sc = Scene(w, h, 800 + i, kind="dynamic", n_train=NT, fg_frac=0.05, switch_at=5)
+        gs = GpuScene(sc)
+        data.append((gs.render(0, NT), [f.cpu().pin_memory() for f in gs.render(NT, NF)]))
+    h = [srv.admit(*cams[i], data[i][0]) for i in range(3)]
+    assert [c.id for c in h] == [0, 1, 2]
+    srv.start()
+    for j in range(NF // 2):
+        for i in range(3):
+            srv.submit(h[i], data[i][1][j])
+    free_before = torch.cuda.mem_get_info()[0]
+    srv.leave(h[1])
+    assert len(h[1].masks) == NF // 2 and torch.cuda.mem_get_info()[0] > free_before
+    with pytest.raises(cog.CogError):
+        cog.cog_server_submit(srv.srv, 1, data[1][1][0], np.empty((61, 97), np.uint8))
+    with pytest.raises(cog.CogError):
+        cog.cog_server_remove(srv.srv, 1)          # already left
+    with pytest.raises(cog.CogError):
+        cog.cog_server_remove(srv.srv, 7)          # no such camera
+    late = srv.admit(*cams[3], data[3][0])
+    assert late is not None and late.id == 1       # the freed index
+    for j in range(NF):
+        if j >= NF // 2:
+            for i in (0, 2):
+                srv.submit(h[i], data[i][1][j])
+        srv.submit(late, data[3][1][j])
+    stats = srv.stop()
+    assert stats["frames"] == 3 * NF + NF // 2 and stats["cameras"] == 3
+    for i, cam in ((0, h[0]), (1, h[1]), (2, h[2]), (3, late)):
+        w, hh, k, dt = cams[i]
+        got = sorted(cam.masks, key=lambda x: x[0])
+        n = len(got)
+        assert [s for s, _ in got] == list(range(n)) and n == (NF // 2 if i == 1 else NF)
+        p = cog.cog_default_params(w, hh, k, state_dtype=dt)
+        c = cog.cog_create(p, torch.cuda.current_stream().cuda_stream)
+        cog.cog_train_prior(c, data[i][0], NT)
+        m = torch.empty((hh, w), dtype=torch.uint8, device="cuda")
+        for j in range(n):
+            cog.cog_apply(c, data[i][1][j].cuda(), m)
+            assert np.array_equal(m.cpu().numpy(), got[j][1]), (i, j)
+        cog.cog_destroy(c)
+    srv.close()
+
+
+def test_last_camera_cannot_leave(cog):
+    from paper_1705_09339_gb300.serve import FrameServer
+    srv = FrameServer(reserve_bytes=1 << 30)
+    tr = torch.zeros((2, 48, 64, 3), dtype=torch.uint8, device="cuda")
+    cam = srv.admit(64, 48, 3, "f16", tr)
+    srv.start()
+    with pytest.raises(cog.CogError) as e:
+        cog.cog_server_remove(srv.srv, cam.id)
+    assert e.value.status == cog.COG_ERR_INVALID_ARG
+    # the camera still serves
+    f = torch.zeros((48, 64, 3), dtype=torch.uint8).pin_memory()
+    srv.submit(cam, f)
+    assert srv.stop()["frames"] == 1
     srv.close()
