@@ -186,7 +186,8 @@ def issue_rate(kernel: str, ms_per_launch: float):
 class Clocks:
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,utilization.gpu")
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,utilization.gpu,"
+         "pstate,clocks.mem")
 
     def __init__(self, gpu_index: int):
         self.proc = None
@@ -212,7 +213,7 @@ class Clocks:
         except Exception:
             self.proc.kill()
         self.fh.close()
-        sm, mx, reasons, util = [], 0.0, set(), []
+        sm, mx, reasons, util, mem, pst = [], 0.0, set(), [], [], {}
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         with open(self.path) as f:
             lines = f.readlines()
@@ -236,10 +237,17 @@ class Clocks:
                 util.append(float(v[9]))
             except (IndexError, ValueError):
                 pass
+            if len(v) > 11:
+                pst[v[10]] = pst.get(v[10], 0) + 1
+                try:
+                    mem.append(float(v[11]))
+                except ValueError:
+                    pass
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm), "gpu_util_pct_median": statistics.median(util) if util else None}
+                "samples": len(sm), "gpu_util_pct_median": statistics.median(util) if util else None,
+                "mem_mhz": statistics.median(mem) if mem else None, "pstates": pst}
 
 
 # ---------------------------------------------------------------- our arm
@@ -894,7 +902,8 @@ def run_serve(args, rank, local_rank, world):
     four other sizes), K=5, FP16 state resident on the device, 100 training
     frames each; each camera emits frames with exponential inter-arrival
     times of mean 1/30 s for `--duration` seconds.  Frames come from a pool
-    of eight pinned host frames per camera.  The server admits cameras by
+    of eight pinned host frames per camera, carved from the server's pinned
+    arena (a few large page-locked allocations).  The server admits cameras by
     free HBM; the native server (cog_server_*) runs continuous batching
     (cog_batch_apply_active).  Reports p50/p99 latency from submission to
     mask in host memory, and aggregate Mpixel/s."""
@@ -927,7 +936,9 @@ def run_serve(args, rank, local_rank, world):
         if cam is None:
             continue
         pool = gs.render(100, 8).cpu()
-        pools[cam.id] = [pool[j].pin_memory() for j in range(8)]
+        pools[cam.id] = [srv.arena.take((h, w, 3)) for _ in range(8)]
+        for j in range(8):
+            pools[cam.id][j].copy_(pool[j])
     # everything allocated so far lives for the whole run: keep it out of
     # the garbage collector's passes so they stay short while serving
     import gc

@@ -462,8 +462,19 @@ cog_status cog_batch_destroy(cog_batch *batch);
  * Synchronises the stream. */
 cog_status cog_read_stats(cog_ctx *ctx, cog_stats *last, cog_stats *total);
 
-/* Waits for the context's stream; returns any sticky error. */
+/* Waits for the context's stream; returns any sticky error, and
+ * COG_ERR_DEVICE when a kernel set the context's device error word (a
+ * bounded wait gave up, or in the COG_DEBUG build a bounds check failed:
+ * the message names the check, the index and its limit). */
 cog_status cog_sync(cog_ctx *ctx);
+
+/* 1 in the COG_DEBUG build of this library (libcog_debug.so: every
+ * data-dependent index of the kernels -- survivor-queue slots, pixels taken
+ * from queue entries and shared lists, batch streams and tiles -- is checked
+ * before its access; a failure skips the access and sets the device error
+ * word, reported by the next cog_sync), 0 otherwise.  A sanitizer
+ * substitute; the paper has no counterpart. */
+int32_t cog_debug_build(void);
 
 /* Byte image of the state buffer (cog_layout.total bytes) to or from host
  * memory.  Synchronous. */

@@ -18,6 +18,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build", platform.machine())
 LIB = os.path.join(PKG, "libcog.so")
+DEBUG_LIB = os.path.join(PKG, "libcog_debug.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # host code: no FP contraction, so the host-side arithmetic (the grouping
@@ -40,10 +41,11 @@ def _newer(target: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def _compile(src: str, obj: str, headers: list[str], verbose: bool) -> str:
+def _compile(src: str, obj: str, headers: list[str], verbose: bool, defs: list[str] | None = None) -> str:
     if not _newer(obj, [src] + headers):
         return ""
-    cmd = [nvcc()] + NVCC_FLAGS + (["-Xptxas", "-v"] if verbose else []) + ["-c", src, "-o", obj + ".tmp"]
+    cmd = [nvcc()] + NVCC_FLAGS + (defs or []) + (["-Xptxas", "-v"] if verbose else []) + ["-c", src, "-o",
+                                                                                        obj + ".tmp"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -51,11 +53,12 @@ def _compile(src: str, obj: str, headers: list[str], verbose: bool) -> str:
     return r.stderr
 
 
-def build_lib(sources: list[str], headers: list[str], out: str, tag: str, verbose: bool = False) -> str:
+def build_lib(sources: list[str], headers: list[str], out: str, tag: str, verbose: bool = False,
+              defs: list[str] | None = None) -> str:
     os.makedirs(BUILD, exist_ok=True)
     objs = [os.path.join(BUILD, f"{tag}_{os.path.splitext(os.path.basename(s))[0]}.o") for s in sources]
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(sources), os.cpu_count() or 4))) as ex:
-        logs = list(ex.map(lambda a: _compile(a[0], a[1], headers, verbose), zip(sources, objs)))
+        logs = list(ex.map(lambda a: _compile(a[0], a[1], headers, verbose, defs), zip(sources, objs)))
     if verbose:
         for l in logs:
             if l:
@@ -69,10 +72,14 @@ def build_lib(sources: list[str], headers: list[str], out: str, tag: str, verbos
     return out
 
 
-def build(verbose: bool = False) -> str:
+def build(verbose: bool = False, debug: bool = False) -> str:
+    """Builds libcog.so, or with debug=True its COG_DEBUG variant
+    libcog_debug.so (every data-dependent kernel index bounds-checked)."""
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hdrs = sorted(glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h"))
                   + glob.glob(os.path.join(ROOT, "include", "*.h")))
+    if debug:
+        return build_lib(srcs, hdrs, DEBUG_LIB, "cogdbg", verbose, ["-DCOG_DEBUG"])
     return build_lib(srcs, hdrs, LIB, "cog", verbose)
 
 

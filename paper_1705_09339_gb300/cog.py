@@ -14,7 +14,9 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libcog.so")
+# COG_LIB_VARIANT=debug loads the COG_DEBUG build (libcog_debug.so, every
+# data-dependent kernel index bounds-checked) instead of libcog.so
+LIB_PATH = os.path.join(_PKG, "libcog_debug.so" if os.environ.get("COG_LIB_VARIANT") == "debug" else "libcog.so")
 
 COG_OK, COG_ERR_INVALID_ARG, COG_ERR_OOM, COG_ERR_CUDA, COG_ERR_STATE, COG_ERR_TIMEOUT, COG_ERR_DEVICE = range(7)
 STATUS_NAMES = ["COG_OK", "COG_ERR_INVALID_ARG", "COG_ERR_OOM", "COG_ERR_CUDA", "COG_ERR_STATE",
@@ -81,7 +83,7 @@ class CogError(RuntimeError):
 
 def _load() -> C.CDLL:
     if not os.path.exists(LIB_PATH):
-        raise ImportError(f"libcog.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+        raise ImportError(f"{os.path.basename(LIB_PATH)} is not built ({LIB_PATH}); run __graft_entry__.build()")
     lib = C.CDLL(LIB_PATH)
     vp, i32, sz = C.c_void_p, C.c_int32, C.c_size_t
     P = C.POINTER
@@ -104,6 +106,7 @@ def _load() -> C.CDLL:
         "cog_apply_host_frames": (C.c_int, [vp, vp, i32, vp]),
         "cog_read_stats": (C.c_int, [vp, P(cog_stats), P(cog_stats)]),
         "cog_sync": (C.c_int, [vp]),
+        "cog_debug_build": (C.c_int32, []),
         "cog_export_state": (C.c_int, [vp, vp, sz]),
         "cog_import_state": (C.c_int, [vp, vp, sz]),
         "cog_info": (C.c_int, [vp, P(C.c_int64), P(vp)]),

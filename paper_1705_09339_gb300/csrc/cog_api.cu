@@ -332,6 +332,13 @@ static cog_status read_ctl(cog_ctx *c, std::vector<uint32_t> &ctl)
     cudaError_t e = cudaMemcpyAsync(ctl.data(), c->sp.ctl, CTL_BYTES, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "reading the control block");
+    if (ctl[CTL_ERR_WORD] & DERR_BOUNDS) {
+        c->sticky = COG_ERR_DEVICE;
+        const uint32_t *d = ctl.data() + CTL_DBG_WORD;
+        return set_err(c, COG_ERR_DEVICE, "device error word 0x%x: bounds check %u failed (index %llu, limit %llu)",
+                       ctl[CTL_ERR_WORD], d[0], (unsigned long long)d[1] | (unsigned long long)d[2] << 32,
+                       (unsigned long long)d[3] | (unsigned long long)d[4] << 32);
+    }
     if (ctl[CTL_ERR_WORD]) {
         c->sticky = COG_ERR_DEVICE;
         return set_err(c, COG_ERR_DEVICE, "device error word 0x%x (a bounded wait gave up)", ctl[CTL_ERR_WORD]);
@@ -786,6 +793,15 @@ cog_status cog_read_stats(cog_ctx *c, cog_stats *last, cog_stats *total)
         total->n_stage[5] = (int64_t)tot[6] + (c->frame_no > 0 ? l.n_stage[5] : 0);
     }
     return COG_OK;
+}
+
+int32_t cog_debug_build(void)
+{
+#ifdef COG_DEBUG
+    return 1;
+#else
+    return 0;
+#endif
 }
 
 cog_status cog_sync(cog_ctx *c)

@@ -325,6 +325,7 @@ __device__ __forceinline__ void k1_cta(const ApplyArgs &A, uint32_t cta)
     for (int i = 0; i < PPT; i++) {
         if (!(X.need1 >> i & 1u)) continue;
         const uint32_t slot = (uint32_t)tid * PPT + i;
+        if (!in_bounds(ctl, dst, CPX, DBG_K1_LIST)) continue;
         L.ix[dst] = X.Iw[i] | (X.D[i] << 24);
         if (WIDE) {
             L.cs[dst] = X.cv.w[i];
@@ -344,9 +345,9 @@ __device__ __forceinline__ void k1_cta(const ApplyArgs &A, uint32_t cta)
         const uint32_t j = j0 + (uint32_t)lane;
         bool surv = false;
         uint4 ent = make_uint4(0, 0, 0, 0);
-        if (j < n1) {
-            const uint32_t ix = L.ix[j], cs = L.cs[j];
-            const uint32_t p = cbase + (WIDE ? (uint32_t)L.slot[j] : (cs >> 16));
+        const uint32_t ix = j < n1 ? L.ix[j] : 0u, cs = j < n1 ? L.cs[j] : 0u;
+        const uint32_t p = cbase + (WIDE ? (j < n1 ? (uint32_t)L.slot[j] : 0u) : (cs >> 16));
+        if (j < n1 && in_bounds(ctl, p, (uint64_t)dp.P, DBG_K1_PIXEL)) {
             const int D = (int)(ix >> 24);
             const float Cm = conf_on ? Store<T>::unbits(WIDE ? cs : (cs & 0xffffu)) : 0.5f;
             S1Rec<T> r;
@@ -372,7 +373,9 @@ __device__ __forceinline__ void k1_cta(const ApplyArgs &A, uint32_t cta)
             uint32_t base = 0;
             if (lane == 0) base = atomicAdd(A.s.ctl + ctl_qcnt(n % 3, seg), (uint32_t)__popc(b));
             base = __shfl_sync(0xffffffffu, base, 0);
-            if (surv) A.s.queue[(int64_t)seg * A.s.qseg_cap + base + __popc(b & lt)] = ent;
+            const uint32_t k = base + __popc(b & lt);
+            if (surv && in_bounds(ctl, k, (uint64_t)A.s.qseg_cap, DBG_K1_QUEUE))
+                A.s.queue[(int64_t)seg * A.s.qseg_cap + k] = ent;
         }
         ne += __popc(b);
     }
@@ -428,16 +431,18 @@ template <typename T, int K, bool PC = false> struct S2In {
 };
 
 template <typename T, int K, bool PC = false, bool M1 = false>
-__device__ __forceinline__ void s2_load(const ApplyArgs &A, int64_t qi, S2In<T, K, PC> &in)
+__device__ __forceinline__ bool s2_load(const ApplyArgs &A, int64_t qi, S2In<T, K, PC> &in)
 {
     in.e = __ldcg(A.s.queue + qi);
     const int64_t p = in.e.x;
+    if (!in_bounds(A.s.ctl, (uint64_t)p, (uint64_t)A.dp.P, DBG_K2_PIXEL)) return false;
 #pragma unroll
     for (int c = 0; c < 3; c++) in.qk[c] = prior_level(A.s.kde, p, c, (in.e.y >> (8 * c)) & 0xffu, A.dp.kde_bits == 4);
     const uint4 *src = reinterpret_cast<const uint4 *>(A.s.gmm + p * RecSel<T, K, PC>::BYTES);
 #pragma unroll
     for (int i = 0; i < RecSel<T, K, PC>::NV; i++) in.rec[i] = src[i];
     if (M1) in.s1.load(A.s.s1, p);
+    return true;
 }
 
 // Confidence of a pixel decided at stage 2 (Sec. 2, "Confidence Measure"):
@@ -603,18 +608,20 @@ __device__ __forceinline__ void k2_cta(const ApplyArgs &A, uint32_t cta, uint32_
     const bool flag = flag_s;
     const uint32_t nq = segp_s[QSEG];
     const uint32_t stride = ncta * TPB;
-    auto entry = [&](uint32_t q) -> int64_t {   // flat index -> queue slot
+    auto entry = [&](uint32_t q) -> int64_t {   // flat index -> queue slot (-1: failed check)
         int lo = 0;
 #pragma unroll
         for (int step = QSEG / 2; step >= 1; step >>= 1)
             if (segp_s[lo + step] <= q) lo += step;
+        if (!in_bounds(ctl, q - segp_s[lo], (uint64_t)A.s.qseg_cap, DBG_K2_QUEUE)) return -1;
         return (int64_t)lo * A.s.qseg_cap + (q - segp_s[lo]);
     };
     uint32_t cbg = 0, cfg = 0, cil = 0;
     for (uint32_t q = cta * TPB + tid; q < nq; q += stride) {
         constexpr bool PC = V == 1;
         S2In<T, K, PC> a;
-        s2_load<T, K, PC, V == 2>(A, entry(q), a);
+        const int64_t qi = entry(q);
+        if (qi < 0 || !s2_load<T, K, PC, V == 2>(A, qi, a)) continue;
         int st;
         if constexpr (PC) st = s2_finish_pc<T, K>(A, a, flag);
         else st = s2_finish<T, K, V == 2>(A, a, flag);
@@ -662,7 +669,11 @@ __global__ void __launch_bounds__(TPB, K1_THREADS_PER_SM / TPB) stage01_batch_ke
     const uint32_t total = __ldg(G.k1_pre + G.n);
     for (uint32_t t = blockIdx.x; t < total; t += gridDim.x) {
         const int s = batch_stream(G.k1_pre, G.n, t);
-        k1_cta<T, TPB>(G.descs[s], t - __ldg(G.k1_pre + s));
+        if (!in_bounds(G.descs[0].s.ctl, (uint64_t)s, (uint64_t)G.n, DBG_BATCH_STREAM)) break;
+        const uint32_t tile = t - __ldg(G.k1_pre + s);
+        if (!in_bounds(G.descs[s].s.ctl, (uint64_t)tile * TPB * PPT, (uint64_t)G.descs[s].dp.P, DBG_BATCH_TILE))
+            continue;   // the same for every thread of the CTA
+        k1_cta<T, TPB>(G.descs[s], tile);
     }
 }
 
@@ -674,6 +685,7 @@ __global__ void __launch_bounds__(TPB) stage2_batch_kernel(const BatchGroupDev G
     grid_wait_prior();
     if (blockIdx.x >= __ldg(G.k2_pre + G.n)) return;
     const int s = batch_stream(G.k2_pre, G.n, blockIdx.x);
+    if (!in_bounds(G.descs[0].s.ctl, (uint64_t)s, (uint64_t)G.n, DBG_BATCH_STREAM)) return;
     k2_cta<T, K, TPB, V>(G.descs[s], blockIdx.x - G.k2_pre[s], G.k2_pre[s + 1] - G.k2_pre[s]);
 }
 

@@ -429,9 +429,14 @@ __device__ __forceinline__ void clip_tile(const ClipArgs &A, ClipWarp<T, G> *Ws,
         {
             const uint32_t ns = Q.n[t & 1];
             for (uint32_t q = threadIdx.x; q < ns; q += NW * 32) {
+                if (!in_bounds(A.s.ctl, q, (uint64_t)NW * G * 128, DBG_CLIP_ENTRY)) break;
                 const uint32_t e = Q.q[q];
                 const int slot = (int)(e & 0xffu);
-                clip_s2<T, K, G, PC>(A, Ws[e >> 8], (int64_t)cbase + (e >> 8) * (G * 128) + slot, slot, flag);
+                const int64_t pp = (int64_t)cbase + (e >> 8) * (G * 128) + slot;
+                if (!in_bounds(A.s.ctl, e >> 8, (uint64_t)NW, DBG_CLIP_ENTRY) ||
+                    !in_bounds(A.s.ctl, (uint64_t)pp, (uint64_t)P, DBG_CLIP_PIXEL))
+                    continue;
+                clip_s2<T, K, G, PC>(A, Ws[e >> 8], pp, slot, flag);
             }
         }
         __syncthreads();

@@ -351,6 +351,29 @@ __device__ __forceinline__ float conf_next(const DevParams &dp, float Cm, float 
     return __fmaf_rn(__fsub_rn(1.f, dp.eta), Cm, __fmul_rn(dp.eta, ci));
 }
 
+// Bounds check of the COG_DEBUG build: true when i < n.  A failure sets
+// DERR_BOUNDS, the first one records its site, index and limit, and the
+// caller skips the access.  Other builds compile every check to true.
+#ifdef COG_DEBUG
+static __device__ __noinline__ bool dbg_fail(uint32_t *ctl, uint64_t i, uint64_t n, uint32_t site)
+{
+    if (atomicCAS(ctl + CTL_DBG_WORD, 0u, site) == 0u) {
+        ctl[CTL_DBG_WORD + 1] = (uint32_t)i;
+        ctl[CTL_DBG_WORD + 2] = (uint32_t)(i >> 32);
+        ctl[CTL_DBG_WORD + 3] = (uint32_t)n;
+        ctl[CTL_DBG_WORD + 4] = (uint32_t)(n >> 32);
+    }
+    atomicOr(ctl + CTL_ERR_WORD, DERR_BOUNDS);
+    return false;
+}
+__device__ __forceinline__ bool in_bounds(uint32_t *ctl, uint64_t i, uint64_t n, uint32_t site)
+{
+    return i < n || dbg_fail(ctl, i, n, site);
+}
+#else
+__device__ __forceinline__ constexpr bool in_bounds(uint32_t *, uint64_t, uint64_t, uint32_t) { return true; }
+#endif
+
 // The scene prior's level for channel c of pixel p at grey level v, on the
 // 0..255 scale the confidence and the nullification test use (Sec. 2,
 // "Scene Prior in Background Model"): the stored byte of the 8-bit prior,

@@ -140,6 +140,27 @@ constexpr int CLIP_TMAX = 32;          // frames per launch (their flags fit one
 constexpr int CLIP_SLOTS = 8;          // counter slots per (frame, field)
 constexpr uint32_t DERR_GRID_TIMEOUT = 2u;   // a grid-wide wait of the clip kernel gave up
 constexpr uint32_t DERR_CLIP_RUNS = 4u;      // the clip kernel's reruns did not converge
+constexpr uint32_t DERR_BOUNDS = 8u;         // COG_DEBUG build: an index failed its bounds check
+
+// COG_DEBUG build (a sanitizer substitute): the data-dependent indices of
+// the kernels (survivor-queue slots, pixels taken from queue entries and
+// shared lists, batch streams and tiles) are checked before each access.
+// The first failed check writes its site, index and limit into the words
+// from CTL_DBG_WORD (site, index low/high, limit low/high); every failure
+// sets DERR_BOUNDS, and the access is skipped.
+constexpr int CTL_DBG_WORD = CTL_ERR_WORD + 8;
+enum DbgSite : uint32_t {
+    DBG_K1_LIST = 1,      // stage-1 list entry of a CTA (< pixels of the CTA)
+    DBG_K1_PIXEL = 2,     // pixel of a stage-1 list entry (< P)
+    DBG_K1_QUEUE = 3,     // survivor-queue write (< segment capacity)
+    DBG_K2_QUEUE = 4,     // survivor-queue read (< the segment's written length)
+    DBG_K2_PIXEL = 5,     // pixel of a queue entry (< P)
+    DBG_BATCH_STREAM = 6, // batch stream of a tile or mixture CTA (< streams)
+    DBG_BATCH_TILE = 7,   // a stream's stage-0/1 tile (first pixel < P)
+    DBG_CLIP_ENTRY = 8,   // clip survivor entry: warp area and slot
+    DBG_CLIP_PIXEL = 9,   // clip survivor pixel (< P)
+    DBG_PLAIN_TILE = 10,  // plain mixture tile (first pixel < P)
+};
 // per-frame counters of a run: 3 banks (runs rotate) x CLIP_TMAX frames x
 // CTL_FIELDS fields x CLIP_SLOTS slots, each slot on its own 128-byte line
 __host__ __device__ constexpr int clip_cnt_word(int bank, int t, int f, int s)

@@ -33,6 +33,7 @@ __global__ void __launch_bounds__(PLAIN_TPB) plain_gmm_kernel(const DevParams dp
     __shared__ __align__(8) uint64_t bar;
     const int tid = threadIdx.x;
     const int64_t p0 = (int64_t)blockIdx.x * PLAIN_TPB;
+    if (!in_bounds(err - CTL_ERR_WORD, (uint64_t)p0, (uint64_t)dp.P, DBG_PLAIN_TILE)) return;
     const int npx = (int)min((int64_t)PLAIN_TPB, dp.P - p0);
     const int fbytes = npx * 3, fbulk = frame_al16 ? (fbytes & ~15) : 0;
     if (tid == 0) {

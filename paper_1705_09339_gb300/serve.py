@@ -24,6 +24,33 @@ import numpy as np
 from . import cog
 
 
+class PinnedArena:
+    """Page-locked host memory handed out from a few large allocations.
+    Frames and masks that the copy engines move every step come from here
+    rather than from one pinned allocation each: thousands of small pinned
+    buffers spread the DMA over many more pages to translate."""
+
+    def __init__(self, chunk_bytes: int = 256 << 20):
+        import torch
+        self.torch = torch
+        self.chunk = chunk_bytes
+        self.blocks = []
+        self.off = 0
+
+    def take(self, shape, dtype=None):
+        """A pinned tensor of `shape` (uint8 unless given), 256-byte aligned."""
+        torch = self.torch
+        dtype = dtype or torch.uint8
+        nbytes = int(np.prod(shape)) * torch.empty((), dtype=dtype).element_size()
+        span = (nbytes + 255) // 256 * 256
+        if not self.blocks or self.off + span > self.blocks[-1].numel():
+            self.blocks.append(torch.empty(max(self.chunk, span), dtype=torch.uint8, pin_memory=True))
+            self.off = 0
+        t = self.blocks[-1][self.off:self.off + nbytes]
+        self.off += span
+        return t.view(dtype).view(shape)
+
+
 class Camera:
     def __init__(self, cid: int, width: int, height: int, K: int, dtype: str):
         self.id, self.width, self.height, self.K, self.dtype = cid, width, height, K, dtype
@@ -48,6 +75,7 @@ class FrameServer:
         self.cameras: list[Camera | None] = []   # by stream index; None: the camera left
         self.refused: list[tuple] = []
         self.keep_masks = keep_masks
+        self.arena = PinnedArena()   # mask rings; callers may take their frame buffers here too
         self.results = collections.defaultdict(list)   # camera id -> (seq, mask) when keep_masks
         self._keep = []          # host buffers referenced by queued frames
         self.srv = None
@@ -71,7 +99,7 @@ class FrameServer:
         cog.cog_train_prior(cam.ctx, train_frames, train_frames.shape[0])
         cog.cog_sync(cam.ctx)
         if not self.keep_masks:
-            cam.mask_ring = [torch.empty((height, width), dtype=torch.uint8).pin_memory() for _ in range(self.RING)]
+            cam.mask_ring = [self.arena.take((height, width)) for _ in range(self.RING)]
         if self.srv is not None:
             try:
                 idx = cog.cog_server_add(self.srv, cam.ctx)
