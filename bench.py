@@ -548,7 +548,7 @@ def sub_serve(args, rank, local_rank, world, duration=60.0, cameras=256) -> dict
     a.duration, a.cameras, a.timeline = duration, cameras, ""
     r = run_serve(a, rank, local_rank, world)
     keep = ("metric", "config", "latency_ms", "latency_split_ms", "frames", "steps", "aggregate_mpixel_per_s",
-            "frame_period_ms", "p99_under_frame_period", "clocks")
+            "frame_period_ms", "p99_under_frame_period", "clocks", "h2d_probe")
     return {k: r[k] for k in keep if k in r}
 
 
@@ -939,6 +939,7 @@ def run_serve(args, rank, local_rank, world):
         pools[cam.id] = [srv.arena.take((h, w, 3)) for _ in range(8)]
         for j in range(8):
             pools[cam.id][j].copy_(pool[j])
+    h2d = h2d_probe(torch, dev, [f for cid in pools for f in pools[cid]])
     # everything allocated so far lives for the whole run: keep it out of
     # the garbage collector's passes so they stay short while serving
     import gc
@@ -989,8 +990,80 @@ def run_serve(args, rank, local_rank, world):
         "latency_ms": lat, "latency_split_ms": split, "frames": st["frames"],
         "aggregate_mpixel_per_s": st["mpixel_per_s"],
         "frame_period_ms": 33.3, "p99_under_frame_period": lat["p99"] is not None and lat["p99"] < 33.3,
-        "clocks": clk,
+        "clocks": clk, "h2d_probe": h2d,
     }
+
+
+def _registered_copy(torch, frames, huge: bool):
+    """The pool's frames copied into one anonymous mapping (transparent huge
+    pages asked for, or refused) that is then page-locked with
+    cudaHostRegister; returns (tensors, release) or None."""
+    import mmap
+    total = sum((f.numel() + 255) // 256 * 256 for f in frames)
+    align = 512 << 20
+    try:
+        mm = mmap.mmap(-1, total + align, flags=mmap.MAP_PRIVATE | mmap.MAP_ANONYMOUS)
+        mm.madvise(mmap.MADV_HUGEPAGE if huge else mmap.MADV_NOHUGEPAGE)
+    except Exception:
+        return None
+    raw = np.frombuffer(mm, dtype=np.uint8)
+    off = (-raw.ctypes.data) % align
+    buf = torch.from_numpy(raw[off:off + total])
+    views, o = [], 0
+    for f in frames:
+        n = f.numel()
+        v = buf[o:o + n].view(f.shape)
+        v.copy_(f)
+        views.append(v)
+        o += (n + 255) // 256 * 256
+    cudart = torch.cuda.cudart()
+    if int(cudart.cudaHostRegister(buf.data_ptr(), total, 0)) != 0:
+        return None
+
+    def release():
+        cudart.cudaHostUnregister(buf.data_ptr())
+    return views, release, mm
+
+
+def h2d_probe(torch, dev, frames) -> dict:
+    """Host-to-device copy bandwidth from the serving pool's frames (the
+    server's arena: cog_host_alloc), timed with events on one stream: one
+    large frame copied 20 times, then every frame of the pool once, twice
+    over.  The same for copies of the pool in cudaHostAlloc memory (one
+    pinned tensor per frame, `hostalloc_`) and in memory with transparent
+    huge pages locked by cudaHostRegister (`reg_thp_`)."""
+    st = torch.cuda.Stream(dev)
+    big_n = max(f.numel() for f in frames)
+    dst = torch.empty(big_n, dtype=torch.uint8, device=dev)
+    out = {"pool_gb": round(sum(f.numel() for f in frames) / 1e9, 3), "frames": len(frames)}
+
+    def run(tag, fr):
+        big = max(fr, key=lambda f: f.numel())
+        with torch.cuda.stream(st):
+            for name, seq in (("hot", [big] * 20), ("pass1", fr), ("pass2", fr)):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                for f in seq:
+                    dst[:f.numel()].copy_(f.view(-1), non_blocking=True)
+                e1.record(st)
+                st.synchronize()
+                out[f"{tag}{name}_gbs"] = round(sum(f.numel() for f in seq) / (e0.elapsed_time(e1) / 1e3) / 1e9, 1)
+
+    run("", frames)
+    # the same frames in cudaHostAlloc memory, one pinned tensor each
+    pinned = [f.pin_memory() for f in frames]
+    run("hostalloc_", pinned)
+    del pinned
+    for tag, huge in (("reg_thp_", True),):
+        r = _registered_copy(torch, frames, huge)
+        if r is None:
+            out[tag + "error"] = "mapping or cudaHostRegister failed"
+            continue
+        views, release, mm = r
+        run(tag, views)
+        release()          # the copies have finished (run synchronises)
+        del views, mm      # the mapping goes with its last reference
+    return out
 
 
 def _oracle_sample(sc, rows, n_frames, t0):

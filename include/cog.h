@@ -279,11 +279,12 @@ cog_status cog_server_read_timeline(cog_server *s, float *submit_ms, float *wait
                                     int64_t *n);
 /* Per-step record of the completed steps: the host time the worker spent
  * issuing each step (enqueue_ms, in issue order) and, in parts_ms
- * (nullable, 8 floats per step, in completion order), that time split into
+ * (nullable, 10 floats per step, in completion order), that time split into
  * the frame uploads, the batched step (plan upload and graph launch) and
  * the mask downloads with the completion event, then the step's GPU times
  * from CUDA events: uploads, wait until the compute stream took the step,
- * batched step, wait until the download stream took it, downloads.  Copies
+ * batched step, wait until the download stream took it, downloads; then the
+ * step's frame count and the megabytes of frames it uploaded.  Copies
  * min(cap, completed) entries, *n = steps completed. */
 cog_status cog_server_read_steps(cog_server *s, float *enqueue_ms, float *parts_ms, int64_t cap, int64_t *n);
 /* Clears the counters, latency and step records and restarts the clock of
@@ -510,6 +511,19 @@ cog_status cog_profile_end(cog_ctx *ctx, double *stage01_ms, double *stage2_ms, 
  * limit applies to every kernel of the process on that device and ends with
  * the process. */
 cog_status cog_set_l2_fetch_bytes(int32_t bytes);
+
+/* Page-locked host memory for frames and masks that the copy engines move
+ * (cog_apply_host_frames, the frame server): anonymous memory, zeroed, then
+ * locked with cudaHostRegister; cog_host_free unlocks and unmaps it.  On the
+ * Grace host of a GB300, host-to-device copies out of such memory ran at
+ * 158-180 GB/s from its first use, where memory from cudaHostAlloc ran at
+ * 7 GB/s on a first pass over 3.6 GB and at 53-88 GB/s afterwards.  Any
+ * size (rounded up to whole pages); COG_ERR_OOM if the mapping fails,
+ * COG_ERR_CUDA if it cannot be locked; cog_host_free of a pointer not from
+ * cog_host_alloc returns COG_ERR_INVALID_ARG.  Thread-safe.  The library
+ * has no counterpart in the paper; this is deployment plumbing. */
+cog_status cog_host_alloc(size_t bytes, void **out);
+cog_status cog_host_free(void *ptr);
 
 /* Human-readable description of the context's last error ("" if none).
  * With ctx == NULL: the last error of a failed cog_create on this thread. */

@@ -113,6 +113,8 @@ def _load() -> C.CDLL:
         "cog_profile_begin": (C.c_int, [vp, i32]),
         "cog_set_launch": (C.c_int, [vp, i32, i32, i32]),
         "cog_set_l2_fetch_bytes": (C.c_int, [i32]),
+        "cog_host_alloc": (C.c_int, [sz, P(vp)]),
+        "cog_host_free": (C.c_int, [vp]),
         "cog_profile_end": (C.c_int, [vp, P(C.c_double), P(C.c_double), P(C.c_int64)]),
         "cog_last_error_string": (C.c_char_p, [vp]),
         "cog_destroy": (C.c_int, [vp]),
@@ -512,6 +514,17 @@ def _scheck(status: int, srv=None):
         raise CogError(status, msg.decode() if msg else "")
 
 
+def cog_host_alloc(nbytes: int) -> int:
+    """Page-locked host memory (cog_host_alloc); returns its address."""
+    p = C.c_void_p()
+    _check(lib.cog_host_alloc(int(nbytes), C.byref(p)))
+    return p.value
+
+
+def cog_host_free(ptr: int) -> None:
+    _check(lib.cog_host_free(ptr))
+
+
 def cog_server_create(ctxs) -> C.c_void_p:
     arr = (C.c_void_p * len(ctxs))(*[c.value if isinstance(c, C.c_void_p) else c for c in ctxs])
     srv = C.c_void_p()
@@ -573,14 +586,14 @@ def cog_server_read_timeline(srv):
 
 
 def cog_server_read_steps(srv):
-    """(enqueue ms [steps], parts ms [steps, 8]) of the completed steps: host
-    time per step; its split into uploads, batched step, downloads; then the
-    GPU times of uploads, compute wait, batched step, download wait,
-    downloads."""
+    """(enqueue ms [steps], parts [steps, 10]) of the completed steps: host
+    time per step; its split into uploads, batched step, downloads (ms);
+    then the GPU times of uploads, compute wait, batched step, download
+    wait, downloads (ms); then the step's frames and uploaded megabytes."""
     n = C.c_int64(0)
     _scheck(lib.cog_server_read_steps(srv, None, None, 0, C.byref(n)), srv)
     e = np.empty(n.value, np.float32)
-    parts = np.empty((n.value, 8), np.float32)
+    parts = np.empty((n.value, 10), np.float32)
     _scheck(lib.cog_server_read_steps(srv, e.ctypes.data, parts.ctypes.data, n.value, C.byref(n)), srv)
     return e, parts
 

@@ -1,11 +1,15 @@
 // cog_api.cu -- host side of the C ABI declared in include/cog.h: parameter
 // validation, the state layout, context lifetime, stream-ordered launches,
 // sticky error reporting, statistics and state export/import.
+#include <sys/mman.h>
+#include <unistd.h>
+
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -866,6 +870,51 @@ cog_status cog_set_l2_fetch_bytes(int32_t bytes)
     if (e != cudaSuccess) {
         cudaGetLastError();
         return set_err(nullptr, COG_ERR_CUDA, "cudaDeviceSetLimit: %s", cudaGetErrorString(e));
+    }
+    return COG_OK;
+}
+
+// page-locked host blocks handed out by cog_host_alloc: address -> length
+static std::mutex g_host_mu;
+static std::map<void *, size_t> g_host_blocks;
+
+cog_status cog_host_alloc(size_t bytes, void **out)
+{
+    if (!out || bytes == 0) return set_err(nullptr, COG_ERR_INVALID_ARG, "need bytes > 0 and out");
+    *out = nullptr;
+    const size_t page = (size_t)sysconf(_SC_PAGESIZE);
+    const size_t len = (bytes + page - 1) / page * page;
+    void *p = mmap(nullptr, len, PROT_READ | PROT_WRITE, MAP_PRIVATE | MAP_ANONYMOUS, -1, 0);
+    if (p == MAP_FAILED) return set_err(nullptr, COG_ERR_OOM, "mmap of %zu bytes failed", len);
+    memset(p, 0, len);   // every page present before it is locked
+    cudaError_t e = cudaHostRegister(p, len, cudaHostRegisterDefault);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        munmap(p, len);
+        return set_err(nullptr, COG_ERR_CUDA, "cudaHostRegister: %s", cudaGetErrorString(e));
+    }
+    std::lock_guard<std::mutex> lk(g_host_mu);
+    g_host_blocks[p] = len;
+    *out = p;
+    return COG_OK;
+}
+
+cog_status cog_host_free(void *ptr)
+{
+    size_t len = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_host_mu);
+        auto it = g_host_blocks.find(ptr);
+        if (it == g_host_blocks.end())
+            return set_err(nullptr, COG_ERR_INVALID_ARG, "not a block from cog_host_alloc");
+        len = it->second;
+        g_host_blocks.erase(it);
+    }
+    cudaError_t e = cudaHostUnregister(ptr);
+    munmap(ptr, len);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(nullptr, COG_ERR_CUDA, "cudaHostUnregister: %s", cudaGetErrorString(e));
     }
     return COG_OK;
 }

@@ -115,7 +115,22 @@ template <typename T> struct K1Px {
     uint32_t need1;           // bits: past stage 0
 };
 
-// Loads and stage 0 of a thread's pixels p0 .. p0 + 3.
+// A thread's stage-0 inputs copied ahead into shared memory by the batched
+// stage-0/1 kernel (previous frame + label, confidence words, frame words).
+template <typename T> struct K1Slot {
+    const uint4 *jl;
+    const uint32_t *cv;
+    const uint32_t *fr;
+};
+template <typename T, int TPB> struct K1Pre {
+    uint4 jl[TPB];
+    uint32_t cv[TPB][VecN<T, PPT>::NW];
+    uint32_t fr[TPB][4];
+    __device__ __forceinline__ K1Slot<T> slot(int tid) const { return {&jl[tid], cv[tid], fr[tid]}; }
+};
+
+// Loads and stage 0 of a thread's pixels p0 .. p0 + 3 (PF: a full group
+// whose inputs were copied ahead, with no temporal sampling).
 //   Stage 0 (Sec. 2, CHP): a background pixel whose D = max_c |I_c - J_c|
 //   is at most tau_fd (0.5 + C-) keeps its label.  D is an integer, so the
 //   test is D <= floor(tau).
@@ -123,8 +138,8 @@ template <typename T> struct K1Px {
 //   frame off its 64-pixel block's phase, a pixel with C- >= c_skip is not
 //   looked at (a group of 4 never straddles two blocks); a group whose
 //   pixels are all skipped reads no frame bytes.
-template <typename T, bool FULL>
-__device__ __forceinline__ void k1_stage0(const ApplyArgs &A, K1Px<T> &X, uint32_t p0)
+template <typename T, bool FULL, bool PF = false>
+__device__ __forceinline__ void k1_stage0(const ApplyArgs &A, K1Px<T> &X, uint32_t p0, const K1Slot<T> *pf = nullptr)
 {
     const DevParams &dp = A.dp;
     const bool conf_on = dp.flags & COG_CONF;
@@ -136,7 +151,12 @@ __device__ __forceinline__ void k1_stage0(const ApplyArgs &A, K1Px<T> &X, uint32
     X.jl = make_uint4(0, 0, 0, 0);
 #pragma unroll
     for (int i = 0; i < VecN<T, PPT>::NW; i++) X.cv.w[i] = 0;
-    if (FULL || nact > 0) {
+    if (PF) {
+        X.jl = *pf->jl;
+#pragma unroll
+        for (int i = 0; i < VecN<T, PPT>::NW; i++) X.cv.w[i] = pf->cv[i];
+        w0 = pf->fr[0]; w1 = pf->fr[1]; w2 = pf->fr[2];
+    } else if (FULL || nact > 0) {
         // the planes are padded to whole 4-pixel groups: vector loads stay in bounds
         X.jl = *reinterpret_cast<const uint4 *>(A.s.jl + p0);
         X.cv.load(reinterpret_cast<const T *>(A.s.conf) + p0);
@@ -247,6 +267,18 @@ __device__ __forceinline__ uint32_t k1_own_out(const ApplyArgs &A, const K1Px<T>
     return fd;
 }
 
+// Shared memory of a stage-0/1 CTA: its stage-1 list and per-warp counts.
+template <typename T, int TPB> struct K1Shared {
+    K1List<T, TPB * PPT> L;
+    uint32_t wcnt[TPB / 32];
+    uint32_t cnt[TPB / 32][4];
+};
+template <typename T, int TPB> __device__ __forceinline__ K1Shared<T, TPB> &k1_shared()
+{
+    __shared__ K1Shared<T, TPB> sh;
+    return sh;
+}
+
 // One CTA of the stage-0/1 pass over stream A: tile `cta` of its frame
 // (CPX = 4 TPB consecutive pixels, each thread owning 4 of them).
 //   1. every thread loads its pixels, runs stage 0 and writes its outputs;
@@ -259,16 +291,17 @@ __device__ __forceinline__ uint32_t k1_own_out(const ApplyArgs &A, const K1Px<T>
 //      queue segment of the warp (one atomic per warp pass);
 //   4. the stage counts are summed over the CTA and added to the frame's
 //      counters once.
-template <typename T, int TPB>
-__device__ __forceinline__ void k1_cta(const ApplyArgs &A, uint32_t cta)
+template <typename T, int TPB, bool PF = false>
+__device__ __forceinline__ void k1_cta(const ApplyArgs &A, uint32_t cta, const K1Slot<T> *pf = nullptr)
 {
     static_assert(PPT == 4 && K1_G == 1, "frame and mask vector widths assume one group of 4 pixels per thread");
     constexpr int NW = TPB / 32, CPX = TPB * PPT;
     constexpr bool WIDE = Store<T>::bytes == 4;
     static_assert(CPX <= 65536, "slots fit 16 bits");
-    __shared__ K1List<T, CPX> L;
-    __shared__ uint32_t wcnt_s[NW];
-    __shared__ uint32_t cnt_s[NW][4];
+    K1Shared<T, TPB> &sh = k1_shared<T, TPB>();   // one copy per kernel, whichever variants it inlines
+    K1List<T, CPX> &L = sh.L;
+    uint32_t(&wcnt_s)[NW] = sh.wcnt;
+    uint32_t(&cnt_s)[NW][4] = sh.cnt;
     const DevParams &dp = A.dp;
     const bool conf_on = dp.flags & COG_CONF;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -295,7 +328,10 @@ __device__ __forceinline__ void k1_cta(const ApplyArgs &A, uint32_t cta)
     // ---- 1. stage 0 and the owners' outputs
     K1Px<T> X;
     uint32_t fd;
-    if ((int64_t)cbase + CPX <= dp.P) {
+    if (PF) {
+        k1_stage0<T, true, true>(A, X, p0, pf);
+        fd = k1_own_out<T, true>(A, X, p0);
+    } else if ((int64_t)cbase + CPX <= dp.P) {
         k1_stage0<T, true>(A, X, p0);
         fd = k1_own_out<T, true>(A, X, p0);
     } else {
@@ -639,6 +675,137 @@ __device__ __forceinline__ void k2_cta(const ApplyArgs &A, uint32_t cta, uint32_
     if (tid < 3 && cnt_s[tid]) atomicAdd(ctl + ctl_slot(n % 3, 2 + tid, cta & (CTL_SLOTS - 1)), cnt_s[tid]);
 }
 
+// The same walk over stream A's survivor queue, software-pipelined for a
+// CTA that takes many survivors per thread (the batched step): each thread
+// loads queue entries two survivors ahead into registers, and copies the
+// next survivor's record, its three prior words (and with COG_MODE1 its
+// stage-1 record) into its own shared-memory slot with cp.async while it
+// runs the mixture step of the current one.  No thread reads another's
+// slot, so the per-thread copy groups need no barrier.
+template <typename T, int K, int TPB, int V> struct K2Pipe {
+    static constexpr bool PC = V == 1, M1 = V == 2;
+    static constexpr int RNV = RecSel<T, K, PC>::NV;
+    static constexpr int SNV = M1 ? S1Rec<T>::NV : 0;
+    static constexpr int W = RNV + SNV + 1;   // uint4 words per slot: record, stage-1 record, prior words
+    uint4 slot[2][W][TPB];                    // [buffer][word][thread]: consecutive threads, consecutive words
+};
+
+template <typename T, int K, int TPB, int V>
+__device__ __forceinline__ void k2_issue_copies(const ApplyArgs &A, K2Pipe<T, K, TPB, V> &S, int b, uint4 e)
+{
+    using PP = K2Pipe<T, K, TPB, V>;
+    const int tid = threadIdx.x;
+    const int64_t p = e.x;
+    const uint8_t *rec = A.s.gmm + p * RecSel<T, K, PP::PC>::BYTES;
+#pragma unroll
+    for (int i = 0; i < PP::RNV; i++) cp_async16(&S.slot[b][i][tid], rec + 16 * i);
+    if constexpr (PP::M1) {
+#pragma unroll
+        for (int i = 0; i < PP::SNV; i++)
+            cp_async16(&S.slot[b][PP::RNV + i][tid], A.s.s1 + p * S1Rec<T>::BYTES + 16 * i);
+    }
+    // the aligned word holding each channel's prior level
+    uint32_t *pw = reinterpret_cast<uint32_t *>(&S.slot[b][PP::W - 1][tid]);
+    const bool four = A.dp.kde_bits == 4;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const uint32_t v = (e.y >> (8 * c)) & 0xffu;
+        const int64_t byte = four ? (p * 3 + c) * 128 + (v >> 1) : (p * 3 + c) * 256 + v;
+        cp_async4(pw + c, A.s.kde + (byte & ~(int64_t)3));
+    }
+}
+
+template <typename T, int K, int TPB, int V>
+__device__ __forceinline__ void k2_cta_pipe(const ApplyArgs &A, uint32_t cta, uint32_t ncta)
+{
+    using PP = K2Pipe<T, K, TPB, V>;
+    __shared__ PP S;
+    __shared__ uint32_t flag_s, cnt_s[3], segp_s[QSEG + 1];
+    const DevParams &dp = A.dp;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const uint32_t n = A.frame_no;
+    uint32_t *ctl = A.s.ctl;
+    if (tid < 32) {
+        const bool f = illum_flag_prev(dp, ctl, n, lane);
+        const uint32_t len = __ldcg(ctl + ctl_qcnt(n % 3, lane));
+        uint32_t incl = len;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += t;
+        }
+        segp_s[lane] = incl - len;
+        if (lane == 31) segp_s[QSEG] = incl;
+        if (lane == 0) flag_s = f;
+    }
+    if (tid < 3) cnt_s[tid] = 0;
+    __syncthreads();
+    const bool flag = flag_s;
+    const uint32_t nq = segp_s[QSEG];
+    const uint32_t stride = ncta * TPB;
+    // queue entry of flat index q; x = 0xffffffff marks a missing entry
+    auto load_entry = [&](uint32_t q) -> uint4 {
+        if (q >= nq) return make_uint4(0xffffffffu, 0, 0, 0);
+        int lo = 0;
+#pragma unroll
+        for (int step = QSEG / 2; step >= 1; step >>= 1)
+            if (segp_s[lo + step] <= q) lo += step;
+        if (!in_bounds(ctl, q - segp_s[lo], (uint64_t)A.s.qseg_cap, DBG_K2_QUEUE)) return make_uint4(0xffffffffu, 0, 0, 0);
+        uint4 e = __ldcg(A.s.queue + (int64_t)lo * A.s.qseg_cap + (q - segp_s[lo]));
+        if (!in_bounds(ctl, (uint64_t)e.x, (uint64_t)dp.P, DBG_K2_PIXEL)) e.x = 0xffffffffu;
+        return e;
+    };
+    const uint32_t q0 = cta * TPB + tid;
+    uint4 ea = load_entry(q0), eb = load_entry(q0 + stride);
+    if (ea.x != 0xffffffffu) k2_issue_copies<T, K, TPB, V>(A, S, 0, ea);
+    cp_async_commit();
+    uint32_t cbg = 0, cfg = 0, cil = 0;
+    int b = 0;
+    for (uint32_t q = q0; q < nq; q += stride, b ^= 1) {
+        const uint4 ec = load_entry(q + 2 * stride);
+        if (eb.x != 0xffffffffu) k2_issue_copies<T, K, TPB, V>(A, S, b ^ 1, eb);
+        cp_async_commit();
+        cp_async_wait<1>();   // this survivor's copies (the group before the one just committed)
+        if (ea.x != 0xffffffffu) {
+            S2In<T, K, PP::PC> a;
+            a.e = ea;
+#pragma unroll
+            for (int i = 0; i < PP::RNV; i++) a.rec[i] = S.slot[b][i][tid];
+            if constexpr (PP::M1) {
+#pragma unroll
+                for (int i = 0; i < PP::SNV; i++) a.s1.u[i] = S.slot[b][PP::RNV + i][tid];
+            }
+            const uint4 w = S.slot[b][PP::W - 1][tid];
+            const uint32_t wv[3] = {w.x, w.y, w.z};
+            const bool four = dp.kde_bits == 4;
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                const uint32_t v = (ea.y >> (8 * c)) & 0xffu;
+                const uint32_t byte = four ? (v >> 1) : v;   // the byte's offset within the row
+                const uint32_t x = (wv[c] >> (8 * (byte & 3u))) & 0xffu;   // rows start word-aligned
+                a.qk[c] = four ? 17u * ((x >> ((v & 1u) << 2)) & 15u) : x;
+            }
+            int st;
+            if constexpr (PP::PC) st = s2_finish_pc<T, K>(A, a, flag);
+            else st = s2_finish<T, K, PP::M1>(A, a, flag);
+            cbg += st == COG_ST_GMM_BG; cfg += st == COG_ST_FG; cil += st == COG_ST_ILLUM;
+        }
+        ea = eb;
+        eb = ec;
+    }
+    cp_async_wait<0>();
+    cbg = __reduce_add_sync(0xffffffffu, cbg);
+    cfg = __reduce_add_sync(0xffffffffu, cfg);
+    cil = __reduce_add_sync(0xffffffffu, cil);
+    if (lane == 0) {
+        if (cbg) atomicAdd(&cnt_s[0], cbg);
+        if (cfg) atomicAdd(&cnt_s[1], cfg);
+        if (cil) atomicAdd(&cnt_s[2], cil);
+    }
+    __syncthreads();
+    if (tid < 3 && cnt_s[tid]) atomicAdd(ctl + ctl_slot(n % 3, 2 + tid, cta & (CTL_SLOTS - 1)), cnt_s[tid]);
+}
+
 template <typename T, int K, int TPB, int V>
 __global__ void __launch_bounds__(TPB) stage2_kernel(const ApplyArgs A)
 {
@@ -660,21 +827,61 @@ __device__ __forceinline__ int batch_stream(const uint32_t *pre, int n, uint32_t
 }
 
 // A persistent grid walks the active streams' tiles (the step plan's
-// prefix gives inactive streams no tiles).
+// prefix gives inactive streams no tiles).  Each thread copies its next
+// tile's stage-0 inputs into its shared slot with cp.async while the CTA
+// runs the current tile, for full tiles of streams with 4-byte aligned
+// frames and no temporal sampling (the others load as they go).
 template <typename T, int TPB>
 __global__ void __launch_bounds__(TPB, K1_THREADS_PER_SM / TPB) stage01_batch_kernel(const BatchGroupDev G)
 {
+    __shared__ K1Pre<T, TPB> pre[2];
     grid_launch_dependents();
     grid_wait_prior();
+    const int tid = threadIdx.x;
     const uint32_t total = __ldg(G.k1_pre + G.n);
-    for (uint32_t t = blockIdx.x; t < total; t += gridDim.x) {
-        const int s = batch_stream(G.k1_pre, G.n, t);
-        if (!in_bounds(G.descs[0].s.ctl, (uint64_t)s, (uint64_t)G.n, DBG_BATCH_STREAM)) break;
-        const uint32_t tile = t - __ldg(G.k1_pre + s);
-        if (!in_bounds(G.descs[s].s.ctl, (uint64_t)tile * TPB * PPT, (uint64_t)G.descs[s].dp.P, DBG_BATCH_TILE))
-            continue;   // the same for every thread of the CTA
-        k1_cta<T, TPB>(G.descs[s], tile);
+    // stream and tile of the CTA's t-th tile; false past the end or on a
+    // failed check (the same for every thread of the CTA)
+    auto locate = [&](uint32_t t, int &s, uint32_t &tile) -> bool {
+        if (t >= total) return false;
+        s = batch_stream(G.k1_pre, G.n, t);
+        if (!in_bounds(G.descs[0].s.ctl, (uint64_t)s, (uint64_t)G.n, DBG_BATCH_STREAM)) return false;
+        tile = t - __ldg(G.k1_pre + s);
+        return in_bounds(G.descs[s].s.ctl, (uint64_t)tile * TPB * PPT, (uint64_t)G.descs[s].dp.P, DBG_BATCH_TILE);
+    };
+    auto prefetch = [&](const ApplyArgs &A, uint32_t tile, int b) -> bool {
+        const uint32_t cbase = tile * TPB * PPT, p0 = cbase + (uint32_t)tid * PPT;
+        if ((int64_t)cbase + TPB * PPT > A.dp.P || !A.frame_al4 || (A.dp.flags & COG_SAMPLE)) return false;
+        cp_async16(&pre[b].jl[tid], A.s.jl + p0);
+        const T *cv = reinterpret_cast<const T *>(A.s.conf) + p0;
+        if (VecN<T, PPT>::NW == 4) cp_async16(pre[b].cv[tid], cv);
+        else cp_async8(pre[b].cv[tid], cv);
+        const uint8_t *f = A.frame + (size_t)p0 * 3;
+#pragma unroll
+        for (int i = 0; i < 3; i++) cp_async4(&pre[b].fr[tid][i], f + 4 * i);
+        return true;
+    };
+    uint32_t t = blockIdx.x, tile = 0;
+    int s = 0, b = 0;
+    bool ok = locate(t, s, tile);
+    bool pf = ok && prefetch(G.descs[s], tile, 0);
+    cp_async_commit();
+    while (ok) {
+        const uint32_t tn = t + gridDim.x;
+        uint32_t tile_n = 0;
+        int sn = 0;
+        const bool ok_n = locate(tn, sn, tile_n);
+        const bool pf_n = ok_n && prefetch(G.descs[sn], tile_n, b ^ 1);
+        cp_async_commit();
+        cp_async_wait<1>();   // this tile's copies (the group before the one just committed)
+        if (pf) {
+            const K1Slot<T> sl = pre[b].slot(tid);
+            k1_cta<T, TPB, true>(G.descs[s], tile, &sl);
+        } else {
+            k1_cta<T, TPB>(G.descs[s], tile);
+        }
+        t = tn; s = sn; tile = tile_n; ok = ok_n; pf = pf_n; b ^= 1;
     }
+    cp_async_wait<0>();
 }
 
 // The mixture-stage CTAs are split among the active streams only.
@@ -686,7 +893,12 @@ __global__ void __launch_bounds__(TPB) stage2_batch_kernel(const BatchGroupDev G
     if (blockIdx.x >= __ldg(G.k2_pre + G.n)) return;
     const int s = batch_stream(G.k2_pre, G.n, blockIdx.x);
     if (!in_bounds(G.descs[0].s.ctl, (uint64_t)s, (uint64_t)G.n, DBG_BATCH_STREAM)) return;
-    k2_cta<T, K, TPB, V>(G.descs[s], blockIdx.x - G.k2_pre[s], G.k2_pre[s + 1] - G.k2_pre[s]);
+    // a batch gives each CTA many survivors per thread: the pipelined walk,
+    // where its shared slots fit
+    if constexpr (sizeof(K2Pipe<T, K, TPB, V>) <= 40 * 1024)
+        k2_cta_pipe<T, K, TPB, V>(G.descs[s], blockIdx.x - G.k2_pre[s], G.k2_pre[s + 1] - G.k2_pre[s]);
+    else
+        k2_cta<T, K, TPB, V>(G.descs[s], blockIdx.x - G.k2_pre[s], G.k2_pre[s + 1] - G.k2_pre[s]);
 }
 
 // Launch with programmatic stream serialization: the kernel may be

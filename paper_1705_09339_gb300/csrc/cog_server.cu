@@ -56,6 +56,9 @@ constexpr auto COMPLETION_SPIN = std::chrono::microseconds(3000);
 //   2 batched step starts, 3 batched step done (compute stream),
 //   4 downloads start, 5 downloads done (down stream)
 constexpr int STEP_TIMERS = 6;
+// Floats per completed step in the step record: 3 host times, 5 GPU times,
+// the frames of the step and the megabytes it uploaded
+constexpr int STEP_RECORD = 10;
 
 struct Pending {
     const uint8_t *frame;   // host, height x width x 3
@@ -137,7 +140,7 @@ struct cog_server {
     std::vector<float> sub_ms;           // submission time of each done frame, since creation
     std::vector<float> wait_ms;          // submission -> taken by the worker, per done frame
     std::vector<float> enq_ms;           // per step issued: host time to issue it
-    std::vector<float> step_parts_ms;    // per step completed: 3 host parts, then 5 GPU times
+    std::vector<float> step_parts_ms;    // per step completed: STEP_RECORD floats
     int64_t frames = 0, pixels = 0, steps = 0, submitted = 0;
     int steps_in_flight = 0;             // issued and not yet completed (under mu)
     clk::time_point t0;
@@ -470,6 +473,10 @@ static void server_completer(cog_server *s)
             s->steps_in_flight--;
             s->step_parts_ms.insert(s->step_parts_ms.end(), step.host_parts, step.host_parts + 3);
             s->step_parts_ms.insert(s->step_parts_ms.end(), g, g + 5);
+            int64_t up_bytes = 0;
+            for (const Pick &k : step.picks) up_bytes += s->streams[k.stream].P * 3;
+            s->step_parts_ms.push_back((float)step.picks.size());
+            s->step_parts_ms.push_back((float)((double)up_bytes / 1e6));
             for (const Pick &k : step.picks) {
                 Stream &q = s->streams[k.stream];
                 q.inflight--;
@@ -741,11 +748,11 @@ cog_status cog_server_read_steps(cog_server *s, float *enqueue_ms, float *parts_
 {
     if (!s || !n || cap < 0 || (cap > 0 && !enqueue_ms)) return COG_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(s->mu);
-    const int64_t done = (int64_t)(s->step_parts_ms.size() / 8);
+    const int64_t done = (int64_t)(s->step_parts_ms.size() / STEP_RECORD);
     const int64_t m = std::min<int64_t>(cap, done);
     if (m > 0) {
         memcpy(enqueue_ms, s->enq_ms.data(), sizeof(float) * (size_t)std::min<int64_t>(m, (int64_t)s->enq_ms.size()));
-        if (parts_ms) memcpy(parts_ms, s->step_parts_ms.data(), sizeof(float) * 8 * (size_t)m);
+        if (parts_ms) memcpy(parts_ms, s->step_parts_ms.data(), sizeof(float) * STEP_RECORD * (size_t)m);
     }
     *n = done;
     return COG_OK;

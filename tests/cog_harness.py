@@ -125,7 +125,7 @@ def oracle_state(o):
                 prev=s.prev, kde=s.kde, qa=s.qa, qb=s.qb, top=s.top, wc=s.wc)
 
 
-def random_state(rng, P, K, dtype="f32", fg_frac=0.2, mode1=False, perchan=False, kde_bits=8):
+def random_state(rng, P, K, dtype="f32", fg_frac=0.2, mode1=False, perchan=False, kde_bits=8, kde_const=None):
     """A seeded model state with the value ranges the method produces,
     rounded to the storage type so both sides start from the same values."""
     q = {"f32": np.float32, "f16": np.float16, "bf16": None}[dtype]
@@ -149,7 +149,10 @@ def random_state(rng, P, K, dtype="f32", fg_frac=0.2, mode1=False, perchan=False
     conf = rng.uniform(0, 1, P)
     qa = rng.integers(0, 256, P)
     qb = np.minimum(rng.integers(0, 256, P), 255 - qa)
-    if kde_bits == 4:
+    if kde_const is not None:
+        # one level everywhere (large frames: no random table of P x 768)
+        kde = np.full((P, 3, 256), kde_const, np.uint8)
+    elif kde_bits == 4:
         # levels of 15; level 0 (17 * 0 < q_null = 13) is the nullified one
         kde = rng.integers(0, 16, (P, 3, 256)).astype(np.uint8)
         kde[rng.random((P, 3, 256)) < 0.3] = 0

@@ -104,6 +104,10 @@ def test_server_add_rejects_bad_arguments(cog):
     idx = C.c_int32(0)
     assert cog.lib.cog_server_add(None, None, C.byref(idx)) == cog.COG_ERR_INVALID_ARG
     assert cog.lib.cog_server_remove(None, 0, None) == cog.COG_ERR_INVALID_ARG
+    ptr = C.c_void_p()
+    assert cog.lib.cog_host_alloc(0, C.byref(ptr)) == cog.COG_ERR_INVALID_ARG
+    assert cog.lib.cog_host_alloc(16, None) == cog.COG_ERR_INVALID_ARG
+    assert cog.lib.cog_host_free(None) == cog.COG_ERR_INVALID_ARG   # not a block of cog_host_alloc
 
 
 def test_group_rejects_bad_arguments(cog):

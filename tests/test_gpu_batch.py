@@ -19,11 +19,13 @@ def cog():
     return cog
 
 
-# "+pc": per-channel mixtures (a group of its own in the batch); "+q4": the
-# 4-bit scene prior (in the same group as the 8-bit streams)
+# "+pc": per-channel mixtures, "+m1": stage 1 as the rank-1 mode (each a
+# group of its own in the batch); "+q4": the 4-bit scene prior (in the same
+# group as the 8-bit streams)
 SPECS = [(160, 120, 3, "f32"), (320, 240, 5, "f16"), (97, 61, 3, "f32"), (640, 480, 5, "f16"),
          (33, 1, 5, "f16"), (200, 100, 3, "bf16"), (160, 120, 5, "f16"), (128, 96, 5, "f16+pc"),
-         (64, 48, 3, "f32+pc"), (176, 144, 5, "f16+q4"), (45, 31, 3, "f32+pc+q4")]
+         (64, 48, 3, "f32+pc"), (176, 144, 5, "f16+q4"), (45, 31, 3, "f32+pc+q4"), (120, 90, 5, "f16+m1"),
+         (96, 40, 3, "f32+m1+q4")]
 
 
 def _streams(n_train=20, n_test=6):
@@ -43,6 +45,8 @@ def _ctx(cog, w, h, k, dt, fr, n_train, stream):
         p.flags |= cog.COG_PERCHAN
     if "q4" in opts:
         p.kde_bits = 4
+    if "m1" in opts:
+        p.flags |= cog.COG_MODE1
     c = cog.cog_create(p, stream)
     t = torch.from_numpy(fr[:n_train].reshape(n_train, h, w, 3)).cuda()
     cog.cog_train_prior(c, t, n_train)
@@ -162,3 +166,48 @@ def _batch_vs_oracle(cog, specs, NT, NF, s):
             assert e[key] <= 1e-4, (i, key, e[key])
         for key in ("label", "prev", "qa", "qb"):
             assert e[key] == 0, (i, key)
+
+
+@pytest.mark.parametrize("K,dt,flags", [(5, "f16", 15), (3, "f32", 15 | 32), (5, "bf16", 15 | 64)])
+def test_batch_many_survivors_per_thread(cog, K, dt, flags):
+    # seeded random states and frames send most pixels to the mixture stage,
+    # so each of the batch's mixture-stage threads walks many survivors (its
+    # software pipeline runs many rounds); batched and single-stream
+    # application must agree bit for bit
+    from cog_harness import random_frame, random_state, to_cog, params
+    W, H = 1280, 720
+    P = W * H
+    rng = np.random.default_rng(60 + K + flags)
+    st = random_state(rng, P, K, dtype=dt, mode1=bool(flags & 32), perchan=bool(flags & 64), kde_const=60)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ctxs = []
+        for _ in range(2):
+            p = to_cog(params(W, H, K, flags=flags), dt)
+            c = cog.cog_create(p, s.cuda_stream)
+            z = torch.zeros((2, H, W, 3), dtype=torch.uint8, device="cuda")
+            cog.cog_train_prior(c, z, 2)
+            buf = cog.cog_export_state(c, p)
+            cog.cog_import_state(c, cog.encode_state(buf, p, st))
+            ctxs.append((c, p))
+        b = cog.cog_batch_create([ctxs[1][0]], s.cuda_stream)
+        ms = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+        mb = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+        for t in range(3):
+            f = torch.from_numpy(random_frame(rng, st, mix=(0.1, 0.5, 0.4)).reshape(H, W, 3)).cuda()
+            cog.cog_apply(ctxs[0][0], f, ms)
+            cog.cog_batch_apply(b, [f], [mb])
+            cog.cog_batch_sync(b)
+            cog.cog_sync(ctxs[0][0])
+            assert torch.equal(ms, mb), t
+        la, _ = cog.cog_read_stats(ctxs[0][0])
+        lb, _ = cog.cog_read_stats(ctxs[1][0])
+        assert la == lb and la["n_gmm"] > P // 3
+        sa = cog.decode_state(cog.cog_export_state(*ctxs[0]), ctxs[0][1])
+        sb = cog.decode_state(cog.cog_export_state(*ctxs[1]), ctxs[1][1])
+        for key in ("w", "wc", "mu", "var", "rga_m", "rga_v", "conf", "label", "prev", "top"):
+            if key in sa:
+                assert np.array_equal(sa[key], sb[key]), key
+        cog.cog_batch_destroy(b)
+        for c, _ in ctxs:
+            cog.cog_destroy(c)
