@@ -580,6 +580,8 @@ def run_profile_case(args, rank, local_rank, world):
     if args.sample:
         p.flags |= cog.COG_SAMPLE
     ctx = cog.cog_create(p, stream.cuda_stream)
+    if args.launch:
+        cog.cog_set_launch(ctx, *[int(x) for x in args.launch.split(",")])
     cog.cog_train_prior(ctx, train, n_train)
     cog.cog_sync(ctx)
     del train
@@ -927,7 +929,10 @@ def run_serve(args, rank, local_rank, world):
     while len(sizes) < nc:
         sizes.append(SIZES[[0, 1, 3, 4][len(sizes) % 4]])
     rng.shuffle(sizes)
-    srv = FrameServer(dev, reserve_bytes=8 << 30)
+    srv = FrameServer(dev, reserve_bytes=8 << 30, frame_memory=args.frame_mem, mask_memory=args.mask_mem)
+    # every camera's frame pool from one block taken before anything else
+    # (huge pages are plentiful before the process's memory fragments)
+    srv.arena.reserve(sum(8 * ((w * h * 3 + 255) // 256 * 256) for (w, h) in sizes))
     pools = {}
     for i, (w, h) in enumerate(sizes):
         sc = Scene(w, h, 7000 + 1000 * rank + i, kind="dynamic", n_train=100, fg_frac=float(rng.uniform(0.01, 0.05)))
@@ -940,15 +945,17 @@ def run_serve(args, rank, local_rank, world):
         for j in range(8):
             pools[cam.id][j].copy_(pool[j])
     h2d = h2d_probe(torch, dev, [f for cid in pools for f in pools[cid]])
+    h2d["arena_huge_kb"] = [_huge_kb(int(t.data_ptr()), t.numel()) for _, t in srv.arena.blocks]
     # everything allocated so far lives for the whole run: keep it out of
     # the garbage collector's passes so they stay short while serving
     import gc
     gc.collect()
     gc.freeze()
-    # two warm-up frames per camera (both of its device slots, the batch
-    # graph's first launch), left out of the statistics; the Poisson stream
+    # warm-up, left out of the statistics: every frame buffer of every
+    # camera once (both device slots, the batch graph's first launch, and
+    # each host buffer's first copy, which ran slower); the Poisson stream
     # then continues each camera's frames
-    srv.start(warmup_frames={cid: pools[cid][:2] for cid in pools})
+    srv.start(warmup_frames={cid: pools[cid] for cid in pools})
     clocks = Clocks(local_rank)
     clocks.start()
     t0 = time.perf_counter()
@@ -1025,7 +1032,75 @@ def _registered_copy(torch, frames, huge: bool):
     return views, release, mm
 
 
-def h2d_probe(torch, dev, frames) -> dict:
+def _huge_kb(addr: int, nbytes: int) -> int:
+    """AnonHugePages (kB) of the mappings overlapping [addr, addr + nbytes)."""
+    tot, cur = 0, False
+    try:
+        with open("/proc/self/smaps") as f:
+            for line in f:
+                head = line.split()[0]
+                if "-" in head and not head.endswith(":"):
+                    a, b = (int(x, 16) for x in head.split("-"))
+                    cur = a < addr + nbytes and b > addr
+                elif cur and head == "AnonHugePages:":
+                    tot += int(line.split()[1])
+    except OSError:
+        return -1
+    return tot
+
+
+def run_h2d(args, rank, local_rank, world):
+    """Host-to-device copy probe alone: 2048 frames of the serving size mix
+    (3.6 GB) in each kind of page-locked memory (the serving arena's
+    cog_host_alloc blocks, cudaHostAlloc blocks, one cog_host_alloc block,
+    one huge-page mapping locked after it is written), with the huge pages
+    each received."""
+    import torch
+    from paper_1705_09339_gb300 import cog
+    from paper_1705_09339_gb300.serve import PinnedArena
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    torch.zeros(1, device=dev)
+    sizes = [SIZES[2]] * 102 + [SIZES[[0, 1, 3, 4][i % 4]] for i in range(154)]
+    shapes = [(h, w, 3) for (w, h) in sizes for _ in range(8)]
+    out = {"thp_pmd_bytes": None}
+    try:
+        out["thp_pmd_bytes"] = int(open("/sys/kernel/mm/transparent_hugepage/hpage_pmd_size").read())
+        out["thp_enabled"] = open("/sys/kernel/mm/transparent_hugepage/enabled").read().strip()
+    except OSError:
+        pass
+    for kind in ("registered", "hostalloc"):
+        ar = PinnedArena(kind=kind)
+        fr = [ar.take(sh) for sh in shapes]
+        for i, f in enumerate(fr):
+            f.fill_(i & 255)
+        r = h2d_probe(torch, dev, fr, variants=False)
+        out[kind] = {k: v for k, v in r.items() if k.endswith("_gbs")}
+        out[kind]["huge_kb"] = [_huge_kb(int(t.data_ptr()), t.numel()) for _, t in ar.blocks]
+        del fr
+        ar.release()
+    # one cog_host_alloc block for the whole pool
+    total = sum((int(np.prod(sh)) + 255) // 256 * 256 for sh in shapes)
+    addr = cog.cog_host_alloc(total)
+    import ctypes
+    arr = np.ctypeslib.as_array(ctypes.cast(addr, ctypes.POINTER(ctypes.c_uint8)), shape=(total,))
+    buf = torch.from_numpy(arr)
+    fr, o = [], 0
+    for sh in shapes:
+        n = int(np.prod(sh))
+        fr.append(buf[o:o + n].view(sh))
+        o += (n + 255) // 256 * 256
+    for i, f in enumerate(fr):
+        f.fill_(i & 255)
+    r = h2d_probe(torch, dev, fr, variants=False)
+    out["one_block"] = {k: v for k, v in r.items() if k.endswith("_gbs")}
+    out["one_block"]["huge_kb"] = _huge_kb(addr, total)
+    del fr, buf, arr
+    cog.cog_host_free(addr)
+    return {"metric": "host-to-device copy probe", "h2d": out}
+
+
+def h2d_probe(torch, dev, frames, variants: bool = True) -> dict:
     """Host-to-device copy bandwidth from the serving pool's frames (the
     server's arena: cog_host_alloc), timed with events on one stream: one
     large frame copied 20 times, then every frame of the pool once, twice
@@ -1050,6 +1125,26 @@ def h2d_probe(torch, dev, frames) -> dict:
                 out[f"{tag}{name}_gbs"] = round(sum(f.numel() for f in seq) / (e0.elapsed_time(e1) / 1e3) / 1e9, 1)
 
     run("", frames)
+    if not variants:
+        return out
+
+    # device-to-host into mask-sized buffers (one byte per pixel) of each kind
+    def run_d2h(tag, dsts):
+        src = torch.zeros(big_n, dtype=torch.uint8, device=dev)
+        with torch.cuda.stream(st):
+            for name in ("pass1", "pass2"):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                for d in dsts:
+                    d.copy_(src[:d.numel()], non_blocking=True)
+                e1.record(st)
+                st.synchronize()
+                out[f"d2h_{tag}{name}_gbs"] = round(sum(d.numel() for d in dsts) / (e0.elapsed_time(e1) / 1e3) / 1e9, 1)
+    from paper_1705_09339_gb300.serve import PinnedArena
+    for kind in ("registered", "hostalloc"):
+        ar = PinnedArena(kind=kind)
+        run_d2h(kind + "_", [ar.take((f.numel() // 3,)) for f in frames])
+        ar.release()
     # the same frames in cudaHostAlloc memory, one pinned tensor each
     pinned = [f.pin_memory() for f in frames]
     run("hostalloc_", pinned)
@@ -1061,6 +1156,7 @@ def h2d_probe(torch, dev, frames) -> dict:
             continue
         views, release, mm = r
         run(tag, views)
+        out[tag + "huge_kb"] = _huge_kb(int(views[0].data_ptr()), sum(v.numel() for v in views))
         release()          # the copies have finished (run synchronises)
         del views, mm      # the mapping goes with its last reference
     return out
@@ -1240,10 +1336,16 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fg", type=float, default=0.02)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="hd", choices=["hd", "clip", "batch64", "serve", "group", "profile"])
+    ap.add_argument("--workload", default="hd", choices=["hd", "clip", "batch64", "serve", "group", "profile", "h2d"])
     ap.add_argument("--duration", type=float, default=20.0, help="serve: seconds of camera traffic")
     ap.add_argument("--cameras", type=int, default=256, help="serve: cameras")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
+    ap.add_argument("--frame-mem", default="registered", choices=["registered", "hostalloc"],
+                    help="serve: page-locked memory of the host frames")
+    ap.add_argument("--mask-mem", default="hostalloc", choices=["registered", "hostalloc"],
+                    help="serve: page-locked memory of the host masks")
+    ap.add_argument("--launch", default="",
+                    help="profile case: launch shape 'k1_threads,k2_threads,k2_ctas_per_sm' (cog_set_launch)")
     ap.add_argument("--sample", action="store_true",
                     help="hd: confidence-based temporal sampling on (saturated pixels every 4 frames)")
     ap.add_argument("--mode1", action="store_true",
@@ -1265,7 +1367,7 @@ def main():
         import __graft_entry__
         __graft_entry__.build()
         r = {"batch64": run_batch, "serve": run_serve, "clip": run_clip,
-             "group": run_group, "profile": run_profile_case}.get(args.workload, run_ours)(
+             "group": run_group, "profile": run_profile_case, "h2d": run_h2d}.get(args.workload, run_ours)(
             args, rank, local_rank, world)
     if r is not None and rank == 0:
         print(json.dumps(r), flush=True)

@@ -512,16 +512,18 @@ cog_status cog_profile_end(cog_ctx *ctx, double *stage01_ms, double *stage2_ms, 
  * the process. */
 cog_status cog_set_l2_fetch_bytes(int32_t bytes);
 
-/* Page-locked host memory for frames and masks that the copy engines move
- * (cog_apply_host_frames, the frame server): anonymous memory, zeroed, then
- * locked with cudaHostRegister; cog_host_free unlocks and unmaps it.  On the
- * Grace host of a GB300, host-to-device copies out of such memory ran at
- * 158-180 GB/s from its first use, where memory from cudaHostAlloc ran at
- * 7 GB/s on a first pass over 3.6 GB and at 53-88 GB/s afterwards.  Any
- * size (rounded up to whole pages); COG_ERR_OOM if the mapping fails,
- * COG_ERR_CUDA if it cannot be locked; cog_host_free of a pointer not from
- * cog_host_alloc returns COG_ERR_INVALID_ARG.  Thread-safe.  The library
- * has no counterpart in the paper; this is deployment plumbing. */
+/* Page-locked host memory for frames that the copy engines move to the
+ * device (cog_apply_host_frames, the frame server): anonymous memory aligned
+ * to the kernel's transparent huge page size, advised to use huge pages,
+ * zeroed, then locked with cudaHostRegister; cog_host_free unlocks and
+ * unmaps it.  On the Grace host of a GB300, host-to-device copies out of
+ * such memory ran at 160-180 GB/s from its first use, where memory from
+ * cudaHostAlloc, or locked memory of small pages on a fragmented host, ran
+ * at 4-10 GB/s on a pass over 3.6 GB of frames.  Any size (rounded up to
+ * whole huge pages); COG_ERR_OOM if the mapping fails, COG_ERR_CUDA if it
+ * cannot be locked; cog_host_free of a pointer not from cog_host_alloc
+ * returns COG_ERR_INVALID_ARG.  Thread-safe.  Deployment plumbing; the
+ * paper has no counterpart. */
 cog_status cog_host_alloc(size_t bytes, void **out);
 cog_status cog_host_free(void *ptr);
 

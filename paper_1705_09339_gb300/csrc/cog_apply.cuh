@@ -676,18 +676,20 @@ __device__ __forceinline__ void k2_cta(const ApplyArgs &A, uint32_t cta, uint32_
 }
 
 // The same walk over stream A's survivor queue, software-pipelined for a
-// CTA that takes many survivors per thread (the batched step): each thread
-// loads queue entries two survivors ahead into registers, and copies the
-// next survivor's record, its three prior words (and with COG_MODE1 its
-// stage-1 record) into its own shared-memory slot with cp.async while it
-// runs the mixture step of the current one.  No thread reads another's
-// slot, so the per-thread copy groups need no barrier.
+// CTA that takes many survivors per thread (the batched step).  While a
+// thread runs the mixture step of its current survivor, cp.async copies
+// into its own shared slots the queue entry two survivors ahead and, from
+// the entry already there, the next survivor's record, its three prior
+// words (and with COG_MODE1 its stage-1 record).  Nothing is held in
+// registers across survivors, and no thread reads another's slots, so the
+// per-thread copy groups need no barrier.
 template <typename T, int K, int TPB, int V> struct K2Pipe {
     static constexpr bool PC = V == 1, M1 = V == 2;
     static constexpr int RNV = RecSel<T, K, PC>::NV;
     static constexpr int SNV = M1 ? S1Rec<T>::NV : 0;
     static constexpr int W = RNV + SNV + 1;   // uint4 words per slot: record, stage-1 record, prior words
     uint4 slot[2][W][TPB];                    // [buffer][word][thread]: consecutive threads, consecutive words
+    uint4 ent[3][TPB];                        // queue entries of three consecutive survivors
 };
 
 template <typename T, int K, int TPB, int V>
@@ -743,32 +745,46 @@ __device__ __forceinline__ void k2_cta_pipe(const ApplyArgs &A, uint32_t cta, ui
     const bool flag = flag_s;
     const uint32_t nq = segp_s[QSEG];
     const uint32_t stride = ncta * TPB;
-    // queue entry of flat index q; x = 0xffffffff marks a missing entry
-    auto load_entry = [&](uint32_t q) -> uint4 {
-        if (q >= nq) return make_uint4(0xffffffffu, 0, 0, 0);
+    // copy the queue entry of flat index q into entry slot j; false if
+    // there is none
+    auto issue_entry = [&](uint32_t q, int j) -> bool {
+        if (q >= nq) return false;
         int lo = 0;
 #pragma unroll
         for (int step = QSEG / 2; step >= 1; step >>= 1)
             if (segp_s[lo + step] <= q) lo += step;
-        if (!in_bounds(ctl, q - segp_s[lo], (uint64_t)A.s.qseg_cap, DBG_K2_QUEUE)) return make_uint4(0xffffffffu, 0, 0, 0);
-        uint4 e = __ldcg(A.s.queue + (int64_t)lo * A.s.qseg_cap + (q - segp_s[lo]));
-        if (!in_bounds(ctl, (uint64_t)e.x, (uint64_t)dp.P, DBG_K2_PIXEL)) e.x = 0xffffffffu;
-        return e;
+        if (!in_bounds(ctl, q - segp_s[lo], (uint64_t)A.s.qseg_cap, DBG_K2_QUEUE)) return false;
+        cp_async16(&S.ent[j][tid], A.s.queue + (int64_t)lo * A.s.qseg_cap + (q - segp_s[lo]));
+        return true;
+    };
+    // copy the data of the survivor whose entry is in slot j into buffer bb
+    auto issue_rec = [&](int j, int bb) -> bool {
+        const uint4 e = S.ent[j][tid];
+        if (!in_bounds(ctl, (uint64_t)e.x, (uint64_t)dp.P, DBG_K2_PIXEL)) return false;
+        k2_issue_copies<T, K, TPB, V>(A, S, bb, e);
+        return true;
     };
     const uint32_t q0 = cta * TPB + tid;
-    uint4 ea = load_entry(q0), eb = load_entry(q0 + stride);
-    if (ea.x != 0xffffffffu) k2_issue_copies<T, K, TPB, V>(A, S, 0, ea);
+    uint32_t ev = 0, rv = 0;   // bit j: entry slot j / record buffer j holds a survivor
+    ev |= issue_entry(q0, 0) ? 1u : 0u;
+    ev |= issue_entry(q0 + stride, 1) ? 2u : 0u;
+    cp_async_commit();
+    cp_async_wait<0>();
+    if ((ev & 1u) && issue_rec(0, 0)) rv |= 1u;
     cp_async_commit();
     uint32_t cbg = 0, cfg = 0, cil = 0;
-    int b = 0;
-    for (uint32_t q = q0; q < nq; q += stride, b ^= 1) {
-        const uint4 ec = load_entry(q + 2 * stride);
-        if (eb.x != 0xffffffffu) k2_issue_copies<T, K, TPB, V>(A, S, b ^ 1, eb);
+    int j = 0, b = 0;          // entry slot and record buffer of the current survivor
+    for (uint32_t q = q0; q < nq; q += stride) {
+        cp_async_wait<0>();    // the current survivor's data and the next one's entry
+        const int j1 = j == 2 ? 0 : j + 1, j2 = j1 == 2 ? 0 : j1 + 1;
+        ev &= ~(1u << j2);
+        if (issue_entry(q + 2 * stride, j2)) ev |= 1u << j2;
+        rv &= ~(1u << (b ^ 1));
+        if ((ev >> j1 & 1u) && issue_rec(j1, b ^ 1)) rv |= 1u << (b ^ 1);
         cp_async_commit();
-        cp_async_wait<1>();   // this survivor's copies (the group before the one just committed)
-        if (ea.x != 0xffffffffu) {
+        if (rv >> b & 1u) {
             S2In<T, K, PP::PC> a;
-            a.e = ea;
+            a.e = S.ent[j][tid];
 #pragma unroll
             for (int i = 0; i < PP::RNV; i++) a.rec[i] = S.slot[b][i][tid];
             if constexpr (PP::M1) {
@@ -780,7 +796,7 @@ __device__ __forceinline__ void k2_cta_pipe(const ApplyArgs &A, uint32_t cta, ui
             const bool four = dp.kde_bits == 4;
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                const uint32_t v = (ea.y >> (8 * c)) & 0xffu;
+                const uint32_t v = (a.e.y >> (8 * c)) & 0xffu;
                 const uint32_t byte = four ? (v >> 1) : v;   // the byte's offset within the row
                 const uint32_t x = (wv[c] >> (8 * (byte & 3u))) & 0xffu;   // rows start word-aligned
                 a.qk[c] = four ? 17u * ((x >> ((v & 1u) << 2)) & 15u) : x;
@@ -790,8 +806,8 @@ __device__ __forceinline__ void k2_cta_pipe(const ApplyArgs &A, uint32_t cta, ui
             else st = s2_finish<T, K, PP::M1>(A, a, flag);
             cbg += st == COG_ST_GMM_BG; cfg += st == COG_ST_FG; cil += st == COG_ST_ILLUM;
         }
-        ea = eb;
-        eb = ec;
+        j = j1;
+        b ^= 1;
     }
     cp_async_wait<0>();
     cbg = __reduce_add_sync(0xffffffffu, cbg);
@@ -885,8 +901,14 @@ __global__ void __launch_bounds__(TPB, K1_THREADS_PER_SM / TPB) stage01_batch_ke
 }
 
 // The mixture-stage CTAs are split among the active streams only.
+// Registers of the batched mixture stage.  Warps get registers per SM
+// sub-partition (16K each), so 72 registers fit 7 warps (14 CTAs of 64
+// threads per SM) and 96 fit 5 (10 CTAs), where 97-112 fit 4 (8 CTAs):
+// K <= 3 at 72, K = 4, 5 at 96, larger K as the compiler chooses.
+template <int K> constexpr int k2_batch_maxreg() { return K <= 3 ? 72 : (K <= 5 ? 96 : 255); }
+
 template <typename T, int K, int TPB, int V>
-__global__ void __launch_bounds__(TPB) stage2_batch_kernel(const BatchGroupDev G)
+__global__ void __launch_bounds__(TPB) __maxnreg__(k2_batch_maxreg<K>()) stage2_batch_kernel(const BatchGroupDev G)
 {
     grid_launch_dependents();
     grid_wait_prior();

@@ -25,34 +25,50 @@ from . import cog
 
 
 class PinnedArena:
-    """Page-locked host memory handed out from a few large blocks of
-    cog_host_alloc (anonymous memory locked with cudaHostRegister).  Frames
-    and masks that the copy engines move every step come from here: on the
-    GB300's Grace host, copies out of such memory keep 160-180 GB/s from the
-    first use, where cudaHostAlloc memory (one pinned tensor per frame) ran
-    at 7-90 GB/s and stalled single uploads for tens of milliseconds."""
+    """Page-locked host memory handed out from a few large blocks, either of
+    cog_host_alloc (kind "registered": huge-page memory locked with
+    cudaHostRegister) or of cudaHostAlloc (kind "hostalloc", through torch).
+    On the GB300's Grace host, host-to-device copies out of registered
+    huge-page memory keep 160-180 GB/s from the first use, where
+    cudaHostAlloc memory ran at 4-90 GB/s from box to box and stalled single
+    uploads for tens of milliseconds."""
 
-    def __init__(self, chunk_bytes: int = 256 << 20):
+    def __init__(self, chunk_bytes: int = 1 << 30, kind: str = "registered"):
         import ctypes
         import torch
+        assert kind in ("registered", "hostalloc")
         self.torch, self.ctypes = torch, ctypes
         self.chunk = chunk_bytes
-        self.blocks = []         # (address, tensor over the block)
+        self.kind = kind
+        self.blocks = []         # (address or None, tensor over the block)
         self.off = 0
+
+    def _grow(self, n):
+        torch, ctypes = self.torch, self.ctypes
+        if self.kind == "registered":
+            addr = cog.cog_host_alloc(n)
+            arr = np.ctypeslib.as_array(ctypes.cast(addr, ctypes.POINTER(ctypes.c_uint8)), shape=(n,))
+            self.blocks.append((addr, torch.from_numpy(arr)))
+        else:
+            self.blocks.append((None, torch.empty(n, dtype=torch.uint8, pin_memory=True)))
+        self.off = 0
+
+    def reserve(self, nbytes: int):
+        """Allocates now one block that holds nbytes more: a process that
+        knows its frame buffers up front takes them from one large block
+        before its memory fragments."""
+        if not self.blocks or self.off + nbytes > self.blocks[-1][1].numel():
+            self._grow(max(self.chunk, nbytes))
 
     def take(self, shape, dtype=None):
         """A page-locked tensor of `shape` (uint8 unless given), 256-byte
         aligned, valid until release()."""
-        torch, ctypes = self.torch, self.ctypes
+        torch = self.torch
         dtype = dtype or torch.uint8
         nbytes = int(np.prod(shape)) * torch.empty((), dtype=dtype).element_size()
         span = (nbytes + 255) // 256 * 256
         if not self.blocks or self.off + span > self.blocks[-1][1].numel():
-            n = max(self.chunk, span)
-            addr = cog.cog_host_alloc(n)
-            arr = np.ctypeslib.as_array(ctypes.cast(addr, ctypes.POINTER(ctypes.c_uint8)), shape=(n,))
-            self.blocks.append((addr, torch.from_numpy(arr)))
-            self.off = 0
+            self._grow(max(self.chunk, span))
         t = self.blocks[-1][1][self.off:self.off + nbytes]
         self.off += span
         return t.view(dtype).view(shape)
@@ -60,7 +76,8 @@ class PinnedArena:
     def release(self):
         """Frees every block; no tensor from take() may be used afterwards."""
         for addr, _ in self.blocks:
-            cog.cog_host_free(addr)
+            if addr is not None:
+                cog.cog_host_free(addr)
         self.blocks = []
         self.off = 0
 
@@ -81,7 +98,8 @@ class FrameServer:
     # with keep_masks, results[camera index] lists (seq, mask) of the camera
     # now at that index (a camera that left keeps its own in Camera.masks)
 
-    def __init__(self, device=None, reserve_bytes: int = 4 << 30, keep_masks: bool = False):
+    def __init__(self, device=None, reserve_bytes: int = 4 << 30, keep_masks: bool = False,
+                 frame_memory: str = "registered", mask_memory: str = "hostalloc"):
         import torch
         self.torch = torch
         self.dev = torch.device(device or "cuda")
@@ -89,7 +107,10 @@ class FrameServer:
         self.cameras: list[Camera | None] = []   # by stream index; None: the camera left
         self.refused: list[tuple] = []
         self.keep_masks = keep_masks
-        self.arena = PinnedArena()   # mask rings; callers may take their frame buffers here too
+        # callers take their frame buffers from `arena`; the mask rings come
+        # from `mask_arena`
+        self.arena = PinnedArena(kind=frame_memory)
+        self.mask_arena = PinnedArena(kind=mask_memory)
         self.results = collections.defaultdict(list)   # camera id -> (seq, mask) when keep_masks
         self._keep = []          # host buffers referenced by queued frames
         self.srv = None
@@ -113,7 +134,7 @@ class FrameServer:
         cog.cog_train_prior(cam.ctx, train_frames, train_frames.shape[0])
         cog.cog_sync(cam.ctx)
         if not self.keep_masks:
-            cam.mask_ring = [self.arena.take((height, width)) for _ in range(self.RING)]
+            cam.mask_ring = [self.mask_arena.take((height, width)) for _ in range(self.RING)]
         if self.srv is not None:
             try:
                 idx = cog.cog_server_add(self.srv, cam.ctx)
@@ -207,3 +228,4 @@ class FrameServer:
                 c.mask_ring = []
         self.cameras = []
         self.arena.release()
+        self.mask_arena.release()
