@@ -390,15 +390,8 @@ def run_ours(args, rank, local_rank, world):
     # frames -- the frames the device-timed pass above ran -- so the model
     # advances through the stream as it would live
     n_e2e = max(1, args.steps // 3)
-    # frames in registered huge-page memory (cog_host_alloc), masks in
-    # cudaHostAlloc memory: the kinds the serving path measured fastest
-    from paper_1705_09339_gb300.serve import PinnedArena
-    e2e_frames, e2e_masks = PinnedArena(kind="registered"), PinnedArena(kind="hostalloc")
-    n_host = args.warmup + 3 * n_e2e
-    e2e_frames.reserve(n_host * P * 3 + 256)
-    host_frames = e2e_frames.take((n_host, H_, W_, 3))
-    host_frames.copy_(test[:n_host].cpu())
-    host_masks = e2e_masks.take((n_host, H_, W_))
+    host_frames = test[:args.warmup + 3 * n_e2e].cpu().pin_memory()
+    host_masks = torch.empty((args.warmup + 3 * n_e2e, H_, W_), dtype=torch.uint8).pin_memory()
     hf, hm = host_frames.numpy(), host_masks.numpy()
     ctx_e = cog.cog_create(p_cog, stream.cuda_stream)
     tr2 = gs.render(0, N_TRAIN)
@@ -436,8 +429,6 @@ def run_ours(args, rank, local_rank, world):
     cog.cog_destroy(ctx_e)
     cog.cog_destroy(ctx_s)
     del host_frames, host_masks, hf, hm
-    e2e_frames.release()
-    e2e_masks.release()
 
     result = None
     if rank == 0:
@@ -513,8 +504,7 @@ def run_ours(args, rank, local_rank, world):
             "e2e": {"value": round(world * P * n_e2e / t_e2e / 1e6, 1), "unit": UNIT,
                     "h2d_bytes_per_step": P * 3, "d2h_bytes_per_step": P, "steps": n_e2e,
                     "rounds": [round(world * P * n_e2e / t / 1e6, 1) for t in t_rounds],
-                    "api": "cog_apply_host_frames (host frames in page-locked huge-page memory from "
-                           "cog_host_alloc, masks out into cudaHostAlloc memory; uploads and downloads "
+                    "api": "cog_apply_host_frames (pinned host frames in, masks out; uploads and downloads "
                            "overlap the kernels; returns when every mask is on the host)",
                     "protocol": f"three rounds of {n_e2e} consecutive frames each (the device-timed frames), "
                                 f"never repeated, after {args.warmup} untimed frames through the same "
@@ -712,12 +702,8 @@ def run_clip(args, rank, local_rank, world):
     # end to end: each step copies its 32 frames from pinned host memory,
     # runs the clip and copies the 32 masks back
     n_e2e = min(args.steps, 8)
-    from paper_1705_09339_gb300.serve import PinnedArena
-    e2e_frames, e2e_masks = PinnedArena(kind="registered"), PinnedArena(kind="hostalloc")
-    e2e_frames.reserve(n_e2e * T * P * 3 + 256)
-    hf = e2e_frames.take((n_e2e * T, H_, W_, 3))
-    hf.copy_(test[args.warmup * T:(args.warmup + n_e2e) * T].cpu())
-    hm = e2e_masks.take((n_e2e * T, H_, W_))
+    hf = test[args.warmup * T:(args.warmup + n_e2e) * T].cpu().pin_memory()
+    hm = torch.empty((n_e2e * T, H_, W_), dtype=torch.uint8).pin_memory()
     dfr = torch.empty((T, H_, W_, 3), dtype=torch.uint8, device=dev)
     dmk = torch.empty((T, H_, W_), dtype=torch.uint8, device=dev)
     ctx_e = cog.cog_create(p_cog, stream.cuda_stream)
@@ -735,9 +721,6 @@ def run_clip(args, rank, local_rank, world):
         stream.synchronize()
     t_e2e = max_over_ranks([time.perf_counter() - t0], world, dev)[0]
     cog.cog_destroy(ctx_e)
-    del hf, hm
-    e2e_frames.release()
-    e2e_masks.release()
 
     result = None
     if rank == 0:

@@ -355,7 +355,7 @@ def test_caller_owned_state_and_host_buffers():
     ref.close()
 
 
-@pytest.mark.parametrize("pinned", [True, False])
+@pytest.mark.parametrize("pinned", [True, False, "registered"])
 def test_host_frames_pipeline_equals_device_apply(pinned):
     # cog_apply_host_frames overlaps uploads and downloads with the kernels
     # through two device slots; results must equal cog_apply on device
@@ -373,7 +373,21 @@ def test_host_frames_pipeline_equals_device_apply(pinned):
     g.train(fr[:NT])
     host = torch.from_numpy(np.ascontiguousarray(fr[NT:]).reshape(NF, H, W, 3))
     masks = torch.zeros((NF, H, W), dtype=torch.uint8)
-    if pinned:
+    blocks = []
+    if pinned == "registered":
+        # frames and masks in cog_host_alloc memory (huge pages locked with
+        # cudaHostRegister)
+        import ctypes
+        views = []
+        for t in (host, masks):
+            addr = cog.cog_host_alloc(t.numel())
+            blocks.append(addr)
+            a = np.ctypeslib.as_array(ctypes.cast(addr, ctypes.POINTER(ctypes.c_uint8)), shape=(t.numel(),))
+            v = torch.from_numpy(a[:t.numel()]).view(t.shape)
+            v.copy_(t)
+            views.append(v)
+        host, masks = views
+    elif pinned:
         host, masks = host.pin_memory(), masks.pin_memory()
     cog.cog_apply_host_frames(g.ctx, host.numpy(), masks.numpy())
     assert np.array_equal(masks.numpy().reshape(NF, -1), rm)
@@ -384,6 +398,11 @@ def test_host_frames_pipeline_equals_device_apply(pinned):
     cog.cog_apply_host_frames(g.ctx, host.numpy()[:5].copy(), masks.numpy()[:5].copy())
     assert cog.cog_info(g.ctx)[0] == NF + 5
     ref.close(); g.close()
+    del host, masks
+    for addr in blocks:
+        cog.cog_host_free(addr)
+    with pytest.raises(cog.CogError):
+        cog.cog_host_free(blocks[0] if blocks else 8)   # freed already / never allocated
 
 
 def test_mode1_stream_matches_oracle():
