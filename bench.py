@@ -823,6 +823,31 @@ def run_batch(args, rank, local_rank, world):
             ctxs.append(c)
             ctxg.append(g)
     P_tot = sum(w * h for w, h, _, _ in specs)
+    # launch shape of the batch kernels (each group takes its first stream's
+    # cog_set_launch shape when the batch is created): the fastest of four
+    # over three steps each, on the warm-up frames
+    shape, chosen = (128, 64, 0), "default"
+    if args.autotune:
+        best = None
+        for sh in ((128, 64, 0), (256, 64, 0), (128, 128, 0), (256, 128, 0)):
+            for c in ctxs:
+                cog.cog_set_launch(c, *sh)
+            bt = cog.cog_batch_create(ctxs, stream.cuda_stream)
+            with torch.cuda.stream(stream):
+                cog.cog_batch_apply(bt, [f[0] for f in frames], masks)
+                a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                for t in range(1, 4):
+                    cog.cog_batch_apply(bt, [f[t % max(1, args.warmup)] for f in frames], masks)
+                e.record(stream)
+            cog.cog_batch_sync(bt)
+            cog.cog_batch_destroy(bt)
+            ms_sh = a.elapsed_time(e)
+            if best is None or ms_sh < best[0]:
+                best = (ms_sh, sh)
+        shape, chosen = best[1], "autotuner (4 shapes, 3 steps each on the warm-up frames)"
+        for c in ctxs:
+            cog.cog_set_launch(c, *shape)
     b = cog.cog_batch_create(ctxs, stream.cuda_stream)
     with torch.cuda.stream(stream):
         for t in range(args.warmup):
@@ -889,6 +914,8 @@ def run_batch(args, rank, local_rank, world):
                    "streams": NS, "pixels_per_step": P_tot, "size_mix": mix,
                    "K_mix": {"3": sum(1 for s in specs if s[2] == 3), "5": sum(1 for s in specs if s[2] == 5)},
                    "l2": "working set per step far larger than L2 (no flush)", "l2_fetch_bytes": args.l2_fetch,
+                   "launch_shape": {"k1_threads": shape[0], "k2_threads": shape[1], "k2_ctas_per_sm": shape[2],
+                                    "chosen_by": chosen},
                    "parallelism": f"stream-sharded x{world}"},
         "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4),
                      "traffic": None, "kernel": "whole step (all streams' stage01 + stage2 launches)",
