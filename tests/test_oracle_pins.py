@@ -530,6 +530,32 @@ def test_hand_confidence_prior_term_4bit():
     assert abs(o.state.conf[0] - float(Fraction(7, 16) + c_rest / Fraction(2, 5) / 8)) <= 1e-15
 
 
+@pytest.mark.parametrize("flags", [ORC_FD | ORC_RGA | ORC_CONF | ORC_ILLUM, ORC_CONF])
+def test_kde4_equals_kde8_at_17_times_the_levels(flags):
+    # the prior enters as q / Q: a 4-bit level q and the 8-bit level 17 q
+    # are the same fraction of the peak (q/15 = 17q/255, both divisions
+    # correctly rounded from one rational), and 255 q < 15 q_null exactly
+    # when 17 q < q_null.  Runs from one random state, the 4-bit one with
+    # levels q and the 8-bit one with 17 q, must agree bit for bit.
+    from cog_harness import random_frame, random_state, set_oracle_state
+    rng = np.random.default_rng(21)
+    W, H, K = 31, 17, 3
+    P = W * H
+    st = random_state(rng, P, K, kde_bits=4)
+    st8 = dict(st, kde=(17 * st["kde"].astype(np.uint16)).astype(np.uint8))
+    runs = []
+    for bits, state in ((4, st), (8, st8)):
+        o = Oracle(dict(default_params(W, H, K), flags=flags, kde_bits=bits))
+        set_oracle_state(o, state)
+        runs.append(o)
+    frames = [random_frame(np.random.default_rng(100 + t), st) for t in range(6)]
+    for f in frames:
+        r4, r8 = runs[0].apply(f), runs[1].apply(f)
+        assert np.array_equal(r4[0], r8[0]) and np.array_equal(r4[1], r8[1])
+    for k in ("w", "mu", "var", "rga_m", "rga_v", "conf", "label"):
+        assert np.array_equal(getattr(runs[0].state, k), getattr(runs[1].state, k)), k
+
+
 def test_kde_bits_other_than_8_or_4_rejected():
     with pytest.raises(Exception):
         one_pixel(kde_bits=6).train(np.zeros((3, 1, 3), np.uint8))
