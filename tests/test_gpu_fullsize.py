@@ -32,13 +32,14 @@ def stream():
     return sc, gs, pix
 
 
-@pytest.mark.parametrize("dtype", ["f32", "f16"])
-def test_full_size_sampled_pixels_match_oracle(stream, dtype):
+@pytest.mark.parametrize("dtype,bits", [("f32", 8), ("f16", 8), ("f16", 4)])
+def test_full_size_sampled_pixels_match_oracle(stream, dtype, bits):
+    # bits: the scene prior's width (kde_bits), 8 or 4
     import oracle
     from paper_1705_09339_gb300 import cog
     sc, gs, pix = stream
     flags = 1 | 2 | 4                       # FD | RGA | CONF (no illumination coupling)
-    d = params(W, H, K, flags=flags)
+    d = params(W, H, K, flags=flags, kde_bits=bits)
     p = cog.cog_default_params(W, H, K, state_dtype=dtype)
     for k, v in d.items():
         if k not in ("width", "height", "K"):
