@@ -11,8 +11,10 @@
  * holds none of the method's arithmetic.
  *
  * Every routine follows the paper's passage it names:
- *   - scene prior (kernel density over the N training frames): Sec. 2,
- *     "Scene Prior in Background Model" and Eq. 2;
+ *   - scene prior (kernel density over the N training frames, quantised to
+ *     255 or, with kde_bits = 4, to 15 levels of its peak, and entering the
+ *     confidence as the fraction q / Q of the peak): Sec. 2, "Scene Prior in
+ *     Background Model" and Eq. 2;
  *   - residue classes -> confidence weights: Sec. 2, "Determining Learning
  *     Rate Hyper-parameters";
  *   - Stauffer-Grimson mixture update: Eq. 2 (with the garbled variance line
