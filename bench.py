@@ -938,8 +938,8 @@ def run_serve(args, rank, local_rank, world):
     four other sizes), K=5, FP16 state resident on the device, 100 training
     frames each; each camera emits frames with exponential inter-arrival
     times of mean 1/30 s for `--duration` seconds.  Frames come from a pool
-    of eight pinned host frames per camera, carved from the server's pinned
-    arena (a few large page-locked allocations).  The server admits cameras by
+    of eight host frames per camera in one block of the server's arena
+    (registered huge-page memory) taken after the cameras are admitted.  The server admits cameras by
     free HBM; the native server (cog_server_*) runs continuous batching
     (cog_batch_apply_active).  Reports p50/p99 latency from submission to
     mask in host memory, and aggregate Mpixel/s."""
@@ -964,20 +964,25 @@ def run_serve(args, rank, local_rank, world):
         sizes.append(SIZES[[0, 1, 3, 4][len(sizes) % 4]])
     rng.shuffle(sizes)
     srv = FrameServer(dev, reserve_bytes=8 << 30, frame_memory=args.frame_mem, mask_memory=args.mask_mem)
-    # every camera's frame pool from one block taken before anything else
-    # (huge pages are plentiful before the process's memory fragments)
-    srv.arena.reserve(sum(8 * ((w * h * 3 + 255) // 256 * 256) for (w, h) in sizes))
-    pools = {}
+    staged = {}
     for i, (w, h) in enumerate(sizes):
         sc = Scene(w, h, 7000 + 1000 * rank + i, kind="dynamic", n_train=100, fg_frac=float(rng.uniform(0.01, 0.05)))
         gs = GpuScene(sc, dev)
         cam = srv.admit(w, h, 5, "f16", gs.render(0, 100))
         if cam is None:
             continue
-        pool = gs.render(100, 8).cpu()
-        pools[cam.id] = [srv.arena.take((h, w, 3)) for _ in range(8)]
+        staged[cam.id] = gs.render(100, 8).cpu()
+    # every camera's frame pool in one block of page-locked memory taken
+    # after the cameras' device memory: memory locked after the device
+    # allocations kept 158-181 GB/s host-to-device in every process measured,
+    # memory locked before them often far less
+    srv.arena.reserve(sum(8 * ((t.shape[1] * t.shape[2] * 3 + 255) // 256 * 256) for t in staged.values()))
+    pools = {}
+    for cid, pool in staged.items():
+        pools[cid] = [srv.arena.take(tuple(pool.shape[1:])) for _ in range(8)]
         for j in range(8):
-            pools[cam.id][j].copy_(pool[j])
+            pools[cid][j].copy_(pool[j])
+    del staged
     h2d = h2d_probe(torch, dev, [f for cid in pools for f in pools[cid]])
     h2d["arena_huge_kb"] = [_huge_kb(int(t.data_ptr()), t.numel()) for _, t in srv.arena.blocks]
     # everything allocated so far lives for the whole run: keep it out of
