@@ -517,9 +517,10 @@ cog_status cog_set_l2_fetch_bytes(int32_t bytes);
  * to the kernel's transparent huge page size, advised to use huge pages,
  * zeroed, then locked with cudaHostRegister; cog_host_free unlocks and
  * unmaps it.  On the Grace host of a GB300, host-to-device copies out of
- * such memory ran at 160-180 GB/s from its first use, where memory from
- * cudaHostAlloc, or locked memory of small pages on a fragmented host, ran
- * at 4-10 GB/s on a pass over 3.6 GB of frames.  Any size (rounded up to
+ * such memory taken after the process's large device allocations ran at
+ * 150-180 GB/s from its first use, where memory from cudaHostAlloc, or
+ * locked memory taken before those allocations, ran at 2-12 GB/s on a first
+ * pass over 3.6 GB of frames in some processes.  Any size (rounded up to
  * whole huge pages); COG_ERR_OOM if the mapping fails, COG_ERR_CUDA if it
  * cannot be locked; cog_host_free of a pointer not from cog_host_alloc
  * returns COG_ERR_INVALID_ARG.  Thread-safe.  Deployment plumbing; the

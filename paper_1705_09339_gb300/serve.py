@@ -54,9 +54,10 @@ class PinnedArena:
         self.off = 0
 
     def reserve(self, nbytes: int):
-        """Allocates now one block that holds nbytes more: a process that
-        knows its frame buffers up front takes them from one large block
-        before its memory fragments."""
+        """Allocates now one block that holds nbytes more, so that buffers
+        taken next come from one large block.  Take it after the process's
+        large device allocations: blocks locked before them copied at a few
+        GB/s in some processes, blocks locked after them at 150-180 GB/s."""
         if not self.blocks or self.off + nbytes > self.blocks[-1][1].numel():
             self._grow(max(self.chunk, nbytes))
 
